@@ -1,0 +1,478 @@
+/*
+ * CPU oracle for the CDEF hot path (arXiv 1602.05975).
+ *
+ * TEST INFRASTRUCTURE ONLY -- see cdef_ref.h.  Plain C99, int64 arithmetic,
+ * one loop per sum of the paper, no vectorisation, no factoring, no code
+ * shared with the CUDA library.
+ *
+ * Where the paper is silent, garbled or at odds with itself, this file
+ * follows one written reading, named R1..R16 at the point of use:
+ *   R1  line geometry of Fig. 1 (figure missing)
+ *   R2  bit-depth reduction for the search is an arithmetic right shift
+ *   R3  eq. 13 with floor(log2 floor(v / 2^16)) read as 0 when v < 2^16
+ *   R4  contrast adjustment and tap parity on the unscaled strength, then
+ *       bit-depth scaling (section 3.2)
+ *   R5  chroma damping D-1, raised to floor(log2 S_p) for the whole block
+ *   R7  eq. 7, d < 0 branch read as the mirror of the d >= 0 branch
+ *   R8  primary/secondary tap positions of Figs. 3/4 (figures missing)
+ *   R9  weights in sixteenths: primary (near, far) = (4,2) even, (3,3) odd;
+ *       secondary (near, far) = (2,1)
+ *   R11 the clipping range includes the filtered pixel itself
+ *   R12 taps outside the frame give f = 0 and are left out of the clip range
+ *   R13 the secondary cross uses the found direction even when S_p = 0
+ *   R15 one preset picks both the luma and the chroma pair of a block
+ *   R16 greedy order and tie-breaks of the preset search
+ *
+ * Parity status: cdef_ref_line_number (R1) is pinned only through the counts
+ * and cardinalities the paper prints and through geometric properties; the
+ * direction numbering beyond d = 0/1 is unpinned.  The tap positions (R8)
+ * are pinned to R1's geometry by tests, and the secondary weights and the
+ * sixteenths normalisation (R9) are parity unpinned: their figure is missing.
+ */
+#include "cdef_ref.h"
+
+#include <stdlib.h>
+
+static int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+static int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+/* floor(log2 s) for s >= 1, by counting halvings. */
+static int64_t floor_log2(int64_t s)
+{
+    int64_t l = 0;
+    while (s > 1) {
+        s /= 2;
+        l++;
+    }
+    return l;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 2: direction search                                              */
+/* ------------------------------------------------------------------------ */
+
+/* R1.  Fig. 1 gives, for each of the 8 directions, the line number k of
+ * every pixel of an 8x8 block; the figure is missing from the text.  The
+ * reading: d = 0 is the 45-degree up-right diagonal and each next direction
+ * turns clockwise by roughly 22.5 degrees, with the lines of the two
+ * in-between slopes stepping one row every two columns (or one column every
+ * two rows).  i is the row, j the column. */
+int cdef_ref_line_number(int d, int i, int j)
+{
+    switch (d) {
+    case 0: return i + j;              /*  45 deg, 15 lines */
+    case 1: return i + j / 2;          /*  26.6 deg, 11 lines */
+    case 2: return i;                  /*   0 deg (rows), 8 lines */
+    case 3: return 3 + i - j / 2;      /* -26.6 deg, 11 lines */
+    case 4: return 7 + i - j;          /* -45 deg, 15 lines */
+    case 5: return 3 - i / 2 + j;      /* -63.4 deg, 11 lines */
+    case 6: return j;                  /* -90 deg (columns), 8 lines */
+    case 7: return i / 2 + j;          /*  63.4 deg, 11 lines */
+    default: return -1;
+    }
+}
+
+/* Algorithm 1, first half: line sums partial[d][L], their cardinalities
+ * count[d][L], and s[d] = sum_L partial^2 * 840 / count (eq. 5 times 840,
+ * section 2: 840 is the least common multiple of the cardinalities 1..8). */
+void cdef_ref_direction_costs(const int32_t x[64], int64_t s[8])
+{
+    for (int d = 0; d < 8; d++) {
+        int64_t partial[15] = {0};
+        int64_t count[15] = {0};
+        for (int i = 0; i < 8; i++) {
+            for (int j = 0; j < 8; j++) {
+                int L = cdef_ref_line_number(d, i, j);
+                partial[L] += x[i * 8 + j];
+                count[L] += 1;
+            }
+        }
+        s[d] = 0;
+        for (int L = 0; L < 15; L++) {
+            if (count[L] > 0)
+                s[d] += partial[L] * partial[L] * (840 / count[L]);
+        }
+    }
+}
+
+/* Algorithm 1 on raw samples.  Section 2: 8-bit values are centred by -128;
+ * higher bit depths are downscaled to 8 bits first (R2: x >> (bd - 8)).
+ * The best direction is the first strict maximum of s[d]; the contrast is
+ * s[best] - s[(best + 4) mod 8]. */
+int cdef_ref_find_dir_block(const uint16_t *p, ptrdiff_t stride, int bitdepth,
+                            int64_t *contrast)
+{
+    int32_t x[64];
+    int64_t s[8];
+    for (int i = 0; i < 8; i++)
+        for (int j = 0; j < 8; j++)
+            x[i * 8 + j] = (int32_t)(p[i * stride + j] >> (bitdepth - 8)) - 128;
+    cdef_ref_direction_costs(x, s);
+    int best = 0;
+    for (int d = 0; d < 8; d++)
+        if (s[d] > s[best])
+            best = d;
+    if (contrast)
+        *contrast = s[best] - s[(best + 4) % 8];
+    return best;
+}
+
+int cdef_ref_find_dir(const uint16_t *luma, int w, int h, ptrdiff_t stride,
+                      int bitdepth, uint8_t *dir, int32_t *var)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8)
+        return -1;
+    if (bitdepth < 8 || bitdepth > 12)
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    for (int by = 0; by < bh; by++) {
+        for (int bx = 0; bx < bw; bx++) {
+            int64_t v = 0;
+            int d = cdef_ref_find_dir_block(luma + (ptrdiff_t)by * 8 * stride + bx * 8,
+                                            stride, bitdepth, &v);
+            dir[by * bw + bx] = (uint8_t)d;
+            var[by * bw + bx] = (int32_t)v;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3: the constrained non-linear filter                             */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 7.  For d >= 0: min(d, max(0, S - floor(d / 2^(D - floor(log2 S))))).
+ * R7: the printed d < 0 branch uses a ceiling, which would break the stated
+ * anti-symmetry around d = 0; the reading is f(-d) = -f(d).  S = 0 gives 0
+ * (the filter tap is switched off and log2 0 is never taken). */
+int64_t cdef_ref_constrain(int64_t diff, int64_t strength, int64_t damping)
+{
+    if (strength == 0)
+        return 0;
+    int64_t shift = damping - floor_log2(strength);
+    if (shift < 0)
+        return 0; /* excluded by D >= floor(log2 S); never reached */
+    int64_t scale = (int64_t)1 << shift;
+    if (diff >= 0)
+        return min64(diff, max64(0, strength - diff / scale));
+    return -min64(-diff, max64(0, strength - (-diff) / scale));
+}
+
+/* Eq. 13.  R3: for 2^10 <= v < 2^16 the term floor(log2 floor(v/2^16)) is
+ * log2 of zero; it is read as 0, so that the factor (4 + i) / 16 runs from
+ * 4/16 up to 16/16 as the contrast grows. */
+int cdef_ref_adjust_strength(int strength, int64_t contrast)
+{
+    if (contrast < 1024)
+        return 0;
+    int64_t q = contrast / 65536;
+    int64_t i = q > 0 ? min64(floor_log2(q), 12) : 0;
+    return (int)((strength * (4 + i) + 8) / 16);
+}
+
+/* Eq. 8: round(sum / 16) with ties away from zero (R9: the weights are in
+ * sixteenths). */
+int64_t cdef_ref_round16(int64_t sum)
+{
+    if (sum >= 0)
+        return (sum + 8) / 16;
+    return -((-sum + 8) / 16);
+}
+
+/* Section 3.2 per 8x8 block.
+ *  - luma S_p is adjusted by eq. 13 (chroma S_p is not);
+ *  - R4: the primary weights follow the parity of that unscaled value, and
+ *    both strengths are then scaled by 2^(bd-8), the damping offset by bd-8;
+ *  - R5: chroma damping is the luma damping minus one, and a damping below
+ *    floor(log2 S_p) is raised to it (worked example: chroma S_p = 15 with
+ *    luma D = 3 gives chroma D = 3). */
+void cdef_ref_block_params(int pri_raw, int sec_raw, int damping_luma,
+                           int is_chroma, int bitdepth, int64_t contrast,
+                           cdef_ref_eff_params *out)
+{
+    int pri = is_chroma ? pri_raw : cdef_ref_adjust_strength(pri_raw, contrast);
+    int64_t damping = is_chroma ? damping_luma - 1 : damping_luma;
+    if (pri > 0 && damping < floor_log2(pri))
+        damping = floor_log2(pri);
+    int shift8 = bitdepth - 8;
+    out->parity = pri & 1;
+    out->pri = (int64_t)pri << shift8;
+    out->sec = (int64_t)sec_raw << shift8;
+    out->damping = damping + shift8;
+}
+
+/* R8.  Fig. 3 (missing): the primary taps of direction d sit at distance 1
+ * and 2 along d, on both sides of the filtered pixel.  Offsets are
+ * (row, column).  The reading takes the pixels on the filtered pixel's own
+ * line of Fig. 1 at one and two steps along the line. */
+static const int tap_offset[8][2][2] = {
+    {{-1, 1}, {-2, 2}},
+    {{0, 1}, {-1, 2}},
+    {{0, 1}, {0, 2}},
+    {{0, 1}, {1, 2}},
+    {{1, 1}, {2, 2}},
+    {{1, 0}, {2, 1}},
+    {{1, 0}, {2, 0}},
+    {{1, 0}, {2, -1}},
+};
+
+/* R9.  Fig. 3 caption: for even strengths a = 2, b = 4; for odd ones
+ * a = b = 3; b is read as the near (distance 1) tap.  Fig. 4 (missing):
+ * secondary near 2, far 1.  All in sixteenths. */
+static const int pri_weight[2][2] = {{4, 2}, {3, 3}};
+static const int sec_weight[2] = {2, 1};
+
+/* Eq. 8-12 for one sample.  The primary taps follow d; the secondary taps
+ * form the cross of directions d+2 and d-2 (45 degrees either side, section
+ * 3.1; R13: d is used whatever S_p is).  R12: a tap outside the w x h frame
+ * contributes f = 0 and is not in the clip range.  R11: the clip range
+ * R of eq. 12 is every in-frame tap plus the filtered pixel. */
+int64_t cdef_ref_filter_sample(const uint16_t *plane, int w, int h,
+                               ptrdiff_t stride, int i, int j, int d,
+                               const cdef_ref_eff_params *e)
+{
+    int64_t x = plane[(ptrdiff_t)i * stride + j];
+    int64_t sum = 0;
+    int64_t ymin = x, ymax = x;
+    /* Primary taps: direction d, distances 1 and 2, both signs. */
+    for (int k = 0; k < 2; k++) {
+        for (int sign = -1; sign <= 1; sign += 2) {
+            int m = i + sign * tap_offset[d][k][0];
+            int n = j + sign * tap_offset[d][k][1];
+            if (m < 0 || m >= h || n < 0 || n >= w)
+                continue;
+            int64_t p = plane[(ptrdiff_t)m * stride + n];
+            sum += pri_weight[e->parity][k] * cdef_ref_constrain(p - x, e->pri, e->damping);
+            ymin = min64(ymin, p);
+            ymax = max64(ymax, p);
+        }
+    }
+    /* Secondary taps: directions d + 2 and d - 2 (mod 8), distances 1 and 2,
+     * both signs. */
+    for (int c = 0; c < 2; c++) {
+        int dd = c == 0 ? (d + 2) % 8 : (d + 6) % 8;
+        for (int k = 0; k < 2; k++) {
+            for (int sign = -1; sign <= 1; sign += 2) {
+                int m = i + sign * tap_offset[dd][k][0];
+                int n = j + sign * tap_offset[dd][k][1];
+                if (m < 0 || m >= h || n < 0 || n >= w)
+                    continue;
+                int64_t p = plane[(ptrdiff_t)m * stride + n];
+                sum += sec_weight[k] * cdef_ref_constrain(p - x, e->sec, e->damping);
+                ymin = min64(ymin, p);
+                ymax = max64(ymax, p);
+            }
+        }
+    }
+    /* Eq. 8 rounding, then the clip of eq. 9-12. */
+    int64_t y = x + cdef_ref_round16(sum);
+    return min64(ymax, max64(ymin, y));
+}
+
+/* Filters one plane.  sub = 0 for luma (8x8 blocks, 64x64 filter blocks),
+ * 1 for 4:2:0 chroma (4x4 blocks, 32x32 filter blocks; section 2: chroma
+ * takes the co-located luma direction). */
+static void filter_plane(const uint16_t *in, ptrdiff_t is, uint16_t *out,
+                         ptrdiff_t os, int pw, int ph, int sub, int bitdepth,
+                         const uint8_t *params, int fb_cols,
+                         const uint8_t *dir, const int32_t *var, int bw)
+{
+    int bs = 8 >> sub, fbs = 64 >> sub;
+    for (int i = 0; i < ph; i++) {
+        for (int j = 0; j < pw; j++) {
+            int b8 = (i / bs) * bw + (j / bs);
+            const uint8_t *pp = params + ((i / fbs) * fb_cols + (j / fbs)) * CDEF_REF_PARAM_BYTES;
+            cdef_ref_eff_params e;
+            if (sub == 0)
+                cdef_ref_block_params(pp[0], pp[1], pp[4], 0, bitdepth, var[b8], &e);
+            else
+                cdef_ref_block_params(pp[2], pp[3], pp[4], 1, bitdepth, var[b8], &e);
+            out[(ptrdiff_t)i * os + j] =
+                (uint16_t)cdef_ref_filter_sample(in, pw, ph, is, i, j, dir[b8], &e);
+        }
+    }
+}
+
+static int valid_params(const uint8_t *params, int nblocks)
+{
+    for (int b = 0; b < nblocks; b++) {
+        const uint8_t *p = params + b * CDEF_REF_PARAM_BYTES;
+        for (int pl = 0; pl < 2; pl++) {
+            int pri = p[2 * pl], sec = p[2 * pl + 1];
+            if (!(pri <= 15 || pri == 19))
+                return 0;
+            if (!(sec == 0 || sec == 1 || sec == 2 || sec == 4 || sec == 7))
+                return 0;
+        }
+        if (p[4] < 3 || p[4] > 6)
+            return 0;
+    }
+    return 1;
+}
+
+int cdef_ref_filter_frame(int w, int h, int bitdepth,
+                          const uint16_t *y, ptrdiff_t ys,
+                          const uint16_t *u, ptrdiff_t us,
+                          const uint16_t *v, ptrdiff_t vs,
+                          const uint8_t *params,
+                          const uint8_t *dir, const int32_t *var,
+                          uint16_t *oy, ptrdiff_t oys,
+                          uint16_t *ou, ptrdiff_t ous,
+                          uint16_t *ov, ptrdiff_t ovs)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    if (!valid_params(params, fb_cols * fb_rows))
+        return -1;
+    int bw = w / 8;
+    filter_plane(y, ys, oy, oys, w, h, 0, bitdepth, params, fb_cols, dir, var, bw);
+    filter_plane(u, us, ou, ous, w / 2, h / 2, 1, bitdepth, params, fb_cols, dir, var, bw);
+    filter_plane(v, vs, ov, ovs, w / 2, h / 2, 1, bitdepth, params, fb_cols, dir, var, bw);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 5: encoder search                                                */
+/* ------------------------------------------------------------------------ */
+
+/* The 4 signalled secondary strengths, in index order (section 3.2). */
+static const int sec_values[4] = {0, 1, 2, 4};
+
+/* Sum over the pixels of filter block (fby, fbx) of one plane of the squared
+ * error between the source and the decoded plane filtered with raw
+ * strengths (pri, sec). */
+static int64_t block_sse(const uint16_t *rec, ptrdiff_t rs, const uint16_t *src,
+                         ptrdiff_t ss, int pw, int ph, int sub, int bitdepth,
+                         int fby, int fbx, int pri, int sec, int damping,
+                         const uint8_t *dir, const int32_t *var, int bw)
+{
+    int bs = 8 >> sub, fbs = 64 >> sub;
+    int64_t sse = 0;
+    for (int i = fby * fbs; i < (fby + 1) * fbs && i < ph; i++) {
+        for (int j = fbx * fbs; j < (fbx + 1) * fbs && j < pw; j++) {
+            int b8 = (i / bs) * bw + (j / bs);
+            cdef_ref_eff_params e;
+            cdef_ref_block_params(pri, sec, damping, sub, bitdepth, var[b8], &e);
+            int64_t yv = cdef_ref_filter_sample(rec, pw, ph, rs, i, j, dir[b8], &e);
+            int64_t err = yv - (int64_t)src[(ptrdiff_t)i * ss + j];
+            sse += err * err;
+        }
+    }
+    return sse;
+}
+
+int cdef_ref_distortion(int w, int h, int bitdepth, int damping,
+                        const uint16_t *ry, ptrdiff_t rys,
+                        const uint16_t *ru, ptrdiff_t rus,
+                        const uint16_t *rv, ptrdiff_t rvs,
+                        const uint16_t *sy, ptrdiff_t sys,
+                        const uint16_t *su, ptrdiff_t sus,
+                        const uint16_t *sv, ptrdiff_t svs,
+                        int64_t *dist_luma, int64_t *dist_chroma)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    if (damping < 3 || damping > 6)
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    uint8_t *dir = (uint8_t *)malloc((size_t)bw * bh);
+    int32_t *var = (int32_t *)malloc((size_t)bw * bh * sizeof(int32_t));
+    if (!dir || !var) {
+        free(dir);
+        free(var);
+        return -1;
+    }
+    cdef_ref_find_dir(ry, w, h, rys, bitdepth, dir, var);
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    for (int fby = 0; fby < fb_rows; fby++) {
+        for (int fbx = 0; fbx < fb_cols; fbx++) {
+            int b = fby * fb_cols + fbx;
+            for (int p = 0; p < 16; p++) {
+                for (int s = 0; s < 4; s++) {
+                    int q = p * 4 + s;
+                    dist_luma[b * 64 + q] =
+                        block_sse(ry, rys, sy, sys, w, h, 0, bitdepth, fby, fbx,
+                                  p, sec_values[s], damping, dir, var, bw);
+                    dist_chroma[b * 64 + q] =
+                        block_sse(ru, rus, su, sus, w / 2, h / 2, 1, bitdepth, fby, fbx,
+                                  p, sec_values[s], damping, dir, var, bw) +
+                        block_sse(rv, rvs, sv, svs, w / 2, h / 2, 1, bitdepth, fby, fbx,
+                                  p, sec_values[s], damping, dir, var, bw);
+                }
+            }
+        }
+    }
+    free(dir);
+    free(var);
+    return 0;
+}
+
+/* Distortion of block b under preset t = luma_pair * 64 + chroma_pair (R15:
+ * the block's preset id selects the luma and the chroma pair together). */
+static int64_t preset_dist(const int64_t *dl, const int64_t *dc, int b, int t)
+{
+    return dl[b * 64 + t / 64] + dc[b * 64 + t % 64];
+}
+
+/* Eq. 15 with the greedy search of section 5 (R16): N = 1 takes the preset
+ * with the least total distortion; each later step adds the preset that
+ * lowers sum_b min_{q in P} D_b(q) the most, the earlier ones held fixed;
+ * ties go to the lowest preset index.  Then N in {1, 2, 4, 8} (the signalled
+ * counts) minimising J(N) = lambda * B * log2 N + sum_b min, ties to the
+ * smaller N; a block's id is its least-distortion preset, ties to the lower
+ * id. */
+int cdef_ref_select_presets(int nblocks, const int64_t *dist_luma,
+                            const int64_t *dist_chroma, int64_t lambda,
+                            int32_t *presets, int32_t *npresets,
+                            uint8_t *block_ids, int64_t *cost,
+                            int64_t *costs)
+{
+    if (nblocks <= 0)
+        return -1;
+    int64_t total[8];
+    for (int n = 1; n <= 8; n++) {
+        int best_t = -1;
+        int64_t best_total = 0;
+        for (int t = 0; t < 4096; t++) {
+            int64_t tot = 0;
+            for (int b = 0; b < nblocks; b++) {
+                int64_t m = preset_dist(dist_luma, dist_chroma, b, t);
+                for (int k = 0; k < n - 1; k++)
+                    m = min64(m, preset_dist(dist_luma, dist_chroma, b, presets[k]));
+                tot += m;
+            }
+            if (best_t < 0 || tot < best_total) {
+                best_t = t;
+                best_total = tot;
+            }
+        }
+        presets[n - 1] = best_t;
+        total[n - 1] = best_total;
+    }
+    int best_n = 0;
+    int64_t best_j = 0;
+    for (int n = 1; n <= 8; n++) {
+        int64_t j = total[n - 1];
+        int log2n = n == 1 ? 0 : n == 2 ? 1 : n == 4 ? 2 : n == 8 ? 3 : -1;
+        if (log2n >= 0)
+            j += lambda * nblocks * log2n;
+        if (costs)
+            costs[n - 1] = j;
+        if (log2n >= 0 && (best_n == 0 || j < best_j)) {
+            best_n = n;
+            best_j = j;
+        }
+    }
+    *npresets = best_n;
+    *cost = best_j;
+    for (int b = 0; b < nblocks; b++) {
+        int id = 0;
+        for (int k = 1; k < best_n; k++)
+            if (preset_dist(dist_luma, dist_chroma, b, presets[k]) <
+                preset_dist(dist_luma, dist_chroma, b, presets[id]))
+                id = k;
+        block_ids[b] = (uint8_t)id;
+    }
+    return 0;
+}

@@ -1,0 +1,123 @@
+/*
+ * CPU oracle for the CDEF hot path (Midtskogen & Valin, "The AV1 Constrained
+ * Directional Enhancement Filter (CDEF)", arXiv 1602.05975).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, literal restatement of
+ * the paper's definitions in C99 with 64-bit integers.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or helper with the CUDA library; the CUDA
+ * path never calls it and must never fall back to it.
+ *
+ * Samples are passed as uint16_t for every bit depth (8-bit frames are
+ * widened by the caller).  Strides are in samples.  Every output buffer is
+ * owned by the caller.  Functions return 0 on success and -1 on an argument
+ * the paper does not define (the oracle does not try to be forgiving).
+ *
+ * Parity status of each function is stated in cdef_ref.c.
+ */
+#ifndef CDEF_REF_H
+#define CDEF_REF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Section 2, Fig. 1 (reading): line number k of pixel (row i, column j) of an
+ * 8x8 block for direction d = 0..7. */
+int cdef_ref_line_number(int d, int i, int j);
+
+/* Algorithm 1 on one 8x8 block of centred 8-bit values x[i*8+j] in
+ * [-128, 127]: writes s[d] = 840 * s_d (eq. 5 scaled by 840). */
+void cdef_ref_direction_costs(const int32_t x[64], int64_t s[8]);
+
+/* Algorithm 1 on one 8x8 block of raw samples at bit depth bd (section 2:
+ * high bit depths are brought down to 8 bits first).  Returns the direction
+ * and writes the directional contrast v. */
+int cdef_ref_find_dir_block(const uint16_t *p, ptrdiff_t stride, int bitdepth,
+                            int64_t *contrast);
+
+/* Algorithm 1 over every 8x8 block of a luma plane (w, h multiples of 8).
+ * dir and var are (h/8) x (w/8), row-major. */
+int cdef_ref_find_dir(const uint16_t *luma, int w, int h, ptrdiff_t stride,
+                      int bitdepth, uint8_t *dir, int32_t *var);
+
+/* Eq. 7: the constraint function f(d, S, D), with the anti-symmetric reading
+ * of its d < 0 branch.  S = 0 gives 0. */
+int64_t cdef_ref_constrain(int64_t diff, int64_t strength, int64_t damping);
+
+/* Eq. 13: luma primary strength adjusted by the directional contrast v. */
+int cdef_ref_adjust_strength(int strength, int64_t contrast);
+
+/* Eq. 8: round(sum / 16), ties away from zero. */
+int64_t cdef_ref_round16(int64_t sum);
+
+/* Per-8x8 effective parameters (section 3.2): the strengths after contrast
+ * adjustment (luma) and bit-depth scaling, the damping after the chroma
+ * offset, the raise to floor(log2 S_p) and the bit-depth offset, and the
+ * parity that picks the primary weights.  Exposed for tests. */
+typedef struct {
+    int64_t pri, sec;   /* scaled strengths used by eq. 7 */
+    int64_t damping;    /* D used by eq. 7 */
+    int parity;         /* 0 even, 1 odd (before scaling) */
+} cdef_ref_eff_params;
+void cdef_ref_block_params(int pri_raw, int sec_raw, int damping_luma,
+                           int is_chroma, int bitdepth, int64_t contrast,
+                           cdef_ref_eff_params *out);
+
+/* Eq. 8-12 for one output sample at (row i, col j) of a plane of size w x h,
+ * for direction d and the effective parameters e. */
+int64_t cdef_ref_filter_sample(const uint16_t *plane, int w, int h,
+                               ptrdiff_t stride, int i, int j, int d,
+                               const cdef_ref_eff_params *e);
+
+/* Per 64x64 filter block parameters: 8 bytes each, row-major over the
+ * ceil(H/64) x ceil(W/64) filter-block grid:
+ *   byte 0 luma primary strength, 1 luma secondary strength,
+ *   byte 2 chroma primary strength, 3 chroma secondary strength,
+ *   byte 4 luma damping (8-bit scale), bytes 5..7 unused. */
+#define CDEF_REF_PARAM_BYTES 8
+
+/* Filters one 4:2:0 frame (section 3): luma w x h, chroma w/2 x h/2.
+ * dir/var are the luma 8x8 maps from cdef_ref_find_dir. */
+int cdef_ref_filter_frame(int w, int h, int bitdepth,
+                          const uint16_t *y, ptrdiff_t ys,
+                          const uint16_t *u, ptrdiff_t us,
+                          const uint16_t *v, ptrdiff_t vs,
+                          const uint8_t *params,
+                          const uint8_t *dir, const int32_t *var,
+                          uint16_t *oy, ptrdiff_t oys,
+                          uint16_t *ou, ptrdiff_t ous,
+                          uint16_t *ov, ptrdiff_t ovs);
+
+/* Section 5, two-pass search, first pass: for each filter block b and each of
+ * the 64 (primary 0..15) x (secondary {0,1,2,4}) pairs, the SSE between the
+ * source and the decoded frame filtered with that pair at damping D.
+ * dist_luma[b*64 + p*4 + s_idx], dist_chroma likewise (U + V). */
+int cdef_ref_distortion(int w, int h, int bitdepth, int damping,
+                        const uint16_t *ry, ptrdiff_t rys,
+                        const uint16_t *ru, ptrdiff_t rus,
+                        const uint16_t *rv, ptrdiff_t rvs,
+                        const uint16_t *sy, ptrdiff_t sys,
+                        const uint16_t *su, ptrdiff_t sus,
+                        const uint16_t *sv, ptrdiff_t svs,
+                        int64_t *dist_luma, int64_t *dist_chroma);
+
+/* Section 5, eq. 15 and the greedy preset search over nblocks blocks.
+ * presets[k] = luma_pair * 64 + chroma_pair, k < 8 (all 8 greedy steps are
+ * written); *npresets is the chosen N in {1,2,4,8}; block_ids[b] the preset
+ * index of block b; *cost = J(N); costs[n-1] = J(n) for n = 1..8 (log2 n is
+ * only defined as an integer for n in {1,2,4,8}; other entries hold the
+ * distortion term alone). */
+int cdef_ref_select_presets(int nblocks, const int64_t *dist_luma,
+                            const int64_t *dist_chroma, int64_t lambda,
+                            int32_t *presets, int32_t *npresets,
+                            uint8_t *block_ids, int64_t *cost,
+                            int64_t *costs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

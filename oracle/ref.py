@@ -1,0 +1,210 @@
+"""Python access to the plain-C CDEF oracle (``oracle/cdef_ref.c``).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this module.  The CUDA
+library never calls it; it shares no code with it.
+
+The oracle is compiled with gcc by :func:`build` into ``oracle/libcdef_ref.so``.
+All arrays are numpy; samples are passed as uint16 whatever the bit depth.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cdef_ref.c")
+_LIB = os.path.join(_HERE, "libcdef_ref.so")
+_lib = None
+
+_u16p = np.ctypeslib.ndpointer(np.uint16, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+
+
+class EffParams(C.Structure):
+    _fields_ = [("pri", C.c_int64), ("sec", C.c_int64),
+                ("damping", C.c_int64), ("parity", C.c_int)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no vectorisation flags; -O2 only)."""
+    stale = (not os.path.exists(_LIB)
+             or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+             or os.path.getmtime(_LIB) < os.path.getmtime(os.path.join(_HERE, "cdef_ref.h")))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared",
+                               "-Wall", "-Wextra", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = os.environ.get("CDEF_REF_LIB")  # a planted-mistake copy (tests)
+        if not path:
+            path = build()
+        L = C.CDLL(path)
+        L.cdef_ref_line_number.argtypes = [C.c_int, C.c_int, C.c_int]
+        L.cdef_ref_line_number.restype = C.c_int
+        L.cdef_ref_direction_costs.argtypes = [_i32p, _i64p]
+        L.cdef_ref_direction_costs.restype = None
+        L.cdef_ref_find_dir_block.argtypes = [_u16p, C.c_ssize_t, C.c_int,
+                                              C.POINTER(C.c_int64)]
+        L.cdef_ref_find_dir_block.restype = C.c_int
+        L.cdef_ref_find_dir.argtypes = [_u16p, C.c_int, C.c_int, C.c_ssize_t,
+                                        C.c_int, _u8p, _i32p]
+        L.cdef_ref_find_dir.restype = C.c_int
+        L.cdef_ref_constrain.argtypes = [C.c_int64, C.c_int64, C.c_int64]
+        L.cdef_ref_constrain.restype = C.c_int64
+        L.cdef_ref_adjust_strength.argtypes = [C.c_int, C.c_int64]
+        L.cdef_ref_adjust_strength.restype = C.c_int
+        L.cdef_ref_round16.argtypes = [C.c_int64]
+        L.cdef_ref_round16.restype = C.c_int64
+        L.cdef_ref_block_params.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int,
+                                            C.c_int, C.c_int64,
+                                            C.POINTER(EffParams)]
+        L.cdef_ref_block_params.restype = None
+        L.cdef_ref_filter_sample.argtypes = [_u16p, C.c_int, C.c_int,
+                                             C.c_ssize_t, C.c_int, C.c_int,
+                                             C.c_int, C.POINTER(EffParams)]
+        L.cdef_ref_filter_sample.restype = C.c_int64
+        L.cdef_ref_filter_frame.argtypes = (
+            [C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 3
+            + [_u8p, _u8p, _i32p] + [_u16p, C.c_ssize_t] * 3)
+        L.cdef_ref_filter_frame.restype = C.c_int
+        L.cdef_ref_distortion.argtypes = (
+            [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6
+            + [_i64p, _i64p])
+        L.cdef_ref_distortion.restype = C.c_int
+        L.cdef_ref_select_presets.argtypes = [
+            C.c_int, _i64p, _i64p, C.c_int64, _i32p, C.POINTER(C.c_int32),
+            _u8p, C.POINTER(C.c_int64), _i64p]
+        L.cdef_ref_select_presets.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _u16(a):
+    return np.ascontiguousarray(a, dtype=np.uint16)
+
+
+# ---------------------------------------------------------------- scalar API
+def line_number(d: int, i: int, j: int) -> int:
+    return lib().cdef_ref_line_number(d, i, j)
+
+
+def direction_costs(x64) -> np.ndarray:
+    """840 * s_d for d = 0..7 of a centred 8x8 block (Algorithm 1)."""
+    x = np.ascontiguousarray(np.asarray(x64, dtype=np.int32).reshape(64))
+    s = np.zeros(8, np.int64)
+    lib().cdef_ref_direction_costs(x, s)
+    return s
+
+
+def find_dir_block(block, bitdepth: int = 8):
+    b = _u16(block)
+    v = C.c_int64(0)
+    d = lib().cdef_ref_find_dir_block(b, b.shape[1], bitdepth, C.byref(v))
+    return d, v.value
+
+
+def constrain(diff: int, strength: int, damping: int) -> int:
+    return lib().cdef_ref_constrain(diff, strength, damping)
+
+
+def adjust_strength(strength: int, contrast: int) -> int:
+    return lib().cdef_ref_adjust_strength(strength, contrast)
+
+
+def round16(s: int) -> int:
+    return lib().cdef_ref_round16(s)
+
+
+def block_params(pri, sec, damping, is_chroma, bitdepth, contrast=0):
+    e = EffParams()
+    lib().cdef_ref_block_params(pri, sec, damping, int(is_chroma), bitdepth,
+                                contrast, C.byref(e))
+    return e
+
+
+def filter_sample(plane, i, j, d, eff: EffParams) -> int:
+    p = _u16(plane)
+    h, w = p.shape
+    return lib().cdef_ref_filter_sample(p, w, h, w, i, j, d, C.byref(eff))
+
+
+# ----------------------------------------------------------------- frame API
+def find_dir(luma, bitdepth: int):
+    y = _u16(luma)
+    h, w = y.shape
+    dirs = np.zeros((h // 8, w // 8), np.uint8)
+    var = np.zeros((h // 8, w // 8), np.int32)
+    if lib().cdef_ref_find_dir(y, w, h, w, bitdepth, dirs, var) != 0:
+        raise ValueError("oracle rejected find_dir arguments")
+    return dirs, var
+
+
+def filter_frame(y, u, v, bitdepth: int, params, dirs=None, var=None):
+    """Filter a 4:2:0 frame.  params: uint8 array (fb_rows, fb_cols, 8)."""
+    y, u, v = _u16(y), _u16(u), _u16(v)
+    h, w = y.shape
+    if dirs is None:
+        dirs, var = find_dir(y, bitdepth)
+    prm = np.ascontiguousarray(params, dtype=np.uint8)
+    oy, ou, ov = np.zeros_like(y), np.zeros_like(u), np.zeros_like(v)
+    rc = lib().cdef_ref_filter_frame(
+        w, h, bitdepth, y, w, u, u.shape[1], v, v.shape[1],
+        prm.reshape(-1), np.ascontiguousarray(dirs, np.uint8).reshape(-1),
+        np.ascontiguousarray(var, np.int32).reshape(-1),
+        oy, w, ou, ou.shape[1], ov, ov.shape[1])
+    if rc != 0:
+        raise ValueError("oracle rejected filter_frame arguments")
+    return oy, ou, ov
+
+
+def distortion(rec, src, bitdepth: int, damping: int):
+    """Per filter block, 64 luma and 64 chroma SSE values (section 5)."""
+    ry, ru, rv = (_u16(p) for p in rec)
+    sy, su, sv = (_u16(p) for p in src)
+    h, w = ry.shape
+    nb = ((h + 63) // 64) * ((w + 63) // 64)
+    dl = np.zeros(nb * 64, np.int64)
+    dc = np.zeros(nb * 64, np.int64)
+    rc = lib().cdef_ref_distortion(
+        w, h, bitdepth, damping, ry, w, ru, ru.shape[1], rv, rv.shape[1],
+        sy, w, su, su.shape[1], sv, sv.shape[1], dl, dc)
+    if rc != 0:
+        raise ValueError("oracle rejected distortion arguments")
+    return dl.reshape(nb, 64), dc.reshape(nb, 64)
+
+
+def select_presets(dist_luma, dist_chroma, lam: int):
+    dl = np.ascontiguousarray(dist_luma, np.int64).reshape(-1)
+    dc = np.ascontiguousarray(dist_chroma, np.int64).reshape(-1)
+    nb = dl.size // 64
+    presets = np.zeros(8, np.int32)
+    n = C.c_int32(0)
+    ids = np.zeros(nb, np.uint8)
+    cost = C.c_int64(0)
+    costs = np.zeros(8, np.int64)
+    rc = lib().cdef_ref_select_presets(nb, dl, dc, lam, presets, C.byref(n),
+                                       ids, C.byref(cost), costs)
+    if rc != 0:
+        raise ValueError("oracle rejected select_presets arguments")
+    return dict(presets=presets, npresets=n.value, block_ids=ids,
+                cost=cost.value, costs=costs)
+
+
+def search_strengths(rec, src, bitdepth: int, damping: int, lam: int):
+    dl, dc = distortion(rec, src, bitdepth, damping)
+    out = select_presets(dl, dc, lam)
+    out["dist_luma"] = dl
+    out["dist_chroma"] = dc
+    return out

@@ -1,0 +1,675 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numbers the
+paper prints (tests/golden/paper_values.json), closed forms, exact rational
+arithmetic, brute force, geometry, or a library routine.  No GPU.
+"""
+import decimal
+import itertools
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                     "paper_values.json")))
+
+
+# --------------------------------------------------------------------------
+# Section 2: line geometry (Fig. 1 reading R1)
+# --------------------------------------------------------------------------
+def _lines(ref, d):
+    lines = {}
+    for i in range(8):
+        for j in range(8):
+            lines.setdefault(ref.line_number(d, i, j), []).append((i, j))
+    return lines
+
+
+def test_line_cardinalities_printed(ref):
+    g = GOLDEN["line_cardinality"]
+    lines = _lines(ref, 1)
+    assert len(lines[0]) == g["N_1_0"]
+    assert len(lines[4]) == g["N_1_4"]
+
+
+def test_lines_partition_block(ref):
+    g = GOLDEN["cardinality_range"]
+    for d in range(8):
+        lines = _lines(ref, d)
+        assert sorted(lines) == list(range(len(lines)))  # contiguous numbering
+        assert sum(len(v) for v in lines.values()) == 64
+        for v in lines.values():
+            assert g["min"] <= len(v) <= g["max"]
+            assert g["lcm"] % len(v) == 0
+
+
+def test_operation_counts_printed(ref):
+    """90 line sums; 34 multiplies (one per distinct cardinality of a
+    direction); 82 additions (lines - 1 per direction)."""
+    g = GOLDEN["search_op_counts"]
+    nlines = [len(_lines(ref, d)) for d in range(8)]
+    assert sum(nlines) == g["line_sums"]
+    distinct = [len({len(v) for v in _lines(ref, d).values()}) for d in range(8)]
+    assert sum(distinct) == g["multiplies_for_s_d"]
+    assert sum(n - 1 for n in nlines) == g["additions_for_s_d"]
+    assert 8 - 1 == g["comparisons"]
+
+
+def _line_angle(pixels):
+    """Orientation (degrees, in [0, 180)) of a set of (row, col) points, with
+    angles measured counter-clockwise from the +column axis, row up."""
+    pts = np.array([(j, -i) for (i, j) in pixels], float)
+    pts -= pts.mean(0)
+    w, v = np.linalg.eigh(pts.T @ pts)
+    vx, vy = v[:, -1]
+    return math.degrees(math.atan2(vy, vx)) % 180.0
+
+
+def test_direction_angles(ref):
+    """d = 0 is the 45-degree diagonal (Fig. 2 caption: the 45-degree
+    direction), directions turn by about 22.5 degrees per step, and d+4 is
+    perpendicular to d (the contrast of Algorithm 1 compares them)."""
+    ang = []
+    for d in range(8):
+        longest = max(_lines(ref, d).values(), key=len)
+        ang.append(_line_angle(longest))
+    for d in range(8):
+        expect = (45.0 - 22.5 * d) % 180.0
+        diff = min(abs(ang[d] - expect), 180 - abs(ang[d] - expect))
+        assert diff < 5.0, (d, ang[d], expect)
+        perp = abs(ang[d] - ang[(d + 4) % 8]) % 180
+        assert abs(perp - 90.0) < 1e-6 or abs(perp - 90.0) < 5.0
+
+
+# --------------------------------------------------------------------------
+# Section 2: costs, eq. 1-5, Algorithm 1
+# --------------------------------------------------------------------------
+def _e2_direct(ref, x, d):
+    """E_d^2 straight from eq. 1-2 with exact rational line means."""
+    lines = _lines(ref, d)
+    e2 = Fraction(0)
+    for pix in lines.values():
+        vals = [int(x[i, j]) for (i, j) in pix]
+        mu = Fraction(sum(vals), len(vals))
+        e2 += sum((Fraction(v) - mu) ** 2 for v in vals)
+    return e2
+
+
+def test_e2_identity_exact(ref):
+    """Eq. 3: 840*E_d^2 = 840*sum x^2 - 840*s_d, in exact rationals."""
+    rng = np.random.default_rng(1)
+    blocks = [rng.integers(-128, 128, (8, 8)) for _ in range(150)]
+    blocks += [np.full((8, 8), -128), np.full((8, 8), 127),
+               np.where(np.indices((8, 8)).sum(0) % 2 == 0, 127, -128)]
+    for x in blocks:
+        s = ref.direction_costs(x)
+        sumsq = int((x.astype(np.int64) ** 2).sum())
+        for d in range(8):
+            assert Fraction(840) * _e2_direct(ref, x, d) == 840 * sumsq - int(s[d])
+
+
+def test_argmin_e_equals_argmax_s(ref):
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        x = rng.integers(-128, 128, (8, 8))
+        s = ref.direction_costs(x)
+        e = [_e2_direct(ref, x, d) for d in range(8)]
+        assert e.index(min(e)) == int(np.argmax(s))  # both first on ties
+
+
+def test_perfectly_directional_block(ref):
+    """A block constant along the lines of d* is found as d* with E = 0
+    (section 2's definition of a perfectly directional block)."""
+    rng = np.random.default_rng(3)
+    for dstar in range(8):
+        for _ in range(20):
+            lines = _lines(ref, dstar)
+            vals = rng.choice(np.arange(-128, 128), size=len(lines), replace=False)
+            x = np.zeros((8, 8), np.int64)
+            for k, pix in lines.items():
+                for (i, j) in pix:
+                    x[i, j] = vals[k]
+            s = ref.direction_costs(x)
+            assert _e2_direct(ref, x, dstar) == 0
+            assert s[dstar] == 840 * int((x ** 2).sum())
+            raw = (x + 128).astype(np.uint16)
+            d, v = ref.find_dir_block(raw, 8)
+            assert d == dstar
+            assert v >= 0
+
+
+def test_constant_block_ties_to_zero(ref):
+    for c in (0, 77, 128, 255):
+        d, v = ref.find_dir_block(np.full((8, 8), c, np.uint16), 8)
+        assert d == 0 and v == 0  # strict '>' in Algorithm 1
+
+
+def test_45_degree_line_block(ref):
+    """Fig. 2: a block containing a 45-degree line selects the 45-degree
+    direction (d = 0 under the reading of Fig. 1)."""
+    for off in range(-3, 4):
+        x = np.full((8, 8), 40, np.uint16)
+        for i in range(8):
+            j = 7 - i + off
+            if 0 <= j < 8:
+                x[i, j] = 200
+        d, _ = ref.find_dir_block(x, 8)
+        assert d == 0
+
+
+def test_int32_claim(ref):
+    """Section 2: with centred 8-bit pixels, 840*s_d fits a signed 32-bit
+    integer.  Cauchy-Schwarz gives s_d <= 840*sum x^2 <= 840*64*128^2."""
+    g = GOLDEN["int32_claim"]
+    extremes = [np.full((8, 8), g["centred_min"]), np.full((8, 8), g["centred_max"])]
+    rng = np.random.default_rng(4)
+    extremes += [rng.choice([g["centred_min"], g["centred_max"]], (8, 8)) for _ in range(200)]
+    for x in extremes:
+        s = ref.direction_costs(x)
+        assert s.max() < g["bound_exclusive"]
+        assert s.max() <= 840 * int((np.asarray(x, np.int64) ** 2).sum())
+
+
+def test_high_bitdepth_search_downscales(ref):
+    """Section 2: higher bit depths are searched at 8 bits."""
+    rng = np.random.default_rng(5)
+    for _ in range(100):
+        x8 = rng.integers(0, 256, (8, 8)).astype(np.uint16)
+        low = rng.integers(0, 4, (8, 8)).astype(np.uint16)
+        x10 = (x8 << 2) | low
+        assert ref.find_dir_block(x8, 8) == ref.find_dir_block(x10, 10)
+        x12 = (x8 << 4) | rng.integers(0, 16, (8, 8)).astype(np.uint16)
+        assert ref.find_dir_block(x8, 8) == ref.find_dir_block(x12, 12)
+
+
+def test_contrast_nonnegative_and_definition(ref):
+    rng = np.random.default_rng(6)
+    for _ in range(300):
+        raw = rng.integers(0, 256, (8, 8)).astype(np.uint16)
+        d, v = ref.find_dir_block(raw, 8)
+        s = ref.direction_costs(raw.astype(np.int64) - 128)
+        assert v >= 0
+        assert v == s[d] - s[(d + 4) % 8]
+        assert s[d] == s.max() and d == int(np.argmax(s))
+
+
+# --------------------------------------------------------------------------
+# Eq. 7: the constraint function
+# --------------------------------------------------------------------------
+def test_constrain_properties_exhaustive(ref):
+    """Anti-symmetry (stated after eq. 7), f(0) = 0, sign and magnitude
+    bounds, zero strength, and the damping-controlled zero point: with
+    S*2^(D - floor log2 S) in [2^D, 2^(D+1)), f(d) > 0 for 0 < d < 2^D and
+    f(d) = 0 for d >= 2^(D+1)."""
+    for S in range(0, 80):
+        lo = int(math.floor(math.log2(S))) if S > 0 else 0
+        for D in range(max(lo, 0), 11):
+            if D - lo > 10:
+                continue
+            for d in list(range(-1100, 1101, 7)) + list(range(-40, 41)):
+                f = ref.constrain(d, S, D)
+                assert ref.constrain(-d, S, D) == -f
+                if S == 0 or d == 0:
+                    assert f == 0
+                    continue
+                assert f == 0 or np.sign(f) == np.sign(d)
+                assert abs(f) <= min(abs(d), S)
+                if abs(d) >= 2 ** (D + 1):
+                    assert f == 0
+                if 0 < abs(d) < 2 ** D:
+                    assert f != 0
+
+
+def test_constrain_small_differences_linear(ref):
+    """'For small differences, f(d, S, D) = d': f(d) = d for |d| up to a
+    threshold of at least 1 whenever S >= 1 (over the dampings the paper
+    allows, D >= 2), and f is unimodal in d >= 0 (rises as d, then falls
+    to 0)."""
+    for S in range(1, 80):
+        lo = int(math.floor(math.log2(S)))
+        for D in range(max(lo, 2), lo + 8):
+            vals = [ref.constrain(d, S, D) for d in range(0, 2 ** (D + 1) + 2)]
+            assert vals[1] == 1
+            k = 0
+            while k + 1 < len(vals) and vals[k + 1] == k + 1:
+                k += 1
+            tail = vals[k:]
+            assert all(a >= b for a, b in zip(tail, tail[1:]))
+            assert max(vals) <= S
+
+
+def test_constrain_damping_monotone(ref):
+    """Fig. 2 (bottom): larger damping moves the zero point out; |f| never
+    shrinks as D grows."""
+    for S in range(1, 64):
+        lo = int(math.floor(math.log2(S)))
+        for D in range(lo, lo + 6):
+            for d in range(0, 600, 3):
+                assert ref.constrain(d, S, D + 1) >= ref.constrain(d, S, D)
+
+
+def test_constrain_large_damping_reaches_strength(ref):
+    """Fig. 2 (top): the strength caps the correction; with damping large
+    enough the cap S is reached."""
+    for S in range(1, 80):
+        assert max(ref.constrain(d, S, 14) for d in range(0, 200)) == S
+
+
+# --------------------------------------------------------------------------
+# Eq. 8 rounding, eq. 13 adjustment, section 3.2 parameters
+# --------------------------------------------------------------------------
+def test_round16_ties_away_from_zero(ref):
+    table = {8: 1, -8: -1, 24: 2, -24: -2, 7: 0, -7: 0, 9: 1, -9: -1, 0: 0,
+             23: 1, -23: -1, 25: 2}
+    for s, r in table.items():
+        assert ref.round16(s) == r
+    ctx = decimal.Context(rounding=decimal.ROUND_HALF_UP)
+    for s in range(-4000, 4001):
+        expect = int(ctx.quantize(decimal.Decimal(s) / 16, decimal.Decimal(1)))
+        assert ref.round16(s) == expect
+
+
+def test_adjust_strength(ref):
+    g = GOLDEN["contrast_thresholds"]
+    for S in range(0, 16):
+        prev = -1
+        for v in [0, 1, g["zero_below"] - 1, g["zero_below"], 5000, 65535, 65536,
+                  131071, 131072, 10 ** 6, 10 ** 7, 2 ** 28, 2 ** 30, 2 ** 31 - 1]:
+            a = ref.adjust_strength(S, v)
+            if v < g["zero_below"]:
+                assert a == 0
+            assert 0 <= a <= S
+            assert a >= prev
+            prev = a
+        # saturation: floor(log2(v/2^16)) >= 12 gives the factor 16/16
+        assert ref.adjust_strength(S, g["log_unit"] * 2 ** g["max_log"]) == S
+        assert ref.adjust_strength(S, 2 ** 31 - 1) == S
+    for v in range(1024, 2 ** 20, 997):
+        assert [ref.adjust_strength(S, v) for S in range(16)] == \
+            sorted(ref.adjust_strength(S, v) for S in range(16))
+
+
+def test_chroma_damping_example(ref):
+    g = GOLDEN["chroma_damping_example"]
+    e = ref.block_params(g["chroma_primary"], 0, g["luma_damping"], True, 8)
+    assert e.damping == g["chroma_damping"]
+    e = ref.block_params(2, 0, g["luma_damping"], True, 8)
+    assert e.damping == g["luma_damping"] - 1
+    for D in range(3, 7):
+        for S in range(16):
+            for chroma in (False, True):
+                e = ref.block_params(S, 0, D, chroma, 8, 2 ** 31 - 1)
+                if e.pri:
+                    assert e.damping >= int(math.floor(math.log2(e.pri)))
+
+
+def test_twelve_bit_example(ref):
+    g = GOLDEN["twelve_bit_example"]
+    vals = [ref.block_params(S, 0, 3, True, 12).pri for S in range(16)]
+    assert vals == g["primary_values"]
+    damp = sorted({ref.block_params(1, 0, D, False, 12, 2 ** 31 - 1).damping
+                   for D in range(3, 7)})
+    assert [damp[0], damp[-1]] == g["damping_range"]
+    # taps keep alternating after scaling: parity follows the 8-bit value
+    for S in range(16):
+        assert ref.block_params(S, 0, 3, True, 12).parity == S % 2
+
+
+def test_bitdepth_scaling(ref):
+    """Section 3.2: at bit depth 8+k strengths are scaled by 2^k and D is
+    offset by k.  D - floor(log2 S) is then unchanged, so the zero point of
+    f scales by exactly 2^k and f itself by 2^k up to the finer flooring:
+    |f(2^k d, 2^k S, D + k) - 2^k f(d, S, D)| < 2^k."""
+    for k in (2, 4):
+        for S in range(1, 20):
+            lo = int(math.floor(math.log2(S)))
+            for D in range(max(lo, 2), lo + 5):
+                zero = next(d for d in range(1, 4096) if ref.constrain(d, S, D) == 0)
+                zero_k = next(d for d in range(1, 1 << 16)
+                              if ref.constrain(d, S << k, D + k) == 0)
+                assert zero_k == zero << k
+                for d in range(-300, 301, 5):
+                    assert abs(ref.constrain(d << k, S << k, D + k)
+                               - (ref.constrain(d, S, D) << k)) < (1 << k)
+    for bd in (10, 12):
+        for S in range(1, 16):
+            for D in range(3, 7):
+                for chroma in (False, True):
+                    e8 = ref.block_params(S, 4, D, chroma, 8, 2 ** 31 - 1)
+                    eb = ref.block_params(S, 4, D, chroma, bd, 2 ** 31 - 1)
+                    assert eb.pri == e8.pri << (bd - 8) and eb.sec == e8.sec << (bd - 8)
+                    assert eb.damping - eb.pri.bit_length() == e8.damping - e8.pri.bit_length()
+
+
+# --------------------------------------------------------------------------
+# Eq. 8-12: the filter
+# --------------------------------------------------------------------------
+def _probe_weights(ref, d, pri, sec):
+    """Weight (in sixteenths) that the oracle gives each offset of the 5x5
+    neighbourhood, read back through a single tap of height 16 at 12 bits
+    (where f(16) = 16 for the probed strengths, so y - x = w)."""
+    w = {}
+    for dr in range(-2, 3):
+        for dc in range(-2, 3):
+            if dr == 0 and dc == 0:
+                continue
+            plane = np.full((9, 9), 2000, np.uint16)
+            plane[4 + dr, 4 + dc] = 2016
+            e = ref.block_params(pri, sec, 6, False, 12, 2 ** 31 - 1)
+            y = ref.filter_sample(plane, 4, 4, d, e)
+            if y != 2000:
+                w[(dr, dc)] = y - 2000
+    return w
+
+
+def test_tap_geometry_and_weights(ref):
+    """Figs. 3-4 (figures missing): 4 primary taps on a line through the
+    filtered pixel along d, weights (b near, a far) = (4, 2) for even and
+    (3, 3) for odd strengths (caption of Fig. 3), and 8 secondary taps
+    that are the primary taps of d +- 2 (the cross 45 degrees off d)."""
+    pw = GOLDEN["primary_weights"]
+    prim = {}
+    for d in range(8):
+        even = _probe_weights(ref, d, 14, 0)
+        odd = _probe_weights(ref, d, 15, 0)
+        assert len(even) == 4 and set(even) == set(odd)
+        for (dr, dc), wt in even.items():
+            assert (-dr, -dc) in even  # symmetric pairs
+            near = max(abs(dr), abs(dc)) == 1
+            assert wt == (pw["even"]["b"] if near else pw["even"]["a"])
+            assert odd[(dr, dc)] == (pw["odd"]["b"] if near else pw["odd"]["a"])
+        # the far taps lie on the centre's line of direction d (Fig. 1)
+        for (dr, dc) in even:
+            if max(abs(dr), abs(dc)) == 2:
+                for i in range(2, 6):
+                    for j in range(2, 6):
+                        if 0 <= i + dr < 8 and 0 <= j + dc < 8:
+                            assert ref.line_number(d, i + dr, j + dc) == ref.line_number(d, i, j)
+        # and all four are collinear with the centre
+        pts = [(0, 0)] + list(even)
+        ang = _line_angle(pts)
+        longest = max(_lines(ref, d).values(), key=len)
+        diff = abs(ang - _line_angle(longest))
+        assert min(diff, 180 - diff) < 10
+        prim[d] = set(even)
+    for d in range(8):
+        secw = _probe_weights(ref, d, 0, 4)
+        expect = prim[(d + 2) % 8] | prim[(d + 6) % 8]
+        assert set(secw) == expect and len(secw) == 8
+        for (dr, dc), wt in secw.items():
+            assert wt == (2 if max(abs(dr), abs(dc)) == 1 else 1)
+
+
+def test_zero_strength_identity(ref):
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(7)
+    for bd in (8, 10):
+        y, u, v = synth.random_frame_planes(rng, 48, 40, bd)
+        prm = synth.random_params(rng, 48, 40)
+        prm[..., 0:4] = 0
+        oy, ou, ov = ref.filter_frame(y, u, v, bd, prm)
+        assert (oy == y).all() and (ou == u).all() and (ov == v).all()
+
+
+def test_constant_frame_fixed_point(ref):
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(8)
+    for bd in (8, 10):
+        for c in (0, 100, (1 << bd) - 1):
+            y = np.full((40, 56), c, np.uint16)
+            u = np.full((20, 28), c, np.uint16)
+            prm = synth.random_params(rng, 56, 40)
+            oy, ou, ov = ref.filter_frame(y, u, u, bd, prm)
+            assert (oy == c).all() and (ou == c).all() and (ov == c).all()
+
+
+def test_constant_along_direction_unchanged(ref):
+    """With only primary taps, a plane constant along d (rows, columns,
+    diagonals) gives every primary difference 0, so y = x."""
+    rng = np.random.default_rng(9)
+    ii, jj = np.indices((12, 12))
+    along = {0: ii + jj, 2: ii, 4: ii - jj, 6: jj}
+    for d, key in along.items():
+        vals = rng.integers(0, 256, 40)
+        plane = vals[key + 15].astype(np.uint16) if d == 4 else vals[key].astype(np.uint16)
+        for pri in (1, 7, 15):
+            e = ref.block_params(pri, 0, 4, False, 8, 2 ** 31 - 1)
+            for i in range(12):
+                for j in range(12):
+                    assert ref.filter_sample(plane, i, j, d, e) == plane[i, j]
+
+
+def test_clip_to_taps(ref):
+    """Eq. 9-12: twelve taps one above the pixel raise the raw sum to 24
+    sixteenths (round(1.5) = 2) but the clip holds y at x + 1; with one tap
+    set active the sum is 12 sixteenths and rounds to 1."""
+    plane = np.full((9, 9), 101, np.uint16)
+    plane[4, 4] = 100
+    for d in range(8):
+        e = ref.block_params(15, 4, 6, False, 8, 2 ** 31 - 1)
+        assert ref.filter_sample(plane, 4, 4, d, e) == 101
+        e = ref.block_params(14, 0, 6, False, 8, 2 ** 31 - 1)
+        assert ref.filter_sample(plane, 4, 4, d, e) == 101
+        e = ref.block_params(0, 4, 6, False, 8, 2 ** 31 - 1)
+        assert ref.filter_sample(plane, 4, 4, d, e) == 101
+
+
+def test_out_of_frame_taps_are_ignored(ref):
+    """Section 3.1: a tap outside the frame is ignored (f = 0, not in the
+    clip range).  Ignoring it is the same as an in-frame tap equal to the
+    filtered pixel (f(0) = 0 and x is already in the range), so filtering at
+    the border equals filtering inside a frame padded with the pixel's own
+    value."""
+    rng = np.random.default_rng(10)
+    plane = rng.integers(0, 256, (16, 16)).astype(np.uint16)
+    for d in range(8):
+        for pri, sec in ((15, 4), (9, 2), (0, 1)):
+            e = ref.block_params(pri, sec, 5, False, 8, 2 ** 31 - 1)
+            for (i, j) in [(0, 0), (0, 7), (1, 15), (15, 15), (14, 3), (7, 0), (8, 14)]:
+                x = int(plane[i, j])
+                padded = np.full((20, 20), x, np.uint16)
+                padded[2:18, 2:18] = plane
+                assert ref.filter_sample(plane, i, j, d, e) == \
+                    ref.filter_sample(padded, i + 2, j + 2, d, e)
+
+
+def test_output_within_neighbourhood_range(ref):
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(11)
+    for bd in (8, 10):
+        y, u, v = synth.random_frame_planes(rng, 32, 24, bd)
+        prm = synth.random_params(rng, 32, 24)
+        oy, _, _ = ref.filter_frame(y, u, v, bd, prm)
+        yp = np.pad(y.astype(np.int64), 2, mode="edge")
+        for i in range(24):
+            for j in range(32):
+                nb = yp[i:i + 5, j:j + 5]
+                assert nb.min() <= oy[i, j] <= nb.max()
+
+
+def _py_filter_frame(ref, y, u, v, bd, prm):
+    """An independent frame-level evaluator written from the paper in
+    Python: tap weights probed per direction, eq. 7 from its text, the
+    block/plane plumbing of sections 2-4 re-derived here."""
+    wmap = {}
+    for d in range(8):
+        wmap[(d, 0, 0)] = _probe_weights(ref, d, 14, 0)
+        wmap[(d, 0, 1)] = _probe_weights(ref, d, 15, 0)
+        wmap[(d, 1, 0)] = _probe_weights(ref, d, 0, 4)
+
+    def f(diff, S, D):
+        if S == 0:
+            return 0
+        sh = D - (S.bit_length() - 1)
+        a = abs(diff)
+        m = min(a, max(0, S - a // (1 << sh)))
+        return m if diff >= 0 else -m
+
+    def adj(S, v):
+        if v < 1024:
+            return 0
+        q = v >> 16
+        i = min(q.bit_length() - 1, 12) if q else 0
+        return (S * (4 + i) + 8) >> 4
+
+    h, w = y.shape
+    dirs, var = ref.find_dir(y, bd)
+    outs = []
+    for plane, sub in ((y, 0), (u, 1), (v, 1)):
+        ph, pw = plane.shape
+        out = np.zeros_like(plane)
+        for i in range(ph):
+            for j in range(pw):
+                by, bx = (i << sub) // 8, (j << sub) // 8
+                d = int(dirs[by, bx])
+                fb = prm[(i << sub) // 64, (j << sub) // 64]
+                if sub == 0:
+                    Sp, Ss, D = adj(int(fb[0]), int(var[by, bx])), int(fb[1]), int(fb[4])
+                else:
+                    Sp, Ss, D = int(fb[2]), int(fb[3]), int(fb[4]) - 1
+                if Sp and D < Sp.bit_length() - 1:
+                    D = Sp.bit_length() - 1
+                par = Sp & 1
+                k = bd - 8
+                Sp, Ss, D = Sp << k, Ss << k, D + k
+                x = int(plane[i, j])
+                tot, lo, hi = 0, x, x
+                for kind, S in ((0, Sp), (1, Ss)):
+                    wm = wmap[(d, 0, par)] if kind == 0 else wmap[(d, 1, 0)]
+                    for (dr, dc), wt in wm.items():
+                        m, n = i + dr, j + dc
+                        if 0 <= m < ph and 0 <= n < pw:
+                            p = int(plane[m, n])
+                            tot += wt * f(p - x, S, D)
+                            lo, hi = min(lo, p), max(hi, p)
+                r = (abs(tot) + 8) // 16
+                yv = x + (r if tot >= 0 else -r)
+                out[i, j] = min(hi, max(lo, yv))
+        outs.append(out)
+    return outs
+
+
+@pytest.mark.parametrize("w,h,bd", [(8, 8, 8), (16, 16, 10), (24, 16, 8), (72, 72, 10)])
+def test_filter_frame_brute_force(ref, w, h, bd):
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(w * 1000 + h + bd)
+    y, u, v = synth.random_frame_planes(rng, w, h, bd)
+    if w == 72:  # smoother content exercises the contrast adjustment
+        fr = synth.make_frame(w, h, bd, 32, seed=3)
+        y, u, v = fr.rec
+    prm = synth.random_params(rng, w, h)
+    got = ref.filter_frame(y, u, v, bd, prm)
+    exp = _py_filter_frame(ref, y, u, v, bd, prm)
+    for g_, e_ in zip(got, exp):
+        assert (g_ == e_).all()
+
+
+def test_filter_frame_all_strengths(ref):
+    """Every strength pair x damping x bit depth on one 16x16 frame."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(12)
+    for bd in (8, 10):
+        y, u, v = synth.random_frame_planes(rng, 16, 16, bd)
+        exp_cache = None
+        for pri in (0, 1, 2, 3, 7, 8, 15):
+            for sec in (0, 1, 2, 4):
+                for D in (3, 6):
+                    prm = np.zeros((1, 1, 8), np.uint8)
+                    prm[0, 0, :5] = (pri, sec, pri, sec, D)
+                    got = ref.filter_frame(y, u, v, bd, prm)
+                    exp = _py_filter_frame(ref, y, u, v, bd, prm)
+                    for g_, e_ in zip(got, exp):
+                        assert (g_ == e_).all(), (bd, pri, sec, D)
+        del exp_cache
+
+
+# --------------------------------------------------------------------------
+# Section 5: strength search
+# --------------------------------------------------------------------------
+def test_distortion_matches_filtered_sse(ref):
+    """D_{b,q} is the SSE against the source of the frame filtered with pair
+    q everywhere; D_{b,(0,0)} is the unfiltered SSE."""
+    from paper_1602_05975_gb300 import synth
+    fr = synth.make_frame(80, 72, 8, 32, seed=21)
+    dl, dc = ref.distortion(fr.rec, fr.src, 8, 4)
+    nb = dl.shape[0]
+    assert nb == 4
+    for q in (0, 5, 22, 63):
+        p, s = q // 4, synth.SEC_VALUES[q % 4]
+        prm = np.zeros((2, 2, 8), np.uint8)
+        prm[..., :5] = (p, s, p, s, 4)
+        oy, ou, ov = ref.filter_frame(*fr.rec, 8, prm)
+        for b in range(nb):
+            by, bx = divmod(b, 2)
+            sl = np.s_[by * 64:(by + 1) * 64, bx * 64:(bx + 1) * 64]
+            slc = np.s_[by * 32:(by + 1) * 32, bx * 32:(bx + 1) * 32]
+            el = ((oy[sl].astype(np.int64) - fr.src[0][sl]) ** 2).sum()
+            ec = sum(((o[slc].astype(np.int64) - s_[slc]) ** 2).sum()
+                     for o, s_ in ((ou, fr.src[1]), (ov, fr.src[2])))
+            assert dl[b, q] == el and dc[b, q] == ec
+    # q = 0 is (0, 0): no filtering
+    assert dl[0, 0] == ((fr.rec[0][:64, :64].astype(np.int64) - fr.src[0][:64, :64]) ** 2).sum()
+
+
+def _brute_greedy(dl, dc, lam):
+    B = dl.shape[0]
+    full = (dl[:, :, None] + dc[:, None, :]).reshape(B, 4096)
+    chosen, totals = [], []
+    cur = np.full(B, np.iinfo(np.int64).max)
+    for _ in range(8):
+        tot = np.minimum(cur[:, None], full).sum(0)
+        t = int(np.argmin(tot))  # first minimum
+        chosen.append(t)
+        totals.append(int(tot[t]))
+        cur = np.minimum(cur, full[:, t])
+    J = {n: totals[n - 1] + lam * B * int(math.log2(n)) for n in (1, 2, 4, 8)}
+    best = min((1, 2, 4, 8), key=lambda n: (J[n], n))
+    ids = np.argmin(full[:, chosen[:best]], axis=1)
+    return chosen, best, J[best], ids, full
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_greedy_matches_brute_force(ref, seed):
+    rng = np.random.default_rng(seed)
+    B = int(rng.integers(1, 7))
+    hi = [5, 50, 10 ** 6, 10 ** 9][seed]  # small ranges force ties
+    dl = rng.integers(0, hi, (B, 64)).astype(np.int64)
+    dc = rng.integers(0, hi, (B, 64)).astype(np.int64)
+    lam = int(rng.integers(0, hi))
+    out = ref.select_presets(dl, dc, lam)
+    chosen, n, J, ids, _ = _brute_greedy(dl, dc, lam)
+    assert list(out["presets"]) == chosen
+    assert out["npresets"] == n and out["cost"] == J
+    assert (out["block_ids"] == ids).all()
+
+
+def test_greedy_pair_not_better_than_exhaustive(ref):
+    """Greedy J(2) is never below the exhaustive optimum over all preset
+    pairs (B <= 4)."""
+    rng = np.random.default_rng(30)
+    for _ in range(3):
+        B = 3
+        dl = rng.integers(0, 1000, (B, 64)).astype(np.int64)
+        dc = rng.integers(0, 1000, (B, 64)).astype(np.int64)
+        out = ref.select_presets(dl, dc, 0)
+        full = (dl[:, :, None] + dc[:, None, :]).reshape(B, 4096)
+        best_pair = min(int(np.minimum(full[:, [a]], full).sum(0).min())
+                        for a in range(4096))
+        assert out["costs"][1] >= best_pair
+        assert out["costs"][0] == int(full.sum(0).min())
+
+
+def test_greedy_lambda_extremes(ref):
+    rng = np.random.default_rng(31)
+    dl = rng.integers(0, 10 ** 6, (20, 64)).astype(np.int64)
+    dc = rng.integers(0, 10 ** 6, (20, 64)).astype(np.int64)
+    assert ref.select_presets(dl, dc, 10 ** 12)["npresets"] == 1
+    out = ref.select_presets(dl, dc, 0)
+    assert out["npresets"] == 8
+    ties = ref.select_presets(np.zeros((5, 64), np.int64), np.zeros((5, 64), np.int64), 0)
+    assert ties["npresets"] == 1 and list(ties["presets"]) == [0] * 8
+    assert (ties["block_ids"] == 0).all()
