@@ -1,0 +1,393 @@
+"""Throughput benchmark of the CDEF hot path on GB300.
+
+Default workload: 3840x2160 10-bit 4:2:0, 8 frames, direction search +
+filter, one fused launch per frame, streamed on one CUDA stream (the 4K
+10-bit case the HBM-roofline target is stated for).  A step filters all 8
+frames.  Metric: luma megapixels per second (chroma work included).
+
+Prints ONE JSON line (rank 0).  Keys beyond the metric:
+  roofline      HBM roofline of the dominant kernel (the fused filter):
+                algorithmic bytes per launch (every input sample read once,
+                every output sample written once) / mean launch time from
+                CUDA events on the launching stream, against the measured
+                copy bandwidth
+  cpu_baseline  the C oracle timed on this host's cores on a bounded sample
+                of the same frames
+  e2e           same metric through the C ABI with host buffers: pinned
+                host -> device copy, filter, device -> host copy per frame,
+                all inside the timed region
+  clocks        nvidia-smi samples taken during the timed region
+
+--impl reference times the oracle (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s (find_dir+filter)"
+UNIT = "Mpixel/s"
+KERNEL_SOURCES = ["paper_1602_05975_gb300/csrc/filter.cu",
+                  "paper_1602_05975_gb300/csrc/cdef_device.cuh"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:  # noqa: BLE001
+        return None
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+    except Exception:  # noqa: BLE001
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ workload
+WORKLOAD = dict(name="3840x2160 10-bit 4:2:0, 8 frames, direction search + filter, "
+                     "one launch per frame",
+                width=3840, height=2160, bitdepth=10, frames=8, base_seed=2000)
+
+
+def make_frames(rank: int = 0):
+    from paper_1602_05975_gb300 import synth
+    w, h, bd = WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["bitdepth"]
+    return [synth.make_frame(w, h, bd, None, WORKLOAD["base_seed"] + f)
+            for f in range(WORKLOAD["frames"])]
+
+
+def algorithmic_bytes_per_frame() -> int:
+    w, h, bd = WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["bitdepth"]
+    samples = w * h + 2 * (w // 2) * (h // 2)
+    return samples * (1 if bd == 8 else 2) * 2
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+BAND = 120  # rows per oracle task (a multiple of 8)
+
+
+def _oracle_band(args):
+    """Filter one horizontal band of a frame with the oracle (as a frame of
+    its own).  Returns (luma pixels, seconds)."""
+    planes, bd, params = args
+    from oracle import ref
+    t = time.perf_counter()
+    ref.filter_frame(*planes, bd, params)
+    return planes[0].shape[0] * planes[0].shape[1], time.perf_counter() - t
+
+
+def oracle_tasks(frames, nbands):
+    tasks = []
+    for fr in frames:
+        h = fr.height
+        for b0 in range(0, h, BAND):
+            if len(tasks) >= nbands:
+                return tasks
+            b1 = min(h, b0 + BAND)
+            y = fr.rec[0][b0:b1]
+            u = fr.rec[1][b0 // 2:b1 // 2]
+            v = fr.rec[2][b0 // 2:b1 // 2]
+            rows = [(b0 // 64 + k) % fr.params.shape[0] for k in range(-(-(b1 - b0) // 64))]
+            prm = np.ascontiguousarray(fr.params[rows])
+            tasks.append(((y, u, v), fr.bitdepth, prm))
+    return tasks
+
+
+def run_oracle(pool, cores, frames, nbands):
+    from oracle import ref
+    ref.build()
+    tasks = oracle_tasks(frames, nbands)
+    t = time.perf_counter()
+    res = pool.map(_oracle_band, tasks, chunksize=1)
+    wall = time.perf_counter() - t
+    px = sum(r[0] for r in res)
+    return px / wall / 1e6, px, wall
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ main arms
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1602_05975_gb300 import synth  # noqa: F401
+    cores = min(os.cpu_count() or 1, 16)
+    frames = make_frames()[:2]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        for _ in range(args.warmup):
+            run_oracle(pool, cores, frames, cores)
+        vals, pxs, walls = [], 0, 0.0
+        for _ in range(args.steps):
+            v, px, wall = run_oracle(pool, cores, frames, cores)
+            vals.append(v)
+            pxs += px
+            walls += wall
+    value = pxs / walls / 1e6
+    sample = (f"{cores} bands of {WORKLOAD['width']}x{BAND} luma (+chroma) of the 4K 10-bit "
+              f"frames per step, one band per core, each filtered as a frame by the oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": walls / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "sample": "bounded oracle sample"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    pool = None
+    cores = 0
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # spawn the oracle pool before any CUDA work
+        cores = min(os.cpu_count() or 1, 16)
+        pool = mp.get_context("spawn").Pool(cores)
+
+    import torch
+    from paper_1602_05975_gb300 import build, cdef
+    build.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = cdef.Context(local)
+
+    frames = make_frames(rank)
+    nf = len(frames)
+    ins = [cdef.frame_from_numpy(f.rec, f.bitdepth, device=dev) for f in frames]
+    outs = [cdef.alloc_frame(f.width, f.height, f.bitdepth, device=dev, fill=0) for f in frames]
+    prms = [cdef.params_tensor(f.params, device=dev) for f in frames]
+    stream = torch.cuda.Stream(device=dev)
+    px_per_frame = WORKLOAD["width"] * WORKLOAD["height"]
+
+    def step(evs=None):
+        for i in range(nf):
+            if evs is not None:
+                evs[i][0].record(stream)
+            cdef.cdef_filter_frame(ctx, ins[i], prms[i], outs[i], stream=stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+
+    # parity spot check of the benchmark's own launch configuration
+    got = outs[0].to_numpy()
+    if args.check:
+        from oracle import ref
+        exp = ref.filter_frame(*frames[0].rec, frames[0].bitdepth, frames[0].params)
+        for g, e in zip(got, exp):
+            assert np.array_equal(g, e), "bench output differs from the oracle"
+
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(nf)] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for row in evs for (a, b) in row]
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    value = ws * nf * px_per_frame / (ms_per_step * 1e-3) / 1e6
+    assert ctx.status() == 0
+
+    # e2e: host buffers, copies inside the timed region, 3 streams in flight
+    e2e = None
+    if not args.no_e2e:
+        hin = [cdef.frame_from_numpy(f.rec, f.bitdepth, device="cpu", pin=True) for f in frames]
+        hout = [cdef.alloc_frame(f.width, f.height, f.bitdepth, device="cpu") for f in frames]
+        hout = [cdef.Frame(*(t.pin_memory() for t in h.planes()), h.width, h.height, h.bitdepth)
+                for h in hout]
+        streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
+        h2d = sum(t.numel() * t.element_size() for h in hin for t in h.planes())
+        d2h = sum(t.numel() * t.element_size() for h in hout for t in h.planes())
+
+        def e2e_step():
+            for i in range(nf):
+                s = streams[i % len(streams)]
+                with torch.cuda.stream(s):
+                    for dt, st in zip(ins[i].planes(), hin[i].planes()):
+                        dt.copy_(st, non_blocking=True)
+                    cdef.cdef_filter_frame(ctx, ins[i], prms[i], outs[i], stream=s)
+                    for st, dt in zip(hout[i].planes(), outs[i].planes()):
+                        st.copy_(dt, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        tt0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - tt0) * 1e3
+        if ws > 1:
+            tt = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": ws * nf * px_per_frame / (e_ms / args.steps * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        for h, o in zip(hout[:1], outs[:1]):
+            assert all(np.array_equal(a, b) for a, b in zip(h.to_numpy(), o.to_numpy()))
+
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    mean_launch = statistics.mean(launch_ms)
+    achieved = algorithmic_bytes_per_frame() / (mean_launch * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": ncu_traffic("filter_kernel"),
+                "kernel": "filter_kernel (fused find_dir + filter)",
+                "bytes_per_launch": algorithmic_bytes_per_frame(),
+                "mean_launch_us": mean_launch * 1e3,
+                "peak_source": "measured" if peaks else "fallback"}
+
+    cpu = None
+    if pool is not None:
+        v, px, wall = run_oracle(pool, cores, frames[:4], args.cpu_bands)
+        pool.close()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_bands} bands of {WORKLOAD['width']}x{BAND} luma (+chroma) "
+                         f"of the same frames, {px / 1e6:.1f} Mpixel in {wall:.1f} s wall"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "frames_per_step": nf,
+                       "width": WORKLOAD["width"], "height": WORKLOAD["height"],
+                       "bitdepth": WORKLOAD["bitdepth"], "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (8 frames x 49.8 MB per step)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": args.steps * nf,
+        }))
+    if ws > 1:
+        dist.destroy_process_group()
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-bands", type=int, default=36)
+    ap.add_argument("--check", action="store_true", help="oracle check of frame 0")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

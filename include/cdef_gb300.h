@@ -1,0 +1,191 @@
+/*
+ * cdef_gb300 -- C ABI of a GB300 (sm_103a) implementation of the hot path of
+ * the Constrained Directional Enhancement Filter (CDEF) of
+ * Midtskogen & Valin, "The AV1 Constrained Directional Enhancement Filter
+ * (CDEF)", arXiv 1602.05975.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Frames are 4:2:0.  The luma plane is W x H, both multiples of 8
+ *    (section 2 works on 8x8 blocks); the chroma planes are W/2 x H/2.
+ *  - Samples are unsigned integers stored planar and row-major: uint8_t for
+ *    bit depth 8, uint16_t (value in the low bits) for bit depths 10 and 12.
+ *  - Plane memory is DEVICE memory owned by the caller.  `data` must be
+ *    16-byte aligned and `pitch_bytes` a multiple of 16 that is at least
+ *    width * sample size (the tiles are moved by the tensor memory
+ *    accelerator, which needs both).
+ *  - Filter blocks are 64x64 luma (32x32 chroma) pixels (section 4); there
+ *    are B = ceil(W/64) * ceil(H/64) of them, numbered row-major.
+ *  - 8x8 direction maps are (H/8) x (W/8) arrays, row-major, no padding.
+ *  - Every call is asynchronous on the given CUDA stream (cudaStream_t passed
+ *    as void*; NULL = the legacy default stream) unless it says otherwise.
+ *    Results are valid once the stream reaches the call.  No call aborts or
+ *    traps: errors come back as a negative status (cdef_strerror() names
+ *    it) and leave the outputs unspecified.
+ *  - A context is bound to one device.  Calls on one context must not run
+ *    concurrently from several host threads.
+ */
+#ifndef CDEF_GB300_H
+#define CDEF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CDEF_OK 0
+#define CDEF_ERR_ARG (-1)      /* NULL pointer, aliasing, bad pitch/alignment, value out of range */
+#define CDEF_ERR_SIZE (-2)     /* W or H not a positive multiple of 8, or chroma size != W/2 x H/2 */
+#define CDEF_ERR_BITDEPTH (-3) /* bit depth other than 8, 10 or 12, or a plane of the wrong sample size */
+#define CDEF_ERR_NOMEM (-4)    /* over the context's device-memory budget, or allocation failed */
+#define CDEF_ERR_CUDA (-5)     /* a CUDA runtime/driver call failed */
+#define CDEF_ERR_TIMEOUT (-6)  /* a bounded device-side wait gave up */
+#define CDEF_ERR_DEVICE (-7)   /* a kernel reported an internal consistency error */
+
+/* One plane: device pointer, size in samples, row pitch in bytes. */
+typedef struct {
+    void *data;
+    int32_t width;
+    int32_t height;
+    int64_t pitch_bytes;
+} cdef_plane;
+
+/* One 4:2:0 frame. */
+typedef struct {
+    cdef_plane y, u, v;
+    int32_t bitdepth; /* 8, 10 or 12 */
+} cdef_frame;
+
+/* Parameters of one 64x64 filter block, as signalled (section 3.2, 4):
+ *   pri_y, pri_uv : primary strength S^(p), 0..15 (19 accepted: the value
+ *                   the (0,0) preset stands for, section 4)
+ *   sec_y, sec_uv : secondary strength S^(s) in {0, 1, 2, 4} (7 accepted)
+ *   damping       : luma damping D at the 8-bit scale, 3..6; chroma uses
+ *                   D - 1 (section 3.2)
+ * Strengths are the 8-bit values; they are scaled by 2^(bitdepth-8) inside
+ * (section 3.2).  8 bytes, no padding surprises. */
+typedef struct {
+    uint8_t pri_y, sec_y, pri_uv, sec_uv;
+    uint8_t damping;
+    uint8_t reserved[3];
+} cdef_fb_params;
+
+/* One preset of the frame header (section 4), without the skip-condition
+ * bits: the primary and secondary strengths for luma and chroma. */
+typedef struct {
+    uint8_t pri_y, sec_y, pri_uv, sec_uv;
+} cdef_preset;
+
+typedef struct cdef_ctx cdef_ctx;
+
+/* Creates a context on CUDA device `device`.  It owns the library's device
+ * scratch memory (allocated lazily, never more than hbm_budget_bytes in
+ * total; 0 = no limit).  Returns CDEF_OK and *ctx, or an error. */
+int cdef_ctx_create(cdef_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Releases the context and its scratch memory.  NULL is accepted.
+ * Synchronises the device first. */
+int cdef_ctx_destroy(cdef_ctx *ctx);
+
+/* Kernel-reported errors since the last clear.  Strength values out of the
+ * ranges above are found on the device (the parameters live in device
+ * memory): the block is then left unfiltered and the context's status word
+ * is set.  Waits for all work on the device, then returns CDEF_OK or
+ * CDEF_ERR_ARG; clear != 0 resets the word. */
+int cdef_ctx_status(cdef_ctx *ctx, int clear);
+
+/* Direction search, section 2, eq. 1-5 and Algorithm 1.
+ * For every 8x8 block of the luma plane: the direction d in 0..7 that
+ * maximises s_d (first maximum on ties) and the directional contrast
+ * v = s_best - s_{(best+4) mod 8} >= 0, with s_d in the 840-scaled units of
+ * Algorithm 1 (int32 always suffices, section 2).  Samples of bit depth > 8 are brought to 8 bits by an
+ * arithmetic right shift first.
+ *   luma     : host pointer to the plane descriptor (device samples)
+ *   bitdepth : 8, 10 or 12 (must match the plane's sample size)
+ *   dir      : device, (H/8)*(W/8) bytes, written
+ *   var      : device, (H/8)*(W/8) int32, written
+ */
+int cdef_find_dir(cdef_ctx *ctx, const cdef_plane *luma, int32_t bitdepth,
+                  uint8_t *dir, int32_t *var, void *cuda_stream);
+
+/* The CDEF filter over a whole 4:2:0 frame, section 3 (eq. 6-13):
+ * primary taps along the block direction, secondary taps on the cross at
+ * +-45 degrees, each through the constraint f(d, S, D) of eq. 7, the
+ * weighted sum rounded (ties away from zero) and the result clipped to the
+ * range of the filtered pixel and its in-frame taps.  Luma primary
+ * strengths are adjusted per 8x8 block by the contrast (eq. 13); chroma
+ * 4x4 blocks take the co-located luma direction.  Taps outside the frame
+ * are ignored; filter-block borders inside the frame are read across, and
+ * only the unfiltered input is ever read.
+ *   in      : host pointer to the input frame descriptor (device planes)
+ *   params  : DEVICE array of B cdef_fb_params, row-major over filter blocks
+ *   dir,var : DEVICE maps from cdef_find_dir, or both NULL: the direction
+ *             search then runs inside the filter kernel (fused)
+ *   out     : host pointer to the output frame descriptor; same sizes and
+ *             bit depth as `in`; its planes must not overlap `in`'s
+ */
+int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in,
+                      const cdef_fb_params *params, const uint8_t *dir,
+                      const int32_t *var, const cdef_frame *out,
+                      void *cuda_stream);
+
+/* The same filter over n frames of possibly different sizes and bit depths
+ * in one kernel launch (the fused direction search is always used).
+ *   in, out : HOST arrays of n frame descriptors
+ *   params  : HOST array of n DEVICE pointers, params[i] has B_i entries
+ * n <= 64.  Equivalent to n calls of cdef_filter_frame with dir = NULL. */
+int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
+                       const cdef_fb_params *const *params,
+                       const cdef_frame *out, void *cuda_stream);
+
+/* Encoder strength search, section 5, for n frames (sizes may differ).
+ *
+ * First pass: for every filter block b of every frame and each of the 64
+ * strength pairs q = p*4 + s (primary p in 0..15, secondary index s for
+ * S^(s) in {0,1,2,4}), the distortion D_{b,q} = sum of squared differences
+ * between the source and the decoded frame filtered with that pair at the
+ * frame's damping, over the block's in-frame pixels; luma and chroma
+ * (U + V) separately.  Skip-condition bits are not modelled (every 8x8
+ * block counts as coded).
+ *
+ * Second pass, per frame: presets are (luma pair, chroma pair) tuples,
+ * index t = luma_q*64 + chroma_q.  Greedy search for N = 1..8: each step
+ * adds the preset minimising sum_b min_{presets} (D^luma_{b,.} +
+ * D^chroma_{b,.}), ties to the lowest t; then N in {1, 2, 4, 8}
+ * minimising J = lambda*B*log2(N) + that sum (eq. 15; ties to the smaller
+ * N), and each block's id = its least-distortion preset (ties to the lower
+ * id).
+ *
+ *   rec, src     : HOST arrays of n frame descriptors (device planes); src
+ *                  is the uncoded frame, same sizes and bit depth
+ *   damping      : HOST, n luma dampings (3..6), one per frame (section 4)
+ *   lambda       : HOST, n non-negative rate multipliers
+ *   dist_luma,
+ *   dist_chroma  : DEVICE, sum_i B_i * 64 int64 each (frame i's blocks after
+ *                  frame i-1's), written; or both NULL (context scratch)
+ *   presets      : HOST, n*8 entries; presets[i*8+k] for k < npresets[i]
+ *   npresets     : HOST, n entries
+ *   block_ids    : DEVICE, sum_i B_i bytes, written
+ *   cost         : HOST, n entries: J of the chosen N
+ * This call synchronises the stream before returning (host outputs).
+ */
+int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
+                          const cdef_frame *src, const int32_t *damping,
+                          const int64_t *lambda, int64_t *dist_luma,
+                          int64_t *dist_chroma, cdef_preset *presets,
+                          int32_t *npresets, uint8_t *block_ids, int64_t *cost,
+                          void *cuda_stream);
+
+/* A static description of a status code. */
+const char *cdef_strerror(int status);
+
+/* Library version, e.g. "cdef_gb300 0.1 sm_103a". */
+const char *cdef_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,274 @@
+"""Python binding of the cdef_gb300 C ABI (include/cdef_gb300.h).
+
+Argument marshalling only: every step of the CDEF path runs in the CUDA
+kernels of libcdef_gb300.so.  PyTorch provides device memory and streams.
+There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+
+Planes are 2-D CUDA tensors of shape (height, pitch_in_samples) with the
+frame's width in the leading columns: torch.uint8 for 8-bit frames,
+torch.int16 (holding unsigned values) for 10/12-bit frames.  Use
+:func:`alloc_frame` to get correctly pitched planes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcdef_gb300.so")
+
+CDEF_OK = 0
+ERRORS = {-1: "CDEF_ERR_ARG", -2: "CDEF_ERR_SIZE", -3: "CDEF_ERR_BITDEPTH",
+          -4: "CDEF_ERR_NOMEM", -5: "CDEF_ERR_CUDA", -6: "CDEF_ERR_TIMEOUT",
+          -7: "CDEF_ERR_DEVICE"}
+SEC_VALUES = (0, 1, 2, 4)
+MAX_BATCH = 64
+
+
+class CdefError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: {ERRORS.get(status, status)} ({_strerror(status)})")
+        self.status = status
+
+
+class Plane(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32),
+                ("pitch_bytes", C.c_int64)]
+
+
+class FrameDesc(C.Structure):
+    _fields_ = [("y", Plane), ("u", Plane), ("v", Plane), ("bitdepth", C.c_int32)]
+
+
+class Preset(C.Structure):
+    _fields_ = [("pri_y", C.c_uint8), ("sec_y", C.c_uint8), ("pri_uv", C.c_uint8),
+                ("sec_uv", C.c_uint8)]
+
+
+_lib = None
+
+
+def load():
+    """Load libcdef_gb300.so (built by build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing; build it with "
+                           "paper_1602_05975_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    L.cdef_ctx_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t]
+    L.cdef_ctx_destroy.argtypes = [vp]
+    L.cdef_ctx_status.argtypes = [vp, C.c_int]
+    L.cdef_find_dir.argtypes = [vp, C.POINTER(Plane), i32, vp, vp, vp]
+    L.cdef_filter_frame.argtypes = [vp, C.POINTER(FrameDesc), vp, vp, vp,
+                                    C.POINTER(FrameDesc), vp]
+    L.cdef_filter_frames.argtypes = [vp, i32, C.POINTER(FrameDesc), C.POINTER(vp),
+                                     C.POINTER(FrameDesc), vp]
+    L.cdef_search_strengths.argtypes = [vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc),
+                                        C.POINTER(i32), C.POINTER(i64), vp, vp,
+                                        C.POINTER(Preset), C.POINTER(i32), vp,
+                                        C.POINTER(i64), vp]
+    L.cdef_strerror.argtypes = [C.c_int]
+    L.cdef_strerror.restype = C.c_char_p
+    L.cdef_version.restype = C.c_char_p
+    for name in ("cdef_ctx_create", "cdef_ctx_destroy", "cdef_ctx_status", "cdef_find_dir",
+                 "cdef_filter_frame", "cdef_filter_frames", "cdef_search_strengths"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _strerror(status):
+    try:
+        return load().cdef_strerror(status).decode()
+    except Exception:  # noqa: BLE001 - only used inside an error message
+        return "?"
+
+
+def _check(rc, what):
+    if rc != CDEF_OK:
+        raise CdefError(rc, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------- planes
+def sample_dtype(bitdepth: int):
+    return torch.uint8 if bitdepth == 8 else torch.int16
+
+
+def pitch_samples(width: int, bitdepth: int) -> int:
+    """Row pitch (in samples) rounded up to a multiple of 16 bytes."""
+    b = 1 if bitdepth == 8 else 2
+    return ((width * b + 15) // 16 * 16) // b
+
+
+@dataclass
+class Frame:
+    """A 4:2:0 frame in device memory: y, u, v are pitched 2-D tensors."""
+    y: torch.Tensor
+    u: torch.Tensor
+    v: torch.Tensor
+    width: int
+    height: int
+    bitdepth: int
+
+    def planes(self):
+        return (self.y, self.u, self.v)
+
+    def desc(self) -> FrameDesc:
+        d = FrameDesc()
+        for name, t, w, h in (("y", self.y, self.width, self.height),
+                              ("u", self.u, self.width // 2, self.height // 2),
+                              ("v", self.v, self.width // 2, self.height // 2)):
+            p = getattr(d, name)
+            p.data = t.data_ptr()
+            p.width = w
+            p.height = h
+            p.pitch_bytes = t.stride(0) * t.element_size()
+        d.bitdepth = self.bitdepth
+        return d
+
+    def to_numpy(self):
+        """Host copies of the visible planes as uint16 arrays."""
+        out = []
+        for t, w in ((self.y, self.width), (self.u, self.width // 2), (self.v, self.width // 2)):
+            a = t[:, :w].cpu().numpy()
+            out.append(a.view(np.uint16) if a.dtype == np.int16 else a.astype(np.uint16))
+        return tuple(out)
+
+
+def alloc_frame(width: int, height: int, bitdepth: int, device="cuda", fill=None) -> Frame:
+    dt = sample_dtype(bitdepth)
+    planes = []
+    for w, h in ((width, height), (width // 2, height // 2), (width // 2, height // 2)):
+        t = torch.empty((h, pitch_samples(w, bitdepth)), dtype=dt, device=device)
+        if fill is not None:
+            t.fill_(fill)
+        planes.append(t)
+    return Frame(*planes, width, height, bitdepth)
+
+
+def frame_from_numpy(planes, bitdepth: int, device="cuda", pin=False) -> Frame:
+    """Copy host uint16 planes (y, u, v) into a pitched frame (or, with
+    device='cpu' and pin=True, a pinned host frame)."""
+    y = planes[0]
+    h, w = y.shape
+    f = alloc_frame(w, h, bitdepth, device="cpu")
+    for t, a in zip(f.planes(), planes):
+        a = np.asarray(a)
+        if bitdepth == 8:
+            t[:, :a.shape[1]] = torch.from_numpy(a.astype(np.uint8))
+        else:
+            t[:, :a.shape[1]] = torch.from_numpy(a.astype(np.uint16).view(np.int16))
+    if device == "cpu":
+        if pin:
+            f = Frame(*(t.pin_memory() for t in f.planes()), w, h, bitdepth)
+        return f
+    return Frame(*(t.to(device) for t in f.planes()), w, h, bitdepth)
+
+
+def params_tensor(params: np.ndarray, device="cuda") -> torch.Tensor:
+    """(fb_rows, fb_cols, 8) uint8 parameters as a flat device tensor."""
+    p = np.ascontiguousarray(params, dtype=np.uint8)
+    assert p.shape[-1] == 8
+    return torch.from_numpy(p.reshape(-1)).to(device)
+
+
+# --------------------------------------------------------------- context
+class Context:
+    """Owns a cdef_ctx (device scratch, pinned staging) on one GPU."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        self._lib = load()
+        h = C.c_void_p()
+        _check(self._lib.cdef_ctx_create(C.byref(h), device, budget_bytes), "cdef_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            self._lib.cdef_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def status(self, clear=True):
+        return self._lib.cdef_ctx_status(self.handle, int(clear))
+
+
+def cdef_find_dir(ctx: Context, luma: torch.Tensor, width: int, height: int, bitdepth: int,
+                  dirs: torch.Tensor, var: torch.Tensor, stream=None):
+    p = Plane(luma.data_ptr(), width, height, luma.stride(0) * luma.element_size())
+    assert dirs.dtype == torch.uint8 and var.dtype == torch.int32
+    assert dirs.numel() >= (height // 8) * (width // 8) and var.numel() >= dirs.numel()
+    _check(ctx._lib.cdef_find_dir(ctx.handle, C.byref(p), bitdepth, dirs.data_ptr(),
+                                  var.data_ptr(), _stream_ptr(stream)), "cdef_find_dir")
+
+
+def cdef_filter_frame(ctx: Context, src: Frame, params: torch.Tensor, out: Frame,
+                      dirs: torch.Tensor | None = None, var: torch.Tensor | None = None,
+                      stream=None):
+    di, do = src.desc(), out.desc()
+    _check(ctx._lib.cdef_filter_frame(
+        ctx.handle, C.byref(di), params.data_ptr(),
+        None if dirs is None else dirs.data_ptr(), None if var is None else var.data_ptr(),
+        C.byref(do), _stream_ptr(stream)), "cdef_filter_frame")
+
+
+def cdef_filter_frames(ctx: Context, srcs, params, outs, stream=None):
+    n = len(srcs)
+    ins = (FrameDesc * n)(*[f.desc() for f in srcs])
+    os_ = (FrameDesc * n)(*[f.desc() for f in outs])
+    prm = (C.c_void_p * n)(*[p.data_ptr() for p in params])
+    _check(ctx._lib.cdef_filter_frames(ctx.handle, n, ins, prm, os_, _stream_ptr(stream)),
+           "cdef_filter_frames")
+
+
+def cdef_search_strengths(ctx: Context, recs, srcs, damping, lambdas, block_ids: torch.Tensor,
+                          dist_luma: torch.Tensor | None = None,
+                          dist_chroma: torch.Tensor | None = None, stream=None):
+    """Returns per frame: presets [(pri_y, sec_y, pri_uv, sec_uv)]*N, N, J."""
+    n = len(recs)
+    ri = (FrameDesc * n)(*[f.desc() for f in recs])
+    si = (FrameDesc * n)(*[f.desc() for f in srcs])
+    damp = (C.c_int32 * n)(*damping)
+    lam = (C.c_int64 * n)(*lambdas)
+    presets = (Preset * (8 * n))()
+    npre = (C.c_int32 * n)()
+    cost = (C.c_int64 * n)()
+    _check(ctx._lib.cdef_search_strengths(
+        ctx.handle, n, ri, si, damp, lam,
+        None if dist_luma is None else dist_luma.data_ptr(),
+        None if dist_chroma is None else dist_chroma.data_ptr(),
+        presets, npre, block_ids.data_ptr(), cost, _stream_ptr(stream)),
+        "cdef_search_strengths")
+    out = []
+    for i in range(n):
+        ps = [(p.pri_y, p.sec_y, p.pri_uv, p.sec_uv) for p in presets[i * 8:(i + 1) * 8]]
+        out.append(dict(presets=ps, npresets=npre[i], cost=cost[i]))
+    return out
+
+
+def preset_index(p) -> int:
+    """(pri_y, sec_y, pri_uv, sec_uv) -> luma_pair * 64 + chroma_pair."""
+    return (p[0] * 4 + SEC_VALUES.index(p[1])) * 64 + p[2] * 4 + SEC_VALUES.index(p[3])
+
+
+def version() -> str:
+    return load().cdef_version().decode()

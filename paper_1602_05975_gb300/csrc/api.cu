@@ -1,0 +1,359 @@
+// C ABI of cdef_gb300: argument validation, the context (device scratch and
+// pinned staging), and the launches.  See include/cdef_gb300.h.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "cdef_internal.h"
+
+using namespace cdefgb;
+
+struct cdef_ctx {
+    int device;
+    size_t budget;        // 0 = unlimited
+    size_t used;          // bytes of device scratch held
+    int *status;          // device status word (kernel-reported errors)
+    void *scratch;        // search scratch (distortion tables, greedy state)
+    size_t scratch_bytes;
+    SearchResultDev *host_results;  // pinned
+    SearchResultDev *dev_results;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int sample_bytes(int bitdepth) { return bitdepth == 8 ? 1 : 2; }
+
+int check_plane(const cdef_plane &p, int w, int h, int bytes)
+{
+    if (!p.data) return CDEF_ERR_ARG;
+    if (p.width != w || p.height != h) return CDEF_ERR_SIZE;
+    if (reinterpret_cast<uintptr_t>(p.data) % 16) return CDEF_ERR_ARG;
+    if (p.pitch_bytes <= 0 || p.pitch_bytes % 16 || p.pitch_bytes < (int64_t)w * bytes)
+        return CDEF_ERR_ARG;
+    return CDEF_OK;
+}
+
+int check_frame(const cdef_frame *f)
+{
+    if (!f) return CDEF_ERR_ARG;
+    if (f->bitdepth != 8 && f->bitdepth != 10 && f->bitdepth != 12) return CDEF_ERR_BITDEPTH;
+    const int w = f->y.width, h = f->y.height;
+    if (w <= 0 || h <= 0 || w % 8 || h % 8) return CDEF_ERR_SIZE;
+    const int b = sample_bytes(f->bitdepth);
+    int rc;
+    if ((rc = check_plane(f->y, w, h, b))) return rc;
+    if ((rc = check_plane(f->u, w / 2, h / 2, b))) return rc;
+    if ((rc = check_plane(f->v, w / 2, h / 2, b))) return rc;
+    return CDEF_OK;
+}
+
+bool same_geometry(const cdef_frame *a, const cdef_frame *b)
+{
+    return a->bitdepth == b->bitdepth && a->y.width == b->y.width && a->y.height == b->y.height;
+}
+
+bool overlaps(const cdef_plane &a, const cdef_plane &b)
+{
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(a.data);
+    const uintptr_t a1 = a0 + (uintptr_t)a.pitch_bytes * a.height;
+    const uintptr_t b0 = reinterpret_cast<uintptr_t>(b.data);
+    const uintptr_t b1 = b0 + (uintptr_t)b.pitch_bytes * b.height;
+    return a0 < b1 && b0 < a1;
+}
+
+bool frames_overlap(const cdef_frame *a, const cdef_frame *b)
+{
+    const cdef_plane *pa[3] = {&a->y, &a->u, &a->v};
+    const cdef_plane *pb[3] = {&b->y, &b->u, &b->v};
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+            if (overlaps(*pa[i], *pb[j])) return true;
+    return false;
+}
+
+int fb_count(const cdef_frame *f) { return ((f->y.width + 63) / 64) * ((f->y.height + 63) / 64); }
+
+void fill_filter_frame(FilterFrameDev &d, const cdef_frame *in, const cdef_frame *out,
+                       const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
+                       int block_start)
+{
+    const cdef_plane *pi[3] = {&in->y, &in->u, &in->v};
+    const cdef_plane *po[3] = {&out->y, &out->u, &out->v};
+    for (int i = 0; i < 3; i++) {
+        d.p[i].in = static_cast<const uint8_t *>(pi[i]->data);
+        d.p[i].out = static_cast<uint8_t *>(po[i]->data);
+        d.p[i].in_pitch = pi[i]->pitch_bytes;
+        d.p[i].out_pitch = po[i]->pitch_bytes;
+        d.p[i].w = pi[i]->width;
+        d.p[i].h = pi[i]->height;
+    }
+    d.params = params;
+    d.dir = dir;
+    d.var = var;
+    d.bitdepth = in->bitdepth;
+    d.fb_cols = (in->y.width + 63) / 64;
+    d.fb_rows = (in->y.height + 63) / 64;
+    d.block_start = block_start;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? CDEF_OK : CDEF_ERR_CUDA; }
+
+int ensure_scratch(cdef_ctx *ctx, size_t bytes)
+{
+    if (ctx->scratch_bytes >= bytes) return CDEF_OK;
+    const size_t grow = bytes - ctx->scratch_bytes;
+    if (ctx->budget && ctx->used + grow > ctx->budget) return CDEF_ERR_NOMEM;
+    if (ctx->scratch) {
+        cudaFree(ctx->scratch);
+        ctx->used -= ctx->scratch_bytes;
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->scratch = nullptr;
+        return CDEF_ERR_NOMEM;
+    }
+    ctx->scratch_bytes = bytes;
+    ctx->used += bytes;
+    return CDEF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdef_ctx_create(cdef_ctx **out, int device, size_t hbm_budget_bytes)
+{
+    if (!out) return CDEF_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return device < 0 ? CDEF_ERR_ARG : CDEF_ERR_CUDA;
+    }
+    DeviceGuard g(device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    cdef_ctx *ctx = new (std::nothrow) cdef_ctx();
+    if (!ctx) return CDEF_ERR_NOMEM;
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    const size_t fixed = sizeof(int) + sizeof(SearchResultDev) * kMaxBatch;
+    if (ctx->budget && fixed > ctx->budget) {
+        delete ctx;
+        return CDEF_ERR_NOMEM;
+    }
+    if (cudaMalloc(&ctx->status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->dev_results, sizeof(SearchResultDev) * kMaxBatch) != cudaSuccess ||
+        cudaMallocHost(&ctx->host_results, sizeof(SearchResultDev) * kMaxBatch) != cudaSuccess) {
+        cudaGetLastError();
+        cdef_ctx_destroy(ctx);
+        return CDEF_ERR_CUDA;
+    }
+    ctx->used = fixed;
+    *out = ctx;
+    return CDEF_OK;
+}
+
+int cdef_ctx_destroy(cdef_ctx *ctx)
+{
+    if (!ctx) return CDEF_OK;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->status) cudaFree(ctx->status);
+    if (ctx->dev_results) cudaFree(ctx->dev_results);
+    if (ctx->host_results) cudaFreeHost(ctx->host_results);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    delete ctx;
+    return CDEF_OK;
+}
+
+int cdef_ctx_status(cdef_ctx *ctx, int clear)
+{
+    if (!ctx) return CDEF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    int v = 0;
+    if (cudaMemcpy(&v, ctx->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CDEF_ERR_CUDA;
+    if (clear && v && cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess) return CDEF_ERR_CUDA;
+    return v ? CDEF_ERR_ARG : CDEF_OK;
+}
+
+int cdef_find_dir(cdef_ctx *ctx, const cdef_plane *luma, int32_t bitdepth, uint8_t *dir,
+                  int32_t *var, void *cuda_stream)
+{
+    if (!ctx || !luma || !dir || !var) return CDEF_ERR_ARG;
+    if (bitdepth != 8 && bitdepth != 10 && bitdepth != 12) return CDEF_ERR_BITDEPTH;
+    const int w = luma->width, h = luma->height;
+    if (w <= 0 || h <= 0 || w % 8 || h % 8) return CDEF_ERR_SIZE;
+    int rc = check_plane(*luma, w, h, sample_bytes(bitdepth));
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    return cuda_status(launch_find_dir(static_cast<const uint8_t *>(luma->data), luma->pitch_bytes,
+                                       w, h, bitdepth, dir, var,
+                                       static_cast<cudaStream_t>(cuda_stream)));
+}
+
+int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params,
+                      const uint8_t *dir, const int32_t *var, const cdef_frame *out,
+                      void *cuda_stream)
+{
+    if (!ctx || !in || !out || !params) return CDEF_ERR_ARG;
+    if ((dir == nullptr) != (var == nullptr)) return CDEF_ERR_ARG;
+    int rc;
+    if ((rc = check_frame(in)) || (rc = check_frame(out))) return rc;
+    if (!same_geometry(in, out)) return CDEF_ERR_SIZE;
+    if (frames_overlap(in, out)) return CDEF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    FilterBatch<1> b;
+    b.n = 1;
+    b.total_blocks = fb_count(in);
+    fill_filter_frame(b.f[0], in, out, params, dir, var, 0);
+    return cuda_status(launch_filter_single(b, ctx->status, static_cast<cudaStream_t>(cuda_stream)));
+}
+
+int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
+                       const cdef_fb_params *const *params, const cdef_frame *out,
+                       void *cuda_stream)
+{
+    if (!ctx || !in || !out || !params || n <= 0 || n > kMaxBatch) return CDEF_ERR_ARG;
+    int start = 0;
+    for (int i = 0; i < n; i++) {
+        int rc;
+        if ((rc = check_frame(&in[i])) || (rc = check_frame(&out[i]))) return rc;
+        if (!same_geometry(&in[i], &out[i])) return CDEF_ERR_SIZE;
+        if (!params[i]) return CDEF_ERR_ARG;
+        for (int j = 0; j < n; j++)
+            if (frames_overlap(&in[j], &out[i])) return CDEF_ERR_ARG;
+        for (int j = 0; j < i; j++)
+            if (frames_overlap(&out[j], &out[i])) return CDEF_ERR_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    FilterBatch<kMaxBatch> *bp = new (std::nothrow) FilterBatch<kMaxBatch>();
+    if (!bp) return CDEF_ERR_NOMEM;
+    bp->n = n;
+    for (int i = 0; i < n; i++) {
+        fill_filter_frame(bp->f[i], &in[i], &out[i], params[i], nullptr, nullptr, start);
+        start += fb_count(&in[i]);
+    }
+    bp->total_blocks = start;
+    const int rc = cuda_status(launch_filter_batch(*bp, ctx->status, static_cast<cudaStream_t>(cuda_stream)));
+    delete bp;
+    return rc;
+}
+
+int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
+                          const int32_t *damping, const int64_t *lambda, int64_t *dist_luma,
+                          int64_t *dist_chroma, cdef_preset *presets, int32_t *npresets,
+                          uint8_t *block_ids, int64_t *cost, void *cuda_stream)
+{
+    if (!ctx || !rec || !src || !damping || !lambda || !presets || !npresets || !block_ids || !cost)
+        return CDEF_ERR_ARG;
+    if (n <= 0 || n > kMaxBatch) return CDEF_ERR_ARG;
+    if ((dist_luma == nullptr) != (dist_chroma == nullptr)) return CDEF_ERR_ARG;
+    SearchBatch *b = new (std::nothrow) SearchBatch();
+    if (!b) return CDEF_ERR_NOMEM;
+    int total = 0, rc = CDEF_OK;
+    for (int i = 0; i < n && rc == CDEF_OK; i++) {
+        if ((rc = check_frame(&rec[i])) || (rc = check_frame(&src[i]))) break;
+        if (!same_geometry(&rec[i], &src[i])) { rc = CDEF_ERR_SIZE; break; }
+        if (damping[i] < 3 || damping[i] > 6 || lambda[i] < 0) { rc = CDEF_ERR_ARG; break; }
+        SearchFrameDev &f = b->f[i];
+        const cdef_plane *pr[3] = {&rec[i].y, &rec[i].u, &rec[i].v};
+        const cdef_plane *ps[3] = {&src[i].y, &src[i].u, &src[i].v};
+        for (int k = 0; k < 3; k++) {
+            f.rec[k] = static_cast<const uint8_t *>(pr[k]->data);
+            f.src[k] = static_cast<const uint8_t *>(ps[k]->data);
+            f.rec_pitch[k] = pr[k]->pitch_bytes;
+            f.src_pitch[k] = ps[k]->pitch_bytes;
+        }
+        f.w = rec[i].y.width;
+        f.h = rec[i].y.height;
+        f.bitdepth = rec[i].bitdepth;
+        f.damping = damping[i];
+        f.fb_cols = (f.w + 63) / 64;
+        f.fb_rows = (f.h + 63) / 64;
+        f.block_start = total;
+        f.lambda = lambda[i];
+        total += f.fb_cols * f.fb_rows;
+    }
+    if (rc != CDEF_OK) { delete b; return rc; }
+    b->n = n;
+    b->total_blocks = total;
+
+    DeviceGuard g(ctx->device);
+    if (!g.ok) { delete b; return CDEF_ERR_CUDA; }
+    const size_t tables = dist_luma ? 0 : (size_t)total * 64 * sizeof(long long) * 2;
+    const size_t need = tables + (size_t)total * sizeof(long long);
+    if ((rc = ensure_scratch(ctx, need))) { delete b; return rc; }
+    long long *dl = reinterpret_cast<long long *>(dist_luma);
+    long long *dc = reinterpret_cast<long long *>(dist_chroma);
+    long long *cur = static_cast<long long *>(ctx->scratch);
+    if (!dl) {
+        dl = cur + total;
+        dc = dl + (size_t)total * 64;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = launch_search(*b, dl, dc, cur, ctx->dev_results, block_ids, ctx->status, s);
+    delete b;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->host_results, ctx->dev_results, sizeof(SearchResultDev) * n,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return CDEF_ERR_CUDA;
+    static const uint8_t kSec[4] = {0, 1, 2, 4};
+    for (int i = 0; i < n; i++) {
+        const SearchResultDev &r = ctx->host_results[i];
+        npresets[i] = r.npresets;
+        cost[i] = r.cost;
+        for (int k = 0; k < 8; k++) {
+            const int t = r.presets[k], ql = t >> 6, qc = t & 63;
+            cdef_preset &p = presets[i * 8 + k];
+            p.pri_y = (uint8_t)(ql >> 2);
+            p.sec_y = kSec[ql & 3];
+            p.pri_uv = (uint8_t)(qc >> 2);
+            p.sec_uv = kSec[qc & 3];
+        }
+    }
+    return CDEF_OK;
+}
+
+const char *cdef_strerror(int status)
+{
+    switch (status) {
+    case CDEF_OK: return "ok";
+    case CDEF_ERR_ARG: return "invalid argument";
+    case CDEF_ERR_SIZE: return "invalid frame size";
+    case CDEF_ERR_BITDEPTH: return "unsupported bit depth";
+    case CDEF_ERR_NOMEM: return "out of device memory or over budget";
+    case CDEF_ERR_CUDA: return "CUDA error";
+    case CDEF_ERR_TIMEOUT: return "bounded device wait timed out";
+    case CDEF_ERR_DEVICE: return "device-side consistency error";
+    default: return "unknown status";
+    }
+}
+
+const char *cdef_version(void) { return "cdef_gb300 0.1 sm_103a"; }
+
+}  // extern "C"

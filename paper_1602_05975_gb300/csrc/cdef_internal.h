@@ -1,0 +1,86 @@
+// Internal (not exported) descriptors and launchers shared by the C-ABI
+// layer and the kernels of cdef_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/cdef_gb300.h"
+
+namespace cdefgb {
+
+constexpr int kMaxBatch = 64;  // frames per batched launch
+
+// One plane as a kernel sees it.
+struct PlaneDev {
+    const uint8_t *in;   // input samples (device)
+    uint8_t *out;        // output samples (device); unused by the search
+    int64_t in_pitch;    // bytes
+    int64_t out_pitch;   // bytes
+    int w, h;            // samples
+};
+
+// One frame of a filter launch.
+struct FilterFrameDev {
+    PlaneDev p[3];                   // y, u, v
+    const cdef_fb_params *params;    // B entries
+    const uint8_t *dir;              // optional 8x8 maps (NULL: fused search)
+    const int32_t *var;
+    int bitdepth;
+    int fb_cols, fb_rows;
+    int block_start;                 // first CTA index of this frame
+};
+
+template <int MAXF>
+struct FilterBatch {
+    int n;
+    int total_blocks;
+    FilterFrameDev f[MAXF];
+};
+
+// One frame of a strength search launch.
+struct SearchFrameDev {
+    const uint8_t *rec[3];
+    const uint8_t *src[3];
+    int64_t rec_pitch[3], src_pitch[3];
+    int w, h;                        // luma size
+    int bitdepth;
+    int damping;
+    int fb_cols, fb_rows;
+    int block_start;                 // first filter block of this frame in the tables
+    long long lambda;
+};
+
+struct SearchBatch {
+    int n;
+    int total_blocks;
+    SearchFrameDev f[kMaxBatch];
+};
+
+// Per-frame result of the preset search (device).
+struct SearchResultDev {
+    int presets[8];
+    long long totals[8];
+    long long cost;
+    int npresets;
+    int pad;
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_find_dir(const uint8_t *luma, int64_t pitch, int w, int h,
+                            int bitdepth, uint8_t *dir, int32_t *var,
+                            cudaStream_t s);
+cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status,
+                                 cudaStream_t s);
+cudaError_t launch_filter_batch(const FilterBatch<kMaxBatch> &b, int *status,
+                                cudaStream_t s);
+cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
+                          long long *dist_chroma, long long *cur,
+                          SearchResultDev *results, uint8_t *block_ids,
+                          int *status, cudaStream_t s);
+
+// Device status word values (set by kernels, read by the host).
+constexpr int kStatusBadParams = 1;
+
+}  // namespace cdefgb

@@ -1,0 +1,261 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, bit for
+bit on every direction, contrast, output sample and int64 distortion.  All
+integer work: the tolerance is zero."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cdef():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1602_05975_gb300 import build, cdef as _c
+    build.build()
+    _c.load()
+    return _c
+
+
+@pytest.fixture(scope="module")
+def ctx(cdef):
+    c = cdef.Context(0)
+    yield c
+    c.close()
+
+
+def _gpu_filter(cdef, ctx, planes, bd, params, with_maps=False):
+    h, w = planes[0].shape
+    inp = cdef.frame_from_numpy(planes, bd)
+    out = cdef.alloc_frame(w, h, bd, fill=0)
+    prm = cdef.params_tensor(params)
+    if with_maps:
+        dirs = torch.zeros((h // 8) * (w // 8), dtype=torch.uint8, device="cuda")
+        var = torch.zeros((h // 8) * (w // 8), dtype=torch.int32, device="cuda")
+        cdef.cdef_find_dir(ctx, inp.y, w, h, bd, dirs, var)
+        cdef.cdef_filter_frame(ctx, inp, prm, out, dirs, var)
+    else:
+        cdef.cdef_filter_frame(ctx, inp, prm, out)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    return out.to_numpy()
+
+
+def _assert_frames_equal(got, exp):
+    for g, e, name in zip(got, exp, "yuv"):
+        bad = np.argwhere(g != e)
+        assert bad.size == 0, f"plane {name}: {len(bad)} mismatches, first at {bad[:5].tolist()}"
+
+
+# --------------------------------------------------------------- direction search
+@pytest.mark.parametrize("w,h,bd,kind", [
+    (8, 8, 8, "rand"), (352, 288, 8, "synth"), (136, 72, 10, "rand"),
+    (200, 96, 10, "synth"), (64, 48, 12, "rand"), (1024, 8, 8, "rand")])
+def test_find_dir_parity(cdef, ctx, ref, w, h, bd, kind):
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(w + h + bd)
+    if kind == "rand":
+        y = synth.random_frame_planes(rng, w, h, bd)[0]
+    else:
+        y = synth.make_frame(w, h, bd, 32, seed=5).rec[0]
+    inp = cdef.frame_from_numpy((y, y[::2, ::2], y[::2, ::2]), bd)
+    dirs = torch.zeros((h // 8) * (w // 8), dtype=torch.uint8, device="cuda")
+    var = torch.zeros_like(dirs, dtype=torch.int32)
+    cdef.cdef_find_dir(ctx, inp.y, w, h, bd, dirs, var)
+    torch.cuda.synchronize()
+    ed, ev = ref.find_dir(y, bd)
+    assert np.array_equal(dirs.cpu().numpy().reshape(ed.shape), ed)
+    assert np.array_equal(var.cpu().numpy().reshape(ev.shape), ev)
+
+
+def test_find_dir_extremes(cdef, ctx, ref):
+    """Constant, perfectly directional and maximum-contrast blocks."""
+    blocks = [np.full((8, 8), 0), np.full((8, 8), 255),
+              np.where(np.indices((8, 8)).sum(0) % 2 == 0, 255, 0)]
+    ii, jj = np.indices((8, 8))
+    for key in (ii + jj, ii, jj, ii - jj + 7, ii + jj // 2, ii // 2 + jj):
+        blocks.append((key * 37) % 256)
+    y = np.concatenate(blocks, axis=1).astype(np.uint16)
+    h, w = y.shape
+    inp = cdef.frame_from_numpy((y, y[::2, ::2], y[::2, ::2]), 8)
+    dirs = torch.zeros(w // 8, dtype=torch.uint8, device="cuda")
+    var = torch.zeros(w // 8, dtype=torch.int32, device="cuda")
+    cdef.cdef_find_dir(ctx, inp.y, w, h, 8, dirs, var)
+    torch.cuda.synchronize()
+    ed, ev = ref.find_dir(y, 8)
+    assert np.array_equal(dirs.cpu().numpy(), ed.reshape(-1))
+    assert np.array_equal(var.cpu().numpy(), ev.reshape(-1))
+
+
+# --------------------------------------------------------------- filter
+FILTER_CASES = [
+    (8, 8, 8, "rand"), (16, 8, 8, "rand"), (72, 72, 8, "rand"), (72, 72, 10, "rand"),
+    (352, 288, 8, "synth"), (136, 80, 10, "synth"), (200, 136, 8, "synth"),
+    (64, 64, 10, "rand"), (120, 16, 12, "rand"), (8, 200, 8, "synth"),
+]
+
+
+@pytest.mark.parametrize("w,h,bd,kind", FILTER_CASES)
+@pytest.mark.parametrize("with_maps", [False, True])
+def test_filter_parity(cdef, ctx, ref, w, h, bd, kind, with_maps):
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(w * 7 + h * 3 + bd)
+    if kind == "rand":
+        planes = synth.random_frame_planes(rng, w, h, bd)
+    else:
+        planes = synth.make_frame(w, h, min(bd, 10), 32, seed=w + h).rec
+        if bd == 12:
+            planes = tuple(p << 2 for p in planes)
+    prm = synth.random_params(rng, w, h)
+    got = _gpu_filter(cdef, ctx, planes, bd, prm, with_maps)
+    exp = ref.filter_frame(*planes, bd, prm)
+    _assert_frames_equal(got, exp)
+
+
+@pytest.mark.parametrize("bd", [8, 10])
+def test_filter_every_strength(cdef, ctx, ref, bd):
+    """Every (primary, secondary, damping) combination, one per filter block,
+    including the special values 19 and 7."""
+    from paper_1602_05975_gb300 import synth
+    combos = [(p, s, d) for p in list(range(16)) + [19] for s in (0, 1, 2, 4, 7) for d in (3, 4, 5, 6)]
+    fbc = 20
+    fbr = -(-len(combos) // fbc)
+    w, h = fbc * 64, fbr * 64
+    fr = synth.make_frame(w, h, bd, 64, seed=bd)
+    prm = np.zeros((fbr, fbc, 8), np.uint8)
+    rng = np.random.default_rng(bd)
+    for k, (p, s, d) in enumerate(combos):
+        prm[k // fbc, k % fbc, :5] = (p, s, combos[-1 - k][0], combos[-1 - k][1], d)
+    got = _gpu_filter(cdef, ctx, fr.rec, bd, prm)
+    exp = ref.filter_frame(*fr.rec, bd, prm)
+    _assert_frames_equal(got, exp)
+    del rng
+
+
+def test_filter_extreme_planes(cdef, ctx, ref):
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(99)
+    for bd in (8, 10):
+        mx = (1 << bd) - 1
+        for planes in (
+            tuple(np.zeros(s, np.uint16) for s in ((40, 48), (20, 24), (20, 24))),
+            tuple(np.full(s, mx, np.uint16) for s in ((40, 48), (20, 24), (20, 24))),
+            tuple((rng.integers(0, 2, s) * mx).astype(np.uint16) for s in ((40, 48), (20, 24), (20, 24))),
+        ):
+            prm = synth.random_params(rng, 48, 40)
+            prm[..., 0] = 15
+            prm[..., 1] = 4
+            got = _gpu_filter(cdef, ctx, planes, bd, prm)
+            exp = ref.filter_frame(*planes, bd, prm)
+            _assert_frames_equal(got, exp)
+
+
+def test_filter_batch_mixed(cdef, ctx, ref):
+    """One launch over frames of different sizes and bit depths equals each
+    frame filtered alone."""
+    from paper_1602_05975_gb300 import synth
+    specs = [(136, 72, 8), (64, 64, 10), (352, 288, 8), (8, 8, 10), (200, 136, 10)]
+    frames, ins, outs, prms = [], [], [], []
+    for k, (w, h, bd) in enumerate(specs):
+        fr = synth.make_frame(w, h, bd, 32, seed=100 + k)
+        frames.append(fr)
+        ins.append(cdef.frame_from_numpy(fr.rec, bd))
+        outs.append(cdef.alloc_frame(w, h, bd, fill=0))
+        prms.append(cdef.params_tensor(fr.params))
+    cdef.cdef_filter_frames(ctx, ins, prms, outs)
+    torch.cuda.synchronize()
+    for fr, o in zip(frames, outs):
+        _assert_frames_equal(o.to_numpy(), ref.filter_frame(*fr.rec, fr.bitdepth, fr.params))
+
+
+def test_invalid_params_flagged(cdef, ctx):
+    from paper_1602_05975_gb300 import synth
+    fr = synth.make_frame(128, 64, 8, 32, seed=7)
+    prm = fr.params.copy()
+    prm[0, 1, 0] = 16  # primary strength out of range
+    inp = cdef.frame_from_numpy(fr.rec, 8)
+    out = cdef.alloc_frame(128, 64, 8, fill=0)
+    ctx.status(clear=True)
+    cdef.cdef_filter_frame(ctx, inp, cdef.params_tensor(prm), out)
+    torch.cuda.synchronize()
+    assert ctx.status(clear=True) == -1
+    y = out.to_numpy()[0]
+    assert np.array_equal(y[:, 64:128], fr.rec[0][:, 64:128])  # block left unfiltered
+    assert ctx.status() == 0
+
+
+def test_argument_errors(cdef, ctx):
+    f = cdef.alloc_frame(64, 64, 8)
+    o = cdef.alloc_frame(64, 64, 8)
+    prm = torch.zeros(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(cdef.CdefError) as e:
+        cdef.cdef_filter_frame(ctx, f, prm, f)  # in-place
+    assert e.value.status == -1
+    bad = cdef.Frame(f.y, f.u, f.v, 60, 64, 8)  # width not a multiple of 8
+    with pytest.raises(cdef.CdefError) as e:
+        cdef.cdef_filter_frame(ctx, bad, prm, o)
+    assert e.value.status == -2
+    o10 = cdef.alloc_frame(64, 64, 10)
+    with pytest.raises(cdef.CdefError) as e:
+        cdef.cdef_filter_frame(ctx, f, prm, o10)  # bit depth mismatch
+    assert e.value.status == -2
+    odd = cdef.Frame(f.y[:, 1:], f.u, f.v, 56, 64, 8)  # misaligned data pointer
+    with pytest.raises(cdef.CdefError) as e:
+        cdef.cdef_filter_frame(ctx, odd, prm, o)
+    assert e.value.status == -1
+    b7 = cdef.Frame(f.y, f.u, f.v, 64, 64, 7)
+    with pytest.raises(cdef.CdefError) as e:
+        cdef.cdef_filter_frame(ctx, b7, prm, o)
+    assert e.value.status == -3
+
+
+# --------------------------------------------------------------- strength search
+SEARCH_CASES = [
+    [(128, 72, 8)],
+    [(80, 64, 10)],
+    [(64, 64, 8), (136, 72, 8), (72, 136, 10)],
+    [(8, 8, 8)],
+]
+
+
+@pytest.mark.parametrize("specs", SEARCH_CASES)
+def test_search_parity(cdef, ctx, ref, specs):
+    from paper_1602_05975_gb300 import synth
+    frames = [synth.make_frame(w, h, bd, None, seed=200 + k) for k, (w, h, bd) in enumerate(specs)]
+    recs = [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames]
+    srcs = [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames]
+    nbs = [f.params.shape[0] * f.params.shape[1] for f in frames]
+    tot = sum(nbs)
+    damping = [3 + (k % 4) for k in range(len(frames))]
+    lambdas = [int(f.q) ** 2 * (1 << (2 * (f.bitdepth - 8))) for f in frames]
+    ids = torch.zeros(tot, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(tot * 64, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(tot * 64, dtype=torch.int64, device="cuda")
+    res = cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc)
+    dl, dc, ids = dl.cpu().numpy(), dc.cpu().numpy(), ids.cpu().numpy()
+    off = 0
+    for k, f in enumerate(frames):
+        o = ref.search_strengths(f.rec, f.src, f.bitdepth, damping[k], lambdas[k])
+        nb = nbs[k]
+        assert np.array_equal(dl[off * 64:(off + nb) * 64].reshape(nb, 64), o["dist_luma"])
+        assert np.array_equal(dc[off * 64:(off + nb) * 64].reshape(nb, 64), o["dist_chroma"])
+        assert res[k]["npresets"] == o["npresets"]
+        assert res[k]["cost"] == o["cost"]
+        got_t = [cdef.preset_index(p) for p in res[k]["presets"]]
+        assert got_t == list(o["presets"])
+        assert np.array_equal(ids[off:off + nb], o["block_ids"])
+        off += nb
+
+
+def test_search_scratch_tables(cdef, ctx, ref):
+    """With no caller tables the context's scratch is used; presets equal."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(136, 72, 8, 16, seed=300)
+    ids = torch.zeros(6, dtype=torch.uint8, device="cuda")
+    res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(f.rec, 8)],
+                                     [cdef.frame_from_numpy(f.src, 8)], [5], [256], ids)[0]
+    o = ref.search_strengths(f.rec, f.src, 8, 5, 256)
+    assert res["cost"] == o["cost"] and res["npresets"] == o["npresets"]
+    assert np.array_equal(ids.cpu().numpy(), o["block_ids"])
