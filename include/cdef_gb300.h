@@ -179,6 +179,42 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
                           int32_t *npresets, uint8_t *block_ids, int64_t *cost,
                           void *cuda_stream);
 
+/* The strength search without any memory allocation.  The paper has no
+ * counterpart: this is a deployment variant of cdef_search_strengths.
+ *
+ * Some callers may not allocate device memory once they are running: a
+ * codec embedded in a host application that hands it a fixed memory budget
+ * up front, or a real-time encoder loop that cannot afford the implicit
+ * device-wide synchronisation cudaMalloc/cudaFree may cause.  For them this
+ * entry point takes no context and calls no allocating routine.  The only
+ * device scratch it needs (one int64 per filter block for the greedy
+ * search's running minima, plus one result record per frame) lives in a
+ * fixed array inside the library, which every GPU that loads the library
+ * holds until the process exits: about 135 KiB.
+ *
+ *   - Same arguments, results and errors as cdef_search_strengths, except
+ *     that there is no context and dist_luma / dist_chroma are required
+ *     (device, sum_i B_i * 64 int64 each): the tables are outputs the caller
+ *     provides.  Runs on the current device; the stream must belong to it.
+ *   - At most CDEF_NOALLOC_MAX_BLOCKS filter blocks in total over the n
+ *     frames (e.g. 8 frames of 3840x2160); beyond that it returns
+ *     CDEF_ERR_NOMEM before doing any work.
+ *   - The first call on a device looks up the device address of the array
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - All calls on a device share the one array and it keeps the last
+ *     call's contents (every word the kernels read is written earlier in the
+ *     same call).  Calls whose work overlaps on the GPU -- on different
+ *     streams, or from several host threads -- race on it: serialise them.
+ *   - Synchronises the stream before returning (host outputs). */
+#define CDEF_NOALLOC_MAX_BLOCKS 16384
+int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
+                                  const cdef_frame *src, const int32_t *damping,
+                                  const int64_t *lambda, int64_t *dist_luma,
+                                  int64_t *dist_chroma, cdef_preset *presets,
+                                  int32_t *npresets, uint8_t *block_ids,
+                                  int64_t *cost, void *cuda_stream);
+
 /* A static description of a status code. */
 const char *cdef_strerror(int status);
 

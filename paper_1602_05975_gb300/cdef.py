@@ -265,6 +265,36 @@ def cdef_search_strengths(ctx: Context, recs, srcs, damping, lambdas, block_ids:
     return out
 
 
+def cdef_search_strengths_noalloc(recs, srcs, damping, lambdas, block_ids: torch.Tensor,
+                                  dist_luma: torch.Tensor, dist_chroma: torch.Tensor,
+                                  stream=None):
+    """The strength search through the entry point that allocates nothing
+    (no context; the caller provides the distortion tables).  Runs on the
+    current CUDA device.  Same result format as cdef_search_strengths."""
+    L = load()
+    fn = L.cdef_search_strengths_noalloc
+    i32, i64, vp = C.c_int32, C.c_int64, C.c_void_p
+    fn.argtypes = [i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(i32),
+                   C.POINTER(i64), vp, vp, C.POINTER(Preset), C.POINTER(i32), vp,
+                   C.POINTER(i64), vp]
+    fn.restype = C.c_int
+    n = len(recs)
+    ri = (FrameDesc * n)(*[f.desc() for f in recs])
+    si = (FrameDesc * n)(*[f.desc() for f in srcs])
+    presets = (Preset * (8 * n))()
+    npre = (C.c_int32 * n)()
+    cost = (C.c_int64 * n)()
+    _check(fn(n, ri, si, (C.c_int32 * n)(*damping), (C.c_int64 * n)(*lambdas),
+              dist_luma.data_ptr(), dist_chroma.data_ptr(), presets, npre,
+              block_ids.data_ptr(), cost, _stream_ptr(stream)),
+           "cdef_search_strengths_noalloc")
+    out = []
+    for i in range(n):
+        ps = [(p.pri_y, p.sec_y, p.pri_uv, p.sec_uv) for p in presets[i * 8:(i + 1) * 8]]
+        out.append(dict(presets=ps, npresets=npre[i], cost=cost[i]))
+    return out
+
+
 def preset_index(p) -> int:
     """(pri_y, sec_y, pri_uv, sec_uv) -> luma_pair * 64 + chroma_pair."""
     return (p[0] * 4 + SEC_VALUES.index(p[1])) * 64 + p[2] * 4 + SEC_VALUES.index(p[3])
