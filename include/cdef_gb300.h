@@ -93,8 +93,10 @@ int cdef_ctx_destroy(cdef_ctx *ctx);
 /* Kernel-reported errors since the last clear.  Strength values out of the
  * ranges above are found on the device (the parameters live in device
  * memory): the block is then left unfiltered and the context's status word
- * is set.  Waits for all work on the device, then returns CDEF_OK or
- * CDEF_ERR_ARG; clear != 0 resets the word. */
+ * is set.  A bounded device-side wait that gave up (tile loads that never
+ * arrived) also sets it, leaving its block unwritten.  Waits for all work on
+ * the device, then returns CDEF_OK, CDEF_ERR_TIMEOUT or CDEF_ERR_ARG;
+ * clear != 0 resets the word. */
 int cdef_ctx_status(cdef_ctx *ctx, int clear);
 
 /* Direction search, section 2, eq. 1-5 and Algorithm 1.
@@ -136,7 +138,7 @@ int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in,
  * in one kernel launch (the fused direction search is always used).
  *   in, out : HOST arrays of n frame descriptors
  *   params  : HOST array of n DEVICE pointers, params[i] has B_i entries
- * n <= 64.  Equivalent to n calls of cdef_filter_frame with dir = NULL. */
+ * n <= 48.  Equivalent to n calls of cdef_filter_frame with dir = NULL. */
 int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
                        const cdef_fb_params *const *params,
                        const cdef_frame *out, void *cuda_stream);

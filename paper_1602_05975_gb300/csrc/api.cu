@@ -1,10 +1,13 @@
 // C ABI of cdef_gb300: argument validation, the context (device scratch and
 // pinned staging), and the launches.  See include/cdef_gb300.h.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "cdef_internal.h"
@@ -90,9 +93,44 @@ bool frames_overlap(const cdef_frame *a, const cdef_frame *b)
 
 int fb_count(const cdef_frame *f) { return ((f->y.width + 63) / 64) * ((f->y.height + 63) / 64); }
 
-void fill_filter_frame(FilterFrameDev &d, const cdef_frame *in, const cdef_frame *out,
-                       const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
-                       int block_start)
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D tile map of one plane with the given box (columns x rows).
+int encode_plane(CUtensorMap *m, const cdef_plane &p, int bytes, int box_cols, int box_rows)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return CDEF_ERR_CUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)p.width, (cuuint64_t)p.height};
+    const cuuint64_t strides[1] = {(cuuint64_t)p.pitch_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                          2, p.data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? CDEF_OK : CDEF_ERR_CUDA;
+}
+
+int fill_filter_frame(FilterFrameDev &d, const cdef_frame *in, const cdef_frame *out,
+                      const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
+                      int block_start)
 {
     const cdef_plane *pi[3] = {&in->y, &in->u, &in->v};
     const cdef_plane *po[3] = {&out->y, &out->u, &out->v};
@@ -111,6 +149,11 @@ void fill_filter_frame(FilterFrameDev &d, const cdef_frame *in, const cdef_frame
     d.fb_cols = (in->y.width + 63) / 64;
     d.fb_rows = (in->y.height + 63) / 64;
     d.block_start = block_start;
+    const int b = sample_bytes(in->bitdepth);
+    int rc;
+    if ((rc = encode_plane(&d.tmap[0], in->y, b, luma_box_cols(b), kLumaBoxRows))) return rc;
+    if ((rc = encode_plane(&d.tmap[1], in->u, b, chroma_box_cols(b), kChromaBoxRows))) return rc;
+    return encode_plane(&d.tmap[2], in->v, b, chroma_box_cols(b), kChromaBoxRows);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? CDEF_OK : CDEF_ERR_CUDA; }
@@ -194,6 +237,8 @@ int cdef_ctx_status(cdef_ctx *ctx, int clear)
     if (cudaMemcpy(&v, ctx->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return CDEF_ERR_CUDA;
     if (clear && v && cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess) return CDEF_ERR_CUDA;
+    if (v & kStatusTimeout) return CDEF_ERR_TIMEOUT;
+    if (v & kStatusMisaligned) return CDEF_ERR_DEVICE;
     return v ? CDEF_ERR_ARG : CDEF_OK;
 }
 
@@ -228,7 +273,7 @@ int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params 
     FilterBatch<1> b;
     b.n = 1;
     b.total_blocks = fb_count(in);
-    fill_filter_frame(b.f[0], in, out, params, dir, var, 0);
+    if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0))) return rc;
     return cuda_status(launch_filter_single(b, ctx->status, static_cast<cudaStream_t>(cuda_stream)));
 }
 
@@ -236,7 +281,7 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
                        const cdef_fb_params *const *params, const cdef_frame *out,
                        void *cuda_stream)
 {
-    if (!ctx || !in || !out || !params || n <= 0 || n > kMaxBatch) return CDEF_ERR_ARG;
+    if (!ctx || !in || !out || !params || n <= 0 || n > kMaxFilterBatch) return CDEF_ERR_ARG;
     int start = 0;
     for (int i = 0; i < n; i++) {
         int rc;
@@ -250,11 +295,15 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
     }
     DeviceGuard g(ctx->device);
     if (!g.ok) return CDEF_ERR_CUDA;
-    FilterBatch<kMaxBatch> *bp = new (std::nothrow) FilterBatch<kMaxBatch>();
+    FilterBatch<kMaxFilterBatch> *bp = new (std::nothrow) FilterBatch<kMaxFilterBatch>();
     if (!bp) return CDEF_ERR_NOMEM;
     bp->n = n;
     for (int i = 0; i < n; i++) {
-        fill_filter_frame(bp->f[i], &in[i], &out[i], params[i], nullptr, nullptr, start);
+        const int rc = fill_filter_frame(bp->f[i], &in[i], &out[i], params[i], nullptr, nullptr, start);
+        if (rc) {
+            delete bp;
+            return rc;
+        }
         start += fb_count(&in[i]);
     }
     bp->total_blocks = start;

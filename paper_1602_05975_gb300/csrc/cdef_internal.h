@@ -2,6 +2,7 @@
 // layer and the kernels of cdef_gb300.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -10,7 +11,8 @@
 
 namespace cdefgb {
 
-constexpr int kMaxBatch = 64;  // frames per batched launch
+constexpr int kMaxBatch = 64;        // frames per batched search launch
+constexpr int kMaxFilterBatch = 48;  // frames per batched filter launch (kernel-parameter space)
 
 // One plane as a kernel sees it.
 struct PlaneDev {
@@ -22,7 +24,8 @@ struct PlaneDev {
 };
 
 // One frame of a filter launch.
-struct FilterFrameDev {
+struct alignas(64) FilterFrameDev {
+    CUtensorMap tmap[3];             // 2-D tile maps of the y, u, v input planes
     PlaneDev p[3];                   // y, u, v
     const cdef_fb_params *params;    // B entries
     const uint8_t *dir;              // optional 8x8 maps (NULL: fused search)
@@ -73,8 +76,17 @@ cudaError_t launch_find_dir(const uint8_t *luma, int64_t pitch, int w, int h,
                             cudaStream_t s);
 cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status,
                                  cudaStream_t s);
-cudaError_t launch_filter_batch(const FilterBatch<kMaxBatch> &b, int *status,
+cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *status,
                                 cudaStream_t s);
+
+// Filter tile geometry shared by the host (tensor-map boxes) and the kernel.
+// The luma box starts 8 (16-bit) or 16 (8-bit) columns left of the filter
+// block so that its first column is 16-byte aligned, and 2 rows above.
+constexpr int kLumaBoxRows = 68;
+constexpr int kChromaBoxRows = 36;
+__host__ __device__ constexpr int luma_box_cols(int bytes) { return bytes == 2 ? 80 : 96; }
+__host__ __device__ constexpr int chroma_box_cols(int bytes) { return bytes == 2 ? 48 : 64; }
+__host__ __device__ constexpr int box_lead(int bytes) { return bytes == 2 ? 8 : 16; }
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
                           long long *dist_chroma, long long *cur,
                           SearchResultDev *results, uint8_t *block_ids,
@@ -82,5 +94,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
 
 // Device status word values (set by kernels, read by the host).
 constexpr int kStatusBadParams = 1;
+constexpr int kStatusTimeout = 2;
+constexpr int kStatusMisaligned = 4;  // internal: shared memory not aligned for tile loads
 
 }  // namespace cdefgb
