@@ -23,6 +23,8 @@ struct cdef_ctx {
     size_t scratch_bytes;
     SearchResultDev *host_results;  // pinned
     SearchResultDev *dev_results;
+    unsigned *work;       // kWorkSlots pairs of filter work counters (zeroed)
+    unsigned next_slot;   // next pair handed to a launch
 };
 
 namespace {
@@ -198,7 +200,8 @@ int cdef_ctx_create(cdef_ctx **out, int device, size_t hbm_budget_bytes)
     if (!ctx) return CDEF_ERR_NOMEM;
     ctx->device = device;
     ctx->budget = hbm_budget_bytes;
-    const size_t fixed = sizeof(int) + sizeof(SearchResultDev) * kMaxBatch;
+    const size_t fixed = sizeof(int) + sizeof(SearchResultDev) * kMaxBatch +
+                         sizeof(unsigned) * 2 * kWorkSlots;
     if (ctx->budget && fixed > ctx->budget) {
         delete ctx;
         return CDEF_ERR_NOMEM;
@@ -206,6 +209,8 @@ int cdef_ctx_create(cdef_ctx **out, int device, size_t hbm_budget_bytes)
     if (cudaMalloc(&ctx->status, sizeof(int)) != cudaSuccess ||
         cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&ctx->dev_results, sizeof(SearchResultDev) * kMaxBatch) != cudaSuccess ||
+        cudaMalloc(&ctx->work, sizeof(unsigned) * 2 * kWorkSlots) != cudaSuccess ||
+        cudaMemset(ctx->work, 0, sizeof(unsigned) * 2 * kWorkSlots) != cudaSuccess ||
         cudaMallocHost(&ctx->host_results, sizeof(SearchResultDev) * kMaxBatch) != cudaSuccess) {
         cudaGetLastError();
         cdef_ctx_destroy(ctx);
@@ -225,6 +230,7 @@ int cdef_ctx_destroy(cdef_ctx *ctx)
     if (ctx->dev_results) cudaFree(ctx->dev_results);
     if (ctx->host_results) cudaFreeHost(ctx->host_results);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->work) cudaFree(ctx->work);
     delete ctx;
     return CDEF_OK;
 }
@@ -274,7 +280,8 @@ int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params 
     b.n = 1;
     b.total_blocks = fb_count(in);
     if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0))) return rc;
-    return cuda_status(launch_filter_single(b, ctx->status, static_cast<cudaStream_t>(cuda_stream)));
+    unsigned *work = ctx->work + 2 * (ctx->next_slot++ % kWorkSlots);
+    return cuda_status(launch_filter_single(b, ctx->status, work, static_cast<cudaStream_t>(cuda_stream)));
 }
 
 int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
@@ -307,7 +314,8 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
         start += fb_count(&in[i]);
     }
     bp->total_blocks = start;
-    const int rc = cuda_status(launch_filter_batch(*bp, ctx->status, static_cast<cudaStream_t>(cuda_stream)));
+    unsigned *work = ctx->work + 2 * (ctx->next_slot++ % kWorkSlots);
+    const int rc = cuda_status(launch_filter_batch(*bp, ctx->status, work, static_cast<cudaStream_t>(cuda_stream)));
     delete bp;
     return rc;
 }

@@ -74,10 +74,13 @@ struct SearchResultDev {
 cudaError_t launch_find_dir(const uint8_t *luma, int64_t pitch, int w, int h,
                             int bitdepth, uint8_t *dir, int32_t *var,
                             cudaStream_t s);
-cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status,
+// `work` is a pair of zeroed device counters owned by this launch until it
+// completes (the kernel leaves them zeroed again).
+cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status, unsigned *work,
                                  cudaStream_t s);
 cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *status,
-                                cudaStream_t s);
+                                unsigned *work, cudaStream_t s);
+constexpr int kWorkSlots = 1024;  // counter pairs per context (launches in flight at once)
 
 // Filter tile geometry shared by the host (tensor-map boxes) and the kernel.
 // The luma box starts 8 (16-bit) or 16 (8-bit) columns left of the filter

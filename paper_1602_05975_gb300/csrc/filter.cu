@@ -91,6 +91,7 @@ struct FilterSmem {
     BlockC cb;
     uint8_t dir[64];
     int var[64];
+    int blk[2];                                         // block id of each raw buffer
     alignas(8) uint64_t bar[2];
 };
 
@@ -482,7 +483,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         uint8_t *o_a = (luma ? F.p[0].out : F.p[1].out) + (int64_t)oy * (luma ? F.p[0].out_pitch : F.p[1].out_pitch);
         uint8_t *o_b = F.p[2].out + (int64_t)oy * F.p[2].out_pitch;
         const int64_t pa = luma ? F.p[0].out_pitch : F.p[1].out_pitch, pb = F.p[2].out_pitch;
-#pragma unroll 2
+#pragma unroll 1  // a compact loop body: the hot code has to stay in the instruction cache
         for (int i = 0; i < rows; i++) {
             const uint32_t *b = base + i * pitch;
             const uint32_t X = b[0];
@@ -539,56 +540,73 @@ __device__ __forceinline__ void issue_loads(const FilterBatch<MAXF> &batch, int 
     tma_load_2d(raw.v, &F.tmap[2], r.fbx * 32 - lead, r.fby * 32 - 2, bar);
 }
 
-// Persistent: each CTA walks blocks blockIdx.x, + gridDim.x, ...; the tiles
-// of its next block are loaded while it filters the current one.
+// Persistent: each CTA takes blocks from the launch's work counter
+// (work[0], dynamic so that blocks of uneven cost balance out); the tiles of
+// its next block are loaded while it filters the current one.  The last CTA
+// to finish resets the counter pair (work[1] counts finished CTAs), so a
+// counter slot is ready for its next launch.
 template <int MAXF>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
-filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status)
+filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsigned *work)
 {
     // A direct cast keeps every access in the shared state space (LDS/STS).
     extern __shared__ __align__(128) uint8_t smem_bytes[];
     FilterSmem &sm = *reinterpret_cast<FilterSmem *>(smem_bytes);
     const int tid = threadIdx.x;
     const int total = batch.total_blocks;
-    int blk = blockIdx.x;
-    if (blk >= total) return;
+
     if (smem_u32(smem_bytes) & 127) {  // the tile loads need 128-byte aligned destinations
         if (tid == 0) atomicOr(status, kStatusMisaligned);
-        return;
-    }
-
-    if (tid == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
-        issue_loads(batch, blk, sm.raw[0], &sm.bar[0]);
-    }
-    if (tid < 192) {  // tap offset tables [luma/chroma][d][tap]
-        const int pl = tid / 96, d = (tid / 12) & 7, t = tid % 12;
-        int dr, dc;
-        tap_rc(d, t, dr, dc);
-        sm.off[pl][d][t] = pl == 0 ? luma_off(dr, dc) : dr * kChromaPitch + dc;
-    }
-    __syncthreads();
-
-    for (int it = 0; blk < total; it++, blk += gridDim.x) {
-        const int buf = it & 1;
-        const int nxt = blk + gridDim.x;
-        if (tid == 0 && nxt < total) issue_loads(batch, nxt, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
-        const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, kWaitCycles);
-        if (__syncthreads_or(!arrived)) {  // the whole CTA leaves together
-            if (tid == 0) {
-                atomicOr(status, kStatusTimeout);
-                if (nxt < total) mbar_wait_bounded(&sm.bar[buf ^ 1], ((it + 1) >> 1) & 1, kWaitCycles);
-            }
-            return;
+    } else {
+        if (tid == 0) {
+            mbar_init(&sm.bar[0], 1);
+            mbar_init(&sm.bar[1], 1);
+            const int b = (int)atomicAdd(&work[0], 1u);
+            sm.blk[0] = b;
+            if (b < total) issue_loads(batch, b, sm.raw[0], &sm.bar[0]);
         }
-        const BlockRef r = locate(batch, blk);
-        const FilterFrameDev &F = batch.f[r.fi];
-        if (F.bitdepth == 8)
-            process_block<uint8_t>(F, r.fby, r.fbx, status, sm, sm.raw[buf]);
-        else
-            process_block<uint16_t>(F, r.fby, r.fbx, status, sm, sm.raw[buf]);
-        __syncthreads();  // shared tiles and tables are free for the next block
+        if (tid < 192) {  // tap offset tables [luma/chroma][d][tap]
+            const int pl = tid / 96, d = (tid / 12) & 7, t = tid % 12;
+            int dr, dc;
+            tap_rc(d, t, dr, dc);
+            sm.off[pl][d][t] = pl == 0 ? luma_off(dr, dc) : dr * kChromaPitch + dc;
+        }
+        __syncthreads();
+
+        for (int it = 0;; it++) {
+            const int buf = it & 1;
+            const int blk = sm.blk[buf];
+            if (blk >= total) break;
+            if (tid == 0) {
+                const int nb = (int)atomicAdd(&work[0], 1u);
+                sm.blk[buf ^ 1] = nb;
+                if (nb < total) issue_loads(batch, nb, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
+            }
+            const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, kWaitCycles);
+            if (__syncthreads_or(!arrived)) {  // the whole CTA leaves together
+                if (tid == 0) {
+                    atomicOr(status, kStatusTimeout);
+                    if (sm.blk[buf ^ 1] < total)  // let the prefetch in flight land first
+                        mbar_wait_bounded(&sm.bar[buf ^ 1], ((it + 1) >> 1) & 1, kWaitCycles);
+                }
+                break;
+            }
+            const BlockRef r = locate(batch, blk);
+            const FilterFrameDev &F = batch.f[r.fi];
+            if (F.bitdepth == 8)
+                process_block<uint8_t>(F, r.fby, r.fbx, status, sm, sm.raw[buf]);
+            else
+                process_block<uint16_t>(F, r.fby, r.fbx, status, sm, sm.raw[buf]);
+            __syncthreads();  // shared tiles, tables and the next block id are settled
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&work[1], 1u) == gridDim.x - 1) {  // last CTA: reset for the next launch
+            work[0] = 0;
+            work[1] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -618,17 +636,19 @@ int persistent_grid(int total)
 
 }  // namespace
 
-cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status, cudaStream_t s)
+cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status, unsigned *work,
+                                 cudaStream_t s)
 {
     const int grid = persistent_grid<1>(b.total_blocks);
-    filter_kernel<1><<<grid, kThreads, kSmemBytes, s>>>(b, status);
+    filter_kernel<1><<<grid, kThreads, kSmemBytes, s>>>(b, status, work);
     return cudaGetLastError();
 }
 
-cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *status, cudaStream_t s)
+cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *status, unsigned *work,
+                                cudaStream_t s)
 {
     const int grid = persistent_grid<kMaxFilterBatch>(b.total_blocks);
-    filter_kernel<kMaxFilterBatch><<<grid, kThreads, kSmemBytes, s>>>(b, status);
+    filter_kernel<kMaxFilterBatch><<<grid, kThreads, kSmemBytes, s>>>(b, status, work);
     return cudaGetLastError();
 }
 
