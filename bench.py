@@ -370,6 +370,60 @@ def run_ours(args):
     ctx.close()
 
 
+SEARCH_WORKLOAD = dict(
+    name="strength search: 16 frames 8-bit 4:2:0, 640x360 / 1280x720 / 1920x1080 (6/5/5), "
+         "64 luma + 64 chroma strength pairs per 64x64 block, greedy presets, one call",
+    sizes=[(640, 360), (1280, 720), (1920, 1080)], frames=16, base_seed=3000)
+
+
+def run_search(args):
+    """Batched strength search over 16 mixed-size frames in one call;
+    metric: candidate (block, strength pair, plane group) evaluations per
+    second, 128 per 64x64 block."""
+    import torch
+    from paper_1602_05975_gb300 import build, cdef, synth
+    build.build()
+    ctx = cdef.Context(0)
+    frames = []
+    for f in range(SEARCH_WORKLOAD["frames"]):
+        w, h = SEARCH_WORKLOAD["sizes"][f % 3]
+        frames.append(synth.make_frame(w, h, 8, None, SEARCH_WORKLOAD["base_seed"] + f))
+    recs = [cdef.frame_from_numpy(fr.rec, 8) for fr in frames]
+    srcs = [cdef.frame_from_numpy(fr.src, 8) for fr in frames]
+    nb = sum(fr.params.shape[0] * fr.params.shape[1] for fr in frames)
+    damping = [4 + (fr.q > 16) + (fr.q > 32) for fr in frames]   # larger damping for larger Q
+    lambdas = [fr.q * fr.q for fr in frames]
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc, stream=stream)
+    if args.check:
+        from oracle import ref
+        o = ref.search_strengths(frames[0].rec, frames[0].src, 8, damping[0], lambdas[0])
+        n0 = frames[0].params.shape[0] * frames[0].params.shape[1]
+        assert (dl[:n0 * 64].cpu().numpy().reshape(n0, 64) == o["dist_luma"]).all()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc, stream=stream)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    print(json.dumps({
+        "metric": "strength-search candidates/s", "value": nb * 128 / sec, "unit": "candidates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": SEARCH_WORKLOAD["name"], "blocks": nb,
+                                        "luma_pixels": sum(f.width * f.height for f in frames)},
+        "clocks": clk}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,9 +434,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-bands", type=int, default=36)
     ap.add_argument("--check", action="store_true", help="oracle check of frame 0")
+    ap.add_argument("--workload", default="filter", choices=["filter", "search"],
+                    help="filter: the 4K 10-bit filter (default line); search: batched "
+                         "strength search over 16 mixed frames")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "search" and args.impl == "ours":
+        run_search(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

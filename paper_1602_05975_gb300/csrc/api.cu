@@ -95,9 +95,13 @@ bool frames_overlap(const cdef_frame *a, const cdef_frame *b)
 
 int fb_count(const cdef_frame *f) { return ((f->y.width + 63) / 64) * ((f->y.height + 63) / 64); }
 
+}  // namespace
+
+namespace cdefgb {
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
 // link-time dependency on libcuda).
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -130,6 +134,19 @@ int encode_plane(CUtensorMap *m, const cdef_plane &p, int bytes, int box_cols, i
     return r == CUDA_SUCCESS ? CDEF_OK : CDEF_ERR_CUDA;
 }
 
+int encode_frame_tiles(CUtensorMap maps[3], const cdef_frame *f)
+{
+    const int b = f->bitdepth == 8 ? 1 : 2;
+    int rc;
+    if ((rc = encode_plane(&maps[0], f->y, b, luma_box_cols(b), kLumaBoxRows))) return rc;
+    if ((rc = encode_plane(&maps[1], f->u, b, chroma_box_cols(b), kChromaBoxRows))) return rc;
+    return encode_plane(&maps[2], f->v, b, chroma_box_cols(b), kChromaBoxRows);
+}
+
+}  // namespace cdefgb
+
+namespace {
+
 int fill_filter_frame(FilterFrameDev &d, const cdef_frame *in, const cdef_frame *out,
                       const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
                       int block_start)
@@ -151,11 +168,7 @@ int fill_filter_frame(FilterFrameDev &d, const cdef_frame *in, const cdef_frame 
     d.fb_cols = (in->y.width + 63) / 64;
     d.fb_rows = (in->y.height + 63) / 64;
     d.block_start = block_start;
-    const int b = sample_bytes(in->bitdepth);
-    int rc;
-    if ((rc = encode_plane(&d.tmap[0], in->y, b, luma_box_cols(b), kLumaBoxRows))) return rc;
-    if ((rc = encode_plane(&d.tmap[1], in->u, b, chroma_box_cols(b), kChromaBoxRows))) return rc;
-    return encode_plane(&d.tmap[2], in->v, b, chroma_box_cols(b), kChromaBoxRows);
+    return encode_frame_tiles(d.tmap, in);
 }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? CDEF_OK : CDEF_ERR_CUDA; }
@@ -335,8 +348,10 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
     for (int i = 0; i < n && rc == CDEF_OK; i++) {
         if ((rc = check_frame(&rec[i])) || (rc = check_frame(&src[i]))) break;
         if (!same_geometry(&rec[i], &src[i])) { rc = CDEF_ERR_SIZE; break; }
+        if (rec[i].bitdepth > 10) { rc = CDEF_ERR_BITDEPTH; break; }
         if (damping[i] < 3 || damping[i] > 6 || lambda[i] < 0) { rc = CDEF_ERR_ARG; break; }
         SearchFrameDev &f = b->f[i];
+        if ((rc = encode_frame_tiles(f.tmap, &rec[i]))) break;
         const cdef_plane *pr[3] = {&rec[i].y, &rec[i].u, &rec[i].v};
         const cdef_plane *ps[3] = {&src[i].y, &src[i].u, &src[i].v};
         for (int k = 0; k < 3; k++) {
@@ -361,18 +376,21 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
 
     DeviceGuard g(ctx->device);
     if (!g.ok) { delete b; return CDEF_ERR_CUDA; }
+    const size_t greedy = search_scratch_bytes(n, total);
     const size_t tables = dist_luma ? 0 : (size_t)total * 64 * sizeof(long long) * 2;
-    const size_t need = tables + (size_t)total * sizeof(long long);
-    if ((rc = ensure_scratch(ctx, need))) { delete b; return rc; }
+    if ((rc = ensure_scratch(ctx, greedy + tables))) { delete b; return rc; }
+    unsigned long long *cur = static_cast<unsigned long long *>(ctx->scratch);
+    unsigned long long *tot = cur + total;
     long long *dl = reinterpret_cast<long long *>(dist_luma);
     long long *dc = reinterpret_cast<long long *>(dist_chroma);
-    long long *cur = static_cast<long long *>(ctx->scratch);
     if (!dl) {
-        dl = cur + total;
+        dl = reinterpret_cast<long long *>(static_cast<char *>(ctx->scratch) + greedy);
         dc = dl + (size_t)total * 64;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    cudaError_t e = launch_search(*b, dl, dc, cur, ctx->dev_results, block_ids, ctx->status, s);
+    unsigned *work = ctx->work + 2 * (ctx->next_slot++ % kWorkSlots);
+    cudaError_t e = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status,
+                                  work, s);
     delete b;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->host_results, ctx->dev_results, sizeof(SearchResultDev) * n,

@@ -11,7 +11,7 @@
 
 namespace cdefgb {
 
-constexpr int kMaxBatch = 64;        // frames per batched search launch
+constexpr int kMaxBatch = 48;        // frames per batched search launch (kernel-parameter space)
 constexpr int kMaxFilterBatch = 48;  // frames per batched filter launch (kernel-parameter space)
 
 // One plane as a kernel sees it.
@@ -43,7 +43,8 @@ struct FilterBatch {
 };
 
 // One frame of a strength search launch.
-struct SearchFrameDev {
+struct alignas(64) SearchFrameDev {
+    CUtensorMap tmap[3];             // 2-D tile maps of the decoded y, u, v planes
     const uint8_t *rec[3];
     const uint8_t *src[3];
     int64_t rec_pitch[3], src_pitch[3];
@@ -90,10 +91,21 @@ constexpr int kChromaBoxRows = 36;
 __host__ __device__ constexpr int luma_box_cols(int bytes) { return bytes == 2 ? 80 : 96; }
 __host__ __device__ constexpr int chroma_box_cols(int bytes) { return bytes == 2 ? 48 : 64; }
 __host__ __device__ constexpr int box_lead(int bytes) { return bytes == 2 ? 8 : 16; }
+// Strength search: distortion tables, then the greedy preset search.
+// Device scratch: `cur` one u64 per block, `tot` 4096 u64 per frame (zeroed
+// by the call itself), `work` a zeroed counter pair (left zeroed).
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
-                          long long *dist_chroma, long long *cur,
-                          SearchResultDev *results, uint8_t *block_ids,
-                          int *status, cudaStream_t s);
+                          long long *dist_chroma, unsigned long long *cur,
+                          unsigned long long *tot, SearchResultDev *results,
+                          uint8_t *block_ids, int *status, unsigned *work, cudaStream_t s);
+constexpr size_t search_scratch_bytes(int nframes, int nblocks)
+{
+    return sizeof(unsigned long long) * ((size_t)nblocks + (size_t)nframes * 4096);
+}
+
+// Host: the three 2-D tile maps (filter-block boxes with halo) of a frame's
+// planes; returns a CDEF status.
+int encode_frame_tiles(CUtensorMap maps[3], const cdef_frame *f);
 
 // Device status word values (set by kernels, read by the host).
 constexpr int kStatusBadParams = 1;

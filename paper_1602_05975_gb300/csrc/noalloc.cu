@@ -19,8 +19,11 @@ using namespace cdefgb;
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr size_t kCurBytes = sizeof(long long) * CDEF_NOALLOC_MAX_BLOCKS;
-constexpr size_t kScratchBytes = kCurBytes + sizeof(SearchResultDev) * kMaxBatch;
+// greedy state (per-block minima, per-frame preset totals), result records,
+// one work-counter pair
+constexpr size_t kGreedyBytes = search_scratch_bytes(kMaxBatch, CDEF_NOALLOC_MAX_BLOCKS);
+constexpr size_t kResultBytes = sizeof(SearchResultDev) * kMaxBatch;
+constexpr size_t kScratchBytes = kGreedyBytes + kResultBytes + 2 * sizeof(unsigned) + sizeof(int);
 
 // The scratch itself.  In host code `g_scratch` names a host-side shadow,
 // not device memory: its device address comes from cudaGetSymbolAddress.
@@ -93,8 +96,11 @@ extern "C" int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
         if (rec[i].bitdepth != src[i].bitdepth || rec[i].y.width != src[i].y.width ||
             rec[i].y.height != src[i].y.height)
             return CDEF_ERR_SIZE;
+        if (rec[i].bitdepth > 10) return CDEF_ERR_BITDEPTH;
         if (damping[i] < 3 || damping[i] > 6 || lambda[i] < 0) return CDEF_ERR_ARG;
         SearchFrameDev &f = b.f[i];
+        int trc;
+        if ((trc = encode_frame_tiles(f.tmap, &rec[i]))) return trc;
         const cdef_plane *pr[3] = {&rec[i].y, &rec[i].u, &rec[i].v};
         const cdef_plane *ps[3] = {&src[i].y, &src[i].u, &src[i].v};
         for (int k = 0; k < 3; k++) {
@@ -120,16 +126,21 @@ extern "C" int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
     void *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc) return rc;
-    long long *cur = static_cast<long long *>(scratch);
-    SearchResultDev *results =
-        reinterpret_cast<SearchResultDev *>(static_cast<unsigned char *>(scratch) + kCurBytes);
+    unsigned char *base = static_cast<unsigned char *>(scratch);
+    unsigned long long *cur = reinterpret_cast<unsigned long long *>(base);
+    unsigned long long *tot = cur + CDEF_NOALLOC_MAX_BLOCKS;
+    SearchResultDev *results = reinterpret_cast<SearchResultDev *>(base + kGreedyBytes);
+    unsigned *work = reinterpret_cast<unsigned *>(base + kGreedyBytes + kResultBytes);
+    int *status = reinterpret_cast<int *>(work + 2);
     // Every scratch word the kernels read is written by them first in this
-    // call (the running minima are reset by the greedy kernel, the result
-    // records written whole), so nothing needs clearing here.
+    // call (the greedy minima and preset totals are reset at its start, the
+    // result records written whole); the work counters start at zero (static
+    // storage) and every launch leaves them at zero again.  The status word
+    // only collects error bits and is not read here.
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = launch_search(b, reinterpret_cast<long long *>(dist_luma),
-                                  reinterpret_cast<long long *>(dist_chroma), cur, results,
-                                  block_ids, nullptr, s);
+                                  reinterpret_cast<long long *>(dist_chroma), cur, tot, results,
+                                  block_ids, status, work, s);
     SearchResultDev host[kMaxBatch];  // pageable stack copy: no pinned allocation
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host, results, sizeof(SearchResultDev) * n, cudaMemcpyDeviceToHost, s);

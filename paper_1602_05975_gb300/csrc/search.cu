@@ -1,372 +1,573 @@
 // Encoder strength search (section 5).
 //
-// dist_kernel: one CTA per 64x64 filter block of any frame of the batch.
-//   The decoded tiles (plus the 2-pixel halo) are staged in shared memory,
-//   the 64 luma directions found (section 2), and then every pixel is
-//   filtered under all 64 (primary, secondary) strength pairs at once: the
-//   constrained primary sum is formed once per primary strength (16) and the
-//   secondary sum once per secondary strength (4), and the 64 pairs only
-//   add, round, clip and accumulate (y - source)^2.  This factoring is
-//   exact: eq. 8 is a sum of the two tap sets, each depending on one
-//   strength only.  Each thread keeps 64 32-bit partial SSEs for the pixels
-//   it owns; they are reduced into 64-bit block totals.
+// dist_kernel: persistent CTAs take 64x64 filter blocks of any frame of the
+//   batch from a work counter.  The decoded tiles are staged exactly as for
+//   the filter (TMA, double buffering, biased 16-bit pair layout; see
+//   tile.cuh), the 64 luma directions found (section 2), and every word of
+//   two samples is then filtered under all 64 (primary, secondary) strength
+//   pairs at once.  The clamped primary sum is formed once per primary
+//   strength (16) and the secondary sum once per secondary strength (4):
+//   exact, since eq. 8 is the sum of the two tap sets, each depending on one
+//   strength only.  Each of the 64 pairs then only rounds, clips (eq. 9-12,
+//   when both strengths are on) and accumulates (y - source)^2 into one of 64
+//   per-lane registers.  Lanes cover the 8 columns of 8x8 blocks of a block
+//   row, so their 64 sums are reduced across the warp by a butterfly that
+//   leaves lane l with pairs 2l and 2l + 1, then across warps in shared
+//   memory, into 64-bit block totals.
 //
-// greedy_kernel: one CTA per frame; the greedy preset search and the eq. 15
-//   choice of N, with int64 totals.
+// Greedy preset search (eq. 15), several kernels per step so that every SM
+//   works: greedy_partial adds, for chunks of blocks of each frame, the
+//   contribution min(best so far, D_luma + D_chroma) of each of the 4096
+//   (luma pair, chroma pair) presets to the frame's totals; greedy_select
+//   takes each frame's least total (lowest index on ties) and lowers the
+//   blocks' best distortion; greedy_final picks N in {1, 2, 4, 8} by J and
+//   each block's preset.
 #include <climits>
 
-#include "cdef_device.cuh"
-#include "cdef_internal.h"
+#include "tile.cuh"
 
 namespace cdefgb {
 
 namespace {
 
+using namespace tile;
+
 constexpr int kThreads = 256;
-constexpr int kLumaRows = 64 + 4, kLumaPitch = 72;
-constexpr int kChromaRows = 32 + 4, kChromaPitch = 40;
-constexpr int kSentinel = 0x7fff;
+constexpr int kMinCtas = 2;
 
 struct SearchSmem {
-    int16_t y[kLumaRows * kLumaPitch];
-    int16_t u[kChromaRows * kChromaPitch];
-    int16_t v[kChromaRows * kChromaPitch];
+    RawTiles raw[2];
+    PairTiles t;
+    alignas(16) int off[2][8][12];    // tap word offsets [luma/chroma][d][tap]
+    int cost[64][8];
+    alignas(16) SetC pset[64][16];    // luma primary sets per 8x8 block and signalled strength
+    alignas(16) SetC cset[16];        // chroma primary sets per signalled strength
+    alignas(16) SetC sset[3][4];      // secondary: luma; chroma at D - 1; chroma at D = 3
+    uint32_t pbits[64];               // luma: bit p odd adjusted strength, bit 16 + p adjusted > 0
+    uint32_t cbits;                   // chroma: the same per signalled strength
+    uint32_t craised;                 // chroma: bit p, damping raised to floor(log2 p) = 3
     uint8_t dir[64];
     int var[64];
-    unsigned long long acc[64];
+    unsigned long long acc[64];       // block totals of the current plane group
+    int blk[2];
+    alignas(8) uint64_t bar[2];
 };
 
+// The signalled secondary strengths {0, 1, 2, 4} by index.
+__device__ __forceinline__ int sec_value(int i) { return i == 3 ? 4 : i; }
+
+// Packed biased pair of source samples at (row, x), (row, x + 1) (luma) or
+// the (U, V) word at (row, x) (chroma).
 template <typename T>
-__device__ __forceinline__ int load_sample(const uint8_t *plane, int64_t pitch, int y, int x)
+__device__ __forceinline__ uint32_t load_src_pair(const uint8_t *row, int x)
 {
-    return (int)__ldg(reinterpret_cast<const T *>(plane + (int64_t)y * pitch) + x);
+    if (sizeof(T) == 2) return __ldg(reinterpret_cast<const uint32_t *>(row + 2 * x)) + kBias * kLanes;
+    const uint32_t two = __ldg(reinterpret_cast<const uint16_t *>(row + x));
+    return __byte_perm(two, 0, 0x4140) + kBias * kLanes;
 }
 
 template <typename T>
-__device__ void stage_tile(int16_t *tile, int pitch, int rows, int cols, const uint8_t *plane,
-                           int64_t ppitch, int pw, int ph, int y0, int x0)
+__device__ __forceinline__ uint32_t load_src_uv(const uint8_t *urow, const uint8_t *vrow, int x)
 {
-    for (int idx = threadIdx.x; idx < rows * cols; idx += kThreads) {
-        const int r = idx / cols, c = idx - r * cols;
-        const int y = y0 + r, x = x0 + c;
-        int v = kSentinel;
-        if (y >= 0 && y < ph && x >= 0 && x < pw) v = load_sample<T>(plane, ppitch, y, x);
-        tile[r * pitch + c] = (int16_t)v;
-    }
+    const uint32_t u = __ldg(reinterpret_cast<const T *>(urow) + x);
+    const uint32_t v = __ldg(reinterpret_cast<const T *>(vrow) + x);
+    return (u | (v << 16)) + kBias * kLanes;
 }
 
-// The 12 tap values of the pixel at tile position (r, c): [0..3] primary
-// (near +, near -, far +, far -), [4..11] secondary (d+2 then d-2, same
-// order).  Out-of-frame taps read the sentinel.
-__device__ __forceinline__ void gather_taps(const int16_t *tile, int pitch, int r, int c, int d,
-                                            int p[12])
+// Squared error of both lanes, added to acc.  8-bit errors fit a byte, so
+// one dot-product instruction squares and adds both.
+template <typename T>
+__device__ __forceinline__ uint32_t add_sq(uint32_t acc, uint32_t y, uint32_t s)
+{
+    const uint32_t e = __vmaxu2(y, s) - __vminu2(y, s);   // |y - s| per lane
+    if (sizeof(T) == 1) return __dp2a_lo(e, __byte_perm(e, 0, 0x0020), acc);
+    const uint32_t lo = e & 0xffffu, hi = e >> 16;
+    return acc + lo * lo + hi * hi;
+}
+
+// Weighted sum of the 4 primary clamped values for one set.
+__device__ __forceinline__ uint32_t pri_sum(const uint32_t v[12], uint32_t X, const SetC &s, bool odd)
+{
+    const uint32_t xk1 = X + s.kb, xk2 = s.kb - X;
+    const uint32_t n = tap(v[0], X, xk1, xk2, s) + tap(v[1], X, xk1, xk2, s);
+    const uint32_t f = tap(v[2], X, xk1, xk2, s) + tap(v[3], X, xk1, xk2, s);
+    const uint32_t t3 = n + f, t2 = n + n + f;
+    return odd ? t3 + t3 + t3 : t2 + t2;   // weights 3,3 or 4,2
+}
+
+__device__ __forceinline__ uint32_t sec_sum(const uint32_t v[12], uint32_t X, const SetC &s)
+{
+    const uint32_t xk1 = X + s.kb, xk2 = s.kb - X;
+    const uint32_t n = tap(v[4], X, xk1, xk2, s) + tap(v[5], X, xk1, xk2, s) +
+                       tap(v[6], X, xk1, xk2, s) + tap(v[7], X, xk1, xk2, s);
+    const uint32_t f = tap(v[8], X, xk1, xk2, s) + tap(v[9], X, xk1, xk2, s) +
+                       tap(v[10], X, xk1, xk2, s) + tap(v[11], X, xk1, xk2, s);
+    return n + n + f;   // weights 2, 1
+}
+
+// Sums 64 per-lane values across the warp; lane l ends with the totals of
+// entries 2l and 2l + 1 in a[0], a[1].
+__device__ __forceinline__ void butterfly64(uint32_t a[64], int lane)
 {
 #pragma unroll
-    for (int s = 0; s < 3; s++) {
-        const int dd = s == 0 ? d : (d + (s == 1 ? 2 : 6)) & 7;
+    for (int o = 16, n = 64; o >= 1; o >>= 1, n >>= 1) {
+        const bool upper = lane & o;
+        const int half = n >> 1;
 #pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const int dr = tap_dr(dd, k), dc = tap_dc(dd, k);
-            p[s * 4 + k * 2 + 0] = tile[(r + dr) * pitch + c + dc];
-            p[s * 4 + k * 2 + 1] = tile[(r - dr) * pitch + c - dc];
+        for (int i = 0; i < 32; i++) {
+            if (i < half) {
+                const uint32_t give = upper ? a[i] : a[i + half];
+                const uint32_t keep = upper ? a[i + half] : a[i];
+                a[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+            }
         }
     }
 }
 
-// Constrained, weighted primary sum for strength S / shift sh / weights.
-__device__ __forceinline__ int pri_sum(const int p[12], int x, int S, int sh, int w0, int w1)
-{
-    int s = 0;
-#pragma unroll
-    for (int t = 0; t < 4; t++) {
-        const int f = p[t] == kSentinel ? 0 : constrain(p[t] - x, S, sh);
-        s += (t < 2 ? w0 : w1) * f;
-    }
-    return s;
-}
-
-__device__ __forceinline__ int sec_sum(const int p[12], int x, int S, int sh)
-{
-    int s = 0;
-#pragma unroll
-    for (int t = 4; t < 12; t++) {
-        const int f = p[t] == kSentinel ? 0 : constrain(p[t] - x, S, sh);
-        s += (((t - 4) & 3) < 2 ? 2 : 1) * f;
-    }
-    return s;
-}
-
-// Accumulate the 64 strength pairs' squared errors of one pixel.
-// chroma: the damping is D - 1 raised to floor(log2 S_p) (section 3.2),
-// so the secondary shift may depend on the primary strength.
-__device__ __forceinline__ void accumulate_pixel(const int16_t *tile, int pitch, int r, int c,
-                                                 int d, int v, bool chroma, int damping,
-                                                 int sh8, int src, unsigned acc[64])
-{
-    int p[12];
-    gather_taps(tile, pitch, r, c, d, p);
-    const int x = tile[r * pitch + c];
-    int mn = x, mx = x;
-#pragma unroll
-    for (int t = 0; t < 12; t++) {
-        if (p[t] != kSentinel) {
-            mn = min(mn, p[t]);
-            mx = max(mx, p[t]);
-        }
-    }
-    const int Dp = chroma ? damping - 1 : damping;
-    // secondary sums for the plane damping, and for the damping raised to 3
-    // (only reachable when Dp < 3, i.e. chroma with D = 3)
-    int Qa[4], Qb[4];
-    const int svals[4] = {0, 1, 2, 4};
-#pragma unroll
-    for (int s = 0; s < 4; s++) {
-        const int S = svals[s];
-        Qa[s] = S ? sec_sum(p, x, S << sh8, max(0, Dp - ilog2(S))) : 0;
-        Qb[s] = S ? sec_sum(p, x, S << sh8, max(0, max(Dp, 3) - ilog2(S))) : 0;
-    }
-#pragma unroll
-    for (int pi = 0; pi < 16; pi++) {
-        const int Sp = chroma ? pi : adjust_strength(pi, v);
-        const int lp = Sp ? ilog2(Sp) : 0;
-        const int D = (Sp && Dp < lp) ? lp : Dp;
-        const int P = Sp ? pri_sum(p, x, Sp << sh8, D - lp, (Sp & 1) ? 3 : 4, (Sp & 1) ? 3 : 2) : 0;
-        const bool raised = D != Dp;
-#pragma unroll
-        for (int s = 0; s < 4; s++) {
-            const int Q = raised ? Qb[s] : Qa[s];
-            const int y = min(mx, max(mn, x + round16(P + Q)));
-            const int e = y - src;
-            acc[pi * 4 + s] += (unsigned)(e * e);
-        }
-    }
-}
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Reduce the 64 per-thread partial SSEs into sm.acc and write them out.
-__device__ void reduce_store(unsigned acc[64], SearchSmem &sm, long long *out)
-{
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 64) sm.acc[threadIdx.x] = 0;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 64; q++) {
-        const unsigned long long s = warp_sum_u64(acc[q]);
-        if (lane == 0) atomicAdd(&sm.acc[q], s);
-    }
-    __syncthreads();
-    if (threadIdx.x < 64) out[threadIdx.x] = (long long)sm.acc[threadIdx.x];
-    __syncthreads();
-}
-
 template <typename T>
-__device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, long long *dl,
-                           long long *dc, SearchSmem &sm)
+__device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global,
+                           SearchSmem &sm, const RawTiles &raw, long long *dist_luma,
+                           long long *dist_chroma)
 {
     const int sh8 = F.bitdepth - 8;
+    const int W = F.w, H = F.h, CW = F.w >> 1, CH = F.h >> 1;
     const int ly0 = fby * 64, lx0 = fbx * 64, cy0 = fby * 32, cx0 = fbx * 32;
-    const int cw = F.w >> 1, ch = F.h >> 1;
-    stage_tile<T>(sm.y, kLumaPitch, kLumaRows, kLumaRows, F.rec[0], F.rec_pitch[0], F.w, F.h,
-                  ly0 - 2, lx0 - 2);
-    stage_tile<T>(sm.u, kChromaPitch, kChromaRows, kChromaRows, F.rec[1], F.rec_pitch[1], cw, ch,
-                  cy0 - 2, cx0 - 2);
-    stage_tile<T>(sm.v, kChromaPitch, kChromaRows, kChromaRows, F.rec[2], F.rec_pitch[2], cw, ch,
-                  cy0 - 2, cx0 - 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = F.damping;
+
+    const bool border = fby == 0 || fbx == 0 || ly0 + 66 > H || lx0 + 66 > W ||
+                        cy0 + 34 > CH || cx0 + 34 > CW;
+    stage_relayout<T, kThreads>(sm.t, raw, border, ly0, lx0, H, W, cy0, cx0, CH, CW);
     __syncthreads();
-    if (threadIdx.x < 64) {
-        const int by = threadIdx.x >> 3, bx = threadIdx.x & 7;
-        int d = 0, v = 0;
-        if (ly0 + by * 8 < F.h && lx0 + bx * 8 < F.w) {
-            const int16_t *b = sm.y + (2 + by * 8) * kLumaPitch + 2 + bx * 8;
-            d = find_dir_8x8([&](int i, int j) { return (int)b[i * kLumaPitch + j]; }, sh8, &v);
+
+    {   // direction search: four threads per 8x8 block, two directions each
+        const int b = (warp >> 2) * 32 + lane;
+        switch (warp & 3) {
+        case 0: dir_costs<0>(sm.t.le, b, sh8, sm.cost); break;
+        case 1: dir_costs<1>(sm.t.le, b, sh8, sm.cost); break;
+        case 2: dir_costs<2>(sm.t.le, b, sh8, sm.cost); break;
+        default: dir_costs<3>(sm.t.le, b, sh8, sm.cost); break;
         }
-        sm.dir[threadIdx.x] = (uint8_t)d;
-        sm.var[threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (tid < 64) {
+        int best = 0, bc = sm.cost[tid][0];
+#pragma unroll
+        for (int k = 1; k < 8; k++)
+            if (sm.cost[tid][k] > bc) { bc = sm.cost[tid][k]; best = k; }
+        sm.dir[tid] = (uint8_t)best;
+        sm.var[tid] = bc - sm.cost[tid][(best + 4) & 7];
+        sm.acc[tid] = 0;
     }
     __syncthreads();
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned acc[64];
-#pragma unroll
-    for (int q = 0; q < 64; q++) acc[q] = 0;
-    for (int k = warp; k < 64; k += kThreads / 32) {
-        const int by = k >> 3, bx = k & 7;
-        if (ly0 + by * 8 >= F.h || lx0 + bx * 8 >= F.w) continue;
-        const int r = lane >> 2, c = (lane & 3) * 2;
+    // ---- strength tables (section 3.2)
+    for (int e = tid; e < 64 * 16; e += kThreads) {
+        const int k = e >> 4, p = e & 15;
+        const int S = adjust_strength(p, sm.var[k]);
+        const int lp = S ? ilog2(S) : 0;
+        const int Deff = (S && D < lp) ? lp : D;
+        sm.pset[k][p] = make_set(S << sh8, S ? Deff - lp : 0);
+    }
+    if (tid < 64) {
+        uint32_t bits = 0;
+        for (int p = 0; p < 16; p++) {
+            const int S = adjust_strength(p, sm.var[tid]);
+            bits |= ((uint32_t)(S & 1) << p) | ((uint32_t)(S > 0) << (16 + p));
+        }
+        sm.pbits[tid] = bits;
+    } else if (tid < 80) {
+        const int p = tid - 64, Dc = D - 1, lp = p ? ilog2(p) : 0;
+        const int Deff = (p && Dc < lp) ? lp : Dc;
+        sm.cset[p] = make_set(p << sh8, p ? Deff - lp : 0);
+    } else if (tid < 92) {
+        const int g = (tid - 80) >> 2, si = (tid - 80) & 3, s = sec_value(si);
+        const int Dg = g == 0 ? D : g == 1 ? D - 1 : 3;
+        sm.sset[g][si] = make_set(s << sh8, s ? Dg - ilog2(s) : 0);
+    } else if (tid == 92) {
+        uint32_t bits = 0, raised = 0;
+        for (int p = 0; p < 16; p++) {
+            bits |= ((uint32_t)(p & 1) << p) | ((uint32_t)(p > 0) << (16 + p));
+            if (p && ilog2(p) > D - 1) raised |= 1u << p;
+        }
+        sm.cbits = bits;
+        sm.craised = raised;
+    }
+    __syncthreads();
+
+    // ---- both plane groups through one code path: task 0 luma, task 1 chroma
+    const int bw = W >> 3;
 #pragma unroll 1
-        for (int q = 0; q < 2; q++) {
-            const int gy = ly0 + by * 8 + r, gx = lx0 + bx * 8 + c + q;
-            const int src = load_sample<T>(F.src[0], F.src_pitch[0], gy, gx);
-            accumulate_pixel(sm.y, kLumaPitch, 2 + by * 8 + r, 2 + bx * 8 + c + q, sm.dir[k],
-                             sm.var[k], false, F.damping, sh8, src, acc);
-        }
-    }
-    reduce_store(acc, sm, dl);
+    for (int task = 0; task < 2; task++) {
+        const bool luma = task == 0;
+        const int bx = lane >> 2, sub = lane & 3;
+        const int blk = warp * 8 + bx;
+        const int gby = fby * 8 + warp, gbx = fbx * 8 + bx;
+        const bool inside = luma ? (gby * 8 < H && gbx * 8 < W) : (gby * 4 < CH && gbx * 4 < CW);
+        const bool edge = gby == 0 || gbx == 0 || gby == (H >> 3) - 1 || gbx == bw - 1;
+        const bool any_edge = __any_sync(0xffffffffu, inside && edge);
+        const int rows = luma ? 8 : 4;
+        const int pitch = luma ? kLumaPitch : kChromaPitch;
+        const uint32_t *base = luma ? sm.t.le + (2 + warp * 8) * kLumaPitch + 4 + bx * 4 + sub
+                                    : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
+        const int4 *op = reinterpret_cast<const int4 *>(sm.off[task][sm.dir[blk]]);
+        const int4 o0 = op[0], o1 = op[1], o2 = op[2];
+        const int o[12] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w};
+        const SetC *ps = luma ? sm.pset[blk] : sm.cset;
+        const uint32_t bits = luma ? sm.pbits[blk] : sm.cbits;
+        const uint32_t raised = luma ? 0u : sm.craised;
+        const SetC *ss = luma ? sm.sset[0] : sm.sset[1];
+        const int oy = luma ? ly0 + warp * 8 : cy0 + warp * 4;
+        const int ox = luma ? lx0 + bx * 8 + 2 * sub : cx0 + bx * 4 + sub;
+        const uint8_t *sa = luma ? F.src[0] : F.src[1];
+        const int64_t spa = luma ? F.src_pitch[0] : F.src_pitch[1];
 
+        uint32_t acc[64];
 #pragma unroll
-    for (int q = 0; q < 64; q++) acc[q] = 0;
-    for (int k = warp; k < 64; k += kThreads / 32) {
-        const int by = k >> 3, bx = k & 7;
-        if (cy0 + by * 4 >= ch || cx0 + bx * 4 >= cw) continue;
-        const int pl = lane >> 4, r = (lane & 15) >> 2, c = lane & 3;
-        const int gy = cy0 + by * 4 + r, gx = cx0 + bx * 4 + c;
-        const int src = load_sample<T>(F.src[1 + pl], F.src_pitch[1 + pl], gy, gx);
-        accumulate_pixel(pl ? sm.v : sm.u, kChromaPitch, 2 + by * 4 + r, 2 + bx * 4 + c, sm.dir[k],
-                         0, true, F.damping, sh8, src, acc);
+        for (int q = 0; q < 64; q++) acc[q] = 0;
+        if (inside) {
+#pragma unroll 1
+            for (int i = 0; i < rows; i++) {
+                const uint32_t *b = base + i * pitch;
+                const uint32_t X = b[0];
+                uint32_t v[12];
+#pragma unroll
+                for (int k = 0; k < 12; k++) v[k] = b[o[k]];
+                if (any_edge) {
+#pragma unroll
+                    for (int k = 0; k < 12; k++) v[k] = in_frame(v[k], X);
+                }
+                uint32_t mn = X, mx = X;
+#pragma unroll
+                for (int k = 0; k < 12; k += 2) {
+                    mn = __vimin3_u16x2(mn, v[k], v[k + 1]);
+                    mx = __vimax3_u16x2(mx, v[k], v[k + 1]);
+                }
+                const uint32_t S = luma ? load_src_pair<T>(sa + (int64_t)(oy + i) * spa, ox)
+                                        : load_src_uv<T>(sa + (int64_t)(oy + i) * spa,
+                                                         F.src[2] + (int64_t)(oy + i) * F.src_pitch[2], ox);
+                uint32_t Q[4], Qr[4];
+                Q[0] = Qr[0] = 12u * X;
+#pragma unroll
+                for (int s = 1; s < 4; s++) Q[s] = sec_sum(v, X, ss[s]);
+                if (raised) {
+#pragma unroll
+                    for (int s = 1; s < 4; s++) Qr[s] = sec_sum(v, X, sm.sset[2][s]);
+                } else {
+#pragma unroll
+                    for (int s = 1; s < 4; s++) Qr[s] = Q[s];
+                }
+                const uint32_t C = 4096u * kLanes - 24u * X;
+#pragma unroll
+                for (int p = 0; p < 16; p++) {
+                    const SetC sc = ps[p];
+                    const uint32_t T0 = pri_sum(v, X, sc, (bits >> p) & 1) + C;
+                    const bool on = (bits >> (16 + p)) & 1;
+                    const bool rz = (raised >> p) & 1;
+#pragma unroll
+                    for (int s = 0; s < 4; s++) {
+                        // eq. 8 rounding of (P + Q - 24x) / 16, ties away from zero
+                        const uint32_t u = T0 + (rz ? Qr[s] : Q[s]);
+                        const uint32_t pos = (u >> 12) & kLanes;
+                        const uint32_t w = u + pos + 7u * kLanes;
+                        uint32_t y = X + ((w >> 4) & (0x0fffu * kLanes)) - 256u * kLanes;
+                        if (s > 0 && on) y = __vminu2(__vmaxu2(y, mn), mx);   // eq. 9-12
+                        acc[p * 4 + s] = add_sq<T>(acc[p * 4 + s], y, S);
+                    }
+                }
+            }
+        }
+        butterfly64(acc, lane);
+        atomicAdd(&sm.acc[2 * lane], (unsigned long long)acc[0]);
+        atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)acc[1]);
+        __syncthreads();
+        if (tid < 64) {
+            long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64;
+            out[tid] = (long long)sm.acc[tid];
+            sm.acc[tid] = 0;
+        }
+        __syncthreads();
     }
-    reduce_store(acc, sm, dc);
 }
 
-__global__ void __launch_bounds__(kThreads)
-dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, long long *dist_chroma)
+struct SBlockRef {
+    int fi, fby, fbx;
+};
+
+__device__ __forceinline__ SBlockRef slocate(const SearchBatch &batch, int blk)
 {
-    __shared__ SearchSmem sm;
-    const int blk = blockIdx.x;
     int fi = 0;
     while (fi + 1 < batch.n && blk >= batch.f[fi + 1].block_start) fi++;
-    const SearchFrameDev &F = batch.f[fi];
-    const int local = blk - F.block_start;
-    const int fby = local / F.fb_cols, fbx = local - fby * F.fb_cols;
-    long long *dl = dist_luma + (int64_t)blk * 64;
-    long long *dc = dist_chroma + (int64_t)blk * 64;
-    if (F.bitdepth == 8)
-        dist_block<uint8_t>(F, fby, fbx, dl, dc, sm);
-    else
-        dist_block<uint16_t>(F, fby, fbx, dl, dc, sm);
+    const int local = blk - batch.f[fi].block_start;
+    const int fby = local / batch.f[fi].fb_cols;
+    return {fi, fby, local - fby * batch.f[fi].fb_cols};
+}
+
+__device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTiles &raw, uint64_t *bar)
+{
+    const SBlockRef r = slocate(batch, blk);
+    const SearchFrameDev &F = batch.f[r.fi];
+    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar);
+}
+
+// Persistent distortion kernel (same work-counter scheme as the filter).
+__global__ void __launch_bounds__(kThreads, kMinCtas)
+dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, long long *dist_chroma,
+            int *status, unsigned *work)
+{
+    extern __shared__ __align__(128) uint8_t smem_bytes[];
+    SearchSmem &sm = *reinterpret_cast<SearchSmem *>(smem_bytes);
+    const int tid = threadIdx.x;
+    const int total = batch.total_blocks;
+
+    if (smem_u32(smem_bytes) & 127) {
+        if (tid == 0) atomicOr(status, kStatusMisaligned);
+    } else {
+        if (tid == 0) {
+            mbar_init(&sm.bar[0], 1);
+            mbar_init(&sm.bar[1], 1);
+            const int b = (int)atomicAdd(&work[0], 1u);
+            sm.blk[0] = b;
+            if (b < total) sissue(batch, b, sm.raw[0], &sm.bar[0]);
+        }
+        if (tid < 192) {
+            const int pl = tid / 96, d = (tid / 12) & 7, t = tid % 12;
+            int dr, dc;
+            tap_rc(d, t, dr, dc);
+            sm.off[pl][d][t] = pl == 0 ? luma_off(dr, dc) : dr * kChromaPitch + dc;
+        }
+        __syncthreads();
+        for (int it = 0;; it++) {
+            const int buf = it & 1;
+            const int blk = sm.blk[buf];
+            if (blk >= total) break;
+            if (tid == 0) {
+                const int nb = (int)atomicAdd(&work[0], 1u);
+                sm.blk[buf ^ 1] = nb;
+                if (nb < total) sissue(batch, nb, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
+            }
+            const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, kWaitCycles);
+            if (__syncthreads_or(!arrived)) {
+                if (tid == 0) {
+                    atomicOr(status, kStatusTimeout);
+                    if (sm.blk[buf ^ 1] < total)
+                        mbar_wait_bounded(&sm.bar[buf ^ 1], ((it + 1) >> 1) & 1, kWaitCycles);
+                }
+                break;
+            }
+            const SBlockRef r = slocate(batch, blk);
+            const SearchFrameDev &F = batch.f[r.fi];
+            if (F.bitdepth == 8)
+                dist_block<uint8_t>(F, r.fby, r.fbx, blk, sm, sm.raw[buf], dist_luma, dist_chroma);
+            else
+                dist_block<uint16_t>(F, r.fby, r.fbx, blk, sm, sm.raw[buf], dist_luma, dist_chroma);
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&work[1], 1u) == gridDim.x - 1) {
+            work[0] = 0;
+            work[1] = 0;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
-// Greedy preset search, one CTA per frame (section 5, eq. 15).
-constexpr int kGreedyThreads = 512;
-constexpr int kTuplesPerThread = 4096 / kGreedyThreads;
-constexpr int kChunk = 16;
+// Greedy preset search.
+constexpr int kChunk = 16;        // blocks per greedy_partial CTA
+constexpr int kPartThreads = 256;
+constexpr int kTuples = 4096;
 
-__device__ __forceinline__ bool better(long long a, int ta, long long b, int tb)
+__device__ __forceinline__ int frame_chunks(const SearchFrameDev &F)
+{
+    return (F.fb_cols * F.fb_rows + kChunk - 1) / kChunk;
+}
+
+__global__ void greedy_init(const __grid_constant__ SearchBatch batch, unsigned long long *cur,
+                            unsigned long long *tot)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch.total_blocks; i += stride)
+        cur[i] = ULLONG_MAX;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch.n * kTuples; i += stride) tot[i] = 0;
+}
+
+// One chunk of one frame: adds sum_b min(cur_b, Dl[b][t >> 6] + Dc[b][t & 63])
+// over the chunk's blocks to tot[frame][t] for all 4096 presets t.
+__global__ void __launch_bounds__(kPartThreads)
+greedy_partial(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
+               const long long *__restrict__ dc, const unsigned long long *__restrict__ cur,
+               unsigned long long *tot)
+{
+    __shared__ unsigned long long s_dl[kChunk][64], s_dc[kChunk][64], s_cur[kChunk];
+    int c = blockIdx.x, fi = 0;
+    while (fi < batch.n && c >= frame_chunks(batch.f[fi])) c -= frame_chunks(batch.f[fi++]);
+    if (fi >= batch.n) return;
+    const SearchFrameDev &F = batch.f[fi];
+    const int B = F.fb_cols * F.fb_rows;
+    const int b0 = c * kChunk, nb = min(kChunk, B - b0);
+    const int g0 = F.block_start + b0;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nb * 64; i += kPartThreads) {
+        s_dl[i >> 6][i & 63] = (unsigned long long)dl[(int64_t)(g0 + (i >> 6)) * 64 + (i & 63)];
+        s_dc[i >> 6][i & 63] = (unsigned long long)dc[(int64_t)(g0 + (i >> 6)) * 64 + (i & 63)];
+    }
+    if (tid < nb) s_cur[tid] = cur[g0 + tid];
+    __syncthreads();
+    constexpr int K = kTuples / kPartThreads;   // 16 presets per thread
+    unsigned long long a[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) a[k] = 0;
+    const int ci = tid & 63, l0 = tid >> 6;
+    for (int b = 0; b < nb; b++) {
+        const unsigned long long cv = s_cur[b], dcv = s_dc[b][ci];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const unsigned long long v = s_dl[b][l0 + 4 * k] + dcv;
+            a[k] += v < cv ? v : cv;
+        }
+    }
+    unsigned long long *t = tot + (int64_t)fi * kTuples;
+#pragma unroll
+    for (int k = 0; k < K; k++) atomicAdd(&t[tid + kPartThreads * k], a[k]);
+}
+
+__device__ __forceinline__ bool better(unsigned long long a, int ta, unsigned long long b, int tb)
 {
     return a < b || (a == b && ta < tb);
 }
 
-__global__ void __launch_bounds__(kGreedyThreads)
-greedy_kernel(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dist_luma,
-              const long long *__restrict__ dist_chroma, long long *cur, SearchResultDev *res,
-              uint8_t *block_ids)
+// Per frame: the least total (lowest preset index on ties) becomes preset
+// `step`; the blocks' best distortion is lowered; the totals are cleared.
+__global__ void __launch_bounds__(1024)
+greedy_select(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
+              const long long *__restrict__ dc, unsigned long long *cur, unsigned long long *tot,
+              SearchResultDev *res, int step)
 {
-    __shared__ long long s_dl[kChunk][64], s_dc[kChunk][64], s_cur[kChunk];
-    __shared__ long long s_best[kGreedyThreads / 32];
-    __shared__ int s_bt[kGreedyThreads / 32];
-    __shared__ int s_presets[8];
-    __shared__ long long s_tot[8];
-
-    const SearchFrameDev &F = batch.f[blockIdx.x];
-    const int B = F.fb_cols * F.fb_rows;
-    const long long *dl = dist_luma + (int64_t)F.block_start * 64;
-    const long long *dc = dist_chroma + (int64_t)F.block_start * 64;
-    long long *cb = cur + F.block_start;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    for (int b = tid; b < B; b += kGreedyThreads) cb[b] = LLONG_MAX;
+    __shared__ unsigned long long s_v[32];
+    __shared__ int s_t[32];
+    const int fi = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SearchFrameDev &F = batch.f[fi];
+    unsigned long long *t = tot + (int64_t)fi * kTuples;
+    unsigned long long bv = ULLONG_MAX;
+    int bt = INT_MAX;
+    for (int i = tid; i < kTuples; i += 1024) {
+        const unsigned long long v = t[i];
+        if (better(v, i, bv, bt)) { bv = v; bt = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+        if (better(ov, ot, bv, bt)) { bv = ov; bt = ot; }
+    }
+    if (lane == 0) { s_v[warp] = bv; s_t[warp] = bt; }
     __syncthreads();
-
-    for (int n = 0; n < 8; n++) {
-        long long tot[kTuplesPerThread];
-#pragma unroll
-        for (int k = 0; k < kTuplesPerThread; k++) tot[k] = 0;
-        for (int c0 = 0; c0 < B; c0 += kChunk) {
-            const int nb = min(kChunk, B - c0);
-            for (int i = tid; i < nb * 64; i += kGreedyThreads) {
-                s_dl[i >> 6][i & 63] = dl[(int64_t)(c0 + (i >> 6)) * 64 + (i & 63)];
-                s_dc[i >> 6][i & 63] = dc[(int64_t)(c0 + (i >> 6)) * 64 + (i & 63)];
-            }
-            if (tid < nb) s_cur[tid] = cb[c0 + tid];
-            __syncthreads();
-            for (int bb = 0; bb < nb; bb++) {
-                const long long cv = s_cur[bb];
-                const long long cval = s_dc[bb][tid & 63];
-#pragma unroll
-                for (int k = 0; k < kTuplesPerThread; k++) {
-                    const int l = (tid >> 6) + k * (kGreedyThreads >> 6);
-                    tot[k] += min(cv, s_dl[bb][l] + cval);
-                }
-            }
-            __syncthreads();
-        }
-        // arg-min over the 4096 tuples, lowest index on ties
-        long long bv = tot[0];
-        int bt = tid;
-#pragma unroll
-        for (int k = 1; k < kTuplesPerThread; k++) {
-            const int t = tid + k * kGreedyThreads;
-            if (better(tot[k], t, bv, bt)) { bv = tot[k]; bt = t; }
-        }
+    if (warp == 0) {
+        bv = s_v[lane];
+        bt = s_t[lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
             const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
             if (better(ov, ot, bv, bt)) { bv = ov; bt = ot; }
         }
-        if (lane == 0) { s_best[warp] = bv; s_bt[warp] = bt; }
-        __syncthreads();
-        if (tid == 0) {
-            long long v = s_best[0];
-            int t = s_bt[0];
-            for (int w = 1; w < kGreedyThreads / 32; w++)
-                if (better(s_best[w], s_bt[w], v, t)) { v = s_best[w]; t = s_bt[w]; }
-            s_presets[n] = t;
-            s_tot[n] = v;
+        if (lane == 0) {
+            res[fi].presets[step] = bt;
+            res[fi].totals[step] = (long long)bv;
+            s_t[0] = bt;
         }
-        __syncthreads();
-        const int t = s_presets[n];
-        for (int b = tid; b < B; b += kGreedyThreads)
-            cb[b] = min(cb[b], dl[(int64_t)b * 64 + (t >> 6)] + dc[(int64_t)b * 64 + (t & 63)]);
-        __syncthreads();
     }
+    __syncthreads();
+    const int best = s_t[0];
+    const int B = F.fb_cols * F.fb_rows;
+    for (int b = tid; b < B; b += 1024) {
+        const int g = F.block_start + b;
+        const unsigned long long d = (unsigned long long)(dl[(int64_t)g * 64 + (best >> 6)] +
+                                                          dc[(int64_t)g * 64 + (best & 63)]);
+        if (d < cur[g]) cur[g] = d;
+    }
+    for (int i = tid; i < kTuples; i += 1024) t[i] = 0;
+}
 
+// Per frame: N in {1, 2, 4, 8} by J = lambda B log2 N + total (ties to the
+// smaller N), then each block's least-distortion preset (ties to the lower id).
+__global__ void greedy_final(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
+                             const long long *__restrict__ dc, SearchResultDev *res, uint8_t *block_ids)
+{
     __shared__ int s_n;
-    if (tid == 0) {
+    const int fi = blockIdx.x;
+    const SearchFrameDev &F = batch.f[fi];
+    const int B = F.fb_cols * F.fb_rows;
+    SearchResultDev &r = res[fi];
+    if (threadIdx.x == 0) {
         int bn = 0;
         long long bj = 0;
         for (int lg = 0; lg < 4; lg++) {
             const int n = 1 << lg;
-            const long long j = s_tot[n - 1] + F.lambda * (long long)B * lg;
+            const long long j = r.totals[n - 1] + F.lambda * (long long)B * lg;
             if (bn == 0 || j < bj) { bn = n; bj = j; }
         }
-        SearchResultDev &r = res[blockIdx.x];
-        for (int k = 0; k < 8; k++) { r.presets[k] = s_presets[k]; r.totals[k] = s_tot[k]; }
         r.cost = bj;
         r.npresets = bn;
         s_n = bn;
     }
     __syncthreads();
     const int N = s_n;
-    for (int b = tid; b < B; b += kGreedyThreads) {
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const int g = F.block_start + b;
         int id = 0;
-        long long best = dl[(int64_t)b * 64 + (s_presets[0] >> 6)] + dc[(int64_t)b * 64 + (s_presets[0] & 63)];
-        for (int k = 1; k < N; k++) {
-            const long long v = dl[(int64_t)b * 64 + (s_presets[k] >> 6)] +
-                                dc[(int64_t)b * 64 + (s_presets[k] & 63)];
+        long long best = LLONG_MAX;
+        for (int k = 0; k < N; k++) {
+            const int t = r.presets[k];
+            const long long v = dl[(int64_t)g * 64 + (t >> 6)] + dc[(int64_t)g * 64 + (t & 63)];
             if (v < best) { best = v; id = k; }
         }
-        block_ids[F.block_start + b] = (uint8_t)id;
+        block_ids[g] = (uint8_t)id;
     }
+}
+
+constexpr size_t kSmemBytes = sizeof(SearchSmem);
+
+int dist_grid(int total)
+{
+    static int cached_dev = -1, cached_ctas = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != cached_dev) {
+        cudaFuncSetAttribute(dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaFuncSetAttribute(dist_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        int sms = 0, occ = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dist_kernel, kThreads, kSmemBytes);
+        cached_ctas = sms * (occ > 0 ? occ : 1);
+        cached_dev = dev;
+    }
+    return total < cached_ctas ? total : cached_ctas;
 }
 
 }  // namespace
 
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long *dist_chroma,
-                          long long *cur, SearchResultDev *results, uint8_t *block_ids,
-                          int *status, cudaStream_t s)
+                          unsigned long long *cur, unsigned long long *tot, SearchResultDev *results,
+                          uint8_t *block_ids, int *status, unsigned *work, cudaStream_t s)
 {
-    (void)status;
-    dist_kernel<<<b.total_blocks, kThreads, 0, s>>>(b, dist_luma, dist_chroma);
+    dist_kernel<<<dist_grid(b.total_blocks), kThreads, kSmemBytes, s>>>(b, dist_luma, dist_chroma,
+                                                                        status, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    greedy_kernel<<<b.n, kGreedyThreads, 0, s>>>(b, dist_luma, dist_chroma, cur, results, block_ids);
+    greedy_init<<<64, 256, 0, s>>>(b, cur, tot);
+    int chunks = 0;
+    for (int i = 0; i < b.n; i++)
+        chunks += (b.f[i].fb_cols * b.f[i].fb_rows + kChunk - 1) / kChunk;
+    for (int step = 0; step < 8; step++) {
+        greedy_partial<<<chunks, kPartThreads, 0, s>>>(b, dist_luma, dist_chroma, cur, tot);
+        greedy_select<<<b.n, 1024, 0, s>>>(b, dist_luma, dist_chroma, cur, tot, results, step);
+    }
+    greedy_final<<<b.n, 256, 0, s>>>(b, dist_luma, dist_chroma, results, block_ids);
     return cudaGetLastError();
 }
 
