@@ -172,6 +172,7 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
  *   npresets     : HOST, n entries
  *   block_ids    : DEVICE, sum_i B_i bytes, written
  *   cost         : HOST, n entries: J of the chosen N
+ * 1 <= n <= 48; bit depth 8 or 10 (CDEF_ERR_BITDEPTH otherwise).
  * This call synchronises the stream before returning (host outputs).
  */
 int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
@@ -189,10 +190,11 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
  * up front, or a real-time encoder loop that cannot afford the implicit
  * device-wide synchronisation cudaMalloc/cudaFree may cause.  For them this
  * entry point takes no context and calls no allocating routine.  The only
- * device scratch it needs (one int64 per filter block for the greedy
- * search's running minima, plus one result record per frame) lives in a
- * fixed array inside the library, which every GPU that loads the library
- * holds until the process exits: about 135 KiB.
+ * device scratch it needs (one 64-bit running minimum per filter block and
+ * 4096 64-bit preset totals per frame for the greedy search, one result
+ * record per frame, a work counter) lives in a fixed array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits: about 1.63 MiB (CDEF_NOALLOC_MAX_BLOCKS blocks, 48 frames).
  *
  *   - Same arguments, results and errors as cdef_search_strengths, except
  *     that there is no context and dist_luma / dist_chroma are required
