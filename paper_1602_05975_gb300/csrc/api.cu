@@ -25,6 +25,10 @@ struct cdef_ctx {
     SearchResultDev *dev_results;
     unsigned *work;       // kWorkSlots pairs of filter work counters (zeroed)
     unsigned next_slot;   // next pair handed to a launch
+    cudaStream_t capture; // records the search's launches into a graph
+    cudaGraphExec_t search_exec;  // the last search graph, updated per call
+    SearchBatch *search_key;      // what search_exec was recorded for
+    void *search_ptrs[5];         // and its tables, ids and scratch pointers
 };
 
 namespace {
@@ -224,7 +228,8 @@ int cdef_ctx_create(cdef_ctx **out, int device, size_t hbm_budget_bytes)
         cudaMalloc(&ctx->dev_results, sizeof(SearchResultDev) * kMaxBatch) != cudaSuccess ||
         cudaMalloc(&ctx->work, sizeof(unsigned) * 2 * kWorkSlots) != cudaSuccess ||
         cudaMemset(ctx->work, 0, sizeof(unsigned) * 2 * kWorkSlots) != cudaSuccess ||
-        cudaMallocHost(&ctx->host_results, sizeof(SearchResultDev) * kMaxBatch) != cudaSuccess) {
+        cudaMallocHost(&ctx->host_results, sizeof(SearchResultDev) * kMaxBatch) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         cdef_ctx_destroy(ctx);
         return CDEF_ERR_CUDA;
@@ -244,6 +249,9 @@ int cdef_ctx_destroy(cdef_ctx *ctx)
     if (ctx->host_results) cudaFreeHost(ctx->host_results);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->work) cudaFree(ctx->work);
+    if (ctx->search_exec) cudaGraphExecDestroy(ctx->search_exec);
+    if (ctx->capture) cudaStreamDestroy(ctx->capture);
+    delete ctx->search_key;
     delete ctx;
     return CDEF_OK;
 }
@@ -293,7 +301,7 @@ int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params 
     b.n = 1;
     b.total_blocks = fb_count(in);
     if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0))) return rc;
-    unsigned *work = ctx->work + 2 * (ctx->next_slot++ % kWorkSlots);
+    unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
     return cuda_status(launch_filter_single(b, ctx->status, work, static_cast<cudaStream_t>(cuda_stream)));
 }
 
@@ -327,7 +335,7 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
         start += fb_count(&in[i]);
     }
     bp->total_blocks = start;
-    unsigned *work = ctx->work + 2 * (ctx->next_slot++ % kWorkSlots);
+    unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
     const int rc = cuda_status(launch_filter_batch(*bp, ctx->status, work, static_cast<cudaStream_t>(cuda_stream)));
     delete bp;
     return rc;
@@ -388,9 +396,46 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
         dc = dl + (size_t)total * 64;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    unsigned *work = ctx->work + 2 * (ctx->next_slot++ % kWorkSlots);
-    cudaError_t e = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status,
-                                  work, s);
+    // Search calls synchronise before returning, so they never overlap: the
+    // search owns counter pair 0 (filter launches take pairs 1..).
+    unsigned *work = ctx->work;
+    // The whole search (distortion kernel, 8 greedy steps, final choice) as
+    // one graph launch.  A call on the same frames and buffers as the last
+    // one relaunches its graph; otherwise the launches are recorded on the
+    // capture stream and the cached executable graph updated in place
+    // (re-instantiated if the shape changed).
+    void *const ptrs[5] = {dl, dc, block_ids, cur, tot};
+    const bool same = ctx->search_exec && ctx->search_key &&
+                      memcmp(ctx->search_key, b, sizeof(SearchBatch)) == 0 &&
+                      memcmp(ctx->search_ptrs, ptrs, sizeof(ptrs)) == 0;
+    cudaError_t e = same ? cudaSuccess : cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess && !same) {
+        const cudaError_t le = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids,
+                                             ctx->status, work, ctx->capture);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(ctx->capture, &graph);
+        if (e == cudaSuccess && le != cudaSuccess) e = le;
+        if (e == cudaSuccess) {
+            cudaGraphExecUpdateResultInfo info;
+            if (!ctx->search_exec || cudaGraphExecUpdate(ctx->search_exec, graph, &info) != cudaSuccess) {
+                cudaGetLastError();
+                if (ctx->search_exec) cudaGraphExecDestroy(ctx->search_exec);
+                ctx->search_exec = nullptr;
+                e = cudaGraphInstantiate(&ctx->search_exec, graph, 0);
+            }
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess) {
+            if (!ctx->search_key) ctx->search_key = new (std::nothrow) SearchBatch();
+            if (ctx->search_key) {
+                memcpy(ctx->search_key, b, sizeof(SearchBatch));
+                memcpy(ctx->search_ptrs, ptrs, sizeof(ptrs));
+            }
+        } else if (ctx->search_key) {
+            memset(ctx->search_key, 0, sizeof(SearchBatch));
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(ctx->search_exec, s);
     delete b;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->host_results, ctx->dev_results, sizeof(SearchResultDev) * n,
