@@ -41,6 +41,8 @@ sys.path.insert(0, ROOT)
 METRIC = "Mpixel/s (find_dir+filter)"
 UNIT = "Mpixel/s"
 KERNEL_SOURCES = ["paper_1602_05975_gb300/csrc/filter.cu",
+                  "paper_1602_05975_gb300/csrc/tile.cuh",
+                  "paper_1602_05975_gb300/csrc/tma.cuh",
                   "paper_1602_05975_gb300/csrc/cdef_device.cuh"]
 
 
@@ -62,7 +64,7 @@ def ncu_traffic(kernel: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel sources."""
     try:
-        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        d = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.txt")))
     except Exception:  # noqa: BLE001
         return None
     e = d.get(kernel)
@@ -129,12 +131,30 @@ def run_oracle(pool, cores, frames, nbands):
     res = pool.map(_oracle_band, tasks, chunksize=1)
     wall = time.perf_counter() - t
     px = sum(r[0] for r in res)
-    return px / wall / 1e6, px, wall
+    return px / wall / 1e6, px, wall, sum(r[1] for r in res)
+
+
+def oracle_sample(frames, nbands) -> str:
+    n = len(oracle_tasks(frames, nbands))
+    total = sum(-(-f.height // BAND) for f in frames)
+    what = "all" if n == total else f"{n} of the {total}"
+    return (f"{what} {WORKLOAD['width']}x{BAND} bands (luma + chroma) of the {len(frames)} "
+            f"{WORKLOAD['width']}x{WORKLOAD['height']} {WORKLOAD['bitdepth']}-bit frames, "
+            f"one band per task, each filtered as a frame of its own by the oracle")
 
 
 # ------------------------------------------------------------------ clocks
+def _smi_time(stamp: str):
+    """nvidia-smi's `YYYY/MM/DD hh:mm:ss.mmm` local time → epoch seconds."""
+    try:
+        whole, _, frac = stamp.partition(".")
+        return time.mktime(time.strptime(whole, "%Y/%m/%d %H:%M:%S")) + float("0." + (frac or "0"))
+    except Exception:  # noqa: BLE001
+        return None
+
+
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -149,10 +169,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:  # noqa: BLE001
             self.proc = None
+
+    def mark(self, which: str):
+        """Host wall-clock bounds of the timed region."""
+        setattr(self, which, time.time())
 
     def stop(self):
         if self.proc is None:
@@ -166,18 +190,29 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
+            if len(parts) >= 10:
+                parts[0] = _smi_time(parts[0])
                 rows.append(parts)
         os.unlink(self.path)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        # samples taken while the timed region ran (the nearest one if the
+        # region was shorter than the sampling period)
+        t0, t1 = getattr(self, "begin", None), getattr(self, "end", None)
+        inside = rows
+        if t0 is not None and t1 is not None and all(r[0] is not None for r in rows):
+            inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05]
+            if not inside:
+                mid = 0.5 * (t0 + t1)
+                inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        sm = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        reasons = sorted({n for r in inside for n, v in zip(names, r[6:10])
+                          if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(inside)}
 
 
 # ------------------------------------------------------------------ main arms
@@ -194,20 +229,19 @@ def run_reference(args):
         return
     from paper_1602_05975_gb300 import synth  # noqa: F401
     cores = min(os.cpu_count() or 1, 16)
-    frames = make_frames()[:2]
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
+        frames = make_frames()
+        nb = args.cpu_bands or 10**9
         for _ in range(args.warmup):
-            run_oracle(pool, cores, frames, cores)
-        vals, pxs, walls = [], 0, 0.0
+            run_oracle(pool, cores, frames, nb)
+        pxs, walls = 0, 0.0
         for _ in range(args.steps):
-            v, px, wall = run_oracle(pool, cores, frames, cores)
-            vals.append(v)
+            v, px, wall, _ = run_oracle(pool, cores, frames, nb)
             pxs += px
             walls += wall
     value = pxs / walls / 1e6
-    sample = (f"{cores} bands of {WORKLOAD['width']}x{BAND} luma (+chroma) of the 4K 10-bit "
-              f"frames per step, one band per core, each filtered as a frame by the oracle")
+    sample = f"per step, {oracle_sample(frames, nb)}"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -277,11 +311,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    clocks.mark("begin")
     t0.record(stream)
     for k in range(args.steps):
         step(evs[k])
     t1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark("end")
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
     launch_ms = [a.elapsed_time(b) for row in evs for (a, b) in row]
@@ -346,11 +382,12 @@ def run_ours(args):
 
     cpu = None
     if pool is not None:
-        v, px, wall = run_oracle(pool, cores, frames[:4], args.cpu_bands)
+        nb = args.cpu_bands or 10**9
+        v, px, wall, cpu_s = run_oracle(pool, cores, frames, nb)
         pool.close()
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_bands} bands of {WORKLOAD['width']}x{BAND} luma (+chroma) "
-                         f"of the same frames, {px / 1e6:.1f} Mpixel in {wall:.1f} s wall"}
+               "sample": f"{oracle_sample(frames, nb)}: {px / 1e6:.1f} Mpixel, "
+                         f"{cpu_s:.1f} s of CPU work in {wall:.1f} s wall"}
 
     if rank == 0:
         print(json.dumps({
@@ -408,11 +445,13 @@ def run_search(args):
     clocks = ClockSampler(0)
     clocks.start()
     time.sleep(0.3)
+    clocks.mark("begin")
     t0 = time.perf_counter()
     for _ in range(args.steps):
         cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc, stream=stream)
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / args.steps
+    clocks.mark("end")
     clk = clocks.stop()
     print(json.dumps({
         "metric": "strength-search candidates/s", "value": nb * 128 / sec, "unit": "candidates/s",
@@ -432,7 +471,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-bands", type=int, default=36)
+    ap.add_argument("--cpu-bands", type=int, default=0,
+                    help="oracle sample: number of 120-row bands (0 = the whole step)")
     ap.add_argument("--check", action="store_true", help="oracle check of frame 0")
     ap.add_argument("--workload", default="filter", choices=["filter", "search"],
                     help="filter: the 4K 10-bit filter (default line); search: batched "
