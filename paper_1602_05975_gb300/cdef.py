@@ -27,7 +27,7 @@ ERRORS = {-1: "CDEF_ERR_ARG", -2: "CDEF_ERR_SIZE", -3: "CDEF_ERR_BITDEPTH",
           -4: "CDEF_ERR_NOMEM", -5: "CDEF_ERR_CUDA", -6: "CDEF_ERR_TIMEOUT",
           -7: "CDEF_ERR_DEVICE"}
 SEC_VALUES = (0, 1, 2, 4)
-MAX_BATCH = 64
+MAX_BATCH = 48  # frames per cdef_filter_frames / cdef_search_strengths call
 
 
 class CdefError(RuntimeError):
@@ -158,6 +158,36 @@ def alloc_frame(width: int, height: int, bitdepth: int, device="cuda", fill=None
             t.fill_(fill)
         planes.append(t)
     return Frame(*planes, width, height, bitdepth)
+
+
+def packed_layout(width: int, height: int, bitdepth: int, extra_bytes: int = 0):
+    """Byte offsets of the y, u, v planes (and of `extra_bytes` after them)
+    in one flat buffer, each 256-byte aligned, and the buffer's size."""
+    b = 1 if bitdepth == 8 else 2
+    offs, o = [], 0
+    for w, h in ((width, height), (width // 2, height // 2), (width // 2, height // 2)):
+        offs.append(o)
+        o += -(-h * pitch_samples(w, bitdepth) * b // 256) * 256
+    offs.append(o)
+    return offs, o + -(-extra_bytes // 256) * 256
+
+
+def alloc_packed(width: int, height: int, bitdepth: int, device="cuda", pin=False,
+                 extra_bytes: int = 0):
+    """A frame whose three planes are views into one flat uint8 buffer (one
+    copy moves the whole frame).  Returns (flat, frame, extra) where `extra`
+    is a uint8 view of `extra_bytes` after the planes (e.g. parameters)."""
+    offs, size = packed_layout(width, height, bitdepth, extra_bytes)
+    flat = torch.empty(size, dtype=torch.uint8, device=device)
+    if pin:
+        flat = flat.pin_memory()
+    dt, b = sample_dtype(bitdepth), (1 if bitdepth == 8 else 2)
+    planes = []
+    for k, (w, h) in enumerate(((width, height), (width // 2, height // 2),
+                                (width // 2, height // 2))):
+        p = pitch_samples(w, bitdepth)
+        planes.append(flat[offs[k]:offs[k] + h * p * b].view(dt).view(h, p))
+    return flat, Frame(*planes, width, height, bitdepth), flat[offs[3]:offs[3] + extra_bytes]
 
 
 def frame_from_numpy(planes, bitdepth: int, device="cuda", pin=False) -> Frame:

@@ -24,7 +24,7 @@ struct PlaneDev {
 };
 
 // One frame of a filter launch.
-struct alignas(64) FilterFrameDev {
+struct FilterFrameDev {  // aligned as CUtensorMap requires
     CUtensorMap tmap[3];             // 2-D tile maps of the y, u, v input planes
     PlaneDev p[3];                   // y, u, v
     const cdef_fb_params *params;    // B entries
@@ -43,7 +43,7 @@ struct FilterBatch {
 };
 
 // One frame of a strength search launch.
-struct alignas(64) SearchFrameDev {
+struct SearchFrameDev {  // aligned as CUtensorMap requires
     CUtensorMap tmap[3];             // 2-D tile maps of the decoded y, u, v planes
     const uint8_t *rec[3];
     const uint8_t *src[3];

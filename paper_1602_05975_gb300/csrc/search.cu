@@ -40,7 +40,7 @@ struct SearchSmem {
     PairTiles t;
     alignas(16) int off[2][8][12];    // tap word offsets [luma/chroma][d][tap]
     int cost[64][8];
-    alignas(16) SetC pset[64][16];    // luma primary sets per 8x8 block and signalled strength
+    alignas(16) SetC pset[64][17];    // luma primary sets per 8x8 block and signalled strength
     alignas(16) SetC cset[16];        // chroma primary sets per signalled strength
     alignas(16) SetC sset[3][4];      // secondary: luma; chroma at D - 1; chroma at D = 3
     uint32_t pbits[64];               // luma: bit p odd adjusted strength, bit 16 + p adjusted > 0
@@ -49,6 +49,7 @@ struct SearchSmem {
     uint8_t dir[64];
     int var[64];
     unsigned long long acc[64];       // block totals of the current plane group
+    unsigned long long base[2];       // sum of (x - s)^2 over the same pixels, per plane group
     int blk[2];
     alignas(8) uint64_t bar[2];
 };
@@ -83,6 +84,13 @@ __device__ __forceinline__ uint32_t add_sq(uint32_t acc, uint32_t y, uint32_t s)
     if (sizeof(T) == 1) return __dp2a_lo(e, __byte_perm(e, 0, 0x0020), acc);
     const uint32_t lo = e & 0xffffu, hi = e >> 16;
     return acc + lo * lo + hi * hi;
+}
+
+// Per 16-bit lane a + b, the lanes read as signed and independent (no carry
+// between them); every sum formed with it here stays within int16.
+__device__ __forceinline__ uint32_t sadd16(uint32_t a, uint32_t b)
+{
+    return __viaddmax_s16x2(a, b, 0x80008000u);
 }
 
 // Weighted sum of the 4 primary clamped values for one set.
@@ -158,6 +166,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         sm.dir[tid] = (uint8_t)best;
         sm.var[tid] = bc - sm.cost[tid][(best + 4) & 7];
         sm.acc[tid] = 0;
+        if (tid < 2) sm.base[tid] = 0;
     }
     __syncthreads();
 
@@ -222,7 +231,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         const uint8_t *sa = luma ? F.src[0] : F.src[1];
         const int64_t spa = luma ? F.src_pitch[0] : F.src_pitch[1];
 
-        uint32_t acc[64];
+        uint32_t acc[64], sse0 = 0;
 #pragma unroll
         for (int q = 0; q < 64; q++) acc[q] = 0;
         if (inside) {
@@ -246,6 +255,15 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 const uint32_t S = luma ? load_src_pair<T>(sa + (int64_t)(oy + i) * spa, ox)
                                         : load_src_uv<T>(sa + (int64_t)(oy + i) * spa,
                                                          F.src[2] + (int64_t)(oy + i) * F.src_pitch[2], ox);
+                // Squared error of one candidate, with e = y - s = (x - s) + r:
+                // e^2 = (x - s)^2 + r (2 (x - s) + r).  The first term does not
+                // depend on the candidate and is summed once per pixel; the
+                // second is formed from the candidate's correction r, which
+                // at 8 and 10 bits stays within a signed byte (|r| <= 57).
+                sse0 = add_sq<T>(sse0, X, S);
+                const uint32_t two_xs = sadd16(2u * (X + 4096u * kLanes - S), 0xdf00u * kLanes);
+                const uint32_t rlo = __vmaxu2(mn - X + 2048u * kLanes, 1792u * kLanes) - 1792u * kLanes;
+                const uint32_t rhi = mx - X + 256u * kLanes;
                 uint32_t Q[4], Qr[4];
                 Q[0] = Qr[0] = 12u * X;
 #pragma unroll
@@ -262,7 +280,6 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 for (int p = 0; p < 16; p++) {
                     const SetC sc = ps[p];
                     const uint32_t T0 = pri_sum(v, X, sc, (bits >> p) & 1) + C;
-                    const bool on = (bits >> (16 + p)) & 1;
                     const bool rz = (raised >> p) & 1;
 #pragma unroll
                     for (int s = 0; s < 4; s++) {
@@ -270,20 +287,30 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                         const uint32_t u = T0 + (rz ? Qr[s] : Q[s]);
                         const uint32_t pos = (u >> 12) & kLanes;
                         const uint32_t w = u + pos + 7u * kLanes;
-                        uint32_t y = X + ((w >> 4) & (0x0fffu * kLanes)) - 256u * kLanes;
-                        if (s > 0 && on) y = __vminu2(__vmaxu2(y, mn), mx);   // eq. 9-12
-                        acc[p * 4 + s] = add_sq<T>(acc[p * 4 + s], y, S);
+                        uint32_t rb = (w >> 4) & (0x0fffu * kLanes);   // r + 256 per lane
+                        // eq. 9-12 on r: x + r is held in [min, max].  Where the
+                        // adjusted primary strength is 0 only the secondary set
+                        // contributes, its weights sum to 12/16 < 1, and the
+                        // clip cannot bind: it is applied without a test.
+                        if (s > 0) rb = __vminu2(__vmaxu2(rb, rlo), rhi);
+                        const uint32_t a = sadd16(rb, two_xs);           // 2 (x - s) + r
+                        acc[p * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)__byte_perm(rb, 0, 0x0020),
+                                                             (int)acc[p * 4 + s]);
                     }
                 }
             }
         }
         butterfly64(acc, lane);
-        atomicAdd(&sm.acc[2 * lane], (unsigned long long)acc[0]);
-        atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)acc[1]);
+        // the warp totals of r (2 (x - s) + r) are signed and fit 32 bits
+        atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
+        atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) sse0 += __shfl_xor_sync(0xffffffffu, sse0, o);
+        if (lane == 0) atomicAdd(&sm.base[task], (unsigned long long)sse0);
         __syncthreads();
         if (tid < 64) {
             long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64;
-            out[tid] = (long long)sm.acc[tid];
+            out[tid] = (long long)(sm.acc[tid] + sm.base[task]);
             sm.acc[tid] = 0;
         }
         __syncthreads();

@@ -1,0 +1,409 @@
+"""Decode-side CDEF serving loop with continuous batching.
+
+Requests are single 4:2:0 frames of any supported size and bit depth, each
+with its own per-64x64 parameters (section 4: one primary/secondary strength
+pair per plane group and a damping value per filter block).  The server
+
+* admits queued requests in arrival order while their device buffers fit an
+  HBM budget (input frame + parameters + output frame per request);
+* launches every admitted request that is not yet on the device as one
+  batch through the batched filter entry point (``cdef_filter_frames``: one
+  launch for frames of mixed sizes and bit depths), as soon as fewer than
+  ``max_inflight`` batches are on the device -- requests that arrive while a
+  batch runs join the next one;
+* overlaps the host-to-device copies of the next batch, the filter launch of
+  the current one and the device-to-host copies of the previous one on three
+  CUDA streams;
+* frees a request's buffers when its output has reached the host.
+
+The scheduling is host logic over a small backend interface, so that it can
+be driven by a fake backend in tests (no GPU) and by :class:`CudaBackend`
+on the GPU.  ``max_batch=1, max_inflight=1`` turns the same loop into the
+one-frame-at-a-time server used as the comparison point.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Callable, Optional
+
+import numpy as np
+
+# Signalled ranges of section 4: primary 0..15 (19 for the skip mapping),
+# secondary {0, 1, 2, 4} (7 for the skip mapping), damping 3..6.
+_PRI_OK = set(range(16)) | {19}
+_SEC_OK = {0, 1, 2, 4, 7}
+
+
+def validate_params(params: np.ndarray, width: int, height: int) -> Optional[str]:
+    """Host-side check of a request's parameter array; None if valid."""
+    rows, cols = -(-height // 64), -(-width // 64)
+    if params.shape != (rows, cols, 8):
+        return f"params shape {params.shape}, expected {(rows, cols, 8)}"
+    p = params.reshape(-1, 8)
+    for k, ok in ((0, _PRI_OK), (1, _SEC_OK), (2, _PRI_OK), (3, _SEC_OK)):
+        if not set(np.unique(p[:, k]).tolist()) <= ok:
+            return "strength out of range"
+    if p[:, 4].min() < 3 or p[:, 4].max() > 6:
+        return "damping out of range"
+    return None
+
+
+@dataclasses.dataclass(eq=False)
+class Request:
+    """One frame to filter.  `frame` and `params` are backend inputs (for
+    :class:`CudaBackend`: a pinned host frame and a (rows, cols, 8) uint8
+    array); `arrival` is seconds from the start of the run."""
+    rid: int
+    width: int
+    height: int
+    bitdepth: int
+    frame: object
+    params: np.ndarray
+    arrival: float = 0.0
+    # filled in by the server
+    status: str = "new"            # queued, admitted, launched, ok, rejected, failed, cancelled
+    error: str = ""
+    t_submit: float = math.nan
+    t_admit: float = math.nan
+    t_launch: float = math.nan
+    t_done: float = math.nan
+    need: int = 0                  # device bytes held while admitted
+    slot: object = None            # backend buffers
+    out: object = None             # backend output (CudaBackend: pinned host flat buffer)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+
+class Backend:
+    """What the server needs from a device."""
+
+    def need_bytes(self, req: Request) -> int:
+        raise NotImplementedError
+
+    def reserve(self, req: Request) -> None:
+        """Give `req` device buffers (called at admission)."""
+        raise NotImplementedError
+
+    def release(self, req: Request) -> None:
+        raise NotImplementedError
+
+    def launch(self, reqs: list) -> object:
+        """Enqueue upload, filter and download of `reqs`; returns a handle.
+        Raises on a launch error."""
+        raise NotImplementedError
+
+    def poll(self, handle) -> Optional[list]:
+        """None while the batch runs, else one status per request: "ok" or
+        an error text."""
+        raise NotImplementedError
+
+
+class Server:
+    def __init__(self, backend: Backend, budget_bytes: int, max_batch: int = 48,
+                 max_inflight: int = 2, clock: Callable[[], float] = time.perf_counter,
+                 on_done: Optional[Callable[[Request], None]] = None):
+        if max_batch < 1 or max_inflight < 1:
+            raise ValueError("max_batch and max_inflight must be >= 1")
+        self.backend = backend
+        self.budget = int(budget_bytes)
+        self.max_batch = max_batch
+        self.max_inflight = max_inflight
+        self.clock = clock
+        self.on_done = on_done
+        self.queue: collections.deque = collections.deque()   # waiting for admission
+        self.ready: list = []                                  # admitted, not launched
+        self.inflight: list = []                               # (handle, [requests])
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.batches = 0
+        self.batch_sizes: list = []
+        self.finished: list = []
+        self._by_id: dict = {}
+
+    # ------------------------------------------------------------ requests
+    def submit(self, req: Request, now: Optional[float] = None) -> bool:
+        """Queue a request; False (and status "rejected") if it can never run."""
+        req.t_submit = self.clock() if now is None else now
+        self._by_id[req.rid] = req
+        why = validate_params(req.params, req.width, req.height)
+        if why is None and (req.width <= 0 or req.height <= 0 or req.width % 8 or req.height % 8):
+            why = "frame size must be a positive multiple of 8"
+        if why is None and req.bitdepth not in (8, 10, 12):
+            why = "bit depth must be 8, 10 or 12"
+        if why is None:
+            req.need = self.backend.need_bytes(req)
+            if req.need > self.budget:
+                why = f"needs {req.need} device bytes, budget is {self.budget}"
+        if why is not None:
+            self._finish(req, "rejected", why, req.t_submit)
+            return False
+        req.status = "queued"
+        self.queue.append(req)
+        return True
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a request that has not been launched."""
+        req = self._by_id.get(rid)
+        if req is None or req.status not in ("queued", "admitted"):
+            return False
+        if req.status == "queued":
+            self.queue.remove(req)
+        else:
+            self.ready.remove(req)
+            self._free(req)
+        self._finish(req, "cancelled", "", self.clock())
+        return True
+
+    # ------------------------------------------------------------ the loop
+    def step(self, now: Optional[float] = None) -> bool:
+        """One scheduling pass; True if anything changed."""
+        now = self.clock() if now is None else now
+        progress = False
+        # 1. completed batches
+        still = []
+        for handle, reqs in self.inflight:
+            res = self.backend.poll(handle)
+            if res is None:
+                still.append((handle, reqs))
+                continue
+            progress = True
+            for r, st in zip(reqs, res):
+                self._free(r)
+                if st == "ok":
+                    self._finish(r, "ok", "", now)
+                else:
+                    self._finish(r, "failed", st, now)
+        self.inflight = still
+        # 2. admission, first come first served, under the budget
+        while self.queue and self.in_use + self.queue[0].need <= self.budget:
+            r = self.queue.popleft()
+            self.backend.reserve(r)
+            self.in_use += r.need
+            self.peak_in_use = max(self.peak_in_use, self.in_use)
+            r.status, r.t_admit = "admitted", now
+            self.ready.append(r)
+            progress = True
+        # 3. continuous batching: launch what is admitted while the device
+        #    has room for another batch
+        while self.ready and len(self.inflight) < self.max_inflight:
+            batch, self.ready = self.ready[:self.max_batch], self.ready[self.max_batch:]
+            try:
+                handle = self.backend.launch(batch)
+            except Exception as e:  # noqa: BLE001 - the batch fails, the server goes on
+                for r in batch:
+                    self._free(r)
+                    self._finish(r, "failed", f"launch: {e}", now)
+                progress = True
+                continue
+            for r in batch:
+                r.status, r.t_launch = "launched", now
+            self.inflight.append((handle, batch))
+            self.batches += 1
+            self.batch_sizes.append(len(batch))
+            progress = True
+        return progress
+
+    def idle(self) -> bool:
+        return not (self.queue or self.ready or self.inflight)
+
+    def drain(self, timeout: float = 60.0) -> None:
+        t_end = self.clock() + timeout
+        while not self.idle():
+            if not self.step() and self.clock() > t_end:
+                raise TimeoutError("requests still pending")
+
+    def run(self, requests: list, timeout: float = 600.0) -> dict:
+        """Serve `requests` with real-time arrivals at start + r.arrival and
+        return the statistics."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        start = self.clock()
+        base = self.clock
+        self.clock = lambda: base() - start          # run-relative times
+        try:
+            i, n = 0, len(reqs)
+            while i < n or not self.idle():
+                now = self.clock()
+                if now > timeout:
+                    raise TimeoutError(f"{n - len(self.finished)} requests unfinished")
+                while i < n and reqs[i].arrival <= now:
+                    self.submit(reqs[i], now)
+                    i += 1
+                if not self.step(now) and self.idle() and i < n:
+                    # nothing to do before the next arrival: sleep through
+                    # most of the gap, spin the rest (sleep overshoots)
+                    gap = reqs[i].arrival - self.clock()
+                    if gap > 300e-6:
+                        time.sleep(gap - 200e-6)
+            wall = self.clock()
+        finally:
+            self.clock = base
+        return summarize(reqs, wall, self)
+
+    # ------------------------------------------------------------ internals
+    def _free(self, r: Request) -> None:
+        if r.slot is not None:
+            self.backend.release(r)
+            r.slot = None
+        if r.status in ("admitted", "launched"):
+            self.in_use -= r.need
+
+    def _finish(self, r: Request, status: str, error: str, now: float) -> None:
+        r.status, r.error, r.t_done = status, error, now
+        self.finished.append(r)
+        if self.on_done is not None:
+            self.on_done(r)
+
+
+def percentile(xs, q):
+    if not xs:
+        return math.nan
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
+
+
+def summarize(reqs, wall: float, server: Server) -> dict:
+    ok = [r for r in reqs if r.status == "ok"]
+    lat = [r.latency for r in ok]
+    px = sum(r.width * r.height for r in ok)
+    counts = collections.Counter(r.status for r in reqs)
+    return {
+        "requests": len(reqs), "ok": len(ok), "status": dict(counts),
+        "wall_s": wall, "frames_per_s": len(ok) / wall if wall > 0 else math.nan,
+        "mpixel_per_s": px / wall / 1e6 if wall > 0 else math.nan,
+        "p50_ms": percentile(lat, 50) * 1e3, "p99_ms": percentile(lat, 99) * 1e3,
+        "mean_ms": float(np.mean(lat)) * 1e3 if lat else math.nan,
+        "batches": server.batches,
+        "mean_batch": float(np.mean(server.batch_sizes)) if server.batch_sizes else 0.0,
+        "peak_device_bytes": server.peak_in_use,
+    }
+
+
+def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of `rate` requests/s."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, n))
+
+
+# ---------------------------------------------------------------- CUDA
+class CudaBackend(Backend):
+    """Device buffers, copies and launches for the server.
+
+    Each request's input frame and parameters travel in one host-to-device
+    copy into one flat device buffer, and its output in one device-to-host
+    copy into a pinned host buffer (``req.out``, valid once the request is
+    done).  Buffers are cached per (size, bit depth) and reused; cached free
+    buffers are dropped when a new size needs the room, so that the device
+    memory held never exceeds the server's budget."""
+
+    def __init__(self, ctx, budget_bytes: int, device: int = 0):
+        import torch
+        from . import cdef
+        self.torch, self.cdef, self.ctx = torch, cdef, ctx
+        self.device = torch.device("cuda", device)
+        self.budget = budget_bytes
+        self.up = torch.cuda.Stream(device=self.device)
+        self.comp = torch.cuda.Stream(device=self.device)
+        self.down = torch.cuda.Stream(device=self.device)
+        self.free: dict = collections.defaultdict(list)   # key -> [slot]
+        self.free_bytes = 0
+        self.held_bytes = 0
+        self.host_out: dict = collections.defaultdict(list)
+
+    @staticmethod
+    def key(req: Request):
+        return (req.width, req.height, req.bitdepth)
+
+    def _sizes(self, req: Request):
+        n_params = (-(-req.height // 64)) * (-(-req.width // 64)) * 8
+        _, in_b = self.cdef.packed_layout(req.width, req.height, req.bitdepth, n_params)
+        _, out_b = self.cdef.packed_layout(req.width, req.height, req.bitdepth)
+        return n_params, in_b, out_b
+
+    def need_bytes(self, req: Request) -> int:
+        _, in_b, out_b = self._sizes(req)
+        return in_b + out_b
+
+    def reserve(self, req: Request) -> None:
+        k = self.key(req)
+        if self.free[k]:
+            req.slot = self.free[k].pop()
+            self.free_bytes -= req.need
+        else:
+            # drop cached buffers of other sizes until the new one fits
+            for kk in list(self.free):
+                while self.held_bytes + req.need > self.budget and self.free[kk]:
+                    s = self.free[kk].pop()
+                    self.held_bytes -= s["bytes"]
+                    self.free_bytes -= s["bytes"]
+            n_params, _, _ = self._sizes(req)
+            flat_in, f_in, prm = self.cdef.alloc_packed(req.width, req.height, req.bitdepth,
+                                                        device=self.device, extra_bytes=n_params)
+            flat_out, f_out, _ = self.cdef.alloc_packed(req.width, req.height, req.bitdepth,
+                                                        device=self.device)
+            req.slot = {"flat_in": flat_in, "in": f_in, "params": prm, "flat_out": flat_out,
+                        "out": f_out, "bytes": req.need}
+            self.held_bytes += req.need
+        hk = self.host_out[k]
+        req.slot["host_out"] = hk.pop() if hk else self.cdef.alloc_packed(
+            req.width, req.height, req.bitdepth, device="cpu", pin=True)
+
+    def release(self, req: Request) -> None:
+        s = req.slot
+        self.host_out[self.key(req)].append(s.pop("host_out"))
+        self.free[self.key(req)].append(s)
+        self.free_bytes += s["bytes"]
+
+    def launch(self, reqs: list):
+        torch = self.torch
+        with torch.cuda.stream(self.up):
+            for r in reqs:
+                r.slot["flat_in"].copy_(r.frame, non_blocking=True)
+        ev_up = torch.cuda.Event()
+        ev_up.record(self.up)
+        self.comp.wait_event(ev_up)
+        self.cdef.cdef_filter_frames(self.ctx, [r.slot["in"] for r in reqs],
+                                     [r.slot["params"] for r in reqs],
+                                     [r.slot["out"] for r in reqs], stream=self.comp)
+        ev_c = torch.cuda.Event()
+        ev_c.record(self.comp)
+        self.down.wait_event(ev_c)
+        with torch.cuda.stream(self.down):
+            for r in reqs:
+                r.slot["host_out"][0].copy_(r.slot["flat_out"], non_blocking=True)
+        ev_d = torch.cuda.Event()
+        ev_d.record(self.down)
+        # keep the host output reachable from the request once it is done
+        for r in reqs:
+            r.out = r.slot["host_out"]
+        return (ev_d, len(reqs))
+
+    def poll(self, handle):
+        ev, n = handle
+        if not ev.query():
+            return None
+        # The context's status word collects device-side parameter errors.
+        # Requests are validated on the host before they are queued, so it
+        # stays 0; if it is ever set, the batch that saw it fails.
+        st = self.ctx.status()
+        return ["ok"] * n if st == 0 else [f"device status {st}"] * n
+
+
+def pack_request_input(cdef, frame_planes, params: np.ndarray, bitdepth: int):
+    """One pinned host buffer holding a frame's planes (uint16 numpy y, u, v)
+    and its parameters in the layout :class:`CudaBackend` copies."""
+    h, w = frame_planes[0].shape
+    n_params = params.size
+    flat, f, prm = cdef.alloc_packed(w, h, bitdepth, device="cpu", extra_bytes=n_params)
+    import torch
+    for t, a in zip(f.planes(), frame_planes):
+        a = np.asarray(a)
+        if bitdepth == 8:
+            t[:, :a.shape[1]] = torch.from_numpy(a.astype(np.uint8))
+        else:
+            t[:, :a.shape[1]] = torch.from_numpy(a.astype(np.uint16).view(np.int16))
+    prm.copy_(torch.from_numpy(np.ascontiguousarray(params, dtype=np.uint8).reshape(-1)))
+    return flat.pin_memory()
