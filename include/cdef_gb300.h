@@ -182,6 +182,34 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
                           int32_t *npresets, uint8_t *block_ids, int64_t *cost,
                           void *cuda_stream);
 
+/* Launch configuration of the strength search's distortion kernel (the
+ * first pass of cdef_search_strengths).  No paper counterpart: it decides
+ * how the work is cut, never what is computed -- every configuration gives
+ * identical tables, presets, ids and J.
+ *   search_groups      : 1, 2 or 4.  The 16 primary strengths of a filter
+ *                        block are split into this many work units of
+ *                        64/groups luma and 64/groups chroma candidate
+ *                        pairs each, so that a small search (few blocks)
+ *                        still occupies every SM.
+ *   search_ctas_per_sm : 1 or 2 persistent CTAs per SM.
+ * A field of 0 means "autotuned": the first search of a batch shape (frame
+ * count, sizes and bit depths) on a context times every configuration on
+ * that call's own inputs, on the call's stream, and keeps the fastest for
+ * the later searches of that shape. */
+typedef struct {
+    int32_t search_groups;
+    int32_t search_ctas_per_sm;
+    int32_t reserved[2];
+} cdef_tuning;
+
+/* Fix the configuration (NULL or zero fields: autotune, the default).
+ * CDEF_ERR_ARG for a value outside the lists above.  Host only. */
+int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *tuning);
+
+/* The configuration the context's last search ran with (all zero before
+ * the first search).  Host only. */
+int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
+
 /* The strength search without any memory allocation.  The paper has no
  * counterpart: this is a deployment variant of cdef_search_strengths.
  *

@@ -50,6 +50,11 @@ class Preset(C.Structure):
                 ("sec_uv", C.c_uint8)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("search_groups", C.c_int32), ("search_ctas_per_sm", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
+
+
 _lib = None
 
 
@@ -75,11 +80,14 @@ def load():
                                         C.POINTER(i32), C.POINTER(i64), vp, vp,
                                         C.POINTER(Preset), C.POINTER(i32), vp,
                                         C.POINTER(i64), vp]
+    L.cdef_ctx_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.cdef_ctx_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.cdef_strerror.argtypes = [C.c_int]
     L.cdef_strerror.restype = C.c_char_p
     L.cdef_version.restype = C.c_char_p
     for name in ("cdef_ctx_create", "cdef_ctx_destroy", "cdef_ctx_status", "cdef_find_dir",
-                 "cdef_filter_frame", "cdef_filter_frames", "cdef_search_strengths"):
+                 "cdef_filter_frame", "cdef_filter_frames", "cdef_search_strengths",
+                 "cdef_ctx_set_tuning", "cdef_ctx_get_tuning"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -240,6 +248,17 @@ class Context:
 
     def status(self, clear=True):
         return self._lib.cdef_ctx_status(self.handle, int(clear))
+
+    def set_tuning(self, search_groups: int = 0, search_ctas_per_sm: int = 0):
+        """Fix the strength search's launch configuration (0 = autotune)."""
+        t = Tuning(search_groups, search_ctas_per_sm)
+        _check(self._lib.cdef_ctx_set_tuning(self.handle, C.byref(t)), "cdef_ctx_set_tuning")
+
+    def tuning(self):
+        """(search_groups, search_ctas_per_sm) of the last search."""
+        t = Tuning()
+        _check(self._lib.cdef_ctx_get_tuning(self.handle, C.byref(t)), "cdef_ctx_get_tuning")
+        return t.search_groups, t.search_ctas_per_sm
 
 
 def cdef_find_dir(ctx: Context, luma: torch.Tensor, width: int, height: int, bitdepth: int,

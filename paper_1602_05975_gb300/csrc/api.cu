@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 
 #include "cdef_internal.h"
 
@@ -29,6 +30,10 @@ struct cdef_ctx {
     cudaGraphExec_t search_exec;  // the last search graph, updated per call
     SearchBatch *search_key;      // what search_exec was recorded for
     void *search_ptrs[5];         // and its tables, ids and scratch pointers
+    SearchTune search_key_tune;   // and its launch configuration
+    SearchTune forced;            // fields > 0 fixed by cdef_ctx_set_tuning
+    SearchTune last;              // configuration of the last search
+    std::unordered_map<uint64_t, SearchTune> *tuned;  // autotuned, per batch shape
 };
 
 namespace {
@@ -252,7 +257,30 @@ int cdef_ctx_destroy(cdef_ctx *ctx)
     if (ctx->search_exec) cudaGraphExecDestroy(ctx->search_exec);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
     delete ctx->search_key;
+    delete ctx->tuned;
     delete ctx;
+    return CDEF_OK;
+}
+
+int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *t)
+{
+    if (!ctx) return CDEF_ERR_ARG;
+    if (!t) {
+        ctx->forced = {0, 0};
+        return CDEF_OK;
+    }
+    const int g = t->search_groups, c = t->search_ctas_per_sm;
+    if (!(g == 0 || g == 1 || g == 2 || g == 4) || c < 0 || c > 2) return CDEF_ERR_ARG;
+    ctx->forced = {g, c};
+    return CDEF_OK;
+}
+
+int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last)
+{
+    if (!ctx || !last) return CDEF_ERR_ARG;
+    memset(last, 0, sizeof(*last));
+    last->search_groups = ctx->last.groups;
+    last->search_ctas_per_sm = ctx->last.ctas_per_sm;
     return CDEF_OK;
 }
 
@@ -341,6 +369,86 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
     return rc;
 }
 
+namespace {
+
+// Batch shape for the autotuner: frame count, sizes and bit depths.
+uint64_t search_shape(const SearchBatch &b)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+    mix((uint64_t)b.n);
+    for (int i = 0; i < b.n; i++) {
+        mix((uint64_t)b.f[i].w);
+        mix((uint64_t)b.f[i].h);
+        mix((uint64_t)b.f[i].bitdepth);
+    }
+    return h;
+}
+
+// The distortion kernel's launch configuration for this call: fixed by the
+// caller, known for this batch shape, or found now by timing every
+// candidate configuration (a warm-up run and a timed run each) on the call's
+// own inputs.  The runs write the call's outputs, which every configuration
+// computes identically.
+int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long long *dc,
+                       unsigned long long *cur, unsigned long long *tot, uint8_t *block_ids,
+                       cudaStream_t s, SearchTune *out)
+{
+    if (ctx->forced.groups > 0 && ctx->forced.ctas_per_sm > 0) {
+        *out = ctx->forced;
+        return CDEF_OK;
+    }
+    if (!ctx->tuned) ctx->tuned = new (std::nothrow) std::unordered_map<uint64_t, SearchTune>();
+    if (!ctx->tuned) return CDEF_ERR_NOMEM;
+    const uint64_t key = search_shape(b) ^ ((uint64_t)ctx->forced.groups << 56) ^
+                         ((uint64_t)ctx->forced.ctas_per_sm << 60);
+    auto it = ctx->tuned->find(key);
+    if (it != ctx->tuned->end()) {
+        *out = it->second;
+        return CDEF_OK;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return CDEF_ERR_CUDA;
+    }
+    SearchTune best{0, 0};
+    float best_ms = 0.f;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kNumSearchTunes && e == cudaSuccess; k++) {
+        const SearchTune t = kSearchTunes[k];
+        if ((ctx->forced.groups > 0 && t.groups != ctx->forced.groups) ||
+            (ctx->forced.ctas_per_sm > 0 && t.ctas_per_sm != ctx->forced.ctas_per_sm))
+            continue;
+        e = launch_search(b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status, ctx->work,
+                          t, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess)
+            e = launch_search(b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status,
+                              ctx->work, t, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best.groups == 0 || ms < best_ms)) {
+            best = t;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || best.groups == 0) {
+        cudaGetLastError();
+        return CDEF_ERR_CUDA;
+    }
+    (*ctx->tuned)[key] = best;
+    *out = best;
+    return CDEF_OK;
+}
+
+}  // namespace
+
 int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
                           const int32_t *damping, const int64_t *lambda, int64_t *dist_luma,
                           int64_t *dist_chroma, cdef_preset *presets, int32_t *npresets,
@@ -399,6 +507,12 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
     // Search calls synchronise before returning, so they never overlap: the
     // search owns counter pair 0 (filter launches take pairs 1..).
     unsigned *work = ctx->work;
+    SearchTune tune;
+    if ((rc = choose_search_tune(ctx, *b, dl, dc, cur, tot, block_ids, s, &tune))) {
+        delete b;
+        return rc;
+    }
+    ctx->last = tune;
     // The whole search (distortion kernel, 8 greedy steps, final choice) as
     // one graph launch.  A call on the same frames and buffers as the last
     // one relaunches its graph; otherwise the launches are recorded on the
@@ -407,11 +521,13 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
     void *const ptrs[5] = {dl, dc, block_ids, cur, tot};
     const bool same = ctx->search_exec && ctx->search_key &&
                       memcmp(ctx->search_key, b, sizeof(SearchBatch)) == 0 &&
-                      memcmp(ctx->search_ptrs, ptrs, sizeof(ptrs)) == 0;
+                      memcmp(ctx->search_ptrs, ptrs, sizeof(ptrs)) == 0 &&
+                      ctx->search_key_tune.groups == tune.groups &&
+                      ctx->search_key_tune.ctas_per_sm == tune.ctas_per_sm;
     cudaError_t e = same ? cudaSuccess : cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess && !same) {
         const cudaError_t le = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids,
-                                             ctx->status, work, ctx->capture);
+                                             ctx->status, work, tune, ctx->capture);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(ctx->capture, &graph);
         if (e == cudaSuccess && le != cudaSuccess) e = le;
@@ -430,6 +546,7 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
             if (ctx->search_key) {
                 memcpy(ctx->search_key, b, sizeof(SearchBatch));
                 memcpy(ctx->search_ptrs, ptrs, sizeof(ptrs));
+                ctx->search_key_tune = tune;
             }
         } else if (ctx->search_key) {
             memset(ctx->search_key, 0, sizeof(SearchBatch));

@@ -91,13 +91,34 @@ constexpr int kChromaBoxRows = 36;
 __host__ __device__ constexpr int luma_box_cols(int bytes) { return bytes == 2 ? 80 : 96; }
 __host__ __device__ constexpr int chroma_box_cols(int bytes) { return bytes == 2 ? 48 : 64; }
 __host__ __device__ constexpr int box_lead(int bytes) { return bytes == 2 ? 8 : 16; }
+// Launch configuration of the distortion kernel.  `groups` (1, 2 or 4):
+// the 16 primary strengths of a filter block are split into this many work
+// units (64 / groups luma and as many chroma candidates each), which gives
+// small searches more units than there are SMs; `ctas_per_sm` (1 or 2):
+// persistent CTAs per SM.  Every configuration computes the same tables.
+struct SearchTune {
+    int groups;
+    int ctas_per_sm;
+};
+constexpr SearchTune kSearchTunes[] = {{1, 2}, {1, 1}, {2, 2}, {4, 2}};
+constexpr int kNumSearchTunes = sizeof(kSearchTunes) / sizeof(kSearchTunes[0]);
+// The configuration used without timing: enough work units to give every
+// persistent CTA a few of them.
+inline SearchTune default_search_tune(int total_blocks, int sms)
+{
+    if (total_blocks >= 4 * 2 * sms) return {1, 2};
+    if (2 * total_blocks >= 4 * 2 * sms) return {2, 2};
+    return {4, 2};
+}
+
 // Strength search: distortion tables, then the greedy preset search.
 // Device scratch: `cur` one u64 per block, `tot` 4096 u64 per frame (zeroed
 // by the call itself), `work` a zeroed counter pair (left zeroed).
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
                           long long *dist_chroma, unsigned long long *cur,
                           unsigned long long *tot, SearchResultDev *results,
-                          uint8_t *block_ids, int *status, unsigned *work, cudaStream_t s);
+                          uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
+                          cudaStream_t s);
 constexpr size_t search_scratch_bytes(int nframes, int nblocks)
 {
     return sizeof(unsigned long long) * ((size_t)nblocks + (size_t)nframes * 4096);

@@ -138,9 +138,15 @@ extern "C" int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
     // storage) and every launch leaves them at zero again.  The status word
     // only collects error bits and is not read here.
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CDEF_ERR_CUDA;
+    }
     cudaError_t e = launch_search(b, reinterpret_cast<long long *>(dist_luma),
                                   reinterpret_cast<long long *>(dist_chroma), cur, tot, results,
-                                  block_ids, status, work, s);
+                                  block_ids, status, work, default_search_tune(total, sms), s);
     SearchResultDev host[kMaxBatch];  // pageable stack copy: no pinned allocation
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host, results, sizeof(SearchResultDev) * n, cudaMemcpyDeviceToHost, s);

@@ -113,30 +113,43 @@ __device__ __forceinline__ uint32_t sec_sum(const uint32_t v[12], uint32_t X, co
     return n + n + f;   // weights 2, 1
 }
 
-// Sums 64 per-lane values across the warp; lane l ends with the totals of
-// entries 2l and 2l + 1 in a[0], a[1].
-__device__ __forceinline__ void butterfly64(uint32_t a[64], int lane)
+// Sums N (16, 32 or 64) per-lane values across the warp.  Lane l ends with
+// the totals of entries 2l, 2l + 1 in a[0], a[1] (N = 64), of entry l in
+// a[0] (N = 32), or of entry l / 2 in a[0] (N = 16).
+template <int N>
+__device__ __forceinline__ void butterfly(uint32_t (&a)[N], int lane)
 {
 #pragma unroll
-    for (int o = 16, n = 64; o >= 1; o >>= 1, n >>= 1) {
-        const bool upper = lane & o;
-        const int half = n >> 1;
+    for (int o = 16, n = N; o >= 1; o >>= 1, n >>= 1) {
+        if (n > 1) {
+            const bool upper = lane & o;
+            const int half = n >> 1;
 #pragma unroll
-        for (int i = 0; i < 32; i++) {
-            if (i < half) {
-                const uint32_t give = upper ? a[i] : a[i + half];
-                const uint32_t keep = upper ? a[i + half] : a[i];
-                a[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+            for (int i = 0; i < N / 2; i++) {
+                if (i < half) {
+                    const uint32_t give = upper ? a[i] : a[i + half];
+                    const uint32_t keep = upper ? a[i + half] : a[i];
+                    a[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+                }
             }
+        } else {
+            a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
         }
     }
 }
 
-template <typename T>
-__device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global,
+// One work unit: filter block (fby, fbx) of frame F, primary strengths
+// grp * 16 / kG .. (grp + 1) * 16 / kG - 1 with all four secondary
+// strengths, for both plane groups (64 / kG luma and 64 / kG chroma
+// candidates).
+template <typename T, int kG>
+__device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global, int grp,
                            SearchSmem &sm, const RawTiles &raw, long long *dist_luma,
                            long long *dist_chroma)
 {
+    constexpr int kPP = 16 / kG;           // primary strengths per unit
+    constexpr int kN = 4 * kPP;            // candidates per plane group
+    const int p0 = kG == 1 ? 0 : grp * kPP;
     const int sh8 = F.bitdepth - 8;
     const int W = F.w, H = F.h, CW = F.w >> 1, CH = F.h >> 1;
     const int ly0 = fby * 64, lx0 = fbx * 64, cy0 = fby * 32, cx0 = fbx * 32;
@@ -231,9 +244,9 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         const uint8_t *sa = luma ? F.src[0] : F.src[1];
         const int64_t spa = luma ? F.src_pitch[0] : F.src_pitch[1];
 
-        uint32_t acc[64], sse0 = 0;
+        uint32_t acc[kN], sse0 = 0;
 #pragma unroll
-        for (int q = 0; q < 64; q++) acc[q] = 0;
+        for (int q = 0; q < kN; q++) acc[q] = 0;
         if (inside) {
 #pragma unroll 1
             for (int i = 0; i < rows; i++) {
@@ -277,7 +290,8 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 }
                 const uint32_t C = 4096u * kLanes - 24u * X;
 #pragma unroll
-                for (int p = 0; p < 16; p++) {
+                for (int pp = 0; pp < kPP; pp++) {
+                    const int p = p0 + pp;
                     const SetC sc = ps[p];
                     const uint32_t T0 = pri_sum(v, X, sc, (bits >> p) & 1) + C;
                     const bool rz = (raised >> p) & 1;
@@ -294,22 +308,28 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                         // clip cannot bind: it is applied without a test.
                         if (s > 0) rb = __vminu2(__vmaxu2(rb, rlo), rhi);
                         const uint32_t a = sadd16(rb, two_xs);           // 2 (x - s) + r
-                        acc[p * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)__byte_perm(rb, 0, 0x0020),
-                                                             (int)acc[p * 4 + s]);
+                        acc[pp * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)__byte_perm(rb, 0, 0x0020),
+                                                              (int)acc[pp * 4 + s]);
                     }
                 }
             }
         }
-        butterfly64(acc, lane);
+        butterfly<kN>(acc, lane);
         // the warp totals of r (2 (x - s) + r) are signed and fit 32 bits
-        atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
-        atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
+        if (kN == 64) {
+            atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
+            atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
+        } else if (kN == 32) {
+            atomicAdd(&sm.acc[lane], (unsigned long long)(long long)(int)acc[0]);
+        } else if (!(lane & 1)) {
+            atomicAdd(&sm.acc[lane >> 1], (unsigned long long)(long long)(int)acc[0]);
+        }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) sse0 += __shfl_xor_sync(0xffffffffu, sse0, o);
         if (lane == 0) atomicAdd(&sm.base[task], (unsigned long long)sse0);
         __syncthreads();
-        if (tid < 64) {
-            long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64;
+        if (tid < kN) {
+            long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
             out[tid] = (long long)(sm.acc[tid] + sm.base[task]);
             sm.acc[tid] = 0;
         }
@@ -338,6 +358,8 @@ __device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTil
 }
 
 // Persistent distortion kernel (same work-counter scheme as the filter).
+// Work unit u is filter block u / kG, primary-strength group u % kG.
+template <int kG>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
 dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, long long *dist_chroma,
             int *status, unsigned *work)
@@ -345,7 +367,7 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
     extern __shared__ __align__(128) uint8_t smem_bytes[];
     SearchSmem &sm = *reinterpret_cast<SearchSmem *>(smem_bytes);
     const int tid = threadIdx.x;
-    const int total = batch.total_blocks;
+    const int total = batch.total_blocks * kG;
 
     if (smem_u32(smem_bytes) & 127) {
         if (tid == 0) atomicOr(status, kStatusMisaligned);
@@ -355,7 +377,7 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             mbar_init(&sm.bar[1], 1);
             const int b = (int)atomicAdd(&work[0], 1u);
             sm.blk[0] = b;
-            if (b < total) sissue(batch, b, sm.raw[0], &sm.bar[0]);
+            if (b < total) sissue(batch, b / kG, sm.raw[0], &sm.bar[0]);
         }
         if (tid < 192) {
             const int pl = tid / 96, d = (tid / 12) & 7, t = tid % 12;
@@ -371,7 +393,7 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             if (tid == 0) {
                 const int nb = (int)atomicAdd(&work[0], 1u);
                 sm.blk[buf ^ 1] = nb;
-                if (nb < total) sissue(batch, nb, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
+                if (nb < total) sissue(batch, nb / kG, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
             }
             const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, kWaitCycles);
             if (__syncthreads_or(!arrived)) {
@@ -382,12 +404,15 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
                 }
                 break;
             }
-            const SBlockRef r = slocate(batch, blk);
+            const int fb = blk / kG, grp = blk - fb * kG;
+            const SBlockRef r = slocate(batch, fb);
             const SearchFrameDev &F = batch.f[r.fi];
             if (F.bitdepth == 8)
-                dist_block<uint8_t>(F, r.fby, r.fbx, blk, sm, sm.raw[buf], dist_luma, dist_chroma);
+                dist_block<uint8_t, kG>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf], dist_luma,
+                                        dist_chroma);
             else
-                dist_block<uint16_t>(F, r.fby, r.fbx, blk, sm, sm.raw[buf], dist_luma, dist_chroma);
+                dist_block<uint16_t, kG>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf], dist_luma,
+                                         dist_chroma);
             __syncthreads();
         }
     }
@@ -558,33 +583,53 @@ __global__ void greedy_final(const __grid_constant__ SearchBatch batch, const lo
 
 constexpr size_t kSmemBytes = sizeof(SearchSmem);
 
-int dist_grid(int total)
+// Persistent grid: `per_sm` CTAs on every SM (at most what fits), never more
+// CTAs than work units.
+template <int kG>
+int dist_grid(int units, int per_sm)
 {
-    static int cached_dev = -1, cached_ctas = 0;
+    static int cached_dev = -1, cached_sms = 0, cached_occ = 1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != cached_dev) {
-        cudaFuncSetAttribute(dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        cudaFuncSetAttribute(dist_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(dist_kernel<kG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
+        cudaFuncSetAttribute(dist_kernel<kG>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dist_kernel, kThreads, kSmemBytes);
-        cached_ctas = sms * (occ > 0 ? occ : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dist_kernel<kG>, kThreads, kSmemBytes);
+        cached_sms = sms;
+        cached_occ = occ > 0 ? occ : 1;
         cached_dev = dev;
     }
-    return total < cached_ctas ? total : cached_ctas;
+    const int ctas = cached_sms * (per_sm < cached_occ ? per_sm : cached_occ);
+    return units < ctas ? units : ctas;
+}
+
+template <int kG>
+cudaError_t launch_dist(const SearchBatch &b, long long *dl, long long *dc, int *status,
+                        unsigned *work, int per_sm, cudaStream_t s)
+{
+    const int units = b.total_blocks * kG;
+    dist_kernel<kG><<<dist_grid<kG>(units, per_sm), kThreads, kSmemBytes, s>>>(b, dl, dc, status,
+                                                                              work);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long *dist_chroma,
                           unsigned long long *cur, unsigned long long *tot, SearchResultDev *results,
-                          uint8_t *block_ids, int *status, unsigned *work, cudaStream_t s)
+                          uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
+                          cudaStream_t s)
 {
-    dist_kernel<<<dist_grid(b.total_blocks), kThreads, kSmemBytes, s>>>(b, dist_luma, dist_chroma,
-                                                                        status, work);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    switch (tune.groups) {
+    case 2: e = launch_dist<2>(b, dist_luma, dist_chroma, status, work, tune.ctas_per_sm, s); break;
+    case 4: e = launch_dist<4>(b, dist_luma, dist_chroma, status, work, tune.ctas_per_sm, s); break;
+    default: e = launch_dist<1>(b, dist_luma, dist_chroma, status, work, tune.ctas_per_sm, s); break;
+    }
     if (e != cudaSuccess) return e;
     greedy_init<<<64, 256, 0, s>>>(b, cur, tot);
     int chunks = 0;

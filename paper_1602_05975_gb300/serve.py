@@ -5,7 +5,9 @@ with its own per-64x64 parameters (section 4: one primary/secondary strength
 pair per plane group and a damping value per filter block).  The server
 
 * admits queued requests in arrival order while their device buffers fit an
-  HBM budget (input frame + parameters + output frame per request);
+  HBM budget (input frame + parameters + output frame per request) and the
+  next batch has room (requests are not given buffers earlier than the
+  batch that will carry them needs them);
 * launches every admitted request that is not yet on the device as one
   batch through the batched filter entry point (``cdef_filter_frames``: one
   launch for frames of mixed sizes and bit depths), as soon as fewer than
@@ -53,9 +55,11 @@ def validate_params(params: np.ndarray, width: int, height: int) -> Optional[str
 
 @dataclasses.dataclass(eq=False)
 class Request:
-    """One frame to filter.  `frame` and `params` are backend inputs (for
-    :class:`CudaBackend`: a pinned host frame and a (rows, cols, 8) uint8
-    array); `arrival` is seconds from the start of the run."""
+    """One frame to filter.  `frame` is the backend's input (for
+    :class:`CudaBackend`: a pinned host buffer in the packed frame layout of
+    ``cdef.packed_layout``), `params` the (rows, cols, 8) uint8 parameters
+    (`params_host`: optionally the same bytes in pinned host memory), and
+    `arrival` seconds from the start of the run."""
     rid: int
     width: int
     height: int
@@ -72,7 +76,9 @@ class Request:
     t_done: float = math.nan
     need: int = 0                  # device bytes held while admitted
     slot: object = None            # backend buffers
-    out: object = None             # backend output (CudaBackend: pinned host flat buffer)
+    out: object = None             # backend output (CudaBackend: (flat, Frame, _) in pinned
+                                   # host memory, valid while on_done runs)
+    params_host: object = None
 
     @property
     def latency(self) -> float:
@@ -106,9 +112,12 @@ class Backend:
 class Server:
     def __init__(self, backend: Backend, budget_bytes: int, max_batch: int = 48,
                  max_inflight: int = 2, clock: Callable[[], float] = time.perf_counter,
-                 on_done: Optional[Callable[[Request], None]] = None):
+                 on_done: Optional[Callable[[Request], None]] = None,
+                 max_ready: Optional[int] = None):
         if max_batch < 1 or max_inflight < 1:
             raise ValueError("max_batch and max_inflight must be >= 1")
+        # admitted requests waiting for a launch: by default one batch
+        self.max_ready = max_batch if max_ready is None else max_ready
         self.backend = backend
         self.budget = int(budget_bytes)
         self.max_batch = max_batch
@@ -180,7 +189,8 @@ class Server:
                     self._finish(r, "failed", st, now)
         self.inflight = still
         # 2. admission, first come first served, under the budget
-        while self.queue and self.in_use + self.queue[0].need <= self.budget:
+        while (self.queue and len(self.ready) < self.max_ready
+               and self.in_use + self.queue[0].need <= self.budget):
             r = self.queue.popleft()
             self.backend.reserve(r)
             self.in_use += r.need
@@ -359,9 +369,14 @@ class CudaBackend(Backend):
 
     def launch(self, reqs: list):
         torch = self.torch
+        for r in reqs:
+            if r.params_host is None:
+                r.params_host = torch.from_numpy(
+                    np.ascontiguousarray(r.params, dtype=np.uint8).reshape(-1)).pin_memory()
         with torch.cuda.stream(self.up):
             for r in reqs:
-                r.slot["flat_in"].copy_(r.frame, non_blocking=True)
+                r.slot["flat_in"][:r.frame.numel()].copy_(r.frame, non_blocking=True)
+                r.slot["params"].copy_(r.params_host, non_blocking=True)
         ev_up = torch.cuda.Event()
         ev_up.record(self.up)
         self.comp.wait_event(ev_up)
@@ -392,18 +407,22 @@ class CudaBackend(Backend):
         return ["ok"] * n if st == 0 else [f"device status {st}"] * n
 
 
-def pack_request_input(cdef, frame_planes, params: np.ndarray, bitdepth: int):
-    """One pinned host buffer holding a frame's planes (uint16 numpy y, u, v)
-    and its parameters in the layout :class:`CudaBackend` copies."""
-    h, w = frame_planes[0].shape
-    n_params = params.size
-    flat, f, prm = cdef.alloc_packed(w, h, bitdepth, device="cpu", extra_bytes=n_params)
+def pack_frame(cdef, frame_planes, bitdepth: int):
+    """A frame's planes (uint16 numpy y, u, v) in one pinned host buffer in
+    the packed layout :class:`CudaBackend` copies."""
     import torch
+    h, w = frame_planes[0].shape
+    flat, f, _ = cdef.alloc_packed(w, h, bitdepth, device="cpu")
+    flat.zero_()
     for t, a in zip(f.planes(), frame_planes):
         a = np.asarray(a)
         if bitdepth == 8:
             t[:, :a.shape[1]] = torch.from_numpy(a.astype(np.uint8))
         else:
             t[:, :a.shape[1]] = torch.from_numpy(a.astype(np.uint16).view(np.int16))
-    prm.copy_(torch.from_numpy(np.ascontiguousarray(params, dtype=np.uint8).reshape(-1)))
     return flat.pin_memory()
+
+
+def unpack_frame(out) -> tuple:
+    """Copies of the visible planes of a CudaBackend output as uint16 arrays."""
+    return tuple(np.array(p, dtype=np.uint16) for p in out[1].to_numpy())

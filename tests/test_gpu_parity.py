@@ -259,3 +259,45 @@ def test_search_scratch_tables(cdef, ctx, ref):
     o = ref.search_strengths(f.rec, f.src, 8, 5, 256)
     assert res["cost"] == o["cost"] and res["npresets"] == o["npresets"]
     assert np.array_equal(ids.cpu().numpy(), o["block_ids"])
+
+
+@pytest.mark.parametrize("groups,ctas", [(1, 2), (1, 1), (2, 2), (4, 2), (0, 0)])
+def test_search_every_launch_configuration(cdef, ctx, ref, groups, ctas):
+    """Every configuration the autotuner may pick (and the autotuner itself)
+    gives the oracle's tables, presets, ids and J, on a mixed 8/10-bit batch
+    whose frames have ragged edges."""
+    from paper_1602_05975_gb300 import synth
+    specs = [(200, 136, 8, 16, 600), (136, 72, 10, 32, 601), (72, 264, 8, 64, 602)]
+    frames = [synth.make_frame(w, h, bd, q, seed=s) for w, h, bd, q, s in specs]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    ctx.set_tuning(groups, ctas)
+    try:
+        res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames],
+                                         [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames],
+                                         [5, 4, 6], [256, 1024, 4096], ids, dl, dc)
+        used = ctx.tuning()
+    finally:
+        ctx.set_tuning(0, 0)
+    if groups:
+        assert used == (groups, ctas)
+    else:
+        assert used in [(1, 2), (1, 1), (2, 2), (4, 2)]
+    o0 = 0
+    for f, r, d, lam in zip(frames, res, [5, 4, 6], [256, 1024, 4096]):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths(f.rec, f.src, f.bitdepth, d, lam)
+        assert np.array_equal(dl[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_luma"])
+        assert np.array_equal(dc[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_chroma"])
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        assert r["cost"] == o["cost"] and r["npresets"] == o["npresets"]
+        o0 += b
+
+
+def test_tuning_rejects_unknown_configurations(cdef, ctx):
+    for g, c in [(3, 1), (8, 1), (1, 3), (-1, 0)]:
+        with pytest.raises(cdef.CdefError):
+            ctx.set_tuning(g, c)
+    ctx.set_tuning(0, 0)

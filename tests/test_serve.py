@@ -263,3 +263,17 @@ def test_poisson_arrivals_rate():
     t = serve.poisson_arrivals(20000, rate=1000.0, seed=1)
     assert np.all(np.diff(t) > 0)
     assert abs(20000 / t[-1] - 1000.0) < 30.0
+
+
+def test_admission_window_is_one_batch():
+    fb, clk = FakeBackend(latency=50), Clock()
+    s = serve.Server(fb, budget_bytes=1 << 40, max_batch=4, max_inflight=1, clock=clk)
+    for i in range(20):
+        s.submit(req(i))
+    s.step()
+    s.step()
+    # one batch on the device, at most one more admitted, the rest queued
+    assert len(s.inflight) == 1 and len(s.ready) == 4 and len(s.queue) == 12
+    assert s.in_use == 8 * req(0).width * req(0).height * 3
+    drain(s, clk)
+    assert len(s.finished) == 20
