@@ -210,6 +210,22 @@ int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *tuning);
  * the first search).  Host only. */
 int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
 
+/* Overlap of consecutive filter calls on one stream.  No paper counterpart.
+ * Every cdef_filter_frame / cdef_filter_frames launch lets the next kernel
+ * on its stream be scheduled before it ends (programmatic dependent
+ * launch).  By default (enable = 0) a filter launch still waits, before it
+ * reads or writes any memory, until the previous kernel on the stream has
+ * finished and its writes are visible: ordinary stream order.  With
+ * enable = 1 the wait is dropped: the filter calls of a run of consecutive
+ * filter calls on one stream (no other operation between them) may execute
+ * concurrently, a frame's filtering running alongside the previous frame's
+ * last CTAs.  The caller then promises that no call of such a run writes
+ * memory that another call of the run reads or writes, and that the first
+ * call of the run does not depend on a kernel enqueued just before it
+ * (independent frames of a decoded sequence, each with its own output).
+ * Host only; applies to later calls. */
+int cdef_ctx_set_overlap(cdef_ctx *ctx, int enable);
+
 /* The strength search without any memory allocation.  The paper has no
  * counterpart: this is a deployment variant of cdef_search_strengths.
  *

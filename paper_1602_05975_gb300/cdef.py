@@ -81,13 +81,14 @@ def load():
                                         C.POINTER(Preset), C.POINTER(i32), vp,
                                         C.POINTER(i64), vp]
     L.cdef_ctx_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.cdef_ctx_set_overlap.argtypes = [vp, C.c_int]
     L.cdef_ctx_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.cdef_strerror.argtypes = [C.c_int]
     L.cdef_strerror.restype = C.c_char_p
     L.cdef_version.restype = C.c_char_p
     for name in ("cdef_ctx_create", "cdef_ctx_destroy", "cdef_ctx_status", "cdef_find_dir",
                  "cdef_filter_frame", "cdef_filter_frames", "cdef_search_strengths",
-                 "cdef_ctx_set_tuning", "cdef_ctx_get_tuning"):
+                 "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -248,6 +249,12 @@ class Context:
 
     def status(self, clear=True):
         return self._lib.cdef_ctx_status(self.handle, int(clear))
+
+    def set_overlap(self, enable: bool):
+        """Declare consecutive filter calls on a stream independent (see
+        cdef_ctx_set_overlap): they may then run concurrently."""
+        _check(self._lib.cdef_ctx_set_overlap(self.handle, int(bool(enable))),
+               "cdef_ctx_set_overlap")
 
     def set_tuning(self, search_groups: int = 0, search_ctas_per_sm: int = 0):
         """Fix the strength search's launch configuration (0 = autotune)."""

@@ -33,6 +33,7 @@ struct cdef_ctx {
     SearchTune search_key_tune;   // and its launch configuration
     SearchTune forced;            // fields > 0 fixed by cdef_ctx_set_tuning
     SearchTune last;              // configuration of the last search
+    bool overlap;                 // filter calls on a stream declared independent
     std::unordered_map<uint64_t, SearchTune> *tuned;  // autotuned, per batch shape
 };
 
@@ -275,6 +276,13 @@ int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *t)
     return CDEF_OK;
 }
 
+int cdef_ctx_set_overlap(cdef_ctx *ctx, int enable)
+{
+    if (!ctx) return CDEF_ERR_ARG;
+    ctx->overlap = enable != 0;
+    return CDEF_OK;
+}
+
 int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last)
 {
     if (!ctx || !last) return CDEF_ERR_ARG;
@@ -330,7 +338,8 @@ int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params 
     b.total_blocks = fb_count(in);
     if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0))) return rc;
     unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
-    return cuda_status(launch_filter_single(b, ctx->status, work, static_cast<cudaStream_t>(cuda_stream)));
+    return cuda_status(launch_filter_single(b, ctx->status, work, ctx->overlap,
+                                            static_cast<cudaStream_t>(cuda_stream)));
 }
 
 int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
@@ -364,7 +373,8 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
     }
     bp->total_blocks = start;
     unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
-    const int rc = cuda_status(launch_filter_batch(*bp, ctx->status, work, static_cast<cudaStream_t>(cuda_stream)));
+    const int rc = cuda_status(launch_filter_batch(*bp, ctx->status, work, ctx->overlap,
+                                                   static_cast<cudaStream_t>(cuda_stream)));
     delete bp;
     return rc;
 }

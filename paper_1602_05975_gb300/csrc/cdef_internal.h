@@ -76,11 +76,15 @@ cudaError_t launch_find_dir(const uint8_t *luma, int64_t pitch, int w, int h,
                             int bitdepth, uint8_t *dir, int32_t *var,
                             cudaStream_t s);
 // `work` is a pair of zeroed device counters owned by this launch until it
-// completes (the kernel leaves them zeroed again).
+// completes (the kernel leaves them zeroed again).  Launches are
+// programmatic dependents of the previous grid on the stream; with
+// `overlap` false each waits for that grid's completion before touching
+// memory, with `overlap` true (the caller's promise that consecutive calls
+// are independent) it runs alongside the previous grid's last CTAs.
 cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status, unsigned *work,
-                                 cudaStream_t s);
+                                 bool overlap, cudaStream_t s);
 cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *status,
-                                unsigned *work, cudaStream_t s);
+                                unsigned *work, bool overlap, cudaStream_t s);
 constexpr int kWorkSlots = 1024;  // counter pairs per context (launches in flight at once)
 
 // Filter tile geometry shared by the host (tensor-map boxes) and the kernel.

@@ -74,8 +74,11 @@ __device__ __forceinline__ uint32_t filter_word(uint32_t X, uint32_t v[12], cons
     uint32_t P = 12u * X, Q = 12u * X, mn = X, mx = X;
     if (any_p) {
         const uint32_t xk1 = X + bc.p.kb, xk2 = bc.p.kb - X;
-        const uint32_t n = tap(v[0], X, xk1, xk2, bc.p) + tap(v[1], X, xk1, xk2, bc.p);
-        const uint32_t f = tap(v[2], X, xk1, xk2, bc.p) + tap(v[3], X, xk1, xk2, bc.p);
+        const uint32_t xp = X + bc.p.posb, xm = sadd16(X, bc.pneg);
+        const uint32_t n = tap_folded(v[0], xk1, xk2, xp, xm, bc.p) +
+                           tap_folded(v[1], xk1, xk2, xp, xm, bc.p);
+        const uint32_t f = tap_folded(v[2], xk1, xk2, xp, xm, bc.p) +
+                           tap_folded(v[3], xk1, xk2, xp, xm, bc.p);
         if (bc.flags & 4) {
             const uint32_t t = n + f;
             P = t + t + t;                 // weights 3, 3
@@ -86,10 +89,12 @@ __device__ __forceinline__ uint32_t filter_word(uint32_t X, uint32_t v[12], cons
     }
     if (any_s) {
         const uint32_t xk1 = X + bc.s.kb, xk2 = bc.s.kb - X;
-        const uint32_t n = tap(v[4], X, xk1, xk2, bc.s) + tap(v[5], X, xk1, xk2, bc.s) +
-                           tap(v[6], X, xk1, xk2, bc.s) + tap(v[7], X, xk1, xk2, bc.s);
-        const uint32_t f = tap(v[8], X, xk1, xk2, bc.s) + tap(v[9], X, xk1, xk2, bc.s) +
-                           tap(v[10], X, xk1, xk2, bc.s) + tap(v[11], X, xk1, xk2, bc.s);
+        const uint32_t xp = X + bc.s.posb, xm = sadd16(X, bc.sneg);
+        uint32_t n = 0, f = 0;
+#pragma unroll
+        for (int k = 4; k < 8; k++) n += tap_folded(v[k], xk1, xk2, xp, xm, bc.s);
+#pragma unroll
+        for (int k = 8; k < 12; k++) f += tap_folded(v[k], xk1, xk2, xp, xm, bc.s);
         Q = n + n + f;                     // weights 2, 1
     }
     if (any_clip) {
@@ -314,8 +319,16 @@ __device__ __forceinline__ void issue_loads(const FilterBatch<MAXF> &batch, int 
 // counter slot is ready for its next launch.
 template <int MAXF>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
-filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsigned *work)
+filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsigned *work,
+              int dep_wait)
 {
+    // The next launch on the stream may be scheduled as soon as every CTA of
+    // this one is running (programmatic dependent launch); it fills the SMs
+    // this grid's last CTAs leave idle.  Unless the caller declared
+    // consecutive calls independent, each launch first waits here until the
+    // previous grid on the stream has finished and its writes are visible.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (dep_wait) asm volatile("griddepcontrol.wait;" ::: "memory");
     // A direct cast keeps every access in the shared state space (LDS/STS).
     extern __shared__ __align__(128) uint8_t smem_bytes[];
     FilterSmem &sm = *reinterpret_cast<FilterSmem *>(smem_bytes);
@@ -401,22 +414,36 @@ int persistent_grid(int total)
     return total < cached_ctas ? total : cached_ctas;
 }
 
+template <int MAXF>
+cudaError_t launch_pdl(const FilterBatch<MAXF> &b, int *status, unsigned *work, bool overlap,
+                       cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(persistent_grid<MAXF>(b.total_blocks));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int dep_wait = overlap ? 0 : 1;
+    return cudaLaunchKernelEx(&cfg, filter_kernel<MAXF>, b, status, work, dep_wait);
+}
+
 }  // namespace
 
 cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status, unsigned *work,
-                                 cudaStream_t s)
+                                 bool overlap, cudaStream_t s)
 {
-    const int grid = persistent_grid<1>(b.total_blocks);
-    filter_kernel<1><<<grid, kThreads, kSmemBytes, s>>>(b, status, work);
-    return cudaGetLastError();
+    return launch_pdl<1>(b, status, work, overlap, s);
 }
 
 cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *status, unsigned *work,
-                                cudaStream_t s)
+                                bool overlap, cudaStream_t s)
 {
-    const int grid = persistent_grid<kMaxFilterBatch>(b.total_blocks);
-    filter_kernel<kMaxFilterBatch><<<grid, kThreads, kSmemBytes, s>>>(b, status, work);
-    return cudaGetLastError();
+    return launch_pdl<kMaxFilterBatch>(b, status, work, overlap, s);
 }
 
 }  // namespace cdefgb

@@ -86,13 +86,6 @@ __device__ __forceinline__ uint32_t add_sq(uint32_t acc, uint32_t y, uint32_t s)
     return acc + lo * lo + hi * hi;
 }
 
-// Per 16-bit lane a + b, the lanes read as signed and independent (no carry
-// between them); every sum formed with it here stays within int16.
-__device__ __forceinline__ uint32_t sadd16(uint32_t a, uint32_t b)
-{
-    return __viaddmax_s16x2(a, b, 0x80008000u);
-}
-
 // Weighted sum of the 4 primary clamped values for one set.
 __device__ __forceinline__ uint32_t pri_sum(const uint32_t v[12], uint32_t X, const SetC &s, bool odd)
 {

@@ -45,8 +45,23 @@ struct SetC {
 struct alignas(16) BlockC {
     SetC p, s;
     uint32_t flags;  // bit0 primary on, bit1 secondary on, bit2 odd primary strength
-    uint32_t pad[3];
+    uint32_t pneg;   // -posb of p per 16-bit lane (two's complement)
+    uint32_t sneg;   // the same for s
+    uint32_t pad;
 };
+
+// Per 16-bit lane a + b, the lanes read as signed and independent (no carry
+// between them); every sum formed with it here stays within int16.
+__device__ __forceinline__ uint32_t sadd16(uint32_t a, uint32_t b)
+{
+    return __viaddmax_s16x2(a, b, 0x80008000u);
+}
+
+// -v in each 16-bit lane (lanes 1..0xffff).
+__host__ __device__ constexpr uint32_t lane_neg(uint32_t v)
+{
+    return ((0x10000u - (v & 0xffffu)) & 0xffffu) | (((0x10000u - (v >> 16)) & 0xffffu) << 16);
+}
 
 // Raw TMA destinations, double-buffered: the next block's tiles land while
 // the current block is filtered.
@@ -87,6 +102,9 @@ __device__ __forceinline__ BlockC make_block_consts(const Eff &e)
     b.p = make_set(e.pri, e.psh);
     b.s = make_set(e.sec, e.ssh);
     b.flags = (e.pri ? 1u : 0u) | (e.sec ? 2u : 0u) | (e.w0 == 3 ? 4u : 0u);
+    b.pneg = lane_neg(b.p.posb);
+    b.sneg = lane_neg(b.s.posb);
+    b.pad = 0;
     return b;
 }
 
@@ -103,6 +121,18 @@ __device__ __forceinline__ uint32_t tap(uint32_t p, uint32_t X, uint32_t xk1, ui
     const uint32_t lim = m - s.posb;
     const uint32_t lo = X - lim;
     return __viaddmin_u16x2(lim, X, __vmaxu2(p, lo));   // min(x + lim, max(p, x - lim))
+}
+
+// The same tap with the limit's offset folded into per-word constants:
+// xp = x + posb and xm = x - posb (per lane), so that x - lim = xp - L and
+// x + lim = L + xm with L the shifted value.  One operation fewer per tap.
+__device__ __forceinline__ uint32_t tap_folded(uint32_t p, uint32_t xk1, uint32_t xk2, uint32_t xp,
+                                               uint32_t xm, const SetC &s)
+{
+    const uint32_t t1 = xk1 - p;
+    uint32_t m = __vmaxu2(__viaddmin_u16x2(p, xk2, t1), kB1 * kLanes);
+    m = __umulhi(m, s.mul) & s.mask;
+    return __viaddmin_u16x2(m, xm, __vmaxu2(p, xp - m));   // min(x + lim, max(p, x - lim))
 }
 
 // Lanes of p holding the out-of-frame marker 0 take the centre's value.
@@ -153,37 +183,59 @@ __device__ __forceinline__ bool valid_strengths(int pri, int sec)
 
 // Direction search: line sums of directions Q and Q + 4 for block `blk`
 // (Algorithm 1), from the biased luma pairs; costs into `cost`.
+//
+// The two samples of a pair word lie on the same line of direction d
+// (d = 1, 2, 3) or on neighbouring lines k and k + 1 (d = 0, 5, 6, 7) or k and
+// k - 1 (d = 4), with k the low sample's line.  So each word is added whole
+// into a packed accumulator indexed by k, and the line sums are recovered at
+// the end: line k = low lane of acc[k] + high lane of acc[k - 1], acc[k + 1]
+// or acc[k].  A lane holds at most 8 samples below 2^12 (no carry).  At bit
+// depths above 8 each sample is first shifted per lane: (x + 128) >> sh8 =
+// (x >> sh8) + (128 >> sh8) exactly.
+__host__ __device__ constexpr int hi_step(int d) { return d == 4 ? -1 : (d >= 1 && d <= 3) ? 0 : 1; }
+
+template <int D>
+__device__ __forceinline__ int dir_cost_from(const uint32_t (&acc)[15], int bias)
+{
+    constexpr LineWeights LW = make_line_weights();
+    constexpr int st = hi_step(D);
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < 15; k++) {
+        if (!LW.w[D][k]) continue;
+        int raw = (int)(acc[k] & 0xffffu);
+        if (st == 0) raw += (int)(acc[k] >> 16);
+        else if (k - st >= 0 && k - st < 15) raw += (int)(acc[k - st] >> 16);
+        const int part = raw - (840 / LW.w[D][k]) * bias;
+        s += part * part * LW.w[D][k];
+    }
+    return s;
+}
+
 template <int Q>
 __device__ __forceinline__ void dir_costs(const uint32_t *le, int blk, int sh8, int (*cost)[8])
 {
-    constexpr LineWeights LW = make_line_weights();
-    int pa[15], pb[15];
+    uint32_t pa[15], pb[15];
 #pragma unroll
     for (int k = 0; k < 15; k++) pa[k] = pb[k] = 0;
     const uint4 *b = reinterpret_cast<const uint4 *>(le + (2 + (blk >> 3) * 8) * kLumaPitch + 4 +
                                                      (blk & 7) * 4);
+    const uint32_t mask = (0xffffu >> sh8) * kLanes;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const uint4 q = b[i * (kLumaPitch / 4)];
         const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int m = 0; m < 4; m++) {
-            const int x0 = (int)(((w4[m] & 0xffffu) - kBias) >> sh8) - 128;
-            const int x1 = (int)(((w4[m] >> 16) - kBias) >> sh8) - 128;
-            pa[line_of(Q, i, 2 * m)] += x0;
-            pa[line_of(Q, i, 2 * m + 1)] += x1;
-            pb[line_of(Q + 4, i, 2 * m)] += x0;
-            pb[line_of(Q + 4, i, 2 * m + 1)] += x1;
+            const uint32_t w = sh8 ? (w4[m] >> sh8) & mask : w4[m];
+            pa[line_of(Q, i, 2 * m)] += w;
+            pb[line_of(Q + 4, i, 2 * m)] += w;
         }
     }
-    int sa = 0, sb = 0;
-#pragma unroll
-    for (int k = 0; k < 15; k++) {
-        if (LW.w[Q][k]) sa += pa[k] * pa[k] * LW.w[Q][k];
-        if (LW.w[Q + 4][k]) sb += pb[k] * pb[k] * LW.w[Q + 4][k];
-    }
-    cost[blk][Q] = sa;
-    cost[blk][Q + 4] = sb;
+    // each sample carries (x >> sh8) + (128 >> sh8); x' = (x >> sh8) - 128
+    const int bias = (int)(kBias >> sh8) + 128;
+    cost[blk][Q] = dir_cost_from<Q>(pa, bias);
+    cost[blk][Q + 4] = dir_cost_from<Q + 4>(pb, bias);
 }
 
 // Biased word of two samples; each lane is 0 where its sample is outside

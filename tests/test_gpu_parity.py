@@ -301,3 +301,104 @@ def test_tuning_rejects_unknown_configurations(cdef, ctx):
         with pytest.raises(cdef.CdefError):
             ctx.set_tuning(g, c)
     ctx.set_tuning(0, 0)
+
+
+# --------------------------------------------------------------- full-size frames
+@pytest.mark.parametrize("w,h,bd,seed", [(3840, 2160, 10, 2000), (1920, 1080, 8, 1000)])
+def test_benchmark_frames_full(cdef, ctx, ref, w, h, bd, seed):
+    """The benchmark's own frames and launch (fused direction search), every
+    output sample and the standalone direction maps against the oracle."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(w, h, bd, None, seed)
+    _assert_frames_equal(_gpu_filter(cdef, ctx, f.rec, bd, f.params),
+                         ref.filter_frame(*f.rec, bd, f.params))
+    inp = cdef.frame_from_numpy(f.rec, bd)
+    dirs = torch.zeros((h // 8) * (w // 8), dtype=torch.uint8, device="cuda")
+    var = torch.zeros_like(dirs, dtype=torch.int32)
+    cdef.cdef_find_dir(ctx, inp.y, w, h, bd, dirs, var)
+    torch.cuda.synchronize()
+    ed, ev = ref.find_dir(f.rec[0], bd)
+    assert np.array_equal(dirs.cpu().numpy().reshape(ed.shape), ed)
+    assert np.array_equal(var.cpu().numpy().reshape(ev.shape), ev)
+
+
+@pytest.mark.parametrize("bd", [8, 10])
+def test_largest_frame_sampled(cdef, ctx, ref, bd):
+    """7680x4320 (8K): the whole frame on the GPU; sampled 64x64 blocks
+    (corners, edges, interior) against the oracle run on the 3x3-block
+    neighbourhood with the full frame's direction maps.  A block's output
+    depends only on its pixels, a 2-pixel halo, its parameters and its 8x8
+    directions, so the centre block of such a crop is exact."""
+    from paper_1602_05975_gb300 import synth
+    w, h = 7680, 4320
+    rng = np.random.default_rng(bd)
+    planes = synth.random_frame_planes(rng, w, h, bd)
+    # smooth the random planes a little so that directions and strengths vary
+    planes = tuple(((p.astype(np.int64) + np.roll(p, 1, 0) + np.roll(p, 1, 1)) // 3).astype(np.uint16)
+                   for p in planes)
+    params = synth.random_params(rng, w, h)
+    got = _gpu_filter(cdef, ctx, planes, bd, params)
+    dirs, var = ref.find_dir(planes[0], bd)
+    rows, cols = params.shape[:2]
+    picks = [(0, 0), (0, cols - 1), (rows - 1, 0), (rows - 1, cols - 1), (0, cols // 2),
+             (rows // 2, 0), (rows - 1, cols // 3)] + \
+            [(int(rng.integers(1, rows - 1)), int(rng.integers(1, cols - 1))) for _ in range(5)]
+    for by, bx in picks:
+        r0, r1 = max(by - 1, 0), min(by + 2, rows)
+        c0, c1 = max(bx - 1, 0), min(bx + 2, cols)
+        y0, y1, x0, x1 = r0 * 64, min(r1 * 64, h), c0 * 64, min(c1 * 64, w)
+        crop = (planes[0][y0:y1, x0:x1], planes[1][y0 // 2:y1 // 2, x0 // 2:x1 // 2],
+                planes[2][y0 // 2:y1 // 2, x0 // 2:x1 // 2])
+        exp = ref.filter_frame(*crop, bd, params[r0:r1, c0:c1],
+                               dirs[y0 // 8:y1 // 8, x0 // 8:x1 // 8],
+                               var[y0 // 8:y1 // 8, x0 // 8:x1 // 8])
+        ly, lx = by * 64, bx * 64
+        ey, ex = min(ly + 64, h), min(lx + 64, w)
+        assert np.array_equal(got[0][ly:ey, lx:ex], exp[0][ly - y0:ey - y0, lx - x0:ex - x0]), (by, bx)
+        for k in (1, 2):
+            assert np.array_equal(got[k][ly // 2:ey // 2, lx // 2:ex // 2],
+                                  exp[k][(ly - y0) // 2:(ey - y0) // 2,
+                                         (lx - x0) // 2:(ex - x0) // 2]), (by, bx, k)
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_consecutive_frames_on_one_stream(cdef, ctx, ref, overlap):
+    """A run of filter calls on one stream, launched as programmatic
+    dependents of each other, with and without the independence promise:
+    every frame equals the oracle."""
+    from paper_1602_05975_gb300 import synth
+    frames = [synth.make_frame(w, h, bd, None, 700 + i)
+              for i, (w, h, bd) in enumerate([(352, 288, 8), (640, 360, 10), (200, 136, 8),
+                                              (640, 360, 10), (1280, 720, 8), (96, 64, 10)])]
+    ins = [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames]
+    outs = [cdef.alloc_frame(f.width, f.height, f.bitdepth, fill=0) for f in frames]
+    prms = [cdef.params_tensor(f.params) for f in frames]
+    stream = torch.cuda.Stream()
+    ctx.set_overlap(overlap)
+    try:
+        for _ in range(3):
+            for i, o, p in zip(ins, outs, prms):
+                cdef.cdef_filter_frame(ctx, i, p, o, stream=stream)
+        stream.synchronize()
+    finally:
+        ctx.set_overlap(False)
+    assert ctx.status() == 0
+    for f, o in zip(frames, outs):
+        _assert_frames_equal(o.to_numpy(), ref.filter_frame(*f.rec, f.bitdepth, f.params))
+
+
+def test_stream_order_kept_without_overlap(cdef, ctx, ref):
+    """Without the promise a filter call reads what the kernel just before
+    it on the stream wrote: filter a frame, then filter that output again."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(640, 360, 10, 32, seed=720)
+    a = cdef.frame_from_numpy(f.rec, 10)
+    b = cdef.alloc_frame(640, 360, 10, fill=0)
+    c = cdef.alloc_frame(640, 360, 10, fill=0)
+    p = cdef.params_tensor(f.params)
+    stream = torch.cuda.Stream()
+    cdef.cdef_filter_frame(ctx, a, p, b, stream=stream)
+    cdef.cdef_filter_frame(ctx, b, p, c, stream=stream)
+    stream.synchronize()
+    once = ref.filter_frame(*f.rec, 10, f.params)
+    _assert_frames_equal(c.to_numpy(), ref.filter_frame(*once, 10, f.params))
