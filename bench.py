@@ -609,6 +609,9 @@ def run_serve(args):
     budget = W["budget"]
     batched_be = serve.CudaBackend(ctx, budget)
     single_be = serve.CudaBackend(ctx, budget)
+    shapes = [(w, h, bd) for (w, h) in W["sizes"] for bd in W["bitdepths"]]
+    batched_be.prewarm(shapes, 24)      # up to three batches of each size in flight
+    single_be.prewarm(shapes, 2)
 
     def batched(on_done=None):
         return serve.Server(batched_be, budget, max_batch=cdef.MAX_BATCH, max_inflight=2,

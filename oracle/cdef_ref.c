@@ -476,3 +476,117 @@ int cdef_ref_select_presets(int nblocks, const int64_t *dist_luma,
     }
     return 0;
 }
+
+/* Section 5, last paragraphs: "iteratively re-optimizing one preset at a
+ * time" after the greedy search.  Reading (R17): for a fixed set size N,
+ * starting from the greedy presets, one pass visits slots k = 0..N-1 in
+ * order and replaces preset k by the preset t in [0, 4096) that minimises
+ * sum_b min(D_b(t), min_{j != k} D_b(presets[j])), keeping the current
+ * preset when it attains that minimum and otherwise taking the lowest such
+ * t; passes repeat until one changes nothing or max_passes have run.
+ * Every change strictly lowers the total, so the loop terminates.  Writes
+ * the refined presets in place, the set's total, and the passes run. */
+static int64_t set_total(int nblocks, const int64_t *dl, const int64_t *dc,
+                         const int32_t *presets, int n)
+{
+    int64_t tot = 0;
+    for (int b = 0; b < nblocks; b++) {
+        int64_t m = preset_dist(dl, dc, b, presets[0]);
+        for (int k = 1; k < n; k++)
+            m = min64(m, preset_dist(dl, dc, b, presets[k]));
+        tot += m;
+    }
+    return tot;
+}
+
+int cdef_ref_refine_presets(int nblocks, const int64_t *dist_luma,
+                            const int64_t *dist_chroma, int32_t *presets, int n,
+                            int max_passes, int64_t *total, int *passes)
+{
+    if (nblocks <= 0 || n < 1 || n > 8 || max_passes < 0)
+        return -1;
+    int run = 0;
+    for (int pass = 0; pass < max_passes; pass++) {
+        int changed = 0;
+        run++;
+        for (int k = 0; k < n; k++) {
+            int32_t trial[8];
+            for (int j = 0; j < n; j++)
+                trial[j] = presets[j];
+            int64_t cur_total = set_total(nblocks, dist_luma, dist_chroma, trial, n);
+            int best_t = presets[k];
+            int64_t best_total = cur_total;
+            for (int t = 0; t < 4096; t++) {
+                trial[k] = t;
+                int64_t tot = set_total(nblocks, dist_luma, dist_chroma, trial, n);
+                if (tot < best_total || (tot == best_total && best_t != presets[k] && t < best_t)) {
+                    best_t = t;
+                    best_total = tot;
+                }
+            }
+            if (best_t != presets[k]) {
+                presets[k] = best_t;
+                changed = 1;
+            }
+        }
+        if (!changed)
+            break;
+    }
+    *total = set_total(nblocks, dist_luma, dist_chroma, presets, n);
+    if (passes)
+        *passes = run;
+    return 0;
+}
+
+/* Greedy search (cdef_ref_select_presets) followed by the refinement above
+ * for each N in {1, 2, 4, 8} (each from the greedy prefix of that size),
+ * then N by J (ties to the smaller N) and block ids over the refined set
+ * of that N (ties to the lower index).  max_passes = 0 gives the greedy
+ * result.  presets receives the chosen set (npresets entries). */
+int cdef_ref_select_presets_refined(int nblocks, const int64_t *dist_luma,
+                                    const int64_t *dist_chroma, int64_t lambda,
+                                    int max_passes, int32_t *presets,
+                                    int32_t *npresets, uint8_t *block_ids,
+                                    int64_t *cost)
+{
+    int32_t greedy[8];
+    int32_t np = 0;
+    int64_t c = 0;
+    int rc = cdef_ref_select_presets(nblocks, dist_luma, dist_chroma, lambda, greedy, &np,
+                                     block_ids, &c, NULL);
+    if (rc)
+        return rc;
+    int best_n = 0;
+    int64_t best_j = 0;
+    int32_t best_set[8] = {0};
+    for (int lg = 0; lg < 4; lg++) {
+        const int n = 1 << lg;
+        int32_t set[8];
+        for (int k = 0; k < n; k++)
+            set[k] = greedy[k];
+        int64_t tot = 0;
+        if (cdef_ref_refine_presets(nblocks, dist_luma, dist_chroma, set, n, max_passes, &tot,
+                                    NULL))
+            return -1;
+        const int64_t j = tot + lambda * nblocks * lg;
+        if (best_n == 0 || j < best_j) {
+            best_n = n;
+            best_j = j;
+            for (int k = 0; k < n; k++)
+                best_set[k] = set[k];
+        }
+    }
+    for (int k = 0; k < 8; k++)
+        presets[k] = k < best_n ? best_set[k] : 0;
+    *npresets = best_n;
+    *cost = best_j;
+    for (int b = 0; b < nblocks; b++) {
+        int id = 0;
+        for (int k = 1; k < best_n; k++)
+            if (preset_dist(dist_luma, dist_chroma, b, best_set[k]) <
+                preset_dist(dist_luma, dist_chroma, b, best_set[id]))
+                id = k;
+        block_ids[b] = (uint8_t)id;
+    }
+    return 0;
+}

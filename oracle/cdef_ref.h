@@ -117,6 +117,20 @@ int cdef_ref_select_presets(int nblocks, const int64_t *dist_luma,
                             uint8_t *block_ids, int64_t *cost,
                             int64_t *costs);
 
+/* Section 5: iterative re-optimisation of one preset at a time (reading
+ * R17 in cdef_ref.c), on n presets (in/out), at most max_passes passes. */
+int cdef_ref_refine_presets(int nblocks, const int64_t *dist_luma,
+                            const int64_t *dist_chroma, int32_t *presets, int n,
+                            int max_passes, int64_t *total, int *passes);
+
+/* Greedy search, then the refinement for each N in {1, 2, 4, 8}, then N
+ * by J and the block ids (max_passes = 0: the greedy result). */
+int cdef_ref_select_presets_refined(int nblocks, const int64_t *dist_luma,
+                                    const int64_t *dist_chroma, int64_t lambda,
+                                    int max_passes, int32_t *presets,
+                                    int32_t *npresets, uint8_t *block_ids,
+                                    int64_t *cost);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,14 @@ def lib():
             C.c_int, _i64p, _i64p, C.c_int64, _i32p, C.POINTER(C.c_int32),
             _u8p, C.POINTER(C.c_int64), _i64p]
         L.cdef_ref_select_presets.restype = C.c_int
+        L.cdef_ref_refine_presets.argtypes = [
+            C.c_int, _i64p, _i64p, _i32p, C.c_int, C.c_int, C.POINTER(C.c_int64),
+            C.POINTER(C.c_int)]
+        L.cdef_ref_refine_presets.restype = C.c_int
+        L.cdef_ref_select_presets_refined.argtypes = [
+            C.c_int, _i64p, _i64p, C.c_int64, C.c_int, _i32p, C.POINTER(C.c_int32),
+            _u8p, C.POINTER(C.c_int64)]
+        L.cdef_ref_select_presets_refined.restype = C.c_int
         _lib = L
     return _lib
 
@@ -202,9 +210,39 @@ def select_presets(dist_luma, dist_chroma, lam: int):
                 cost=cost.value, costs=costs)
 
 
-def search_strengths(rec, src, bitdepth: int, damping: int, lam: int):
+def refine_presets(dist_luma, dist_chroma, presets, max_passes: int):
+    """Section 5: re-optimise one preset at a time (reading R17)."""
+    dl = np.ascontiguousarray(dist_luma, np.int64).reshape(-1)
+    dc = np.ascontiguousarray(dist_chroma, np.int64).reshape(-1)
+    p = np.ascontiguousarray(presets, np.int32).copy()
+    total = C.c_int64(0)
+    passes = C.c_int(0)
+    if lib().cdef_ref_refine_presets(dl.size // 64, dl, dc, p, p.size, max_passes,
+                                     C.byref(total), C.byref(passes)) != 0:
+        raise ValueError("oracle rejected refine_presets arguments")
+    return p, total.value, passes.value
+
+
+def select_presets_refined(dist_luma, dist_chroma, lam: int, max_passes: int):
+    dl = np.ascontiguousarray(dist_luma, np.int64).reshape(-1)
+    dc = np.ascontiguousarray(dist_chroma, np.int64).reshape(-1)
+    nb = dl.size // 64
+    presets = np.zeros(8, np.int32)
+    n = C.c_int32(0)
+    ids = np.zeros(nb, np.uint8)
+    cost = C.c_int64(0)
+    if lib().cdef_ref_select_presets_refined(nb, dl, dc, lam, max_passes, presets, C.byref(n),
+                                             ids, C.byref(cost)) != 0:
+        raise ValueError("oracle rejected select_presets_refined arguments")
+    return dict(presets=presets, npresets=n.value, block_ids=ids, cost=cost.value)
+
+
+def search_strengths(rec, src, bitdepth: int, damping: int, lam: int, refine_passes: int = 0):
     dl, dc = distortion(rec, src, bitdepth, damping)
-    out = select_presets(dl, dc, lam)
+    if refine_passes:
+        out = select_presets_refined(dl, dc, lam, refine_passes)
+    else:
+        out = select_presets(dl, dc, lam)
     out["dist_luma"] = dl
     out["dist_chroma"] = dc
     return out

@@ -673,3 +673,70 @@ def test_greedy_lambda_extremes(ref):
     ties = ref.select_presets(np.zeros((5, 64), np.int64), np.zeros((5, 64), np.int64), 0)
     assert ties["npresets"] == 1 and list(ties["presets"]) == [0] * 8
     assert (ties["block_ids"] == 0).all()
+
+
+# --------------------------------------------------------------- section 5: preset re-optimisation
+def _constructed_tables():
+    """Three blocks, luma-only costs (chroma 0): options X = 1, Y = 2, Z = 3
+    (luma indices); every other option costs 1000.  The best single preset
+    is Z, greedy then adds X, but {X, Y} costs nothing."""
+    dl = np.full((3, 64), 1000, np.int64)
+    dc = np.zeros((3, 64), np.int64)
+    dl[0, [1, 2, 3]] = [0, 10, 4]
+    dl[1, [1, 2, 3]] = [10, 0, 4]
+    dl[2, [1, 2, 3]] = [0, 0, 0]
+    return dl, dc
+
+
+def test_refinement_escapes_greedy_trap(ref):
+    dl, dc = _constructed_tables()
+    g = ref.select_presets(dl, dc, 0)
+    assert list(g["presets"][:2]) == [3 * 64, 1 * 64]            # Z, then X
+    p, total, passes = ref.refine_presets(dl, dc, g["presets"][:2], 8)
+    assert sorted(int(t) >> 6 for t in p) == [1, 2] and total == 0
+    assert passes == 2                                            # one changing pass, one quiet
+
+
+def _total(dl, dc, presets):
+    d = dl[:, np.asarray(presets) >> 6] + dc[:, np.asarray(presets) & 63]
+    return int(d.min(axis=1).sum())
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_refinement_is_a_local_optimum_and_never_worse(ref, seed):
+    rng = np.random.default_rng(seed)
+    dl = rng.integers(0, 500, (5, 64)).astype(np.int64)
+    dc = rng.integers(0, 500, (5, 64)).astype(np.int64)
+    g = ref.select_presets(dl, dc, 0)
+    for n in (2, 4):
+        start = g["presets"][:n].copy()
+        p, total, _ = ref.refine_presets(dl, dc, start, 16)
+        assert total == _total(dl, dc, p) <= _total(dl, dc, start)
+        # brute force: no single replacement lowers the total
+        for k in range(n):
+            best = min(_total(dl, dc, np.concatenate([p[:k], [t], p[k + 1:]]))
+                       for t in range(4096))
+            assert best == total
+
+
+def test_refinement_keeps_a_local_optimum_and_zero_passes_is_greedy(ref):
+    rng = np.random.default_rng(9)
+    dl = rng.integers(0, 300, (4, 64)).astype(np.int64)
+    dc = rng.integers(0, 300, (4, 64)).astype(np.int64)
+    g = ref.select_presets(dl, dc, 5)
+    r0 = ref.select_presets_refined(dl, dc, 5, 0)
+    assert r0["cost"] == g["cost"] and r0["npresets"] == g["npresets"]
+    assert list(r0["presets"][:g["npresets"]]) == list(g["presets"][:g["npresets"]])
+    p, total, _ = ref.refine_presets(dl, dc, g["presets"][:2], 16)
+    p2, total2, passes2 = ref.refine_presets(dl, dc, p, 16)
+    assert list(p2) == list(p) and total2 == total and passes2 == 1
+
+
+def test_refined_selection_cost_not_above_greedy(ref):
+    dl, dc = _constructed_tables()
+    for lam in (0, 1, 3, 100):
+        g = ref.select_presets(dl, dc, lam)
+        r = ref.select_presets_refined(dl, dc, lam, 8)
+        assert r["cost"] <= g["cost"]
+    r = ref.select_presets_refined(dl, dc, 0, 8)
+    assert r["cost"] == 0 and r["npresets"] == 2
