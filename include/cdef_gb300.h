@@ -210,6 +210,17 @@ int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *tuning);
  * the first search).  Host only. */
 int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
 
+/* Preset re-optimisation of cdef_search_strengths (section 5: "iteratively
+ * re-optimizing one preset at a time" after the greedy search).  For each
+ * N in {2, 4, 8}, starting from the greedy presets 1..N, a pass re-chooses
+ * preset k = 1..N in turn as the preset minimising the frame's total with
+ * the others fixed (the current preset kept when it attains the minimum,
+ * else the lowest index); passes repeat until one changes nothing or
+ * max_passes have run.  N, J and the block ids then follow from the
+ * re-optimised sets.  0 (the default) = the greedy search alone; at most 16.
+ * Host only; applies to later searches on the context. */
+int cdef_ctx_set_search_refine(cdef_ctx *ctx, int max_passes);
+
 /* Overlap of consecutive filter calls on one stream.  No paper counterpart.
  * Every cdef_filter_frame / cdef_filter_frames launch lets the next kernel
  * on its stream be scheduled before it ends (programmatic dependent

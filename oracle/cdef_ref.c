@@ -577,7 +577,7 @@ int cdef_ref_select_presets_refined(int nblocks, const int64_t *dist_luma,
         }
     }
     for (int k = 0; k < 8; k++)
-        presets[k] = k < best_n ? best_set[k] : 0;
+        presets[k] = k < best_n ? best_set[k] : greedy[k];
     *npresets = best_n;
     *cost = best_j;
     for (int b = 0; b < nblocks; b++) {

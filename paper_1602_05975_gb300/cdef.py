@@ -82,13 +82,15 @@ def load():
                                         C.POINTER(i64), vp]
     L.cdef_ctx_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.cdef_ctx_set_overlap.argtypes = [vp, C.c_int]
+    L.cdef_ctx_set_search_refine.argtypes = [vp, C.c_int]
     L.cdef_ctx_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.cdef_strerror.argtypes = [C.c_int]
     L.cdef_strerror.restype = C.c_char_p
     L.cdef_version.restype = C.c_char_p
     for name in ("cdef_ctx_create", "cdef_ctx_destroy", "cdef_ctx_status", "cdef_find_dir",
                  "cdef_filter_frame", "cdef_filter_frames", "cdef_search_strengths",
-                 "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap"):
+                 "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap",
+                 "cdef_ctx_set_search_refine"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -249,6 +251,12 @@ class Context:
 
     def status(self, clear=True):
         return self._lib.cdef_ctx_status(self.handle, int(clear))
+
+    def set_search_refine(self, max_passes: int):
+        """Re-optimise the searched presets one at a time for at most
+        `max_passes` passes (0 = greedy only)."""
+        _check(self._lib.cdef_ctx_set_search_refine(self.handle, int(max_passes)),
+               "cdef_ctx_set_search_refine")
 
     def set_overlap(self, enable: bool):
         """Declare consecutive filter calls on a stream independent (see

@@ -34,6 +34,8 @@ struct cdef_ctx {
     SearchTune forced;            // fields > 0 fixed by cdef_ctx_set_tuning
     SearchTune last;              // configuration of the last search
     bool overlap;                 // filter calls on a stream declared independent
+    int refine_passes;            // preset re-optimisation passes of the search (0 = greedy)
+    int search_key_refine;        // refine_passes search_exec was recorded with
     std::unordered_map<uint64_t, SearchTune> *tuned;  // autotuned, per batch shape
 };
 
@@ -276,6 +278,13 @@ int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *t)
     return CDEF_OK;
 }
 
+int cdef_ctx_set_search_refine(cdef_ctx *ctx, int max_passes)
+{
+    if (!ctx || max_passes < 0 || max_passes > kMaxRefinePasses) return CDEF_ERR_ARG;
+    ctx->refine_passes = max_passes;
+    return CDEF_OK;
+}
+
 int cdef_ctx_set_overlap(cdef_ctx *ctx, int enable)
 {
     if (!ctx) return CDEF_ERR_ARG;
@@ -432,11 +441,11 @@ int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long 
             (ctx->forced.ctas_per_sm > 0 && t.ctas_per_sm != ctx->forced.ctas_per_sm))
             continue;
         e = launch_search(b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status, ctx->work,
-                          t, s);
+                          t, ctx->refine_passes, s);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         if (e == cudaSuccess)
             e = launch_search(b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status,
-                              ctx->work, t, s);
+                              ctx->work, t, ctx->refine_passes, s);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -533,11 +542,13 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
                       memcmp(ctx->search_key, b, sizeof(SearchBatch)) == 0 &&
                       memcmp(ctx->search_ptrs, ptrs, sizeof(ptrs)) == 0 &&
                       ctx->search_key_tune.groups == tune.groups &&
-                      ctx->search_key_tune.ctas_per_sm == tune.ctas_per_sm;
+                      ctx->search_key_tune.ctas_per_sm == tune.ctas_per_sm &&
+                      ctx->search_key_refine == ctx->refine_passes;
     cudaError_t e = same ? cudaSuccess : cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess && !same) {
         const cudaError_t le = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids,
-                                             ctx->status, work, tune, ctx->capture);
+                                             ctx->status, work, tune, ctx->refine_passes,
+                                             ctx->capture);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(ctx->capture, &graph);
         if (e == cudaSuccess && le != cudaSuccess) e = le;
@@ -557,6 +568,7 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
                 memcpy(ctx->search_key, b, sizeof(SearchBatch));
                 memcpy(ctx->search_ptrs, ptrs, sizeof(ptrs));
                 ctx->search_key_tune = tune;
+                ctx->search_key_refine = ctx->refine_passes;
             }
         } else if (ctx->search_key) {
             memset(ctx->search_key, 0, sizeof(SearchBatch));

@@ -64,11 +64,14 @@ struct SearchBatch {
 
 // Per-frame result of the preset search (device).
 struct SearchResultDev {
-    int presets[8];
-    long long totals[8];
-    long long cost;
+    int presets[8];          // the chosen set (first npresets entries)
+    long long cost;          // J of the chosen N
     int npresets;
     int pad;
+    int greedy[8];           // greedy order
+    long long totals[8];     // greedy totals over the first 1..8 presets
+    int refined[4][8];       // per N = 1, 2, 4, 8: the (re-optimised) set
+    long long ref_totals[4];
 };
 
 // Launchers (return cudaGetLastError() of the launch).
@@ -118,14 +121,28 @@ inline SearchTune default_search_tune(int total_blocks, int sms)
 // Strength search: distortion tables, then the greedy preset search.
 // Device scratch: `cur` one u64 per block, `tot` 4096 u64 per frame (zeroed
 // by the call itself), `work` a zeroed counter pair (left zeroed).
+// `refine_passes`: 0 = the greedy presets; > 0 = then re-optimise each set
+// one preset at a time for at most that many passes (section 5).
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
                           long long *dist_chroma, unsigned long long *cur,
                           unsigned long long *tot, SearchResultDev *results,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
-                          cudaStream_t s);
+                          int refine_passes, cudaStream_t s);
+// The preset selection alone (one cooperative launch); `ctl` is the control
+// block that follows `tot` in the scratch.
+cudaError_t launch_presets(const SearchBatch &b, const long long *dl, const long long *dc,
+                           unsigned long long *cur, unsigned long long *tot, void *ctl,
+                           SearchResultDev *results, uint8_t *block_ids, int *status,
+                           int refine_passes, cudaStream_t s);
+size_t preset_ctl_bytes();
+constexpr int kMaxRefinePasses = 16;
+constexpr size_t kPresetCtlBytes = 512;   // barrier and per-frame flags of launch_presets
+// Scratch of one search: `cur` one u64 per block, `tot` 4096 u64 per frame,
+// then the preset kernel's control block.
 constexpr size_t search_scratch_bytes(int nframes, int nblocks)
 {
-    return sizeof(unsigned long long) * ((size_t)nblocks + (size_t)nframes * 4096);
+    return sizeof(unsigned long long) * ((size_t)nblocks + (size_t)nframes * 4096) +
+           kPresetCtlBytes;
 }
 
 // Host: the three 2-D tile maps (filter-block boxes with halo) of a frame's

@@ -146,7 +146,7 @@ extern "C" int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
     }
     cudaError_t e = launch_search(b, reinterpret_cast<long long *>(dist_luma),
                                   reinterpret_cast<long long *>(dist_chroma), cur, tot, results,
-                                  block_ids, status, work, default_search_tune(total, sms), s);
+                                  block_ids, status, work, default_search_tune(total, sms), 0, s);
     SearchResultDev host[kMaxBatch];  // pageable stack copy: no pinned allocation
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host, results, sizeof(SearchResultDev) * n, cudaMemcpyDeviceToHost, s);

@@ -1,0 +1,389 @@
+// Preset selection of the strength search (section 5, eq. 15): the greedy
+// search, the optional one-at-a-time re-optimisation of the presets, and
+// the final choice of N and of each block's preset, as ONE persistent
+// kernel whose phases are separated by grid-wide barriers.
+//
+// Phases of one step:
+//   partial  every CTA takes chunks of 16 filter blocks of any frame and
+//            adds, for all 4096 (luma pair, chroma pair) presets t, the
+//            chunk's sum_b min(best_b, D_b(t)) to the frame's totals (u64
+//            atomics); best_b is the block's least distortion over the
+//            presets kept so far (greedy) or over all presets but the one
+//            being re-chosen (re-optimisation);
+//   select   one CTA per frame takes the least total (greedy: lowest index
+//            on ties; re-optimisation: the current preset if it attains the
+//            least total, else the lowest index), records it, lowers the
+//            blocks' best distortion (greedy) and clears the totals.
+// The kernel is launched cooperatively (every CTA resident), so the
+// barriers complete; each barrier wait is bounded and sets the timeout
+// status bit when it gives up.
+#include <climits>
+
+#include "cdef_internal.h"
+#include "tma.cuh"
+
+namespace cdefgb {
+namespace {
+
+constexpr int kChunk = 16;         // blocks per partial unit
+constexpr int kThreads = 256;
+constexpr int kTuples = 4096;
+constexpr int kPerThread = kTuples / kThreads;
+constexpr long long kBarrierCycles = 1ll << 30;
+
+struct Ctl {                       // lives in device scratch
+    unsigned arrive;               // CTAs arrived at the current barrier
+    unsigned gen;                  // barrier generation
+    unsigned done_frames[4];       // per set size: frames whose re-optimisation converged
+                                   // (never reset inside a launch: every CTA reads the
+                                   // count of its size after the pass's barrier)
+    unsigned changed[kMaxBatch];   // the current pass changed a preset
+    unsigned done[kMaxBatch];      // the frame's re-optimisation converged
+};
+
+static_assert(sizeof(Ctl) <= kPresetCtlBytes, "preset control block outgrew its scratch");
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier; false when the wait gave up (status set).
+__device__ bool grid_sync(Ctl *ctl, int *status)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire(&ctl->gen);
+        __threadfence();
+        if (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1) {
+            atomicExch(&ctl->arrive, 0u);
+            __threadfence();
+            st_release(&ctl->gen, g + 1);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire(&ctl->gen) == g) {
+                if (clock64() - t0 > kBarrierCycles) {
+                    atomicOr(status, kStatusTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ int frame_chunks(const SearchFrameDev &F)
+{
+    return (F.fb_cols * F.fb_rows + kChunk - 1) / kChunk;
+}
+
+__device__ __forceinline__ unsigned long long dist_of(const long long *dl, const long long *dc,
+                                                      int g, int t)
+{
+    return (unsigned long long)(dl[(int64_t)g * 64 + (t >> 6)] + dc[(int64_t)g * 64 + (t & 63)]);
+}
+
+struct Shared {
+    unsigned long long dl[kChunk][64], dc[kChunk][64], cur[kChunk];
+    unsigned long long red_v[kThreads / 32];
+    int red_t[kThreads / 32];
+    int best;
+};
+
+// partial phase.  refine_lg < 0: greedy (best_b from `cur`); otherwise the
+// re-optimisation of slot k of the set of size n = 1 << refine_lg.
+__device__ void partial_phase(const SearchBatch &batch, const long long *dl, const long long *dc,
+                              const unsigned long long *cur, unsigned long long *tot,
+                              const SearchResultDev *res, const Ctl *ctl, int refine_lg, int k,
+                              Shared &sh)
+{
+    const int tid = threadIdx.x;
+    int units = 0;
+    for (int f = 0; f < batch.n; f++) units += frame_chunks(batch.f[f]);
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        int fi = 0, c = u;
+        while (c >= frame_chunks(batch.f[fi])) c -= frame_chunks(batch.f[fi++]);
+        if (refine_lg >= 0 && __ldcg(&ctl->done[fi])) continue;
+        const SearchFrameDev &F = batch.f[fi];
+        const int B = F.fb_cols * F.fb_rows;
+        const int b0 = c * kChunk, nb = min(kChunk, B - b0);
+        const int g0 = F.block_start + b0;
+        for (int i = tid; i < nb * 64; i += kThreads) {
+            sh.dl[i >> 6][i & 63] = (unsigned long long)dl[(int64_t)(g0 + (i >> 6)) * 64 + (i & 63)];
+            sh.dc[i >> 6][i & 63] = (unsigned long long)dc[(int64_t)(g0 + (i >> 6)) * 64 + (i & 63)];
+        }
+        __syncthreads();
+        if (tid < nb) {
+            if (refine_lg < 0) {
+                sh.cur[tid] = __ldcg(&cur[g0 + tid]);
+            } else {
+                const int n = 1 << refine_lg;
+                unsigned long long m = ULLONG_MAX;
+                for (int j = 0; j < n; j++) {
+                    if (j == k) continue;
+                    const int t = __ldcg(&res[fi].refined[refine_lg][j]);
+                    const unsigned long long v = sh.dl[tid][t >> 6] + sh.dc[tid][t & 63];
+                    m = v < m ? v : m;
+                }
+                sh.cur[tid] = m;
+            }
+        }
+        __syncthreads();
+        unsigned long long a[kPerThread];
+#pragma unroll
+        for (int q = 0; q < kPerThread; q++) a[q] = 0;
+        const int ci = tid & 63, l0 = tid >> 6;
+        for (int b = 0; b < nb; b++) {
+            const unsigned long long cv = sh.cur[b], dcv = sh.dc[b][ci];
+#pragma unroll
+            for (int q = 0; q < kPerThread; q++) {
+                const unsigned long long v = sh.dl[b][l0 + 4 * q] + dcv;
+                a[q] += v < cv ? v : cv;
+            }
+        }
+        unsigned long long *t = tot + (int64_t)fi * kTuples;
+#pragma unroll
+        for (int q = 0; q < kPerThread; q++) atomicAdd(&t[tid + kThreads * q], a[q]);
+        __syncthreads();   // before the next unit overwrites the shared tables
+    }
+}
+
+__device__ __forceinline__ bool better(unsigned long long a, int ta, unsigned long long b, int tb)
+{
+    return a < b || (a == b && ta < tb);
+}
+
+// The least of a frame's totals and its lowest index (whole CTA).
+__device__ void frame_argmin(unsigned long long *t, Shared &sh, unsigned long long *min_v,
+                             int *min_t)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long bv = ULLONG_MAX;
+    int bt = INT_MAX;
+    for (int i = tid; i < kTuples; i += kThreads) {
+        const unsigned long long v = __ldcg(&t[i]);
+        if (better(v, i, bv, bt)) { bv = v; bt = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+        if (better(ov, ot, bv, bt)) { bv = ov; bt = ot; }
+    }
+    if (lane == 0) { sh.red_v[warp] = bv; sh.red_t[warp] = bt; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < kThreads / 32; w++)
+            if (better(sh.red_v[w], sh.red_t[w], sh.red_v[0], sh.red_t[0])) {
+                sh.red_v[0] = sh.red_v[w];
+                sh.red_t[0] = sh.red_t[w];
+            }
+    }
+    __syncthreads();
+    *min_v = sh.red_v[0];
+    *min_t = sh.red_t[0];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads)
+preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
+              const long long *__restrict__ dc, unsigned long long *cur, unsigned long long *tot,
+              SearchResultDev *res, uint8_t *block_ids, int *status, Ctl *ctl, int refine_passes)
+{
+    __shared__ Shared sh;
+    const int tid = threadIdx.x;
+    const int stride = gridDim.x * kThreads;
+    const int n = batch.n;
+
+    for (int i = blockIdx.x * kThreads + tid; i < batch.total_blocks; i += stride) cur[i] = ULLONG_MAX;
+    for (int i = blockIdx.x * kThreads + tid; i < n * kTuples; i += stride) tot[i] = 0;
+    if (blockIdx.x == 0 && tid < n) {
+        ctl->changed[tid] = 0;
+        ctl->done[tid] = 0;
+    }
+    if (blockIdx.x == 0 && tid < 4) ctl->done_frames[tid] = 0;
+    if (!grid_sync(ctl, status)) return;
+
+    // ---- greedy: preset `step` is the best addition to presets 0..step-1
+    for (int step = 0; step < 8; step++) {
+        partial_phase(batch, dl, dc, cur, tot, res, ctl, -1, 0, sh);
+        if (!grid_sync(ctl, status)) return;
+        for (int f = blockIdx.x; f < n; f += gridDim.x) {
+            unsigned long long *t = tot + (int64_t)f * kTuples;
+            unsigned long long v;
+            int best;
+            frame_argmin(t, sh, &v, &best);
+            if (tid == 0) {
+                res[f].greedy[step] = best;
+                res[f].totals[step] = (long long)v;
+            }
+            const SearchFrameDev &F = batch.f[f];
+            const int B = F.fb_cols * F.fb_rows;
+            for (int b = tid; b < B; b += kThreads) {
+                const int g = F.block_start + b;
+                const unsigned long long d = dist_of(dl, dc, g, best);
+                if (d < __ldcg(&cur[g])) cur[g] = d;
+            }
+            for (int i = tid; i < kTuples; i += kThreads) t[i] = 0;
+            __syncthreads();
+        }
+        if (!grid_sync(ctl, status)) return;
+    }
+
+    // ---- sets of size 1, 2, 4, 8 from the greedy prefixes
+    for (int f = blockIdx.x; f < n; f += gridDim.x) {
+        if (tid < 4) {
+            const int sz = 1 << tid;
+            for (int j = 0; j < 8; j++) res[f].refined[tid][j] = j < sz ? res[f].greedy[j] : 0;
+            res[f].ref_totals[tid] = res[f].totals[sz - 1];
+        }
+    }
+    if (!grid_sync(ctl, status)) return;
+
+    // ---- re-optimisation, one preset at a time (sizes 2, 4, 8; size 1 is
+    // exhaustive already)
+    for (int lg = 1; lg <= 3 && refine_passes > 0; lg++) {
+        const int sz = 1 << lg;
+        for (int pass = 0; pass < refine_passes; pass++) {
+            for (int k = 0; k < sz; k++) {
+                partial_phase(batch, dl, dc, cur, tot, res, ctl, lg, k, sh);
+                if (!grid_sync(ctl, status)) return;
+                for (int f = blockIdx.x; f < n; f += gridDim.x) {
+                    if (__ldcg(&ctl->done[f])) continue;
+                    unsigned long long *t = tot + (int64_t)f * kTuples;
+                    const int old = __ldcg(&res[f].refined[lg][k]);
+                    const unsigned long long old_v = __ldcg(&t[old]);
+                    unsigned long long v;
+                    int best;
+                    frame_argmin(t, sh, &v, &best);
+                    if (tid == 0) {
+                        if (old_v == v) best = old;        // keep the current preset on ties
+                        if (best != old) {
+                            res[f].refined[lg][k] = best;
+                            ctl->changed[f] = 1;
+                        }
+                        res[f].ref_totals[lg] = (long long)v;
+                    }
+                    for (int i = tid; i < kTuples; i += kThreads) t[i] = 0;
+                    __syncthreads();
+                }
+                if (!grid_sync(ctl, status)) return;
+            }
+            // end of the pass: a frame whose pass changed nothing is done
+            for (int f = blockIdx.x; f < n; f += gridDim.x) {
+                if (tid == 0 && !ctl->done[f]) {
+                    if (!ctl->changed[f]) {
+                        ctl->done[f] = 1;
+                        atomicAdd(&ctl->done_frames[lg], 1u);
+                    }
+                    ctl->changed[f] = 0;
+                }
+            }
+            if (!grid_sync(ctl, status)) return;
+            if (ld_acquire(&ctl->done_frames[lg]) == (unsigned)n) break;
+        }
+        // next size: every frame starts again (each CTA resets only the
+        // flags of its own frames, which no other CTA reads before the
+        // barrier below)
+        for (int f = blockIdx.x; f < n; f += gridDim.x)
+            if (tid == 0) {
+                ctl->done[f] = 0;
+                ctl->changed[f] = 0;
+            }
+        if (!grid_sync(ctl, status)) return;
+    }
+
+    // ---- N in {1, 2, 4, 8} by J (ties to the smaller N), then each block's
+    // least-distortion preset of that set (ties to the lower index)
+    for (int f = blockIdx.x; f < n; f += gridDim.x) {
+        const SearchFrameDev &F = batch.f[f];
+        const int B = F.fb_cols * F.fb_rows;
+        if (tid == 0) {
+            int bl = 0;
+            long long bj = 0;
+            for (int lg = 0; lg < 4; lg++) {
+                const long long j = res[f].ref_totals[lg] + F.lambda * (long long)B * lg;
+                if (lg == 0 || j < bj) { bl = lg; bj = j; }
+            }
+            res[f].cost = bj;
+            res[f].npresets = 1 << bl;
+            // entries past N keep the greedy order (unspecified for callers)
+            for (int j = 0; j < 8; j++)
+                res[f].presets[j] = j < (1 << bl) ? res[f].refined[bl][j] : res[f].greedy[j];
+            sh.best = 1 << bl;
+        }
+        __syncthreads();
+        const int N = sh.best;
+        for (int b = tid; b < B; b += kThreads) {
+            const int g = F.block_start + b;
+            int id = 0;
+            long long bestd = LLONG_MAX;
+            for (int j = 0; j < N; j++) {
+                const int t = res[f].presets[j];
+                const long long v = dl[(int64_t)g * 64 + (t >> 6)] + dc[(int64_t)g * 64 + (t & 63)];
+                if (v < bestd) { bestd = v; id = j; }
+            }
+            block_ids[g] = (uint8_t)id;
+        }
+        __syncthreads();
+    }
+}
+
+int preset_grid()
+{
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != cached_dev) {
+        int sms = 0, occ = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, preset_kernel, kThreads, 0);
+        cached = sms * (occ < 2 ? (occ > 0 ? occ : 1) : 2);
+        cached_dev = dev;
+    }
+    return cached;
+}
+
+}  // namespace
+
+size_t preset_ctl_bytes() { return sizeof(Ctl); }
+
+cudaError_t launch_presets(const SearchBatch &b, const long long *dl, const long long *dc,
+                           unsigned long long *cur, unsigned long long *tot, void *ctl,
+                           SearchResultDev *results, uint8_t *block_ids, int *status,
+                           int refine_passes, cudaStream_t s)
+{
+    // a barrier abandoned by an earlier timed-out launch must not leave
+    // CTAs counted: the arrival count starts at zero
+    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(preset_grid());
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    Ctl *c = static_cast<Ctl *>(ctl);
+    return cudaLaunchKernelEx(&cfg, preset_kernel, b, dl, dc, cur, tot, results, block_ids, status,
+                              c, refine_passes);
+}
+
+}  // namespace cdefgb

@@ -15,13 +15,9 @@
 //   leaves lane l with pairs 2l and 2l + 1, then across warps in shared
 //   memory, into 64-bit block totals.
 //
-// Greedy preset search (eq. 15), several kernels per step so that every SM
-//   works: greedy_partial adds, for chunks of blocks of each frame, the
-//   contribution min(best so far, D_luma + D_chroma) of each of the 4096
-//   (luma pair, chroma pair) presets to the frame's totals; greedy_select
-//   takes each frame's least total (lowest index on ties) and lowers the
-//   blocks' best distortion; greedy_final picks N in {1, 2, 4, 8} by J and
-//   each block's preset.
+// The preset selection that follows (greedy search, optional
+//   re-optimisation, N and block ids; eq. 15) is one persistent kernel in
+//   presets.cu.
 #include <climits>
 
 #include "tile.cuh"
@@ -419,161 +415,6 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
     }
 }
 
-// ---------------------------------------------------------------------------
-// Greedy preset search.
-constexpr int kChunk = 16;        // blocks per greedy_partial CTA
-constexpr int kPartThreads = 256;
-constexpr int kTuples = 4096;
-
-__device__ __forceinline__ int frame_chunks(const SearchFrameDev &F)
-{
-    return (F.fb_cols * F.fb_rows + kChunk - 1) / kChunk;
-}
-
-__global__ void greedy_init(const __grid_constant__ SearchBatch batch, unsigned long long *cur,
-                            unsigned long long *tot)
-{
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch.total_blocks; i += stride)
-        cur[i] = ULLONG_MAX;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch.n * kTuples; i += stride) tot[i] = 0;
-}
-
-// One chunk of one frame: adds sum_b min(cur_b, Dl[b][t >> 6] + Dc[b][t & 63])
-// over the chunk's blocks to tot[frame][t] for all 4096 presets t.
-__global__ void __launch_bounds__(kPartThreads)
-greedy_partial(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
-               const long long *__restrict__ dc, const unsigned long long *__restrict__ cur,
-               unsigned long long *tot)
-{
-    __shared__ unsigned long long s_dl[kChunk][64], s_dc[kChunk][64], s_cur[kChunk];
-    int c = blockIdx.x, fi = 0;
-    while (fi < batch.n && c >= frame_chunks(batch.f[fi])) c -= frame_chunks(batch.f[fi++]);
-    if (fi >= batch.n) return;
-    const SearchFrameDev &F = batch.f[fi];
-    const int B = F.fb_cols * F.fb_rows;
-    const int b0 = c * kChunk, nb = min(kChunk, B - b0);
-    const int g0 = F.block_start + b0;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < nb * 64; i += kPartThreads) {
-        s_dl[i >> 6][i & 63] = (unsigned long long)dl[(int64_t)(g0 + (i >> 6)) * 64 + (i & 63)];
-        s_dc[i >> 6][i & 63] = (unsigned long long)dc[(int64_t)(g0 + (i >> 6)) * 64 + (i & 63)];
-    }
-    if (tid < nb) s_cur[tid] = cur[g0 + tid];
-    __syncthreads();
-    constexpr int K = kTuples / kPartThreads;   // 16 presets per thread
-    unsigned long long a[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) a[k] = 0;
-    const int ci = tid & 63, l0 = tid >> 6;
-    for (int b = 0; b < nb; b++) {
-        const unsigned long long cv = s_cur[b], dcv = s_dc[b][ci];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const unsigned long long v = s_dl[b][l0 + 4 * k] + dcv;
-            a[k] += v < cv ? v : cv;
-        }
-    }
-    unsigned long long *t = tot + (int64_t)fi * kTuples;
-#pragma unroll
-    for (int k = 0; k < K; k++) atomicAdd(&t[tid + kPartThreads * k], a[k]);
-}
-
-__device__ __forceinline__ bool better(unsigned long long a, int ta, unsigned long long b, int tb)
-{
-    return a < b || (a == b && ta < tb);
-}
-
-// Per frame: the least total (lowest preset index on ties) becomes preset
-// `step`; the blocks' best distortion is lowered; the totals are cleared.
-__global__ void __launch_bounds__(1024)
-greedy_select(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
-              const long long *__restrict__ dc, unsigned long long *cur, unsigned long long *tot,
-              SearchResultDev *res, int step)
-{
-    __shared__ unsigned long long s_v[32];
-    __shared__ int s_t[32];
-    const int fi = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SearchFrameDev &F = batch.f[fi];
-    unsigned long long *t = tot + (int64_t)fi * kTuples;
-    unsigned long long bv = ULLONG_MAX;
-    int bt = INT_MAX;
-    for (int i = tid; i < kTuples; i += 1024) {
-        const unsigned long long v = t[i];
-        if (better(v, i, bv, bt)) { bv = v; bt = i; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-        if (better(ov, ot, bv, bt)) { bv = ov; bt = ot; }
-    }
-    if (lane == 0) { s_v[warp] = bv; s_t[warp] = bt; }
-    __syncthreads();
-    if (warp == 0) {
-        bv = s_v[lane];
-        bt = s_t[lane];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-            if (better(ov, ot, bv, bt)) { bv = ov; bt = ot; }
-        }
-        if (lane == 0) {
-            res[fi].presets[step] = bt;
-            res[fi].totals[step] = (long long)bv;
-            s_t[0] = bt;
-        }
-    }
-    __syncthreads();
-    const int best = s_t[0];
-    const int B = F.fb_cols * F.fb_rows;
-    for (int b = tid; b < B; b += 1024) {
-        const int g = F.block_start + b;
-        const unsigned long long d = (unsigned long long)(dl[(int64_t)g * 64 + (best >> 6)] +
-                                                          dc[(int64_t)g * 64 + (best & 63)]);
-        if (d < cur[g]) cur[g] = d;
-    }
-    for (int i = tid; i < kTuples; i += 1024) t[i] = 0;
-}
-
-// Per frame: N in {1, 2, 4, 8} by J = lambda B log2 N + total (ties to the
-// smaller N), then each block's least-distortion preset (ties to the lower id).
-__global__ void greedy_final(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
-                             const long long *__restrict__ dc, SearchResultDev *res, uint8_t *block_ids)
-{
-    __shared__ int s_n;
-    const int fi = blockIdx.x;
-    const SearchFrameDev &F = batch.f[fi];
-    const int B = F.fb_cols * F.fb_rows;
-    SearchResultDev &r = res[fi];
-    if (threadIdx.x == 0) {
-        int bn = 0;
-        long long bj = 0;
-        for (int lg = 0; lg < 4; lg++) {
-            const int n = 1 << lg;
-            const long long j = r.totals[n - 1] + F.lambda * (long long)B * lg;
-            if (bn == 0 || j < bj) { bn = n; bj = j; }
-        }
-        r.cost = bj;
-        r.npresets = bn;
-        s_n = bn;
-    }
-    __syncthreads();
-    const int N = s_n;
-    for (int b = threadIdx.x; b < B; b += blockDim.x) {
-        const int g = F.block_start + b;
-        int id = 0;
-        long long best = LLONG_MAX;
-        for (int k = 0; k < N; k++) {
-            const int t = r.presets[k];
-            const long long v = dl[(int64_t)g * 64 + (t >> 6)] + dc[(int64_t)g * 64 + (t & 63)];
-            if (v < best) { best = v; id = k; }
-        }
-        block_ids[g] = (uint8_t)id;
-    }
-}
-
 constexpr size_t kSmemBytes = sizeof(SearchSmem);
 
 // Persistent grid: `per_sm` CTAs on every SM (at most what fits), never more
@@ -615,7 +456,7 @@ cudaError_t launch_dist(const SearchBatch &b, long long *dl, long long *dc, int 
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long *dist_chroma,
                           unsigned long long *cur, unsigned long long *tot, SearchResultDev *results,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
-                          cudaStream_t s)
+                          int refine_passes, cudaStream_t s)
 {
     cudaError_t e;
     switch (tune.groups) {
@@ -624,16 +465,9 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     default: e = launch_dist<1>(b, dist_luma, dist_chroma, status, work, tune.ctas_per_sm, s); break;
     }
     if (e != cudaSuccess) return e;
-    greedy_init<<<64, 256, 0, s>>>(b, cur, tot);
-    int chunks = 0;
-    for (int i = 0; i < b.n; i++)
-        chunks += (b.f[i].fb_cols * b.f[i].fb_rows + kChunk - 1) / kChunk;
-    for (int step = 0; step < 8; step++) {
-        greedy_partial<<<chunks, kPartThreads, 0, s>>>(b, dist_luma, dist_chroma, cur, tot);
-        greedy_select<<<b.n, 1024, 0, s>>>(b, dist_luma, dist_chroma, cur, tot, results, step);
-    }
-    greedy_final<<<b.n, 256, 0, s>>>(b, dist_luma, dist_chroma, results, block_ids);
-    return cudaGetLastError();
+    void *ctl = tot + (size_t)b.n * 4096;
+    return launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
+                          refine_passes, s);
 }
 
 }  // namespace cdefgb

@@ -402,3 +402,39 @@ def test_stream_order_kept_without_overlap(cdef, ctx, ref):
     stream.synchronize()
     once = ref.filter_frame(*f.rec, 10, f.params)
     _assert_frames_equal(c.to_numpy(), ref.filter_frame(*once, 10, f.params))
+
+
+@pytest.mark.parametrize("passes", [1, 4, 16])
+def test_search_preset_refinement(cdef, ctx, ref, passes):
+    """Section 5's one-at-a-time re-optimisation of the presets after the
+    greedy search: presets, N, J and block ids equal the oracle's."""
+    from paper_1602_05975_gb300 import synth
+    specs = [(200, 136, 8, 16, 610), (136, 72, 10, 32, 611), (320, 192, 8, 64, 612)]
+    frames = [synth.make_frame(w, h, bd, q, seed=s) for w, h, bd, q, s in specs]
+    damping, lambdas = [5, 4, 6], [64, 512, 4096]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    ctx.set_search_refine(passes)
+    try:
+        res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames],
+                                         [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames],
+                                         damping, lambdas, ids)
+    finally:
+        ctx.set_search_refine(0)
+    assert ctx.status() == 0
+    o0 = 0
+    for f, r, d, lam in zip(frames, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths(f.rec, f.src, f.bitdepth, d, lam, refine_passes=passes)
+        g = ref.search_strengths(f.rec, f.src, f.bitdepth, d, lam)
+        assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"] <= g["cost"]
+        assert ([cdef.preset_index(p) for p in r["presets"][:r["npresets"]]] ==
+                [int(t) for t in o["presets"][:o["npresets"]]])
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
+
+
+def test_search_refine_rejects_bad_pass_counts(cdef, ctx):
+    for p in (-1, 17):
+        with pytest.raises(cdef.CdefError):
+            ctx.set_search_refine(p)
