@@ -191,6 +191,8 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        if getattr(self, "disabled", False):
+            return
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -480,6 +482,7 @@ def run_search(args):
     from paper_1602_05975_gb300 import build, cdef, synth
     build.build()
     ctx = cdef.Context(0)
+    ctx.set_search_refine(args.refine)
     frames = []
     for f in range(SEARCH_WORKLOAD["frames"]):
         w, h = SEARCH_WORKLOAD["sizes"][f % 3]
@@ -556,6 +559,7 @@ def run_search(args):
                                         "luma_pixels": sum(f.width * f.height for f in frames),
                                         "l2": "L2 flushed (256 MB write) before each call"},
         "tuning": dict(zip(("search_groups", "search_ctas_per_sm"), tune)),
+        "refine_passes": args.refine,
         "plain": {"ms_per_step": plain_sec * 1e3, "value": nb * 128 / plain_sec,
                   "what": "one cdef_search_strengths call per frame, identical outputs"},
         "clocks": clk}))
@@ -644,7 +648,7 @@ def run_serve(args):
     assert mismatches == 0, f"{mismatches} served results differ from the single-frame path"
 
     keys = ("frames_per_s", "mpixel_per_s", "p50_ms", "p99_ms", "mean_ms", "batches",
-            "mean_batch", "peak_device_bytes", "wall_s", "ok")
+            "mean_batch", "peak_device_bytes", "wall_s", "ok", "p99_tail")
     # 2. capacities: all requests present at t = 0 (after a warm-up run)
     ncap = min(n, 2000)
     one_at_a_time().run(requests(np.zeros(400), 400), timeout=600)
@@ -654,6 +658,7 @@ def run_serve(args):
 
     # 3. Poisson arrivals at fractions of the one-at-a-time capacity
     clocks = ClockSampler(0)
+    clocks.disabled = args.no_clocks
     clocks.start()
     rates = {}
     for k, frac in enumerate(W["rates"]):
@@ -706,6 +711,10 @@ def main():
                          "1080p 8-bit frames; search: batched strength search over 16 mixed "
                          "frames; serve: the serving loop")
     ap.add_argument("--requests", type=int, default=0, help="serve: requests per rate")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="search: preset re-optimisation passes after the greedy search")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="do not sample nvidia-smi clocks during the run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

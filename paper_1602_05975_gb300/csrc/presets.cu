@@ -343,7 +343,10 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
     }
 }
 
-int preset_grid()
+// As many CTAs as the partial phases have chunks (and at least one per
+// frame for the select phases), at most two per SM: fewer CTAs make the
+// barriers of small searches cheaper.
+int preset_grid(const SearchBatch &b)
 {
     static int cached_dev = -1, cached = 0;
     int dev = 0;
@@ -355,7 +358,10 @@ int preset_grid()
         cached = sms * (occ < 2 ? (occ > 0 ? occ : 1) : 2);
         cached_dev = dev;
     }
-    return cached;
+    int units = 0;
+    for (int i = 0; i < b.n; i++) units += (b.f[i].fb_cols * b.f[i].fb_rows + kChunk - 1) / kChunk;
+    const int want = units > b.n ? units : b.n;
+    return want < cached ? want : cached;
 }
 
 }  // namespace
@@ -372,7 +378,7 @@ cudaError_t launch_presets(const SearchBatch &b, const long long *dl, const long
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(preset_grid());
+    cfg.gridDim = dim3(preset_grid(b));
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;

@@ -286,6 +286,15 @@ def percentile(xs, q):
 def summarize(reqs, wall: float, server: Server) -> dict:
     ok = [r for r in reqs if r.status == "ok"]
     lat = [r.latency for r in ok]
+    # where the slowest 1% spent their time: queued (arrival to admission),
+    # admitted (to launch), launched (on the device and copies, to done)
+    tail = {}
+    if ok:
+        cut = percentile(lat, 99)
+        slow = [r for r in ok if r.latency >= cut]
+        tail = {"queued_ms": float(np.mean([r.t_admit - r.arrival for r in slow])) * 1e3,
+                "admitted_ms": float(np.mean([r.t_launch - r.t_admit for r in slow])) * 1e3,
+                "launched_ms": float(np.mean([r.t_done - r.t_launch for r in slow])) * 1e3}
     px = sum(r.width * r.height for r in ok)
     counts = collections.Counter(r.status for r in reqs)
     return {
@@ -297,6 +306,7 @@ def summarize(reqs, wall: float, server: Server) -> dict:
         "batches": server.batches,
         "mean_batch": float(np.mean(server.batch_sizes)) if server.batch_sizes else 0.0,
         "peak_device_bytes": server.peak_in_use,
+        "p99_tail": tail,
     }
 
 
