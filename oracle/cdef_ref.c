@@ -269,24 +269,56 @@ int64_t cdef_ref_filter_sample(const uint16_t *plane, int w, int h,
     return min64(ymax, max64(ymin, y));
 }
 
+/* Section 4, skip semantics (readings R18-R20).  Byte 5 of a filter
+ * block's parameters holds the presets' skip-condition bits: bit 0 luma,
+ * bit 1 chroma.  `coded` (NULL = every block coded) marks the 8x8 luma
+ * blocks with coded residual; the 4:2:0 chroma 4x4 block follows its
+ * co-located luma 8x8 block.
+ *   - A filter block with no coded 8x8 block is not filtered at all.
+ *   - Otherwise an 8x8 block without coded residual is filtered only when
+ *     its plane group's skip-condition bit is set.
+ *   - Strengths (0, 0) with the skip-condition bit set stand for primary 19
+ *     and secondary 7 (the skip condition stays set). */
+static int fb_has_coded(const uint8_t *coded, int bw, int bh, int fby, int fbx)
+{
+    if (!coded)
+        return 1;
+    for (int r = fby * 8; r < fby * 8 + 8 && r < bh; r++)
+        for (int c = fbx * 8; c < fbx * 8 + 8 && c < bw; c++)
+            if (coded[r * bw + c])
+                return 1;
+    return 0;
+}
+
 /* Filters one plane.  sub = 0 for luma (8x8 blocks, 64x64 filter blocks),
  * 1 for 4:2:0 chroma (4x4 blocks, 32x32 filter blocks; section 2: chroma
  * takes the co-located luma direction). */
 static void filter_plane(const uint16_t *in, ptrdiff_t is, uint16_t *out,
                          ptrdiff_t os, int pw, int ph, int sub, int bitdepth,
                          const uint8_t *params, int fb_cols,
-                         const uint8_t *dir, const int32_t *var, int bw)
+                         const uint8_t *dir, const int32_t *var, int bw, int bh,
+                         const uint8_t *coded)
 {
     int bs = 8 >> sub, fbs = 64 >> sub;
     for (int i = 0; i < ph; i++) {
         for (int j = 0; j < pw; j++) {
             int b8 = (i / bs) * bw + (j / bs);
-            const uint8_t *pp = params + ((i / fbs) * fb_cols + (j / fbs)) * CDEF_REF_PARAM_BYTES;
+            int fby = i / fbs, fbx = j / fbs;
+            const uint8_t *pp = params + (fby * fb_cols + fbx) * CDEF_REF_PARAM_BYTES;
+            int skip_bit = (pp[5] >> sub) & 1;
+            int on = fb_has_coded(coded, bw, bh, fby, fbx) &&
+                     (!coded || coded[b8] || skip_bit);
+            if (!on) {
+                out[(ptrdiff_t)i * os + j] = in[(ptrdiff_t)i * is + j];
+                continue;
+            }
+            int pri = pp[2 * sub], sec = pp[2 * sub + 1];
+            if (skip_bit && pri == 0 && sec == 0) {
+                pri = 19;
+                sec = 7;
+            }
             cdef_ref_eff_params e;
-            if (sub == 0)
-                cdef_ref_block_params(pp[0], pp[1], pp[4], 0, bitdepth, var[b8], &e);
-            else
-                cdef_ref_block_params(pp[2], pp[3], pp[4], 1, bitdepth, var[b8], &e);
+            cdef_ref_block_params(pri, sec, pp[4], sub, bitdepth, sub ? 0 : var[b8], &e);
             out[(ptrdiff_t)i * os + j] =
                 (uint16_t)cdef_ref_filter_sample(in, pw, ph, is, i, j, dir[b8], &e);
         }
@@ -304,10 +336,34 @@ static int valid_params(const uint8_t *params, int nblocks)
             if (!(sec == 0 || sec == 1 || sec == 2 || sec == 4 || sec == 7))
                 return 0;
         }
-        if (p[4] < 3 || p[4] > 6)
+        if (p[4] < 3 || p[4] > 6 || p[5] > 3)
             return 0;
     }
     return 1;
+}
+
+int cdef_ref_filter_frame_coded(int w, int h, int bitdepth,
+                                const uint16_t *y, ptrdiff_t ys,
+                                const uint16_t *u, ptrdiff_t us,
+                                const uint16_t *v, ptrdiff_t vs,
+                                const uint8_t *params, const uint8_t *coded,
+                                const uint8_t *dir, const int32_t *var,
+                                uint16_t *oy, ptrdiff_t oys,
+                                uint16_t *ou, ptrdiff_t ous,
+                                uint16_t *ov, ptrdiff_t ovs)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    if (!valid_params(params, fb_cols * fb_rows))
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    filter_plane(y, ys, oy, oys, w, h, 0, bitdepth, params, fb_cols, dir, var, bw, bh, coded);
+    filter_plane(u, us, ou, ous, w / 2, h / 2, 1, bitdepth, params, fb_cols, dir, var, bw, bh,
+                 coded);
+    filter_plane(v, vs, ov, ovs, w / 2, h / 2, 1, bitdepth, params, fb_cols, dir, var, bw, bh,
+                 coded);
+    return 0;
 }
 
 int cdef_ref_filter_frame(int w, int h, int bitdepth,
@@ -320,16 +376,8 @@ int cdef_ref_filter_frame(int w, int h, int bitdepth,
                           uint16_t *ou, ptrdiff_t ous,
                           uint16_t *ov, ptrdiff_t ovs)
 {
-    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
-        return -1;
-    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
-    if (!valid_params(params, fb_cols * fb_rows))
-        return -1;
-    int bw = w / 8;
-    filter_plane(y, ys, oy, oys, w, h, 0, bitdepth, params, fb_cols, dir, var, bw);
-    filter_plane(u, us, ou, ous, w / 2, h / 2, 1, bitdepth, params, fb_cols, dir, var, bw);
-    filter_plane(v, vs, ov, ovs, w / 2, h / 2, 1, bitdepth, params, fb_cols, dir, var, bw);
-    return 0;
+    return cdef_ref_filter_frame_coded(w, h, bitdepth, y, ys, u, us, v, vs, params, NULL, dir,
+                                       var, oy, oys, ou, ous, ov, ovs);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -77,7 +77,9 @@ int64_t cdef_ref_filter_sample(const uint16_t *plane, int w, int h,
  * ceil(H/64) x ceil(W/64) filter-block grid:
  *   byte 0 luma primary strength, 1 luma secondary strength,
  *   byte 2 chroma primary strength, 3 chroma secondary strength,
- *   byte 4 luma damping (8-bit scale), bytes 5..7 unused. */
+ *   byte 4 luma damping (8-bit scale),
+ *   byte 5 skip-condition bits of the presets (section 4): bit 0 luma,
+ *          bit 1 chroma; bytes 6..7 unused. */
 #define CDEF_REF_PARAM_BYTES 8
 
 /* Filters one 4:2:0 frame (section 3): luma w x h, chroma w/2 x h/2.
@@ -91,6 +93,19 @@ int cdef_ref_filter_frame(int w, int h, int bitdepth,
                           uint16_t *oy, ptrdiff_t oys,
                           uint16_t *ou, ptrdiff_t ous,
                           uint16_t *ov, ptrdiff_t ovs);
+
+/* The filter with the skip semantics of section 4 (readings R18-R20 in
+ * cdef_ref.c): `coded` marks the 8x8 luma blocks with coded residual
+ * ((h/8) x (w/8) bytes, nonzero = coded; NULL = all coded). */
+int cdef_ref_filter_frame_coded(int w, int h, int bitdepth,
+                                const uint16_t *y, ptrdiff_t ys,
+                                const uint16_t *u, ptrdiff_t us,
+                                const uint16_t *v, ptrdiff_t vs,
+                                const uint8_t *params, const uint8_t *coded,
+                                const uint8_t *dir, const int32_t *var,
+                                uint16_t *oy, ptrdiff_t oys,
+                                uint16_t *ou, ptrdiff_t ous,
+                                uint16_t *ov, ptrdiff_t ovs);
 
 /* Section 5, two-pass search, first pass: for each filter block b and each of
  * the 64 (primary 0..15) x (secondary {0,1,2,4}) pairs, the SSE between the

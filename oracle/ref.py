@@ -79,6 +79,10 @@ def lib():
             [C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 3
             + [_u8p, _u8p, _i32p] + [_u16p, C.c_ssize_t] * 3)
         L.cdef_ref_filter_frame.restype = C.c_int
+        L.cdef_ref_filter_frame_coded.argtypes = (
+            [C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 3
+            + [_u8p, C.c_void_p, _u8p, _i32p] + [_u16p, C.c_ssize_t] * 3)
+        L.cdef_ref_filter_frame_coded.restype = C.c_int
         L.cdef_ref_distortion.argtypes = (
             [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6
             + [_i64p, _i64p])
@@ -159,17 +163,23 @@ def find_dir(luma, bitdepth: int):
     return dirs, var
 
 
-def filter_frame(y, u, v, bitdepth: int, params, dirs=None, var=None):
-    """Filter a 4:2:0 frame.  params: uint8 array (fb_rows, fb_cols, 8)."""
+def filter_frame(y, u, v, bitdepth: int, params, dirs=None, var=None, coded=None):
+    """Filter a 4:2:0 frame.  params: uint8 array (fb_rows, fb_cols, 8);
+    coded: optional (h/8, w/8) array, nonzero where the 8x8 block has coded
+    residual (section 4 skip semantics; None = all coded)."""
     y, u, v = _u16(y), _u16(u), _u16(v)
     h, w = y.shape
     if dirs is None:
         dirs, var = find_dir(y, bitdepth)
     prm = np.ascontiguousarray(params, dtype=np.uint8)
+    cod = None if coded is None else np.ascontiguousarray(coded, dtype=np.uint8)
+    if cod is not None and cod.shape != (h // 8, w // 8):
+        raise ValueError("coded map shape")
     oy, ou, ov = np.zeros_like(y), np.zeros_like(u), np.zeros_like(v)
-    rc = lib().cdef_ref_filter_frame(
+    rc = lib().cdef_ref_filter_frame_coded(
         w, h, bitdepth, y, w, u, u.shape[1], v, v.shape[1],
-        prm.reshape(-1), np.ascontiguousarray(dirs, np.uint8).reshape(-1),
+        prm.reshape(-1), None if cod is None else cod.ctypes.data,
+        np.ascontiguousarray(dirs, np.uint8).reshape(-1),
         np.ascontiguousarray(var, np.int32).reshape(-1),
         oy, w, ou, ou.shape[1], ov, ov.shape[1])
     if rc != 0:

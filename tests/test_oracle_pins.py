@@ -740,3 +740,94 @@ def test_refined_selection_cost_not_above_greedy(ref):
         assert r["cost"] <= g["cost"]
     r = ref.select_presets_refined(dl, dc, 0, 8)
     assert r["cost"] == 0 and r["npresets"] == 2
+
+
+# --------------------------------------------------------------- section 4: skip semantics
+def _skip_case(seed=11, w=192, h=128, bd=8):
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(seed)
+    f = synth.make_frame(w, h, bd, 32, seed=seed)
+    params = synth.random_params(rng, w, h)
+    params[..., 0] = np.maximum(params[..., 0], 3)      # every block really filters
+    params[..., 2] = np.maximum(params[..., 2], 3)
+    return f, params, rng
+
+
+def _block(planes, fby, fbx, sub=0):
+    s = 64 >> sub
+    return planes[sub > 0 and 1 or 0][fby * s:(fby + 1) * s, fbx * s:(fbx + 1) * s]
+
+
+def test_skipped_filter_block_is_not_filtered(ref):
+    """Section 4: a filter block without coded residual has CDEF disabled,
+    whatever its parameters and skip-condition bits."""
+    f, params, _ = _skip_case()
+    params[..., 5] = 3
+    coded = np.ones((f.height // 8, f.width // 8), np.uint8)
+    coded[0:8, 8:16] = 0                                   # filter block (0, 1) has none
+    out = ref.filter_frame(*f.rec, 8, params, coded=coded)
+    full = ref.filter_frame(*f.rec, 8, params)
+    assert np.array_equal(out[0][0:64, 64:128], f.rec[0][0:64, 64:128])
+    for k in (1, 2):
+        assert np.array_equal(out[k][0:32, 32:64], f.rec[k][0:32, 32:64])
+    assert not np.array_equal(full[0][0:64, 64:128], f.rec[0][0:64, 64:128])
+    # other filter blocks are untouched by the map
+    assert np.array_equal(out[0][:, 128:], full[0][:, 128:])
+
+
+def test_uncoded_8x8_filtered_only_with_skip_condition(ref):
+    """Section 4: in a coded filter block an 8x8 block without residual is
+    filtered only when the preset's skip-condition bit is set (per plane
+    group; chroma follows the co-located luma block)."""
+    f, params, _ = _skip_case()
+    coded = np.ones((f.height // 8, f.width // 8), np.uint8)
+    coded[2, 3] = 0                                        # luma rows 16..23, cols 24..31
+    params[..., 5] = 0
+    off = ref.filter_frame(*f.rec, 8, params, coded=coded)
+    full = ref.filter_frame(*f.rec, 8, params)
+    assert np.array_equal(off[0][16:24, 24:32], f.rec[0][16:24, 24:32])
+    assert np.array_equal(off[1][8:12, 12:16], f.rec[1][8:12, 12:16])
+    m = np.ones(off[0].shape, bool)
+    m[16:24, 24:32] = False
+    assert np.array_equal(off[0][m], full[0][m])
+    params[..., 5] = 1                                     # luma skip condition only
+    lum = ref.filter_frame(*f.rec, 8, params, coded=coded)
+    assert np.array_equal(lum[0], full[0])
+    assert np.array_equal(lum[1][8:12, 12:16], f.rec[1][8:12, 12:16])
+    params[..., 5] = 2                                     # chroma only
+    chro = ref.filter_frame(*f.rec, 8, params, coded=coded)
+    assert np.array_equal(chro[1], full[1]) and np.array_equal(chro[2], full[2])
+    assert np.array_equal(chro[0][16:24, 24:32], f.rec[0][16:24, 24:32])
+
+
+def test_zero_strengths_with_skip_condition_mean_19_and_7(ref):
+    """Section 4: (0, 0) with the skip-condition bit set filters with primary
+    19 and secondary 7; without it, (0, 0) is the identity."""
+    f, params, _ = _skip_case(seed=12)
+    params[..., 0:4] = 0
+    params[..., 5] = 0
+    ident = ref.filter_frame(*f.rec, 8, params)
+    assert all(np.array_equal(a, b) for a, b in zip(ident, f.rec))
+    params[..., 5] = 3
+    mapped = ref.filter_frame(*f.rec, 8, params)
+    explicit = params.copy()
+    explicit[..., 5] = 0
+    explicit[..., 0], explicit[..., 1], explicit[..., 2], explicit[..., 3] = 19, 7, 19, 7
+    assert all(np.array_equal(a, b) for a, b in zip(mapped, ref.filter_frame(*f.rec, 8, explicit)))
+    assert not np.array_equal(mapped[0], f.rec[0])
+
+
+def test_all_coded_map_equals_no_map(ref):
+    f, params, rng = _skip_case(seed=13, bd=10)
+    params[..., 5] = rng.integers(0, 4, params.shape[:2])
+    coded = np.ones((f.height // 8, f.width // 8), np.uint8) * 7
+    a = ref.filter_frame(*f.rec, 10, params, coded=coded)
+    b = ref.filter_frame(*f.rec, 10, params)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+
+
+def test_skip_bits_out_of_range_rejected(ref):
+    f, params, _ = _skip_case(seed=14)
+    params[0, 0, 5] = 4
+    with pytest.raises(ValueError):
+        ref.filter_frame(*f.rec, 8, params)
