@@ -65,12 +65,18 @@ typedef struct {
  *   sec_y, sec_uv : secondary strength S^(s) in {0, 1, 2, 4} (7 accepted)
  *   damping       : luma damping D at the 8-bit scale, 3..6; chroma uses
  *                   D - 1 (section 3.2)
+ *   skip          : the preset's skip-condition bits (section 4): bit 0
+ *                   luma, bit 1 chroma; 0..3.  With a bit set, strengths
+ *                   (0, 0) of that plane group stand for (19, 7), and (with
+ *                   cdef_filter_frame_coded) 8x8 blocks without coded
+ *                   residual are filtered too.
  * Strengths are the 8-bit values; they are scaled by 2^(bitdepth-8) inside
  * (section 3.2).  8 bytes, no padding surprises. */
 typedef struct {
     uint8_t pri_y, sec_y, pri_uv, sec_uv;
     uint8_t damping;
-    uint8_t reserved[3];
+    uint8_t skip;
+    uint8_t reserved[2];
 } cdef_fb_params;
 
 /* One preset of the frame header (section 4), without the skip-condition
@@ -133,6 +139,18 @@ int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in,
                       const cdef_fb_params *params, const uint8_t *dir,
                       const int32_t *var, const cdef_frame *out,
                       void *cuda_stream);
+
+/* The filter with the skip semantics of section 4 (fused direction search):
+ *   coded : DEVICE (H/8) x (W/8) bytes, row-major, nonzero where the 8x8
+ *           luma block has coded residual (the 4:2:0 chroma 4x4 block
+ *           follows its co-located luma block); required.
+ * A filter block without any coded 8x8 block is copied unfiltered; in the
+ * others an 8x8 block without coded residual is copied unfiltered unless
+ * its plane group's skip-condition bit (params.skip) is set.  Otherwise as
+ * cdef_filter_frame (which treats every 8x8 block as coded). */
+int cdef_filter_frame_coded(cdef_ctx *ctx, const cdef_frame *in,
+                            const cdef_fb_params *params, const uint8_t *coded,
+                            const cdef_frame *out, void *cuda_stream);
 
 /* The same filter over n frames of possibly different sizes and bit depths
  * in one kernel launch (the fused direction search is always used).

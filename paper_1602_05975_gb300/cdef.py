@@ -74,6 +74,8 @@ def load():
     L.cdef_find_dir.argtypes = [vp, C.POINTER(Plane), i32, vp, vp, vp]
     L.cdef_filter_frame.argtypes = [vp, C.POINTER(FrameDesc), vp, vp, vp,
                                     C.POINTER(FrameDesc), vp]
+    L.cdef_filter_frame_coded.argtypes = [vp, C.POINTER(FrameDesc), vp, vp,
+                                          C.POINTER(FrameDesc), vp]
     L.cdef_filter_frames.argtypes = [vp, i32, C.POINTER(FrameDesc), C.POINTER(vp),
                                      C.POINTER(FrameDesc), vp]
     L.cdef_search_strengths.argtypes = [vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc),
@@ -88,7 +90,8 @@ def load():
     L.cdef_strerror.restype = C.c_char_p
     L.cdef_version.restype = C.c_char_p
     for name in ("cdef_ctx_create", "cdef_ctx_destroy", "cdef_ctx_status", "cdef_find_dir",
-                 "cdef_filter_frame", "cdef_filter_frames", "cdef_search_strengths",
+                 "cdef_filter_frame", "cdef_filter_frame_coded", "cdef_filter_frames",
+                 "cdef_search_strengths",
                  "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap",
                  "cdef_ctx_set_search_refine"):
         getattr(L, name).restype = C.c_int
@@ -293,6 +296,16 @@ def cdef_filter_frame(ctx: Context, src: Frame, params: torch.Tensor, out: Frame
         ctx.handle, C.byref(di), params.data_ptr(),
         None if dirs is None else dirs.data_ptr(), None if var is None else var.data_ptr(),
         C.byref(do), _stream_ptr(stream)), "cdef_filter_frame")
+
+
+def cdef_filter_frame_coded(ctx: Context, src: Frame, params: torch.Tensor, coded: torch.Tensor,
+                            out: Frame, stream=None):
+    """The filter with section 4's skip semantics; `coded` is a uint8 CUDA
+    tensor of (H/8) x (W/8) coded-residual flags."""
+    di, do = src.desc(), out.desc()
+    _check(ctx._lib.cdef_filter_frame_coded(ctx.handle, C.byref(di), params.data_ptr(),
+                                            coded.data_ptr(), C.byref(do), _stream_ptr(stream)),
+           "cdef_filter_frame_coded")
 
 
 def cdef_filter_frames(ctx: Context, srcs, params, outs, stream=None):

@@ -161,8 +161,9 @@ namespace {
 
 int fill_filter_frame(FilterFrameDev &d, const cdef_frame *in, const cdef_frame *out,
                       const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
-                      int block_start)
+                      int block_start, const uint8_t *coded = nullptr)
 {
+    d.coded = coded;
     const cdef_plane *pi[3] = {&in->y, &in->u, &in->v};
     const cdef_plane *po[3] = {&out->y, &out->u, &out->v};
     for (int i = 0; i < 3; i++) {
@@ -330,9 +331,11 @@ int cdef_find_dir(cdef_ctx *ctx, const cdef_plane *luma, int32_t bitdepth, uint8
                                        static_cast<cudaStream_t>(cuda_stream)));
 }
 
-int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params,
-                      const uint8_t *dir, const int32_t *var, const cdef_frame *out,
-                      void *cuda_stream)
+namespace {
+
+int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params,
+               const uint8_t *dir, const int32_t *var, const uint8_t *coded,
+               const cdef_frame *out, void *cuda_stream)
 {
     if (!ctx || !in || !out || !params) return CDEF_ERR_ARG;
     if ((dir == nullptr) != (var == nullptr)) return CDEF_ERR_ARG;
@@ -345,10 +348,26 @@ int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params 
     FilterBatch<1> b;
     b.n = 1;
     b.total_blocks = fb_count(in);
-    if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0))) return rc;
+    if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0, coded))) return rc;
     unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
     return cuda_status(launch_filter_single(b, ctx->status, work, ctx->overlap,
                                             static_cast<cudaStream_t>(cuda_stream)));
+}
+
+}  // namespace
+
+int cdef_filter_frame(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params,
+                      const uint8_t *dir, const int32_t *var, const cdef_frame *out,
+                      void *cuda_stream)
+{
+    return filter_one(ctx, in, params, dir, var, nullptr, out, cuda_stream);
+}
+
+int cdef_filter_frame_coded(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params,
+                            const uint8_t *coded, const cdef_frame *out, void *cuda_stream)
+{
+    if (!coded) return CDEF_ERR_ARG;
+    return filter_one(ctx, in, params, nullptr, nullptr, coded, out, cuda_stream);
 }
 
 int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,

@@ -30,6 +30,7 @@ struct FilterFrameDev {  // aligned as CUtensorMap requires
     const cdef_fb_params *params;    // B entries
     const uint8_t *dir;              // optional 8x8 maps (NULL: fused search)
     const int32_t *var;
+    const uint8_t *coded;            // optional 8x8 coded-residual map (NULL: all coded)
     int bitdepth;
     int fb_cols, fb_rows;
     int block_start;                 // first CTA index of this frame

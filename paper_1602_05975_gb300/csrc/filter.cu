@@ -56,7 +56,9 @@ struct FilterSmem {
     int cost[64][8];
     BlockC lb[64];
     BlockC cb;
+    BlockC bz;                                          // identity set (unfiltered blocks)
     uint8_t dir[64];
+    uint8_t coded[64];                                  // 8x8 block has coded residual
     int var[64];
     int blk[2];                                         // block id of each raw buffer
     alignas(8) uint64_t bar[2];
@@ -149,10 +151,22 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
 
     cdef_fb_params prm = F.params[fby * F.fb_cols + fbx];
     if (!valid_strengths(prm.pri_y, prm.sec_y) || !valid_strengths(prm.pri_uv, prm.sec_uv) ||
-        prm.damping < 3 || prm.damping > 6) {
+        prm.damping < 3 || prm.damping > 6 || prm.skip > 3) {
         if (tid == 0) atomicOr(status, kStatusBadParams);
         prm.pri_y = prm.sec_y = prm.pri_uv = prm.sec_uv = 0;  // identity, defined output
         prm.damping = 3;
+        prm.skip = 0;
+    }
+    // Section 4: strengths (0, 0) with the skip-condition bit set stand for
+    // primary 19 and secondary 7.
+    const bool skip_l = prm.skip & 1, skip_c = (prm.skip >> 1) & 1;
+    if (skip_l && prm.pri_y == 0 && prm.sec_y == 0) {
+        prm.pri_y = 19;
+        prm.sec_y = 7;
+    }
+    if (skip_c && prm.pri_uv == 0 && prm.sec_uv == 0) {
+        prm.pri_uv = 19;
+        prm.sec_uv = 7;
     }
 
     // does the 2-pixel halo of this block reach outside the frame?
@@ -175,10 +189,12 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         }
         __syncthreads();
     }
+    int coded = 0;
     if (tid < 64) {
         const int gby = fby * 8 + (tid >> 3), gbx = fbx * 8 + (tid & 7);
         int d = 0, v = 0;
         if (gby * 8 < H && gbx * 8 < W) {
+            coded = F.coded ? F.coded[gby * bw + gbx] != 0 : 1;
             if (fused) {
                 int best = 0, bc = sm.cost[tid][0];
 #pragma unroll
@@ -195,11 +211,17 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         }
         sm.dir[tid] = (uint8_t)d;
         sm.var[tid] = v;
+        sm.coded[tid] = (uint8_t)coded;
         sm.lb[tid] = make_block_consts(make_eff(prm.pri_y, prm.sec_y, prm.damping, false, v, sh8));
     }
     if (tid == 64)
         sm.cb = make_block_consts(make_eff(prm.pri_uv, prm.sec_uv, prm.damping, true, 0, sh8));
-    __syncthreads();
+    if (tid == 65) sm.bz = make_block_consts(make_eff(0, 0, prm.damping, false, 0, sh8));
+    // Section 4: a filter block without coded residual is not filtered; in
+    // one that has some, an 8x8 block without it is filtered only when its
+    // plane group's skip-condition bit is set (chroma: the co-located luma
+    // block's flag).
+    const bool any_coded = __syncthreads_or(coded);
 
     const int warp = tid >> 5, lane = tid & 31;
     if (F.bitdepth > 10) {
@@ -225,8 +247,9 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
                 return w2 ? (int)(w2 - kBias) : -1;
             };
             const int r = 2 + rr, c = pl ? 2 + cc : 8 + cc;
+            const bool on = any_coded && (sm.coded[blk] || (pl ? skip_c : skip_l));
             reinterpret_cast<T *>(F.p[pl].out + (int64_t)gy * F.p[pl].out_pitch)[gx] =
-                (T)filter_scalar(px, r, c, sm.dir[blk], e);
+                (T)(on ? filter_scalar(px, r, c, sm.dir[blk], e) : px(r, c));
         }
         return;
     }
@@ -247,7 +270,11 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         const int pitch = luma ? kLumaPitch : kChromaPitch;
         const uint32_t *base = luma ? sm.t.le + (2 + warp * 8) * kLumaPitch + 4 + bx * 4 + sub
                                     : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
-        const BlockC bc = luma ? sm.lb[blk] : sm.cb;
+        // a block that is not filtered (section 4) takes the identity set
+        // (strengths 0: every tap clamps to x, no clip), so the loop below
+        // needs no per-word test
+        const bool on = any_coded && (sm.coded[blk] || (luma ? skip_l : skip_c));
+        const BlockC bc = !on ? sm.bz : luma ? sm.lb[blk] : sm.cb;
         const unsigned fl = inside ? bc.flags : 0u;
         const bool any_p = __any_sync(0xffffffffu, fl & 1), any_s = __any_sync(0xffffffffu, fl & 2);
         const bool any_clip = __any_sync(0xffffffffu, (fl & 3) == 3);

@@ -438,3 +438,56 @@ def test_search_refine_rejects_bad_pass_counts(cdef, ctx):
     for p in (-1, 17):
         with pytest.raises(cdef.CdefError):
             ctx.set_search_refine(p)
+
+
+# --------------------------------------------------------------- section 4 skip semantics
+@pytest.mark.parametrize("w,h,bd,density", [(200, 136, 8, 0.5), (352, 288, 10, 0.2),
+                                            (136, 72, 12, 0.7), (640, 360, 8, 0.0),
+                                            (64, 64, 10, 1.0)])
+def test_filter_coded_parity(cdef, ctx, ref, w, h, bd, density):
+    """Coded-residual maps, skip-condition bits and the (0,0)+skip mapping:
+    every output sample equals the oracle's."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(w * 3 + h + bd)
+    f = synth.make_frame(w, h, bd, 32, seed=800 + w)
+    params = synth.random_params(rng, w, h)
+    params[..., 5] = rng.integers(0, 4, params.shape[:2])
+    zero = rng.random(params.shape[:2]) < 0.3                 # some (0, 0) presets
+    params[zero, 0] = 0
+    params[zero, 1] = 0
+    coded = (rng.random((h // 8, w // 8)) < density).astype(np.uint8)
+    coded[:8, :8] = 0                                          # a skipped filter block
+    inp = cdef.frame_from_numpy(f.rec, bd)
+    out = cdef.alloc_frame(w, h, bd, fill=0)
+    cmap = torch.from_numpy(coded.reshape(-1)).cuda()
+    cdef.cdef_filter_frame_coded(ctx, inp, cdef.params_tensor(params), cmap, out)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    _assert_frames_equal(out.to_numpy(), ref.filter_frame(*f.rec, bd, params, coded=coded))
+
+
+def test_filter_skip_bits_without_map(cdef, ctx, ref):
+    """cdef_filter_frame (every block coded) honours the (0,0)+skip mapping."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(5)
+    f = synth.make_frame(200, 136, 10, 32, seed=830)
+    params = synth.random_params(rng, 200, 136)
+    params[..., 0:4] = 0
+    params[..., 5] = rng.integers(0, 4, params.shape[:2])
+    _assert_frames_equal(_gpu_filter(cdef, ctx, f.rec, 10, params),
+                         ref.filter_frame(*f.rec, 10, params))
+
+
+def test_filter_bad_skip_bits_flagged(cdef, ctx):
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(64, 64, 8, 32, seed=831)
+    params = f.params.copy()
+    params[..., 5] = 4
+    inp = cdef.frame_from_numpy(f.rec, 8)
+    out = cdef.alloc_frame(64, 64, 8, fill=0)
+    cdef.cdef_filter_frame(ctx, inp, cdef.params_tensor(params), out)
+    torch.cuda.synchronize()
+    assert ctx.status() != 0
+    assert ctx.status() == 0          # cleared by the read
+    got = out.to_numpy()
+    assert all(np.array_equal(g, e) for g, e in zip(got, f.rec))
