@@ -638,3 +638,209 @@ int cdef_ref_select_presets_refined(int nblocks, const int64_t *dist_luma,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Section 5 with section 4's skip semantics                                */
+/* ------------------------------------------------------------------------ */
+
+/* Reading R21.  The search covers the 128 combinations of a plane group
+ * that section 5 counts (16 primary x 4 secondary strengths x the skip-
+ * condition bit), index q = k * 64 + p * 4 + s.  D_{b,q} is the squared
+ * error of what the decoder outputs for filter block b with that preset
+ * (cdef_ref_filter_frame_coded): a pixel of 8x8 block j is filtered when
+ * the filter block has coded residual and (j is coded or k = 1); strengths
+ * (0, 0) with k = 1 stand for (19, 7).  A filter block without coded
+ * residual is never filtered: its entries are all the unfiltered SSE, and
+ * skipped[b] = 1 (it signals no preset id). */
+static int64_t block_sse_coded(const uint16_t *rec, ptrdiff_t rs, const uint16_t *src,
+                               ptrdiff_t ss, int pw, int ph, int sub, int bitdepth,
+                               int fby, int fbx, int pri, int sec, int k, int damping,
+                               const uint8_t *dir, const int32_t *var, int bw,
+                               const uint8_t *coded, int fb_coded)
+{
+    int bs = 8 >> sub, fbs = 64 >> sub;
+    int64_t sse = 0;
+    for (int i = fby * fbs; i < (fby + 1) * fbs && i < ph; i++) {
+        for (int j = fbx * fbs; j < (fbx + 1) * fbs && j < pw; j++) {
+            int b8 = (i / bs) * bw + (j / bs);
+            int on = fb_coded && (!coded || coded[b8] || k);
+            int64_t yv = rec[(ptrdiff_t)i * rs + j];
+            if (on) {
+                cdef_ref_eff_params e;
+                cdef_ref_block_params(pri, sec, damping, sub, bitdepth, sub ? 0 : var[b8], &e);
+                yv = cdef_ref_filter_sample(rec, pw, ph, rs, i, j, dir[b8], &e);
+            }
+            int64_t err = yv - (int64_t)src[(ptrdiff_t)i * ss + j];
+            sse += err * err;
+        }
+    }
+    return sse;
+}
+
+int cdef_ref_distortion_coded(int w, int h, int bitdepth, int damping,
+                              const uint16_t *ry, ptrdiff_t rys,
+                              const uint16_t *ru, ptrdiff_t rus,
+                              const uint16_t *rv, ptrdiff_t rvs,
+                              const uint16_t *sy, ptrdiff_t sys,
+                              const uint16_t *su, ptrdiff_t sus,
+                              const uint16_t *sv, ptrdiff_t svs,
+                              const uint8_t *coded, int64_t *dist_luma,
+                              int64_t *dist_chroma, uint8_t *skipped)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    if (damping < 3 || damping > 6)
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    uint8_t *dir = (uint8_t *)malloc((size_t)bw * bh);
+    int32_t *var = (int32_t *)malloc((size_t)bw * bh * sizeof(int32_t));
+    if (!dir || !var) {
+        free(dir);
+        free(var);
+        return -1;
+    }
+    cdef_ref_find_dir(ry, w, h, rys, bitdepth, dir, var);
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    for (int fby = 0; fby < fb_rows; fby++) {
+        for (int fbx = 0; fbx < fb_cols; fbx++) {
+            int b = fby * fb_cols + fbx;
+            int fb_coded = fb_has_coded(coded, bw, bh, fby, fbx);
+            skipped[b] = (uint8_t)!fb_coded;
+            for (int k = 0; k < 2; k++) {
+                for (int p = 0; p < 16; p++) {
+                    for (int s = 0; s < 4; s++) {
+                        int q = k * 64 + p * 4 + s;
+                        int pri = p, sec = sec_values[s];
+                        if (k && p == 0 && s == 0) {
+                            pri = 19;
+                            sec = 7;
+                        }
+                        dist_luma[b * 128 + q] =
+                            block_sse_coded(ry, rys, sy, sys, w, h, 0, bitdepth, fby, fbx, pri,
+                                            sec, k, damping, dir, var, bw, coded, fb_coded);
+                        dist_chroma[b * 128 + q] =
+                            block_sse_coded(ru, rus, su, sus, w / 2, h / 2, 1, bitdepth, fby,
+                                            fbx, pri, sec, k, damping, dir, var, bw, coded,
+                                            fb_coded) +
+                            block_sse_coded(rv, rvs, sv, svs, w / 2, h / 2, 1, bitdepth, fby,
+                                            fbx, pri, sec, k, damping, dir, var, bw, coded,
+                                            fb_coded);
+                    }
+                }
+            }
+        }
+    }
+    free(dir);
+    free(var);
+    return 0;
+}
+
+/* Preset selection over tables of `width` combinations per plane group
+ * (presets t = luma_q * width + chroma_q), blocks with skipped[b] set left
+ * out of every sum and of B.  The same rules as cdef_ref_select_presets
+ * (greedy, R16) and cdef_ref_refine_presets (R17), restated for any width. */
+static int64_t gen_dist(const int64_t *dl, const int64_t *dc, int width, int b, int t)
+{
+    return dl[(int64_t)b * width + t / width] + dc[(int64_t)b * width + t % width];
+}
+
+static int64_t gen_total(int nblocks, const int64_t *dl, const int64_t *dc, int width,
+                         const uint8_t *skipped, const int32_t *set, int n)
+{
+    int64_t tot = 0;
+    for (int b = 0; b < nblocks; b++) {
+        if (skipped && skipped[b])
+            continue;
+        int64_t m = gen_dist(dl, dc, width, b, set[0]);
+        for (int k = 1; k < n; k++)
+            m = min64(m, gen_dist(dl, dc, width, b, set[k]));
+        tot += m;
+    }
+    return tot;
+}
+
+int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
+                                    const int64_t *dist_chroma, int width,
+                                    const uint8_t *skipped, int64_t lambda, int max_passes,
+                                    int32_t *presets, int32_t *npresets,
+                                    uint8_t *block_ids, int64_t *cost)
+{
+    if (nblocks <= 0 || (width != 64 && width != 128) || max_passes < 0)
+        return -1;
+    const int ntuples = width * width;
+    int coded_blocks = 0;
+    for (int b = 0; b < nblocks; b++)
+        coded_blocks += !(skipped && skipped[b]);
+    /* greedy */
+    int32_t greedy[8];
+    int64_t totals[8];
+    for (int n = 1; n <= 8; n++) {
+        int best_t = -1;
+        int64_t best_total = 0;
+        for (int t = 0; t < ntuples; t++) {
+            greedy[n - 1] = t;
+            int64_t tot = gen_total(nblocks, dist_luma, dist_chroma, width, skipped, greedy, n);
+            if (best_t < 0 || tot < best_total) {
+                best_t = t;
+                best_total = tot;
+            }
+        }
+        greedy[n - 1] = best_t;
+        totals[n - 1] = best_total;
+    }
+    /* re-optimisation per set size, then N by J */
+    int best_n = 0;
+    int64_t best_j = 0;
+    int32_t best_set[8] = {0};
+    for (int lg = 0; lg < 4; lg++) {
+        const int n = 1 << lg;
+        int32_t set[8];
+        for (int k = 0; k < n; k++)
+            set[k] = greedy[k];
+        int64_t tot = totals[n - 1];
+        for (int pass = 0; pass < max_passes; pass++) {
+            int changed = 0;
+            for (int k = 0; k < n; k++) {
+                const int32_t old = set[k];
+                int best_t = old;
+                int64_t best_total = gen_total(nblocks, dist_luma, dist_chroma, width, skipped,
+                                               set, n);
+                for (int t = 0; t < ntuples; t++) {
+                    set[k] = t;
+                    int64_t v = gen_total(nblocks, dist_luma, dist_chroma, width, skipped, set, n);
+                    if (v < best_total || (v == best_total && best_t != old && t < best_t)) {
+                        best_t = t;
+                        best_total = v;
+                    }
+                }
+                set[k] = best_t;
+                if (best_t != old)
+                    changed = 1;
+                tot = best_total;
+            }
+            if (!changed)
+                break;
+        }
+        const int64_t j = tot + lambda * coded_blocks * lg;
+        if (best_n == 0 || j < best_j) {
+            best_n = n;
+            best_j = j;
+            for (int k = 0; k < n; k++)
+                best_set[k] = set[k];
+        }
+    }
+    for (int k = 0; k < 8; k++)
+        presets[k] = k < best_n ? best_set[k] : greedy[k];
+    *npresets = best_n;
+    *cost = best_j;
+    for (int b = 0; b < nblocks; b++) {
+        int id = 0;
+        if (!(skipped && skipped[b]))
+            for (int k = 1; k < best_n; k++)
+                if (gen_dist(dist_luma, dist_chroma, width, b, best_set[k]) <
+                    gen_dist(dist_luma, dist_chroma, width, b, best_set[id]))
+                    id = k;
+        block_ids[b] = (uint8_t)id;
+    }
+    return 0;
+}

@@ -146,6 +146,31 @@ int cdef_ref_select_presets_refined(int nblocks, const int64_t *dist_luma,
                                     int32_t *npresets, uint8_t *block_ids,
                                     int64_t *cost);
 
+/* Section 5 with section 4's skip semantics (reading R21 in cdef_ref.c):
+ * per filter block 128 luma and 128 chroma combinations q = k*64 + p*4 + s
+ * (k the skip-condition bit; (0,0) with k = 1 is (19,7)), computed on the
+ * decoder's output for `coded` ((h/8) x (w/8) bytes, nonzero = coded
+ * residual; NULL = all coded).  skipped[b] = 1 for filter blocks without
+ * coded residual (entries = unfiltered SSE). */
+int cdef_ref_distortion_coded(int w, int h, int bitdepth, int damping,
+                              const uint16_t *ry, ptrdiff_t rys,
+                              const uint16_t *ru, ptrdiff_t rus,
+                              const uint16_t *rv, ptrdiff_t rvs,
+                              const uint16_t *sy, ptrdiff_t sys,
+                              const uint16_t *su, ptrdiff_t sus,
+                              const uint16_t *sv, ptrdiff_t svs,
+                              const uint8_t *coded, int64_t *dist_luma,
+                              int64_t *dist_chroma, uint8_t *skipped);
+
+/* Greedy search, optional re-optimisation, N by J and block ids over tables
+ * of `width` (64 or 128) combinations per plane group; blocks with
+ * skipped[b] set (or none when NULL) are left out of every sum and of B. */
+int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
+                                    const int64_t *dist_chroma, int width,
+                                    const uint8_t *skipped, int64_t lambda, int max_passes,
+                                    int32_t *presets, int32_t *npresets,
+                                    uint8_t *block_ids, int64_t *cost);
+
 #ifdef __cplusplus
 }
 #endif

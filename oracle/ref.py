@@ -99,6 +99,14 @@ def lib():
             C.c_int, _i64p, _i64p, C.c_int64, C.c_int, _i32p, C.POINTER(C.c_int32),
             _u8p, C.POINTER(C.c_int64)]
         L.cdef_ref_select_presets_refined.restype = C.c_int
+        L.cdef_ref_distortion_coded.argtypes = (
+            [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6
+            + [C.c_void_p, _i64p, _i64p, _u8p])
+        L.cdef_ref_distortion_coded.restype = C.c_int
+        L.cdef_ref_select_presets_general.argtypes = [
+            C.c_int, _i64p, _i64p, C.c_int, C.c_void_p, C.c_int64, C.c_int, _i32p,
+            C.POINTER(C.c_int32), _u8p, C.POINTER(C.c_int64)]
+        L.cdef_ref_select_presets_general.restype = C.c_int
         _lib = L
     return _lib
 
@@ -255,4 +263,50 @@ def search_strengths(rec, src, bitdepth: int, damping: int, lam: int, refine_pas
         out = select_presets(dl, dc, lam)
     out["dist_luma"] = dl
     out["dist_chroma"] = dc
+    return out
+
+
+def distortion_coded(rec, src, bitdepth: int, damping: int, coded=None):
+    """Section 5 with section 4's skip semantics (reading R21): per filter
+    block 128 luma and 128 chroma SSE values, and the skipped-block flags."""
+    ry, ru, rv = (_u16(p) for p in rec)
+    sy, su, sv = (_u16(p) for p in src)
+    h, w = ry.shape
+    nb = ((h + 63) // 64) * ((w + 63) // 64)
+    cod = None if coded is None else np.ascontiguousarray(coded, dtype=np.uint8)
+    dl = np.zeros(nb * 128, np.int64)
+    dc = np.zeros(nb * 128, np.int64)
+    sk = np.zeros(nb, np.uint8)
+    rc = lib().cdef_ref_distortion_coded(
+        w, h, bitdepth, damping, ry, w, ru, ru.shape[1], rv, rv.shape[1],
+        sy, w, su, su.shape[1], sv, sv.shape[1], None if cod is None else cod.ctypes.data,
+        dl, dc, sk)
+    if rc != 0:
+        raise ValueError("oracle rejected distortion_coded arguments")
+    return dl.reshape(nb, 128), dc.reshape(nb, 128), sk
+
+
+def select_presets_general(dist_luma, dist_chroma, width: int, skipped, lam: int,
+                           max_passes: int = 0):
+    dl = np.ascontiguousarray(dist_luma, np.int64).reshape(-1)
+    dc = np.ascontiguousarray(dist_chroma, np.int64).reshape(-1)
+    nb = dl.size // width
+    sk = None if skipped is None else np.ascontiguousarray(skipped, np.uint8)
+    presets = np.zeros(8, np.int32)
+    n = C.c_int32(0)
+    ids = np.zeros(nb, np.uint8)
+    cost = C.c_int64(0)
+    if lib().cdef_ref_select_presets_general(nb, dl, dc, width,
+                                             None if sk is None else sk.ctypes.data, lam,
+                                             max_passes, presets, C.byref(n), ids,
+                                             C.byref(cost)) != 0:
+        raise ValueError("oracle rejected select_presets_general arguments")
+    return dict(presets=presets, npresets=n.value, block_ids=ids, cost=cost.value)
+
+
+def search_strengths_coded(rec, src, bitdepth: int, damping: int, lam: int, coded=None,
+                           refine_passes: int = 0):
+    dl, dc, sk = distortion_coded(rec, src, bitdepth, damping, coded)
+    out = select_presets_general(dl, dc, 128, sk, lam, refine_passes)
+    out.update(dist_luma=dl, dist_chroma=dc, skipped=sk)
     return out

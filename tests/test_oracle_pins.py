@@ -831,3 +831,84 @@ def test_skip_bits_out_of_range_rejected(ref):
     params[0, 0, 5] = 4
     with pytest.raises(ValueError):
         ref.filter_frame(*f.rec, 8, params)
+
+
+# --------------------------------------------------------------- section 5 with section 4's skip bits
+def _sse_blocks(out, src, sub):
+    s = 64 >> sub
+    planes = (0,) if sub == 0 else (1, 2)
+    h, w = out[planes[0]].shape
+    res = []
+    for by in range(-(-h // s)):
+        for bx in range(-(-w // s)):
+            e = 0
+            for k in planes:
+                d = out[k][by * s:(by + 1) * s, bx * s:(bx + 1) * s].astype(np.int64) - \
+                    src[k][by * s:(by + 1) * s, bx * s:(bx + 1) * s].astype(np.int64)
+                e += int((d * d).sum())
+            res.append(e)
+    return res
+
+
+@pytest.mark.parametrize("bd", [8, 10])
+def test_coded_distortion_is_sse_of_decoder_output(ref, bd):
+    """Each of the 128 entries is the squared error of what the decoder
+    outputs (section 4 semantics) for that preset."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(192, 72, bd, 32, seed=40 + bd)
+    rng = np.random.default_rng(bd)
+    coded = (rng.random((9, 24)) < 0.5).astype(np.uint8)
+    coded[:, 16:] = 0                                     # filter blocks 2 and 5 skipped
+    dl, dc, sk = ref.distortion_coded(f.rec, f.src, bd, 5, coded)
+    assert list(sk) == [0, 0, 1, 0, 0, 1]
+    params = np.zeros(f.params.shape, np.uint8)
+    params[..., 4] = 5
+    for q in range(128):
+        k, p, s = q >> 6, (q & 63) >> 2, q & 3
+        params[..., 0] = params[..., 2] = p
+        params[..., 1] = params[..., 3] = (0, 1, 2, 4)[s]
+        params[..., 5] = 3 * k
+        out = ref.filter_frame(*f.rec, bd, params, coded=coded)
+        assert _sse_blocks(out, f.src, 0) == list(dl[:, q]), q
+        assert _sse_blocks(out, f.src, 1) == list(dc[:, q]), q
+    # skipped blocks: every entry is the unfiltered error
+    assert (dl[sk == 1] == dl[sk == 1][:, :1]).all()
+
+
+def test_coded_tables_with_every_block_coded(ref):
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(128, 64, 8, 16, seed=44)
+    dl, dc, sk = ref.distortion_coded(f.rec, f.src, 8, 4, None)
+    old_l, old_c = ref.distortion(f.rec, f.src, 8, 4)
+    assert not sk.any()
+    assert (dl[:, 1:64] == old_l[:, 1:]).all() and (dl[:, 65:] == old_l[:, 1:]).all()
+    assert (dc[:, 1:64] == old_c[:, 1:]).all() and (dc[:, 65:] == old_c[:, 1:]).all()
+    assert (dl[:, 0] == old_l[:, 0]).all()                # (0, 0), no skip bit: unfiltered
+    assert (dl[:, 64] != old_l[:, 0]).any()                # (0, 0) + skip: (19, 7)
+
+
+def test_general_selection_matches_width_64_functions(ref):
+    rng = np.random.default_rng(21)
+    dl = rng.integers(0, 400, (5, 64)).astype(np.int64)
+    dc = rng.integers(0, 400, (5, 64)).astype(np.int64)
+    for lam, passes in [(0, 0), (7, 0), (3, 4), (50, 16)]:
+        a = ref.select_presets_general(dl, dc, 64, None, lam, passes)
+        b = ref.select_presets_refined(dl, dc, lam, passes)
+        assert a["cost"] == b["cost"] and a["npresets"] == b["npresets"]
+        assert list(a["presets"]) == list(b["presets"])
+        assert np.array_equal(a["block_ids"], b["block_ids"])
+
+
+def test_skipped_blocks_leave_the_selection(ref):
+    """Blocks without coded residual signal no preset: their distortion is
+    constant and they count neither in the sums nor in B."""
+    rng = np.random.default_rng(22)
+    dl = rng.integers(0, 400, (6, 128)).astype(np.int64)
+    dc = rng.integers(0, 400, (6, 128)).astype(np.int64)
+    sk = np.array([0, 1, 0, 0, 1, 0], np.uint8)
+    full = ref.select_presets_general(dl, dc, 128, sk, 9, 2)
+    sub = ref.select_presets_general(dl[sk == 0], dc[sk == 0], 128, None, 9, 2)
+    assert full["cost"] == sub["cost"] and full["npresets"] == sub["npresets"]
+    assert list(full["presets"]) == list(sub["presets"])
+    assert list(full["block_ids"][sk == 0]) == list(sub["block_ids"])
+    assert (full["block_ids"][sk == 1] == 0).all()
