@@ -85,6 +85,16 @@ typedef struct {
     uint8_t pri_y, sec_y, pri_uv, sec_uv;
 } cdef_preset;
 
+/* One preset with its skip-condition bits (section 4): the strengths as in
+ * cdef_preset and skip = bit 0 luma, bit 1 chroma.  Strengths (0, 0) with
+ * the plane group's bit set stand for (19, 7).  Converts to cdef_fb_params
+ * field for field (pri/sec/skip). */
+typedef struct {
+    uint8_t pri_y, sec_y, pri_uv, sec_uv;
+    uint8_t skip;
+    uint8_t reserved[3];
+} cdef_preset_coded;
+
 typedef struct cdef_ctx cdef_ctx;
 
 /* Creates a context on CUDA device `device`.  It owns the library's device
@@ -199,6 +209,31 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
                           int64_t *dist_chroma, cdef_preset *presets,
                           int32_t *npresets, uint8_t *block_ids, int64_t *cost,
                           void *cuda_stream);
+
+/* The strength search with section 4's skip semantics (section 5 counts
+ * 16 x 4 x 2 = 128 combinations per plane group: the skip-condition bit is
+ * searched too).  For every filter block the 128 luma and 128 chroma
+ * entries q = skip * 64 + p * 4 + s are the squared error, against the
+ * source, of what cdef_filter_frame_coded outputs for that preset: with the
+ * bit clear the frame's 8x8 blocks without coded residual stay unfiltered,
+ * and (p, s) = (0, 0) with the bit set filters with (19, 7).  A filter
+ * block without coded residual is never filtered and signals no preset: all
+ * its entries are its unfiltered error, it is left out of the sums and of
+ * B in J, and its id is 0.  Presets are (luma q, chroma q) pairs, index
+ * luma_q * 128 + chroma_q; otherwise as cdef_search_strengths (greedy
+ * search, optional re-optimisation, N by J, ids).
+ *   coded        : HOST array of n DEVICE maps, (H/8) x (W/8) bytes each,
+ *                  nonzero where the 8x8 luma block has coded residual
+ *   dist_luma,
+ *   dist_chroma  : DEVICE, sum_i B_i * 128 int64 each, or both NULL
+ *   presets      : HOST, n*8 entries (first npresets[i] of frame i valid)
+ * Synchronises the stream before returning. */
+int cdef_search_strengths_coded(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
+                                const cdef_frame *src, const uint8_t *const *coded,
+                                const int32_t *damping, const int64_t *lambda,
+                                int64_t *dist_luma, int64_t *dist_chroma,
+                                cdef_preset_coded *presets, int32_t *npresets,
+                                uint8_t *block_ids, int64_t *cost, void *cuda_stream);
 
 /* Launch configuration of the strength search's distortion kernel (the
  * first pass of cdef_search_strengths).  No paper counterpart: it decides

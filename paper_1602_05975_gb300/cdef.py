@@ -50,6 +50,11 @@ class Preset(C.Structure):
                 ("sec_uv", C.c_uint8)]
 
 
+class PresetCoded(C.Structure):
+    _fields_ = [("pri_y", C.c_uint8), ("sec_y", C.c_uint8), ("pri_uv", C.c_uint8),
+                ("sec_uv", C.c_uint8), ("skip", C.c_uint8), ("reserved", C.c_uint8 * 3)]
+
+
 class Tuning(C.Structure):
     _fields_ = [("search_groups", C.c_int32), ("search_ctas_per_sm", C.c_int32),
                 ("reserved", C.c_int32 * 2)]
@@ -86,6 +91,9 @@ def load():
     L.cdef_ctx_set_overlap.argtypes = [vp, C.c_int]
     L.cdef_ctx_set_search_refine.argtypes = [vp, C.c_int]
     L.cdef_ctx_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.cdef_search_strengths_coded.argtypes = [
+        vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(vp), C.POINTER(i32),
+        C.POINTER(i64), vp, vp, C.POINTER(PresetCoded), C.POINTER(i32), vp, C.POINTER(i64), vp]
     L.cdef_strerror.argtypes = [C.c_int]
     L.cdef_strerror.restype = C.c_char_p
     L.cdef_version.restype = C.c_char_p
@@ -93,7 +101,7 @@ def load():
                  "cdef_filter_frame", "cdef_filter_frame_coded", "cdef_filter_frames",
                  "cdef_search_strengths",
                  "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap",
-                 "cdef_ctx_set_search_refine"):
+                 "cdef_ctx_set_search_refine", "cdef_search_strengths_coded"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -370,6 +378,42 @@ def cdef_search_strengths_noalloc(recs, srcs, damping, lambdas, block_ids: torch
         ps = [(p.pri_y, p.sec_y, p.pri_uv, p.sec_uv) for p in presets[i * 8:(i + 1) * 8]]
         out.append(dict(presets=ps, npresets=npre[i], cost=cost[i]))
     return out
+
+
+def cdef_search_strengths_coded(ctx: Context, recs, srcs, coded, damping, lambdas,
+                                block_ids: torch.Tensor, dist_luma: torch.Tensor | None = None,
+                                dist_chroma: torch.Tensor | None = None, stream=None):
+    """The 128-combination search with section 4's skip semantics; `coded`
+    is a list of uint8 CUDA tensors ((H/8) x (W/8) coded-residual flags).
+    Returns per frame: presets [(pri_y, sec_y, pri_uv, sec_uv, skip)]*8, N, J."""
+    n = len(recs)
+    ri = (FrameDesc * n)(*[f.desc() for f in recs])
+    si = (FrameDesc * n)(*[f.desc() for f in srcs])
+    cm = (C.c_void_p * n)(*[c.data_ptr() for c in coded])
+    damp = (C.c_int32 * n)(*damping)
+    lam = (C.c_int64 * n)(*lambdas)
+    presets = (PresetCoded * (8 * n))()
+    npre = (C.c_int32 * n)()
+    cost = (C.c_int64 * n)()
+    _check(ctx._lib.cdef_search_strengths_coded(
+        ctx.handle, n, ri, si, cm, damp, lam,
+        None if dist_luma is None else dist_luma.data_ptr(),
+        None if dist_chroma is None else dist_chroma.data_ptr(),
+        presets, npre, block_ids.data_ptr(), cost, _stream_ptr(stream)),
+        "cdef_search_strengths_coded")
+    out = []
+    for i in range(n):
+        ps = [(p.pri_y, p.sec_y, p.pri_uv, p.sec_uv, p.skip) for p in presets[i * 8:(i + 1) * 8]]
+        out.append(dict(presets=ps, npresets=npre[i], cost=cost[i]))
+    return out
+
+
+def preset_index_coded(p) -> int:
+    """(pri_y, sec_y, pri_uv, sec_uv, skip) -> luma_q * 128 + chroma_q with
+    q = skip_bit * 64 + pri * 4 + secondary index."""
+    ql = (p[4] & 1) * 64 + p[0] * 4 + SEC_VALUES.index(p[1])
+    qc = ((p[4] >> 1) & 1) * 64 + p[2] * 4 + SEC_VALUES.index(p[3])
+    return ql * 128 + qc
 
 
 def preset_index(p) -> int:

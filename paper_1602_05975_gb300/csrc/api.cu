@@ -29,7 +29,7 @@ struct cdef_ctx {
     cudaStream_t capture; // records the search's launches into a graph
     cudaGraphExec_t search_exec;  // the last search graph, updated per call
     SearchBatch *search_key;      // what search_exec was recorded for
-    void *search_ptrs[5];         // and its tables, ids and scratch pointers
+    void *search_ptrs[6];         // and its tables, ids and scratch pointers
     SearchTune search_key_tune;   // and its launch configuration
     SearchTune forced;            // fields > 0 fixed by cdef_ctx_set_tuning
     SearchTune last;              // configuration of the last search
@@ -430,7 +430,7 @@ uint64_t search_shape(const SearchBatch &b)
 // computes identically.
 int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long long *dc,
                        unsigned long long *cur, unsigned long long *tot, uint8_t *block_ids,
-                       cudaStream_t s, SearchTune *out)
+                       uint8_t *skipped, cudaStream_t s, SearchTune *out)
 {
     if (ctx->forced.groups > 0 && ctx->forced.ctas_per_sm > 0) {
         *out = ctx->forced;
@@ -439,7 +439,7 @@ int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long 
     if (!ctx->tuned) ctx->tuned = new (std::nothrow) std::unordered_map<uint64_t, SearchTune>();
     if (!ctx->tuned) return CDEF_ERR_NOMEM;
     const uint64_t key = search_shape(b) ^ ((uint64_t)ctx->forced.groups << 56) ^
-                         ((uint64_t)ctx->forced.ctas_per_sm << 60);
+                         ((uint64_t)ctx->forced.ctas_per_sm << 60) ^ (skipped ? 1ull << 52 : 0);
     auto it = ctx->tuned->find(key);
     if (it != ctx->tuned->end()) {
         *out = it->second;
@@ -460,11 +460,11 @@ int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long 
             (ctx->forced.ctas_per_sm > 0 && t.ctas_per_sm != ctx->forced.ctas_per_sm))
             continue;
         e = launch_search(b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status, ctx->work,
-                          t, ctx->refine_passes, s);
+                          t, ctx->refine_passes, s, skipped);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         if (e == cudaSuccess)
             e = launch_search(b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status,
-                              ctx->work, t, ctx->refine_passes, s);
+                              ctx->work, t, ctx->refine_passes, s, skipped);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -487,13 +487,21 @@ int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long 
 
 }  // namespace
 
-int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
-                          const int32_t *damping, const int64_t *lambda, int64_t *dist_luma,
-                          int64_t *dist_chroma, cdef_preset *presets, int32_t *npresets,
-                          uint8_t *block_ids, int64_t *cost, void *cuda_stream)
+namespace {
+
+// The strength search; `coded` (host array of n device maps) selects the
+// 128-combination variant with section 4's skip semantics.  Exactly one of
+// presets / presets_coded is non-null.
+int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
+                const uint8_t *const *coded, const int32_t *damping, const int64_t *lambda,
+                int64_t *dist_luma, int64_t *dist_chroma, cdef_preset *presets,
+                cdef_preset_coded *presets_coded, int32_t *npresets, uint8_t *block_ids,
+                int64_t *cost, void *cuda_stream)
 {
-    if (!ctx || !rec || !src || !damping || !lambda || !presets || !npresets || !block_ids || !cost)
+    if (!ctx || !rec || !src || !damping || !lambda || !(presets || presets_coded) || !npresets ||
+        !block_ids || !cost)
         return CDEF_ERR_ARG;
+    const int width = coded ? 128 : 64;
     if (n <= 0 || n > kMaxBatch) return CDEF_ERR_ARG;
     if ((dist_luma == nullptr) != (dist_chroma == nullptr)) return CDEF_ERR_ARG;
     SearchBatch *b = new (std::nothrow) SearchBatch();
@@ -504,7 +512,9 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
         if (!same_geometry(&rec[i], &src[i])) { rc = CDEF_ERR_SIZE; break; }
         if (rec[i].bitdepth > 10) { rc = CDEF_ERR_BITDEPTH; break; }
         if (damping[i] < 3 || damping[i] > 6 || lambda[i] < 0) { rc = CDEF_ERR_ARG; break; }
+        if (coded && !coded[i]) { rc = CDEF_ERR_ARG; break; }
         SearchFrameDev &f = b->f[i];
+        f.coded = coded ? coded[i] : nullptr;
         if ((rc = encode_frame_tiles(f.tmap, &rec[i]))) break;
         const cdef_plane *pr[3] = {&rec[i].y, &rec[i].u, &rec[i].v};
         const cdef_plane *ps[3] = {&src[i].y, &src[i].u, &src[i].v};
@@ -530,8 +540,8 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
 
     DeviceGuard g(ctx->device);
     if (!g.ok) { delete b; return CDEF_ERR_CUDA; }
-    const size_t greedy = search_scratch_bytes(n, total);
-    const size_t tables = dist_luma ? 0 : (size_t)total * 64 * sizeof(long long) * 2;
+    const size_t greedy = search_scratch_bytes(n, total, width);
+    const size_t tables = dist_luma ? 0 : (size_t)total * width * sizeof(long long) * 2;
     if ((rc = ensure_scratch(ctx, greedy + tables))) { delete b; return rc; }
     unsigned long long *cur = static_cast<unsigned long long *>(ctx->scratch);
     unsigned long long *tot = cur + total;
@@ -539,14 +549,19 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
     long long *dc = reinterpret_cast<long long *>(dist_chroma);
     if (!dl) {
         dl = reinterpret_cast<long long *>(static_cast<char *>(ctx->scratch) + greedy);
-        dc = dl + (size_t)total * 64;
+        dc = dl + (size_t)total * width;
     }
+    uint8_t *skipped = nullptr;   // per-block flags of the 128-combination search
+    if (coded)
+        skipped = static_cast<uint8_t *>(ctx->scratch) +
+                  sizeof(unsigned long long) * ((size_t)total + (size_t)n * width * width) +
+                  kPresetCtlBytes;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // Search calls synchronise before returning, so they never overlap: the
     // search owns counter pair 0 (filter launches take pairs 1..).
     unsigned *work = ctx->work;
     SearchTune tune;
-    if ((rc = choose_search_tune(ctx, *b, dl, dc, cur, tot, block_ids, s, &tune))) {
+    if ((rc = choose_search_tune(ctx, *b, dl, dc, cur, tot, block_ids, skipped, s, &tune))) {
         delete b;
         return rc;
     }
@@ -556,7 +571,7 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
     // one relaunches its graph; otherwise the launches are recorded on the
     // capture stream and the cached executable graph updated in place
     // (re-instantiated if the shape changed).
-    void *const ptrs[5] = {dl, dc, block_ids, cur, tot};
+    void *const ptrs[6] = {dl, dc, block_ids, cur, tot, skipped};
     const bool same = ctx->search_exec && ctx->search_key &&
                       memcmp(ctx->search_key, b, sizeof(SearchBatch)) == 0 &&
                       memcmp(ctx->search_ptrs, ptrs, sizeof(ptrs)) == 0 &&
@@ -567,7 +582,7 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
     if (e == cudaSuccess && !same) {
         const cudaError_t le = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids,
                                              ctx->status, work, tune, ctx->refine_passes,
-                                             ctx->capture);
+                                             ctx->capture, skipped);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(ctx->capture, &graph);
         if (e == cudaSuccess && le != cudaSuccess) e = le;
@@ -606,15 +621,50 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const
         npresets[i] = r.npresets;
         cost[i] = r.cost;
         for (int k = 0; k < 8; k++) {
-            const int t = r.presets[k], ql = t >> 6, qc = t & 63;
-            cdef_preset &p = presets[i * 8 + k];
-            p.pri_y = (uint8_t)(ql >> 2);
-            p.sec_y = kSec[ql & 3];
-            p.pri_uv = (uint8_t)(qc >> 2);
-            p.sec_uv = kSec[qc & 3];
+            const int t = r.presets[k], ql = t / width, qc = t % width;
+            if (presets) {
+                cdef_preset &p = presets[i * 8 + k];
+                p.pri_y = (uint8_t)(ql >> 2);
+                p.sec_y = kSec[ql & 3];
+                p.pri_uv = (uint8_t)(qc >> 2);
+                p.sec_uv = kSec[qc & 3];
+            } else {
+                // q = skip * 64 + p * 4 + s
+                cdef_preset_coded &p = presets_coded[i * 8 + k];
+                memset(&p, 0, sizeof(p));
+                p.pri_y = (uint8_t)((ql >> 2) & 15);
+                p.sec_y = kSec[ql & 3];
+                p.pri_uv = (uint8_t)((qc >> 2) & 15);
+                p.sec_uv = kSec[qc & 3];
+                p.skip = (uint8_t)((ql >> 6) | ((qc >> 6) << 1));
+            }
         }
     }
     return CDEF_OK;
+}
+
+}  // namespace
+
+int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
+                          const int32_t *damping, const int64_t *lambda, int64_t *dist_luma,
+                          int64_t *dist_chroma, cdef_preset *presets, int32_t *npresets,
+                          uint8_t *block_ids, int64_t *cost, void *cuda_stream)
+{
+    if (!presets) return CDEF_ERR_ARG;
+    return search_impl(ctx, n, rec, src, nullptr, damping, lambda, dist_luma, dist_chroma, presets,
+                       nullptr, npresets, block_ids, cost, cuda_stream);
+}
+
+int cdef_search_strengths_coded(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
+                                const cdef_frame *src, const uint8_t *const *coded,
+                                const int32_t *damping, const int64_t *lambda,
+                                int64_t *dist_luma, int64_t *dist_chroma,
+                                cdef_preset_coded *presets, int32_t *npresets,
+                                uint8_t *block_ids, int64_t *cost, void *cuda_stream)
+{
+    if (!coded || !presets) return CDEF_ERR_ARG;
+    return search_impl(ctx, n, rec, src, coded, damping, lambda, dist_luma, dist_chroma, nullptr,
+                       presets, npresets, block_ids, cost, cuda_stream);
 }
 
 const char *cdef_strerror(int status)

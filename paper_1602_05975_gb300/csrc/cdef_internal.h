@@ -55,6 +55,7 @@ struct SearchFrameDev {  // aligned as CUtensorMap requires
     int fb_cols, fb_rows;
     int block_start;                 // first filter block of this frame in the tables
     long long lambda;
+    const uint8_t *coded;            // 8x8 coded-residual map (128-combination search only)
 };
 
 struct SearchBatch {
@@ -124,26 +125,32 @@ inline SearchTune default_search_tune(int total_blocks, int sms)
 // by the call itself), `work` a zeroed counter pair (left zeroed).
 // `refine_passes`: 0 = the greedy presets; > 0 = then re-optimise each set
 // one preset at a time for at most that many passes (section 5).
+// `skipped` non-null: the 128-combination search of section 5 with section
+// 4's skip semantics (each frame's `coded` map; tables of 128 entries per
+// block; `skipped` receives one flag per block); null: 64 combinations.
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
                           long long *dist_chroma, unsigned long long *cur,
                           unsigned long long *tot, SearchResultDev *results,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
-                          int refine_passes, cudaStream_t s);
+                          int refine_passes, cudaStream_t s, uint8_t *skipped = nullptr);
 // The preset selection alone (one cooperative launch); `ctl` is the control
 // block that follows `tot` in the scratch.
+// `width`: combinations per plane group in the tables (64 or 128; presets
+// are width * width); `skipped` (may be null): blocks left out of the sums.
 cudaError_t launch_presets(const SearchBatch &b, const long long *dl, const long long *dc,
                            unsigned long long *cur, unsigned long long *tot, void *ctl,
                            SearchResultDev *results, uint8_t *block_ids, int *status,
-                           int refine_passes, cudaStream_t s);
+                           int refine_passes, int width, const uint8_t *skipped,
+                           cudaStream_t s);
 size_t preset_ctl_bytes();
 constexpr int kMaxRefinePasses = 16;
 constexpr size_t kPresetCtlBytes = 512;   // barrier and per-frame flags of launch_presets
 // Scratch of one search: `cur` one u64 per block, `tot` 4096 u64 per frame,
 // then the preset kernel's control block.
-constexpr size_t search_scratch_bytes(int nframes, int nblocks)
+constexpr size_t search_scratch_bytes(int nframes, int nblocks, int width = 64)
 {
-    return sizeof(unsigned long long) * ((size_t)nblocks + (size_t)nframes * 4096) +
-           kPresetCtlBytes;
+    return sizeof(unsigned long long) * ((size_t)nblocks + (size_t)nframes * width * width) +
+           kPresetCtlBytes + (width == 128 ? ((size_t)nblocks + 15) / 16 * 16 : 0);
 }
 
 // Host: the three 2-D tile maps (filter-block boxes with halo) of a frame's

@@ -27,8 +27,8 @@ namespace {
 
 constexpr int kChunk = 16;         // blocks per partial unit
 constexpr int kThreads = 256;
-constexpr int kTuples = 4096;
-constexpr int kPerThread = kTuples / kThreads;
+constexpr int kMaxWidth = 128;     // combinations per plane group (64 or 128)
+constexpr int kPerThread = 16;     // presets per thread and group of 4096
 constexpr long long kBarrierCycles = 1ll << 30;
 
 struct Ctl {                       // lives in device scratch
@@ -92,13 +92,14 @@ __device__ __forceinline__ int frame_chunks(const SearchFrameDev &F)
 }
 
 __device__ __forceinline__ unsigned long long dist_of(const long long *dl, const long long *dc,
-                                                      int g, int t)
+                                                      int width, int g, int t)
 {
-    return (unsigned long long)(dl[(int64_t)g * 64 + (t >> 6)] + dc[(int64_t)g * 64 + (t & 63)]);
+    return (unsigned long long)(dl[(int64_t)g * width + t / width] +
+                                dc[(int64_t)g * width + t % width]);
 }
 
 struct Shared {
-    unsigned long long dl[kChunk][64], dc[kChunk][64], cur[kChunk];
+    unsigned long long dl[kChunk][kMaxWidth], dc[kChunk][kMaxWidth], cur[kChunk];
     unsigned long long red_v[kThreads / 32];
     int red_t[kThreads / 32];
     int best;
@@ -109,8 +110,9 @@ struct Shared {
 __device__ void partial_phase(const SearchBatch &batch, const long long *dl, const long long *dc,
                               const unsigned long long *cur, unsigned long long *tot,
                               const SearchResultDev *res, const Ctl *ctl, int refine_lg, int k,
-                              Shared &sh)
+                              int width, const uint8_t *skipped, Shared &sh)
 {
+    const int ntuples = width * width;
     const int tid = threadIdx.x;
     int units = 0;
     for (int f = 0; f < batch.n; f++) units += frame_chunks(batch.f[f]);
@@ -122,42 +124,52 @@ __device__ void partial_phase(const SearchBatch &batch, const long long *dl, con
         const int B = F.fb_cols * F.fb_rows;
         const int b0 = c * kChunk, nb = min(kChunk, B - b0);
         const int g0 = F.block_start + b0;
-        for (int i = tid; i < nb * 64; i += kThreads) {
-            sh.dl[i >> 6][i & 63] = (unsigned long long)dl[(int64_t)(g0 + (i >> 6)) * 64 + (i & 63)];
-            sh.dc[i >> 6][i & 63] = (unsigned long long)dc[(int64_t)(g0 + (i >> 6)) * 64 + (i & 63)];
+        for (int i = tid; i < nb * width; i += kThreads) {
+            const int b = i / width, q = i - b * width;
+            sh.dl[b][q] = (unsigned long long)dl[(int64_t)(g0 + b) * width + q];
+            sh.dc[b][q] = (unsigned long long)dc[(int64_t)(g0 + b) * width + q];
         }
         __syncthreads();
         if (tid < nb) {
-            if (refine_lg < 0) {
-                sh.cur[tid] = __ldcg(&cur[g0 + tid]);
+            unsigned long long m;
+            if (skipped && skipped[g0 + tid]) {
+                m = 0;   // no preset id: the block adds nothing to any total
+            } else if (refine_lg < 0) {
+                m = __ldcg(&cur[g0 + tid]);
             } else {
                 const int n = 1 << refine_lg;
-                unsigned long long m = ULLONG_MAX;
+                m = ULLONG_MAX;
                 for (int j = 0; j < n; j++) {
                     if (j == k) continue;
                     const int t = __ldcg(&res[fi].refined[refine_lg][j]);
-                    const unsigned long long v = sh.dl[tid][t >> 6] + sh.dc[tid][t & 63];
+                    const unsigned long long v = sh.dl[tid][t / width] + sh.dc[tid][t % width];
                     m = v < m ? v : m;
                 }
-                sh.cur[tid] = m;
             }
+            sh.cur[tid] = m;
         }
         __syncthreads();
-        unsigned long long a[kPerThread];
+        // thread tid, group g: presets t = g * 4096 + tid + 256 q, whose
+        // chroma combination is always tid % width
+        const int ci = tid % width, lstep = kThreads / width;
+        unsigned long long *t = tot + (int64_t)fi * ntuples;
+        for (int g = 0; g < ntuples / 4096; g++) {
+            const int l0 = (g * 4096 + tid) / width;
+            unsigned long long a[kPerThread];
 #pragma unroll
-        for (int q = 0; q < kPerThread; q++) a[q] = 0;
-        const int ci = tid & 63, l0 = tid >> 6;
-        for (int b = 0; b < nb; b++) {
-            const unsigned long long cv = sh.cur[b], dcv = sh.dc[b][ci];
+            for (int q = 0; q < kPerThread; q++) a[q] = 0;
+            for (int b = 0; b < nb; b++) {
+                const unsigned long long cv = sh.cur[b], dcv = sh.dc[b][ci];
 #pragma unroll
-            for (int q = 0; q < kPerThread; q++) {
-                const unsigned long long v = sh.dl[b][l0 + 4 * q] + dcv;
-                a[q] += v < cv ? v : cv;
+                for (int q = 0; q < kPerThread; q++) {
+                    const unsigned long long v = sh.dl[b][l0 + lstep * q] + dcv;
+                    a[q] += v < cv ? v : cv;
+                }
             }
-        }
-        unsigned long long *t = tot + (int64_t)fi * kTuples;
 #pragma unroll
-        for (int q = 0; q < kPerThread; q++) atomicAdd(&t[tid + kThreads * q], a[q]);
+            for (int q = 0; q < kPerThread; q++)
+                atomicAdd(&t[g * 4096 + tid + kThreads * q], a[q]);
+        }
         __syncthreads();   // before the next unit overwrites the shared tables
     }
 }
@@ -168,13 +180,13 @@ __device__ __forceinline__ bool better(unsigned long long a, int ta, unsigned lo
 }
 
 // The least of a frame's totals and its lowest index (whole CTA).
-__device__ void frame_argmin(unsigned long long *t, Shared &sh, unsigned long long *min_v,
-                             int *min_t)
+__device__ void frame_argmin(unsigned long long *t, int ntuples, Shared &sh,
+                             unsigned long long *min_v, int *min_t)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long bv = ULLONG_MAX;
     int bt = INT_MAX;
-    for (int i = tid; i < kTuples; i += kThreads) {
+    for (int i = tid; i < ntuples; i += kThreads) {
         const unsigned long long v = __ldcg(&t[i]);
         if (better(v, i, bv, bt)) { bv = v; bt = i; }
     }
@@ -202,15 +214,17 @@ __device__ void frame_argmin(unsigned long long *t, Shared &sh, unsigned long lo
 __global__ void __launch_bounds__(kThreads)
 preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
               const long long *__restrict__ dc, unsigned long long *cur, unsigned long long *tot,
-              SearchResultDev *res, uint8_t *block_ids, int *status, Ctl *ctl, int refine_passes)
+              SearchResultDev *res, uint8_t *block_ids, int *status, Ctl *ctl, int refine_passes,
+              int width, const uint8_t *skipped)
 {
     __shared__ Shared sh;
     const int tid = threadIdx.x;
     const int stride = gridDim.x * kThreads;
     const int n = batch.n;
+    const int ntuples = width * width;
 
     for (int i = blockIdx.x * kThreads + tid; i < batch.total_blocks; i += stride) cur[i] = ULLONG_MAX;
-    for (int i = blockIdx.x * kThreads + tid; i < n * kTuples; i += stride) tot[i] = 0;
+    for (int i = blockIdx.x * kThreads + tid; i < n * ntuples; i += stride) tot[i] = 0;
     if (blockIdx.x == 0 && tid < n) {
         ctl->changed[tid] = 0;
         ctl->done[tid] = 0;
@@ -220,13 +234,13 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
 
     // ---- greedy: preset `step` is the best addition to presets 0..step-1
     for (int step = 0; step < 8; step++) {
-        partial_phase(batch, dl, dc, cur, tot, res, ctl, -1, 0, sh);
+        partial_phase(batch, dl, dc, cur, tot, res, ctl, -1, 0, width, skipped, sh);
         if (!grid_sync(ctl, status)) return;
         for (int f = blockIdx.x; f < n; f += gridDim.x) {
-            unsigned long long *t = tot + (int64_t)f * kTuples;
+            unsigned long long *t = tot + (int64_t)f * ntuples;
             unsigned long long v;
             int best;
-            frame_argmin(t, sh, &v, &best);
+            frame_argmin(t, ntuples, sh, &v, &best);
             if (tid == 0) {
                 res[f].greedy[step] = best;
                 res[f].totals[step] = (long long)v;
@@ -235,10 +249,10 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
             const int B = F.fb_cols * F.fb_rows;
             for (int b = tid; b < B; b += kThreads) {
                 const int g = F.block_start + b;
-                const unsigned long long d = dist_of(dl, dc, g, best);
+                const unsigned long long d = dist_of(dl, dc, width, g, best);
                 if (d < __ldcg(&cur[g])) cur[g] = d;
             }
-            for (int i = tid; i < kTuples; i += kThreads) t[i] = 0;
+            for (int i = tid; i < ntuples; i += kThreads) t[i] = 0;
             __syncthreads();
         }
         if (!grid_sync(ctl, status)) return;
@@ -260,16 +274,16 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
         const int sz = 1 << lg;
         for (int pass = 0; pass < refine_passes; pass++) {
             for (int k = 0; k < sz; k++) {
-                partial_phase(batch, dl, dc, cur, tot, res, ctl, lg, k, sh);
+                partial_phase(batch, dl, dc, cur, tot, res, ctl, lg, k, width, skipped, sh);
                 if (!grid_sync(ctl, status)) return;
                 for (int f = blockIdx.x; f < n; f += gridDim.x) {
                     if (__ldcg(&ctl->done[f])) continue;
-                    unsigned long long *t = tot + (int64_t)f * kTuples;
+                    unsigned long long *t = tot + (int64_t)f * ntuples;
                     const int old = __ldcg(&res[f].refined[lg][k]);
                     const unsigned long long old_v = __ldcg(&t[old]);
                     unsigned long long v;
                     int best;
-                    frame_argmin(t, sh, &v, &best);
+                    frame_argmin(t, ntuples, sh, &v, &best);
                     if (tid == 0) {
                         if (old_v == v) best = old;        // keep the current preset on ties
                         if (best != old) {
@@ -278,7 +292,7 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
                         }
                         res[f].ref_totals[lg] = (long long)v;
                     }
-                    for (int i = tid; i < kTuples; i += kThreads) t[i] = 0;
+                    for (int i = tid; i < ntuples; i += kThreads) t[i] = 0;
                     __syncthreads();
                 }
                 if (!grid_sync(ctl, status)) return;
@@ -313,10 +327,13 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
         const SearchFrameDev &F = batch.f[f];
         const int B = F.fb_cols * F.fb_rows;
         if (tid == 0) {
+            int coded_blocks = B;   // blocks that signal a preset id
+            if (skipped)
+                for (int b = 0; b < B; b++) coded_blocks -= skipped[F.block_start + b] != 0;
             int bl = 0;
             long long bj = 0;
             for (int lg = 0; lg < 4; lg++) {
-                const long long j = res[f].ref_totals[lg] + F.lambda * (long long)B * lg;
+                const long long j = res[f].ref_totals[lg] + F.lambda * (long long)coded_blocks * lg;
                 if (lg == 0 || j < bj) { bl = lg; bj = j; }
             }
             res[f].cost = bj;
@@ -331,11 +348,12 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
         for (int b = tid; b < B; b += kThreads) {
             const int g = F.block_start + b;
             int id = 0;
-            long long bestd = LLONG_MAX;
-            for (int j = 0; j < N; j++) {
-                const int t = res[f].presets[j];
-                const long long v = dl[(int64_t)g * 64 + (t >> 6)] + dc[(int64_t)g * 64 + (t & 63)];
-                if (v < bestd) { bestd = v; id = j; }
+            if (!(skipped && skipped[g])) {
+                long long bestd = LLONG_MAX;
+                for (int j = 0; j < N; j++) {
+                    const long long v = (long long)dist_of(dl, dc, width, g, res[f].presets[j]);
+                    if (v < bestd) { bestd = v; id = j; }
+                }
             }
             block_ids[g] = (uint8_t)id;
         }
@@ -371,8 +389,9 @@ size_t preset_ctl_bytes() { return sizeof(Ctl); }
 cudaError_t launch_presets(const SearchBatch &b, const long long *dl, const long long *dc,
                            unsigned long long *cur, unsigned long long *tot, void *ctl,
                            SearchResultDev *results, uint8_t *block_ids, int *status,
-                           int refine_passes, cudaStream_t s)
+                           int refine_passes, int width, const uint8_t *skipped, cudaStream_t s)
 {
+    if (width != 64 && width != kMaxWidth) return cudaErrorInvalidValue;
     // a barrier abandoned by an earlier timed-out launch must not leave
     // CTAs counted: the arrival count starts at zero
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned), s);
@@ -389,7 +408,7 @@ cudaError_t launch_presets(const SearchBatch &b, const long long *dl, const long
     cfg.numAttrs = 1;
     Ctl *c = static_cast<Ctl *>(ctl);
     return cudaLaunchKernelEx(&cfg, preset_kernel, b, dl, dc, cur, tot, results, block_ids, status,
-                              c, refine_passes);
+                              c, refine_passes, width, skipped);
 }
 
 }  // namespace cdefgb

@@ -36,15 +36,22 @@ struct SearchSmem {
     PairTiles t;
     alignas(16) int off[2][8][12];    // tap word offsets [luma/chroma][d][tap]
     int cost[64][8];
-    alignas(16) SetC pset[64][17];    // luma primary sets per 8x8 block and signalled strength
-    alignas(16) SetC cset[16];        // chroma primary sets per signalled strength
+    // luma primary sets per 8x8 block and signalled strength (entry 16: the
+    // strength 19 of the (0,0)+skip preset); 17 entries per row also keep
+    // the eight blocks a warp reads at once in different banks
+    alignas(16) SetC pset[64][17];
+    alignas(16) SetC cset[17];        // chroma primary sets per signalled strength (16: 19)
     alignas(16) SetC sset[3][4];      // secondary: luma; chroma at D - 1; chroma at D = 3
-    uint32_t pbits[64];               // luma: bit p odd adjusted strength, bit 16 + p adjusted > 0
+    alignas(16) SetC s7[64];          // secondary 7 of the (19, 7) preset, per luma block
+    alignas(16) SetC s7c;             // and for chroma
+    uint32_t pbits[64];               // luma: bit p set when the adjusted strength is odd
     uint32_t cbits;                   // chroma: the same per signalled strength
     uint32_t craised;                 // chroma: bit p, damping raised to floor(log2 p) = 3
     uint8_t dir[64];
+    uint8_t coded[64];                // 8x8 block has coded residual (128-combination search)
     int var[64];
     unsigned long long acc[64];       // block totals of the current plane group
+    unsigned long long accu[64];      // the part of them from blocks without coded residual
     unsigned long long base[2];       // sum of (x - s)^2 over the same pixels, per plane group
     int blk[2];
     alignas(8) uint64_t bar[2];
@@ -131,10 +138,54 @@ __device__ __forceinline__ void butterfly(uint32_t (&a)[N], int lane)
 // grp * 16 / kG .. (grp + 1) * 16 / kG - 1 with all four secondary
 // strengths, for both plane groups (64 / kG luma and 64 / kG chroma
 // candidates).
-template <typename T, int kG>
+// Levels LO..HI-1 of a warp reduction of N values (offsets 1 << level, in
+// increasing order): after level l a lane keeps N >> (l + 1) entries, the
+// upper half when its bit l is set.  `a` holds the N >> LO entries still
+// live before level LO.
+template <int N, int LO, int HI, int LEN>
+__device__ __forceinline__ void wreduce(uint32_t (&a)[LEN], int lane)
+{
+#pragma unroll
+    for (int lvl = LO; lvl < HI; lvl++) {
+        const int o = 1 << lvl, n = N >> lvl;
+        if (n > 1) {
+            const bool upper = lane & o;
+            const int half = n >> 1;
+#pragma unroll
+            for (int i = 0; i < LEN / 2; i++) {
+                if (i < half) {
+                    const uint32_t give = upper ? a[i] : a[i + half];
+                    const uint32_t keep = upper ? a[i + half] : a[i];
+                    a[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+                }
+            }
+        } else {
+            a[0] += __shfl_xor_sync(0xffffffffu, a[0], o);
+        }
+    }
+}
+
+// The first entry a lane holds after all five levels of wreduce<N>.
+__device__ __forceinline__ int wentry(int N, int lane)
+{
+    int e = 0;
+#pragma unroll
+    for (int lvl = 0; lvl < 5; lvl++) {
+        const int n = N >> lvl;
+        if (n > 1) e += (n >> 1) * ((lane >> lvl) & 1);
+    }
+    return e;
+}
+
+// kCoded: the 128-combination search of section 5 with section 4's skip
+// semantics.  The (0, 0) slot, whose error is sum (x - s)^2 with no work,
+// evaluates the (19, 7) preset instead; each candidate's sum is also kept
+// for the 8x8 blocks without coded residual, so that the skip-bit-clear
+// entries (those blocks unfiltered) follow as base + total - uncoded part.
+template <typename T, int kG, bool kCoded>
 __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global, int grp,
                            SearchSmem &sm, const RawTiles &raw, long long *dist_luma,
-                           long long *dist_chroma)
+                           long long *dist_chroma, uint8_t *skipped)
 {
     constexpr int kPP = 16 / kG;           // primary strengths per unit
     constexpr int kN = 4 * kPP;            // candidates per plane group
@@ -168,6 +219,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         sm.dir[tid] = (uint8_t)best;
         sm.var[tid] = bc - sm.cost[tid][(best + 4) & 7];
         sm.acc[tid] = 0;
+        sm.accu[tid] = 0;
         if (tid < 2) sm.base[tid] = 0;
     }
     __syncthreads();
@@ -180,11 +232,21 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         const int Deff = (S && D < lp) ? lp : D;
         sm.pset[k][p] = make_set(S << sh8, S ? Deff - lp : 0);
     }
+    int cflag = 0;
     if (tid < 64) {
         uint32_t bits = 0;
         for (int p = 0; p < 16; p++) {
             const int S = adjust_strength(p, sm.var[tid]);
-            bits |= ((uint32_t)(S & 1) << p) | ((uint32_t)(S > 0) << (16 + p));
+            bits |= (uint32_t)(S & 1) << p;
+        }
+        if (kCoded) {   // the (19, 7) preset of this 8x8 block (section 4)
+            const Eff e = make_eff(19, 7, D, false, sm.var[tid], sh8);
+            sm.pset[tid][16] = make_set(e.pri, e.psh);
+            sm.s7[tid] = make_set(e.sec, e.ssh);
+            bits |= (uint32_t)(e.w0 == 3) << 16;
+            const int gby = fby * 8 + (tid >> 3), gbx = fbx * 8 + (tid & 7);
+            if (gby * 8 < H && gbx * 8 < W) cflag = F.coded[gby * (W >> 3) + gbx] != 0;
+            sm.coded[tid] = (uint8_t)cflag;
         }
         sm.pbits[tid] = bits;
     } else if (tid < 80) {
@@ -198,13 +260,21 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
     } else if (tid == 92) {
         uint32_t bits = 0, raised = 0;
         for (int p = 0; p < 16; p++) {
-            bits |= ((uint32_t)(p & 1) << p) | ((uint32_t)(p > 0) << (16 + p));
+            bits |= (uint32_t)(p & 1) << p;
             if (p && ilog2(p) > D - 1) raised |= 1u << p;
+        }
+        if (kCoded) {
+            const Eff e = make_eff(19, 7, D, true, 0, sh8);
+            sm.cset[16] = make_set(e.pri, e.psh);
+            sm.s7c = make_set(e.sec, e.ssh);
+            bits |= (uint32_t)(e.w0 == 3) << 16;
         }
         sm.cbits = bits;
         sm.craised = raised;
     }
-    __syncthreads();
+    // section 4: a filter block without coded residual is never filtered
+    const bool any_coded = kCoded ? __syncthreads_or(cflag) != 0 : (__syncthreads(), true);
+    if (kCoded && grp == 0 && tid == 0) skipped[blk_global] = (uint8_t)!any_coded;
 
     // ---- both plane groups through one code path: task 0 luma, task 1 chroma
     const int bw = W >> 3;
@@ -228,6 +298,8 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         const uint32_t bits = luma ? sm.pbits[blk] : sm.cbits;
         const uint32_t raised = luma ? 0u : sm.craised;
         const SetC *ss = luma ? sm.sset[0] : sm.sset[1];
+        SetC s7 = {};
+        if (kCoded) s7 = luma ? sm.s7[blk] : sm.s7c;
         const int oy = luma ? ly0 + warp * 8 : cy0 + warp * 4;
         const int ox = luma ? lx0 + bx * 8 + 2 * sub : cx0 + bx * 4 + sub;
         const uint8_t *sa = luma ? F.src[0] : F.src[1];
@@ -284,10 +356,14 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     const SetC sc = ps[p];
                     const uint32_t T0 = pri_sum(v, X, sc, (bits >> p) & 1) + C;
                     const bool rz = (raised >> p) & 1;
+                    const bool slot19 = kCoded && p == 0;   // (0, 0) slot: the (19, 7) preset
+                    uint32_t u19 = 0;
+                    if (slot19)
+                        u19 = pri_sum(v, X, ps[16], (bits >> 16) & 1) + C + sec_sum(v, X, s7);
 #pragma unroll
                     for (int s = 0; s < 4; s++) {
                         // eq. 8 rounding of (P + Q - 24x) / 16, ties away from zero
-                        const uint32_t u = T0 + (rz ? Qr[s] : Q[s]);
+                        const uint32_t u = (slot19 && s == 0) ? u19 : T0 + (rz ? Qr[s] : Q[s]);
                         const uint32_t pos = (u >> 12) & kLanes;
                         const uint32_t w = u + pos + 7u * kLanes;
                         uint32_t rb = (w >> 4) & (0x0fffu * kLanes);   // r + 256 per lane
@@ -295,7 +371,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                         // adjusted primary strength is 0 only the secondary set
                         // contributes, its weights sum to 12/16 < 1, and the
                         // clip cannot bind: it is applied without a test.
-                        if (s > 0) rb = __vminu2(__vmaxu2(rb, rlo), rhi);
+                        if (s > 0 || slot19) rb = __vminu2(__vmaxu2(rb, rlo), rhi);
                         const uint32_t a = sadd16(rb, two_xs);           // 2 (x - s) + r
                         acc[pp * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)__byte_perm(rb, 0, 0x0020),
                                                               (int)acc[pp * 4 + s]);
@@ -303,24 +379,57 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 }
             }
         }
-        butterfly<kN>(acc, lane);
         // the warp totals of r (2 (x - s) + r) are signed and fit 32 bits
-        if (kN == 64) {
-            atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
-            atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
-        } else if (kN == 32) {
-            atomicAdd(&sm.acc[lane], (unsigned long long)(long long)(int)acc[0]);
-        } else if (!(lane & 1)) {
-            atomicAdd(&sm.acc[lane >> 1], (unsigned long long)(long long)(int)acc[0]);
+        if (!kCoded) {
+            butterfly<kN>(acc, lane);
+            if (kN == 64) {
+                atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
+                atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
+            } else if (kN == 32) {
+                atomicAdd(&sm.acc[lane], (unsigned long long)(long long)(int)acc[0]);
+            } else if (!(lane & 1)) {
+                atomicAdd(&sm.acc[lane >> 1], (unsigned long long)(long long)(int)acc[0]);
+            }
+        } else {
+            // the four lanes of one 8x8 block first, then the uncoded blocks'
+            // part is split off and both are summed across the warp
+            wreduce<kN, 0, 2>(acc, lane);
+            constexpr int kQ = kN / 4;
+            uint32_t un[kQ];
+            const bool unc = !sm.coded[blk];
+#pragma unroll
+            for (int i = 0; i < kQ; i++) un[i] = unc ? acc[i] : 0u;
+            wreduce<kN, 2, 5>(acc, lane);
+            wreduce<kN, 2, 5>(un, lane);
+            const int e = wentry(kN, lane);
+            if (kN >= 32 || !(lane & 16)) {
+#pragma unroll
+                for (int j = 0; j < (kN >= 64 ? 2 : 1); j++) {
+                    atomicAdd(&sm.acc[e + j], (unsigned long long)(long long)(int)acc[j]);
+                    atomicAdd(&sm.accu[e + j], (unsigned long long)(long long)(int)un[j]);
+                }
+            }
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) sse0 += __shfl_xor_sync(0xffffffffu, sse0, o);
         if (lane == 0) atomicAdd(&sm.base[task], (unsigned long long)sse0);
         __syncthreads();
         if (tid < kN) {
-            long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
-            out[tid] = (long long)(sm.acc[tid] + sm.base[task]);
+            const long long base_sse = (long long)sm.base[task];
+            if (!kCoded) {
+                long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
+                out[tid] = (long long)sm.acc[tid] + base_sse;
+            } else {
+                // q = k * 64 + p * 4 + s; skip bit clear: blocks without coded
+                // residual unfiltered, (0, 0) the unfiltered error
+                long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 128 +
+                                 4 * p0 + tid;
+                const long long tot = (long long)sm.acc[tid], un = (long long)sm.accu[tid];
+                out[0] = (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un;
+                out[64] = !any_coded ? base_sse : base_sse + tot;
+            }
             sm.acc[tid] = 0;
+            sm.accu[tid] = 0;
         }
         __syncthreads();
     }
@@ -348,10 +457,10 @@ __device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTil
 
 // Persistent distortion kernel (same work-counter scheme as the filter).
 // Work unit u is filter block u / kG, primary-strength group u % kG.
-template <int kG>
+template <int kG, bool kCoded>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
 dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, long long *dist_chroma,
-            int *status, unsigned *work)
+            uint8_t *skipped, int *status, unsigned *work)
 {
     extern __shared__ __align__(128) uint8_t smem_bytes[];
     SearchSmem &sm = *reinterpret_cast<SearchSmem *>(smem_bytes);
@@ -397,11 +506,11 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             const SBlockRef r = slocate(batch, fb);
             const SearchFrameDev &F = batch.f[r.fi];
             if (F.bitdepth == 8)
-                dist_block<uint8_t, kG>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf], dist_luma,
-                                        dist_chroma);
+                dist_block<uint8_t, kG, kCoded>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf],
+                                                dist_luma, dist_chroma, skipped);
             else
-                dist_block<uint16_t, kG>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf], dist_luma,
-                                         dist_chroma);
+                dist_block<uint16_t, kG, kCoded>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf],
+                                                 dist_luma, dist_chroma, skipped);
             __syncthreads();
         }
     }
@@ -419,20 +528,21 @@ constexpr size_t kSmemBytes = sizeof(SearchSmem);
 
 // Persistent grid: `per_sm` CTAs on every SM (at most what fits), never more
 // CTAs than work units.
-template <int kG>
+template <int kG, bool kCoded>
 int dist_grid(int units, int per_sm)
 {
     static int cached_dev = -1, cached_sms = 0, cached_occ = 1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != cached_dev) {
-        cudaFuncSetAttribute(dist_kernel<kG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(dist_kernel<kG, kCoded>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSmemBytes);
-        cudaFuncSetAttribute(dist_kernel<kG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(dist_kernel<kG, kCoded>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dist_kernel<kG>, kThreads, kSmemBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dist_kernel<kG, kCoded>, kThreads,
+                                                      kSmemBytes);
         cached_sms = sms;
         cached_occ = occ > 0 ? occ : 1;
         cached_dev = dev;
@@ -442,12 +552,16 @@ int dist_grid(int units, int per_sm)
 }
 
 template <int kG>
-cudaError_t launch_dist(const SearchBatch &b, long long *dl, long long *dc, int *status,
-                        unsigned *work, int per_sm, cudaStream_t s)
+cudaError_t launch_dist(const SearchBatch &b, long long *dl, long long *dc, uint8_t *skipped,
+                        int *status, unsigned *work, int per_sm, cudaStream_t s)
 {
     const int units = b.total_blocks * kG;
-    dist_kernel<kG><<<dist_grid<kG>(units, per_sm), kThreads, kSmemBytes, s>>>(b, dl, dc, status,
-                                                                              work);
+    if (skipped)
+        dist_kernel<kG, true><<<dist_grid<kG, true>(units, per_sm), kThreads, kSmemBytes, s>>>(
+            b, dl, dc, skipped, status, work);
+    else
+        dist_kernel<kG, false><<<dist_grid<kG, false>(units, per_sm), kThreads, kSmemBytes, s>>>(
+            b, dl, dc, nullptr, status, work);
     return cudaGetLastError();
 }
 
@@ -456,18 +570,20 @@ cudaError_t launch_dist(const SearchBatch &b, long long *dl, long long *dc, int 
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long *dist_chroma,
                           unsigned long long *cur, unsigned long long *tot, SearchResultDev *results,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
-                          int refine_passes, cudaStream_t s)
+                          int refine_passes, cudaStream_t s, uint8_t *skipped)
 {
     cudaError_t e;
+    const int per_sm = tune.ctas_per_sm;
     switch (tune.groups) {
-    case 2: e = launch_dist<2>(b, dist_luma, dist_chroma, status, work, tune.ctas_per_sm, s); break;
-    case 4: e = launch_dist<4>(b, dist_luma, dist_chroma, status, work, tune.ctas_per_sm, s); break;
-    default: e = launch_dist<1>(b, dist_luma, dist_chroma, status, work, tune.ctas_per_sm, s); break;
+    case 2: e = launch_dist<2>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;
+    case 4: e = launch_dist<4>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;
+    default: e = launch_dist<1>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;
     }
     if (e != cudaSuccess) return e;
-    void *ctl = tot + (size_t)b.n * 4096;
+    const int width = skipped ? 128 : 64;
+    void *ctl = tot + (size_t)b.n * width * width;
     return launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
-                          refine_passes, s);
+                          refine_passes, width, skipped, s);
 }
 
 }  // namespace cdefgb

@@ -491,3 +491,49 @@ def test_filter_bad_skip_bits_flagged(cdef, ctx):
     assert ctx.status() == 0          # cleared by the read
     got = out.to_numpy()
     assert all(np.array_equal(g, e) for g, e in zip(got, f.rec))
+
+
+# --------------------------------------------------------------- 128-combination search
+@pytest.mark.parametrize("groups,passes", [(0, 0), (1, 0), (2, 0), (4, 0), (0, 4)])
+def test_search_coded_parity(cdef, ctx, ref, groups, passes):
+    """Section 5 with section 4's skip bits: 128-entry tables, skipped filter
+    blocks, presets, N, J and ids equal the oracle's, for every launch
+    configuration and with re-optimisation."""
+    from paper_1602_05975_gb300 import synth
+    specs = [(200, 136, 8, 16, 900), (136, 72, 10, 32, 901), (192, 128, 8, 64, 902)]
+    frames = [synth.make_frame(w, h, bd, q, seed=s) for w, h, bd, q, s in specs]
+    rng = np.random.default_rng(77)
+    maps = []
+    for f in frames:
+        m = (rng.random((f.height // 8, f.width // 8)) < 0.6).astype(np.uint8)
+        m[:8, :8] = 0                                          # first filter block skipped
+        maps.append(m)
+    damping, lambdas = [5, 4, 6], [64, 512, 4096]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(nb * 128, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(nb * 128, dtype=torch.int64, device="cuda")
+    ctx.set_tuning(groups, 2 if groups else 0)
+    ctx.set_search_refine(passes)
+    try:
+        res = cdef.cdef_search_strengths_coded(
+            ctx, [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames],
+            [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames],
+            [torch.from_numpy(m.reshape(-1)).cuda() for m in maps], damping, lambdas, ids, dl, dc)
+    finally:
+        ctx.set_tuning(0, 0)
+        ctx.set_search_refine(0)
+    assert ctx.status() == 0
+    o0 = 0
+    for f, m, r, d, lam in zip(frames, maps, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths_coded(f.rec, f.src, f.bitdepth, d, lam, m, passes)
+        assert np.array_equal(dl[o0 * 128:(o0 + b) * 128].cpu().numpy().reshape(b, 128),
+                              o["dist_luma"])
+        assert np.array_equal(dc[o0 * 128:(o0 + b) * 128].cpu().numpy().reshape(b, 128),
+                              o["dist_chroma"])
+        assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"]
+        assert ([cdef.preset_index_coded(p) for p in r["presets"][:r["npresets"]]] ==
+                [int(t) for t in o["presets"][:o["npresets"]]])
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
