@@ -572,7 +572,7 @@ SERVE_WORKLOAD = dict(
          "8 GiB; continuous batching against one frame at a time",
     sizes=[(640, 360), (1280, 720), (1920, 1080), (3840, 2160)], bitdepths=(8, 10),
     requests=10000, rates=(0.5, 0.8, 1.0, 1.5), budget=8 << 30, contents=2, seed=0,
-    base_seed=4000, verify_requests=400)
+    base_seed=4000, verify_requests=400, batch_bytes=256 << 20)
 
 
 def run_serve(args):
@@ -614,12 +614,12 @@ def run_serve(args):
     batched_be = serve.CudaBackend(ctx, budget)
     single_be = serve.CudaBackend(ctx, budget)
     shapes = [(w, h, bd) for (w, h) in W["sizes"] for bd in W["bitdepths"]]
-    batched_be.prewarm(shapes, 24)      # up to three batches of each size in flight
+    batched_be.prewarm(shapes, 24)      # up to four batches of each size held
     single_be.prewarm(shapes, 2)
 
     def batched(on_done=None):
-        return serve.Server(batched_be, budget, max_batch=cdef.MAX_BATCH, max_inflight=2,
-                            on_done=on_done)
+        return serve.Server(batched_be, budget, max_batch=cdef.MAX_BATCH, max_inflight=3,
+                            on_done=on_done, max_batch_bytes=W["batch_bytes"])
 
     def one_at_a_time(on_done=None):
         return serve.Server(single_be, budget, max_batch=1, max_inflight=1, on_done=on_done)

@@ -114,9 +114,13 @@ class Server:
     def __init__(self, backend: Backend, budget_bytes: int, max_batch: int = 48,
                  max_inflight: int = 2, clock: Callable[[], float] = time.perf_counter,
                  on_done: Optional[Callable[[Request], None]] = None,
-                 max_ready: Optional[int] = None):
+                 max_ready: Optional[int] = None, max_batch_bytes: int = 0):
         if max_batch < 1 or max_inflight < 1:
             raise ValueError("max_batch and max_inflight must be >= 1")
+        # a batch also ends before its device buffers pass this many bytes
+        # (0: no limit), so that a burst of large frames does not become one
+        # long launch that every later request waits for
+        self.max_batch_bytes = int(max_batch_bytes)
         # admitted requests waiting for a launch: by default one batch
         self.max_ready = max_batch if max_ready is None else max_ready
         self.backend = backend
@@ -202,7 +206,13 @@ class Server:
         # 3. continuous batching: launch what is admitted while the device
         #    has room for another batch
         while self.ready and len(self.inflight) < self.max_inflight:
-            batch, self.ready = self.ready[:self.max_batch], self.ready[self.max_batch:]
+            cut, size = 0, 0
+            while cut < min(len(self.ready), self.max_batch):
+                size += self.ready[cut].need
+                if cut > 0 and self.max_batch_bytes and size > self.max_batch_bytes:
+                    break
+                cut += 1
+            batch, self.ready = self.ready[:cut], self.ready[cut:]
             try:
                 handle = self.backend.launch(batch)
             except Exception as e:  # noqa: BLE001 - the batch fails, the server goes on

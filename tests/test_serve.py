@@ -277,3 +277,18 @@ def test_admission_window_is_one_batch():
     assert s.in_use == 8 * req(0).width * req(0).height * 3
     drain(s, clk)
     assert len(s.finished) == 20
+
+
+def test_batches_cut_by_bytes():
+    fb, clk = FakeBackend(), Clock()
+    one = 64 * 64 * 3
+    s = serve.Server(fb, budget_bytes=1 << 40, max_batch=48, max_inflight=1, clock=clk,
+                     max_batch_bytes=3 * one)
+    for i in range(10):
+        s.submit(req(i))
+    drain(s, clk)
+    assert [len(b) for b in fb.launches] == [3, 3, 3, 1]
+    big = serve.Server(fb, budget_bytes=1 << 40, max_batch_bytes=one // 2, clock=clk)
+    big.submit(req(99))                 # larger than the cap: still launched alone
+    drain(big, clk)
+    assert fb.launches[-1] == [99]
