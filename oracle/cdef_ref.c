@@ -293,11 +293,11 @@ static int fb_has_coded(const uint8_t *coded, int bw, int bh, int fby, int fbx)
 /* Filters one plane.  sub = 0 for luma (8x8 blocks, 64x64 filter blocks),
  * 1 for 4:2:0 chroma (4x4 blocks, 32x32 filter blocks; section 2: chroma
  * takes the co-located luma direction). */
-static void filter_plane(const uint16_t *in, ptrdiff_t is, uint16_t *out,
-                         ptrdiff_t os, int pw, int ph, int sub, int bitdepth,
-                         const uint8_t *params, int fb_cols,
-                         const uint8_t *dir, const int32_t *var, int bw, int bh,
-                         const uint8_t *coded)
+static void filter_plane_g(const uint16_t *in, ptrdiff_t is, uint16_t *out,
+                           ptrdiff_t os, int pw, int ph, int sub, int chroma, int bitdepth,
+                           const uint8_t *params, int fb_cols,
+                           const uint8_t *dir, const int32_t *var, int bw, int bh,
+                           const uint8_t *coded)
 {
     int bs = 8 >> sub, fbs = 64 >> sub;
     for (int i = 0; i < ph; i++) {
@@ -305,24 +305,34 @@ static void filter_plane(const uint16_t *in, ptrdiff_t is, uint16_t *out,
             int b8 = (i / bs) * bw + (j / bs);
             int fby = i / fbs, fbx = j / fbs;
             const uint8_t *pp = params + (fby * fb_cols + fbx) * CDEF_REF_PARAM_BYTES;
-            int skip_bit = (pp[5] >> sub) & 1;
+            int skip_bit = (pp[5] >> chroma) & 1;
             int on = fb_has_coded(coded, bw, bh, fby, fbx) &&
                      (!coded || coded[b8] || skip_bit);
             if (!on) {
                 out[(ptrdiff_t)i * os + j] = in[(ptrdiff_t)i * is + j];
                 continue;
             }
-            int pri = pp[2 * sub], sec = pp[2 * sub + 1];
+            int pri = pp[2 * chroma], sec = pp[2 * chroma + 1];
             if (skip_bit && pri == 0 && sec == 0) {
                 pri = 19;
                 sec = 7;
             }
             cdef_ref_eff_params e;
-            cdef_ref_block_params(pri, sec, pp[4], sub, bitdepth, sub ? 0 : var[b8], &e);
+            cdef_ref_block_params(pri, sec, pp[4], chroma, bitdepth, chroma ? 0 : var[b8], &e);
             out[(ptrdiff_t)i * os + j] =
                 (uint16_t)cdef_ref_filter_sample(in, pw, ph, is, i, j, dir[b8], &e);
         }
     }
+}
+
+static void filter_plane(const uint16_t *in, ptrdiff_t is, uint16_t *out,
+                         ptrdiff_t os, int pw, int ph, int sub, int bitdepth,
+                         const uint8_t *params, int fb_cols,
+                         const uint8_t *dir, const int32_t *var, int bw, int bh,
+                         const uint8_t *coded)
+{
+    filter_plane_g(in, is, out, os, pw, ph, sub, sub, bitdepth, params, fb_cols, dir, var, bw,
+                   bh, coded);
 }
 
 static int valid_params(const uint8_t *params, int nblocks)
@@ -841,6 +851,52 @@ int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
                     gen_dist(dist_luma, dist_chroma, width, b, best_set[id]))
                     id = k;
         block_ids[b] = (uint8_t)id;
+    }
+    return 0;
+}
+
+/* Chroma formats other than 4:2:0 (section 4, last paragraph; reading R25):
+ *   format 422: chroma planes are w/2 x h; their subsampling differs
+ *               horizontally and vertically, so chroma is not filtered (the
+ *               output planes equal the input planes);
+ *   format 444: chroma planes are w x h; each is filtered like the luma
+ *               plane (8x8 blocks, 64x64 filter blocks) with the chroma
+ *               strengths and damping (no contrast adjustment) and the
+ *               co-located luma block's direction.
+ * Luma is filtered as for 4:2:0; skip semantics as cdef_ref_filter_frame_coded. */
+int cdef_ref_filter_frame_format(int w, int h, int bitdepth, int format,
+                                 const uint16_t *y, ptrdiff_t ys,
+                                 const uint16_t *u, ptrdiff_t us,
+                                 const uint16_t *v, ptrdiff_t vs,
+                                 const uint8_t *params, const uint8_t *coded,
+                                 const uint8_t *dir, const int32_t *var,
+                                 uint16_t *oy, ptrdiff_t oys,
+                                 uint16_t *ou, ptrdiff_t ous,
+                                 uint16_t *ov, ptrdiff_t ovs)
+{
+    if (format == 420)
+        return cdef_ref_filter_frame_coded(w, h, bitdepth, y, ys, u, us, v, vs, params, coded,
+                                           dir, var, oy, oys, ou, ous, ov, ovs);
+    if (format != 422 && format != 444)
+        return -1;
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    if (!valid_params(params, fb_cols * fb_rows))
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    filter_plane(y, ys, oy, oys, w, h, 0, bitdepth, params, fb_cols, dir, var, bw, bh, coded);
+    if (format == 422) {
+        for (int i = 0; i < h; i++)
+            for (int j = 0; j < w / 2; j++) {
+                ou[(ptrdiff_t)i * ous + j] = u[(ptrdiff_t)i * us + j];
+                ov[(ptrdiff_t)i * ovs + j] = v[(ptrdiff_t)i * vs + j];
+            }
+    } else {
+        filter_plane_g(u, us, ou, ous, w, h, 0, 1, bitdepth, params, fb_cols, dir, var, bw, bh,
+                       coded);
+        filter_plane_g(v, vs, ov, ovs, w, h, 0, 1, bitdepth, params, fb_cols, dir, var, bw, bh,
+                       coded);
     }
     return 0;
 }

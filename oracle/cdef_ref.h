@@ -107,6 +107,19 @@ int cdef_ref_filter_frame_coded(int w, int h, int bitdepth,
                                 uint16_t *ou, ptrdiff_t ous,
                                 uint16_t *ov, ptrdiff_t ovs);
 
+/* Chroma formats (reading R25 in cdef_ref.c): format 420, 422 (chroma
+ * planes w/2 x h, not filtered) or 444 (chroma planes w x h, filtered in
+ * 8x8 blocks with the chroma strengths and the luma directions). */
+int cdef_ref_filter_frame_format(int w, int h, int bitdepth, int format,
+                                 const uint16_t *y, ptrdiff_t ys,
+                                 const uint16_t *u, ptrdiff_t us,
+                                 const uint16_t *v, ptrdiff_t vs,
+                                 const uint8_t *params, const uint8_t *coded,
+                                 const uint8_t *dir, const int32_t *var,
+                                 uint16_t *oy, ptrdiff_t oys,
+                                 uint16_t *ou, ptrdiff_t ous,
+                                 uint16_t *ov, ptrdiff_t ovs);
+
 /* Section 5, two-pass search, first pass: for each filter block b and each of
  * the 64 (primary 0..15) x (secondary {0,1,2,4}) pairs, the SSE between the
  * source and the decoded frame filtered with that pair at damping D.

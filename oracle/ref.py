@@ -83,6 +83,10 @@ def lib():
             [C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 3
             + [_u8p, C.c_void_p, _u8p, _i32p] + [_u16p, C.c_ssize_t] * 3)
         L.cdef_ref_filter_frame_coded.restype = C.c_int
+        L.cdef_ref_filter_frame_format.argtypes = (
+            [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 3
+            + [_u8p, C.c_void_p, _u8p, _i32p] + [_u16p, C.c_ssize_t] * 3)
+        L.cdef_ref_filter_frame_format.restype = C.c_int
         L.cdef_ref_distortion.argtypes = (
             [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6
             + [_i64p, _i64p])
@@ -310,3 +314,20 @@ def search_strengths_coded(rec, src, bitdepth: int, damping: int, lam: int, code
     out = select_presets_general(dl, dc, 128, sk, lam, refine_passes)
     out.update(dist_luma=dl, dist_chroma=dc, skipped=sk)
     return out
+
+
+def filter_frame_format(y, u, v, bitdepth: int, params, fmt: int, coded=None):
+    """The filter for chroma format 420, 422 or 444 (reading R25)."""
+    y, u, v = _u16(y), _u16(u), _u16(v)
+    h, w = y.shape
+    dirs, var = find_dir(y, bitdepth)
+    prm = np.ascontiguousarray(params, dtype=np.uint8)
+    cod = None if coded is None else np.ascontiguousarray(coded, dtype=np.uint8)
+    oy, ou, ov = np.zeros_like(y), np.zeros_like(u), np.zeros_like(v)
+    rc = lib().cdef_ref_filter_frame_format(
+        w, h, bitdepth, fmt, y, w, u, u.shape[1], v, v.shape[1], prm.reshape(-1),
+        None if cod is None else cod.ctypes.data, np.ascontiguousarray(dirs, np.uint8).reshape(-1),
+        np.ascontiguousarray(var, np.int32).reshape(-1), oy, w, ou, ou.shape[1], ov, ov.shape[1])
+    if rc != 0:
+        raise ValueError("oracle rejected filter_frame_format arguments")
+    return oy, ou, ov

@@ -912,3 +912,58 @@ def test_skipped_blocks_leave_the_selection(ref):
     assert list(full["presets"]) == list(sub["presets"])
     assert list(full["block_ids"][sk == 0]) == list(sub["block_ids"])
     assert (full["block_ids"][sk == 1] == 0).all()
+
+
+# --------------------------------------------------------------- chroma formats (section 4)
+def _format_frame(fmt, w=192, h=136, bd=8, seed=60):
+    rng = np.random.default_rng(seed)
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(w, h, bd, 32, seed=seed)
+    cw, ch = (w // 2, h) if fmt == 422 else (w, h)
+    mx = (1 << bd) - 1
+    u = np.clip(f.rec[0][:ch, :cw].astype(np.int64) // 2 + rng.integers(0, 40, (ch, cw)), 0, mx)
+    v = np.clip(mx - f.rec[0][:ch, :cw].astype(np.int64) + rng.integers(0, 40, (ch, cw)), 0, mx)
+    return f, u.astype(np.uint16), v.astype(np.uint16), synth.random_params(rng, w, h)
+
+
+def test_422_chroma_is_not_filtered(ref):
+    """Section 4: with different horizontal and vertical subsampling (4:2:2)
+    the filter is disabled for chroma; luma is filtered as for 4:2:0."""
+    f, u, v, params = _format_frame(422)
+    oy, ou, ov = ref.filter_frame_format(f.rec[0], u, v, 8, params, 422)
+    assert np.array_equal(ou, u) and np.array_equal(ov, v)
+    assert np.array_equal(oy, ref.filter_frame(*f.rec, 8, params)[0])
+
+
+def test_444_chroma_matches_luma_path_for_secondary_only(ref):
+    """4:4:4 chroma is filtered like luma with the chroma parameters: with
+    primary strengths 0 (no contrast adjustment involved) a chroma plane
+    equal to the luma plane at chroma damping D + 1 gives the luma output
+    at damping D (chroma uses D - 1, section 3.2)."""
+    f, _, _, params = _format_frame(444, bd=10, seed=61)
+    params[..., 0] = params[..., 2] = 0
+    params[..., 4] = np.minimum(params[..., 4], 5)
+    y = f.rec[0]
+    luma = ref.filter_frame_format(y, y, y, 10, params, 444)[0]
+    up = params.copy()
+    up[..., 4] += 1
+    up[..., 3] = up[..., 1]
+    chroma = ref.filter_frame_format(y, y, y, 10, up, 444)
+    assert np.array_equal(chroma[1], luma) and np.array_equal(chroma[2], luma)
+
+
+def test_444_identities(ref):
+    f, u, v, params = _format_frame(444, seed=62)
+    params[..., 2] = params[..., 3] = 0                      # chroma strengths 0
+    oy, ou, ov = ref.filter_frame_format(f.rec[0], u, v, 8, params, 444)
+    assert np.array_equal(ou, u) and np.array_equal(ov, v)
+    const = np.full_like(u, 77)
+    params[..., 2], params[..., 3] = 9, 2
+    _, cu, _ = ref.filter_frame_format(f.rec[0], const, const, 8, params, 444)
+    assert np.array_equal(cu, const)
+
+
+def test_unknown_format_rejected(ref):
+    f, u, v, params = _format_frame(444, seed=63)
+    with pytest.raises(ValueError):
+        ref.filter_frame_format(f.rec[0], u, v, 8, params, 411)
