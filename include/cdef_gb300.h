@@ -6,8 +6,14 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- *  - Frames are 4:2:0.  The luma plane is W x H, both multiples of 8
- *    (section 2 works on 8x8 blocks); the chroma planes are W/2 x H/2.
+ *  - Frames are 4:2:0: the luma plane is W x H, both multiples of 8
+ *    (section 2 works on 8x8 blocks), the chroma planes W/2 x H/2.
+ *    cdef_filter_frame and cdef_filter_frame_coded also take 4:2:2 frames
+ *    (chroma W/2 x H: section 4 disables chroma filtering when the
+ *    subsampling differs horizontally and vertically, so the chroma planes
+ *    are copied) and 4:4:4 frames (chroma W x H: each chroma plane is
+ *    filtered in 8x8 blocks with the chroma strengths and damping and the
+ *    co-located luma direction).  The format follows from the plane sizes.
  *  - Samples are unsigned integers stored planar and row-major: uint8_t for
  *    bit depth 8, uint16_t (value in the low bits) for bit depths 10 and 12.
  *  - Plane memory is DEVICE memory owned by the caller.  `data` must be

@@ -136,24 +136,32 @@ def pitch_samples(width: int, bitdepth: int) -> int:
     return ((width * b + 15) // 16 * 16) // b
 
 
+def chroma_size(width: int, height: int, chroma: int = 420):
+    """Chroma plane size for format 420, 422 or 444."""
+    return {420: (width // 2, height // 2), 422: (width // 2, height),
+            444: (width, height)}[chroma]
+
+
 @dataclass
 class Frame:
-    """A 4:2:0 frame in device memory: y, u, v are pitched 2-D tensors."""
+    """A frame in device memory: y, u, v are pitched 2-D tensors; `chroma`
+    is the format (420, 422 or 444)."""
     y: torch.Tensor
     u: torch.Tensor
     v: torch.Tensor
     width: int
     height: int
     bitdepth: int
+    chroma: int = 420
 
     def planes(self):
         return (self.y, self.u, self.v)
 
     def desc(self) -> FrameDesc:
         d = FrameDesc()
+        cw, ch = chroma_size(self.width, self.height, self.chroma)
         for name, t, w, h in (("y", self.y, self.width, self.height),
-                              ("u", self.u, self.width // 2, self.height // 2),
-                              ("v", self.v, self.width // 2, self.height // 2)):
+                              ("u", self.u, cw, ch), ("v", self.v, cw, ch)):
             p = getattr(d, name)
             p.data = t.data_ptr()
             p.width = w
@@ -165,21 +173,24 @@ class Frame:
     def to_numpy(self):
         """Host copies of the visible planes as uint16 arrays."""
         out = []
-        for t, w in ((self.y, self.width), (self.u, self.width // 2), (self.v, self.width // 2)):
+        cw = chroma_size(self.width, self.height, self.chroma)[0]
+        for t, w in ((self.y, self.width), (self.u, cw), (self.v, cw)):
             a = t[:, :w].cpu().numpy()
             out.append(a.view(np.uint16) if a.dtype == np.int16 else a.astype(np.uint16))
         return tuple(out)
 
 
-def alloc_frame(width: int, height: int, bitdepth: int, device="cuda", fill=None) -> Frame:
+def alloc_frame(width: int, height: int, bitdepth: int, device="cuda", fill=None,
+                chroma: int = 420) -> Frame:
     dt = sample_dtype(bitdepth)
+    cw, ch = chroma_size(width, height, chroma)
     planes = []
-    for w, h in ((width, height), (width // 2, height // 2), (width // 2, height // 2)):
+    for w, h in ((width, height), (cw, ch), (cw, ch)):
         t = torch.empty((h, pitch_samples(w, bitdepth)), dtype=dt, device=device)
         if fill is not None:
             t.fill_(fill)
         planes.append(t)
-    return Frame(*planes, width, height, bitdepth)
+    return Frame(*planes, width, height, bitdepth, chroma)
 
 
 def packed_layout(width: int, height: int, bitdepth: int, extra_bytes: int = 0):
@@ -217,7 +228,9 @@ def frame_from_numpy(planes, bitdepth: int, device="cuda", pin=False) -> Frame:
     device='cpu' and pin=True, a pinned host frame)."""
     y = planes[0]
     h, w = y.shape
-    f = alloc_frame(w, h, bitdepth, device="cpu")
+    ch, cw = np.asarray(planes[1]).shape
+    chroma = {(w // 2, h // 2): 420, (w // 2, h): 422, (w, h): 444}[(cw, ch)]
+    f = alloc_frame(w, h, bitdepth, device="cpu", chroma=chroma)
     for t, a in zip(f.planes(), planes):
         a = np.asarray(a)
         if bitdepth == 8:
@@ -226,9 +239,9 @@ def frame_from_numpy(planes, bitdepth: int, device="cuda", pin=False) -> Frame:
             t[:, :a.shape[1]] = torch.from_numpy(a.astype(np.uint16).view(np.int16))
     if device == "cpu":
         if pin:
-            f = Frame(*(t.pin_memory() for t in f.planes()), w, h, bitdepth)
+            f = Frame(*(t.pin_memory() for t in f.planes()), w, h, bitdepth, chroma)
         return f
-    return Frame(*(t.to(device) for t in f.planes()), w, h, bitdepth)
+    return Frame(*(t.to(device) for t in f.planes()), w, h, bitdepth, chroma)
 
 
 def params_tensor(params: np.ndarray, device="cuda") -> torch.Tensor:

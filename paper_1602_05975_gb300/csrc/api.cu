@@ -37,6 +37,9 @@ struct cdef_ctx {
     int refine_passes;            // preset re-optimisation passes of the search (0 = greedy)
     int search_key_refine;        // refine_passes search_exec was recorded with
     std::unordered_map<uint64_t, SearchTune> *tuned;  // autotuned, per batch shape
+    uint8_t *maps_dir;            // direction maps of 4:4:4 filtering
+    int32_t *maps_var;
+    size_t maps_blocks;
 };
 
 namespace {
@@ -67,23 +70,41 @@ int check_plane(const cdef_plane &p, int w, int h, int bytes)
     return CDEF_OK;
 }
 
-int check_frame(const cdef_frame *f)
+// Chroma format from the plane sizes: 420 (W/2 x H/2), 422 (W/2 x H),
+// 444 (W x H); 0 for anything else.
+int chroma_format(const cdef_frame *f)
+{
+    const int w = f->y.width, h = f->y.height, cw = f->u.width, ch = f->u.height;
+    if (cw == w / 2 && ch == h / 2) return 420;
+    if (cw == w / 2 && ch == h) return 422;
+    if (cw == w && ch == h) return 444;
+    return 0;
+}
+
+// `formats`: bit 0 4:2:0, bit 1 4:2:2, bit 2 4:4:4 accepted.
+int check_frame(const cdef_frame *f, int formats = 1)
 {
     if (!f) return CDEF_ERR_ARG;
     if (f->bitdepth != 8 && f->bitdepth != 10 && f->bitdepth != 12) return CDEF_ERR_BITDEPTH;
     const int w = f->y.width, h = f->y.height;
     if (w <= 0 || h <= 0 || w % 8 || h % 8) return CDEF_ERR_SIZE;
+    const int fmt = chroma_format(f);
+    if (!((fmt == 420 && (formats & 1)) || (fmt == 422 && (formats & 2)) ||
+          (fmt == 444 && (formats & 4))))
+        return CDEF_ERR_SIZE;
+    const int cw = f->u.width, ch = f->u.height;
     const int b = sample_bytes(f->bitdepth);
     int rc;
     if ((rc = check_plane(f->y, w, h, b))) return rc;
-    if ((rc = check_plane(f->u, w / 2, h / 2, b))) return rc;
-    if ((rc = check_plane(f->v, w / 2, h / 2, b))) return rc;
+    if ((rc = check_plane(f->u, cw, ch, b))) return rc;
+    if ((rc = check_plane(f->v, cw, ch, b))) return rc;
     return CDEF_OK;
 }
 
 bool same_geometry(const cdef_frame *a, const cdef_frame *b)
 {
-    return a->bitdepth == b->bitdepth && a->y.width == b->y.width && a->y.height == b->y.height;
+    return a->bitdepth == b->bitdepth && a->y.width == b->y.width && a->y.height == b->y.height &&
+           a->u.width == b->u.width && a->u.height == b->u.height;
 }
 
 bool overlaps(const cdef_plane &a, const cdef_plane &b)
@@ -164,6 +185,7 @@ int fill_filter_frame(FilterFrameDev &d, const cdef_frame *in, const cdef_frame 
                       int block_start, const uint8_t *coded = nullptr)
 {
     d.coded = coded;
+    d.mode = 0;
     const cdef_plane *pi[3] = {&in->y, &in->u, &in->v};
     const cdef_plane *po[3] = {&out->y, &out->u, &out->v};
     for (int i = 0; i < 3; i++) {
@@ -257,6 +279,8 @@ int cdef_ctx_destroy(cdef_ctx *ctx)
     if (ctx->dev_results) cudaFree(ctx->dev_results);
     if (ctx->host_results) cudaFreeHost(ctx->host_results);
     if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->maps_dir) cudaFree(ctx->maps_dir);
+    if (ctx->maps_var) cudaFree(ctx->maps_var);
     if (ctx->work) cudaFree(ctx->work);
     if (ctx->search_exec) cudaGraphExecDestroy(ctx->search_exec);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
@@ -333,6 +357,67 @@ int cdef_find_dir(cdef_ctx *ctx, const cdef_plane *luma, int32_t bitdepth, uint8
 
 namespace {
 
+// One launch of the filter over a single plane in the luma slot: mode 1 the
+// luma plane, mode 2 a 4:4:4 chroma plane (chroma parameters, maps given).
+int plane_pass(cdef_ctx *ctx, const cdef_frame *in, const cdef_plane &pin, const cdef_plane &pout,
+               const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
+               const uint8_t *coded, int mode, bool overlap, cudaStream_t s)
+{
+    FilterBatch<1> b;
+    b.n = 1;
+    b.total_blocks = fb_count(in);
+    FilterFrameDev &d = b.f[0];
+    memset(&d, 0, sizeof(d));
+    for (int i = 0; i < 3; i++) {
+        d.p[i].in = static_cast<const uint8_t *>(pin.data);
+        d.p[i].out = static_cast<uint8_t *>(pout.data);
+        d.p[i].in_pitch = pin.pitch_bytes;
+        d.p[i].out_pitch = pout.pitch_bytes;
+        d.p[i].w = pin.width;
+        d.p[i].h = pin.height;
+    }
+    d.params = params;
+    d.dir = dir;
+    d.var = var;
+    d.coded = coded;
+    d.mode = mode;
+    d.bitdepth = in->bitdepth;
+    d.fb_cols = (in->y.width + 63) / 64;
+    d.fb_rows = (in->y.height + 63) / 64;
+    d.block_start = 0;
+    const int bytes = sample_bytes(in->bitdepth);
+    int rc = encode_plane(&d.tmap[0], pin, bytes, luma_box_cols(bytes), kLumaBoxRows);
+    if (rc) return rc;
+    d.tmap[1] = d.tmap[2] = d.tmap[0];   // not loaded in modes 1 and 2
+    unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
+    return cuda_status(launch_filter_single(b, ctx->status, work, overlap, s));
+}
+
+int ensure_maps(cdef_ctx *ctx, size_t blocks)
+{
+    if (ctx->maps_blocks >= blocks) return CDEF_OK;
+    const size_t bytes = blocks * (sizeof(uint8_t) + sizeof(int32_t));
+    const size_t old = ctx->maps_blocks * (sizeof(uint8_t) + sizeof(int32_t));
+    if (ctx->budget && ctx->used - old + bytes > ctx->budget) return CDEF_ERR_NOMEM;
+    if (ctx->maps_var) cudaFree(ctx->maps_var);
+    if (ctx->maps_dir) cudaFree(ctx->maps_dir);
+    ctx->maps_var = nullptr;
+    ctx->maps_dir = nullptr;
+    ctx->used -= old;
+    ctx->maps_blocks = 0;
+    if (cudaMalloc(&ctx->maps_var, blocks * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&ctx->maps_dir, blocks) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->maps_var) cudaFree(ctx->maps_var);
+        ctx->maps_var = nullptr;
+        ctx->maps_dir = nullptr;
+        return CDEF_ERR_NOMEM;
+    }
+    ctx->maps_blocks = blocks;
+    ctx->used += bytes;
+    return CDEF_OK;
+}
+
 int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params,
                const uint8_t *dir, const int32_t *var, const uint8_t *coded,
                const cdef_frame *out, void *cuda_stream)
@@ -340,18 +425,52 @@ int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params
     if (!ctx || !in || !out || !params) return CDEF_ERR_ARG;
     if ((dir == nullptr) != (var == nullptr)) return CDEF_ERR_ARG;
     int rc;
-    if ((rc = check_frame(in)) || (rc = check_frame(out))) return rc;
+    if ((rc = check_frame(in, 7)) || (rc = check_frame(out, 7))) return rc;
     if (!same_geometry(in, out)) return CDEF_ERR_SIZE;
     if (frames_overlap(in, out)) return CDEF_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return CDEF_ERR_CUDA;
-    FilterBatch<1> b;
-    b.n = 1;
-    b.total_blocks = fb_count(in);
-    if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0, coded))) return rc;
-    unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
-    return cuda_status(launch_filter_single(b, ctx->status, work, ctx->overlap,
-                                            static_cast<cudaStream_t>(cuda_stream)));
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int fmt = chroma_format(in);
+    if (fmt == 420) {
+        FilterBatch<1> b;
+        b.n = 1;
+        b.total_blocks = fb_count(in);
+        if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0, coded))) return rc;
+        unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
+        return cuda_status(launch_filter_single(b, ctx->status, work, ctx->overlap, s));
+    }
+    if (fmt == 422) {
+        // section 4: chroma subsampled differently in the two directions is
+        // not filtered; luma as for 4:2:0
+        if ((rc = plane_pass(ctx, in, in->y, out->y, params, dir, var, coded, 1, ctx->overlap, s)))
+            return rc;
+        const size_t row = (size_t)in->u.width * sample_bytes(in->bitdepth);
+        const cdef_plane *ci[2] = {&in->u, &in->v}, *co[2] = {&out->u, &out->v};
+        for (int k = 0; k < 2; k++)
+            if (cudaMemcpy2DAsync(co[k]->data, co[k]->pitch_bytes, ci[k]->data, ci[k]->pitch_bytes,
+                                  row, ci[k]->height, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                cudaGetLastError();
+                return CDEF_ERR_CUDA;
+            }
+        return CDEF_OK;
+    }
+    // 4:4:4: the luma directions first (unless given), then each plane in
+    // the luma geometry; every launch waits for the one before it (they
+    // share the maps)
+    if (!dir) {
+        const size_t blocks = (size_t)(in->y.width / 8) * (in->y.height / 8);
+        if ((rc = ensure_maps(ctx, blocks))) return rc;
+        dir = ctx->maps_dir;
+        var = ctx->maps_var;
+        if ((rc = cuda_status(launch_find_dir(static_cast<const uint8_t *>(in->y.data),
+                                              in->y.pitch_bytes, in->y.width, in->y.height,
+                                              in->bitdepth, ctx->maps_dir, ctx->maps_var, s))))
+            return rc;
+    }
+    if ((rc = plane_pass(ctx, in, in->y, out->y, params, dir, var, coded, 1, false, s))) return rc;
+    if ((rc = plane_pass(ctx, in, in->u, out->u, params, dir, var, coded, 2, false, s))) return rc;
+    return plane_pass(ctx, in, in->v, out->v, params, dir, var, coded, 2, false, s);
 }
 
 }  // namespace

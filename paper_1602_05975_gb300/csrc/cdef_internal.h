@@ -31,6 +31,9 @@ struct FilterFrameDev {  // aligned as CUtensorMap requires
     const uint8_t *dir;              // optional 8x8 maps (NULL: fused search)
     const int32_t *var;
     const uint8_t *coded;            // optional 8x8 coded-residual map (NULL: all coded)
+    int mode;                        // 0: 4:2:0 luma + chroma; 1: the luma plane alone;
+                                     // 2: a full-resolution (4:4:4) chroma plane in the
+                                     //    luma slot, with maps (chroma parameters)
     int bitdepth;
     int fb_cols, fb_rows;
     int block_start;                 // first CTA index of this frame

@@ -170,9 +170,10 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
     }
 
     // does the 2-pixel halo of this block reach outside the frame?
+    const bool with_chroma = F.mode == 0;   // 4:2:0 chroma rides along
     const bool border = fby == 0 || fbx == 0 || ly0 + 66 > H || lx0 + 66 > W ||
-                        cy0 + 34 > CH || cx0 + 34 > CW;
-    stage_relayout<T, kThreads>(sm.t, raw, border, ly0, lx0, H, W, cy0, cx0, CH, CW);
+                        (with_chroma && (cy0 + 34 > CH || cx0 + 34 > CW));
+    stage_relayout<T, kThreads>(sm.t, raw, border, ly0, lx0, H, W, cy0, cx0, CH, CW, with_chroma);
     __syncthreads();
 
     // ---- direction search
@@ -212,7 +213,10 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         sm.dir[tid] = (uint8_t)d;
         sm.var[tid] = v;
         sm.coded[tid] = (uint8_t)coded;
-        sm.lb[tid] = make_block_consts(make_eff(prm.pri_y, prm.sec_y, prm.damping, false, v, sh8));
+        // mode 2: the plane in the luma slot is a 4:4:4 chroma plane
+        sm.lb[tid] = F.mode == 2
+                         ? make_block_consts(make_eff(prm.pri_uv, prm.sec_uv, prm.damping, true, 0, sh8))
+                         : make_block_consts(make_eff(prm.pri_y, prm.sec_y, prm.damping, false, v, sh8));
     }
     if (tid == 64)
         sm.cb = make_block_consts(make_eff(prm.pri_uv, prm.sec_uv, prm.damping, true, 0, sh8));
@@ -226,15 +230,16 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
     const int warp = tid >> 5, lane = tid & 31;
     if (F.bitdepth > 10) {
         // 12-bit: scalar path over every sample
-        for (int i = tid; i < 64 * 64 + 2 * 32 * 32; i += kThreads) {
+        for (int i = tid; i < (with_chroma ? 64 * 64 + 2 * 32 * 32 : 64 * 64); i += kThreads) {
             const int pl = i < 4096 ? 0 : (i < 5120 ? 1 : 2);
             const int j = pl == 0 ? i : (i - 4096 - (pl - 1) * 1024);
             const int w = pl ? 32 : 64, rr = j / w, cc = j - rr * w;
             const int gy = (pl ? cy0 : ly0) + rr, gx = (pl ? cx0 : lx0) + cc;
             if (gy >= F.p[pl].h || gx >= F.p[pl].w) continue;
             const int blk = pl ? (rr >> 2) * 8 + (cc >> 2) : (rr >> 3) * 8 + (cc >> 3);
-            const Eff e = pl ? make_eff(prm.pri_uv, prm.sec_uv, prm.damping, true, 0, sh8)
-                             : make_eff(prm.pri_y, prm.sec_y, prm.damping, false, sm.var[blk], sh8);
+            const bool cpl = pl || F.mode == 2;   // chroma parameters
+            const Eff e = cpl ? make_eff(prm.pri_uv, prm.sec_uv, prm.damping, true, 0, sh8)
+                              : make_eff(prm.pri_y, prm.sec_y, prm.damping, false, sm.var[blk], sh8);
             auto px = [&](int r2, int c2) -> int {
                 uint32_t w2;
                 if (pl == 0) {
@@ -247,7 +252,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
                 return w2 ? (int)(w2 - kBias) : -1;
             };
             const int r = 2 + rr, c = pl ? 2 + cc : 8 + cc;
-            const bool on = any_coded && (sm.coded[blk] || (pl ? skip_c : skip_l));
+            const bool on = any_coded && (sm.coded[blk] || (cpl ? skip_c : skip_l));
             reinterpret_cast<T *>(F.p[pl].out + (int64_t)gy * F.p[pl].out_pitch)[gx] =
                 (T)(on ? filter_scalar(px, r, c, sm.dir[blk], e) : px(r, c));
         }
@@ -258,7 +263,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
     // column x pair column, 8 rows), task 1 = row `warp` of 4x4 chroma blocks
     // (lane = block column x column, 4 rows).  One code path for both.
 #pragma unroll 1
-    for (int task = 0; task < 2; task++) {
+    for (int task = 0; task < (with_chroma ? 2 : 1); task++) {
         const bool luma = task == 0;
         const int bx = lane >> 2, sub = lane & 3;
         const int blk = warp * 8 + bx;
@@ -273,7 +278,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         // a block that is not filtered (section 4) takes the identity set
         // (strengths 0: every tap clamps to x, no clip), so the loop below
         // needs no per-word test
-        const bool on = any_coded && (sm.coded[blk] || (luma ? skip_l : skip_c));
+        const bool on = any_coded && (sm.coded[blk] || ((luma && F.mode != 2) ? skip_l : skip_c));
         const BlockC bc = !on ? sm.bz : luma ? sm.lb[blk] : sm.cb;
         const unsigned fl = inside ? bc.flags : 0u;
         const bool any_p = __any_sync(0xffffffffu, fl & 1), any_s = __any_sync(0xffffffffu, fl & 2);
@@ -336,7 +341,7 @@ __device__ __forceinline__ void issue_loads(const FilterBatch<MAXF> &batch, int 
 {
     const BlockRef r = locate(batch, blk);
     const FilterFrameDev &F = batch.f[r.fi];
-    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar);
+    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar, F.mode == 0);
 }
 
 // Persistent: each CTA takes blocks from the launch's work counter

@@ -250,7 +250,7 @@ __device__ __forceinline__ uint32_t mark(uint32_t w, bool lo_in, bool hi_in)
 template <typename T, int kThreads>
 __device__ __forceinline__ void stage_relayout(PairTiles &sm, const RawTiles &raw, bool border,
                                                int ly0, int lx0, int H, int W, int cy0, int cx0,
-                                               int CH, int CW)
+                                               int CH, int CW, bool chroma = true)
 {
     constexpr int B = sizeof(T);
     constexpr uint32_t kb = kBias * kLanes;
@@ -291,7 +291,7 @@ __device__ __forceinline__ void stage_relayout(PairTiles &sm, const RawTiles &ra
     }
     // chroma: (U, V) words, 4 per step; tile column c is raw column c + lead - 2
     constexpr int cc = chroma_box_cols(B), lead = box_lead(B);
-    for (int i = threadIdx.x; i < kChromaRows * (kChromaPitch / 4); i += kThreads) {
+    for (int i = threadIdx.x; chroma && i < kChromaRows * (kChromaPitch / 4); i += kThreads) {
         const int r = i / (kChromaPitch / 4), q = i - r * (kChromaPitch / 4);
         const T *ur = reinterpret_cast<const T *>(raw.u) + r * cc + 4 * q + lead - 2;
         const T *vr = reinterpret_cast<const T *>(raw.v) + r * cc + 4 * q + lead - 2;
@@ -311,16 +311,20 @@ __device__ __forceinline__ void stage_relayout(PairTiles &sm, const RawTiles &ra
 // Issued by one thread: the three tile loads of filter block (fby, fbx)
 // into `raw`, completing on `bar`.  `maps` are the y, u, v tile maps.
 __device__ __forceinline__ void issue_tile_loads(const CUtensorMap *maps, int bitdepth, int fby,
-                                                 int fbx, RawTiles &raw, uint64_t *bar)
+                                                 int fbx, RawTiles &raw, uint64_t *bar,
+                                                 bool chroma = true)
 {
     const int B = bitdepth == 8 ? 1 : 2;
     const int lead = box_lead(B);
     // order earlier generic-proxy reads of this buffer before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(bar, kLumaRows * luma_box_cols(B) * B + 2 * kChromaRows * chroma_box_cols(B) * B);
+    mbar_arrive_expect_tx(bar, kLumaRows * luma_box_cols(B) * B +
+                                   (chroma ? 2 * kChromaRows * chroma_box_cols(B) * B : 0));
     tma_load_2d(raw.y, &maps[0], fbx * 64 - lead, fby * 64 - 2, bar);
-    tma_load_2d(raw.u, &maps[1], fbx * 32 - lead, fby * 32 - 2, bar);
-    tma_load_2d(raw.v, &maps[2], fbx * 32 - lead, fby * 32 - 2, bar);
+    if (chroma) {
+        tma_load_2d(raw.u, &maps[1], fbx * 32 - lead, fby * 32 - 2, bar);
+        tma_load_2d(raw.v, &maps[2], fbx * 32 - lead, fby * 32 - 2, bar);
+    }
 }
 
 }  // namespace tile

@@ -537,3 +537,47 @@ def test_search_coded_parity(cdef, ctx, ref, groups, passes):
                 [int(t) for t in o["presets"][:o["npresets"]]])
         assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
         o0 += b
+
+
+# --------------------------------------------------------------- chroma formats
+@pytest.mark.parametrize("fmt,w,h,bd", [(422, 200, 136, 8), (444, 200, 136, 10),
+                                        (444, 352, 288, 8), (422, 136, 72, 12),
+                                        (444, 72, 64, 12)])
+@pytest.mark.parametrize("with_map", [False, True])
+def test_filter_chroma_formats(cdef, ctx, ref, fmt, w, h, bd, with_map):
+    """4:2:2 (chroma copied, section 4) and 4:4:4 (full-resolution chroma)
+    frames: every output sample equals the oracle's."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(fmt + w + bd)
+    f = synth.make_frame(w, h, bd, 32, seed=950 + w)
+    cw, ch = cdef.chroma_size(w, h, fmt)
+    mx = (1 << bd) - 1
+    u = np.clip(f.rec[0][:ch, :cw].astype(np.int64) // 2 + rng.integers(0, 60, (ch, cw)), 0, mx)
+    v = np.clip(mx - f.rec[0][:ch, :cw].astype(np.int64) + rng.integers(0, 60, (ch, cw)), 0, mx)
+    planes = (f.rec[0], u.astype(np.uint16), v.astype(np.uint16))
+    params = synth.random_params(rng, w, h)
+    params[..., 5] = rng.integers(0, 4, params.shape[:2])
+    coded = (rng.random((h // 8, w // 8)) < 0.6).astype(np.uint8) if with_map else None
+    inp = cdef.frame_from_numpy(planes, bd)
+    out = cdef.alloc_frame(w, h, bd, fill=0, chroma=fmt)
+    prm = cdef.params_tensor(params)
+    if with_map:
+        cdef.cdef_filter_frame_coded(ctx, inp, prm, torch.from_numpy(coded.reshape(-1)).cuda(), out)
+    else:
+        cdef.cdef_filter_frame(ctx, inp, prm, out)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    _assert_frames_equal(out.to_numpy(), ref.filter_frame_format(*planes, bd, params, fmt, coded))
+
+
+def test_chroma_formats_rejected_where_unsupported(cdef, ctx):
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(64, 64, 8, 32, seed=960)
+    y = f.rec[0]
+    inp = cdef.frame_from_numpy((y, y, y), 8)                       # 4:4:4
+    out = cdef.alloc_frame(64, 64, 8, fill=0, chroma=444)
+    with pytest.raises(cdef.CdefError):
+        cdef.cdef_filter_frames(ctx, [inp], [cdef.params_tensor(f.params)], [out])
+    with pytest.raises(cdef.CdefError):
+        cdef.cdef_search_strengths(ctx, [inp], [inp], [4], [16],
+                                   torch.zeros(1, dtype=torch.uint8, device="cuda"))
