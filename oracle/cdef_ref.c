@@ -31,6 +31,7 @@
  */
 #include "cdef_ref.h"
 
+#include <math.h>
 #include <stdlib.h>
 
 static int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -899,4 +900,120 @@ int cdef_ref_filter_frame_format(int w, int h, int bitdepth, int format,
                        coded);
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 5, eq. 14: the SSIM-weighted distortion                          */
+/* ------------------------------------------------------------------------ */
+
+/* Readings R22-R24.  R22: the 8x8 distortion function of eq. 14 is taken
+ * over the 8x8 blocks of each plane (luma 64, each 4:2:0 chroma plane 16 per
+ * filter block), with sigma^2 the population variance of the 64 source
+ * samples and of the 64 filtered decoded samples; chroma sums U and V.
+ * An 8x8 block cut by the frame edge (4:2:0 chroma planes whose size is
+ * not a multiple of 8) uses its n in-frame samples.  R23: C1 = 6.25 *
+ * 4^(bd-8) and C2 = 312.5 * 16^(bd-8) (the constants scale with the units
+ * of a variance and of its square).  R24: the table holds the sum over the
+ * 8x8 blocks of round(256 * D_8x8) (ties away from zero), each D_8x8
+ * evaluated in IEEE double precision in exactly this order:
+ *   vs = (n sum s^2 - (sum s)^2) / n^2, vd likewise,
+ *   D = ((vs + vd) + C1) / (2 sqrt(vs vd + C2)) * sse,
+ * so that the preset search stays in exact integers. */
+static int64_t eq14_term(int64_t n, int64_t s1s, int64_t s2s, int64_t s1d, int64_t s2d,
+                         int64_t sse, int bitdepth)
+{
+    const double c1 = 6.25 * (double)(1 << (2 * (bitdepth - 8)));
+    const double c2 = 312.5 * (double)(1 << (4 * (bitdepth - 8)));
+    const double nn = (double)(n * n);
+    const double vs = (double)(n * s2s - s1s * s1s) / nn;
+    const double vd = (double)(n * s2d - s1d * s1d) / nn;
+    const double num = (vs + vd) + c1;
+    const double den = 2.0 * sqrt(vs * vd + c2);
+    const double d = num / den * (double)sse;
+    return (int64_t)llround(256.0 * d);
+}
+
+static int64_t block_eq14(const uint16_t *rec, ptrdiff_t rs, const uint16_t *src, ptrdiff_t ss,
+                          int pw, int ph, int sub, int bitdepth, int fby, int fbx, int pri,
+                          int sec, int damping, const uint8_t *dir, const int32_t *var, int bw)
+{
+    int bs = 8 >> sub, fbs = 64 >> sub;
+    int64_t total = 0;
+    /* 8x8 blocks of this plane inside the filter block */
+    for (int by = fby * fbs; by < (fby + 1) * fbs && by < ph; by += 8) {
+        for (int bx = fbx * fbs; bx < (fbx + 1) * fbs && bx < pw; bx += 8) {
+            int64_t n = 0, s1s = 0, s2s = 0, s1d = 0, s2d = 0, sse = 0;
+            for (int i = by; i < by + 8 && i < ph; i++) {
+                for (int j = bx; j < bx + 8 && j < pw; j++) {
+                    n++;
+                    int b8 = (i / bs) * bw + (j / bs);
+                    cdef_ref_eff_params e;
+                    cdef_ref_block_params(pri, sec, damping, sub, bitdepth, sub ? 0 : var[b8], &e);
+                    int64_t d = cdef_ref_filter_sample(rec, pw, ph, rs, i, j, dir[b8], &e);
+                    int64_t sv = src[(ptrdiff_t)i * ss + j];
+                    s1s += sv;
+                    s2s += sv * sv;
+                    s1d += d;
+                    s2d += d * d;
+                    sse += (d - sv) * (d - sv);
+                }
+            }
+            total += eq14_term(n, s1s, s2s, s1d, s2d, sse, bitdepth);
+        }
+    }
+    return total;
+}
+
+int cdef_ref_distortion_eq14(int w, int h, int bitdepth, int damping,
+                             const uint16_t *ry, ptrdiff_t rys,
+                             const uint16_t *ru, ptrdiff_t rus,
+                             const uint16_t *rv, ptrdiff_t rvs,
+                             const uint16_t *sy, ptrdiff_t sys,
+                             const uint16_t *su, ptrdiff_t sus,
+                             const uint16_t *sv, ptrdiff_t svs,
+                             int64_t *dist_luma, int64_t *dist_chroma)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    if (damping < 3 || damping > 6)
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    uint8_t *dir = (uint8_t *)malloc((size_t)bw * bh);
+    int32_t *var = (int32_t *)malloc((size_t)bw * bh * sizeof(int32_t));
+    if (!dir || !var) {
+        free(dir);
+        free(var);
+        return -1;
+    }
+    cdef_ref_find_dir(ry, w, h, rys, bitdepth, dir, var);
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    for (int fby = 0; fby < fb_rows; fby++) {
+        for (int fbx = 0; fbx < fb_cols; fbx++) {
+            int b = fby * fb_cols + fbx;
+            for (int p = 0; p < 16; p++) {
+                for (int s = 0; s < 4; s++) {
+                    int q = p * 4 + s;
+                    dist_luma[b * 64 + q] =
+                        block_eq14(ry, rys, sy, sys, w, h, 0, bitdepth, fby, fbx, p,
+                                   sec_values[s], damping, dir, var, bw);
+                    dist_chroma[b * 64 + q] =
+                        block_eq14(ru, rus, su, sus, w / 2, h / 2, 1, bitdepth, fby, fbx, p,
+                                   sec_values[s], damping, dir, var, bw) +
+                        block_eq14(rv, rvs, sv, svs, w / 2, h / 2, 1, bitdepth, fby, fbx, p,
+                                   sec_values[s], damping, dir, var, bw);
+                }
+            }
+        }
+    }
+    free(dir);
+    free(var);
+    return 0;
+}
+
+/* The eq. 14 value of one 8x8 block from its sums (R22-R24), exported for
+ * the pins. */
+int64_t cdef_ref_eq14_term(int64_t n, int64_t s1s, int64_t s2s, int64_t s1d, int64_t s2d,
+                           int64_t sse, int bitdepth)
+{
+    return eq14_term(n, s1s, s2s, s1d, s2d, sse, bitdepth);
 }

@@ -184,6 +184,23 @@ int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
                                     int32_t *presets, int32_t *npresets,
                                     uint8_t *block_ids, int64_t *cost);
 
+/* Section 5, eq. 14 (readings R22-R24 in cdef_ref.c): per filter block, 64
+ * luma and 64 chroma entries sum_8x8 round(256 * D_8x8). */
+int cdef_ref_distortion_eq14(int w, int h, int bitdepth, int damping,
+                             const uint16_t *ry, ptrdiff_t rys,
+                             const uint16_t *ru, ptrdiff_t rus,
+                             const uint16_t *rv, ptrdiff_t rvs,
+                             const uint16_t *sy, ptrdiff_t sys,
+                             const uint16_t *su, ptrdiff_t sus,
+                             const uint16_t *sv, ptrdiff_t svs,
+                             int64_t *dist_luma, int64_t *dist_chroma);
+
+/* round(256 * D_8x8) of eq. 14 from one 8x8 block's sums over its n
+ * in-frame samples: source sum and sum of squares, filtered sum and sum of
+ * squares, squared error. */
+int64_t cdef_ref_eq14_term(int64_t n, int64_t s1s, int64_t s2s, int64_t s1d, int64_t s2d,
+                           int64_t sse, int bitdepth);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,14 +32,16 @@ class EffParams(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no vectorisation flags; -O2 only)."""
+    """Compile the oracle with gcc (no vectorisation flags; -O2 only;
+    floating-point expressions evaluated as written: no fused multiply-add
+    contraction, on any host)."""
     stale = (not os.path.exists(_LIB)
              or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
              or os.path.getmtime(_LIB) < os.path.getmtime(os.path.join(_HERE, "cdef_ref.h")))
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared",
-                               "-Wall", "-Wextra", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -111,6 +113,11 @@ def lib():
             C.c_int, _i64p, _i64p, C.c_int, C.c_void_p, C.c_int64, C.c_int, _i32p,
             C.POINTER(C.c_int32), _u8p, C.POINTER(C.c_int64)]
         L.cdef_ref_select_presets_general.restype = C.c_int
+        L.cdef_ref_distortion_eq14.argtypes = (
+            [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6 + [_i64p, _i64p])
+        L.cdef_ref_distortion_eq14.restype = C.c_int
+        L.cdef_ref_eq14_term.argtypes = [C.c_int64] * 6 + [C.c_int]
+        L.cdef_ref_eq14_term.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -331,3 +338,32 @@ def filter_frame_format(y, u, v, bitdepth: int, params, fmt: int, coded=None):
     if rc != 0:
         raise ValueError("oracle rejected filter_frame_format arguments")
     return oy, ou, ov
+
+
+def distortion_eq14(rec, src, bitdepth: int, damping: int):
+    """Section 5, eq. 14 (readings R22-R24): per filter block 64 luma and 64
+    chroma entries, each the sum over 8x8 blocks of round(256 * D_8x8)."""
+    ry, ru, rv = (_u16(p) for p in rec)
+    sy, su, sv = (_u16(p) for p in src)
+    h, w = ry.shape
+    nb = ((h + 63) // 64) * ((w + 63) // 64)
+    dl = np.zeros(nb * 64, np.int64)
+    dc = np.zeros(nb * 64, np.int64)
+    rc = lib().cdef_ref_distortion_eq14(
+        w, h, bitdepth, damping, ry, w, ru, ru.shape[1], rv, rv.shape[1],
+        sy, w, su, su.shape[1], sv, sv.shape[1], dl, dc)
+    if rc != 0:
+        raise ValueError("oracle rejected distortion_eq14 arguments")
+    return dl.reshape(nb, 64), dc.reshape(nb, 64)
+
+
+def eq14_term(n, s1s, s2s, s1d, s2d, sse, bitdepth: int) -> int:
+    return lib().cdef_ref_eq14_term(n, s1s, s2s, s1d, s2d, sse, bitdepth)
+
+
+def search_strengths_eq14(rec, src, bitdepth: int, damping: int, lam: int,
+                          refine_passes: int = 0):
+    dl, dc = distortion_eq14(rec, src, bitdepth, damping)
+    out = select_presets_general(dl, dc, 64, None, lam, refine_passes)
+    out.update(dist_luma=dl, dist_chroma=dc)
+    return out

@@ -967,3 +967,78 @@ def test_unknown_format_rejected(ref):
     f, u, v, params = _format_frame(444, seed=63)
     with pytest.raises(ValueError):
         ref.filter_frame_format(f.rec[0], u, v, 8, params, 411)
+
+
+# --------------------------------------------------------------- section 5, eq. 14
+def _sums(sv, dv):
+    sv = sv.astype(np.int64).ravel()
+    dv = dv.astype(np.int64).ravel()
+    return (sv.size, int(sv.sum()), int((sv * sv).sum()), int(dv.sum()), int((dv * dv).sum()),
+            int(((dv - sv) ** 2).sum()))
+
+
+def test_eq14_term_invariances(ref):
+    """The 8x8 function of eq. 14 is symmetric in source and decoded block,
+    translation invariant (variances and errors do not change), and scales
+    with the squared error when both variances vanish."""
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        s = rng.integers(0, 256, 64)
+        d = np.clip(s + rng.integers(-20, 21, 64), 0, 255)
+        t = ref.eq14_term(*_sums(s, d), 8)
+        assert t == ref.eq14_term(*_sums(d, s), 8)
+        assert t == ref.eq14_term(*_sums(s + 300, d + 300), 8)
+        assert t >= 0
+    # flat blocks: D = C1 / (2 sqrt(C2)) * sse with C1 = 6.25, C2 = 312.5
+    s = np.full(64, 100)
+    d = np.full(64, 103)
+    assert ref.eq14_term(*_sums(s, d), 8) == round(256 * 6.25 / (2 * 312.5 ** 0.5) * 64 * 9)
+
+
+def test_eq14_constants_scale_with_bit_depth(ref):
+    """R23: at 10 bits samples x4 give exactly 16 times the 8-bit value
+    (before the rounding to 1/256)."""
+    rng = np.random.default_rng(4)
+    for _ in range(100):
+        s = rng.integers(0, 256, 64)
+        d = np.clip(s + rng.integers(-30, 31, 64), 0, 255)
+        t8 = ref.eq14_term(*_sums(s, d), 8)
+        t10 = ref.eq14_term(*_sums(4 * s, 4 * d), 10)
+        assert abs(t10 - 16 * t8) <= 8
+
+
+def test_eq14_large_variance_tends_to_sse(ref):
+    s = np.tile(np.array([0, 255]), 32)
+    d = s.copy()
+    d[0] = 5
+    t = ref.eq14_term(*_sums(s, d), 8)
+    assert abs(t / 256 - 25) < 0.02 * 25
+
+
+def test_eq14_tables_from_decoder_output(ref):
+    """Each table entry is the sum over the 8x8 blocks of every plane of the
+    eq. 14 value of the filter oracle's output for that strength pair
+    (chroma 8x8 blocks cut by the frame edge included)."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(136, 72, 8, 32, seed=71)         # chroma 68x36: partial 8x8 blocks
+    dl, dc = ref.distortion_eq14(f.rec, f.src, 8, 5)
+    params = np.zeros(f.params.shape, np.uint8)
+    params[..., 4] = 5
+    for q in (0, 5, 22, 37, 63):
+        p, s = q >> 2, (0, 1, 2, 4)[q & 3]
+        params[..., 0] = params[..., 2] = p
+        params[..., 1] = params[..., 3] = s
+        out = ref.filter_frame(*f.rec, 8, params)
+        for pl, tab in ((0, dl), (1, dc)):
+            fb = 64 >> (pl > 0)
+            planes = (0,) if pl == 0 else (1, 2)
+            h, w = out[planes[0]].shape
+            for b in range(tab.shape[0]):
+                by, bx = divmod(b, f.params.shape[1])
+                tot = 0
+                for k in planes:
+                    for y in range(by * fb, min((by + 1) * fb, h), 8):
+                        for x in range(bx * fb, min((bx + 1) * fb, w), 8):
+                            tot += ref.eq14_term(*_sums(f.src[k][y:y + 8, x:x + 8],
+                                                        out[k][y:y + 8, x:x + 8]), 8)
+                assert tab[b, q] == tot, (q, pl, b)
