@@ -269,6 +269,23 @@ int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *tuning);
  * the first search).  Host only. */
 int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
 
+/* Distortion measure of cdef_search_strengths (section 5):
+ *   CDEF_METRIC_SSE  (default) D = sum of squared errors over the block;
+ *   CDEF_METRIC_EQ14 D = sum over the 8x8 blocks of each plane (4:2:0 chroma
+ *                    8x8 blocks cut by the frame edge use their samples) of
+ *                    eq. 14, ((s_var + d_var + C1) / (2 sqrt(s_var d_var +
+ *                    C2))) * squared error, with population variances of the
+ *                    source and filtered blocks, C1 = 6.25 * 4^(bd-8), C2 =
+ *                    312.5 * 16^(bd-8); each 8x8 value in units of 1/256,
+ *                    rounded half away from zero after an IEEE
+ *                    double-precision evaluation in a fixed order, so that the
+ *                    tables are exact integers.  Not available with
+ *                    cdef_search_strengths_coded (CDEF_ERR_ARG).
+ * Host only; applies to later searches on the context. */
+#define CDEF_METRIC_SSE 0
+#define CDEF_METRIC_EQ14 1
+int cdef_ctx_set_search_metric(cdef_ctx *ctx, int metric);
+
 /* Preset re-optimisation of cdef_search_strengths (section 5: "iteratively
  * re-optimizing one preset at a time" after the greedy search).  For each
  * N in {2, 4, 8}, starting from the greedy presets 1..N, a pass re-chooses

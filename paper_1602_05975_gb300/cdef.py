@@ -90,6 +90,7 @@ def load():
     L.cdef_ctx_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.cdef_ctx_set_overlap.argtypes = [vp, C.c_int]
     L.cdef_ctx_set_search_refine.argtypes = [vp, C.c_int]
+    L.cdef_ctx_set_search_metric.argtypes = [vp, C.c_int]
     L.cdef_ctx_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.cdef_search_strengths_coded.argtypes = [
         vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(vp), C.POINTER(i32),
@@ -101,7 +102,8 @@ def load():
                  "cdef_filter_frame", "cdef_filter_frame_coded", "cdef_filter_frames",
                  "cdef_search_strengths",
                  "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap",
-                 "cdef_ctx_set_search_refine", "cdef_search_strengths_coded"):
+                 "cdef_ctx_set_search_refine", "cdef_search_strengths_coded",
+                 "cdef_ctx_set_search_metric"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -281,6 +283,11 @@ class Context:
         `max_passes` passes (0 = greedy only)."""
         _check(self._lib.cdef_ctx_set_search_refine(self.handle, int(max_passes)),
                "cdef_ctx_set_search_refine")
+
+    def set_search_metric(self, metric: str):
+        """'sse' (default) or 'eq14' (section 5's SSIM-weighted distortion)."""
+        m = {"sse": 0, "eq14": 1}[metric]
+        _check(self._lib.cdef_ctx_set_search_metric(self.handle, m), "cdef_ctx_set_search_metric")
 
     def set_overlap(self, enable: bool):
         """Declare consecutive filter calls on a stream independent (see

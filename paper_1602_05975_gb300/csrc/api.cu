@@ -35,6 +35,7 @@ struct cdef_ctx {
     SearchTune last;              // configuration of the last search
     bool overlap;                 // filter calls on a stream declared independent
     int refine_passes;            // preset re-optimisation passes of the search (0 = greedy)
+    int metric;                   // search distortion: 0 squared error, 1 eq. 14
     int search_key_refine;        // refine_passes search_exec was recorded with
     std::unordered_map<uint64_t, SearchTune> *tuned;  // autotuned, per batch shape
     uint8_t *maps_dir;            // direction maps of 4:4:4 filtering
@@ -300,6 +301,13 @@ int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *t)
     const int g = t->search_groups, c = t->search_ctas_per_sm;
     if (!(g == 0 || g == 1 || g == 2 || g == 4) || c < 0 || c > 2) return CDEF_ERR_ARG;
     ctx->forced = {g, c};
+    return CDEF_OK;
+}
+
+int cdef_ctx_set_search_metric(cdef_ctx *ctx, int metric)
+{
+    if (!ctx || (metric != CDEF_METRIC_SSE && metric != CDEF_METRIC_EQ14)) return CDEF_ERR_ARG;
+    ctx->metric = metric;
     return CDEF_OK;
 }
 
@@ -680,7 +688,10 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
     // search owns counter pair 0 (filter launches take pairs 1..).
     unsigned *work = ctx->work;
     SearchTune tune;
-    if ((rc = choose_search_tune(ctx, *b, dl, dc, cur, tot, block_ids, skipped, s, &tune))) {
+    if (ctx->metric == CDEF_METRIC_EQ14) {
+        if (coded) { delete b; return CDEF_ERR_ARG; }
+        tune = {8, 2};   // the eq. 14 tables: 8 candidates per work unit
+    } else if ((rc = choose_search_tune(ctx, *b, dl, dc, cur, tot, block_ids, skipped, s, &tune))) {
         delete b;
         return rc;
     }

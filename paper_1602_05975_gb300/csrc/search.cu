@@ -52,6 +52,11 @@ struct SearchSmem {
     int var[64];
     unsigned long long acc[64];       // block totals of the current plane group
     unsigned long long accu[64];      // the part of them from blocks without coded residual
+    unsigned long long acc14c[8];     // eq. 14: chroma block totals of the unit's candidates
+    // eq. 14: sums over the 4-row halves of the 4:2:0 chroma 8x8 blocks,
+    // [plane][block][half][value]: per candidate (r, r(2x + r), r(2(x - s) + r)),
+    // then n, x, x^2, s, s^2, (x - s)^2
+    int e14h[2][16][2][30];
     unsigned long long base[2];       // sum of (x - s)^2 over the same pixels, per plane group
     int blk[2];
     alignas(8) uint64_t bar[2];
@@ -177,12 +182,39 @@ __device__ __forceinline__ int wentry(int N, int lane)
     return e;
 }
 
+// Eq. 14 for one 8x8 block from its sums over its n samples (source sum and
+// sum of squares, filtered sum and sum of squares, squared error), in 1/256
+// units rounded half away from zero.  Every operation is a correctly
+// rounded IEEE double operation, in a fixed order (no contraction): the
+// value is exactly reproducible.
+__device__ long long eq14_value(long long n, long long s1s, long long s2s, long long s1d,
+                                long long s2d, long long sse, int bitdepth)
+{
+    const double c1 = __dmul_rn(6.25, (double)(1 << (2 * (bitdepth - 8))));
+    const double c2 = __dmul_rn(312.5, (double)(1 << (4 * (bitdepth - 8))));
+    const double nn = (double)(n * n);
+    const double vs = __ddiv_rn((double)(n * s2s - s1s * s1s), nn);
+    const double vd = __ddiv_rn((double)(n * s2d - s1d * s1d), nn);
+    const double num = __dadd_rn(__dadd_rn(vs, vd), c1);
+    const double den = __dmul_rn(2.0, __dsqrt_rn(__dadd_rn(__dmul_rn(vs, vd), c2)));
+    const double d = __dmul_rn(__ddiv_rn(num, den), (double)sse);
+    return llround(__dmul_rn(256.0, d));
+}
+
+// kEq14: the tables hold section 5's eq. 14 instead of the squared error:
+// per 8x8 block of each plane ((sigma_s^2 + sigma_d^2 + C1) /
+// (2 sqrt(sigma_s^2 sigma_d^2 + C2))) * squared error, summed over the
+// filter block.  With d = x + r, a candidate needs per 8x8 block the sums
+// of r, r (2x + r) and r (2 (x - s) + r) besides sums that do not depend on
+// it, kept per sample lane (the two samples of a word belong to U and V in
+// the chroma task).
+//
 // kCoded: the 128-combination search of section 5 with section 4's skip
 // semantics.  The (0, 0) slot, whose error is sum (x - s)^2 with no work,
 // evaluates the (19, 7) preset instead; each candidate's sum is also kept
 // for the 8x8 blocks without coded residual, so that the skip-bit-clear
 // entries (those blocks unfiltered) follow as base + total - uncoded part.
-template <typename T, int kG, bool kCoded>
+template <typename T, int kG, bool kCoded, bool kEq14>
 __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global, int grp,
                            SearchSmem &sm, const RawTiles &raw, long long *dist_luma,
                            long long *dist_chroma, uint8_t *skipped)
@@ -220,6 +252,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         sm.var[tid] = bc - sm.cost[tid][(best + 4) & 7];
         sm.acc[tid] = 0;
         sm.accu[tid] = 0;
+        if (tid < 8) sm.acc14c[tid] = 0;
         if (tid < 2) sm.base[tid] = 0;
     }
     __syncthreads();
@@ -305,9 +338,19 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         const uint8_t *sa = luma ? F.src[0] : F.src[1];
         const int64_t spa = luma ? F.src_pitch[0] : F.src_pitch[1];
 
-        uint32_t acc[kN], sse0 = 0;
+        uint32_t acc[kEq14 ? 1 : kN], sse0 = 0;
 #pragma unroll
-        for (int q = 0; q < kN; q++) acc[q] = 0;
+        for (int q = 0; q < (kEq14 ? 1 : kN); q++) acc[q] = 0;
+        // eq. 14: per candidate and sample lane the sums of r, r (2x + r),
+        // r (2 (x - s) + r); then per lane x, x^2, s, s^2, (x - s)^2
+        constexpr int kE = kEq14 ? kN : 1;
+        int e6[kE][6], e0[10];
+#pragma unroll
+        for (int q = 0; q < kE; q++)
+#pragma unroll
+            for (int j = 0; j < 6; j++) e6[q][j] = 0;
+#pragma unroll
+        for (int j = 0; j < 10; j++) e0[j] = 0;
         if (inside) {
 #pragma unroll 1
             for (int i = 0; i < rows; i++) {
@@ -336,6 +379,17 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 // at 8 and 10 bits stays within a signed byte (|r| <= 57).
                 sse0 = add_sq<T>(sse0, X, S);
                 const uint32_t two_xs = sadd16(2u * (X + 4096u * kLanes - S), 0xdf00u * kLanes);
+                uint32_t two_x = 0;
+                if (kEq14) {
+                    const int xl = (int)(X & 0xffffu) - (int)kBias, xh = (int)(X >> 16) - (int)kBias;
+                    const int sl = (int)(S & 0xffffu) - (int)kBias, sh = (int)(S >> 16) - (int)kBias;
+                    e0[0] += xl; e0[1] += xh;
+                    e0[2] += xl * xl; e0[3] += xh * xh;
+                    e0[4] += sl; e0[5] += sh;
+                    e0[6] += sl * sl; e0[7] += sh * sh;
+                    e0[8] += (xl - sl) * (xl - sl); e0[9] += (xh - sh) * (xh - sh);
+                    two_x = sadd16(X + X, 0xfe00u * kLanes);   // 2x - 256 per lane
+                }
                 const uint32_t rlo = __vmaxu2(mn - X + 2048u * kLanes, 1792u * kLanes) - 1792u * kLanes;
                 const uint32_t rhi = mx - X + 256u * kLanes;
                 uint32_t Q[4], Qr[4];
@@ -373,63 +427,169 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                         // clip cannot bind: it is applied without a test.
                         if (s > 0 || slot19) rb = __vminu2(__vmaxu2(rb, rlo), rhi);
                         const uint32_t a = sadd16(rb, two_xs);           // 2 (x - s) + r
-                        acc[pp * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)__byte_perm(rb, 0, 0x0020),
-                                                              (int)acc[pp * 4 + s]);
+                        const uint32_t r8 = __byte_perm(rb, 0, 0x0020);  // r of both lanes, bytes 0, 1
+                        if (kEq14) {
+                            const int c = pp * 4 + s;
+                            const int rl = (int)(r8 & 0xffu), rh = (int)(r8 & 0xff00u);
+                            const int ax = (int)sadd16(rb, two_x);       // 2x + r
+                            e6[c][0] = __dp2a_lo((int)kLanes, rl, e6[c][0]);
+                            e6[c][1] = __dp2a_lo((int)kLanes, rh, e6[c][1]);
+                            e6[c][2] = __dp2a_lo(ax, rl, e6[c][2]);
+                            e6[c][3] = __dp2a_lo(ax, rh, e6[c][3]);
+                            e6[c][4] = __dp2a_lo((int)a, rl, e6[c][4]);
+                            e6[c][5] = __dp2a_lo((int)a, rh, e6[c][5]);
+                        } else {
+                            acc[pp * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)r8, (int)acc[pp * 4 + s]);
+                        }
                     }
                 }
             }
         }
-        // the warp totals of r (2 (x - s) + r) are signed and fit 32 bits
-        if (!kCoded) {
-            butterfly<kN>(acc, lane);
-            if (kN == 64) {
-                atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
-                atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
-            } else if (kN == 32) {
-                atomicAdd(&sm.acc[lane], (unsigned long long)(long long)(int)acc[0]);
-            } else if (!(lane & 1)) {
-                atomicAdd(&sm.acc[lane >> 1], (unsigned long long)(long long)(int)acc[0]);
-            }
-        } else {
-            // the four lanes of one 8x8 block first, then the uncoded blocks'
-            // part is split off and both are summed across the warp
-            wreduce<kN, 0, 2>(acc, lane);
-            constexpr int kQ = kN / 4;
-            uint32_t un[kQ];
-            const bool unc = !sm.coded[blk];
+        if constexpr (kEq14) {
+            if (luma) {
+                // the two samples of a word are neighbours in one 8x8 block:
+                // add the lanes, then the four lanes of the block
+                int n = inside ? 16 : 0, sx = e0[0] + e0[1], sx2 = e0[2] + e0[3];
+                int ssum = e0[4] + e0[5], ss2 = e0[6] + e0[7], sxs = e0[8] + e0[9];
+                int A[kN], BX[kN], BS[kN];
 #pragma unroll
-            for (int i = 0; i < kQ; i++) un[i] = unc ? acc[i] : 0u;
-            wreduce<kN, 2, 5>(acc, lane);
-            wreduce<kN, 2, 5>(un, lane);
-            const int e = wentry(kN, lane);
-            if (kN >= 32 || !(lane & 16)) {
+                for (int c = 0; c < kN; c++) {
+                    A[c] = e6[c][0] + e6[c][1];
+                    BX[c] = e6[c][2] + e6[c][3];
+                    BS[c] = e6[c][4] + e6[c][5];
+                }
 #pragma unroll
-                for (int j = 0; j < (kN >= 64 ? 2 : 1); j++) {
-                    atomicAdd(&sm.acc[e + j], (unsigned long long)(long long)(int)acc[j]);
-                    atomicAdd(&sm.accu[e + j], (unsigned long long)(long long)(int)un[j]);
+                for (int o = 1; o <= 2; o <<= 1) {
+                    n += __shfl_xor_sync(0xffffffffu, n, o);
+                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                    sx2 += __shfl_xor_sync(0xffffffffu, sx2, o);
+                    ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+                    ss2 += __shfl_xor_sync(0xffffffffu, ss2, o);
+                    sxs += __shfl_xor_sync(0xffffffffu, sxs, o);
+#pragma unroll
+                    for (int c = 0; c < kN; c++) {
+                        A[c] += __shfl_xor_sync(0xffffffffu, A[c], o);
+                        BX[c] += __shfl_xor_sync(0xffffffffu, BX[c], o);
+                        BS[c] += __shfl_xor_sync(0xffffffffu, BS[c], o);
+                    }
+                }
+                // each of the block's four lanes evaluates a quarter of the
+                // candidates
+#pragma unroll
+                for (int c = 0; c < kN; c++) {
+                    if (n > 0 && (c * 4) / kN == sub) {
+                        const long long t = eq14_value(n, ssum, ss2, sx + A[c], (long long)sx2 + BX[c],
+                                                       (long long)sxs + BS[c], F.bitdepth);
+                        atomicAdd(&sm.acc[c], (unsigned long long)t);
+                    }
+                }
+            } else {
+                // (U, V) lanes: per plane, the 4-row half of a chroma 8x8
+                // block is eight lanes (two 4x4 blocks) of this warp; the
+                // other half is the next warp's
+                const int cb = (warp >> 1) * 4 + (bx >> 1), half = warp & 1;
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    int vals[30];
+#pragma unroll
+                    for (int c = 0; c < kN; c++) {
+                        vals[3 * c] = e6[c][k];
+                        vals[3 * c + 1] = e6[c][2 + k];
+                        vals[3 * c + 2] = e6[c][4 + k];
+                    }
+                    vals[24] = inside ? 4 : 0;
+                    vals[25] = e0[k];
+                    vals[26] = e0[2 + k];
+                    vals[27] = e0[4 + k];
+                    vals[28] = e0[6 + k];
+                    vals[29] = e0[8 + k];
+#pragma unroll
+                    for (int o = 1; o <= 4; o <<= 1)
+#pragma unroll
+                        for (int j = 0; j < 30; j++) vals[j] += __shfl_xor_sync(0xffffffffu, vals[j], o);
+                    if ((lane & 7) == 0)
+#pragma unroll
+                        for (int j = 0; j < 30; j++) sm.e14h[k][cb][half][j] = vals[j];
                 }
             }
+            __syncthreads();
+        } else {
+            // the warp totals of r (2 (x - s) + r) are signed and fit 32 bits
+            if (!kCoded) {
+                butterfly<kN>(acc, lane);
+                if (kN == 64) {
+                    atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
+                    atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
+                } else if (kN == 32) {
+                    atomicAdd(&sm.acc[lane], (unsigned long long)(long long)(int)acc[0]);
+                } else if (!(lane & 1)) {
+                    atomicAdd(&sm.acc[lane >> 1], (unsigned long long)(long long)(int)acc[0]);
+                }
+            } else {
+                // the four lanes of one 8x8 block first, then the uncoded blocks'
+                // part is split off and both are summed across the warp
+                wreduce<kN, 0, 2>(acc, lane);
+                constexpr int kQ = kN / 4;
+                uint32_t un[kQ];
+                const bool unc = !sm.coded[blk];
+    #pragma unroll
+                for (int i = 0; i < kQ; i++) un[i] = unc ? acc[i] : 0u;
+                wreduce<kN, 2, 5>(acc, lane);
+                wreduce<kN, 2, 5>(un, lane);
+                const int e = wentry(kN, lane);
+                if (kN >= 32 || !(lane & 16)) {
+    #pragma unroll
+                    for (int j = 0; j < (kN >= 64 ? 2 : 1); j++) {
+                        atomicAdd(&sm.acc[e + j], (unsigned long long)(long long)(int)acc[j]);
+                        atomicAdd(&sm.accu[e + j], (unsigned long long)(long long)(int)un[j]);
+                    }
+                }
+            }
+    #pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) sse0 += __shfl_xor_sync(0xffffffffu, sse0, o);
+            if (lane == 0) atomicAdd(&sm.base[task], (unsigned long long)sse0);
+            __syncthreads();
+            if (tid < kN) {
+                const long long base_sse = (long long)sm.base[task];
+                if (!kCoded) {
+                    long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
+                    out[tid] = (long long)sm.acc[tid] + base_sse;
+                } else {
+                    // q = k * 64 + p * 4 + s; skip bit clear: blocks without coded
+                    // residual unfiltered, (0, 0) the unfiltered error
+                    long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 128 +
+                                     4 * p0 + tid;
+                    const long long tot = (long long)sm.acc[tid], un = (long long)sm.accu[tid];
+                    out[0] = (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un;
+                    out[64] = !any_coded ? base_sse : base_sse + tot;
+                }
+                sm.acc[tid] = 0;
+                sm.accu[tid] = 0;
+            }
+            __syncthreads();
         }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) sse0 += __shfl_xor_sync(0xffffffffu, sse0, o);
-        if (lane == 0) atomicAdd(&sm.base[task], (unsigned long long)sse0);
+    }
+    if constexpr (kEq14) {
+        // chroma 8x8 blocks: two planes x 16 blocks x the unit's candidates
+        for (int i = tid; i < 2 * 16 * kN; i += kThreads) {
+            const int k = i / (16 * kN), cb = (i / kN) % 16, c = i % kN;
+            const int *h0 = sm.e14h[k][cb][0], *h1 = sm.e14h[k][cb][1];
+            const int n = h0[24] + h1[24];
+            if (n > 0) {
+                const long long sx = h0[25] + h1[25], sx2 = h0[26] + h1[26];
+                const long long ssum = h0[27] + h1[27], ss2 = h0[28] + h1[28], sxs = h0[29] + h1[29];
+                const long long t = eq14_value(n, ssum, ss2, sx + h0[3 * c] + h1[3 * c],
+                                               sx2 + h0[3 * c + 1] + h1[3 * c + 1],
+                                               sxs + h0[3 * c + 2] + h1[3 * c + 2], F.bitdepth);
+                atomicAdd(&sm.acc14c[c], (unsigned long long)t);
+            }
+        }
         __syncthreads();
         if (tid < kN) {
-            const long long base_sse = (long long)sm.base[task];
-            if (!kCoded) {
-                long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
-                out[tid] = (long long)sm.acc[tid] + base_sse;
-            } else {
-                // q = k * 64 + p * 4 + s; skip bit clear: blocks without coded
-                // residual unfiltered, (0, 0) the unfiltered error
-                long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 128 +
-                                 4 * p0 + tid;
-                const long long tot = (long long)sm.acc[tid], un = (long long)sm.accu[tid];
-                out[0] = (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un;
-                out[64] = !any_coded ? base_sse : base_sse + tot;
-            }
+            dist_luma[(int64_t)blk_global * 64 + 4 * p0 + tid] = (long long)sm.acc[tid];
+            dist_chroma[(int64_t)blk_global * 64 + 4 * p0 + tid] = (long long)sm.acc14c[tid];
             sm.acc[tid] = 0;
-            sm.accu[tid] = 0;
+            sm.acc14c[tid] = 0;
         }
         __syncthreads();
     }
@@ -457,7 +617,7 @@ __device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTil
 
 // Persistent distortion kernel (same work-counter scheme as the filter).
 // Work unit u is filter block u / kG, primary-strength group u % kG.
-template <int kG, bool kCoded>
+template <int kG, bool kCoded, bool kEq14>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
 dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, long long *dist_chroma,
             uint8_t *skipped, int *status, unsigned *work)
@@ -506,10 +666,10 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             const SBlockRef r = slocate(batch, fb);
             const SearchFrameDev &F = batch.f[r.fi];
             if (F.bitdepth == 8)
-                dist_block<uint8_t, kG, kCoded>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf],
+                dist_block<uint8_t, kG, kCoded, kEq14>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf],
                                                 dist_luma, dist_chroma, skipped);
             else
-                dist_block<uint16_t, kG, kCoded>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf],
+                dist_block<uint16_t, kG, kCoded, kEq14>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf],
                                                  dist_luma, dist_chroma, skipped);
             __syncthreads();
         }
@@ -528,21 +688,20 @@ constexpr size_t kSmemBytes = sizeof(SearchSmem);
 
 // Persistent grid: `per_sm` CTAs on every SM (at most what fits), never more
 // CTAs than work units.
-template <int kG, bool kCoded>
+template <int kG, bool kCoded, bool kEq14>
 int dist_grid(int units, int per_sm)
 {
     static int cached_dev = -1, cached_sms = 0, cached_occ = 1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != cached_dev) {
-        cudaFuncSetAttribute(dist_kernel<kG, kCoded>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
-        cudaFuncSetAttribute(dist_kernel<kG, kCoded>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        auto *kern = dist_kernel<kG, kCoded, kEq14>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dist_kernel<kG, kCoded>, kThreads,
-                                                      kSmemBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, kSmemBytes);
         cached_sms = sms;
         cached_occ = occ > 0 ? occ : 1;
         cached_dev = dev;
@@ -557,11 +716,21 @@ cudaError_t launch_dist(const SearchBatch &b, long long *dl, long long *dc, uint
 {
     const int units = b.total_blocks * kG;
     if (skipped)
-        dist_kernel<kG, true><<<dist_grid<kG, true>(units, per_sm), kThreads, kSmemBytes, s>>>(
-            b, dl, dc, skipped, status, work);
+        dist_kernel<kG, true, false><<<dist_grid<kG, true, false>(units, per_sm), kThreads,
+                                        kSmemBytes, s>>>(b, dl, dc, skipped, status, work);
     else
-        dist_kernel<kG, false><<<dist_grid<kG, false>(units, per_sm), kThreads, kSmemBytes, s>>>(
-            b, dl, dc, nullptr, status, work);
+        dist_kernel<kG, false, false><<<dist_grid<kG, false, false>(units, per_sm), kThreads,
+                                         kSmemBytes, s>>>(b, dl, dc, nullptr, status, work);
+    return cudaGetLastError();
+}
+
+// Eq. 14 tables: eight candidates per work unit (two primary strengths).
+cudaError_t launch_dist_eq14(const SearchBatch &b, long long *dl, long long *dc, int *status,
+                             unsigned *work, cudaStream_t s)
+{
+    const int units = b.total_blocks * 8;
+    dist_kernel<8, false, true><<<dist_grid<8, false, true>(units, 2), kThreads, kSmemBytes, s>>>(
+        b, dl, dc, nullptr, status, work);
     return cudaGetLastError();
 }
 
@@ -574,6 +743,13 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
 {
     cudaError_t e;
     const int per_sm = tune.ctas_per_sm;
+    if (tune.groups == 8) {   // eq. 14 tables
+        e = launch_dist_eq14(b, dist_luma, dist_chroma, status, work, s);
+        if (e != cudaSuccess) return e;
+        void *ctl = tot + (size_t)b.n * 4096;
+        return launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
+                              refine_passes, 64, nullptr, s);
+    }
     switch (tune.groups) {
     case 2: e = launch_dist<2>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;
     case 4: e = launch_dist<4>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;

@@ -581,3 +581,56 @@ def test_chroma_formats_rejected_where_unsupported(cdef, ctx):
     with pytest.raises(cdef.CdefError):
         cdef.cdef_search_strengths(ctx, [inp], [inp], [4], [16],
                                    torch.zeros(1, dtype=torch.uint8, device="cuda"))
+
+
+# --------------------------------------------------------------- eq. 14 distortion
+@pytest.mark.parametrize("passes", [0, 2])
+def test_search_eq14_parity(cdef, ctx, ref, passes):
+    """Section 5's eq. 14 tables (8x8 SSIM weighting, 1/256 units) and the
+    presets, N, J and ids they give equal the oracle's, including 4:2:0
+    chroma 8x8 blocks cut by the frame edge."""
+    from paper_1602_05975_gb300 import synth
+    specs = [(200, 136, 8, 16, 1100), (136, 72, 10, 32, 1101), (192, 120, 8, 64, 1102)]
+    frames = [synth.make_frame(w, h, bd, q, seed=s) for w, h, bd, q, s in specs]
+    damping, lambdas = [5, 4, 6], [64 * 256, 512 * 256, 4096 * 256]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    ctx.set_search_metric("eq14")
+    ctx.set_search_refine(passes)
+    try:
+        res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames],
+                                         [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames],
+                                         damping, lambdas, ids, dl, dc)
+    finally:
+        ctx.set_search_metric("sse")
+        ctx.set_search_refine(0)
+    assert ctx.status() == 0
+    o0 = 0
+    for f, r, d, lam in zip(frames, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths_eq14(f.rec, f.src, f.bitdepth, d, lam, passes)
+        assert np.array_equal(dl[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_luma"])
+        assert np.array_equal(dc[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_chroma"])
+        assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"]
+        assert ([cdef.preset_index(p) for p in r["presets"][:r["npresets"]]] ==
+                [int(t) for t in o["presets"][:o["npresets"]]])
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
+
+
+def test_search_metric_rejections(cdef, ctx):
+    from paper_1602_05975_gb300 import synth
+    assert ctx._lib.cdef_ctx_set_search_metric(ctx.handle, 2) != 0
+    f = synth.make_frame(64, 64, 8, 32, seed=1110)
+    fr = cdef.frame_from_numpy(f.rec, 8)
+    ctx.set_search_metric("eq14")
+    try:
+        with pytest.raises(cdef.CdefError):     # eq. 14 is not offered with the skip bits
+            cdef.cdef_search_strengths_coded(ctx, [fr], [fr],
+                                             [torch.ones(64, dtype=torch.uint8, device="cuda")],
+                                             [4], [16], torch.zeros(1, dtype=torch.uint8,
+                                                                    device="cuda"))
+    finally:
+        ctx.set_search_metric("sse")
