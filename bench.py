@@ -119,6 +119,30 @@ def algorithmic_bytes_per_frame() -> int:
     return samples * (1 if bd == 8 else 2) * 2
 
 
+# The method's integer operations (Eq. 1-12): per filtered sample (luma or
+# chroma) 12 taps x 8 (difference, magnitude, shift, subtraction, clamp at 0,
+# minimum, sign, weighted accumulation), 24 for the clip range over the taps,
+# 4 for the rounding of Eq. 8 and the addition, 2 for the clip; per luma 8x8
+# block the direction search's 376 additions, 124 multiplications and 7
+# comparisons (section 2's count), 64 or 128 (shift first above 8 bits) for
+# the offset of the samples and 1 for the contrast.
+OPS_PER_SAMPLE = 12 * 8 + 24 + 4 + 2
+
+
+def algorithmic_ops_per_frame() -> int:
+    w, h, bd = WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["bitdepth"]
+    samples = w * h + 2 * (w // 2) * (h // 2)
+    search_per_block = 376 + 124 + 7 + 64 * (1 if bd == 8 else 2) + 1
+    return samples * OPS_PER_SAMPLE + (w // 8) * (h // 8) * search_per_block
+
+
+def alu_peak_gops() -> float:
+    """152 SMs x 4 schedulers x 32 lanes issue one 32-bit operation each per
+    clock at 2070 MHz; every value of the 8/10-bit path fits 16 bits, so a
+    lane can carry two of the method's operations."""
+    return 152 * 4 * 32 * 2 * 2.07
+
+
 # ------------------------------------------------------------------ oracle (CPU)
 BAND = 120  # rows per oracle task (a multiple of 8)
 
@@ -420,17 +444,21 @@ def run_ours(args):
     # region's time over the launches (CUDA events on the launching stream)
     mean_launch = ms_per_step / nf
     achieved = algorithmic_bytes_per_frame() / (mean_launch * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm,
+    ops = algorithmic_ops_per_frame() / (mean_launch * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": ops, "peak": alu_peak_gops(), "unit": "Gop/s",
+                "frac": ops / alu_peak_gops(),
                 "traffic": ncu_traffic("filter_kernel") if WORKLOAD is FILTER_WORKLOADS["filter"]
                 else None,
                 "kernel": "filter_kernel (fused find_dir + filter)",
+                "ops_per_launch": algorithmic_ops_per_frame(),
+                "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz",
+                "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "peak_source": "measured" if peaks else "fallback"},
                 "bytes_per_launch": algorithmic_bytes_per_frame(),
                 "mean_launch_us": mean_launch * 1e3,
                 "launch_time": "timed region / launches (consecutive frames overlap)"
                 if not args.no_overlap else "timed region / launches",
-                "isolated_launch_us": statistics.mean(isolated_ms) * 1e3,
-                "peak_source": "measured" if peaks else "fallback"}
+                "isolated_launch_us": statistics.mean(isolated_ms) * 1e3}
 
     cpu = None
     if pool is not None:
@@ -476,13 +504,17 @@ SEARCH_WORKLOAD = dict(
 
 def run_search(args):
     """Batched strength search over 16 mixed-size frames in one call;
-    metric: candidate (block, strength pair, plane group) evaluations per
-    second, 128 per 64x64 block."""
+    metric: candidate (block, strength combination, plane group) evaluations
+    per second, 128 per 64x64 block (256 in the search over coded-residual
+    maps, where the skip-condition bit doubles the combinations)."""
     import torch
     from paper_1602_05975_gb300 import build, cdef, synth
     build.build()
     ctx = cdef.Context(0)
     ctx.set_search_refine(args.refine)
+    variant = args.search_variant
+    if variant == "eq14":
+        ctx.set_search_metric("eq14")
     frames = []
     for f in range(SEARCH_WORKLOAD["frames"]):
         w, h = SEARCH_WORKLOAD["sizes"][f % 3]
@@ -492,13 +524,40 @@ def run_search(args):
     nb = sum(fr.params.shape[0] * fr.params.shape[1] for fr in frames)
     damping = [4 + (fr.q > 16) + (fr.q > 32) for fr in frames]   # larger damping for larger Q
     lambdas = [fr.q * fr.q for fr in frames]
+    width = 128 if variant == "coded" else 64          # table entries per block and group
     ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
-    dl = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
-    dc = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    dl = torch.zeros(nb * width, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(nb * width, dtype=torch.int64, device="cuda")
+    maps = []
+    if variant == "coded":
+        # coded-residual flags: 60% of the 8x8 blocks, one in eight filter blocks fully skipped
+        rng = np.random.default_rng(SEARCH_WORKLOAD["base_seed"])
+        for fr in frames:
+            m = (rng.random((fr.height // 8, fr.width // 8)) < 0.6).astype(np.uint8)
+            m[::16, ::16] = 0
+            fb = (m.shape[0] + 7) // 8, (m.shape[1] + 7) // 8
+            for by in range(fb[0]):
+                for bx in range(fb[1]):
+                    if (by * fb[1] + bx) % 8 == 3:
+                        m[by * 8:by * 8 + 8, bx * 8:bx * 8 + 8] = 0
+            maps.append(torch.from_numpy(m.reshape(-1)).cuda())
     stream = torch.cuda.Stream()
+
+    def call(sl=slice(None)):
+        a = int(starts[sl.start or 0])
+        b = int(starts[len(frames) if sl.stop is None else sl.stop])
+        args_ = (recs[sl], srcs[sl])
+        if variant == "coded":
+            args_ += (maps[sl],)
+        return (cdef.cdef_search_strengths_coded if variant == "coded"
+                else cdef.cdef_search_strengths)(
+            ctx, *args_, damping[sl], lambdas[sl], ids[a:b], dl[a * width:b * width],
+            dc[a * width:b * width], stream=stream)
+
+    starts = np.cumsum([0] + [fr.params.shape[0] * fr.params.shape[1] for fr in frames])
     for _ in range(args.warmup):
-        cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc, stream=stream)
-    if args.check:
+        call()
+    if args.check and variant == "sse":
         from oracle import ref
         o = ref.search_strengths(frames[0].rec, frames[0].src, 8, damping[0], lambdas[0])
         n0 = frames[0].params.shape[0] * frames[0].params.shape[1]
@@ -519,26 +578,18 @@ def run_search(args):
         return time.perf_counter() - t, r
 
     clocks.mark("begin")
-    sec = sum(timed(lambda: cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids,
-                                                       dl, dc, stream=stream))[0]
-              for _ in range(args.steps)) / args.steps
+    sec = sum(timed(call)[0] for _ in range(args.steps)) / args.steps
     clocks.mark("end")
     clk = clocks.stop()
     tune = ctx.tuning()
     batched = [dl.clone(), dc.clone(), ids.clone()]
-    res_b = cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc,
-                                       stream=stream)
+    res_b = call()
 
     # the plain path: one call (one frame) at a time, same outputs
-    starts = np.cumsum([0] + [fr.params.shape[0] * fr.params.shape[1] for fr in frames])
-
     def plain():
         out = []
         for i in range(len(frames)):
-            a, b = int(starts[i]), int(starts[i + 1])
-            out += cdef.cdef_search_strengths(ctx, recs[i:i + 1], srcs[i:i + 1], damping[i:i + 1],
-                                              lambdas[i:i + 1], ids[a:b], dl[a * 64:b * 64],
-                                              dc[a * 64:b * 64], stream=stream)
+            out += call(slice(i, i + 1))
         return out
 
     for _ in range(args.warmup):
@@ -552,15 +603,16 @@ def run_search(args):
     assert same, "batched and one-frame-at-a-time searches differ"
     assert ctx.status() == 0
     print(json.dumps({
-        "metric": "strength-search candidates/s", "value": nb * 128 / sec, "unit": "candidates/s",
+        "metric": "strength-search candidates/s", "value": nb * 2 * width / sec,
+        "unit": "candidates/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": {"workload": SEARCH_WORKLOAD["name"], "blocks": nb,
                                         "luma_pixels": sum(f.width * f.height for f in frames),
                                         "l2": "L2 flushed (256 MB write) before each call"},
         "tuning": dict(zip(("search_groups", "search_ctas_per_sm"), tune)),
-        "refine_passes": args.refine,
-        "plain": {"ms_per_step": plain_sec * 1e3, "value": nb * 128 / plain_sec,
+        "refine_passes": args.refine, "variant": variant,
+        "plain": {"ms_per_step": plain_sec * 1e3, "value": nb * 2 * width / plain_sec,
                   "what": "one cdef_search_strengths call per frame, identical outputs"},
         "clocks": clk}))
     ctx.close()
@@ -713,6 +765,9 @@ def main():
     ap.add_argument("--requests", type=int, default=0, help="serve: requests per rate")
     ap.add_argument("--refine", type=int, default=0,
                     help="search: preset re-optimisation passes after the greedy search")
+    ap.add_argument("--search-variant", default="sse", choices=["sse", "eq14", "coded"],
+                    help="search: squared error (64 pairs), eq. 14 distortion, or the "
+                         "128-combination search with coded-residual maps")
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi clocks during the run")
     args = ap.parse_args()
