@@ -81,6 +81,12 @@ FILTER_WORKLOADS = {
     "filter1080p": dict(name="1920x1080 8-bit 4:2:0, 30 frames, direction search + filter, "
                              "one launch per frame",
                         width=1920, height=1080, bitdepth=8, frames=30, base_seed=1000),
+    "filter444": dict(name="1920x1080 8-bit 4:4:4, 30 frames, direction search + filter "
+                           "(full-resolution chroma), one launch per frame",
+                      width=1920, height=1080, bitdepth=8, frames=30, base_seed=5000, chroma=444),
+    "filter12": dict(name="3840x2160 12-bit 4:2:0, 8 frames, direction search + filter, "
+                          "one launch per frame",
+                     width=3840, height=2160, bitdepth=12, frames=8, base_seed=6000),
 }
 WORKLOAD = FILTER_WORKLOADS["filter"]
 
@@ -93,7 +99,15 @@ def frame_seeds(rank: int = 0):
 def make_frames(rank: int = 0):
     from paper_1602_05975_gb300 import synth
     w, h, bd = WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["bitdepth"]
-    return [synth.make_frame(w, h, bd, None, s) for s in frame_seeds(rank)]
+    return [synth.make_frame(w, h, bd, None, s, WORKLOAD.get("chroma", 420))
+            for s in frame_seeds(rank)]
+
+
+def workload_samples() -> int:
+    from paper_1602_05975_gb300 import synth
+    w, h = WORKLOAD["width"], WORKLOAD["height"]
+    cw, ch = synth.chroma_dims(w, h, WORKLOAD.get("chroma", 420))
+    return w * h + 2 * cw * ch
 
 
 def max_over_ranks(x: float, device=None) -> float:
@@ -114,9 +128,7 @@ def whole_job_rate(ws: int, units_per_rank: float, ms_per_step: float) -> float:
 
 
 def algorithmic_bytes_per_frame() -> int:
-    w, h, bd = WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["bitdepth"]
-    samples = w * h + 2 * (w // 2) * (h // 2)
-    return samples * (1 if bd == 8 else 2) * 2
+    return workload_samples() * (1 if WORKLOAD["bitdepth"] == 8 else 2) * 2
 
 
 # The method's integer operations (Eq. 1-12): per filtered sample (luma or
@@ -131,16 +143,16 @@ OPS_PER_SAMPLE = 12 * 8 + 24 + 4 + 2
 
 def algorithmic_ops_per_frame() -> int:
     w, h, bd = WORKLOAD["width"], WORKLOAD["height"], WORKLOAD["bitdepth"]
-    samples = w * h + 2 * (w // 2) * (h // 2)
+    filtered = w * h if WORKLOAD.get("chroma", 420) == 422 else workload_samples()
     search_per_block = 376 + 124 + 7 + 64 * (1 if bd == 8 else 2) + 1
-    return samples * OPS_PER_SAMPLE + (w // 8) * (h // 8) * search_per_block
+    return filtered * OPS_PER_SAMPLE + (w // 8) * (h // 8) * search_per_block
 
 
-def alu_peak_gops() -> float:
+def alu_peak_gops(bitdepth: int = 8) -> float:
     """152 SMs x 4 schedulers x 32 lanes issue one 32-bit operation each per
     clock at 2070 MHz; every value of the 8/10-bit path fits 16 bits, so a
-    lane can carry two of the method's operations."""
-    return 152 * 4 * 32 * 2 * 2.07
+    lane can carry two of the method's operations (12-bit values do not)."""
+    return 152 * 4 * 32 * (2 if bitdepth <= 10 else 1) * 2.07
 
 
 # ------------------------------------------------------------------ oracle (CPU)
@@ -150,10 +162,13 @@ BAND = 120  # rows per oracle task (a multiple of 8)
 def _oracle_band(args):
     """Filter one horizontal band of a frame with the oracle (as a frame of
     its own).  Returns (luma pixels, seconds)."""
-    planes, bd, params = args
+    planes, bd, params, fmt = args
     from oracle import ref
     t = time.perf_counter()
-    ref.filter_frame(*planes, bd, params)
+    if fmt == 420:
+        ref.filter_frame(*planes, bd, params)
+    else:
+        ref.filter_frame_format(*planes, bd, params, fmt)
     return planes[0].shape[0] * planes[0].shape[1], time.perf_counter() - t
 
 
@@ -166,11 +181,13 @@ def oracle_tasks(frames, nbands):
                 return tasks
             b1 = min(h, b0 + BAND)
             y = fr.rec[0][b0:b1]
-            u = fr.rec[1][b0 // 2:b1 // 2]
-            v = fr.rec[2][b0 // 2:b1 // 2]
+            fmt = WORKLOAD.get("chroma", 420)
+            c0, c1 = (b0 // 2, b1 // 2) if fmt == 420 else (b0, b1)
+            u = fr.rec[1][c0:c1]
+            v = fr.rec[2][c0:c1]
             rows = [(b0 // 64 + k) % fr.params.shape[0] for k in range(-(-(b1 - b0) // 64))]
             prm = np.ascontiguousarray(fr.params[rows])
-            tasks.append(((y, u, v), fr.bitdepth, prm))
+            tasks.append(((y, u, v), fr.bitdepth, prm, fmt))
     return tasks
 
 
@@ -334,7 +351,8 @@ def run_ours(args):
     ins = [cdef.frame_from_numpy(f.rec, f.bitdepth, device=dev) for f in frames]
     # two output sets, alternating by step: no two filter calls that may run
     # concurrently (overlapped launches) write the same buffer
-    out_sets = [[cdef.alloc_frame(f.width, f.height, f.bitdepth, device=dev, fill=0)
+    fmt = WORKLOAD.get("chroma", 420)
+    out_sets = [[cdef.alloc_frame(f.width, f.height, f.bitdepth, device=dev, fill=0, chroma=fmt)
                  for f in frames] for _ in range(2)]
     outs = out_sets[0]
     prms = [cdef.params_tensor(f.params, device=dev) for f in frames]
@@ -362,7 +380,9 @@ def run_ours(args):
     got = outs[0].to_numpy()
     if args.check:
         from oracle import ref
-        exp = ref.filter_frame(*frames[0].rec, frames[0].bitdepth, frames[0].params)
+        exp = (ref.filter_frame(*frames[0].rec, frames[0].bitdepth, frames[0].params) if fmt == 420
+               else ref.filter_frame_format(*frames[0].rec, frames[0].bitdepth, frames[0].params,
+                                            fmt))
         for g, e in zip(got, exp):
             assert np.array_equal(g, e), "bench output differs from the oracle"
 
@@ -405,9 +425,10 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         hin = [cdef.frame_from_numpy(f.rec, f.bitdepth, device="cpu", pin=True) for f in frames]
-        hout = [cdef.alloc_frame(f.width, f.height, f.bitdepth, device="cpu") for f in frames]
-        hout = [cdef.Frame(*(t.pin_memory() for t in h.planes()), h.width, h.height, h.bitdepth)
-                for h in hout]
+        hout = [cdef.alloc_frame(f.width, f.height, f.bitdepth, device="cpu", chroma=fmt)
+                for f in frames]
+        hout = [cdef.Frame(*(t.pin_memory() for t in h.planes()), h.width, h.height, h.bitdepth,
+                           h.chroma) for h in hout]
         streams = [torch.cuda.Stream(device=dev) for _ in range(3)]
         h2d = sum(t.numel() * t.element_size() for h in hin for t in h.planes())
         d2h = sum(t.numel() * t.element_size() for h in hout for t in h.planes())
@@ -445,13 +466,15 @@ def run_ours(args):
     mean_launch = ms_per_step / nf
     achieved = algorithmic_bytes_per_frame() / (mean_launch * 1e-3) / 1e9
     ops = algorithmic_ops_per_frame() / (mean_launch * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": ops, "peak": alu_peak_gops(), "unit": "Gop/s",
-                "frac": ops / alu_peak_gops(),
+    peak_ops = alu_peak_gops(WORKLOAD["bitdepth"])
+    roofline = {"bound": "alu", "achieved": ops, "peak": peak_ops, "unit": "Gop/s",
+                "frac": ops / peak_ops,
                 "traffic": ncu_traffic("filter_kernel") if WORKLOAD is FILTER_WORKLOADS["filter"]
                 else None,
                 "kernel": "filter_kernel (fused find_dir + filter)",
                 "ops_per_launch": algorithmic_ops_per_frame(),
-                "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz",
+                "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz"
+                if WORKLOAD["bitdepth"] <= 10 else "derived: 152 SMs x 128 lanes x 2070 MHz",
                 "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "peak_source": "measured" if peaks else "fallback"},
                 "bytes_per_launch": algorithmic_bytes_per_frame(),
@@ -502,11 +525,59 @@ SEARCH_WORKLOAD = dict(
     sizes=[(640, 360), (1280, 720), (1920, 1080)], frames=16, base_seed=3000)
 
 
+# The strength search's operations per sample and plane group (section 5 on
+# Eq. 7-12, evaluated the factored way: every candidate's filter sum is a
+# primary sum plus a secondary sum): 16 primary strengths x 4 taps x 8 and
+# 3 non-zero secondary strengths x 8 taps x 8 constraint operations, 24 for
+# the clip range, then per candidate 8 (sum of the two sets, rounding of
+# Eq. 8, clip, error, square and accumulation).  Eq. 14 adds the filtered
+# sum and sum of squares per candidate (3); the 128-combination search adds
+# the (19, 7) preset's 12 taps and the uncoded part's accumulation per
+# candidate (1).  Per luma 8x8 block: the direction search as in the filter.
+def search_ops_per_sample(variant: str) -> int:
+    per_cand = {"sse": 8, "eq14": 11, "coded": 9}[variant]
+    extra = 12 * 8 if variant == "coded" else 0
+    return 16 * 4 * 8 + 3 * 8 * 8 + 24 + 64 * per_cand + extra
+
+
+def search_ops(frames, variant: str) -> int:
+    ops = 0
+    for f in frames:
+        samples = f.width * f.height + 2 * (f.width // 2) * (f.height // 2)
+        ops += samples * search_ops_per_sample(variant) + (f.width // 8) * (f.height // 8) * (
+            376 + 124 + 7 + 64 + 1)
+    return ops
+
+
+def _oracle_search(task):
+    """One frame's strength search by the oracle (a worker process).
+    Returns (candidate evaluations, CPU seconds)."""
+    w, h, seed, damping, lam, variant, passes, coded = task
+    from oracle import ref
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(w, h, 8, None, seed)
+    t = time.process_time()
+    if variant == "eq14":
+        ref.search_strengths_eq14(f.rec, f.src, 8, damping, lam, passes)
+    elif variant == "coded":
+        ref.search_strengths_coded(f.rec, f.src, 8, damping, lam, coded, passes)
+    else:
+        ref.search_strengths(f.rec, f.src, 8, damping, lam, passes)
+    blocks = -(-w // 64) * -(-h // 64)
+    return blocks * 2 * (128 if variant == "coded" else 64), time.process_time() - t
+
+
 def run_search(args):
     """Batched strength search over 16 mixed-size frames in one call;
     metric: candidate (block, strength combination, plane group) evaluations
     per second, 128 per 64x64 block (256 in the search over coded-residual
     maps, where the skip-condition bit doubles the combinations)."""
+    pool = None
+    if not args.no_cpu_baseline:
+        # spawn the oracle pool before any CUDA work
+        from oracle import ref
+        ref.build()
+        pool = mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 16))
     import torch
     from paper_1602_05975_gb300 import build, cdef, synth
     build.build()
@@ -582,6 +653,17 @@ def run_search(args):
     clocks.mark("end")
     clk = clocks.stop()
     tune = ctx.tuning()
+    # the distortion kernel's own time: events around it in the search graph
+    ctx.set_stage_timing(True)
+    stage = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        call()
+        stage.append(ctx.stage_times())
+    ctx.set_stage_timing(False)
+    dist_ms = statistics.mean(t[0] for t in stage)
+    pre_ms = statistics.mean(t[1] for t in stage)
     batched = [dl.clone(), dc.clone(), ids.clone()]
     res_b = call()
 
@@ -602,6 +684,31 @@ def run_search(args):
             and torch.equal(batched[2], ids))
     assert same, "batched and one-frame-at-a-time searches differ"
     assert ctx.status() == 0
+    ops = search_ops(frames, variant)
+    roofline = {"bound": "alu", "achieved": ops / (dist_ms * 1e-3) / 1e9, "peak": alu_peak_gops(),
+                "unit": "Gop/s", "frac": ops / (dist_ms * 1e-3) / 1e9 / alu_peak_gops(),
+                "traffic": None, "kernel": "dist_kernel (distortion tables)",
+                "ops_per_launch": ops, "mean_launch_us": dist_ms * 1e3,
+                "launch_time": "CUDA events around the kernel inside the search graph",
+                "preset_kernel_us": pre_ms * 1e3,
+                "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz"}
+    cpu = None
+    if pool is not None:
+        sample = [i for i in range(len(frames)) if (frames[i].width, frames[i].height) == (640, 360)]
+        tasks = [(frames[i].width, frames[i].height, SEARCH_WORKLOAD["base_seed"] + i, damping[i],
+                  lambdas[i], variant, args.refine,
+                  maps[i].cpu().numpy().reshape(frames[i].height // 8, frames[i].width // 8)
+                  if maps else None) for i in sample]
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_search, tasks, chunksize=1)
+        wall = time.perf_counter() - t0
+        pool.close()
+        cand = sum(r[0] for r in res)
+        cpu = {"value": cand / wall, "unit": "candidates/s", "cores": min(len(tasks), pool._processes),
+               "kind": "oracle",
+               "sample": f"the {len(tasks)} 640x360 frames of the workload, one process per frame: "
+                         f"{cand} candidates, {sum(r[1] for r in res):.1f} s of CPU work in "
+                         f"{wall:.1f} s wall"}
     print(json.dumps({
         "metric": "strength-search candidates/s", "value": nb * 2 * width / sec,
         "unit": "candidates/s",
@@ -611,6 +718,7 @@ def run_search(args):
                                         "luma_pixels": sum(f.width * f.height for f in frames),
                                         "l2": "L2 flushed (256 MB write) before each call"},
         "tuning": dict(zip(("search_groups", "search_ctas_per_sm"), tune)),
+        "roofline": roofline, "cpu_baseline": cpu,
         "refine_passes": args.refine, "variant": variant,
         "plain": {"ms_per_step": plain_sec * 1e3, "value": nb * 2 * width / plain_sec,
                   "what": "one cdef_search_strengths call per frame, identical outputs"},
@@ -758,10 +866,11 @@ def main():
                     help="oracle sample: number of 120-row bands (0 = the whole step)")
     ap.add_argument("--check", action="store_true", help="oracle check of frame 0")
     ap.add_argument("--workload", default="filter",
-                    choices=["filter", "filter1080p", "search", "serve"],
+                    choices=["filter", "filter1080p", "filter444", "filter12", "search", "serve"],
                     help="filter: the 4K 10-bit filter (default line); filter1080p: 30 "
-                         "1080p 8-bit frames; search: batched strength search over 16 mixed "
-                         "frames; serve: the serving loop")
+                         "1080p 8-bit frames; filter444: 30 1080p 8-bit 4:4:4 frames; "
+                         "filter12: 8 4K 12-bit frames; search: batched strength search over "
+                         "16 mixed frames; serve: the serving loop")
     ap.add_argument("--requests", type=int, default=0, help="serve: requests per rate")
     ap.add_argument("--refine", type=int, default=0,
                     help="search: preset re-optimisation passes after the greedy search")

@@ -278,13 +278,25 @@ int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
  *                    source and filtered blocks, C1 = 6.25 * 4^(bd-8), C2 =
  *                    312.5 * 16^(bd-8); each 8x8 value in units of 1/256,
  *                    rounded half away from zero after an IEEE
- *                    double-precision evaluation in a fixed order, so that the
+ *                    single-precision evaluation in a fixed order, so that the
  *                    tables are exact integers.  Not available with
  *                    cdef_search_strengths_coded (CDEF_ERR_ARG).
  * Host only; applies to later searches on the context. */
 #define CDEF_METRIC_SSE 0
 #define CDEF_METRIC_EQ14 1
 int cdef_ctx_set_search_metric(cdef_ctx *ctx, int metric);
+
+/* Per-stage device times of the strength search (no paper counterpart: a
+ * profiling aid).  With timing on, later searches on the context record
+ * CUDA events before the distortion-table kernel, between it and the preset
+ * selection (greedy search, re-optimisation, choice of N and ids), and after
+ * it; cdef_ctx_get_stage_times returns the two stage durations of the last
+ * search, in milliseconds.  Returns CDEF_ERR_ARG when no search has run
+ * with timing on since it was last enabled; CDEF_ERR_CUDA if the events
+ * cannot be created or read.  Host only; timing is off by default (it adds
+ * two event records to each search). */
+int cdef_ctx_set_stage_timing(cdef_ctx *ctx, int enable);
+int cdef_ctx_get_stage_times(cdef_ctx *ctx, float *distortion_ms, float *presets_ms);
 
 /* Preset re-optimisation of cdef_search_strengths (section 5: "iteratively
  * re-optimizing one preset at a time" after the greedy search).  For each

@@ -92,6 +92,8 @@ def load():
     L.cdef_ctx_set_search_refine.argtypes = [vp, C.c_int]
     L.cdef_ctx_set_search_metric.argtypes = [vp, C.c_int]
     L.cdef_ctx_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.cdef_ctx_set_stage_timing.argtypes = [vp, C.c_int]
+    L.cdef_ctx_get_stage_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.cdef_search_strengths_coded.argtypes = [
         vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(vp), C.POINTER(i32),
         C.POINTER(i64), vp, vp, C.POINTER(PresetCoded), C.POINTER(i32), vp, C.POINTER(i64), vp]
@@ -103,7 +105,8 @@ def load():
                  "cdef_search_strengths",
                  "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap",
                  "cdef_ctx_set_search_refine", "cdef_search_strengths_coded",
-                 "cdef_ctx_set_search_metric"):
+                 "cdef_ctx_set_search_metric", "cdef_ctx_set_stage_timing",
+                 "cdef_ctx_get_stage_times"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -288,6 +291,18 @@ class Context:
         """'sse' (default) or 'eq14' (section 5's SSIM-weighted distortion)."""
         m = {"sse": 0, "eq14": 1}[metric]
         _check(self._lib.cdef_ctx_set_search_metric(self.handle, m), "cdef_ctx_set_search_metric")
+
+    def set_stage_timing(self, enable: bool):
+        """Record per-stage device times of later strength searches."""
+        _check(self._lib.cdef_ctx_set_stage_timing(self.handle, int(bool(enable))),
+               "cdef_ctx_set_stage_timing")
+
+    def stage_times(self):
+        """(distortion-table ms, preset-selection ms) of the last search."""
+        a, b = C.c_float(), C.c_float()
+        _check(self._lib.cdef_ctx_get_stage_times(self.handle, C.byref(a), C.byref(b)),
+               "cdef_ctx_get_stage_times")
+        return a.value, b.value
 
     def set_overlap(self, enable: bool):
         """Declare consecutive filter calls on a stream independent (see

@@ -37,6 +37,10 @@ struct cdef_ctx {
     int refine_passes;            // preset re-optimisation passes of the search (0 = greedy)
     int metric;                   // search distortion: 0 squared error, 1 eq. 14
     int search_key_refine;        // refine_passes search_exec was recorded with
+    bool stage_timing;            // record stage events in the search graph
+    bool search_key_timing;       // and whether search_exec holds them
+    bool stage_valid;             // the events hold the last search's stages
+    cudaEvent_t stage_ev[3];      // before the tables, between, after the presets
     std::unordered_map<uint64_t, SearchTune> *tuned;  // autotuned, per batch shape
     uint8_t *maps_dir;            // direction maps of 4:4:4 filtering
     int32_t *maps_var;
@@ -285,6 +289,8 @@ int cdef_ctx_destroy(cdef_ctx *ctx)
     if (ctx->work) cudaFree(ctx->work);
     if (ctx->search_exec) cudaGraphExecDestroy(ctx->search_exec);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
+    for (int k = 0; k < 3; k++)
+        if (ctx->stage_ev[k]) cudaEventDestroy(ctx->stage_ev[k]);
     delete ctx->search_key;
     delete ctx->tuned;
     delete ctx;
@@ -322,6 +328,38 @@ int cdef_ctx_set_overlap(cdef_ctx *ctx, int enable)
 {
     if (!ctx) return CDEF_ERR_ARG;
     ctx->overlap = enable != 0;
+    return CDEF_OK;
+}
+
+int cdef_ctx_set_stage_timing(cdef_ctx *ctx, int enable)
+{
+    if (!ctx) return CDEF_ERR_ARG;
+    if (enable && !ctx->stage_ev[0]) {
+        DeviceGuard g(ctx->device);
+        if (!g.ok) return CDEF_ERR_CUDA;
+        for (int k = 0; k < 3; k++) {
+            if (cudaEventCreate(&ctx->stage_ev[k]) != cudaSuccess) {
+                for (int j = 0; j < k; j++) cudaEventDestroy(ctx->stage_ev[j]);
+                for (int j = 0; j < 3; j++) ctx->stage_ev[j] = nullptr;
+                cudaGetLastError();
+                return CDEF_ERR_CUDA;
+            }
+        }
+    }
+    ctx->stage_timing = enable != 0;
+    ctx->stage_valid = false;
+    return CDEF_OK;
+}
+
+int cdef_ctx_get_stage_times(cdef_ctx *ctx, float *distortion_ms, float *presets_ms)
+{
+    if (!ctx || !distortion_ms || !presets_ms || !ctx->stage_valid) return CDEF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok || cudaEventElapsedTime(distortion_ms, ctx->stage_ev[0], ctx->stage_ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(presets_ms, ctx->stage_ev[1], ctx->stage_ev[2]) != cudaSuccess) {
+        cudaGetLastError();
+        return CDEF_ERR_CUDA;
+    }
     return CDEF_OK;
 }
 
@@ -707,12 +745,14 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
                       memcmp(ctx->search_ptrs, ptrs, sizeof(ptrs)) == 0 &&
                       ctx->search_key_tune.groups == tune.groups &&
                       ctx->search_key_tune.ctas_per_sm == tune.ctas_per_sm &&
-                      ctx->search_key_refine == ctx->refine_passes;
+                      ctx->search_key_refine == ctx->refine_passes &&
+                      ctx->search_key_timing == ctx->stage_timing;
     cudaError_t e = same ? cudaSuccess : cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess && !same) {
         const cudaError_t le = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids,
                                              ctx->status, work, tune, ctx->refine_passes,
-                                             ctx->capture, skipped);
+                                             ctx->capture, skipped,
+                                             ctx->stage_timing ? ctx->stage_ev : nullptr);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(ctx->capture, &graph);
         if (e == cudaSuccess && le != cudaSuccess) e = le;
@@ -733,6 +773,7 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
                 memcpy(ctx->search_ptrs, ptrs, sizeof(ptrs));
                 ctx->search_key_tune = tune;
                 ctx->search_key_refine = ctx->refine_passes;
+                ctx->search_key_timing = ctx->stage_timing;
             }
         } else if (ctx->search_key) {
             memset(ctx->search_key, 0, sizeof(SearchBatch));
@@ -744,6 +785,7 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
         e = cudaMemcpyAsync(ctx->host_results, ctx->dev_results, sizeof(SearchResultDev) * n,
                             cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    ctx->stage_valid = e == cudaSuccess && ctx->stage_timing;
     if (e != cudaSuccess) return CDEF_ERR_CUDA;
     static const uint8_t kSec[4] = {0, 1, 2, 4};
     for (int i = 0; i < n; i++) {

@@ -128,6 +128,9 @@ inline SearchTune default_search_tune(int total_blocks, int sms)
 // by the call itself), `work` a zeroed counter pair (left zeroed).
 // `refine_passes`: 0 = the greedy presets; > 0 = then re-optimise each set
 // one preset at a time for at most that many passes (section 5).
+// `stage_events` non-null: three events recorded before the distortion
+// kernel, between it and the preset selection, and after it (event nodes
+// when the stream is being captured into a graph).
 // `skipped` non-null: the 128-combination search of section 5 with section
 // 4's skip semantics (each frame's `coded` map; tables of 128 entries per
 // block; `skipped` receives one flag per block); null: 64 combinations.
@@ -135,7 +138,8 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
                           long long *dist_chroma, unsigned long long *cur,
                           unsigned long long *tot, SearchResultDev *results,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
-                          int refine_passes, cudaStream_t s, uint8_t *skipped = nullptr);
+                          int refine_passes, cudaStream_t s, uint8_t *skipped = nullptr,
+                          const cudaEvent_t *stage_events = nullptr);
 // The preset selection alone (one cooperative launch); `ctl` is the control
 // block that follows `tot` in the scratch.
 // `width`: combinations per plane group in the tables (64 or 128; presets

@@ -185,20 +185,30 @@ __device__ __forceinline__ int wentry(int N, int lane)
 // Eq. 14 for one 8x8 block from its sums over its n samples (source sum and
 // sum of squares, filtered sum and sum of squares, squared error), in 1/256
 // units rounded half away from zero.  Every operation is a correctly
-// rounded IEEE double operation, in a fixed order (no contraction): the
-// value is exactly reproducible.
-__device__ long long eq14_value(long long n, long long s1s, long long s2s, long long s1d,
+// rounded IEEE single-precision operation, in a fixed order (no
+// contraction): the value is exactly reproducible.  n is 64, 32 or 16 (4:2:0
+// planes whose sizes are multiples of 4), so the division by n^2 is an
+// exact scaling by a power of two.
+__device__ long long eq14_value(int n, long long s1s, long long s2s, long long s1d,
                                 long long s2d, long long sse, int bitdepth)
 {
-    const double c1 = __dmul_rn(6.25, (double)(1 << (2 * (bitdepth - 8))));
-    const double c2 = __dmul_rn(312.5, (double)(1 << (4 * (bitdepth - 8))));
-    const double nn = (double)(n * n);
-    const double vs = __ddiv_rn((double)(n * s2s - s1s * s1s), nn);
-    const double vd = __ddiv_rn((double)(n * s2d - s1d * s1d), nn);
-    const double num = __dadd_rn(__dadd_rn(vs, vd), c1);
-    const double den = __dmul_rn(2.0, __dsqrt_rn(__dadd_rn(__dmul_rn(vs, vd), c2)));
-    const double d = __dmul_rn(__ddiv_rn(num, den), (double)sse);
-    return llround(__dmul_rn(256.0, d));
+    const float c1 = __fmul_rn(6.25f, (float)(1 << (2 * (bitdepth - 8))));
+    const float c2 = __fmul_rn(312.5f, (float)(1 << (4 * (bitdepth - 8))));
+    const int nn = n * n;
+    const float xs = __ll2float_rn(n * s2s - s1s * s1s), xd = __ll2float_rn(n * s2d - s1d * s1d);
+    float vs, vd;
+    if ((nn & (nn - 1)) == 0) {
+        const float inv = __frcp_rn((float)nn);   // exact for a power of two
+        vs = __fmul_rn(xs, inv);
+        vd = __fmul_rn(xd, inv);
+    } else {
+        vs = __fdiv_rn(xs, (float)nn);
+        vd = __fdiv_rn(xd, (float)nn);
+    }
+    const float num = __fadd_rn(__fadd_rn(vs, vd), c1);
+    const float den = __fmul_rn(2.0f, __fsqrt_rn(__fadd_rn(__fmul_rn(vs, vd), c2)));
+    const float d = __fmul_rn(__fdiv_rn(num, den), __ll2float_rn(sse));
+    return llroundf(__fmul_rn(256.0f, d));
 }
 
 // kEq14: the tables hold section 5's eq. 14 instead of the squared error:
@@ -736,30 +746,48 @@ cudaError_t launch_dist_eq14(const SearchBatch &b, long long *dl, long long *dc,
 
 }  // namespace
 
+// An event on the stream; inside a stream capture, an event record node of
+// the graph.
+static cudaError_t stage_mark(const cudaEvent_t *ev, int k, cudaStream_t s)
+{
+    if (!ev) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev[k], s, cudaEventRecordExternal)
+                                                : cudaEventRecord(ev[k], s);
+}
+
 cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long *dist_chroma,
                           unsigned long long *cur, unsigned long long *tot, SearchResultDev *results,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
-                          int refine_passes, cudaStream_t s, uint8_t *skipped)
+                          int refine_passes, cudaStream_t s, uint8_t *skipped,
+                          const cudaEvent_t *stage_events)
 {
-    cudaError_t e;
+    cudaError_t e = stage_mark(stage_events, 0, s);
+    if (e != cudaSuccess) return e;
     const int per_sm = tune.ctas_per_sm;
     if (tune.groups == 8) {   // eq. 14 tables
         e = launch_dist_eq14(b, dist_luma, dist_chroma, status, work, s);
+        if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
         if (e != cudaSuccess) return e;
         void *ctl = tot + (size_t)b.n * 4096;
-        return launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
-                              refine_passes, 64, nullptr, s);
+        e = launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
+                           refine_passes, 64, nullptr, s);
+        return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
     }
     switch (tune.groups) {
     case 2: e = launch_dist<2>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;
     case 4: e = launch_dist<4>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;
     default: e = launch_dist<1>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;
     }
+    if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
     if (e != cudaSuccess) return e;
     const int width = skipped ? 128 : 64;
     void *ctl = tot + (size_t)b.n * width * width;
-    return launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
-                          refine_passes, width, skipped, s);
+    e = launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
+                       refine_passes, width, skipped, s);
+    return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
 }
 
 }  // namespace cdefgb

@@ -1,4 +1,4 @@
-"""Seeded synthetic 4:2:0 frames shaped like the paper's test material.
+"""Seeded synthetic frames shaped like the paper's test material.
 
 This module holds input generation only: no step of the CDEF method (no
 direction search, constraint, filtering or distortion) lives here.  Both the
@@ -10,8 +10,8 @@ which is not available here; these frames stand in for it:
 * source: 128 + three random oriented sinusoids (amplitude U[10,40],
   frequency U[1/64, 1/4] cycles/pixel, angle U[0, pi), phase U[0, 2 pi))
   plus 2-6 random step edges of height +-U[10,60], clipped to [16, 235];
-  chroma planes use the same recipe at half resolution with halved
-  amplitudes;
+  chroma planes use the same recipe at their own resolution (half in both
+  directions for 4:2:0, the default) with halved amplitudes;
 * decoded ("reconstructed") frame: each plane is coded by an orthonormal 8x8
   DCT-II in float64, coefficients quantised as rint(c/Q)*Q, inverse DCT,
   rint, clip to the sample range -- quantisation ringing of the kind CDEF is
@@ -100,17 +100,31 @@ def random_params(rng, width, height, damping=None):
     return prm
 
 
+def chroma_dims(width: int, height: int, chroma: int = 420):
+    """(width, height) of a chroma plane: 4:2:0 halves both, 4:2:2 the
+    width, 4:4:4 neither."""
+    if chroma == 420:
+        return width // 2, height // 2
+    if chroma == 422:
+        return width // 2, height
+    if chroma == 444:
+        return width, height
+    raise ValueError("chroma format must be 420, 422 or 444")
+
+
 def make_frame(width: int, height: int, bitdepth: int = 8, q=32,
-               seed: int = 0) -> Frame:
+               seed: int = 0, chroma: int = 420) -> Frame:
     """A source/decoded frame pair plus random per-64x64 CDEF parameters.
-    q=None draws the quantiser step from {16, 32, 64}."""
+    q=None draws the quantiser step from {16, 32, 64}; `chroma` is the
+    chroma format (the chroma recipe at the plane's own resolution)."""
     if width % 8 or height % 8:
         raise ValueError("width and height must be multiples of 8")
+    cw, ch = chroma_dims(width, height, chroma)
     rng = np.random.Generator(np.random.PCG64(seed))
     maxval = (1 << bitdepth) - 1
     src = [_source_plane(rng, width, height, 1.0),
-           _source_plane(rng, width // 2, height // 2, 0.5),
-           _source_plane(rng, width // 2, height // 2, 0.5)]
+           _source_plane(rng, cw, ch, 0.5),
+           _source_plane(rng, cw, ch, 0.5)]
     if q is None:
         q = (16, 32, 64)[int(rng.integers(0, 3))]
     qq = q

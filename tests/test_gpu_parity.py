@@ -634,3 +634,40 @@ def test_search_metric_rejections(cdef, ctx):
                                                                     device="cuda"))
     finally:
         ctx.set_search_metric("sse")
+
+
+@pytest.mark.gpu
+def test_search_stage_timing(cdef, ctx):
+    """Stage events in the search graph: positive stage times, results equal
+    with and without them, and no times before a timed search."""
+    from paper_1602_05975_gb300 import synth
+    frames = [synth.make_frame(w, h, 8, 32, seed=s) for w, h, s in ((192, 128, 1120), (136, 72, 1121))]
+    recs = [cdef.frame_from_numpy(f.rec, 8) for f in frames]
+    srcs = [cdef.frame_from_numpy(f.src, 8) for f in frames]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+
+    def run():
+        ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+        dl = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+        dc = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+        res = cdef.cdef_search_strengths(ctx, recs, srcs, [5, 4], [256, 1024], ids, dl, dc)
+        return res, ids.cpu(), dl.cpu(), dc.cpu()
+
+    plain = run()
+    ctx.set_stage_timing(True)
+    try:
+        with pytest.raises(cdef.CdefError):
+            ctx.stage_times()
+        for metric in ("sse", "eq14"):
+            ctx.set_search_metric(metric)
+            timed = run()
+            t_dist, t_pre = ctx.stage_times()
+            assert t_dist > 0 and t_pre > 0
+            if metric == "sse":
+                assert timed[0] == plain[0]
+                assert all(torch.equal(a, b) for a, b in zip(timed[1:], plain[1:]))
+    finally:
+        ctx.set_search_metric("sse")
+        ctx.set_stage_timing(False)
+    assert ctx.status() == 0
+    assert run()[0] == plain[0]

@@ -1007,6 +1007,36 @@ def test_eq14_constants_scale_with_bit_depth(ref):
         assert abs(t10 - 16 * t8) <= 8
 
 
+def test_eq14_term_within_single_precision_bound_of_exact_value(ref):
+    """R24: the fixed-order single-precision value is within the rounding
+    error of a handful of correctly rounded operations (plus the final
+    rounding to 1/256) of eq. 14 evaluated exactly (rational variances,
+    a 50-digit square root)."""
+    import decimal
+    from fractions import Fraction
+    decimal.getcontext().prec = 50
+    rng = np.random.default_rng(5)
+    for bd in (8, 10):
+        c1 = Fraction(25, 4) * 4 ** (bd - 8)
+        c2 = Fraction(625, 2) * 16 ** (bd - 8)
+        for n in (64, 32, 16):
+            for _ in range(200):
+                s = rng.integers(0, 1 << bd, n)
+                d = np.clip(s + rng.integers(-60, 61, n), 0, (1 << bd) - 1)
+                if rng.random() < 0.3:
+                    d = np.full(n, int(d.mean()))
+                sums = _sums(s, d)
+                _, s1s, s2s, s1d, s2d, sse = sums
+                vs = Fraction(n * s2s - s1s * s1s, n * n)
+                vd = Fraction(n * s2d - s1d * s1d, n * n)
+                root = (decimal.Decimal((vs * vd + c2).numerator)
+                        / decimal.Decimal((vs * vd + c2).denominator)).sqrt()
+                num = decimal.Decimal((vs + vd + c1).numerator) / decimal.Decimal((vs + vd + c1).denominator)
+                exact = 256 * num / (2 * root) * sse
+                got = ref.eq14_term(*sums, bd)
+                assert abs(decimal.Decimal(got) - exact) <= decimal.Decimal(0.5) + exact * decimal.Decimal(2 ** -20)
+
+
 def test_eq14_large_variance_tends_to_sse(ref):
     s = np.tile(np.array([0, 255]), 32)
     d = s.copy()
