@@ -770,13 +770,29 @@ static int64_t gen_total(int nblocks, const int64_t *dl, const int64_t *dc, int 
     return tot;
 }
 
-int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
-                                    const int64_t *dist_chroma, int width,
-                                    const uint8_t *skipped, int64_t lambda, int max_passes,
-                                    int32_t *presets, int32_t *npresets,
-                                    uint8_t *block_ids, int64_t *cost)
+/* Section 5's low-complexity search considers only a subset of the
+ * combinations.  Reading R26: the subset is the caller's choice of allowed
+ * (S_p, S_s) pairs per plane group, bit p * 4 + s of luma_pairs /
+ * chroma_pairs (the same pairs with either skip-condition bit in the
+ * 128-combination search); a preset is a candidate of the greedy search and
+ * of the re-optimisation when its luma and its chroma combination are both
+ * allowed.  Everything else is as in cdef_ref_select_presets_general. */
+static int allowed_preset(int t, int width, uint64_t luma_pairs, uint64_t chroma_pairs)
+{
+    int ql = (t / width) % 64, qc = (t % width) % 64;
+    return (int)((luma_pairs >> ql) & 1) && (int)((chroma_pairs >> qc) & 1);
+}
+
+int cdef_ref_select_presets_subset(int nblocks, const int64_t *dist_luma,
+                                   const int64_t *dist_chroma, int width,
+                                   const uint8_t *skipped, uint64_t luma_pairs,
+                                   uint64_t chroma_pairs, int64_t lambda, int max_passes,
+                                   int32_t *presets, int32_t *npresets,
+                                   uint8_t *block_ids, int64_t *cost)
 {
     if (nblocks <= 0 || (width != 64 && width != 128) || max_passes < 0)
+        return -1;
+    if (luma_pairs == 0 || chroma_pairs == 0)
         return -1;
     const int ntuples = width * width;
     int coded_blocks = 0;
@@ -789,6 +805,8 @@ int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
         int best_t = -1;
         int64_t best_total = 0;
         for (int t = 0; t < ntuples; t++) {
+            if (!allowed_preset(t, width, luma_pairs, chroma_pairs))
+                continue;
             greedy[n - 1] = t;
             int64_t tot = gen_total(nblocks, dist_luma, dist_chroma, width, skipped, greedy, n);
             if (best_t < 0 || tot < best_total) {
@@ -817,6 +835,8 @@ int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
                 int64_t best_total = gen_total(nblocks, dist_luma, dist_chroma, width, skipped,
                                                set, n);
                 for (int t = 0; t < ntuples; t++) {
+                    if (!allowed_preset(t, width, luma_pairs, chroma_pairs))
+                        continue;
                     set[k] = t;
                     int64_t v = gen_total(nblocks, dist_luma, dist_chroma, width, skipped, set, n);
                     if (v < best_total || (v == best_total && best_t != old && t < best_t)) {
@@ -854,6 +874,17 @@ int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
         block_ids[b] = (uint8_t)id;
     }
     return 0;
+}
+
+int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
+                                    const int64_t *dist_chroma, int width,
+                                    const uint8_t *skipped, int64_t lambda, int max_passes,
+                                    int32_t *presets, int32_t *npresets,
+                                    uint8_t *block_ids, int64_t *cost)
+{
+    return cdef_ref_select_presets_subset(nblocks, dist_luma, dist_chroma, width, skipped,
+                                          ~(uint64_t)0, ~(uint64_t)0, lambda, max_passes,
+                                          presets, npresets, block_ids, cost);
 }
 
 /* Chroma formats other than 4:2:0 (section 4, last paragraph; reading R25):

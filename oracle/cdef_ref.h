@@ -184,6 +184,16 @@ int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
                                     int32_t *presets, int32_t *npresets,
                                     uint8_t *block_ids, int64_t *cost);
 
+/* The same over the presets whose luma and chroma combinations are both
+ * allowed: bit p * 4 + s of luma_pairs / chroma_pairs (applied to both
+ * skip-bit halves when width = 128); both masks non-zero (reading R26). */
+int cdef_ref_select_presets_subset(int nblocks, const int64_t *dist_luma,
+                                   const int64_t *dist_chroma, int width,
+                                   const uint8_t *skipped, uint64_t luma_pairs,
+                                   uint64_t chroma_pairs, int64_t lambda, int max_passes,
+                                   int32_t *presets, int32_t *npresets,
+                                   uint8_t *block_ids, int64_t *cost);
+
 /* Section 5, eq. 14 (readings R22-R24 in cdef_ref.c): per filter block, 64
  * luma and 64 chroma entries sum_8x8 round(256 * D_8x8). */
 int cdef_ref_distortion_eq14(int w, int h, int bitdepth, int damping,

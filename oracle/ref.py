@@ -113,6 +113,10 @@ def lib():
             C.c_int, _i64p, _i64p, C.c_int, C.c_void_p, C.c_int64, C.c_int, _i32p,
             C.POINTER(C.c_int32), _u8p, C.POINTER(C.c_int64)]
         L.cdef_ref_select_presets_general.restype = C.c_int
+        L.cdef_ref_select_presets_subset.argtypes = [
+            C.c_int, _i64p, _i64p, C.c_int, C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64,
+            C.c_int, _i32p, C.POINTER(C.c_int32), _u8p, C.POINTER(C.c_int64)]
+        L.cdef_ref_select_presets_subset.restype = C.c_int
         L.cdef_ref_distortion_eq14.argtypes = (
             [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6 + [_i64p, _i64p])
         L.cdef_ref_distortion_eq14.restype = C.c_int
@@ -313,6 +317,46 @@ def select_presets_general(dist_luma, dist_chroma, width: int, skipped, lam: int
                                              C.byref(cost)) != 0:
         raise ValueError("oracle rejected select_presets_general arguments")
     return dict(presets=presets, npresets=n.value, block_ids=ids, cost=cost.value)
+
+
+def select_presets_subset(dist_luma, dist_chroma, width: int, skipped, luma_pairs: int,
+                          chroma_pairs: int, lam: int, max_passes: int = 0):
+    """Reading R26: the selection over presets whose luma and chroma
+    (S_p, S_s) pairs are allowed by the two 64-bit masks."""
+    dl = np.ascontiguousarray(dist_luma, np.int64).reshape(-1)
+    dc = np.ascontiguousarray(dist_chroma, np.int64).reshape(-1)
+    nb = dl.size // width
+    sk = None if skipped is None else np.ascontiguousarray(skipped, np.uint8)
+    presets = np.zeros(8, np.int32)
+    n = C.c_int32(0)
+    ids = np.zeros(nb, np.uint8)
+    cost = C.c_int64(0)
+    if lib().cdef_ref_select_presets_subset(nb, dl, dc, width,
+                                            None if sk is None else sk.ctypes.data,
+                                            luma_pairs, chroma_pairs, lam, max_passes, presets,
+                                            C.byref(n), ids, C.byref(cost)) != 0:
+        raise ValueError("oracle rejected select_presets_subset arguments")
+    return dict(presets=presets, npresets=n.value, block_ids=ids, cost=cost.value)
+
+
+def search_strengths_subset(rec, src, bitdepth: int, damping: int, lam: int, luma_pairs: int,
+                            chroma_pairs: int, refine_passes: int = 0, coded=None,
+                            metric: str = "sse"):
+    """The low-complexity search: full tables (squared error, eq. 14, or the
+    128 combinations when `coded` is given), selection over the subset."""
+    sk = None
+    if coded is not None:
+        dl, dc, sk = distortion_coded(rec, src, bitdepth, damping, coded)
+        width = 128
+    elif metric == "eq14":
+        dl, dc = distortion_eq14(rec, src, bitdepth, damping)
+        width = 64
+    else:
+        dl, dc = distortion(rec, src, bitdepth, damping)
+        width = 64
+    out = select_presets_subset(dl, dc, width, sk, luma_pairs, chroma_pairs, lam, refine_passes)
+    out.update(dist_luma=dl, dist_chroma=dc, skipped=sk)
+    return out
 
 
 def search_strengths_coded(rec, src, bitdepth: int, damping: int, lam: int, coded=None,

@@ -914,6 +914,86 @@ def test_skipped_blocks_leave_the_selection(ref):
     assert (full["block_ids"][sk == 1] == 0).all()
 
 
+# --------------------------------------------------------------- section 5: low-complexity subset
+def _mask(bits):
+    m = 0
+    for q in bits:
+        m |= 1 << q
+    return m
+
+
+@pytest.mark.parametrize("seed", [40, 41, 42])
+def test_subset_greedy_matches_brute_force(ref, seed):
+    """R26: the greedy search over the allowed presets equals a brute-force
+    greedy that only looks at presets whose two pairs are allowed; every
+    chosen preset is allowed."""
+    rng = np.random.default_rng(seed)
+    B = int(rng.integers(1, 6))
+    dl = rng.integers(0, 300, (B, 64)).astype(np.int64)
+    dc = rng.integers(0, 300, (B, 64)).astype(np.int64)
+    lq = sorted(set(rng.integers(0, 64, 9).tolist()))
+    cq = sorted(set(rng.integers(0, 64, 5).tolist()))
+    lam = int(rng.integers(0, 100))
+    out = ref.select_presets_subset(dl, dc, 64, None, _mask(lq), _mask(cq), lam)
+    full = (dl[:, :, None] + dc[:, None, :]).reshape(B, 4096)
+    allowed = np.array([(t // 64 in lq) and (t % 64 in cq) for t in range(4096)])
+    cur = np.full(B, np.iinfo(np.int64).max)
+    chosen, totals = [], []
+    for _ in range(8):
+        tot = np.minimum(cur[:, None], full).sum(0)
+        tot = np.where(allowed, tot, np.iinfo(np.int64).max)
+        t = int(np.argmin(tot))
+        chosen.append(t)
+        totals.append(int(tot[t]))
+        cur = np.minimum(cur, full[:, t])
+    J = {n: totals[n - 1] + lam * B * int(math.log2(n)) for n in (1, 2, 4, 8)}
+    best = min((1, 2, 4, 8), key=lambda n: (J[n], n))
+    assert list(out["presets"]) == chosen
+    assert out["npresets"] == best and out["cost"] == J[best]
+    assert (out["block_ids"] == np.argmin(full[:, chosen[:best]], axis=1)).all()
+    assert all(allowed[t] for t in out["presets"])
+
+
+def test_subset_of_one_pair_and_full_masks(ref):
+    rng = np.random.default_rng(43)
+    dl = rng.integers(0, 500, (7, 64)).astype(np.int64)
+    dc = rng.integers(0, 500, (7, 64)).astype(np.int64)
+    one = ref.select_presets_subset(dl, dc, 64, None, 1 << 22, 1 << 5, 0, 3)
+    assert list(one["presets"]) == [22 * 64 + 5] * 8
+    assert one["npresets"] == 1 and one["cost"] == int((dl[:, 22] + dc[:, 5]).sum())
+    assert (one["block_ids"] == 0).all()
+    every = (1 << 64) - 1
+    for lam, passes in [(0, 0), (30, 4)]:
+        a = ref.select_presets_subset(dl, dc, 64, None, every, every, lam, passes)
+        b = ref.select_presets_general(dl, dc, 64, None, lam, passes)
+        assert list(a["presets"]) == list(b["presets"]) and a["cost"] == b["cost"]
+        # a smaller subset never does better at N = 1
+        c = ref.select_presets_subset(dl, dc, 64, None, every >> 32, every, lam, passes)
+        assert c["cost"] >= b["cost"] or c["npresets"] != 1
+    with pytest.raises(ValueError):
+        ref.select_presets_subset(dl, dc, 64, None, 0, every, 0)
+
+
+def test_subset_applies_to_both_skip_bit_halves(ref):
+    """In the 128-combination tables the mask of pair q allows q and 64 + q:
+    restricting the tables to those columns and searching them in full gives
+    the same presets (mapped back)."""
+    rng = np.random.default_rng(44)
+    dl = rng.integers(0, 400, (5, 128)).astype(np.int64)
+    dc = rng.integers(0, 400, (5, 128)).astype(np.int64)
+    sk = np.array([0, 0, 1, 0, 0], np.uint8)
+    lq, cq = [3, 17, 40], [0, 9]
+    out = ref.select_presets_subset(dl, dc, 128, sk, _mask(lq), _mask(cq), 11, 2)
+    lcols = lq + [64 + q for q in lq]
+    ccols = cq + [64 + q for q in cq]
+    # brute force over the allowed presets, restated with explicit columns
+    full = dl[:, lcols][:, :, None] + dc[:, ccols][:, None, :]
+    best1 = min(int(full[sk == 0, i, j].sum()) for i in range(len(lcols)) for j in range(len(ccols)))
+    t0 = int(out["presets"][0])
+    assert (t0 // 128) in lcols and (t0 % 128) in ccols
+    assert int((dl[sk == 0, t0 // 128] + dc[sk == 0, t0 % 128]).sum()) == best1
+
+
 # --------------------------------------------------------------- chroma formats (section 4)
 def _format_frame(fmt, w=192, h=136, bd=8, seed=60):
     rng = np.random.default_rng(seed)
