@@ -286,6 +286,18 @@ int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
 #define CDEF_METRIC_EQ14 1
 int cdef_ctx_set_search_metric(cdef_ctx *ctx, int metric);
 
+/* Low-complexity strength search (section 5: considering only a subset of
+ * the combinations).  Bit p * 4 + s of luma_pairs / chroma_pairs allows the
+ * pair (S_p = p, S_s = the s-th of 0, 1, 2, 4) for that plane group; in the
+ * 128-combination search it allows the pair with either skip-condition bit.
+ * Later cdef_search_strengths / cdef_search_strengths_coded calls on the
+ * context evaluate only primaries with an allowed pair, write 0 to the
+ * table entries of pairs outside the subset, and choose presets (greedy,
+ * re-optimisation) only among those whose luma and chroma pairs are both
+ * allowed.  Default: every pair (~0 for both).  A zero mask is CDEF_ERR_ARG.
+ * Host only; cdef_search_strengths_noalloc always searches every pair. */
+int cdef_ctx_set_search_subset(cdef_ctx *ctx, uint64_t luma_pairs, uint64_t chroma_pairs);
+
 /* Per-stage device times of the strength search (no paper counterpart: a
  * profiling aid).  With timing on, later searches on the context record
  * CUDA events before the distortion-table kernel, between it and the preset

@@ -93,6 +93,7 @@ def load():
     L.cdef_ctx_set_search_metric.argtypes = [vp, C.c_int]
     L.cdef_ctx_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.cdef_ctx_set_stage_timing.argtypes = [vp, C.c_int]
+    L.cdef_ctx_set_search_subset.argtypes = [vp, C.c_uint64, C.c_uint64]
     L.cdef_ctx_get_stage_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.cdef_search_strengths_coded.argtypes = [
         vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(vp), C.POINTER(i32),
@@ -106,7 +107,7 @@ def load():
                  "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap",
                  "cdef_ctx_set_search_refine", "cdef_search_strengths_coded",
                  "cdef_ctx_set_search_metric", "cdef_ctx_set_stage_timing",
-                 "cdef_ctx_get_stage_times"):
+                 "cdef_ctx_get_stage_times", "cdef_ctx_set_search_subset"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -291,6 +292,12 @@ class Context:
         """'sse' (default) or 'eq14' (section 5's SSIM-weighted distortion)."""
         m = {"sse": 0, "eq14": 1}[metric]
         _check(self._lib.cdef_ctx_set_search_metric(self.handle, m), "cdef_ctx_set_search_metric")
+
+    def set_search_subset(self, luma_pairs: int = (1 << 64) - 1, chroma_pairs: int = (1 << 64) - 1):
+        """Allowed (S_p, S_s) pairs of later searches, bit p * 4 + s per plane
+        group (default: all)."""
+        _check(self._lib.cdef_ctx_set_search_subset(self.handle, luma_pairs, chroma_pairs),
+               "cdef_ctx_set_search_subset")
 
     def set_stage_timing(self, enable: bool):
         """Record per-stage device times of later strength searches."""

@@ -36,6 +36,7 @@ struct cdef_ctx {
     bool overlap;                 // filter calls on a stream declared independent
     int refine_passes;            // preset re-optimisation passes of the search (0 = greedy)
     int metric;                   // search distortion: 0 squared error, 1 eq. 14
+    uint64_t pairs[2];            // allowed (S_p, S_s) pairs of the search (luma, chroma)
     int search_key_refine;        // refine_passes search_exec was recorded with
     bool stage_timing;            // record stage events in the search graph
     bool search_key_timing;       // and whether search_exec holds them
@@ -253,6 +254,7 @@ int cdef_ctx_create(cdef_ctx **out, int device, size_t hbm_budget_bytes)
     if (!ctx) return CDEF_ERR_NOMEM;
     ctx->device = device;
     ctx->budget = hbm_budget_bytes;
+    ctx->pairs[0] = ctx->pairs[1] = ~0ull;
     const size_t fixed = sizeof(int) + sizeof(SearchResultDev) * kMaxBatch +
                          sizeof(unsigned) * 2 * kWorkSlots;
     if (ctx->budget && fixed > ctx->budget) {
@@ -314,6 +316,14 @@ int cdef_ctx_set_search_metric(cdef_ctx *ctx, int metric)
 {
     if (!ctx || (metric != CDEF_METRIC_SSE && metric != CDEF_METRIC_EQ14)) return CDEF_ERR_ARG;
     ctx->metric = metric;
+    return CDEF_OK;
+}
+
+int cdef_ctx_set_search_subset(cdef_ctx *ctx, uint64_t luma_pairs, uint64_t chroma_pairs)
+{
+    if (!ctx || !luma_pairs || !chroma_pairs) return CDEF_ERR_ARG;
+    ctx->pairs[0] = luma_pairs;
+    ctx->pairs[1] = chroma_pairs;
     return CDEF_OK;
 }
 
@@ -604,7 +614,8 @@ int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long 
     if (!ctx->tuned) ctx->tuned = new (std::nothrow) std::unordered_map<uint64_t, SearchTune>();
     if (!ctx->tuned) return CDEF_ERR_NOMEM;
     const uint64_t key = search_shape(b) ^ ((uint64_t)ctx->forced.groups << 56) ^
-                         ((uint64_t)ctx->forced.ctas_per_sm << 60) ^ (skipped ? 1ull << 52 : 0);
+                         ((uint64_t)ctx->forced.ctas_per_sm << 60) ^ (skipped ? 1ull << 52 : 0) ^
+                         ((ctx->pairs[0] & ctx->pairs[1]) != ~0ull ? 1ull << 51 : 0);
     auto it = ctx->tuned->find(key);
     if (it != ctx->tuned->end()) {
         *out = it->second;
@@ -697,6 +708,8 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
         f.fb_rows = (f.h + 63) / 64;
         f.block_start = total;
         f.lambda = lambda[i];
+        f.pairs[0] = ctx->pairs[0];
+        f.pairs[1] = ctx->pairs[1];
         total += f.fb_cols * f.fb_rows;
     }
     if (rc != CDEF_OK) { delete b; return rc; }

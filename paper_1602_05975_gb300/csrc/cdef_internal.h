@@ -59,6 +59,9 @@ struct SearchFrameDev {  // aligned as CUtensorMap requires
     int block_start;                 // first filter block of this frame in the tables
     long long lambda;
     const uint8_t *coded;            // 8x8 coded-residual map (128-combination search only)
+    // allowed (S_p, S_s) pairs of the luma and the chroma group, bit p * 4 + s
+    // (section 5's low-complexity search; all ones: every pair)
+    unsigned long long pairs[2] = {~0ull, ~0ull};
 };
 
 struct SearchBatch {
@@ -66,6 +69,14 @@ struct SearchBatch {
     int total_blocks;
     SearchFrameDev f[kMaxBatch];
 };
+static_assert(sizeof(SearchBatch) <= 32764, "a search batch must fit the kernel parameter space");
+
+// The allowed pairs of plane group g (0 luma, 1 chroma); an empty set is
+// read as every pair.
+__host__ __device__ inline unsigned long long allowed_pairs(const SearchFrameDev &F, int g)
+{
+    return F.pairs[g] ? F.pairs[g] : ~0ull;
+}
 
 // Per-frame result of the preset search (device).
 struct SearchResultDev {

@@ -179,14 +179,20 @@ __device__ __forceinline__ bool better(unsigned long long a, int ta, unsigned lo
     return a < b || (a == b && ta < tb);
 }
 
-// The least of a frame's totals and its lowest index (whole CTA).
-__device__ void frame_argmin(unsigned long long *t, int ntuples, Shared &sh,
+// The least of a frame's totals over the presets whose luma and chroma
+// combinations are both allowed (section 5's low-complexity search; the
+// mask of pair q covers q and 64 + q), and its lowest index (whole CTA).
+__device__ void frame_argmin(unsigned long long *t, int width, const SearchFrameDev &F, Shared &sh,
                              unsigned long long *min_v, int *min_t)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ntuples = width * width;
+    const unsigned long long lp = allowed_pairs(F, 0), cp = allowed_pairs(F, 1);
     unsigned long long bv = ULLONG_MAX;
     int bt = INT_MAX;
     for (int i = tid; i < ntuples; i += kThreads) {
+        const int ql = (i / width) & 63, qc = (i % width) & 63;
+        if (!((lp >> ql) & (cp >> qc) & 1)) continue;
         const unsigned long long v = __ldcg(&t[i]);
         if (better(v, i, bv, bt)) { bv = v; bt = i; }
     }
@@ -240,7 +246,7 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
             unsigned long long *t = tot + (int64_t)f * ntuples;
             unsigned long long v;
             int best;
-            frame_argmin(t, ntuples, sh, &v, &best);
+            frame_argmin(t, width, batch.f[f], sh, &v, &best);
             if (tid == 0) {
                 res[f].greedy[step] = best;
                 res[f].totals[step] = (long long)v;
@@ -283,7 +289,7 @@ preset_kernel(const __grid_constant__ SearchBatch batch, const long long *__rest
                     const unsigned long long old_v = __ldcg(&t[old]);
                     unsigned long long v;
                     int best;
-                    frame_argmin(t, ntuples, sh, &v, &best);
+                    frame_argmin(t, width, batch.f[f], sh, &v, &best);
                     if (tid == 0) {
                         if (old_v == v) best = old;        // keep the current preset on ties
                         if (best != old) {

@@ -348,6 +348,13 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         const uint8_t *sa = luma ? F.src[0] : F.src[1];
         const int64_t spa = luma ? F.src_pitch[0] : F.src_pitch[1];
 
+        // section 5's low-complexity search: primaries with no allowed pair
+        // are not evaluated, entries of pairs outside the subset are 0
+        const unsigned long long pairs = allowed_pairs(F, task);
+        uint32_t pmask = 0;
+#pragma unroll
+        for (int p = 0; p < 16; p++) pmask |= (uint32_t)(((pairs >> (4 * p)) & 15ull) != 0) << p;
+
         uint32_t acc[kEq14 ? 1 : kN], sse0 = 0;
 #pragma unroll
         for (int q = 0; q < (kEq14 ? 1 : kN); q++) acc[q] = 0;
@@ -417,6 +424,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
 #pragma unroll
                 for (int pp = 0; pp < kPP; pp++) {
                     const int p = p0 + pp;
+                    if (!((pmask >> p) & 1)) continue;
                     const SetC sc = ps[p];
                     const uint32_t T0 = pri_sum(v, X, sc, (bits >> p) & 1) + C;
                     const bool rz = (raised >> p) & 1;
@@ -561,17 +569,18 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
             __syncthreads();
             if (tid < kN) {
                 const long long base_sse = (long long)sm.base[task];
+                const bool on = (pairs >> (4 * p0 + tid)) & 1;
                 if (!kCoded) {
                     long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
-                    out[tid] = (long long)sm.acc[tid] + base_sse;
+                    out[tid] = on ? (long long)sm.acc[tid] + base_sse : 0;
                 } else {
                     // q = k * 64 + p * 4 + s; skip bit clear: blocks without coded
                     // residual unfiltered, (0, 0) the unfiltered error
                     long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 128 +
                                      4 * p0 + tid;
                     const long long tot = (long long)sm.acc[tid], un = (long long)sm.accu[tid];
-                    out[0] = (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un;
-                    out[64] = !any_coded ? base_sse : base_sse + tot;
+                    out[0] = !on ? 0 : (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un;
+                    out[64] = !on ? 0 : !any_coded ? base_sse : base_sse + tot;
                 }
                 sm.acc[tid] = 0;
                 sm.accu[tid] = 0;
@@ -596,8 +605,10 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         }
         __syncthreads();
         if (tid < kN) {
-            dist_luma[(int64_t)blk_global * 64 + 4 * p0 + tid] = (long long)sm.acc[tid];
-            dist_chroma[(int64_t)blk_global * 64 + 4 * p0 + tid] = (long long)sm.acc14c[tid];
+            const int q = 4 * p0 + tid;
+            const bool on_l = (allowed_pairs(F, 0) >> q) & 1, on_c = (allowed_pairs(F, 1) >> q) & 1;
+            dist_luma[(int64_t)blk_global * 64 + q] = on_l ? (long long)sm.acc[tid] : 0;
+            dist_chroma[(int64_t)blk_global * 64 + q] = on_c ? (long long)sm.acc14c[tid] : 0;
             sm.acc[tid] = 0;
             sm.acc14c[tid] = 0;
         }

@@ -671,3 +671,78 @@ def test_search_stage_timing(cdef, ctx):
         ctx.set_stage_timing(False)
     assert ctx.status() == 0
     assert run()[0] == plain[0]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("variant,passes", [("sse", 0), ("sse", 3), ("eq14", 2), ("coded", 0),
+                                            ("coded", 2)])
+def test_search_subset_parity(cdef, ctx, ref, variant, passes):
+    """Section 5's low-complexity search (reading R26): tables of allowed
+    pairs equal the oracle's, the others are 0; presets, N, J and ids equal
+    the oracle's selection over the subset, for every launch configuration."""
+    from paper_1602_05975_gb300 import synth
+    specs = [(200, 136, 8, 16, 1130), (136, 72, 10, 32, 1131), (192, 128, 8, 64, 1132)]
+    frames = [synth.make_frame(w, h, bd, q, seed=s) for w, h, bd, q, s in specs]
+    rng = np.random.default_rng(1133)
+    lq = sorted(set(rng.integers(0, 64, 12).tolist()) | {0})
+    cq = sorted(set(rng.integers(0, 64, 6).tolist()))
+    lmask = sum(1 << q for q in lq)
+    cmask = sum(1 << q for q in cq)
+    width = 128 if variant == "coded" else 64
+    maps = []
+    if variant == "coded":
+        for f in frames:
+            m = (rng.random((f.height // 8, f.width // 8)) < 0.6).astype(np.uint8)
+            m[:8, :8] = 0
+            maps.append(m)
+    damping, lambdas = [5, 4, 6], [64, 512, 4096]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+    recs = [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames]
+    srcs = [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames]
+    configs = [(0, 0)] if variant == "eq14" else [(0, 0), (1, 2), (4, 2)]
+    ctx.set_search_subset(lmask, cmask)
+    ctx.set_search_refine(passes)
+    if variant == "eq14":
+        ctx.set_search_metric("eq14")
+    try:
+        for groups, per_sm in configs:
+            ctx.set_tuning(groups, per_sm)
+            ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+            dl = torch.full((nb * width,), -1, dtype=torch.int64, device="cuda")
+            dc = torch.full((nb * width,), -1, dtype=torch.int64, device="cuda")
+            if variant == "coded":
+                res = cdef.cdef_search_strengths_coded(
+                    ctx, recs, srcs, [torch.from_numpy(m.reshape(-1)).cuda() for m in maps],
+                    damping, lambdas, ids, dl, dc)
+            else:
+                res = cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc)
+            assert ctx.status() == 0
+            o0 = 0
+            for i, (f, r, d, lam) in enumerate(zip(frames, res, damping, lambdas)):
+                b = f.params.shape[0] * f.params.shape[1]
+                o = ref.search_strengths_subset(f.rec, f.src, f.bitdepth, d, lam, lmask, cmask,
+                                                passes, maps[i] if maps else None, variant)
+                gl = dl[o0 * width:(o0 + b) * width].cpu().numpy().reshape(b, width)
+                gc = dc[o0 * width:(o0 + b) * width].cpu().numpy().reshape(b, width)
+                cols_l = np.array([((lmask >> (q % 64)) & 1) == 1 for q in range(width)])
+                cols_c = np.array([((cmask >> (q % 64)) & 1) == 1 for q in range(width)])
+                assert np.array_equal(gl[:, cols_l], o["dist_luma"][:, cols_l])
+                assert np.array_equal(gc[:, cols_c], o["dist_chroma"][:, cols_c])
+                assert (gl[:, ~cols_l] == 0).all() and (gc[:, ~cols_c] == 0).all()
+                assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"]
+                idx = cdef.preset_index_coded if variant == "coded" else cdef.preset_index
+                assert [idx(p) for p in r["presets"][:r["npresets"]]] == \
+                    [int(t) for t in o["presets"][:o["npresets"]]]
+                assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+                o0 += b
+    finally:
+        ctx.set_tuning(0, 0)
+        ctx.set_search_refine(0)
+        ctx.set_search_metric("sse")
+        ctx.set_search_subset()
+
+
+@pytest.mark.gpu
+def test_search_subset_rejections(cdef, ctx):
+    assert ctx._lib.cdef_ctx_set_search_subset(ctx.handle, 0, 1) != 0
+    assert ctx._lib.cdef_ctx_set_search_subset(ctx.handle, 1, 0) != 0
