@@ -456,6 +456,29 @@ def run_ours(args):
         e_ms = max_over_ranks(e_ms, dev)
         e2e = {"value": whole_job_rate(ws, nf * px_per_frame, e_ms / args.steps), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+        # the same copies without the filter: the ceiling the link sets
+        def copy_step():
+            for i in range(nf):
+                s = streams[i % len(streams)]
+                with torch.cuda.stream(s):
+                    for dt, st in zip(ins[i].planes(), hin[i].planes()):
+                        dt.copy_(st, non_blocking=True)
+                    for st, dt in zip(hout[i].planes(), outs[i].planes()):
+                        st.copy_(dt, non_blocking=True)
+
+        for _ in range(args.warmup):
+            copy_step()
+        torch.cuda.synchronize()
+        tt0 = time.perf_counter()
+        for _ in range(args.steps):
+            copy_step()
+        torch.cuda.synchronize()
+        c_ms = max_over_ranks((time.perf_counter() - tt0) * 1e3, dev)
+        e2e["copies_only"] = {
+            "value": whole_job_rate(ws, nf * px_per_frame, c_ms / args.steps), "unit": UNIT,
+            "gb_per_s": (h2d + d2h) / (c_ms / args.steps * 1e-3) / 1e9,
+            "what": "the same host-device copies per step without the filter"}
         for h, o in zip(hout[:1], outs[:1]):
             assert all(np.array_equal(a, b) for a, b in zip(h.to_numpy(), o.to_numpy()))
 

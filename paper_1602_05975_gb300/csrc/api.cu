@@ -415,14 +415,13 @@ namespace {
 
 // One launch of the filter over a single plane in the luma slot: mode 1 the
 // luma plane, mode 2 a 4:4:4 chroma plane (chroma parameters, maps given).
-int plane_pass(cdef_ctx *ctx, const cdef_frame *in, const cdef_plane &pin, const cdef_plane &pout,
-               const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
-               const uint8_t *coded, int mode, bool overlap, cudaStream_t s)
+// One plane of a frame as a filter entry in the luma geometry (mode 1: the
+// luma plane, mode 2: a 4:4:4 chroma plane); its blocks start at
+// `block_start` of the launch.
+int fill_plane_dev(FilterFrameDev &d, const cdef_frame *in, const cdef_plane &pin,
+                   const cdef_plane &pout, const cdef_fb_params *params, const uint8_t *dir,
+                   const int32_t *var, const uint8_t *coded, int mode, int block_start)
 {
-    FilterBatch<1> b;
-    b.n = 1;
-    b.total_blocks = fb_count(in);
-    FilterFrameDev &d = b.f[0];
     memset(&d, 0, sizeof(d));
     for (int i = 0; i < 3; i++) {
         d.p[i].in = static_cast<const uint8_t *>(pin.data);
@@ -440,11 +439,23 @@ int plane_pass(cdef_ctx *ctx, const cdef_frame *in, const cdef_plane &pin, const
     d.bitdepth = in->bitdepth;
     d.fb_cols = (in->y.width + 63) / 64;
     d.fb_rows = (in->y.height + 63) / 64;
-    d.block_start = 0;
+    d.block_start = block_start;
     const int bytes = sample_bytes(in->bitdepth);
     int rc = encode_plane(&d.tmap[0], pin, bytes, luma_box_cols(bytes), kLumaBoxRows);
     if (rc) return rc;
     d.tmap[1] = d.tmap[2] = d.tmap[0];   // not loaded in modes 1 and 2
+    return CDEF_OK;
+}
+
+int plane_pass(cdef_ctx *ctx, const cdef_frame *in, const cdef_plane &pin, const cdef_plane &pout,
+               const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
+               const uint8_t *coded, int mode, bool overlap, cudaStream_t s)
+{
+    FilterBatch<1> b;
+    b.n = 1;
+    b.total_blocks = fb_count(in);
+    int rc = fill_plane_dev(b.f[0], in, pin, pout, params, dir, var, coded, mode, 0);
+    if (rc) return rc;
     unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
     return cuda_status(launch_filter_single(b, ctx->status, work, overlap, s));
 }
@@ -511,9 +522,8 @@ int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params
             }
         return CDEF_OK;
     }
-    // 4:4:4: the luma directions first (unless given), then each plane in
-    // the luma geometry; every launch waits for the one before it (they
-    // share the maps)
+    // 4:4:4: the luma directions first (unless given), then the three planes
+    // in the luma geometry as one launch, which waits for the maps
     if (!dir) {
         const size_t blocks = (size_t)(in->y.width / 8) * (in->y.height / 8);
         if ((rc = ensure_maps(ctx, blocks))) return rc;
@@ -524,9 +534,16 @@ int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params
                                               in->bitdepth, ctx->maps_dir, ctx->maps_var, s))))
             return rc;
     }
-    if ((rc = plane_pass(ctx, in, in->y, out->y, params, dir, var, coded, 1, false, s))) return rc;
-    if ((rc = plane_pass(ctx, in, in->u, out->u, params, dir, var, coded, 2, false, s))) return rc;
-    return plane_pass(ctx, in, in->v, out->v, params, dir, var, coded, 2, false, s);
+    FilterBatch<3> b;
+    b.n = 3;
+    const int B = fb_count(in);
+    b.total_blocks = 3 * B;
+    if ((rc = fill_plane_dev(b.f[0], in, in->y, out->y, params, dir, var, coded, 1, 0)) ||
+        (rc = fill_plane_dev(b.f[1], in, in->u, out->u, params, dir, var, coded, 2, B)) ||
+        (rc = fill_plane_dev(b.f[2], in, in->v, out->v, params, dir, var, coded, 2, 2 * B)))
+        return rc;
+    unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
+    return cuda_status(launch_filter_planes(b, ctx->status, work, false, s));
 }
 
 }  // namespace

@@ -104,6 +104,9 @@ cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status, unsigned 
                                  bool overlap, cudaStream_t s);
 cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *status,
                                 unsigned *work, bool overlap, cudaStream_t s);
+// The three planes of a 4:4:4 frame (entries in modes 1, 2, 2) in one launch.
+cudaError_t launch_filter_planes(const FilterBatch<3> &b, int *status, unsigned *work,
+                                 bool overlap, cudaStream_t s);
 constexpr int kWorkSlots = 1024;  // counter pairs per context (launches in flight at once)
 
 // Filter tile geometry shared by the host (tensor-map boxes) and the kernel.

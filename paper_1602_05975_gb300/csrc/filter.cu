@@ -47,10 +47,10 @@ namespace {
 using namespace tile;
 
 constexpr int kThreads = 256;
-constexpr int kMinCtas = 3;                        // resident CTAs per SM the registers are sized for
+constexpr int kMinCtas = 4;                        // resident CTAs per SM the registers are sized for
 
 struct FilterSmem {
-    RawTiles raw[2];
+    RawTiles raw;                                       // the next block's tiles land here
     PairTiles t;
     alignas(16) int off[2][8][12];                      // tap word offsets [luma/chroma][d][tap]
     int cost[64][8];
@@ -60,8 +60,8 @@ struct FilterSmem {
     uint8_t dir[64];
     uint8_t coded[64];                                  // 8x8 block has coded residual
     int var[64];
-    int blk[2];                                         // block id of each raw buffer
-    alignas(8) uint64_t bar[2];
+    int blk_next;                                       // block id of the tiles in `raw`
+    alignas(8) uint64_t bar;
 };
 
 // One filtered word from its centre X and the 12 tap values.
@@ -139,9 +139,11 @@ __device__ __noinline__ int filter_scalar(PX px, int r, int c, int d, Eff e)
 
 // Everything after the tiles have landed: re-layout, direction search,
 // per-block parameters, filtering and stores of one 64x64 filter block.
-template <typename T>
+// `prefetch` runs (on every thread) once the raw tiles have been re-laid,
+// so that the next block's tiles can land in the same buffer.
+template <typename T, typename Prefetch>
 __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *status,
-                              FilterSmem &sm, const RawTiles &raw)
+                              FilterSmem &sm, const RawTiles &raw, Prefetch prefetch)
 {
     const int sh8 = F.bitdepth - 8;
     const int W = F.p[0].w, H = F.p[0].h, CW = F.p[1].w, CH = F.p[1].h;
@@ -175,6 +177,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
                         (with_chroma && (cy0 + 34 > CH || cx0 + 34 > CW));
     stage_relayout<T, kThreads>(sm.t, raw, border, ly0, lx0, H, W, cy0, cx0, CH, CW, with_chroma);
     __syncthreads();
+    prefetch();
 
     // ---- direction search
     const int bw = W >> 3;
@@ -371,11 +374,10 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
         if (tid == 0) atomicOr(status, kStatusMisaligned);
     } else {
         if (tid == 0) {
-            mbar_init(&sm.bar[0], 1);
-            mbar_init(&sm.bar[1], 1);
+            mbar_init(&sm.bar, 1);
             const int b = (int)atomicAdd(&work[0], 1u);
-            sm.blk[0] = b;
-            if (b < total) issue_loads(batch, b, sm.raw[0], &sm.bar[0]);
+            sm.blk_next = b;
+            if (b < total) issue_loads(batch, b, sm.raw, &sm.bar);
         }
         if (tid < 192) {  // tap offset tables [luma/chroma][d][tap]
             const int pl = tid / 96, d = (tid / 12) & 7, t = tid % 12;
@@ -385,30 +387,30 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
         }
         __syncthreads();
 
+        // one tile buffer: block n's tiles are re-laid into the pair tiles,
+        // then block n+1's loads are issued into the buffer while block n is
+        // searched and filtered
         for (int it = 0;; it++) {
-            const int buf = it & 1;
-            const int blk = sm.blk[buf];
+            const int blk = sm.blk_next;
             if (blk >= total) break;
-            if (tid == 0) {
-                const int nb = (int)atomicAdd(&work[0], 1u);
-                sm.blk[buf ^ 1] = nb;
-                if (nb < total) issue_loads(batch, nb, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
-            }
-            const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, kWaitCycles);
+            const bool arrived = mbar_wait_bounded(&sm.bar, it & 1, kWaitCycles);
             if (__syncthreads_or(!arrived)) {  // the whole CTA leaves together
-                if (tid == 0) {
-                    atomicOr(status, kStatusTimeout);
-                    if (sm.blk[buf ^ 1] < total)  // let the prefetch in flight land first
-                        mbar_wait_bounded(&sm.bar[buf ^ 1], ((it + 1) >> 1) & 1, kWaitCycles);
-                }
+                if (tid == 0) atomicOr(status, kStatusTimeout);
                 break;
             }
+            auto prefetch = [&]() {
+                if (tid == 0) {
+                    const int nb = (int)atomicAdd(&work[0], 1u);
+                    sm.blk_next = nb;
+                    if (nb < total) issue_loads(batch, nb, sm.raw, &sm.bar);
+                }
+            };
             const BlockRef r = locate(batch, blk);
             const FilterFrameDev &F = batch.f[r.fi];
             if (F.bitdepth == 8)
-                process_block<uint8_t>(F, r.fby, r.fbx, status, sm, sm.raw[buf]);
+                process_block<uint8_t>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch);
             else
-                process_block<uint16_t>(F, r.fby, r.fbx, status, sm, sm.raw[buf]);
+                process_block<uint16_t>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch);
             __syncthreads();  // shared tiles, tables and the next block id are settled
         }
     }
@@ -476,6 +478,12 @@ cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *stat
                                 bool overlap, cudaStream_t s)
 {
     return launch_pdl<kMaxFilterBatch>(b, status, work, overlap, s);
+}
+
+cudaError_t launch_filter_planes(const FilterBatch<3> &b, int *status, unsigned *work,
+                                 bool overlap, cudaStream_t s)
+{
+    return launch_pdl<3>(b, status, work, overlap, s);
 }
 
 }  // namespace cdefgb

@@ -186,15 +186,22 @@ __device__ void frame_argmin(unsigned long long *t, int width, const SearchFrame
                              unsigned long long *min_v, int *min_t)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ntuples = width * width;
+    const int ntuples = width * width, lg = width == 128 ? 7 : 6;
     const unsigned long long lp = allowed_pairs(F, 0), cp = allowed_pairs(F, 1);
     unsigned long long bv = ULLONG_MAX;
     int bt = INT_MAX;
-    for (int i = tid; i < ntuples; i += kThreads) {
-        const int ql = (i / width) & 63, qc = (i % width) & 63;
-        if (!((lp >> ql) & (cp >> qc) & 1)) continue;
-        const unsigned long long v = __ldcg(&t[i]);
-        if (better(v, i, bv, bt)) { bv = v; bt = i; }
+    if ((lp & cp) == ~0ull) {
+        for (int i = tid; i < ntuples; i += kThreads) {
+            const unsigned long long v = __ldcg(&t[i]);
+            if (better(v, i, bv, bt)) { bv = v; bt = i; }
+        }
+    } else {
+        for (int i = tid; i < ntuples; i += kThreads) {
+            const int ql = (i >> lg) & 63, qc = i & 63;
+            if (!((lp >> ql) & (cp >> qc) & 1)) continue;
+            const unsigned long long v = __ldcg(&t[i]);
+            if (better(v, i, bv, bt)) { bv = v; bt = i; }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

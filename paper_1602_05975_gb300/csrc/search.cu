@@ -224,7 +224,9 @@ __device__ long long eq14_value(int n, long long s1s, long long s2s, long long s
 // evaluates the (19, 7) preset instead; each candidate's sum is also kept
 // for the 8x8 blocks without coded residual, so that the skip-bit-clear
 // entries (those blocks unfiltered) follow as base + total - uncoded part.
-template <typename T, int kG, bool kCoded, bool kEq14>
+// kSub: a subset of the pairs is allowed (section 5's low-complexity
+// search): primaries without an allowed pair are skipped.
+template <typename T, int kG, bool kCoded, bool kEq14, bool kSub>
 __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global, int grp,
                            SearchSmem &sm, const RawTiles &raw, long long *dist_luma,
                            long long *dist_chroma, uint8_t *skipped)
@@ -424,7 +426,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
 #pragma unroll
                 for (int pp = 0; pp < kPP; pp++) {
                     const int p = p0 + pp;
-                    if (!((pmask >> p) & 1)) continue;
+                    if (kSub && !((pmask >> p) & 1)) continue;
                     const SetC sc = ps[p];
                     const uint32_t T0 = pri_sum(v, X, sc, (bits >> p) & 1) + C;
                     const bool rz = (raised >> p) & 1;
@@ -686,12 +688,26 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             const int fb = blk / kG, grp = blk - fb * kG;
             const SBlockRef r = slocate(batch, fb);
             const SearchFrameDev &F = batch.f[r.fi];
-            if (F.bitdepth == 8)
-                dist_block<uint8_t, kG, kCoded, kEq14>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf],
-                                                dist_luma, dist_chroma, skipped);
-            else
-                dist_block<uint16_t, kG, kCoded, kEq14>(F, r.fby, r.fbx, fb, grp, sm, sm.raw[buf],
-                                                 dist_luma, dist_chroma, skipped);
+            const bool sub = (allowed_pairs(F, 0) & allowed_pairs(F, 1)) != ~0ull;
+            if (F.bitdepth == 8) {
+                if (sub)
+                    dist_block<uint8_t, kG, kCoded, kEq14, true>(F, r.fby, r.fbx, fb, grp, sm,
+                                                                 sm.raw[buf], dist_luma,
+                                                                 dist_chroma, skipped);
+                else
+                    dist_block<uint8_t, kG, kCoded, kEq14, false>(F, r.fby, r.fbx, fb, grp, sm,
+                                                                  sm.raw[buf], dist_luma,
+                                                                  dist_chroma, skipped);
+            } else {
+                if (sub)
+                    dist_block<uint16_t, kG, kCoded, kEq14, true>(F, r.fby, r.fbx, fb, grp, sm,
+                                                                  sm.raw[buf], dist_luma,
+                                                                  dist_chroma, skipped);
+                else
+                    dist_block<uint16_t, kG, kCoded, kEq14, false>(F, r.fby, r.fbx, fb, grp, sm,
+                                                                   sm.raw[buf], dist_luma,
+                                                                   dist_chroma, skipped);
+            }
             __syncthreads();
         }
     }
