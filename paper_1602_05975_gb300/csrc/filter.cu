@@ -110,31 +110,79 @@ __device__ __forceinline__ uint32_t filter_word(uint32_t X, uint32_t v[12], cons
 }
 
 // ---------------------------------------------------------------------------
-// Scalar path for 12-bit frames.  `px(r, c)` returns the sample at tile
-// position (r, c), or -1 outside the frame.
-template <typename PX>
-__device__ __noinline__ int filter_scalar(PX px, int r, int c, int d, Eff e)
+// 12-bit frames: sums of 12-bit differences leave the 16-bit lanes, so each
+// sample of a word is filtered with 32-bit arithmetic (eq. 7-12 directly).
+// `p` holds the 12 tap values (biased; 0 outside the frame: such a tap adds
+// nothing and is not in the clip range).
+__device__ __forceinline__ int filter_sample_wide(int x, const int p[12], const Eff &e)
 {
-    const int x = px(r, c);
     int sum = 0, mn = x, mx = x;
-    for (int t = 0; t < 12; t++) {
-        int dr, dc;
-        tap_rc(d, t, dr, dc);
-        const int p = px(r + dr, c + dc);
-        if (p < 0) continue;
-        int w, f;
-        if (t < 4) {
-            w = (t >> 1) ? e.w1 : e.w0;
-            f = constrain(p - x, e.pri, e.psh);
-        } else {
-            w = ((t - 4) >> 2) ? 1 : 2;
-            f = constrain(p - x, e.sec, e.ssh);
-        }
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        const int q = p[k] ? p[k] : x;
+        const int f = k < 4 ? constrain(q - x, e.pri, e.psh) : constrain(q - x, e.sec, e.ssh);
+        const int w = k < 2 ? e.w0 : k < 4 ? e.w1 : k < 8 ? 2 : 1;
         sum += w * f;
-        mn = min(mn, p);
-        mx = max(mx, p);
+        mn = min(mn, q);
+        mx = max(mx, q);
     }
     return min(mx, max(mn, x + round16(sum)));
+}
+
+// The 12-bit filter of one block's planes over the re-laid tiles: the
+// warp/lane geometry of the packed path (task 0 luma rows of 8x8 blocks,
+// task 1 chroma (U, V) rows of 4x4 blocks), both samples of a word in turn.
+__device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int fbx,
+                                         const cdef_fb_params &prm, bool any_coded, bool skip_l,
+                                         bool skip_c, FilterSmem &sm)
+{
+    const int sh8 = F.bitdepth - 8;
+    const int H = F.p[0].h, W = F.p[0].w, CH = F.p[1].h, CW = F.p[1].w;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool with_chroma = F.mode == 0;
+#pragma unroll 1
+    for (int task = 0; task < (with_chroma ? 2 : 1); task++) {
+        const bool luma = task == 0;
+        const int bx = lane >> 2, sub = lane & 3;
+        const int blk = warp * 8 + bx;
+        const int gby = fby * 8 + warp, gbx = fbx * 8 + bx;
+        const bool inside = luma ? (gby * 8 < H && gbx * 8 < W) : (gby * 4 < CH && gbx * 4 < CW);
+        if (!inside) continue;
+        const bool cpl = !luma || F.mode == 2;   // chroma parameters
+        const bool on = any_coded && (sm.coded[blk] || (cpl ? skip_c : skip_l));
+        Eff e = cpl ? make_eff(prm.pri_uv, prm.sec_uv, prm.damping, true, 0, sh8)
+                    : make_eff(prm.pri_y, prm.sec_y, prm.damping, false, sm.var[blk], sh8);
+        if (!on) e.pri = e.sec = 0;   // not filtered (section 4): every tap adds 0
+        const int rows = luma ? 8 : 4;
+        const int pitch = luma ? kLumaPitch : kChromaPitch;
+        const uint32_t *base = luma ? sm.t.le + (2 + warp * 8) * kLumaPitch + 4 + bx * 4 + sub
+                                    : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
+        const int *o = sm.off[task][sm.dir[blk]];
+        const int oy = luma ? fby * 64 + warp * 8 : fby * 32 + warp * 4;
+        const int ox = luma ? fbx * 64 + bx * 8 + 2 * sub : fbx * 32 + bx * 4 + sub;
+        for (int i = 0; i < rows; i++) {
+            const uint32_t *b = base + i * pitch;
+            const uint32_t X = b[0];
+            uint32_t v[12];
+#pragma unroll
+            for (int k = 0; k < 12; k++) v[k] = b[o[k]];
+            int y[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                int p[12];
+#pragma unroll
+                for (int k = 0; k < 12; k++) p[k] = (int)((v[k] >> (16 * h)) & 0xffffu);
+                y[h] = filter_sample_wide((int)((X >> (16 * h)) & 0xffffu), p, e) - (int)kBias;
+            }
+            if (luma) {
+                uint16_t *row = reinterpret_cast<uint16_t *>(F.p[0].out + (int64_t)(oy + i) * F.p[0].out_pitch);
+                *reinterpret_cast<uint32_t *>(row + ox) = (uint32_t)y[0] | ((uint32_t)y[1] << 16);
+            } else {
+                reinterpret_cast<uint16_t *>(F.p[1].out + (int64_t)(oy + i) * F.p[1].out_pitch)[ox] = (uint16_t)y[0];
+                reinterpret_cast<uint16_t *>(F.p[2].out + (int64_t)(oy + i) * F.p[2].out_pitch)[ox] = (uint16_t)y[1];
+            }
+        }
+    }
 }
 
 // Everything after the tiles have landed: re-layout, direction search,
@@ -232,33 +280,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
 
     const int warp = tid >> 5, lane = tid & 31;
     if (F.bitdepth > 10) {
-        // 12-bit: scalar path over every sample
-        for (int i = tid; i < (with_chroma ? 64 * 64 + 2 * 32 * 32 : 64 * 64); i += kThreads) {
-            const int pl = i < 4096 ? 0 : (i < 5120 ? 1 : 2);
-            const int j = pl == 0 ? i : (i - 4096 - (pl - 1) * 1024);
-            const int w = pl ? 32 : 64, rr = j / w, cc = j - rr * w;
-            const int gy = (pl ? cy0 : ly0) + rr, gx = (pl ? cx0 : lx0) + cc;
-            if (gy >= F.p[pl].h || gx >= F.p[pl].w) continue;
-            const int blk = pl ? (rr >> 2) * 8 + (cc >> 2) : (rr >> 3) * 8 + (cc >> 3);
-            const bool cpl = pl || F.mode == 2;   // chroma parameters
-            const Eff e = cpl ? make_eff(prm.pri_uv, prm.sec_uv, prm.damping, true, 0, sh8)
-                              : make_eff(prm.pri_y, prm.sec_y, prm.damping, false, sm.var[blk], sh8);
-            auto px = [&](int r2, int c2) -> int {
-                uint32_t w2;
-                if (pl == 0) {
-                    w2 = sm.t.le[r2 * kLumaPitch + (c2 >> 1)];
-                    w2 = (c2 & 1) ? (w2 >> 16) : (w2 & 0xffff);
-                } else {
-                    w2 = sm.t.cw[r2 * kChromaPitch + c2];
-                    w2 = pl == 2 ? (w2 >> 16) : (w2 & 0xffff);
-                }
-                return w2 ? (int)(w2 - kBias) : -1;
-            };
-            const int r = 2 + rr, c = pl ? 2 + cc : 8 + cc;
-            const bool on = any_coded && (sm.coded[blk] || (cpl ? skip_c : skip_l));
-            reinterpret_cast<T *>(F.p[pl].out + (int64_t)gy * F.p[pl].out_pitch)[gx] =
-                (T)(on ? filter_scalar(px, r, c, sm.dir[blk], e) : px(r, c));
-        }
+        filter_wide(F, fby, fbx, prm, any_coded, skip_l, skip_c, sm);
         return;
     }
 
