@@ -75,7 +75,8 @@ static_assert(sizeof(SearchBatch) <= 32764, "a search batch must fit the kernel 
 // read as every pair.
 __host__ __device__ inline unsigned long long allowed_pairs(const SearchFrameDev &F, int g)
 {
-    return F.pairs[g] ? F.pairs[g] : ~0ull;
+    const unsigned long long v = g ? F.pairs[1] : F.pairs[0];   // no indexed parameter access
+    return v ? v : ~0ull;
 }
 
 // Per-frame result of the preset search (device).

@@ -233,7 +233,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
 {
     constexpr int kPP = 16 / kG;           // primary strengths per unit
     constexpr int kN = 4 * kPP;            // candidates per plane group
-    const int p0 = kG == 1 ? 0 : grp * kPP;
+    const int p0_unit = kG == 1 ? 0 : grp * kPP;
     const int sh8 = F.bitdepth - 8;
     const int W = F.w, H = F.h, CW = F.w >> 1, CH = F.h >> 1;
     const int ly0 = fby * 64, lx0 = fbx * 64, cy0 = fby * 32, cx0 = fbx * 32;
@@ -323,298 +323,307 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
 
     // ---- both plane groups through one code path: task 0 luma, task 1 chroma
     const int bw = W >> 3;
+    // eq. 14: the unit is the whole block and its candidate groups are
+    // evaluated in turn on the same staged tiles, directions and tables
 #pragma unroll 1
-    for (int task = 0; task < 2; task++) {
-        const bool luma = task == 0;
-        const int bx = lane >> 2, sub = lane & 3;
-        const int blk = warp * 8 + bx;
-        const int gby = fby * 8 + warp, gbx = fbx * 8 + bx;
-        const bool inside = luma ? (gby * 8 < H && gbx * 8 < W) : (gby * 4 < CH && gbx * 4 < CW);
-        const bool edge = gby == 0 || gbx == 0 || gby == (H >> 3) - 1 || gbx == bw - 1;
-        const bool any_edge = __any_sync(0xffffffffu, inside && edge);
-        const int rows = luma ? 8 : 4;
-        const int pitch = luma ? kLumaPitch : kChromaPitch;
-        const uint32_t *base = luma ? sm.t.le + (2 + warp * 8) * kLumaPitch + 4 + bx * 4 + sub
-                                    : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
-        const int4 *op = reinterpret_cast<const int4 *>(sm.off[task][sm.dir[blk]]);
-        const int4 o0 = op[0], o1 = op[1], o2 = op[2];
-        const int o[12] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w};
-        const SetC *ps = luma ? sm.pset[blk] : sm.cset;
-        const uint32_t bits = luma ? sm.pbits[blk] : sm.cbits;
-        const uint32_t raised = luma ? 0u : sm.craised;
-        const SetC *ss = luma ? sm.sset[0] : sm.sset[1];
-        SetC s7 = {};
-        if (kCoded) s7 = luma ? sm.s7[blk] : sm.s7c;
-        const int oy = luma ? ly0 + warp * 8 : cy0 + warp * 4;
-        const int ox = luma ? lx0 + bx * 8 + 2 * sub : cx0 + bx * 4 + sub;
-        const uint8_t *sa = luma ? F.src[0] : F.src[1];
-        const int64_t spa = luma ? F.src_pitch[0] : F.src_pitch[1];
+    for (int g = 0; g < (kEq14 ? kG : 1); g++) {
+        const int p0 = kEq14 ? g * kPP : p0_unit;
+    #pragma unroll 1
+        for (int task = 0; task < 2; task++) {
+            const bool luma = task == 0;
+            const int bx = lane >> 2, sub = lane & 3;
+            const int blk = warp * 8 + bx;
+            const int gby = fby * 8 + warp, gbx = fbx * 8 + bx;
+            const bool inside = luma ? (gby * 8 < H && gbx * 8 < W) : (gby * 4 < CH && gbx * 4 < CW);
+            const bool edge = gby == 0 || gbx == 0 || gby == (H >> 3) - 1 || gbx == bw - 1;
+            const bool any_edge = __any_sync(0xffffffffu, inside && edge);
+            const int rows = luma ? 8 : 4;
+            const int pitch = luma ? kLumaPitch : kChromaPitch;
+            const uint32_t *base = luma ? sm.t.le + (2 + warp * 8) * kLumaPitch + 4 + bx * 4 + sub
+                                        : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
+            const int4 *op = reinterpret_cast<const int4 *>(sm.off[task][sm.dir[blk]]);
+            const int4 o0 = op[0], o1 = op[1], o2 = op[2];
+            const int o[12] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w};
+            const SetC *ps = luma ? sm.pset[blk] : sm.cset;
+            const uint32_t bits = luma ? sm.pbits[blk] : sm.cbits;
+            const uint32_t raised = luma ? 0u : sm.craised;
+            const SetC *ss = luma ? sm.sset[0] : sm.sset[1];
+            SetC s7 = {};
+            if (kCoded) s7 = luma ? sm.s7[blk] : sm.s7c;
+            const int oy = luma ? ly0 + warp * 8 : cy0 + warp * 4;
+            const int ox = luma ? lx0 + bx * 8 + 2 * sub : cx0 + bx * 4 + sub;
+            const uint8_t *sa = luma ? F.src[0] : F.src[1];
+            const int64_t spa = luma ? F.src_pitch[0] : F.src_pitch[1];
 
-        // section 5's low-complexity search: primaries with no allowed pair
-        // are not evaluated, entries of pairs outside the subset are 0
-        const unsigned long long pairs = allowed_pairs(F, task);
-        uint32_t pmask = 0;
-#pragma unroll
-        for (int p = 0; p < 16; p++) pmask |= (uint32_t)(((pairs >> (4 * p)) & 15ull) != 0) << p;
+            // section 5's low-complexity search: primaries with no allowed pair
+            // are not evaluated, entries of pairs outside the subset are 0
+            uint32_t pmask = 0xffffu;
+            if (kSub) {
+                const unsigned long long pairs = allowed_pairs(F, task);
+                pmask = 0;
+    #pragma unroll
+                for (int p = 0; p < 16; p++) pmask |= (uint32_t)(((pairs >> (4 * p)) & 15ull) != 0) << p;
+            }
 
-        uint32_t acc[kEq14 ? 1 : kN], sse0 = 0;
-#pragma unroll
-        for (int q = 0; q < (kEq14 ? 1 : kN); q++) acc[q] = 0;
-        // eq. 14: per candidate and sample lane the sums of r, r (2x + r),
-        // r (2 (x - s) + r); then per lane x, x^2, s, s^2, (x - s)^2
-        constexpr int kE = kEq14 ? kN : 1;
-        int e6[kE][6], e0[10];
-#pragma unroll
-        for (int q = 0; q < kE; q++)
-#pragma unroll
-            for (int j = 0; j < 6; j++) e6[q][j] = 0;
-#pragma unroll
-        for (int j = 0; j < 10; j++) e0[j] = 0;
-        if (inside) {
-#pragma unroll 1
-            for (int i = 0; i < rows; i++) {
-                const uint32_t *b = base + i * pitch;
-                const uint32_t X = b[0];
-                uint32_t v[12];
-#pragma unroll
-                for (int k = 0; k < 12; k++) v[k] = b[o[k]];
-                if (any_edge) {
-#pragma unroll
-                    for (int k = 0; k < 12; k++) v[k] = in_frame(v[k], X);
-                }
-                uint32_t mn = X, mx = X;
-#pragma unroll
-                for (int k = 0; k < 12; k += 2) {
-                    mn = __vimin3_u16x2(mn, v[k], v[k + 1]);
-                    mx = __vimax3_u16x2(mx, v[k], v[k + 1]);
-                }
-                const uint32_t S = luma ? load_src_pair<T>(sa + (int64_t)(oy + i) * spa, ox)
-                                        : load_src_uv<T>(sa + (int64_t)(oy + i) * spa,
-                                                         F.src[2] + (int64_t)(oy + i) * F.src_pitch[2], ox);
-                // Squared error of one candidate, with e = y - s = (x - s) + r:
-                // e^2 = (x - s)^2 + r (2 (x - s) + r).  The first term does not
-                // depend on the candidate and is summed once per pixel; the
-                // second is formed from the candidate's correction r, which
-                // at 8 and 10 bits stays within a signed byte (|r| <= 57).
-                sse0 = add_sq<T>(sse0, X, S);
-                const uint32_t two_xs = sadd16(2u * (X + 4096u * kLanes - S), 0xdf00u * kLanes);
-                uint32_t two_x = 0;
-                if (kEq14) {
-                    const int xl = (int)(X & 0xffffu) - (int)kBias, xh = (int)(X >> 16) - (int)kBias;
-                    const int sl = (int)(S & 0xffffu) - (int)kBias, sh = (int)(S >> 16) - (int)kBias;
-                    e0[0] += xl; e0[1] += xh;
-                    e0[2] += xl * xl; e0[3] += xh * xh;
-                    e0[4] += sl; e0[5] += sh;
-                    e0[6] += sl * sl; e0[7] += sh * sh;
-                    e0[8] += (xl - sl) * (xl - sl); e0[9] += (xh - sh) * (xh - sh);
-                    two_x = sadd16(X + X, 0xfe00u * kLanes);   // 2x - 256 per lane
-                }
-                const uint32_t rlo = __vmaxu2(mn - X + 2048u * kLanes, 1792u * kLanes) - 1792u * kLanes;
-                const uint32_t rhi = mx - X + 256u * kLanes;
-                uint32_t Q[4], Qr[4];
-                Q[0] = Qr[0] = 12u * X;
-#pragma unroll
-                for (int s = 1; s < 4; s++) Q[s] = sec_sum(v, X, ss[s]);
-                if (raised) {
-#pragma unroll
-                    for (int s = 1; s < 4; s++) Qr[s] = sec_sum(v, X, sm.sset[2][s]);
-                } else {
-#pragma unroll
-                    for (int s = 1; s < 4; s++) Qr[s] = Q[s];
-                }
-                const uint32_t C = 4096u * kLanes - 24u * X;
-#pragma unroll
-                for (int pp = 0; pp < kPP; pp++) {
-                    const int p = p0 + pp;
-                    if (kSub && !((pmask >> p) & 1)) continue;
-                    const SetC sc = ps[p];
-                    const uint32_t T0 = pri_sum(v, X, sc, (bits >> p) & 1) + C;
-                    const bool rz = (raised >> p) & 1;
-                    const bool slot19 = kCoded && p == 0;   // (0, 0) slot: the (19, 7) preset
-                    uint32_t u19 = 0;
-                    if (slot19)
-                        u19 = pri_sum(v, X, ps[16], (bits >> 16) & 1) + C + sec_sum(v, X, s7);
-#pragma unroll
-                    for (int s = 0; s < 4; s++) {
-                        // eq. 8 rounding of (P + Q - 24x) / 16, ties away from zero
-                        const uint32_t u = (slot19 && s == 0) ? u19 : T0 + (rz ? Qr[s] : Q[s]);
-                        const uint32_t pos = (u >> 12) & kLanes;
-                        const uint32_t w = u + pos + 7u * kLanes;
-                        uint32_t rb = (w >> 4) & (0x0fffu * kLanes);   // r + 256 per lane
-                        // eq. 9-12 on r: x + r is held in [min, max].  Where the
-                        // adjusted primary strength is 0 only the secondary set
-                        // contributes, its weights sum to 12/16 < 1, and the
-                        // clip cannot bind: it is applied without a test.
-                        if (s > 0 || slot19) rb = __vminu2(__vmaxu2(rb, rlo), rhi);
-                        const uint32_t a = sadd16(rb, two_xs);           // 2 (x - s) + r
-                        const uint32_t r8 = __byte_perm(rb, 0, 0x0020);  // r of both lanes, bytes 0, 1
-                        if (kEq14) {
-                            const int c = pp * 4 + s;
-                            const int rl = (int)(r8 & 0xffu), rh = (int)(r8 & 0xff00u);
-                            const int ax = (int)sadd16(rb, two_x);       // 2x + r
-                            e6[c][0] = __dp2a_lo((int)kLanes, rl, e6[c][0]);
-                            e6[c][1] = __dp2a_lo((int)kLanes, rh, e6[c][1]);
-                            e6[c][2] = __dp2a_lo(ax, rl, e6[c][2]);
-                            e6[c][3] = __dp2a_lo(ax, rh, e6[c][3]);
-                            e6[c][4] = __dp2a_lo((int)a, rl, e6[c][4]);
-                            e6[c][5] = __dp2a_lo((int)a, rh, e6[c][5]);
-                        } else {
-                            acc[pp * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)r8, (int)acc[pp * 4 + s]);
+            uint32_t acc[kEq14 ? 1 : kN], sse0 = 0;
+    #pragma unroll
+            for (int q = 0; q < (kEq14 ? 1 : kN); q++) acc[q] = 0;
+            // eq. 14: per candidate and sample lane the sums of r, r (2x + r),
+            // r (2 (x - s) + r); then per lane x, x^2, s, s^2, (x - s)^2
+            constexpr int kE = kEq14 ? kN : 1;
+            int e6[kE][6], e0[10];
+    #pragma unroll
+            for (int q = 0; q < kE; q++)
+    #pragma unroll
+                for (int j = 0; j < 6; j++) e6[q][j] = 0;
+    #pragma unroll
+            for (int j = 0; j < 10; j++) e0[j] = 0;
+            if (inside) {
+    #pragma unroll 1
+                for (int i = 0; i < rows; i++) {
+                    const uint32_t *b = base + i * pitch;
+                    const uint32_t X = b[0];
+                    uint32_t v[12];
+    #pragma unroll
+                    for (int k = 0; k < 12; k++) v[k] = b[o[k]];
+                    if (any_edge) {
+    #pragma unroll
+                        for (int k = 0; k < 12; k++) v[k] = in_frame(v[k], X);
+                    }
+                    uint32_t mn = X, mx = X;
+    #pragma unroll
+                    for (int k = 0; k < 12; k += 2) {
+                        mn = __vimin3_u16x2(mn, v[k], v[k + 1]);
+                        mx = __vimax3_u16x2(mx, v[k], v[k + 1]);
+                    }
+                    const uint32_t S = luma ? load_src_pair<T>(sa + (int64_t)(oy + i) * spa, ox)
+                                            : load_src_uv<T>(sa + (int64_t)(oy + i) * spa,
+                                                             F.src[2] + (int64_t)(oy + i) * F.src_pitch[2], ox);
+                    // Squared error of one candidate, with e = y - s = (x - s) + r:
+                    // e^2 = (x - s)^2 + r (2 (x - s) + r).  The first term does not
+                    // depend on the candidate and is summed once per pixel; the
+                    // second is formed from the candidate's correction r, which
+                    // at 8 and 10 bits stays within a signed byte (|r| <= 57).
+                    sse0 = add_sq<T>(sse0, X, S);
+                    const uint32_t two_xs = sadd16(2u * (X + 4096u * kLanes - S), 0xdf00u * kLanes);
+                    uint32_t two_x = 0;
+                    if (kEq14) {
+                        const int xl = (int)(X & 0xffffu) - (int)kBias, xh = (int)(X >> 16) - (int)kBias;
+                        const int sl = (int)(S & 0xffffu) - (int)kBias, sh = (int)(S >> 16) - (int)kBias;
+                        e0[0] += xl; e0[1] += xh;
+                        e0[2] += xl * xl; e0[3] += xh * xh;
+                        e0[4] += sl; e0[5] += sh;
+                        e0[6] += sl * sl; e0[7] += sh * sh;
+                        e0[8] += (xl - sl) * (xl - sl); e0[9] += (xh - sh) * (xh - sh);
+                        two_x = sadd16(X + X, 0xfe00u * kLanes);   // 2x - 256 per lane
+                    }
+                    const uint32_t rlo = __vmaxu2(mn - X + 2048u * kLanes, 1792u * kLanes) - 1792u * kLanes;
+                    const uint32_t rhi = mx - X + 256u * kLanes;
+                    uint32_t Q[4], Qr[4];
+                    Q[0] = Qr[0] = 12u * X;
+    #pragma unroll
+                    for (int s = 1; s < 4; s++) Q[s] = sec_sum(v, X, ss[s]);
+                    if (raised) {
+    #pragma unroll
+                        for (int s = 1; s < 4; s++) Qr[s] = sec_sum(v, X, sm.sset[2][s]);
+                    } else {
+    #pragma unroll
+                        for (int s = 1; s < 4; s++) Qr[s] = Q[s];
+                    }
+                    const uint32_t C = 4096u * kLanes - 24u * X;
+    #pragma unroll
+                    for (int pp = 0; pp < kPP; pp++) {
+                        const int p = p0 + pp;
+                        if (kSub && !((pmask >> p) & 1)) continue;
+                        const SetC sc = ps[p];
+                        const uint32_t T0 = pri_sum(v, X, sc, (bits >> p) & 1) + C;
+                        const bool rz = (raised >> p) & 1;
+                        const bool slot19 = kCoded && p == 0;   // (0, 0) slot: the (19, 7) preset
+                        uint32_t u19 = 0;
+                        if (slot19)
+                            u19 = pri_sum(v, X, ps[16], (bits >> 16) & 1) + C + sec_sum(v, X, s7);
+    #pragma unroll
+                        for (int s = 0; s < 4; s++) {
+                            // eq. 8 rounding of (P + Q - 24x) / 16, ties away from zero
+                            const uint32_t u = (slot19 && s == 0) ? u19 : T0 + (rz ? Qr[s] : Q[s]);
+                            const uint32_t pos = (u >> 12) & kLanes;
+                            const uint32_t w = u + pos + 7u * kLanes;
+                            uint32_t rb = (w >> 4) & (0x0fffu * kLanes);   // r + 256 per lane
+                            // eq. 9-12 on r: x + r is held in [min, max].  Where the
+                            // adjusted primary strength is 0 only the secondary set
+                            // contributes, its weights sum to 12/16 < 1, and the
+                            // clip cannot bind: it is applied without a test.
+                            if (s > 0 || slot19) rb = __vminu2(__vmaxu2(rb, rlo), rhi);
+                            const uint32_t a = sadd16(rb, two_xs);           // 2 (x - s) + r
+                            const uint32_t r8 = __byte_perm(rb, 0, 0x0020);  // r of both lanes, bytes 0, 1
+                            if (kEq14) {
+                                const int c = pp * 4 + s;
+                                const int rl = (int)(r8 & 0xffu), rh = (int)(r8 & 0xff00u);
+                                const int ax = (int)sadd16(rb, two_x);       // 2x + r
+                                e6[c][0] = __dp2a_lo((int)kLanes, rl, e6[c][0]);
+                                e6[c][1] = __dp2a_lo((int)kLanes, rh, e6[c][1]);
+                                e6[c][2] = __dp2a_lo(ax, rl, e6[c][2]);
+                                e6[c][3] = __dp2a_lo(ax, rh, e6[c][3]);
+                                e6[c][4] = __dp2a_lo((int)a, rl, e6[c][4]);
+                                e6[c][5] = __dp2a_lo((int)a, rh, e6[c][5]);
+                            } else {
+                                acc[pp * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)r8, (int)acc[pp * 4 + s]);
+                            }
                         }
                     }
                 }
             }
+            if constexpr (kEq14) {
+                if (luma) {
+                    // the two samples of a word are neighbours in one 8x8 block:
+                    // add the lanes, then the four lanes of the block
+                    int n = inside ? 16 : 0, sx = e0[0] + e0[1], sx2 = e0[2] + e0[3];
+                    int ssum = e0[4] + e0[5], ss2 = e0[6] + e0[7], sxs = e0[8] + e0[9];
+                    int A[kN], BX[kN], BS[kN];
+    #pragma unroll
+                    for (int c = 0; c < kN; c++) {
+                        A[c] = e6[c][0] + e6[c][1];
+                        BX[c] = e6[c][2] + e6[c][3];
+                        BS[c] = e6[c][4] + e6[c][5];
+                    }
+    #pragma unroll
+                    for (int o = 1; o <= 2; o <<= 1) {
+                        n += __shfl_xor_sync(0xffffffffu, n, o);
+                        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                        sx2 += __shfl_xor_sync(0xffffffffu, sx2, o);
+                        ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+                        ss2 += __shfl_xor_sync(0xffffffffu, ss2, o);
+                        sxs += __shfl_xor_sync(0xffffffffu, sxs, o);
+    #pragma unroll
+                        for (int c = 0; c < kN; c++) {
+                            A[c] += __shfl_xor_sync(0xffffffffu, A[c], o);
+                            BX[c] += __shfl_xor_sync(0xffffffffu, BX[c], o);
+                            BS[c] += __shfl_xor_sync(0xffffffffu, BS[c], o);
+                        }
+                    }
+                    // each of the block's four lanes evaluates a quarter of the
+                    // candidates
+    #pragma unroll
+                    for (int c = 0; c < kN; c++) {
+                        if (n > 0 && (c * 4) / kN == sub) {
+                            const long long t = eq14_value(n, ssum, ss2, sx + A[c], (long long)sx2 + BX[c],
+                                                           (long long)sxs + BS[c], F.bitdepth);
+                            atomicAdd(&sm.acc[c], (unsigned long long)t);
+                        }
+                    }
+                } else {
+                    // (U, V) lanes: per plane, the 4-row half of a chroma 8x8
+                    // block is eight lanes (two 4x4 blocks) of this warp; the
+                    // other half is the next warp's
+                    const int cb = (warp >> 1) * 4 + (bx >> 1), half = warp & 1;
+    #pragma unroll
+                    for (int k = 0; k < 2; k++) {
+                        int vals[30];
+    #pragma unroll
+                        for (int c = 0; c < kN; c++) {
+                            vals[3 * c] = e6[c][k];
+                            vals[3 * c + 1] = e6[c][2 + k];
+                            vals[3 * c + 2] = e6[c][4 + k];
+                        }
+                        vals[24] = inside ? 4 : 0;
+                        vals[25] = e0[k];
+                        vals[26] = e0[2 + k];
+                        vals[27] = e0[4 + k];
+                        vals[28] = e0[6 + k];
+                        vals[29] = e0[8 + k];
+    #pragma unroll
+                        for (int o = 1; o <= 4; o <<= 1)
+    #pragma unroll
+                            for (int j = 0; j < 30; j++) vals[j] += __shfl_xor_sync(0xffffffffu, vals[j], o);
+                        if ((lane & 7) == 0)
+    #pragma unroll
+                            for (int j = 0; j < 30; j++) sm.e14h[k][cb][half][j] = vals[j];
+                    }
+                }
+                __syncthreads();
+            } else {
+                // the warp totals of r (2 (x - s) + r) are signed and fit 32 bits
+                if (!kCoded) {
+                    butterfly<kN>(acc, lane);
+                    if (kN == 64) {
+                        atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
+                        atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
+                    } else if (kN == 32) {
+                        atomicAdd(&sm.acc[lane], (unsigned long long)(long long)(int)acc[0]);
+                    } else if (!(lane & 1)) {
+                        atomicAdd(&sm.acc[lane >> 1], (unsigned long long)(long long)(int)acc[0]);
+                    }
+                } else {
+                    // the four lanes of one 8x8 block first, then the uncoded blocks'
+                    // part is split off and both are summed across the warp
+                    wreduce<kN, 0, 2>(acc, lane);
+                    constexpr int kQ = kN / 4;
+                    uint32_t un[kQ];
+                    const bool unc = !sm.coded[blk];
+        #pragma unroll
+                    for (int i = 0; i < kQ; i++) un[i] = unc ? acc[i] : 0u;
+                    wreduce<kN, 2, 5>(acc, lane);
+                    wreduce<kN, 2, 5>(un, lane);
+                    const int e = wentry(kN, lane);
+                    if (kN >= 32 || !(lane & 16)) {
+        #pragma unroll
+                        for (int j = 0; j < (kN >= 64 ? 2 : 1); j++) {
+                            atomicAdd(&sm.acc[e + j], (unsigned long long)(long long)(int)acc[j]);
+                            atomicAdd(&sm.accu[e + j], (unsigned long long)(long long)(int)un[j]);
+                        }
+                    }
+                }
+        #pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) sse0 += __shfl_xor_sync(0xffffffffu, sse0, o);
+                if (lane == 0) atomicAdd(&sm.base[task], (unsigned long long)sse0);
+                __syncthreads();
+                if (tid < kN) {
+                    const long long base_sse = (long long)sm.base[task];
+                    const bool on = (allowed_pairs(F, task) >> (4 * p0 + tid)) & 1;
+                    if (!kCoded) {
+                        long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
+                        out[tid] = on ? (long long)sm.acc[tid] + base_sse : 0;
+                    } else {
+                        // q = k * 64 + p * 4 + s; skip bit clear: blocks without coded
+                        // residual unfiltered, (0, 0) the unfiltered error
+                        long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 128 +
+                                         4 * p0 + tid;
+                        const long long tot = (long long)sm.acc[tid], un = (long long)sm.accu[tid];
+                        out[0] = !on ? 0 : (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un;
+                        out[64] = !on ? 0 : !any_coded ? base_sse : base_sse + tot;
+                    }
+                    sm.acc[tid] = 0;
+                    sm.accu[tid] = 0;
+                }
+                __syncthreads();
+            }
         }
         if constexpr (kEq14) {
-            if (luma) {
-                // the two samples of a word are neighbours in one 8x8 block:
-                // add the lanes, then the four lanes of the block
-                int n = inside ? 16 : 0, sx = e0[0] + e0[1], sx2 = e0[2] + e0[3];
-                int ssum = e0[4] + e0[5], ss2 = e0[6] + e0[7], sxs = e0[8] + e0[9];
-                int A[kN], BX[kN], BS[kN];
-#pragma unroll
-                for (int c = 0; c < kN; c++) {
-                    A[c] = e6[c][0] + e6[c][1];
-                    BX[c] = e6[c][2] + e6[c][3];
-                    BS[c] = e6[c][4] + e6[c][5];
-                }
-#pragma unroll
-                for (int o = 1; o <= 2; o <<= 1) {
-                    n += __shfl_xor_sync(0xffffffffu, n, o);
-                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                    sx2 += __shfl_xor_sync(0xffffffffu, sx2, o);
-                    ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
-                    ss2 += __shfl_xor_sync(0xffffffffu, ss2, o);
-                    sxs += __shfl_xor_sync(0xffffffffu, sxs, o);
-#pragma unroll
-                    for (int c = 0; c < kN; c++) {
-                        A[c] += __shfl_xor_sync(0xffffffffu, A[c], o);
-                        BX[c] += __shfl_xor_sync(0xffffffffu, BX[c], o);
-                        BS[c] += __shfl_xor_sync(0xffffffffu, BS[c], o);
-                    }
-                }
-                // each of the block's four lanes evaluates a quarter of the
-                // candidates
-#pragma unroll
-                for (int c = 0; c < kN; c++) {
-                    if (n > 0 && (c * 4) / kN == sub) {
-                        const long long t = eq14_value(n, ssum, ss2, sx + A[c], (long long)sx2 + BX[c],
-                                                       (long long)sxs + BS[c], F.bitdepth);
-                        atomicAdd(&sm.acc[c], (unsigned long long)t);
-                    }
-                }
-            } else {
-                // (U, V) lanes: per plane, the 4-row half of a chroma 8x8
-                // block is eight lanes (two 4x4 blocks) of this warp; the
-                // other half is the next warp's
-                const int cb = (warp >> 1) * 4 + (bx >> 1), half = warp & 1;
-#pragma unroll
-                for (int k = 0; k < 2; k++) {
-                    int vals[30];
-#pragma unroll
-                    for (int c = 0; c < kN; c++) {
-                        vals[3 * c] = e6[c][k];
-                        vals[3 * c + 1] = e6[c][2 + k];
-                        vals[3 * c + 2] = e6[c][4 + k];
-                    }
-                    vals[24] = inside ? 4 : 0;
-                    vals[25] = e0[k];
-                    vals[26] = e0[2 + k];
-                    vals[27] = e0[4 + k];
-                    vals[28] = e0[6 + k];
-                    vals[29] = e0[8 + k];
-#pragma unroll
-                    for (int o = 1; o <= 4; o <<= 1)
-#pragma unroll
-                        for (int j = 0; j < 30; j++) vals[j] += __shfl_xor_sync(0xffffffffu, vals[j], o);
-                    if ((lane & 7) == 0)
-#pragma unroll
-                        for (int j = 0; j < 30; j++) sm.e14h[k][cb][half][j] = vals[j];
+            // chroma 8x8 blocks: two planes x 16 blocks x the unit's candidates
+            for (int i = tid; i < 2 * 16 * kN; i += kThreads) {
+                const int k = i / (16 * kN), cb = (i / kN) % 16, c = i % kN;
+                const int *h0 = sm.e14h[k][cb][0], *h1 = sm.e14h[k][cb][1];
+                const int n = h0[24] + h1[24];
+                if (n > 0) {
+                    const long long sx = h0[25] + h1[25], sx2 = h0[26] + h1[26];
+                    const long long ssum = h0[27] + h1[27], ss2 = h0[28] + h1[28], sxs = h0[29] + h1[29];
+                    const long long t = eq14_value(n, ssum, ss2, sx + h0[3 * c] + h1[3 * c],
+                                                   sx2 + h0[3 * c + 1] + h1[3 * c + 1],
+                                                   sxs + h0[3 * c + 2] + h1[3 * c + 2], F.bitdepth);
+                    atomicAdd(&sm.acc14c[c], (unsigned long long)t);
                 }
             }
-            __syncthreads();
-        } else {
-            // the warp totals of r (2 (x - s) + r) are signed and fit 32 bits
-            if (!kCoded) {
-                butterfly<kN>(acc, lane);
-                if (kN == 64) {
-                    atomicAdd(&sm.acc[2 * lane], (unsigned long long)(long long)(int)acc[0]);
-                    atomicAdd(&sm.acc[2 * lane + 1], (unsigned long long)(long long)(int)acc[1]);
-                } else if (kN == 32) {
-                    atomicAdd(&sm.acc[lane], (unsigned long long)(long long)(int)acc[0]);
-                } else if (!(lane & 1)) {
-                    atomicAdd(&sm.acc[lane >> 1], (unsigned long long)(long long)(int)acc[0]);
-                }
-            } else {
-                // the four lanes of one 8x8 block first, then the uncoded blocks'
-                // part is split off and both are summed across the warp
-                wreduce<kN, 0, 2>(acc, lane);
-                constexpr int kQ = kN / 4;
-                uint32_t un[kQ];
-                const bool unc = !sm.coded[blk];
-    #pragma unroll
-                for (int i = 0; i < kQ; i++) un[i] = unc ? acc[i] : 0u;
-                wreduce<kN, 2, 5>(acc, lane);
-                wreduce<kN, 2, 5>(un, lane);
-                const int e = wentry(kN, lane);
-                if (kN >= 32 || !(lane & 16)) {
-    #pragma unroll
-                    for (int j = 0; j < (kN >= 64 ? 2 : 1); j++) {
-                        atomicAdd(&sm.acc[e + j], (unsigned long long)(long long)(int)acc[j]);
-                        atomicAdd(&sm.accu[e + j], (unsigned long long)(long long)(int)un[j]);
-                    }
-                }
-            }
-    #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) sse0 += __shfl_xor_sync(0xffffffffu, sse0, o);
-            if (lane == 0) atomicAdd(&sm.base[task], (unsigned long long)sse0);
             __syncthreads();
             if (tid < kN) {
-                const long long base_sse = (long long)sm.base[task];
-                const bool on = (pairs >> (4 * p0 + tid)) & 1;
-                if (!kCoded) {
-                    long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
-                    out[tid] = on ? (long long)sm.acc[tid] + base_sse : 0;
-                } else {
-                    // q = k * 64 + p * 4 + s; skip bit clear: blocks without coded
-                    // residual unfiltered, (0, 0) the unfiltered error
-                    long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 128 +
-                                     4 * p0 + tid;
-                    const long long tot = (long long)sm.acc[tid], un = (long long)sm.accu[tid];
-                    out[0] = !on ? 0 : (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un;
-                    out[64] = !on ? 0 : !any_coded ? base_sse : base_sse + tot;
-                }
+                const int q = 4 * p0 + tid;
+                const bool on_l = (allowed_pairs(F, 0) >> q) & 1, on_c = (allowed_pairs(F, 1) >> q) & 1;
+                dist_luma[(int64_t)blk_global * 64 + q] = on_l ? (long long)sm.acc[tid] : 0;
+                dist_chroma[(int64_t)blk_global * 64 + q] = on_c ? (long long)sm.acc14c[tid] : 0;
                 sm.acc[tid] = 0;
-                sm.accu[tid] = 0;
+                sm.acc14c[tid] = 0;
             }
             __syncthreads();
         }
-    }
-    if constexpr (kEq14) {
-        // chroma 8x8 blocks: two planes x 16 blocks x the unit's candidates
-        for (int i = tid; i < 2 * 16 * kN; i += kThreads) {
-            const int k = i / (16 * kN), cb = (i / kN) % 16, c = i % kN;
-            const int *h0 = sm.e14h[k][cb][0], *h1 = sm.e14h[k][cb][1];
-            const int n = h0[24] + h1[24];
-            if (n > 0) {
-                const long long sx = h0[25] + h1[25], sx2 = h0[26] + h1[26];
-                const long long ssum = h0[27] + h1[27], ss2 = h0[28] + h1[28], sxs = h0[29] + h1[29];
-                const long long t = eq14_value(n, ssum, ss2, sx + h0[3 * c] + h1[3 * c],
-                                               sx2 + h0[3 * c + 1] + h1[3 * c + 1],
-                                               sxs + h0[3 * c + 2] + h1[3 * c + 2], F.bitdepth);
-                atomicAdd(&sm.acc14c[c], (unsigned long long)t);
-            }
-        }
-        __syncthreads();
-        if (tid < kN) {
-            const int q = 4 * p0 + tid;
-            const bool on_l = (allowed_pairs(F, 0) >> q) & 1, on_c = (allowed_pairs(F, 1) >> q) & 1;
-            dist_luma[(int64_t)blk_global * 64 + q] = on_l ? (long long)sm.acc[tid] : 0;
-            dist_chroma[(int64_t)blk_global * 64 + q] = on_c ? (long long)sm.acc14c[tid] : 0;
-            sm.acc[tid] = 0;
-            sm.acc14c[tid] = 0;
-        }
-        __syncthreads();
     }
 }
 
@@ -640,7 +649,7 @@ __device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTil
 
 // Persistent distortion kernel (same work-counter scheme as the filter).
 // Work unit u is filter block u / kG, primary-strength group u % kG.
-template <int kG, bool kCoded, bool kEq14>
+template <int kG, bool kCoded, bool kEq14, bool kSub>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
 dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, long long *dist_chroma,
             uint8_t *skipped, int *status, unsigned *work)
@@ -648,7 +657,8 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
     extern __shared__ __align__(128) uint8_t smem_bytes[];
     SearchSmem &sm = *reinterpret_cast<SearchSmem *>(smem_bytes);
     const int tid = threadIdx.x;
-    const int total = batch.total_blocks * kG;
+    constexpr int kUnits = kEq14 ? 1 : kG;   // work units per filter block
+    const int total = batch.total_blocks * kUnits;
 
     if (smem_u32(smem_bytes) & 127) {
         if (tid == 0) atomicOr(status, kStatusMisaligned);
@@ -658,7 +668,7 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             mbar_init(&sm.bar[1], 1);
             const int b = (int)atomicAdd(&work[0], 1u);
             sm.blk[0] = b;
-            if (b < total) sissue(batch, b / kG, sm.raw[0], &sm.bar[0]);
+            if (b < total) sissue(batch, b / kUnits, sm.raw[0], &sm.bar[0]);
         }
         if (tid < 192) {
             const int pl = tid / 96, d = (tid / 12) & 7, t = tid % 12;
@@ -674,7 +684,7 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             if (tid == 0) {
                 const int nb = (int)atomicAdd(&work[0], 1u);
                 sm.blk[buf ^ 1] = nb;
-                if (nb < total) sissue(batch, nb / kG, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
+                if (nb < total) sissue(batch, nb / kUnits, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
             }
             const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, kWaitCycles);
             if (__syncthreads_or(!arrived)) {
@@ -685,29 +695,17 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
                 }
                 break;
             }
-            const int fb = blk / kG, grp = blk - fb * kG;
+            const int fb = blk / kUnits, grp = blk - fb * kUnits;
             const SBlockRef r = slocate(batch, fb);
             const SearchFrameDev &F = batch.f[r.fi];
-            const bool sub = (allowed_pairs(F, 0) & allowed_pairs(F, 1)) != ~0ull;
-            if (F.bitdepth == 8) {
-                if (sub)
-                    dist_block<uint8_t, kG, kCoded, kEq14, true>(F, r.fby, r.fbx, fb, grp, sm,
-                                                                 sm.raw[buf], dist_luma,
-                                                                 dist_chroma, skipped);
-                else
-                    dist_block<uint8_t, kG, kCoded, kEq14, false>(F, r.fby, r.fbx, fb, grp, sm,
-                                                                  sm.raw[buf], dist_luma,
-                                                                  dist_chroma, skipped);
-            } else {
-                if (sub)
-                    dist_block<uint16_t, kG, kCoded, kEq14, true>(F, r.fby, r.fbx, fb, grp, sm,
-                                                                  sm.raw[buf], dist_luma,
-                                                                  dist_chroma, skipped);
-                else
-                    dist_block<uint16_t, kG, kCoded, kEq14, false>(F, r.fby, r.fbx, fb, grp, sm,
-                                                                   sm.raw[buf], dist_luma,
-                                                                   dist_chroma, skipped);
-            }
+            if (F.bitdepth == 8)
+                dist_block<uint8_t, kG, kCoded, kEq14, kSub>(F, r.fby, r.fbx, fb, grp, sm,
+                                                             sm.raw[buf], dist_luma, dist_chroma,
+                                                             skipped);
+            else
+                dist_block<uint16_t, kG, kCoded, kEq14, kSub>(F, r.fby, r.fbx, fb, grp, sm,
+                                                              sm.raw[buf], dist_luma, dist_chroma,
+                                                              skipped);
             __syncthreads();
         }
     }
@@ -725,14 +723,14 @@ constexpr size_t kSmemBytes = sizeof(SearchSmem);
 
 // Persistent grid: `per_sm` CTAs on every SM (at most what fits), never more
 // CTAs than work units.
-template <int kG, bool kCoded, bool kEq14>
+template <int kG, bool kCoded, bool kEq14, bool kSub>
 int dist_grid(int units, int per_sm)
 {
     static int cached_dev = -1, cached_sms = 0, cached_occ = 1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != cached_dev) {
-        auto *kern = dist_kernel<kG, kCoded, kEq14>;
+        auto *kern = dist_kernel<kG, kCoded, kEq14, kSub>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
@@ -747,27 +745,47 @@ int dist_grid(int units, int per_sm)
     return units < ctas ? units : ctas;
 }
 
+template <int kG, bool kCoded, bool kEq14, bool kSub>
+void launch_dist_kernel(const SearchBatch &b, long long *dl, long long *dc, uint8_t *skipped,
+                        int *status, unsigned *work, int units, int per_sm, cudaStream_t s)
+{
+    dist_kernel<kG, kCoded, kEq14, kSub><<<dist_grid<kG, kCoded, kEq14, kSub>(units, per_sm),
+                                           kThreads, kSmemBytes, s>>>(b, dl, dc, skipped, status,
+                                                                      work);
+}
+
+// Whether the call searches a subset of the pairs (the same for every frame).
+bool subset_search(const SearchBatch &b)
+{
+    return (allowed_pairs(b.f[0], 0) & allowed_pairs(b.f[0], 1)) != ~0ull;
+}
+
 template <int kG>
 cudaError_t launch_dist(const SearchBatch &b, long long *dl, long long *dc, uint8_t *skipped,
                         int *status, unsigned *work, int per_sm, cudaStream_t s)
 {
     const int units = b.total_blocks * kG;
-    if (skipped)
-        dist_kernel<kG, true, false><<<dist_grid<kG, true, false>(units, per_sm), kThreads,
-                                        kSmemBytes, s>>>(b, dl, dc, skipped, status, work);
-    else
-        dist_kernel<kG, false, false><<<dist_grid<kG, false, false>(units, per_sm), kThreads,
-                                         kSmemBytes, s>>>(b, dl, dc, nullptr, status, work);
+    const bool sub = subset_search(b);
+    if (skipped) {
+        if (sub) launch_dist_kernel<kG, true, false, true>(b, dl, dc, skipped, status, work, units, per_sm, s);
+        else launch_dist_kernel<kG, true, false, false>(b, dl, dc, skipped, status, work, units, per_sm, s);
+    } else {
+        if (sub) launch_dist_kernel<kG, false, false, true>(b, dl, dc, nullptr, status, work, units, per_sm, s);
+        else launch_dist_kernel<kG, false, false, false>(b, dl, dc, nullptr, status, work, units, per_sm, s);
+    }
     return cudaGetLastError();
 }
 
-// Eq. 14 tables: eight candidates per work unit (two primary strengths).
+// Eq. 14 tables: one work unit per filter block, its 64 candidates in eight
+// groups of eight (two primary strengths).
 cudaError_t launch_dist_eq14(const SearchBatch &b, long long *dl, long long *dc, int *status,
                              unsigned *work, cudaStream_t s)
 {
-    const int units = b.total_blocks * 8;
-    dist_kernel<8, false, true><<<dist_grid<8, false, true>(units, 2), kThreads, kSmemBytes, s>>>(
-        b, dl, dc, nullptr, status, work);
+    const int units = b.total_blocks;
+    if (subset_search(b))
+        launch_dist_kernel<8, false, true, true>(b, dl, dc, nullptr, status, work, units, 2, s);
+    else
+        launch_dist_kernel<8, false, true, false>(b, dl, dc, nullptr, status, work, units, 2, s);
     return cudaGetLastError();
 }
 
