@@ -502,15 +502,26 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                         }
                     }
                     // each of the block's four lanes evaluates a quarter of the
-                    // candidates
+                    // candidates; the eight blocks' values are summed across
+                    // the warp before one shared atomic per candidate
+                    constexpr int kC = kN / 4;
+                    long long tv[kC];
+    #pragma unroll
+                    for (int j = 0; j < kC; j++) tv[j] = 0;
     #pragma unroll
                     for (int c = 0; c < kN; c++) {
-                        if (n > 0 && (c * 4) / kN == sub) {
-                            const long long t = eq14_value(n, ssum, ss2, sx + A[c], (long long)sx2 + BX[c],
-                                                           (long long)sxs + BS[c], F.bitdepth);
-                            atomicAdd(&sm.acc[c], (unsigned long long)t);
-                        }
+                        if (n > 0 && (c * 4) / kN == sub)
+                            tv[c % kC] = eq14_value(n, ssum, ss2, sx + A[c], (long long)sx2 + BX[c],
+                                                    (long long)sxs + BS[c], F.bitdepth);
                     }
+    #pragma unroll
+                    for (int o = 4; o <= 16; o <<= 1)
+    #pragma unroll
+                        for (int j = 0; j < kC; j++) tv[j] += __shfl_xor_sync(0xffffffffu, tv[j], o);
+                    if (bx == 0)
+    #pragma unroll
+                        for (int j = 0; j < kC; j++)
+                            atomicAdd(&sm.acc[sub * kC + j], (unsigned long long)tv[j]);
                 } else {
                     // (U, V) lanes: per plane, the 4-row half of a chroma 8x8
                     // block is eight lanes (two 4x4 blocks) of this warp; the
@@ -599,19 +610,24 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
             }
         }
         if constexpr (kEq14) {
-            // chroma 8x8 blocks: two planes x 16 blocks x the unit's candidates
-            for (int i = tid; i < 2 * 16 * kN; i += kThreads) {
-                const int k = i / (16 * kN), cb = (i / kN) % 16, c = i % kN;
+            // chroma 8x8 blocks: two planes x 16 blocks x the unit's candidates,
+            // one per thread; lanes 8 apart hold the same candidate
+            static_assert(2 * 16 * kN == kThreads, "one chroma evaluation per thread");
+            {
+                const int k = tid / (16 * kN), cb = (tid / kN) % 16, c = tid % kN;
                 const int *h0 = sm.e14h[k][cb][0], *h1 = sm.e14h[k][cb][1];
                 const int n = h0[24] + h1[24];
+                long long t = 0;
                 if (n > 0) {
                     const long long sx = h0[25] + h1[25], sx2 = h0[26] + h1[26];
                     const long long ssum = h0[27] + h1[27], ss2 = h0[28] + h1[28], sxs = h0[29] + h1[29];
-                    const long long t = eq14_value(n, ssum, ss2, sx + h0[3 * c] + h1[3 * c],
-                                                   sx2 + h0[3 * c + 1] + h1[3 * c + 1],
-                                                   sxs + h0[3 * c + 2] + h1[3 * c + 2], F.bitdepth);
-                    atomicAdd(&sm.acc14c[c], (unsigned long long)t);
+                    t = eq14_value(n, ssum, ss2, sx + h0[3 * c] + h1[3 * c],
+                                   sx2 + h0[3 * c + 1] + h1[3 * c + 1],
+                                   sxs + h0[3 * c + 2] + h1[3 * c + 2], F.bitdepth);
                 }
+                t += __shfl_xor_sync(0xffffffffu, t, 8);
+                t += __shfl_xor_sync(0xffffffffu, t, 16);
+                if (lane < kN) atomicAdd(&sm.acc14c[c], (unsigned long long)t);
             }
             __syncthreads();
             if (tid < kN) {
