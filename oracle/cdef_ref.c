@@ -887,6 +887,88 @@ int cdef_ref_select_presets_general(int nblocks, const int64_t *dist_luma,
                                           presets, npresets, block_ids, cost);
 }
 
+/* Section 5's tables for the other chroma formats (section 4, last
+ * paragraph; reading R25), at any bit depth.  Luma as cdef_ref_distortion.
+ * Chroma (U + V): format 420 as cdef_ref_distortion; format 422, whose
+ * chroma is not filtered, the unfiltered squared error of the filter
+ * block's chroma region (w/2 x h planes: 32 columns x 64 rows) for every
+ * pair; format 444 the squared error of each plane filtered in 8x8 blocks
+ * of the 64x64 filter block with the chroma strengths and damping and the
+ * co-located luma block's direction. */
+static int64_t block_sse_g(const uint16_t *rec, ptrdiff_t rs, const uint16_t *src, ptrdiff_t ss,
+                           int pw, int ph, int sub, int chroma, int filtered, int bitdepth,
+                           int fby, int fbx, int pri, int sec, int damping, const uint8_t *dir,
+                           const int32_t *var, int bw, int fbw, int fbh)
+{
+    int bs = 8 >> sub;
+    int64_t sse = 0;
+    for (int i = fby * fbh; i < (fby + 1) * fbh && i < ph; i++) {
+        for (int j = fbx * fbw; j < (fbx + 1) * fbw && j < pw; j++) {
+            int64_t yv = rec[(ptrdiff_t)i * rs + j];
+            if (filtered) {
+                int b8 = (i / bs) * bw + (j / bs);
+                cdef_ref_eff_params e;
+                cdef_ref_block_params(pri, sec, damping, chroma, bitdepth, chroma ? 0 : var[b8], &e);
+                yv = cdef_ref_filter_sample(rec, pw, ph, rs, i, j, dir[b8], &e);
+            }
+            int64_t err = yv - (int64_t)src[(ptrdiff_t)i * ss + j];
+            sse += err * err;
+        }
+    }
+    return sse;
+}
+
+int cdef_ref_distortion_format(int w, int h, int bitdepth, int damping, int format,
+                               const uint16_t *ry, ptrdiff_t rys,
+                               const uint16_t *ru, ptrdiff_t rus,
+                               const uint16_t *rv, ptrdiff_t rvs,
+                               const uint16_t *sy, ptrdiff_t sys,
+                               const uint16_t *su, ptrdiff_t sus,
+                               const uint16_t *sv, ptrdiff_t svs,
+                               int64_t *dist_luma, int64_t *dist_chroma)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    if (damping < 3 || damping > 6 || (format != 420 && format != 422 && format != 444))
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    uint8_t *dir = (uint8_t *)malloc((size_t)bw * bh);
+    int32_t *var = (int32_t *)malloc((size_t)bw * bh * sizeof(int32_t));
+    if (!dir || !var) {
+        free(dir);
+        free(var);
+        return -1;
+    }
+    cdef_ref_find_dir(ry, w, h, rys, bitdepth, dir, var);
+    /* chroma plane geometry: size, 8x8-block subsampling, filter-block size */
+    int cw = format == 444 ? w : w / 2, ch = format == 420 ? h / 2 : h;
+    int csub = format == 444 ? 0 : 1;
+    int cfw = format == 444 ? 64 : 32, cfh = format == 420 ? 32 : 64;
+    int cfilt = format != 422;
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    for (int fby = 0; fby < fb_rows; fby++) {
+        for (int fbx = 0; fbx < fb_cols; fbx++) {
+            int b = fby * fb_cols + fbx;
+            for (int p = 0; p < 16; p++) {
+                for (int s = 0; s < 4; s++) {
+                    int q = p * 4 + s;
+                    dist_luma[b * 64 + q] =
+                        block_sse_g(ry, rys, sy, sys, w, h, 0, 0, 1, bitdepth, fby, fbx, p,
+                                    sec_values[s], damping, dir, var, bw, 64, 64);
+                    dist_chroma[b * 64 + q] =
+                        block_sse_g(ru, rus, su, sus, cw, ch, csub, 1, cfilt, bitdepth, fby, fbx,
+                                    p, sec_values[s], damping, dir, var, bw, cfw, cfh) +
+                        block_sse_g(rv, rvs, sv, svs, cw, ch, csub, 1, cfilt, bitdepth, fby, fbx,
+                                    p, sec_values[s], damping, dir, var, bw, cfw, cfh);
+                }
+            }
+        }
+    }
+    free(dir);
+    free(var);
+    return 0;
+}
+
 /* Chroma formats other than 4:2:0 (section 4, last paragraph; reading R25):
  *   format 422: chroma planes are w/2 x h; their subsampling differs
  *               horizontally and vertically, so chroma is not filtered (the

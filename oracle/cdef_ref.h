@@ -194,6 +194,18 @@ int cdef_ref_select_presets_subset(int nblocks, const int64_t *dist_luma,
                                    int32_t *presets, int32_t *npresets,
                                    uint8_t *block_ids, int64_t *cost);
 
+/* Section 5's 64-pair tables for chroma format 420, 422 (chroma not
+ * filtered: its entries are the unfiltered error) or 444 (chroma planes
+ * filtered in the luma geometry), at bit depths 8-12 (reading R25). */
+int cdef_ref_distortion_format(int w, int h, int bitdepth, int damping, int format,
+                               const uint16_t *ry, ptrdiff_t rys,
+                               const uint16_t *ru, ptrdiff_t rus,
+                               const uint16_t *rv, ptrdiff_t rvs,
+                               const uint16_t *sy, ptrdiff_t sys,
+                               const uint16_t *su, ptrdiff_t sus,
+                               const uint16_t *sv, ptrdiff_t svs,
+                               int64_t *dist_luma, int64_t *dist_chroma);
+
 /* Section 5, eq. 14 (readings R22-R24 in cdef_ref.c): per filter block, 64
  * luma and 64 chroma entries sum_8x8 round(256 * D_8x8). */
 int cdef_ref_distortion_eq14(int w, int h, int bitdepth, int damping,

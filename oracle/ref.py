@@ -117,6 +117,9 @@ def lib():
             C.c_int, _i64p, _i64p, C.c_int, C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64,
             C.c_int, _i32p, C.POINTER(C.c_int32), _u8p, C.POINTER(C.c_int64)]
         L.cdef_ref_select_presets_subset.restype = C.c_int
+        L.cdef_ref_distortion_format.argtypes = (
+            [C.c_int] * 5 + [_u16p, C.c_ssize_t] * 6 + [_i64p, _i64p])
+        L.cdef_ref_distortion_format.restype = C.c_int
         L.cdef_ref_distortion_eq14.argtypes = (
             [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6 + [_i64p, _i64p])
         L.cdef_ref_distortion_eq14.restype = C.c_int
@@ -317,6 +320,31 @@ def select_presets_general(dist_luma, dist_chroma, width: int, skipped, lam: int
                                              C.byref(cost)) != 0:
         raise ValueError("oracle rejected select_presets_general arguments")
     return dict(presets=presets, npresets=n.value, block_ids=ids, cost=cost.value)
+
+
+def distortion_format(rec, src, bitdepth: int, damping: int, fmt: int):
+    """Section 5's tables for chroma format 420, 422 or 444 (reading R25),
+    any bit depth: (B, 64) luma and chroma int64 arrays."""
+    ry, ru, rv = (_u16(p) for p in rec)
+    sy, su, sv = (_u16(p) for p in src)
+    h, w = ry.shape
+    nb = ((h + 63) // 64) * ((w + 63) // 64)
+    dl = np.zeros(nb * 64, np.int64)
+    dc = np.zeros(nb * 64, np.int64)
+    rc = lib().cdef_ref_distortion_format(
+        w, h, bitdepth, damping, fmt, ry, w, ru, ru.shape[1], rv, rv.shape[1],
+        sy, w, su, su.shape[1], sv, sv.shape[1], dl, dc)
+    if rc != 0:
+        raise ValueError("oracle rejected distortion_format arguments")
+    return dl.reshape(nb, 64), dc.reshape(nb, 64)
+
+
+def search_strengths_format(rec, src, bitdepth: int, damping: int, lam: int, fmt: int,
+                            refine_passes: int = 0):
+    dl, dc = distortion_format(rec, src, bitdepth, damping, fmt)
+    out = select_presets_general(dl, dc, 64, None, lam, refine_passes)
+    out.update(dist_luma=dl, dist_chroma=dc)
+    return out
 
 
 def select_presets_subset(dist_luma, dist_chroma, width: int, skipped, luma_pairs: int,

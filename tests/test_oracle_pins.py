@@ -1043,6 +1043,48 @@ def test_444_identities(ref):
     assert np.array_equal(cu, const)
 
 
+def _format_src(f, u, v, seed):
+    """A source frame for the format tests: the luma source and chroma
+    planes near the decoded ones (what a coder leaves)."""
+    rng = np.random.default_rng(seed)
+    mx = (1 << f.bitdepth) - 1
+    su = np.clip(u.astype(np.int64) + rng.integers(-6, 7, u.shape), 0, mx).astype(np.uint16)
+    sv = np.clip(v.astype(np.int64) + rng.integers(-6, 7, v.shape), 0, mx).astype(np.uint16)
+    return (f.src[0], su, sv)
+
+
+@pytest.mark.parametrize("fmt,bd", [(444, 8), (444, 10), (422, 8), (420, 12)])
+def test_format_tables_are_sse_of_decoder_output(ref, fmt, bd):
+    """Reading R25 in section 5's tables: each entry is the squared error of
+    what the filter oracle outputs for that strength pair everywhere (4:2:2
+    chroma: the unfiltered error for every pair)."""
+    from paper_1602_05975_gb300 import synth
+    if fmt == 420:
+        f = synth.make_frame(136, 72, bd, 32, seed=75)
+        planes, src = f.rec, f.src
+    else:
+        f, u, v, _ = _format_frame(fmt, w=136, h=72, bd=bd, seed=76)
+        planes, src = (f.rec[0], u, v), _format_src(f, u, v, 77)
+    dl, dc = ref.distortion_format(planes, src, bd, 5, fmt)
+    params = np.zeros(f.params.shape, np.uint8)
+    params[..., 4] = 5
+    for q in (0, 6, 29, 63):
+        p, s = q >> 2, (0, 1, 2, 4)[q & 3]
+        params[..., 0] = params[..., 2] = p
+        params[..., 1] = params[..., 3] = s
+        out = ref.filter_frame_format(*planes, bd, params, fmt)
+        for b in range(dl.shape[0]):
+            by, bx = divmod(b, f.params.shape[1])
+            ly = np.s_[by * 64:(by + 1) * 64, bx * 64:(bx + 1) * 64]
+            el = int(((out[0][ly].astype(np.int64) - src[0][ly]) ** 2).sum())
+            cy, cx = ((64, 64) if fmt == 444 else (64, 32) if fmt == 422 else (32, 32))
+            cs = np.s_[by * cy:(by + 1) * cy, bx * cx:(bx + 1) * cx]
+            ec = sum(int(((out[k][cs].astype(np.int64) - src[k][cs]) ** 2).sum()) for k in (1, 2))
+            assert dl[b, q] == el and dc[b, q] == ec, (fmt, bd, q, b)
+    if fmt == 422:
+        assert (dc == dc[:, :1]).all()      # chroma is not filtered: one value per block
+
+
 def test_unknown_format_rejected(ref):
     f, u, v, params = _format_frame(444, seed=63)
     with pytest.raises(ValueError):
