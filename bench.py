@@ -558,7 +558,7 @@ SEARCH_WORKLOAD = dict(
 # the (19, 7) preset's 12 taps and the uncoded part's accumulation per
 # candidate (1).  Per luma 8x8 block: the direction search as in the filter.
 def search_ops_per_sample(variant: str) -> int:
-    per_cand = {"sse": 8, "eq14": 11, "coded": 9}[variant]
+    per_cand = {"sse": 8, "eq14": 11, "coded": 9, "444": 8, "12bit": 8}[variant]
     extra = 12 * 8 if variant == "coded" else 0
     return 16 * 4 * 8 + 3 * 8 * 8 + 24 + 64 * per_cand + extra
 
@@ -566,7 +566,8 @@ def search_ops_per_sample(variant: str) -> int:
 def search_ops(frames, variant: str) -> int:
     ops = 0
     for f in frames:
-        samples = f.width * f.height + 2 * (f.width // 2) * (f.height // 2)
+        cw, ch = (f.width, f.height) if variant == "444" else (f.width // 2, f.height // 2)
+        samples = f.width * f.height + 2 * cw * ch
         ops += samples * search_ops_per_sample(variant) + (f.width // 8) * (f.height // 8) * (
             376 + 124 + 7 + 64 + 1)
     return ops
@@ -578,9 +579,12 @@ def _oracle_search(task):
     w, h, seed, damping, lam, variant, passes, coded = task
     from oracle import ref
     from paper_1602_05975_gb300 import synth
-    f = synth.make_frame(w, h, 8, None, seed)
+    bd, fmt = search_variant_format(variant)
+    f = synth.make_frame(w, h, bd, None, seed, fmt)
     t = time.process_time()
-    if variant == "eq14":
+    if variant in ("444", "12bit"):
+        ref.search_strengths_format(f.rec, f.src, bd, damping, lam, fmt, passes)
+    elif variant == "eq14":
         ref.search_strengths_eq14(f.rec, f.src, 8, damping, lam, passes)
     elif variant == "coded":
         ref.search_strengths_coded(f.rec, f.src, 8, damping, lam, coded, passes)
@@ -588,6 +592,11 @@ def _oracle_search(task):
         ref.search_strengths(f.rec, f.src, 8, damping, lam, passes)
     blocks = -(-w // 64) * -(-h // 64)
     return blocks * 2 * (128 if variant == "coded" else 64), time.process_time() - t
+
+
+def search_variant_format(variant: str):
+    """(bit depth, chroma format) of the search workload's frames."""
+    return {"444": (8, 444), "12bit": (12, 420)}.get(variant, (8, 420))
 
 
 def run_search(args):
@@ -609,12 +618,13 @@ def run_search(args):
     variant = args.search_variant
     if variant == "eq14":
         ctx.set_search_metric("eq14")
+    bd, fmt = search_variant_format(variant)
     frames = []
     for f in range(SEARCH_WORKLOAD["frames"]):
         w, h = SEARCH_WORKLOAD["sizes"][f % 3]
-        frames.append(synth.make_frame(w, h, 8, None, SEARCH_WORKLOAD["base_seed"] + f))
-    recs = [cdef.frame_from_numpy(fr.rec, 8) for fr in frames]
-    srcs = [cdef.frame_from_numpy(fr.src, 8) for fr in frames]
+        frames.append(synth.make_frame(w, h, bd, None, SEARCH_WORKLOAD["base_seed"] + f, fmt))
+    recs = [cdef.frame_from_numpy(fr.rec, bd) for fr in frames]
+    srcs = [cdef.frame_from_numpy(fr.src, bd) for fr in frames]
     nb = sum(fr.params.shape[0] * fr.params.shape[1] for fr in frames)
     damping = [4 + (fr.q > 16) + (fr.q > 32) for fr in frames]   # larger damping for larger Q
     lambdas = [fr.q * fr.q for fr in frames]
@@ -708,13 +718,17 @@ def run_search(args):
     assert same, "batched and one-frame-at-a-time searches differ"
     assert ctx.status() == 0
     ops = search_ops(frames, variant)
-    roofline = {"bound": "alu", "achieved": ops / (dist_ms * 1e-3) / 1e9, "peak": alu_peak_gops(),
-                "unit": "Gop/s", "frac": ops / (dist_ms * 1e-3) / 1e9 / alu_peak_gops(),
-                "traffic": None, "kernel": "dist_kernel (distortion tables)",
+    peak_ops = alu_peak_gops(bd)
+    roofline = {"bound": "alu", "achieved": ops / (dist_ms * 1e-3) / 1e9, "peak": peak_ops,
+                "unit": "Gop/s", "frac": ops / (dist_ms * 1e-3) / 1e9 / peak_ops,
+                "traffic": None,
+                "kernel": "dist_wide_kernel + find_dir_kernel (distortion tables, 32-bit lanes)"
+                if variant in ("444", "12bit") else "dist_kernel (distortion tables)",
                 "ops_per_launch": ops, "mean_launch_us": dist_ms * 1e3,
                 "launch_time": "CUDA events around the kernel inside the search graph",
                 "preset_kernel_us": pre_ms * 1e3,
-                "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz"}
+                "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz"
+                if bd <= 10 else "derived: 152 SMs x 128 lanes x 2070 MHz"}
     cpu = None
     if pool is not None:
         sample = [i for i in range(len(frames)) if (frames[i].width, frames[i].height) == (640, 360)]
@@ -897,9 +911,11 @@ def main():
     ap.add_argument("--requests", type=int, default=0, help="serve: requests per rate")
     ap.add_argument("--refine", type=int, default=0,
                     help="search: preset re-optimisation passes after the greedy search")
-    ap.add_argument("--search-variant", default="sse", choices=["sse", "eq14", "coded"],
-                    help="search: squared error (64 pairs), eq. 14 distortion, or the "
-                         "128-combination search with coded-residual maps")
+    ap.add_argument("--search-variant", default="sse",
+                    choices=["sse", "eq14", "coded", "444", "12bit"],
+                    help="search: squared error (64 pairs), eq. 14 distortion, the "
+                         "128-combination search with coded-residual maps, or the squared-error "
+                         "search over 8-bit 4:4:4 or 12-bit 4:2:0 frames")
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi clocks during the run")
     args = ap.parse_args()

@@ -206,7 +206,16 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
  *   npresets     : HOST, n entries
  *   block_ids    : DEVICE, sum_i B_i bytes, written
  *   cost         : HOST, n entries: J of the chosen N
- * 1 <= n <= 48; bit depth 8 or 10 (CDEF_ERR_BITDEPTH otherwise).
+ * 1 <= n <= 48; bit depth 8, 10 or 12; chroma format 4:2:0, 4:2:2 or 4:4:4
+ * (inferred from the chroma plane sizes as for cdef_filter_frame).  4:2:2
+ * chroma is not filtered (section 4), so its entries are the unfiltered
+ * error for every pair; 4:4:4 chroma planes are filtered in 8x8 blocks
+ * with the chroma strengths and the co-located luma direction.  A call
+ * holding any 12-bit, 4:2:2 or 4:4:4 frame computes its tables with 32-bit
+ * arithmetic per sample (slower than the packed 8/10-bit 4:2:0 path) and
+ * needs (W/8)(H/8) * 5 bytes of direction maps per frame in the context;
+ * such calls take only the squared-error metric (CDEF_ERR_ARG with
+ * CDEF_METRIC_EQ14).
  * This call synchronises the stream before returning (host outputs).
  */
 int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
@@ -233,7 +242,8 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
  *   dist_luma,
  *   dist_chroma  : DEVICE, sum_i B_i * 128 int64 each, or both NULL
  *   presets      : HOST, n*8 entries (first npresets[i] of frame i valid)
- * Synchronises the stream before returning. */
+ * Frames: 8 or 10-bit 4:2:0 only (CDEF_ERR_ARG for 4:2:2, 4:4:4 or 12-bit
+ * frames).  Synchronises the stream before returning. */
 int cdef_search_strengths_coded(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
                                 const cdef_frame *src, const uint8_t *const *coded,
                                 const int32_t *damping, const int64_t *lambda,

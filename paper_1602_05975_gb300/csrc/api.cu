@@ -29,7 +29,7 @@ struct cdef_ctx {
     cudaStream_t capture; // records the search's launches into a graph
     cudaGraphExec_t search_exec;  // the last search graph, updated per call
     SearchBatch *search_key;      // what search_exec was recorded for
-    void *search_ptrs[6];         // and its tables, ids and scratch pointers
+    void *search_ptrs[7];         // and its tables, ids, scratch and direction-map pointers
     SearchTune search_key_tune;   // and its launch configuration
     SearchTune forced;            // fields > 0 fixed by cdef_ctx_set_tuning
     SearchTune last;              // configuration of the last search
@@ -699,16 +699,25 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
     if ((dist_luma == nullptr) != (dist_chroma == nullptr)) return CDEF_ERR_ARG;
     SearchBatch *b = new (std::nothrow) SearchBatch();
     if (!b) return CDEF_ERR_NOMEM;
+    // frames other than 8/10-bit 4:2:0 take the wide tables (64 pairs,
+    // squared error)
+    bool wide = false;
+    for (int i = 0; i < n; i++)
+        if (rec[i].bitdepth > 10 || chroma_format(&rec[i]) != 420) wide = true;
+    if (wide && (coded || ctx->metric == CDEF_METRIC_EQ14)) { delete b; return CDEF_ERR_ARG; }
     int total = 0, rc = CDEF_OK;
+    size_t maps = 0;
     for (int i = 0; i < n && rc == CDEF_OK; i++) {
-        if ((rc = check_frame(&rec[i])) || (rc = check_frame(&src[i]))) break;
+        if ((rc = check_frame(&rec[i], 7)) || (rc = check_frame(&src[i], 7))) break;
         if (!same_geometry(&rec[i], &src[i])) { rc = CDEF_ERR_SIZE; break; }
-        if (rec[i].bitdepth > 10) { rc = CDEF_ERR_BITDEPTH; break; }
         if (damping[i] < 3 || damping[i] > 6 || lambda[i] < 0) { rc = CDEF_ERR_ARG; break; }
         if (coded && !coded[i]) { rc = CDEF_ERR_ARG; break; }
         SearchFrameDev &f = b->f[i];
         f.coded = coded ? coded[i] : nullptr;
-        if ((rc = encode_frame_tiles(f.tmap, &rec[i]))) break;
+        f.chroma_format = chroma_format(&rec[i]);
+        f.map_start = (int)maps;
+        maps += (size_t)(rec[i].y.width / 8) * (rec[i].y.height / 8);
+        if (!wide && (rc = encode_frame_tiles(f.tmap, &rec[i]))) break;
         const cdef_plane *pr[3] = {&rec[i].y, &rec[i].u, &rec[i].v};
         const cdef_plane *ps[3] = {&src[i].y, &src[i].u, &src[i].v};
         for (int k = 0; k < 3; k++) {
@@ -756,7 +765,15 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
     // search owns counter pair 0 (filter launches take pairs 1..).
     unsigned *work = ctx->work;
     SearchTune tune;
-    if (ctx->metric == CDEF_METRIC_EQ14) {
+    uint8_t *wide_dirs = nullptr;
+    int32_t *wide_vars = nullptr;
+    if (wide) {
+        // direction maps for every frame of the call
+        if ((rc = ensure_maps(ctx, maps))) { delete b; return rc; }
+        wide_dirs = ctx->maps_dir;
+        wide_vars = ctx->maps_var;
+        tune = {1, 1};   // one CTA per filter block and plane group
+    } else if (ctx->metric == CDEF_METRIC_EQ14) {
         if (coded) { delete b; return CDEF_ERR_ARG; }
         tune = {8, 2};   // the eq. 14 tables: 8 candidates per work unit
     } else if ((rc = choose_search_tune(ctx, *b, dl, dc, cur, tot, block_ids, skipped, s, &tune))) {
@@ -769,7 +786,7 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
     // one relaunches its graph; otherwise the launches are recorded on the
     // capture stream and the cached executable graph updated in place
     // (re-instantiated if the shape changed).
-    void *const ptrs[6] = {dl, dc, block_ids, cur, tot, skipped};
+    void *const ptrs[7] = {dl, dc, block_ids, cur, tot, skipped, wide_dirs};
     const bool same = ctx->search_exec && ctx->search_key &&
                       memcmp(ctx->search_key, b, sizeof(SearchBatch)) == 0 &&
                       memcmp(ctx->search_ptrs, ptrs, sizeof(ptrs)) == 0 &&
@@ -782,7 +799,8 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
         const cudaError_t le = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids,
                                              ctx->status, work, tune, ctx->refine_passes,
                                              ctx->capture, skipped,
-                                             ctx->stage_timing ? ctx->stage_ev : nullptr);
+                                             ctx->stage_timing ? ctx->stage_ev : nullptr,
+                                             wide_dirs, wide_vars);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(ctx->capture, &graph);
         if (e == cudaSuccess && le != cudaSuccess) e = le;

@@ -59,6 +59,8 @@ struct SearchFrameDev {  // aligned as CUtensorMap requires
     int block_start;                 // first filter block of this frame in the tables
     long long lambda;
     const uint8_t *coded;            // 8x8 coded-residual map (128-combination search only)
+    int chroma_format = 420;         // 420, 422 or 444 (formats other than 4:2:0: wide tables)
+    int map_start = 0;               // first 8x8 block of this frame in the direction maps
     // allowed (S_p, S_s) pairs of the luma and the chroma group, bit p * 4 + s
     // (section 5's low-complexity search; all ones: every pair)
     unsigned long long pairs[2] = {~0ull, ~0ull};
@@ -143,6 +145,9 @@ inline SearchTune default_search_tune(int total_blocks, int sms)
 // by the call itself), `work` a zeroed counter pair (left zeroed).
 // `refine_passes`: 0 = the greedy presets; > 0 = then re-optimise each set
 // one preset at a time for at most that many passes (section 5).
+// `wide_dirs` / `wide_vars` non-null: the tables come from
+// launch_search_wide (4:2:2, 4:4:4 or 12-bit frames; 64 combinations), the
+// direction maps written there.
 // `stage_events` non-null: three events recorded before the distortion
 // kernel, between it and the preset selection, and after it (event nodes
 // when the stream is being captured into a graph).
@@ -154,7 +159,13 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
                           unsigned long long *tot, SearchResultDev *results,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
                           int refine_passes, cudaStream_t s, uint8_t *skipped = nullptr,
-                          const cudaEvent_t *stage_events = nullptr);
+                          const cudaEvent_t *stage_events = nullptr,
+                          uint8_t *wide_dirs = nullptr, int32_t *wide_vars = nullptr);
+// Section 5's tables for 4:2:2, 4:4:4 and 12-bit frames (32-bit arithmetic
+// per sample): the direction maps of every frame into `dirs` / `vars` (at
+// each frame's map_start), then one CTA per filter block and plane group.
+cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *vars,
+                               long long *dist_luma, long long *dist_chroma, cudaStream_t s);
 // The preset selection alone (one cooperative launch); `ctl` is the control
 // block that follows `tot` in the scratch.
 // `width`: combinations per plane group in the tables (64 or 128; presets

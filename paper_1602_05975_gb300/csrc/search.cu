@@ -823,11 +823,21 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
                           unsigned long long *cur, unsigned long long *tot, SearchResultDev *results,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
                           int refine_passes, cudaStream_t s, uint8_t *skipped,
-                          const cudaEvent_t *stage_events)
+                          const cudaEvent_t *stage_events, uint8_t *wide_dirs,
+                          int32_t *wide_vars)
 {
     cudaError_t e = stage_mark(stage_events, 0, s);
     if (e != cudaSuccess) return e;
     const int per_sm = tune.ctas_per_sm;
+    if (wide_dirs) {   // 4:2:2, 4:4:4 or 12-bit frames
+        e = launch_search_wide(b, wide_dirs, wide_vars, dist_luma, dist_chroma, s);
+        if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
+        if (e != cudaSuccess) return e;
+        void *ctl = tot + (size_t)b.n * 4096;
+        e = launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
+                           refine_passes, 64, nullptr, s);
+        return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
+    }
     if (tune.groups == 8) {   // eq. 14 tables
         e = launch_dist_eq14(b, dist_luma, dist_chroma, status, work, s);
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);

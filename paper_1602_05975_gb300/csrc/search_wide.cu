@@ -1,0 +1,191 @@
+// Strength-search tables (section 5) for the frames the packed distortion
+// kernel does not take: 4:2:2 frames (chroma not filtered, section 4 last
+// paragraph), 4:4:4 frames (each chroma plane filtered in 8x8 blocks of the
+// 64x64 filter block with the chroma strengths and the co-located luma
+// direction) and 12-bit frames (whose sums leave 16-bit lanes).
+//
+// One CTA per (filter block, plane group).  The plane tiles of the block
+// with their 2-sample halo are staged in shared memory as 32-bit samples
+// (-1 outside the frame: such a tap adds nothing and is not in the clip
+// range).  Four threads share an 8x8 (4:2:0 chroma: 4x4) block, so the
+// direction and the strengths of a candidate are per thread; each of the 64
+// (S_p, S_s) candidates is evaluated with eq. 7-12 on every sample and its
+// squared error summed across the CTA.  The direction maps come from the
+// direction-search kernel, launched before this one.
+#include "tile.cuh"
+
+namespace cdefgb {
+namespace {
+
+using tile::tap_rc;
+
+__device__ __forceinline__ int sec_strength(int i) { return i == 3 ? 4 : i; }   // 0, 1, 2, 4
+
+constexpr int kWThreads = 256;
+constexpr int kTile = 68;   // 64 + 2 x 2 halo
+
+struct WideSmem {
+    int tile[2][kTile * kTile];   // the group's planes (luma: one; chroma: U and V)
+    unsigned long long acc[64];
+};
+
+// The group's plane k of frame F: pointers, size, and its geometry within
+// the filter block.
+struct PlaneView {
+    const uint8_t *rec, *src;
+    int64_t rec_pitch, src_pitch;
+    int w, h;         // plane size
+    int fw, fh;       // filter-block extent in this plane
+    int bs;           // block size of one direction (8, or 4 for 4:2:0 chroma)
+};
+
+__device__ __forceinline__ PlaneView plane_view(const SearchFrameDev &F, int k)
+{
+    PlaneView v;
+    v.rec = F.rec[k];
+    v.src = F.src[k];
+    v.rec_pitch = F.rec_pitch[k];
+    v.src_pitch = F.src_pitch[k];
+    if (k == 0 || F.chroma_format == 444) {
+        v.w = F.w;
+        v.h = F.h;
+        v.fw = v.fh = 64;
+        v.bs = 8;
+    } else if (F.chroma_format == 422) {
+        v.w = F.w >> 1;
+        v.h = F.h;
+        v.fw = 32;
+        v.fh = 64;
+        v.bs = 8;   // not filtered
+    } else {
+        v.w = F.w >> 1;
+        v.h = F.h >> 1;
+        v.fw = v.fh = 32;
+        v.bs = 4;
+    }
+    return v;
+}
+
+__device__ __forceinline__ int sample_at(const uint8_t *row, int x, bool wide)
+{
+    return wide ? (int)reinterpret_cast<const uint16_t *>(row)[x] : (int)row[x];
+}
+
+// Eq. 7-12 on one sample of the staged tile (32-bit arithmetic).
+__device__ __forceinline__ int filter_one(const int *t, const int o[12], const Eff &e)
+{
+    const int x = t[0];
+    int sum = 0, mn = x, mx = x;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        const int p = t[o[k]];
+        const int q = p < 0 ? x : p;
+        const int f = k < 4 ? constrain(q - x, e.pri, e.psh) : constrain(q - x, e.sec, e.ssh);
+        const int w = k < 2 ? e.w0 : k < 4 ? e.w1 : k < 8 ? 2 : 1;
+        sum += w * f;
+        mn = min(mn, q);
+        mx = max(mx, q);
+    }
+    return min(mx, max(mn, x + round16(sum)));
+}
+
+__global__ void __launch_bounds__(kWThreads)
+dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__restrict__ dirs,
+                 const int32_t *__restrict__ vars, long long *dist_luma, long long *dist_chroma)
+{
+    __shared__ WideSmem sm;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int blk = blockIdx.x, group = blockIdx.y;
+    int fi = 0;
+    while (fi + 1 < batch.n && blk >= batch.f[fi + 1].block_start) fi++;
+    const SearchFrameDev &F = batch.f[fi];
+    const int local = blk - F.block_start;
+    const int fby = local / F.fb_cols, fbx = local - fby * F.fb_cols;
+    const bool wide = F.bitdepth > 8;
+    const int sh8 = F.bitdepth - 8;
+    const bool filtered = group == 0 || F.chroma_format != 422;
+    const int nplanes = group == 0 ? 1 : 2;
+
+    // stage the planes (rec) of the group with the halo
+    for (int k = 0; k < nplanes; k++) {
+        const PlaneView v = plane_view(F, group == 0 ? 0 : 1 + k);
+        const int y0 = fby * v.fh - 2, x0 = fbx * v.fw - 2;
+        for (int i = tid; i < (v.fh + 4) * (v.fw + 4); i += kWThreads) {
+            const int r = i / (v.fw + 4), c = i - r * (v.fw + 4);
+            const int gy = y0 + r, gx = x0 + c;
+            sm.tile[k][r * kTile + c] = (gy >= 0 && gy < v.h && gx >= 0 && gx < v.w)
+                                            ? sample_at(v.rec + gy * v.rec_pitch, gx, wide)
+                                            : -1;
+        }
+    }
+    if (tid < 64) sm.acc[tid] = 0;
+    __syncthreads();
+
+    // four threads per direction block: 8x8 blocks (two rows each) or 4x4
+    // blocks of 4:2:0 chroma (one row each)
+    const int b8 = tid >> 2, part = tid & 3;
+    const int by = b8 >> 3, bx = b8 & 7;
+    const int gby = fby * 8 + by, gbx = fbx * 8 + bx;   // co-located luma 8x8 block
+    const int bw = F.w >> 3;
+    const bool in_luma = gby * 8 < F.h && gbx * 8 < F.w;
+    const int d = in_luma ? dirs[F.map_start + gby * bw + gbx] : 0;
+    const int var = in_luma ? vars[F.map_start + gby * bw + gbx] : 0;
+    int o[12];
+    for (int k = 0; k < 12; k++) {
+        int dr, dc;
+        tap_rc(d, k, dr, dc);
+        o[k] = dr * kTile + dc;
+    }
+    const unsigned long long pairs = allowed_pairs(F, group);
+
+    for (int q = 0; q < 64; q++) {
+        if (!((pairs >> q) & 1)) continue;
+        const int p = q >> 2, s = sec_strength(q & 3);
+        const Eff e = make_eff(p, s, F.damping, group != 0, var, sh8);
+        long long sse = 0;   // per thread at most 32 samples x 4095^2
+        for (int k = 0; k < nplanes; k++) {
+            const PlaneView v = plane_view(F, group == 0 ? 0 : 1 + k);
+            const int rows = v.bs == 8 ? 2 : 1, cols = v.bs;
+            const int r0 = by * v.bs + part * rows, c0 = bx * v.bs;
+            for (int i = 0; i < rows; i++) {
+                const int gy = fby * v.fh + r0 + i;
+                if (r0 + i >= v.fh || gy >= v.h) break;
+                const uint8_t *srow = v.src + gy * v.src_pitch;
+                for (int j = 0; j < cols; j++) {
+                    const int gx = fbx * v.fw + c0 + j;
+                    if (c0 + j >= v.fw || gx >= v.w) break;
+                    const int *t = &sm.tile[k][(r0 + i + 2) * kTile + c0 + j + 2];
+                    const int y = filtered ? filter_one(t, o, e) : t[0];
+                    const int err = y - sample_at(srow, gx, wide);
+                    sse += (long long)(err * err);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, off);
+        if (lane == 0) atomicAdd(&sm.acc[q], (unsigned long long)sse);
+    }
+    __syncthreads();
+    if (tid < 64) {
+        long long *out = (group == 0 ? dist_luma : dist_chroma) + (int64_t)blk * 64;
+        out[tid] = ((pairs >> tid) & 1) ? (long long)sm.acc[tid] : 0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *vars,
+                               long long *dist_luma, long long *dist_chroma, cudaStream_t s)
+{
+    for (int i = 0; i < b.n; i++) {
+        const SearchFrameDev &F = b.f[i];
+        const cudaError_t e = launch_find_dir(F.rec[0], F.rec_pitch[0], F.w, F.h, F.bitdepth,
+                                              dirs + F.map_start, vars + F.map_start, s);
+        if (e != cudaSuccess) return e;
+    }
+    dist_wide_kernel<<<dim3(b.total_blocks, 2), kWThreads, 0, s>>>(b, dirs, vars, dist_luma,
+                                                                   dist_chroma);
+    return cudaGetLastError();
+}
+
+}  // namespace cdefgb

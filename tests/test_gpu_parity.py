@@ -578,9 +578,11 @@ def test_chroma_formats_rejected_where_unsupported(cdef, ctx):
     out = cdef.alloc_frame(64, 64, 8, fill=0, chroma=444)
     with pytest.raises(cdef.CdefError):
         cdef.cdef_filter_frames(ctx, [inp], [cdef.params_tensor(f.params)], [out])
-    with pytest.raises(cdef.CdefError):
-        cdef.cdef_search_strengths(ctx, [inp], [inp], [4], [16],
-                                   torch.zeros(1, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(cdef.CdefError):     # the packed search of the no-allocation entry
+        cdef.cdef_search_strengths_noalloc([inp], [inp], [4], [16],
+                                           torch.zeros(1, dtype=torch.uint8, device="cuda"),
+                                           torch.zeros(64, dtype=torch.int64, device="cuda"),
+                                           torch.zeros(64, dtype=torch.int64, device="cuda"))
 
 
 # --------------------------------------------------------------- eq. 14 distortion
@@ -746,3 +748,85 @@ def test_search_subset_parity(cdef, ctx, ref, variant, passes):
 def test_search_subset_rejections(cdef, ctx):
     assert ctx._lib.cdef_ctx_set_search_subset(ctx.handle, 0, 1) != 0
     assert ctx._lib.cdef_ctx_set_search_subset(ctx.handle, 1, 0) != 0
+
+
+def _format_search_frame(cdef, fmt, w, h, bd, seed):
+    """A (rec, src) pair of chroma format `fmt`: the synthetic recipe at the
+    format's chroma resolution; the source chroma planes near the decoded
+    ones."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(w, h, bd, 32, seed=seed, chroma=fmt)
+    return f, f.rec, f.src
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("passes", [0, 2])
+def test_search_formats_parity(cdef, ctx, ref, passes):
+    """Section 5 over 4:4:4, 4:2:2 and 12-bit frames (reading R25), mixed
+    with an 8-bit 4:2:0 frame in one call: tables, presets, N, J and ids
+    equal the oracle's."""
+    specs = [(444, 136, 72, 8, 1140), (422, 200, 136, 10, 1141), (420, 136, 72, 12, 1142),
+             (420, 192, 128, 8, 1143), (444, 64, 64, 10, 1144)]
+    frames = [_format_search_frame(cdef, *sp) for sp in specs]
+    damping, lambdas = [5, 4, 6, 3, 5], [64, 512, 4096, 900, 0]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f, _, _ in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.full((nb * 64,), -1, dtype=torch.int64, device="cuda")
+    dc = torch.full((nb * 64,), -1, dtype=torch.int64, device="cuda")
+    ctx.set_search_refine(passes)
+    try:
+        res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(r, f.bitdepth) for f, r, _ in frames],
+                                         [cdef.frame_from_numpy(s_, f.bitdepth) for f, _, s_ in frames],
+                                         damping, lambdas, ids, dl, dc)
+    finally:
+        ctx.set_search_refine(0)
+    assert ctx.status() == 0
+    o0 = 0
+    for (f, r, s_), sp, rr, d, lam in zip(frames, specs, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths_format(r, s_, f.bitdepth, d, lam, sp[0], passes)
+        assert np.array_equal(dl[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_luma"])
+        assert np.array_equal(dc[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_chroma"])
+        assert rr["npresets"] == o["npresets"] and rr["cost"] == o["cost"]
+        assert [cdef.preset_index(p) for p in rr["presets"][:rr["npresets"]]] == \
+            [int(t) for t in o["presets"][:o["npresets"]]]
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
+
+
+@pytest.mark.gpu
+def test_search_formats_subset_and_rejections(cdef, ctx, ref):
+    """The low-complexity subset in the wide tables; the 128-combination
+    search and eq. 14 stay 8/10-bit 4:2:0 (CDEF_ERR_ARG otherwise)."""
+    f, r, s_ = _format_search_frame(cdef, 444, 136, 72, 8, 1150)
+    rec, src = cdef.frame_from_numpy(r, 8), cdef.frame_from_numpy(s_, 8)
+    nb = f.params.shape[0] * f.params.shape[1]
+    lmask, cmask = sum(1 << q for q in (0, 5, 9, 33, 62)), sum(1 << q for q in (1, 2, 40))
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    ctx.set_search_subset(lmask, cmask)
+    try:
+        res = cdef.cdef_search_strengths(ctx, [rec], [src], [5], [300], ids, dl, dc)
+    finally:
+        ctx.set_search_subset()
+    dlo, dco = ref.distortion_format(r, s_, 8, 5, 444)
+    o = ref.select_presets_subset(dlo, dco, 64, None, lmask, cmask, 300)
+    gl = dl.cpu().numpy().reshape(nb, 64)
+    gc = dc.cpu().numpy().reshape(nb, 64)
+    cl = np.array([(lmask >> q) & 1 for q in range(64)], bool)
+    cc = np.array([(cmask >> q) & 1 for q in range(64)], bool)
+    assert np.array_equal(gl[:, cl], dlo[:, cl]) and (gl[:, ~cl] == 0).all()
+    assert np.array_equal(gc[:, cc], dco[:, cc]) and (gc[:, ~cc] == 0).all()
+    assert res[0]["cost"] == o["cost"] and res[0]["npresets"] == o["npresets"]
+    with pytest.raises(cdef.CdefError):
+        cdef.cdef_search_strengths_coded(ctx, [rec], [src],
+                                         [torch.ones(nb * 64, dtype=torch.uint8, device="cuda")],
+                                         [5], [300], ids)
+    ctx.set_search_metric("eq14")
+    try:
+        with pytest.raises(cdef.CdefError):
+            cdef.cdef_search_strengths(ctx, [rec], [src], [5], [300], ids, dl, dc)
+    finally:
+        ctx.set_search_metric("sse")
+    assert ctx.status() == 0
