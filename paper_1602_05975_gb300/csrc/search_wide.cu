@@ -8,18 +8,18 @@
 // with their 2-sample halo are staged in shared memory as 32-bit samples
 // (-1 outside the frame: such a tap adds nothing and is not in the clip
 // range).  Four threads share an 8x8 (4:2:0 chroma: 4x4) block, so the
-// direction and the strengths of a candidate are per thread; each of the 64
-// (S_p, S_s) candidates is evaluated with eq. 7-12 on every sample and its
-// squared error summed across the CTA.  The direction maps come from the
-// direction-search kernel, launched before this one.
+// direction and the strengths of a candidate are per thread.  Per sample the
+// 64 (S_p, S_s) candidates come from 16 primary and 3 secondary constrained
+// sums (eq. 8's sum splits into the two tap sets; chroma blocks whose damping
+// is raised for S_p >= 8 take a second set of secondary sums), each rounded,
+// clipped (eq. 9-12) and its squared error summed across the CTA.  The
+// direction maps come from the direction-search kernel, launched first.
 #include "tile.cuh"
 
 namespace cdefgb {
 namespace {
 
 using tile::tap_rc;
-
-__device__ __forceinline__ int sec_strength(int i) { return i == 3 ? 4 : i; }   // 0, 1, 2, 4
 
 constexpr int kWThreads = 256;
 constexpr int kTile = 68;   // 64 + 2 x 2 halo
@@ -71,22 +71,12 @@ __device__ __forceinline__ int sample_at(const uint8_t *row, int x, bool wide)
     return wide ? (int)reinterpret_cast<const uint16_t *>(row)[x] : (int)row[x];
 }
 
-// Eq. 7-12 on one sample of the staged tile (32-bit arithmetic).
-__device__ __forceinline__ int filter_one(const int *t, const int o[12], const Eff &e)
+// Per direction block and primary strength p: the scaled adjusted strength,
+// the primary shift, whether the weights are 3/3 (odd strength), and
+// whether the block's damping was raised to floor(log2 S_p) (section 3.2).
+__device__ __forceinline__ int pack_primary(int pri, int psh, bool odd, bool raised)
 {
-    const int x = t[0];
-    int sum = 0, mn = x, mx = x;
-#pragma unroll
-    for (int k = 0; k < 12; k++) {
-        const int p = t[o[k]];
-        const int q = p < 0 ? x : p;
-        const int f = k < 4 ? constrain(q - x, e.pri, e.psh) : constrain(q - x, e.sec, e.ssh);
-        const int w = k < 2 ? e.w0 : k < 4 ? e.w1 : k < 8 ? 2 : 1;
-        sum += w * f;
-        mn = min(mn, q);
-        mx = max(mx, q);
-    }
-    return min(mx, max(mn, x + round16(sum)));
+    return pri | (psh << 12) | ((int)odd << 20) | ((int)raised << 21);
 }
 
 __global__ void __launch_bounds__(kWThreads)
@@ -94,6 +84,7 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
                  const int32_t *__restrict__ vars, long long *dist_luma, long long *dist_chroma)
 {
     __shared__ WideSmem sm;
+    __shared__ int prim[64][16];
     const int tid = threadIdx.x, lane = tid & 31;
     const int blk = blockIdx.x, group = blockIdx.y;
     int fi = 0;
@@ -105,6 +96,9 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
     const int sh8 = F.bitdepth - 8;
     const bool filtered = group == 0 || F.chroma_format != 422;
     const int nplanes = group == 0 ? 1 : 2;
+    const bool chroma = group != 0;
+    const int bw = F.w >> 3;
+    const int Dbase = chroma ? F.damping - 1 : F.damping;
 
     // stage the planes (rec) of the group with the halo
     for (int k = 0; k < nplanes; k++) {
@@ -118,6 +112,17 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
                                             : -1;
         }
     }
+    // primary-strength constants per direction block (luma: after eq. 13)
+    for (int i = tid; i < 64 * 16; i += kWThreads) {
+        const int b = i >> 4, p = i & 15;
+        const int gby = fby * 8 + (b >> 3), gbx = fbx * 8 + (b & 7);
+        const int v = (gby * 8 < F.h && gbx * 8 < F.w) ? vars[F.map_start + gby * bw + gbx] : 0;
+        const int pri = chroma ? p : adjust_strength(p, v);
+        const int lp = pri ? ilog2(pri) : 0;
+        const bool raised = pri && Dbase < lp;
+        const int D = raised ? lp : Dbase;
+        prim[b][p] = pack_primary(pri << sh8, pri ? D - lp : 0, pri & 1, raised);
+    }
     if (tid < 64) sm.acc[tid] = 0;
     __syncthreads();
 
@@ -126,10 +131,8 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
     const int b8 = tid >> 2, part = tid & 3;
     const int by = b8 >> 3, bx = b8 & 7;
     const int gby = fby * 8 + by, gbx = fbx * 8 + bx;   // co-located luma 8x8 block
-    const int bw = F.w >> 3;
     const bool in_luma = gby * 8 < F.h && gbx * 8 < F.w;
     const int d = in_luma ? dirs[F.map_start + gby * bw + gbx] : 0;
-    const int var = in_luma ? vars[F.map_start + gby * bw + gbx] : 0;
     int o[12];
     for (int k = 0; k < 12; k++) {
         int dr, dc;
@@ -137,33 +140,84 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
         o[k] = dr * kTile + dc;
     }
     const unsigned long long pairs = allowed_pairs(F, group);
+    uint32_t pmask = 0;   // primaries with an allowed pair
+    for (int p = 0; p < 16; p++) pmask |= (uint32_t)(((pairs >> (4 * p)) & 15ull) != 0) << p;
+    // secondary shifts at the block's damping and at the raised one (3)
+    const int Dhi = Dbase < 3 ? 3 : Dbase;
 
-    for (int q = 0; q < 64; q++) {
-        if (!((pairs >> q) & 1)) continue;
-        const int p = q >> 2, s = sec_strength(q & 3);
-        const Eff e = make_eff(p, s, F.damping, group != 0, var, sh8);
-        long long sse = 0;   // per thread at most 32 samples x 4095^2
-        for (int k = 0; k < nplanes; k++) {
-            const PlaneView v = plane_view(F, group == 0 ? 0 : 1 + k);
-            const int rows = v.bs == 8 ? 2 : 1, cols = v.bs;
-            const int r0 = by * v.bs + part * rows, c0 = bx * v.bs;
-            for (int i = 0; i < rows; i++) {
-                const int gy = fby * v.fh + r0 + i;
-                if (r0 + i >= v.fh || gy >= v.h) break;
-                const uint8_t *srow = v.src + gy * v.src_pitch;
-                for (int j = 0; j < cols; j++) {
-                    const int gx = fbx * v.fw + c0 + j;
-                    if (c0 + j >= v.fw || gx >= v.w) break;
-                    const int *t = &sm.tile[k][(r0 + i + 2) * kTile + c0 + j + 2];
-                    const int y = filtered ? filter_one(t, o, e) : t[0];
-                    const int err = y - sample_at(srow, gx, wide);
-                    sse += (long long)(err * err);
+    // per candidate (p, s) the thread's squared error (at most 32 samples of
+    // 12 bits: below 2^31)
+    int acc[64];
+#pragma unroll
+    for (int q = 0; q < 64; q++) acc[q] = 0;
+    for (int k = 0; k < nplanes; k++) {
+        const PlaneView v = plane_view(F, group == 0 ? 0 : 1 + k);
+        const int rows = v.bs == 8 ? 2 : 1, cols = v.bs;
+        const int r0 = by * v.bs + part * rows, c0 = bx * v.bs;
+        for (int i = 0; i < rows; i++) {
+            const int gy = fby * v.fh + r0 + i;
+            if (r0 + i >= v.fh || gy >= v.h) break;
+            const uint8_t *srow = v.src + gy * v.src_pitch;
+            for (int j = 0; j < cols; j++) {
+                const int gx = fbx * v.fw + c0 + j;
+                if (c0 + j >= v.fw || gx >= v.w) break;
+                const int *t = &sm.tile[k][(r0 + i + 2) * kTile + c0 + j + 2];
+                const int x = t[0], src = sample_at(srow, gx, wide);
+                if (!filtered) {
+                    const int e = x - src;
+#pragma unroll
+                    for (int q = 0; q < 64; q++) acc[q] += e * e;
+                    continue;
+                }
+                int pv[12], mn = x, mx = x;
+#pragma unroll
+                for (int m = 0; m < 12; m++) {
+                    const int pm = t[o[m]];
+                    pv[m] = pm < 0 ? x : pm;   // outside the frame: adds nothing
+                    mn = min(mn, pv[m]);
+                    mx = max(mx, pv[m]);
+                }
+                // secondary sums for S_s = 1, 2, 4 at both dampings (eq. 8's
+                // sum splits into the two tap sets)
+                int qlo[4] = {0, 0, 0, 0}, qhi[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int si = 1; si < 4; si++) {
+                    const int ss = si == 3 ? 4 : si, S = ss << sh8, l2 = ss == 4 ? 2 : ss - 1;
+                    const int shl = max(0, Dbase - l2), shh = max(0, Dhi - l2);
+#pragma unroll
+                    for (int m = 4; m < 12; m++) {
+                        const int w = m < 8 ? 2 : 1;
+                        qlo[si] += w * constrain(pv[m] - x, S, shl);
+                        qhi[si] += w * constrain(pv[m] - x, S, shh);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < 16; p++) {
+                    if (!((pmask >> p) & 1)) continue;
+                    const int pc = prim[b8][p];
+                    const int S = pc & 0xfff, sh = (pc >> 12) & 0xff;
+                    const int w0 = (pc >> 20) & 1 ? 3 : 4, w1 = 6 - w0;
+                    const bool raised = (pc >> 21) & 1;
+                    const int P = w0 * (constrain(pv[0] - x, S, sh) + constrain(pv[1] - x, S, sh)) +
+                                  w1 * (constrain(pv[2] - x, S, sh) + constrain(pv[3] - x, S, sh));
+#pragma unroll
+                    for (int si = 0; si < 4; si++) {
+                        const int y = min(mx, max(mn, x + round16(P + (raised ? qhi[si] : qlo[si]))));
+                        const int e = y - src;
+                        acc[p * 4 + si] += e * e;
+                    }
                 }
             }
         }
+    }
+    // CTA sums: warp shuffles, then one shared atomic per warp and candidate
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, off);
-        if (lane == 0) atomicAdd(&sm.acc[q], (unsigned long long)sse);
+    for (int q = 0; q < 64; q++) {
+        int a = acc[q];
+        long long sum = a;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (lane == 0) atomicAdd(&sm.acc[q], (unsigned long long)sum);
     }
     __syncthreads();
     if (tid < 64) {
