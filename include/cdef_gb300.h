@@ -121,6 +121,14 @@ int cdef_ctx_destroy(cdef_ctx *ctx);
  * clear != 0 resets the word. */
 int cdef_ctx_status(cdef_ctx *ctx, int clear);
 
+/* The same status word without waiting: enqueues on cuda_stream a copy of
+ * it into *host_status (HOST memory; pinned, or the copy is not
+ * asynchronous), which holds it once the stream has passed this point.  0
+ * means no kernel-reported error; any other value is a nonzero status (read
+ * cdef_ctx_status for the code and to clear it).  CDEF_ERR_ARG for NULL
+ * arguments, CDEF_ERR_CUDA if the copy cannot be enqueued. */
+int cdef_ctx_status_async(cdef_ctx *ctx, int32_t *host_status, void *cuda_stream);
+
 /* Direction search, section 2, eq. 1-5 and Algorithm 1.
  * For every 8x8 block of the luma plane: the direction d in 0..7 that
  * maximises s_d (first maximum on ties) and the directional contrast

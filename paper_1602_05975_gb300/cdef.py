@@ -94,6 +94,7 @@ def load():
     L.cdef_ctx_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.cdef_ctx_set_stage_timing.argtypes = [vp, C.c_int]
     L.cdef_ctx_set_search_subset.argtypes = [vp, C.c_uint64, C.c_uint64]
+    L.cdef_ctx_status_async.argtypes = [vp, vp, vp]
     L.cdef_ctx_get_stage_times.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.cdef_search_strengths_coded.argtypes = [
         vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(vp), C.POINTER(i32),
@@ -107,7 +108,8 @@ def load():
                  "cdef_ctx_set_tuning", "cdef_ctx_get_tuning", "cdef_ctx_set_overlap",
                  "cdef_ctx_set_search_refine", "cdef_search_strengths_coded",
                  "cdef_ctx_set_search_metric", "cdef_ctx_set_stage_timing",
-                 "cdef_ctx_get_stage_times", "cdef_ctx_set_search_subset"):
+                 "cdef_ctx_get_stage_times", "cdef_ctx_set_search_subset",
+                 "cdef_ctx_status_async"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -281,6 +283,12 @@ class Context:
 
     def status(self, clear=True):
         return self._lib.cdef_ctx_status(self.handle, int(clear))
+
+    def status_async(self, host_status: torch.Tensor, stream=None):
+        """Enqueue a copy of the status word into host_status[0] (a pinned
+        int32 CPU tensor) on `stream`; read it once the stream is past it."""
+        _check(self._lib.cdef_ctx_status_async(self.handle, host_status.data_ptr(),
+                                               _stream_ptr(stream)), "cdef_ctx_status_async")
 
     def set_search_refine(self, max_passes: int):
         """Re-optimise the searched presets one at a time for at most

@@ -395,6 +395,19 @@ int cdef_ctx_status(cdef_ctx *ctx, int clear)
     return v ? CDEF_ERR_ARG : CDEF_OK;
 }
 
+int cdef_ctx_status_async(cdef_ctx *ctx, int32_t *host_status, void *cuda_stream)
+{
+    if (!ctx || !host_status) return CDEF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    if (cudaMemcpyAsync(host_status, ctx->status, sizeof(int), cudaMemcpyDeviceToHost,
+                        static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return CDEF_ERR_CUDA;
+    }
+    return CDEF_OK;
+}
+
 int cdef_find_dir(cdef_ctx *ctx, const cdef_plane *luma, int32_t bitdepth, uint8_t *dir,
                   int32_t *var, void *cuda_stream)
 {

@@ -350,6 +350,10 @@ class CudaBackend(Backend):
         self.free_bytes = 0
         self.held_bytes = 0
         self.host_out: dict = collections.defaultdict(list)
+        # status words of the batches in flight, copied back on the
+        # device-to-host stream (no synchronous call in the loop)
+        self.status_words = torch.zeros(256, dtype=torch.int32).pin_memory()
+        self.next_word = 0
 
     @staticmethod
     def key(req: Request):
@@ -431,25 +435,31 @@ class CudaBackend(Backend):
         ev_c = torch.cuda.Event()
         ev_c.record(self.comp)
         self.down.wait_event(ev_c)
+        word = self.status_words[self.next_word:self.next_word + 1]
+        self.next_word = (self.next_word + 1) % self.status_words.numel()
         with torch.cuda.stream(self.down):
             for r in reqs:
                 r.slot["host_out"][0].copy_(r.slot["flat_out"], non_blocking=True)
+        self.ctx.status_async(word, stream=self.down)
         ev_d = torch.cuda.Event()
         ev_d.record(self.down)
         # keep the host output reachable from the request once it is done
         for r in reqs:
             r.out = r.slot["host_out"]
-        return (ev_d, len(reqs))
+        return (ev_d, len(reqs), word)
 
     def poll(self, handle):
-        ev, n = handle
+        ev, n, word = handle
         if not ev.query():
             return None
         # The context's status word collects device-side parameter errors.
         # Requests are validated on the host before they are queued, so it
-        # stays 0; if it is ever set, the batch that saw it fails.
+        # stays 0; if it is ever set, the batch that saw it fails (and the
+        # word is read and cleared synchronously).
+        if int(word[0]) == 0:
+            return ["ok"] * n
         st = self.ctx.status()
-        return ["ok"] * n if st == 0 else [f"device status {st}"] * n
+        return [f"device status {st}"] * n
 
 
 def pack_frame(cdef, frame_planes, bitdepth: int):
