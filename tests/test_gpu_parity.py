@@ -178,8 +178,14 @@ def test_invalid_params_flagged(cdef, ctx):
     inp = cdef.frame_from_numpy(fr.rec, 8)
     out = cdef.alloc_frame(128, 64, 8, fill=0)
     ctx.status(clear=True)
-    cdef.cdef_filter_frame(ctx, inp, cdef.params_tensor(prm), out)
+    word = torch.full((1,), -7, dtype=torch.int32).pin_memory()
+    ctx.status_async(word)                                    # before: clean
     torch.cuda.synchronize()
+    assert int(word[0]) == 0
+    cdef.cdef_filter_frame(ctx, inp, cdef.params_tensor(prm), out)
+    ctx.status_async(word)                                    # after, in stream order
+    torch.cuda.synchronize()
+    assert int(word[0]) != 0
     assert ctx.status(clear=True) == -1
     y = out.to_numpy()[0]
     assert np.array_equal(y[:, 64:128], fr.rec[0][:, 64:128])  # block left unfiltered
