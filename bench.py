@@ -769,7 +769,7 @@ SERVE_WORKLOAD = dict(
          "8 GiB; continuous batching against one frame at a time",
     sizes=[(640, 360), (1280, 720), (1920, 1080), (3840, 2160)], bitdepths=(8, 10),
     requests=10000, rates=(0.5, 0.8, 1.0, 1.5), budget=8 << 30, contents=2, seed=0,
-    base_seed=4000, verify_requests=400, batch_bytes=256 << 20)
+    base_seed=4000, verify_requests=400, batch_bytes=256 << 20, inflight=3)
 
 
 def run_serve(args):
@@ -815,8 +815,10 @@ def run_serve(args):
     single_be.prewarm(shapes, 2)
 
     def batched(on_done=None):
-        return serve.Server(batched_be, budget, max_batch=cdef.MAX_BATCH, max_inflight=3,
-                            on_done=on_done, max_batch_bytes=W["batch_bytes"])
+        return serve.Server(batched_be, budget, max_batch=cdef.MAX_BATCH,
+                            max_inflight=args.inflight or W["inflight"], on_done=on_done,
+                            max_batch_bytes=(args.batch_mib << 20) if args.batch_mib
+                            else W["batch_bytes"])
 
     def one_at_a_time(on_done=None):
         return serve.Server(single_be, budget, max_batch=1, max_inflight=1, on_done=on_done)
@@ -882,6 +884,8 @@ def run_serve(args):
                    "batched_capacity": {q: bcap[q] for q in keys},
                    "one_at_a_time_capacity": {q: cap[q] for q in keys},
                    "one_at_a_time_capacity_fps": capacity, "budget_bytes": budget,
+                   "batch_bytes": (args.batch_mib << 20) if args.batch_mib else W["batch_bytes"],
+                   "inflight": args.inflight or W["inflight"],
                    "verified": f"{nv} requests served in mixed batches equal the "
                                f"single-frame path bit for bit",
                    "rates": rates},
@@ -909,6 +913,10 @@ def main():
                          "filter12: 8 4K 12-bit frames; search: batched strength search over "
                          "16 mixed frames; serve: the serving loop")
     ap.add_argument("--requests", type=int, default=0, help="serve: requests per rate")
+    ap.add_argument("--batch-mib", type=int, default=0,
+                    help="serve: byte cap of one batch in MiB (0: the workload's)")
+    ap.add_argument("--inflight", type=int, default=0,
+                    help="serve: batches on the device at once (0: the workload's)")
     ap.add_argument("--refine", type=int, default=0,
                     help="search: preset re-optimisation passes after the greedy search")
     ap.add_argument("--search-variant", default="sse",
