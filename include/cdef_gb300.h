@@ -14,6 +14,9 @@
  *    are copied) and 4:4:4 frames (chroma W x H: each chroma plane is
  *    filtered in 8x8 blocks with the chroma strengths and damping and the
  *    co-located luma direction).  The format follows from the plane sizes.
+ *    A 4:4:4 frame filtered without caller maps (dir = var = NULL) uses the
+ *    context's direction-map scratch: such calls on one context belong on
+ *    one stream (their launches are then ordered).
  *  - Samples are unsigned integers stored planar and row-major: uint8_t for
  *    bit depth 8, uint16_t (value in the low bits) for bit depths 10 and 12.
  *  - Plane memory is DEVICE memory owned by the caller.  `data` must be

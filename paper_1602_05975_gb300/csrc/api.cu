@@ -46,6 +46,9 @@ struct cdef_ctx {
     uint8_t *maps_dir;            // direction maps of 4:4:4 filtering
     int32_t *maps_var;
     size_t maps_blocks;
+    uint8_t *smaps_dir;           // direction maps of the wide strength search
+    int32_t *smaps_var;
+    size_t smaps_blocks;
 };
 
 namespace {
@@ -288,6 +291,8 @@ int cdef_ctx_destroy(cdef_ctx *ctx)
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->maps_dir) cudaFree(ctx->maps_dir);
     if (ctx->maps_var) cudaFree(ctx->maps_var);
+    if (ctx->smaps_dir) cudaFree(ctx->smaps_dir);
+    if (ctx->smaps_var) cudaFree(ctx->smaps_var);
     if (ctx->work) cudaFree(ctx->work);
     if (ctx->search_exec) cudaGraphExecDestroy(ctx->search_exec);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
@@ -473,29 +478,38 @@ int plane_pass(cdef_ctx *ctx, const cdef_frame *in, const cdef_plane &pin, const
     return cuda_status(launch_filter_single(b, ctx->status, work, overlap, s));
 }
 
-int ensure_maps(cdef_ctx *ctx, size_t blocks)
+// Direction maps of at least `blocks` 8x8 blocks in (dir, var, have), held
+// in the context's scratch budget.  The filter's 4:4:4 path and the wide
+// strength search keep separate maps, so that a search never overwrites
+// maps a filter launch on another stream still reads.
+int ensure_map_set(cdef_ctx *ctx, size_t blocks, uint8_t *&dir, int32_t *&var, size_t &have)
 {
-    if (ctx->maps_blocks >= blocks) return CDEF_OK;
+    if (have >= blocks) return CDEF_OK;
     const size_t bytes = blocks * (sizeof(uint8_t) + sizeof(int32_t));
-    const size_t old = ctx->maps_blocks * (sizeof(uint8_t) + sizeof(int32_t));
+    const size_t old = have * (sizeof(uint8_t) + sizeof(int32_t));
     if (ctx->budget && ctx->used - old + bytes > ctx->budget) return CDEF_ERR_NOMEM;
-    if (ctx->maps_var) cudaFree(ctx->maps_var);
-    if (ctx->maps_dir) cudaFree(ctx->maps_dir);
-    ctx->maps_var = nullptr;
-    ctx->maps_dir = nullptr;
+    if (var) cudaFree(var);
+    if (dir) cudaFree(dir);
+    var = nullptr;
+    dir = nullptr;
     ctx->used -= old;
-    ctx->maps_blocks = 0;
-    if (cudaMalloc(&ctx->maps_var, blocks * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&ctx->maps_dir, blocks) != cudaSuccess) {
+    have = 0;
+    if (cudaMalloc(&var, blocks * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&dir, blocks) != cudaSuccess) {
         cudaGetLastError();
-        if (ctx->maps_var) cudaFree(ctx->maps_var);
-        ctx->maps_var = nullptr;
-        ctx->maps_dir = nullptr;
+        if (var) cudaFree(var);
+        var = nullptr;
+        dir = nullptr;
         return CDEF_ERR_NOMEM;
     }
-    ctx->maps_blocks = blocks;
+    have = blocks;
     ctx->used += bytes;
     return CDEF_OK;
+}
+
+int ensure_maps(cdef_ctx *ctx, size_t blocks)
+{
+    return ensure_map_set(ctx, blocks, ctx->maps_dir, ctx->maps_var, ctx->maps_blocks);
 }
 
 int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params,
@@ -782,9 +796,12 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
     int32_t *wide_vars = nullptr;
     if (wide) {
         // direction maps for every frame of the call
-        if ((rc = ensure_maps(ctx, maps))) { delete b; return rc; }
-        wide_dirs = ctx->maps_dir;
-        wide_vars = ctx->maps_var;
+        if ((rc = ensure_map_set(ctx, maps, ctx->smaps_dir, ctx->smaps_var, ctx->smaps_blocks))) {
+            delete b;
+            return rc;
+        }
+        wide_dirs = ctx->smaps_dir;
+        wide_vars = ctx->smaps_var;
         tune = {1, 1};   // one CTA per filter block and plane group
     } else if (ctx->metric == CDEF_METRIC_EQ14) {
         if (coded) { delete b; return CDEF_ERR_ARG; }
