@@ -836,3 +836,56 @@ def test_search_formats_subset_and_rejections(cdef, ctx, ref):
     finally:
         ctx.set_search_metric("sse")
     assert ctx.status() == 0
+
+
+def test_filter_frames_maximum_batch(cdef, ctx, ref):
+    """48 frames (the batch limit) of mixed sizes and bit depths in one
+    launch each equal the oracle; 49 frames are refused."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(1160)
+    sizes = [(64, 64), (136, 72), (72, 136), (200, 40), (8, 8), (128, 64)]
+    frames, ins, outs, prms = [], [], [], []
+    for i in range(48):
+        w, h = sizes[i % len(sizes)]
+        bd = (8, 10, 12)[i % 3]
+        f = synth.make_frame(w, h, bd, 32, seed=1160 + i)
+        frames.append(f)
+        ins.append(cdef.frame_from_numpy(f.rec, bd))
+        outs.append(cdef.alloc_frame(w, h, bd, fill=0))
+        prms.append(cdef.params_tensor(f.params))
+    cdef.cdef_filter_frames(ctx, ins, prms, outs)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    for f, o in zip(frames, outs):
+        _assert_frames_equal(o.to_numpy(), ref.filter_frame(*f.rec, f.bitdepth, f.params))
+    with pytest.raises(cdef.CdefError):
+        cdef.cdef_filter_frames(ctx, ins + ins[:1], prms + prms[:1], outs + [cdef.alloc_frame(64, 64, 8)])
+
+
+def test_search_maximum_batch(cdef, ctx, ref):
+    """48 frames in one search call equal 48 oracle searches; 49 are refused."""
+    from paper_1602_05975_gb300 import synth
+    sizes = [(64, 64), (136, 72), (72, 136), (128, 64)]
+    frames = [synth.make_frame(*sizes[i % 4], (8, 10)[i % 2], None, seed=1170 + i) for i in range(48)]
+    recs = [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames]
+    srcs = [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+    damping = [3 + i % 4 for i in range(48)]
+    lambdas = [f.q * f.q for f in frames]
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(nb * 64, dtype=torch.int64, device="cuda")
+    res = cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc)
+    assert ctx.status() == 0
+    o0 = 0
+    for f, r, d, lam in zip(frames, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths(f.rec, f.src, f.bitdepth, d, lam)
+        assert np.array_equal(dl[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_luma"])
+        assert np.array_equal(dc[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_chroma"])
+        assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"]
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
+    with pytest.raises(cdef.CdefError):
+        cdef.cdef_search_strengths(ctx, recs + recs[:1], srcs + srcs[:1], damping + [4],
+                                   lambdas + [16], ids)
