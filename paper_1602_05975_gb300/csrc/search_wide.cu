@@ -22,7 +22,7 @@ namespace {
 using tile::tap_rc;
 
 constexpr int kWThreads = 256;
-constexpr int kTile = 68;   // 64 + 2 x 2 halo
+constexpr int kTile = 69;   // 64 + 2 x 2 halo, plus one: an odd pitch spreads the rows over the banks
 
 struct WideSmem {
     int tile[2][kTile * kTile];   // the group's planes (luma: one; chroma: U and V)
