@@ -969,6 +969,100 @@ int cdef_ref_distortion_format(int w, int h, int bitdepth, int damping, int form
     return 0;
 }
 
+/* The 128-combination tables (reading R21) for chroma format 420, 422 or
+ * 444 at any bit depth (reading R25): as cdef_ref_distortion_coded, with
+ * the chroma geometry of cdef_ref_distortion_format (4:2:2 chroma is never
+ * filtered, so all its entries are the unfiltered error).  A pixel of the
+ * 8x8 (4:2:0 chroma: 4x4) block j is filtered when the filter block has
+ * coded residual and (j's co-located luma block is coded or the skip bit k
+ * is set); (0, 0) with k set stands for (19, 7). */
+static int64_t block_sse_coded_g(const uint16_t *rec, ptrdiff_t rs, const uint16_t *src,
+                                 ptrdiff_t ss, int pw, int ph, int sub, int chroma, int filtered,
+                                 int bitdepth, int fby, int fbx, int pri, int sec, int k,
+                                 int damping, const uint8_t *dir, const int32_t *var, int bw,
+                                 int fbw, int fbh, const uint8_t *coded, int fb_coded)
+{
+    int bs = 8 >> sub;
+    int64_t sse = 0;
+    for (int i = fby * fbh; i < (fby + 1) * fbh && i < ph; i++) {
+        for (int j = fbx * fbw; j < (fbx + 1) * fbw && j < pw; j++) {
+            int b8 = (i / bs) * bw + (j / bs);
+            int on = filtered && fb_coded && (!coded || coded[b8] || k);
+            int64_t yv = rec[(ptrdiff_t)i * rs + j];
+            if (on) {
+                cdef_ref_eff_params e;
+                cdef_ref_block_params(pri, sec, damping, chroma, bitdepth, chroma ? 0 : var[b8], &e);
+                yv = cdef_ref_filter_sample(rec, pw, ph, rs, i, j, dir[b8], &e);
+            }
+            int64_t err = yv - (int64_t)src[(ptrdiff_t)i * ss + j];
+            sse += err * err;
+        }
+    }
+    return sse;
+}
+
+int cdef_ref_distortion_coded_format(int w, int h, int bitdepth, int damping, int format,
+                                     const uint16_t *ry, ptrdiff_t rys,
+                                     const uint16_t *ru, ptrdiff_t rus,
+                                     const uint16_t *rv, ptrdiff_t rvs,
+                                     const uint16_t *sy, ptrdiff_t sys,
+                                     const uint16_t *su, ptrdiff_t sus,
+                                     const uint16_t *sv, ptrdiff_t svs,
+                                     const uint8_t *coded, int64_t *dist_luma,
+                                     int64_t *dist_chroma, uint8_t *skipped)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    if (damping < 3 || damping > 6 || (format != 420 && format != 422 && format != 444))
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    uint8_t *dir = (uint8_t *)malloc((size_t)bw * bh);
+    int32_t *var = (int32_t *)malloc((size_t)bw * bh * sizeof(int32_t));
+    if (!dir || !var) {
+        free(dir);
+        free(var);
+        return -1;
+    }
+    cdef_ref_find_dir(ry, w, h, rys, bitdepth, dir, var);
+    int cw = format == 444 ? w : w / 2, ch = format == 420 ? h / 2 : h;
+    int csub = format == 444 ? 0 : 1;
+    int cfw = format == 444 ? 64 : 32, cfh = format == 420 ? 32 : 64;
+    int cfilt = format != 422;
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    for (int fby = 0; fby < fb_rows; fby++) {
+        for (int fbx = 0; fbx < fb_cols; fbx++) {
+            int b = fby * fb_cols + fbx;
+            int fb_coded = fb_has_coded(coded, bw, bh, fby, fbx);
+            skipped[b] = (uint8_t)!fb_coded;
+            for (int k = 0; k < 2; k++) {
+                for (int p = 0; p < 16; p++) {
+                    for (int s = 0; s < 4; s++) {
+                        int q = k * 64 + p * 4 + s;
+                        int pri = p, sec = sec_values[s];
+                        if (k && p == 0 && s == 0) {
+                            pri = 19;
+                            sec = 7;
+                        }
+                        dist_luma[b * 128 + q] = block_sse_coded_g(
+                            ry, rys, sy, sys, w, h, 0, 0, 1, bitdepth, fby, fbx, pri, sec, k,
+                            damping, dir, var, bw, 64, 64, coded, fb_coded);
+                        dist_chroma[b * 128 + q] =
+                            block_sse_coded_g(ru, rus, su, sus, cw, ch, csub, 1, cfilt, bitdepth,
+                                              fby, fbx, pri, sec, k, damping, dir, var, bw, cfw,
+                                              cfh, coded, fb_coded) +
+                            block_sse_coded_g(rv, rvs, sv, svs, cw, ch, csub, 1, cfilt, bitdepth,
+                                              fby, fbx, pri, sec, k, damping, dir, var, bw, cfw,
+                                              cfh, coded, fb_coded);
+                    }
+                }
+            }
+        }
+    }
+    free(dir);
+    free(var);
+    return 0;
+}
+
 /* Chroma formats other than 4:2:0 (section 4, last paragraph; reading R25):
  *   format 422: chroma planes are w/2 x h; their subsampling differs
  *               horizontally and vertically, so chroma is not filtered (the

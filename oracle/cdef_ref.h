@@ -206,6 +206,19 @@ int cdef_ref_distortion_format(int w, int h, int bitdepth, int damping, int form
                                const uint16_t *sv, ptrdiff_t svs,
                                int64_t *dist_luma, int64_t *dist_chroma);
 
+/* The 128-combination tables (reading R21) for chroma format 420, 422 or
+ * 444 at bit depths 8-12 (reading R25); skipped[b] as
+ * cdef_ref_distortion_coded. */
+int cdef_ref_distortion_coded_format(int w, int h, int bitdepth, int damping, int format,
+                                     const uint16_t *ry, ptrdiff_t rys,
+                                     const uint16_t *ru, ptrdiff_t rus,
+                                     const uint16_t *rv, ptrdiff_t rvs,
+                                     const uint16_t *sy, ptrdiff_t sys,
+                                     const uint16_t *su, ptrdiff_t sus,
+                                     const uint16_t *sv, ptrdiff_t svs,
+                                     const uint8_t *coded, int64_t *dist_luma,
+                                     int64_t *dist_chroma, uint8_t *skipped);
+
 /* Section 5, eq. 14 (readings R22-R24 in cdef_ref.c): per filter block, 64
  * luma and 64 chroma entries sum_8x8 round(256 * D_8x8). */
 int cdef_ref_distortion_eq14(int w, int h, int bitdepth, int damping,

@@ -120,6 +120,9 @@ def lib():
         L.cdef_ref_distortion_format.argtypes = (
             [C.c_int] * 5 + [_u16p, C.c_ssize_t] * 6 + [_i64p, _i64p])
         L.cdef_ref_distortion_format.restype = C.c_int
+        L.cdef_ref_distortion_coded_format.argtypes = (
+            [C.c_int] * 5 + [_u16p, C.c_ssize_t] * 6 + [C.c_void_p, _i64p, _i64p, _u8p])
+        L.cdef_ref_distortion_coded_format.restype = C.c_int
         L.cdef_ref_distortion_eq14.argtypes = (
             [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6 + [_i64p, _i64p])
         L.cdef_ref_distortion_eq14.restype = C.c_int
@@ -337,6 +340,34 @@ def distortion_format(rec, src, bitdepth: int, damping: int, fmt: int):
     if rc != 0:
         raise ValueError("oracle rejected distortion_format arguments")
     return dl.reshape(nb, 64), dc.reshape(nb, 64)
+
+
+def distortion_coded_format(rec, src, bitdepth: int, damping: int, fmt: int, coded=None):
+    """The 128-combination tables (reading R21) for chroma format 420, 422
+    or 444 at any bit depth, and the skipped-block flags."""
+    ry, ru, rv = (_u16(p) for p in rec)
+    sy, su, sv = (_u16(p) for p in src)
+    h, w = ry.shape
+    nb = ((h + 63) // 64) * ((w + 63) // 64)
+    cod = None if coded is None else np.ascontiguousarray(coded, dtype=np.uint8)
+    dl = np.zeros(nb * 128, np.int64)
+    dc = np.zeros(nb * 128, np.int64)
+    sk = np.zeros(nb, np.uint8)
+    rc = lib().cdef_ref_distortion_coded_format(
+        w, h, bitdepth, damping, fmt, ry, w, ru, ru.shape[1], rv, rv.shape[1],
+        sy, w, su, su.shape[1], sv, sv.shape[1], None if cod is None else cod.ctypes.data,
+        dl, dc, sk)
+    if rc != 0:
+        raise ValueError("oracle rejected distortion_coded_format arguments")
+    return dl.reshape(nb, 128), dc.reshape(nb, 128), sk
+
+
+def search_strengths_coded_format(rec, src, bitdepth: int, damping: int, lam: int, fmt: int,
+                                  coded=None, refine_passes: int = 0):
+    dl, dc, sk = distortion_coded_format(rec, src, bitdepth, damping, fmt, coded)
+    out = select_presets_general(dl, dc, 128, sk, lam, refine_passes)
+    out.update(dist_luma=dl, dist_chroma=dc, skipped=sk)
+    return out
 
 
 def search_strengths_format(rec, src, bitdepth: int, damping: int, lam: int, fmt: int,

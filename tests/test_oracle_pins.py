@@ -1085,6 +1085,42 @@ def test_format_tables_are_sse_of_decoder_output(ref, fmt, bd):
         assert (dc == dc[:, :1]).all()      # chroma is not filtered: one value per block
 
 
+@pytest.mark.parametrize("fmt,bd", [(444, 8), (422, 10), (420, 12)])
+def test_coded_format_tables_are_sse_of_decoder_output(ref, fmt, bd):
+    """Readings R21 and R25 together: each of the 128 entries is the squared
+    error of what the filter oracle outputs with that preset (skip-condition
+    bit included) and the coded-residual map; blocks without residual are
+    flagged and keep the unfiltered error."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(78)
+    if fmt == 420:
+        f = synth.make_frame(136, 72, bd, 32, seed=79)
+        planes, src = f.rec, f.src
+    else:
+        f, u, v, _ = _format_frame(fmt, w=136, h=72, bd=bd, seed=80)
+        planes, src = (f.rec[0], u, v), _format_src(f, u, v, 81)
+    coded = (rng.random((9, 17)) < 0.5).astype(np.uint8)
+    coded[:8, 8:16] = 0                                   # filter block 1: no residual
+    dl, dc, sk = ref.distortion_coded_format(planes, src, bd, 5, fmt, coded)
+    assert list(sk) == [0, 1, 0, 0, 0, 0]
+    params = np.zeros(f.params.shape, np.uint8)
+    params[..., 4] = 5
+    for q in (0, 9, 63, 64, 77, 127):
+        k, p, s = q >> 6, (q >> 2) & 15, (0, 1, 2, 4)[q & 3]
+        params[..., 0] = params[..., 2] = p
+        params[..., 1] = params[..., 3] = s
+        params[..., 5] = 3 * k                            # the same bit for both groups
+        out = ref.filter_frame_format(*planes, bd, params, fmt, coded)
+        for b in range(dl.shape[0]):
+            by, bx = divmod(b, f.params.shape[1])
+            ly = np.s_[by * 64:(by + 1) * 64, bx * 64:(bx + 1) * 64]
+            el = int(((out[0][ly].astype(np.int64) - src[0][ly]) ** 2).sum())
+            cy, cx = ((64, 64) if fmt == 444 else (64, 32) if fmt == 422 else (32, 32))
+            cs = np.s_[by * cy:(by + 1) * cy, bx * cx:(bx + 1) * cx]
+            ec = sum(int(((out[c][cs].astype(np.int64) - src[c][cs]) ** 2).sum()) for c in (1, 2))
+            assert dl[b, q] == el and dc[b, q] == ec, (fmt, bd, q, b)
+
+
 def test_unknown_format_rejected(ref):
     f, u, v, params = _format_frame(444, seed=63)
     with pytest.raises(ValueError):
