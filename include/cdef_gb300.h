@@ -253,8 +253,9 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
  *   dist_luma,
  *   dist_chroma  : DEVICE, sum_i B_i * 128 int64 each, or both NULL
  *   presets      : HOST, n*8 entries (first npresets[i] of frame i valid)
- * Frames: 8 or 10-bit 4:2:0 only (CDEF_ERR_ARG for 4:2:2, 4:4:4 or 12-bit
- * frames).  Synchronises the stream before returning. */
+ * Frames: as cdef_search_strengths (4:2:2, 4:4:4 and 12-bit frames through
+ * the 32-bit path; 4:2:2 chroma entries are the unfiltered error).
+ * Synchronises the stream before returning. */
 int cdef_search_strengths_coded(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
                                 const cdef_frame *src, const uint8_t *const *coded,
                                 const int32_t *damping, const int64_t *lambda,

@@ -731,7 +731,7 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
     bool wide = false;
     for (int i = 0; i < n; i++)
         if (rec[i].bitdepth > 10 || chroma_format(&rec[i]) != 420) wide = true;
-    if (wide && (coded || ctx->metric == CDEF_METRIC_EQ14)) { delete b; return CDEF_ERR_ARG; }
+    if (wide && ctx->metric == CDEF_METRIC_EQ14) { delete b; return CDEF_ERR_ARG; }
     int total = 0, rc = CDEF_OK;
     size_t maps = 0;
     for (int i = 0; i < n && rc == CDEF_OK; i++) {

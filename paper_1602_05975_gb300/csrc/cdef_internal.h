@@ -164,8 +164,11 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
 // Section 5's tables for 4:2:2, 4:4:4 and 12-bit frames (32-bit arithmetic
 // per sample): the direction maps of every frame into `dirs` / `vars` (at
 // each frame's map_start), then one CTA per filter block and plane group.
+// `skipped` non-null: the 128-combination tables over each frame's coded
+// map (one flag per filter block written); null: 64 combinations.
 cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *vars,
-                               long long *dist_luma, long long *dist_chroma, cudaStream_t s);
+                               long long *dist_luma, long long *dist_chroma, uint8_t *skipped,
+                               cudaStream_t s);
 // The preset selection alone (one cooperative launch); `ctl` is the control
 // block that follows `tot` in the scratch.
 // `width`: combinations per plane group in the tables (64 or 128; presets

@@ -850,12 +850,13 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     if (e != cudaSuccess) return e;
     const int per_sm = tune.ctas_per_sm;
     if (wide_dirs) {   // 4:2:2, 4:4:4 or 12-bit frames
-        e = launch_search_wide(b, wide_dirs, wide_vars, dist_luma, dist_chroma, s);
+        e = launch_search_wide(b, wide_dirs, wide_vars, dist_luma, dist_chroma, skipped, s);
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
         if (e != cudaSuccess) return e;
-        void *ctl = tot + (size_t)b.n * 4096;
+        const int width = skipped ? 128 : 64;
+        void *ctl = tot + (size_t)b.n * width * width;
         e = launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
-                           refine_passes, 64, nullptr, s);
+                           refine_passes, width, skipped, s);
         return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
     }
     if (tune.groups == 8) {   // eq. 14 tables

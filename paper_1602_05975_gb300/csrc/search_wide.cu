@@ -79,11 +79,19 @@ __device__ __forceinline__ int pack_primary(int pri, int psh, bool odd, bool rai
     return pri | (psh << 12) | ((int)odd << 20) | ((int)raised << 21);
 }
 
+// kCoded: the 128-combination tables of section 5 with section 4's skip
+// semantics: per candidate the error over every sample and over the samples
+// of 8x8 blocks without coded residual (the threads of such a block), the
+// unfiltered error likewise, and the (19, 7) preset's error; the entries
+// with the skip bit clear leave the uncoded blocks unfiltered.
+template <bool kCoded>
 __global__ void __launch_bounds__(kWThreads)
 dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__restrict__ dirs,
-                 const int32_t *__restrict__ vars, long long *dist_luma, long long *dist_chroma)
+                 const int32_t *__restrict__ vars, long long *dist_luma, long long *dist_chroma,
+                 uint8_t *skipped)
 {
     __shared__ WideSmem sm;
+    __shared__ unsigned long long acc_unc[64], base_sums[4];   // uncoded part; unfiltered, (19, 7)
     __shared__ int prim[64][16];
     const int tid = threadIdx.x, lane = tid & 31;
     const int blk = blockIdx.x, group = blockIdx.y;
@@ -123,7 +131,11 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
         const int D = raised ? lp : Dbase;
         prim[b][p] = pack_primary(pri << sh8, pri ? D - lp : 0, pri & 1, raised);
     }
-    if (tid < 64) sm.acc[tid] = 0;
+    if (tid < 64) {
+        sm.acc[tid] = 0;
+        acc_unc[tid] = 0;
+    }
+    if (tid < 4) base_sums[tid] = 0;
     __syncthreads();
 
     // four threads per direction block: 8x8 blocks (two rows each) or 4x4
@@ -139,6 +151,15 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
         tap_rc(d, k, dr, dc);
         o[k] = dr * kTile + dc;
     }
+    // section 4: the coded-residual flag of the thread's (co-located luma)
+    // 8x8 block, and whether the filter block has any
+    const int cflag = kCoded ? (in_luma && F.coded[gby * bw + gbx] != 0) : 1;
+    const bool any_coded = kCoded ? __syncthreads_or(cflag) != 0 : true;
+    if (kCoded && group == 0 && tid == 0) skipped[blk] = (uint8_t)!any_coded;
+    // the (19, 7) preset of the block (section 4), for the skip-bit-set (0, 0)
+    // entry
+    const Eff e19 = make_eff(19, 7, F.damping, chroma,
+                             chroma ? 0 : (in_luma ? vars[F.map_start + gby * bw + gbx] : 0), sh8);
     const unsigned long long pairs = allowed_pairs(F, group);
     uint32_t pmask = 0;   // primaries with an allowed pair
     for (int p = 0; p < 16; p++) pmask |= (uint32_t)(((pairs >> (4 * p)) & 15ull) != 0) << p;
@@ -147,7 +168,7 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
 
     // per candidate (p, s) the thread's squared error (at most 32 samples of
     // 12 bits: below 2^31)
-    int acc[64];
+    int acc[64], acc19 = 0, accu = 0;   // accu: the unfiltered error
 #pragma unroll
     for (int q = 0; q < 64; q++) acc[q] = 0;
     for (int k = 0; k < nplanes; k++) {
@@ -163,10 +184,12 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
                 if (c0 + j >= v.fw || gx >= v.w) break;
                 const int *t = &sm.tile[k][(r0 + i + 2) * kTile + c0 + j + 2];
                 const int x = t[0], src = sample_at(srow, gx, wide);
+                const int eu = x - src;
+                accu += eu * eu;
                 if (!filtered) {
-                    const int e = x - src;
 #pragma unroll
-                    for (int q = 0; q < 64; q++) acc[q] += e * e;
+                    for (int q = 0; q < 64; q++) acc[q] += eu * eu;
+                    acc19 += eu * eu;
                     continue;
                 }
                 int pv[12], mn = x, mx = x;
@@ -191,6 +214,17 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
                         qhi[si] += w * constrain(pv[m] - x, S, shh);
                     }
                 }
+                if (kCoded) {   // the (19, 7) preset
+                    int P = 0, Q = 0;
+#pragma unroll
+                    for (int m = 0; m < 4; m++)
+                        P += (m < 2 ? e19.w0 : e19.w1) * constrain(pv[m] - x, e19.pri, e19.psh);
+#pragma unroll
+                    for (int m = 4; m < 12; m++)
+                        Q += (m < 8 ? 2 : 1) * constrain(pv[m] - x, e19.sec, e19.ssh);
+                    const int e = min(mx, max(mn, x + round16(P + Q))) - src;
+                    acc19 += e * e;
+                }
 #pragma unroll
                 for (int p = 0; p < 16; p++) {
                     if (!((pmask >> p) & 1)) continue;
@@ -211,25 +245,53 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
         }
     }
     // CTA sums: warp shuffles, then one shared atomic per warp and candidate
+    // (with the skip semantics also the uncoded blocks' part)
 #pragma unroll
     for (int q = 0; q < 64; q++) {
-        int a = acc[q];
-        long long sum = a;
+        long long sum = acc[q], unc = kCoded && !cflag ? acc[q] : 0;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-        if (lane == 0) atomicAdd(&sm.acc[q], (unsigned long long)sum);
+        for (int off = 16; off > 0; off >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, off);
+            if (kCoded) unc += __shfl_xor_sync(0xffffffffu, unc, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&sm.acc[q], (unsigned long long)sum);
+            if (kCoded) atomicAdd(&acc_unc[q], (unsigned long long)unc);
+        }
+    }
+    if (kCoded) {
+        long long v[3] = {accu, cflag ? 0 : accu, acc19};
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+            if (lane == 0) atomicAdd(&base_sums[j], (unsigned long long)v[j]);
+        }
     }
     __syncthreads();
-    if (tid < 64) {
-        long long *out = (group == 0 ? dist_luma : dist_chroma) + (int64_t)blk * 64;
-        out[tid] = ((pairs >> tid) & 1) ? (long long)sm.acc[tid] : 0;
+    if (!kCoded) {
+        if (tid < 64) {
+            long long *out = (group == 0 ? dist_luma : dist_chroma) + (int64_t)blk * 64;
+            out[tid] = ((pairs >> tid) & 1) ? (long long)sm.acc[tid] : 0;
+        }
+    } else if (tid < 128) {
+        // q = k * 64 + p * 4 + s
+        const int q = tid & 63, k = tid >> 6;
+        const long long base = (long long)base_sums[0], base_unc = (long long)base_sums[1];
+        long long v;
+        if (!any_coded) v = base;                                   // never filtered
+        else if (k) v = q == 0 ? (long long)base_sums[2] : (long long)sm.acc[q];
+        else v = q == 0 ? base : (long long)sm.acc[q] - (long long)acc_unc[q] + base_unc;
+        long long *out = (group == 0 ? dist_luma : dist_chroma) + (int64_t)blk * 128;
+        out[tid] = ((pairs >> q) & 1) ? v : 0;
     }
 }
 
 }  // namespace
 
 cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *vars,
-                               long long *dist_luma, long long *dist_chroma, cudaStream_t s)
+                               long long *dist_luma, long long *dist_chroma, uint8_t *skipped,
+                               cudaStream_t s)
 {
     for (int i = 0; i < b.n; i++) {
         const SearchFrameDev &F = b.f[i];
@@ -237,8 +299,12 @@ cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *var
                                               dirs + F.map_start, vars + F.map_start, s);
         if (e != cudaSuccess) return e;
     }
-    dist_wide_kernel<<<dim3(b.total_blocks, 2), kWThreads, 0, s>>>(b, dirs, vars, dist_luma,
-                                                                   dist_chroma);
+    if (skipped)
+        dist_wide_kernel<true><<<dim3(b.total_blocks, 2), kWThreads, 0, s>>>(
+            b, dirs, vars, dist_luma, dist_chroma, skipped);
+    else
+        dist_wide_kernel<false><<<dim3(b.total_blocks, 2), kWThreads, 0, s>>>(
+            b, dirs, vars, dist_luma, dist_chroma, nullptr);
     return cudaGetLastError();
 }
 

@@ -802,8 +802,8 @@ def test_search_formats_parity(cdef, ctx, ref, passes):
 
 @pytest.mark.gpu
 def test_search_formats_subset_and_rejections(cdef, ctx, ref):
-    """The low-complexity subset in the wide tables; the 128-combination
-    search and eq. 14 stay 8/10-bit 4:2:0 (CDEF_ERR_ARG otherwise)."""
+    """The low-complexity subset in the wide tables; eq. 14 stays 8/10-bit
+    4:2:0 (CDEF_ERR_ARG otherwise)."""
     f, r, s_ = _format_search_frame(cdef, 444, 136, 72, 8, 1150)
     rec, src = cdef.frame_from_numpy(r, 8), cdef.frame_from_numpy(s_, 8)
     nb = f.params.shape[0] * f.params.shape[1]
@@ -825,10 +825,6 @@ def test_search_formats_subset_and_rejections(cdef, ctx, ref):
     assert np.array_equal(gl[:, cl], dlo[:, cl]) and (gl[:, ~cl] == 0).all()
     assert np.array_equal(gc[:, cc], dco[:, cc]) and (gc[:, ~cc] == 0).all()
     assert res[0]["cost"] == o["cost"] and res[0]["npresets"] == o["npresets"]
-    with pytest.raises(cdef.CdefError):
-        cdef.cdef_search_strengths_coded(ctx, [rec], [src],
-                                         [torch.ones(nb * 64, dtype=torch.uint8, device="cuda")],
-                                         [5], [300], ids)
     ctx.set_search_metric("eq14")
     try:
         with pytest.raises(cdef.CdefError):
@@ -889,3 +885,46 @@ def test_search_maximum_batch(cdef, ctx, ref):
     with pytest.raises(cdef.CdefError):
         cdef.cdef_search_strengths(ctx, recs + recs[:1], srcs + srcs[:1], damping + [4],
                                    lambdas + [16], ids)
+
+
+@pytest.mark.gpu
+def test_search_coded_formats_parity(cdef, ctx, ref):
+    """The 128-combination search over 4:4:4, 4:2:2 and 12-bit frames (with
+    a 4:2:0 frame in the same call, so the whole call takes the 32-bit
+    path): tables, skipped blocks, presets, N, J and ids equal the oracle's."""
+    specs = [(444, 136, 72, 8, 1180), (422, 200, 136, 10, 1181), (420, 136, 72, 12, 1182),
+             (420, 128, 64, 8, 1183)]
+    frames = [_format_search_frame(cdef, *sp) for sp in specs]
+    rng = np.random.default_rng(1184)
+    maps = []
+    for f, _, _ in frames:
+        m = (rng.random((f.height // 8, f.width // 8)) < 0.5).astype(np.uint8)
+        m[:8, :8] = 0                                       # first filter block: no residual
+        maps.append(m)
+    damping, lambdas = [5, 4, 3, 6], [64, 512, 4096, 0]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f, _, _ in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.full((nb * 128,), -1, dtype=torch.int64, device="cuda")
+    dc = torch.full((nb * 128,), -1, dtype=torch.int64, device="cuda")
+    ctx.set_search_refine(2)
+    try:
+        res = cdef.cdef_search_strengths_coded(
+            ctx, [cdef.frame_from_numpy(r, f.bitdepth) for f, r, _ in frames],
+            [cdef.frame_from_numpy(s_, f.bitdepth) for f, _, s_ in frames],
+            [torch.from_numpy(m.reshape(-1)).cuda() for m in maps], damping, lambdas, ids, dl, dc)
+    finally:
+        ctx.set_search_refine(0)
+    assert ctx.status() == 0
+    o0 = 0
+    for (f, r, s_), sp, m, rr, d, lam in zip(frames, specs, maps, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths_coded_format(r, s_, f.bitdepth, d, lam, sp[0], m, 2)
+        assert np.array_equal(dl[o0 * 128:(o0 + b) * 128].cpu().numpy().reshape(b, 128),
+                              o["dist_luma"])
+        assert np.array_equal(dc[o0 * 128:(o0 + b) * 128].cpu().numpy().reshape(b, 128),
+                              o["dist_chroma"])
+        assert rr["npresets"] == o["npresets"] and rr["cost"] == o["cost"]
+        assert [cdef.preset_index_coded(p) for p in rr["presets"][:rr["npresets"]]] == \
+            [int(t) for t in o["presets"][:o["npresets"]]]
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
