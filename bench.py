@@ -558,15 +558,15 @@ SEARCH_WORKLOAD = dict(
 # the (19, 7) preset's 12 taps and the uncoded part's accumulation per
 # candidate (1).  Per luma 8x8 block: the direction search as in the filter.
 def search_ops_per_sample(variant: str) -> int:
-    per_cand = {"sse": 8, "eq14": 11, "coded": 9, "444": 8, "12bit": 8}[variant]
-    extra = 12 * 8 if variant == "coded" else 0
+    per_cand = {"sse": 8, "eq14": 11, "coded": 9, "444": 8, "12bit": 8, "444coded": 9}[variant]
+    extra = 12 * 8 if variant in ("coded", "444coded") else 0
     return 16 * 4 * 8 + 3 * 8 * 8 + 24 + 64 * per_cand + extra
 
 
 def search_ops(frames, variant: str) -> int:
     ops = 0
     for f in frames:
-        cw, ch = (f.width, f.height) if variant == "444" else (f.width // 2, f.height // 2)
+        cw, ch = (f.width, f.height) if variant.startswith("444") else (f.width // 2, f.height // 2)
         samples = f.width * f.height + 2 * cw * ch
         ops += samples * search_ops_per_sample(variant) + (f.width // 8) * (f.height // 8) * (
             376 + 124 + 7 + 64 + 1)
@@ -582,7 +582,9 @@ def _oracle_search(task):
     bd, fmt = search_variant_format(variant)
     f = synth.make_frame(w, h, bd, None, seed, fmt)
     t = time.process_time()
-    if variant in ("444", "12bit"):
+    if variant == "444coded":
+        ref.search_strengths_coded_format(f.rec, f.src, bd, damping, lam, fmt, coded, passes)
+    elif variant in ("444", "12bit"):
         ref.search_strengths_format(f.rec, f.src, bd, damping, lam, fmt, passes)
     elif variant == "eq14":
         ref.search_strengths_eq14(f.rec, f.src, 8, damping, lam, passes)
@@ -591,12 +593,12 @@ def _oracle_search(task):
     else:
         ref.search_strengths(f.rec, f.src, 8, damping, lam, passes)
     blocks = -(-w // 64) * -(-h // 64)
-    return blocks * 2 * (128 if variant == "coded" else 64), time.process_time() - t
+    return blocks * 2 * (128 if variant.endswith("coded") else 64), time.process_time() - t
 
 
 def search_variant_format(variant: str):
     """(bit depth, chroma format) of the search workload's frames."""
-    return {"444": (8, 444), "12bit": (12, 420)}.get(variant, (8, 420))
+    return {"444": (8, 444), "444coded": (8, 444), "12bit": (12, 420)}.get(variant, (8, 420))
 
 
 def run_search(args):
@@ -628,12 +630,13 @@ def run_search(args):
     nb = sum(fr.params.shape[0] * fr.params.shape[1] for fr in frames)
     damping = [4 + (fr.q > 16) + (fr.q > 32) for fr in frames]   # larger damping for larger Q
     lambdas = [fr.q * fr.q for fr in frames]
-    width = 128 if variant == "coded" else 64          # table entries per block and group
+    coded_variant = variant.endswith("coded")
+    width = 128 if coded_variant else 64               # table entries per block and group
     ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     dl = torch.zeros(nb * width, dtype=torch.int64, device="cuda")
     dc = torch.zeros(nb * width, dtype=torch.int64, device="cuda")
     maps = []
-    if variant == "coded":
+    if coded_variant:
         # coded-residual flags: 60% of the 8x8 blocks, one in eight filter blocks fully skipped
         rng = np.random.default_rng(SEARCH_WORKLOAD["base_seed"])
         for fr in frames:
@@ -651,9 +654,9 @@ def run_search(args):
         a = int(starts[sl.start or 0])
         b = int(starts[len(frames) if sl.stop is None else sl.stop])
         args_ = (recs[sl], srcs[sl])
-        if variant == "coded":
+        if coded_variant:
             args_ += (maps[sl],)
-        return (cdef.cdef_search_strengths_coded if variant == "coded"
+        return (cdef.cdef_search_strengths_coded if coded_variant
                 else cdef.cdef_search_strengths)(
             ctx, *args_, damping[sl], lambdas[sl], ids[a:b], dl[a * width:b * width],
             dc[a * width:b * width], stream=stream)
@@ -723,7 +726,7 @@ def run_search(args):
                 "unit": "Gop/s", "frac": ops / (dist_ms * 1e-3) / 1e9 / peak_ops,
                 "traffic": None,
                 "kernel": "dist_wide_kernel + find_dir_kernel (distortion tables, 32-bit lanes)"
-                if variant in ("444", "12bit") else "dist_kernel (distortion tables)",
+                if variant in ("444", "12bit", "444coded") else "dist_kernel (distortion tables)",
                 "ops_per_launch": ops, "mean_launch_us": dist_ms * 1e3,
                 "launch_time": "CUDA events around the kernel inside the search graph",
                 "preset_kernel_us": pre_ms * 1e3,
@@ -920,7 +923,7 @@ def main():
     ap.add_argument("--refine", type=int, default=0,
                     help="search: preset re-optimisation passes after the greedy search")
     ap.add_argument("--search-variant", default="sse",
-                    choices=["sse", "eq14", "coded", "444", "12bit"],
+                    choices=["sse", "eq14", "coded", "444", "12bit", "444coded"],
                     help="search: squared error (64 pairs), eq. 14 distortion, the "
                          "128-combination search with coded-residual maps, or the squared-error "
                          "search over 8-bit 4:4:4 or 12-bit 4:2:0 frames")
