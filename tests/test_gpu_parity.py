@@ -928,3 +928,82 @@ def test_search_coded_formats_parity(cdef, ctx, ref):
             [int(t) for t in o["presets"][:o["npresets"]]]
         assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
         o0 += b
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_filter_random_fuzz(cdef, ctx, ref, seed):
+    """Random sizes (multiples of 8 from 8 to 264), bit depths, formats,
+    strengths, skip bits and coded maps: every output sample equals the
+    oracle's."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(5000 + seed)
+    for _ in range(10):
+        w, h = 8 * int(rng.integers(1, 34)), 8 * int(rng.integers(1, 34))
+        bd = int(rng.choice([8, 10, 12]))
+        fmt = int(rng.choice([420, 420, 422, 444]))
+        f = synth.make_frame(w, h, bd, int(rng.choice([16, 32, 64])), seed=int(rng.integers(1 << 30)),
+                             chroma=fmt)
+        params = synth.random_params(rng, w, h)
+        params[..., 5] = rng.integers(0, 4, params.shape[:2])
+        coded = (rng.random((h // 8, w // 8)) < rng.random()).astype(np.uint8)
+        inp = cdef.frame_from_numpy(f.rec, bd)
+        out = cdef.alloc_frame(w, h, bd, fill=0, chroma=fmt)
+        cdef.cdef_filter_frame_coded(ctx, inp, cdef.params_tensor(params),
+                                     torch.from_numpy(coded.reshape(-1)).cuda(), out)
+        torch.cuda.synchronize()
+        exp = ref.filter_frame_format(*f.rec, bd, params, fmt, coded)
+        _assert_frames_equal(out.to_numpy(), exp)
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_search_random_fuzz(cdef, ctx, ref, seed):
+    """Random mixed calls (sizes, bit depths, formats, damping, lambda, with
+    or without coded-residual maps): tables, presets, N, J and ids equal
+    the oracle's."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(6000 + seed)
+    with_maps = seed % 2 == 1
+    frames, maps = [], []
+    for _ in range(5):
+        w, h = 8 * int(rng.integers(1, 26)), 8 * int(rng.integers(1, 26))
+        bd = int(rng.choice([8, 10] if seed < 2 else [8, 10, 12]))
+        fmt = 420 if seed < 2 else int(rng.choice([420, 422, 444]))
+        frames.append(synth.make_frame(w, h, bd, None, seed=int(rng.integers(1 << 30)), chroma=fmt))
+        maps.append((rng.random((h // 8, w // 8)) < rng.random()).astype(np.uint8))
+    damping = [int(d) for d in rng.integers(3, 7, len(frames))]
+    lambdas = [int(l) for l in rng.integers(0, 5000, len(frames))]
+    width = 128 if with_maps else 64
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.full((nb * width,), -1, dtype=torch.int64, device="cuda")
+    dc = torch.full((nb * width,), -1, dtype=torch.int64, device="cuda")
+    recs = [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames]
+    srcs = [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames]
+    if with_maps:
+        res = cdef.cdef_search_strengths_coded(ctx, recs, srcs,
+                                               [torch.from_numpy(m.reshape(-1)).cuda() for m in maps],
+                                               damping, lambdas, ids, dl, dc)
+    else:
+        res = cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc)
+    assert ctx.status() == 0
+    o0 = 0
+    for f, m, r, d, lam in zip(frames, maps, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        fmt = {(f.width // 2, f.height // 2): 420, (f.width // 2, f.height): 422,
+               (f.width, f.height): 444}[(f.rec[1].shape[1], f.rec[1].shape[0])]
+        if with_maps:
+            o = ref.search_strengths_coded_format(f.rec, f.src, f.bitdepth, d, lam, fmt, m)
+            idx = cdef.preset_index_coded
+        else:
+            o = ref.search_strengths_format(f.rec, f.src, f.bitdepth, d, lam, fmt)
+            idx = cdef.preset_index
+        assert np.array_equal(dl[o0 * width:(o0 + b) * width].cpu().numpy().reshape(b, width),
+                              o["dist_luma"])
+        assert np.array_equal(dc[o0 * width:(o0 + b) * width].cpu().numpy().reshape(b, width),
+                              o["dist_chroma"])
+        assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"]
+        assert [idx(p) for p in r["presets"][:r["npresets"]]] == \
+            [int(t) for t in o["presets"][:o["npresets"]]]
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
