@@ -854,7 +854,7 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
                 ctx->search_key_timing = ctx->stage_timing;
             }
         } else if (ctx->search_key) {
-            memset(ctx->search_key, 0, sizeof(SearchBatch));
+            memset(static_cast<void *>(ctx->search_key), 0, sizeof(SearchBatch));   // no key: re-record
         }
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(ctx->search_exec, s);
