@@ -180,7 +180,7 @@ cudaError_t launch_presets(const SearchBatch &b, const long long *dl, const long
                            cudaStream_t s);
 size_t preset_ctl_bytes();
 constexpr int kMaxRefinePasses = 16;
-constexpr size_t kPresetCtlBytes = 1024;  // barrier and per-frame flags of launch_presets
+constexpr size_t kPresetCtlBytes = 512;   // barrier and per-frame flags of launch_presets
 // Scratch of one search: `cur` one u64 per block, `tot` 4096 u64 per frame,
 // then the preset kernel's control block.
 constexpr size_t search_scratch_bytes(int nframes, int nblocks, int width = 64)

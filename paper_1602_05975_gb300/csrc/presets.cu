@@ -31,13 +31,8 @@ constexpr int kMaxWidth = 128;     // combinations per plane group (64 or 128)
 constexpr int kPerThread = 16;     // presets per thread and group of 4096
 constexpr long long kBarrierCycles = 1ll << 30;
 
-constexpr unsigned kBarrierGroup = 16;   // CTAs per first-level barrier counter
-constexpr int kMaxBarrierGroups = 32;    // grids of up to 512 CTAs
-
-struct Ctl {                       // lives in device scratch (the first
-                                   // 1 + kMaxBarrierGroups words are zeroed per launch)
-    unsigned arrive;               // barrier groups complete at the current barrier
-    unsigned group_arrive[kMaxBarrierGroups];   // CTAs of each group arrived
+struct Ctl {                       // lives in device scratch
+    unsigned arrive;               // CTAs arrived at the current barrier
     unsigned gen;                  // barrier generation
     unsigned done_frames[4];       // per set size: frames whose re-optimisation converged
                                    // (never reset inside a launch: every CTA reads the
@@ -60,9 +55,7 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier; false when the wait gave up (status set).  Arrivals
-// are counted in two levels (groups of kBarrierGroup CTAs, then the
-// groups), so that they do not all serialise on one counter.
+// Grid-wide barrier; false when the wait gave up (status set).
 __device__ bool grid_sync(Ctl *ctl, int *status)
 {
     __shared__ int s_ok;
@@ -71,16 +64,7 @@ __device__ bool grid_sync(Ctl *ctl, int *status)
         int ok = 1;
         const unsigned g = ld_acquire(&ctl->gen);
         __threadfence();
-        const unsigned grp = blockIdx.x / kBarrierGroup;
-        const unsigned ngroups = (gridDim.x + kBarrierGroup - 1) / kBarrierGroup;
-        const unsigned gsize = min(kBarrierGroup, gridDim.x - grp * kBarrierGroup);
-        bool last = false;
-        if (atomicAdd(&ctl->group_arrive[grp], 1u) == gsize - 1) {
-            atomicExch(&ctl->group_arrive[grp], 0u);
-            __threadfence();
-            last = atomicAdd(&ctl->arrive, 1u) == ngroups - 1;
-        }
-        if (last) {
+        if (atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1) {
             atomicExch(&ctl->arrive, 0u);
             __threadfence();
             st_release(&ctl->gen, g + 1);
@@ -422,13 +406,11 @@ cudaError_t launch_presets(const SearchBatch &b, const long long *dl, const long
 {
     if (width != 64 && width != kMaxWidth) return cudaErrorInvalidValue;
     // a barrier abandoned by an earlier timed-out launch must not leave
-    // CTAs counted: the arrival counts (both levels) start at zero
-    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (1 + kMaxBarrierGroups), s);
+    // CTAs counted: the arrival count starts at zero
+    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    const int grid = preset_grid(b);
-    if (grid > (int)kBarrierGroup * kMaxBarrierGroups) return cudaErrorInvalidConfiguration;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
+    cfg.gridDim = dim3(preset_grid(b));
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
