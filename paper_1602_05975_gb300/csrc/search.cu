@@ -827,6 +827,21 @@ cudaError_t launch_dist_eq14(const SearchBatch &b, long long *dl, long long *dc,
 
 }  // namespace
 
+// The preset selection: the cluster-per-frame kernel where it applies (64
+// combinations, greedy only), else the grid-wide cooperative kernel.
+static cudaError_t select_presets(const SearchBatch &b, const long long *dl, const long long *dc,
+                                  unsigned long long *cur, unsigned long long *tot,
+                                  SearchResultDev *results, uint8_t *block_ids, int *status,
+                                  int refine_passes, int width, const uint8_t *skipped,
+                                  cudaStream_t s)
+{
+    if (width == 64 && !skipped && refine_passes == 0 && preset_cluster_fits(b))
+        return launch_presets_cluster(b, dl, dc, results, block_ids, s);
+    void *ctl = tot + (size_t)b.n * width * width;
+    return launch_presets(b, dl, dc, cur, tot, ctl, results, block_ids, status, refine_passes,
+                          width, skipped, s);
+}
+
 // An event on the stream; inside a stream capture, an event record node of
 // the graph.
 static cudaError_t stage_mark(const cudaEvent_t *ev, int k, cudaStream_t s)
@@ -854,8 +869,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
         if (e != cudaSuccess) return e;
         const int width = skipped ? 128 : 64;
-        void *ctl = tot + (size_t)b.n * width * width;
-        e = launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
+        e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
                            refine_passes, width, skipped, s);
         return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
     }
@@ -863,8 +877,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
         e = launch_dist_eq14(b, dist_luma, dist_chroma, status, work, s);
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
         if (e != cudaSuccess) return e;
-        void *ctl = tot + (size_t)b.n * 4096;
-        e = launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
+        e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
                            refine_passes, 64, nullptr, s);
         return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
     }
@@ -876,8 +889,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
     if (e != cudaSuccess) return e;
     const int width = skipped ? 128 : 64;
-    void *ctl = tot + (size_t)b.n * width * width;
-    e = launch_presets(b, dist_luma, dist_chroma, cur, tot, ctl, results, block_ids, status,
+    e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
                        refine_passes, width, skipped, s);
     return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
 }
