@@ -66,8 +66,8 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
     __syncthreads();
 
     for (int step = 0; step < 8; step++) {
-        // partial totals of this CTA's blocks: thread tid, presets tid + 512 j
-        // (chroma pair tid % 64 for every j, luma pair tid / 64 + 8 j)
+        // partial totals of this CTA's blocks: thread tid, presets tid + kCT j
+        // (chroma pair tid % 64 for every j, luma pair tid / 64 + (kCT / 64) j)
         unsigned long long a[kPer];
 #pragma unroll
         for (int j = 0; j < kPer; j++) a[j] = 0;
@@ -85,7 +85,7 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
                 const unsigned long long cb = sm.cur[s0 + bb], dcv = sm.dc[bb][c];
 #pragma unroll
                 for (int j = 0; j < kPer; j++) {
-                    const unsigned long long v = sm.dl[bb][l0 + 8 * j] + dcv;
+                    const unsigned long long v = sm.dl[bb][l0 + (kCT / 64) * j] + dcv;
                     a[j] += v < cb ? v : cb;
                 }
             }
@@ -98,8 +98,8 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
         // this CTA's slice: the eight partial sums, then its least total
         unsigned long long bv = ULLONG_MAX;
         int bt = INT_MAX;
-        {
-            const int t = rank * kSlice + tid;   // kSlice == kCT: one preset per thread
+        if (tid < kSlice) {   // one preset of the slice per thread
+            const int t = rank * kSlice + tid;
             unsigned long long tot = 0;
 #pragma unroll
             for (int r = 0; r < kCS; r++) tot += cluster.map_shared_rank(sm.part, r)[t];
@@ -195,15 +195,18 @@ bool preset_cluster_fits(const SearchBatch &b)
 cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, const long long *dc,
                                    SearchResultDev *results, uint8_t *block_ids, cudaStream_t s)
 {
-    static_assert(kSlice == kCT, "one preset of the slice per thread");
+    static_assert(kSlice <= kCT && kCT % 64 == 0 && kTuples % kCT == 0, "thread layout");
     constexpr size_t kSmem = sizeof(ClusterSmem);
     static int configured_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != configured_dev) {
-        const cudaError_t e =
+        cudaError_t e =
             cudaFuncSetAttribute(preset_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmem);
+        if (e == cudaSuccess && kCS > 8)
+            e = cudaFuncSetAttribute(preset_cluster_kernel,
+                                     cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
         configured_dev = dev;
     }
