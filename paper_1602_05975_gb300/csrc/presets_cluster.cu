@@ -31,6 +31,7 @@ constexpr int kMaxOwn = 2048;            // blocks one CTA can hold (frames up t
 struct ClusterSmem {
     unsigned long long part[kTuples];            // this CTA's partial totals
     unsigned long long dl[kStage][64], dc[kStage][64];
+    unsigned dl32[kStage][64], dc32[kStage][64]; // the same below 2^32 (narrow tables)
     unsigned long long cur[kMaxOwn];             // best distortion of the CTA's blocks
     unsigned long long red_v[kCT / 32];
     int red_t[kCT / 32];
@@ -45,6 +46,9 @@ __device__ __forceinline__ bool better(unsigned long long a, int ta, unsigned lo
     return a < b || (a == b && ta < tb);
 }
 
+// kNarrow: every table entry of the call is below 2^32 (squared error of
+// 8-bit frames): the per-block minima are taken in 32 bits.
+template <bool kNarrow>
 __global__ void __launch_bounds__(kCT)
 preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
                       const long long *__restrict__ dc, SearchResultDev *res, uint8_t *block_ids)
@@ -77,16 +81,34 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
             for (int i = tid; i < ns * 64; i += kCT) {
                 const int bb = i >> 6, q = i & 63;
                 const int64_t g = (int64_t)(F.block_start + b0 + s0 + bb) * 64 + q;
-                sm.dl[bb][q] = (unsigned long long)dl[g];
-                sm.dc[bb][q] = (unsigned long long)dc[g];
+                if (kNarrow) {
+                    sm.dl32[bb][q] = (unsigned)dl[g];
+                    sm.dc32[bb][q] = (unsigned)dc[g];
+                } else {
+                    sm.dl[bb][q] = (unsigned long long)dl[g];
+                    sm.dc[bb][q] = (unsigned long long)dc[g];
+                }
             }
             __syncthreads();
             for (int bb = 0; bb < ns; bb++) {
-                const unsigned long long cb = sm.cur[s0 + bb], dcv = sm.dc[bb][c];
+                const unsigned long long cb = sm.cur[s0 + bb];
+                if (kNarrow) {
+                    // entries sum to below 2^32 (two tables of 8-bit squared
+                    // errors); the block minimum clamps to 32 bits
+                    const unsigned cb32 = cb > 0xffffffffull ? 0xffffffffu : (unsigned)cb;
+                    const unsigned dcv = sm.dc32[bb][c];
 #pragma unroll
-                for (int j = 0; j < kPer; j++) {
-                    const unsigned long long v = sm.dl[bb][l0 + (kCT / 64) * j] + dcv;
-                    a[j] += v < cb ? v : cb;
+                    for (int j = 0; j < kPer; j++) {
+                        const unsigned v = sm.dl32[bb][l0 + (kCT / 64) * j] + dcv;
+                        a[j] += v < cb32 ? v : cb32;
+                    }
+                } else {
+                    const unsigned long long dcv = sm.dc[bb][c];
+#pragma unroll
+                    for (int j = 0; j < kPer; j++) {
+                        const unsigned long long v = sm.dl[bb][l0 + (kCT / 64) * j] + dcv;
+                        a[j] += v < cb ? v : cb;
+                    }
                 }
             }
             __syncthreads();
@@ -193,7 +215,8 @@ bool preset_cluster_fits(const SearchBatch &b)
 }
 
 cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, const long long *dc,
-                                   SearchResultDev *results, uint8_t *block_ids, cudaStream_t s)
+                                   SearchResultDev *results, uint8_t *block_ids, bool narrow,
+                                   cudaStream_t s)
 {
     static_assert(kSlice <= kCT && kCT % 64 == 0 && kTuples % kCT == 0, "thread layout");
     constexpr size_t kSmem = sizeof(ClusterSmem);
@@ -201,13 +224,13 @@ cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, co
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != configured_dev) {
-        cudaError_t e =
-            cudaFuncSetAttribute(preset_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmem);
-        if (e == cudaSuccess && kCS > 8)
-            e = cudaFuncSetAttribute(preset_cluster_kernel,
-                                     cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
+        for (auto *k : {preset_cluster_kernel<true>, preset_cluster_kernel<false>}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kSmem);
+            if (e == cudaSuccess && kCS > 8)
+                e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+        }
         configured_dev = dev;
     }
     cudaLaunchConfig_t cfg = {};
@@ -222,7 +245,8 @@ cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, co
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, preset_cluster_kernel, b, dl, dc, results, block_ids);
+    return narrow ? cudaLaunchKernelEx(&cfg, preset_cluster_kernel<true>, b, dl, dc, results, block_ids)
+                  : cudaLaunchKernelEx(&cfg, preset_cluster_kernel<false>, b, dl, dc, results, block_ids);
 }
 
 }  // namespace cdefgb

@@ -829,14 +829,20 @@ cudaError_t launch_dist_eq14(const SearchBatch &b, long long *dl, long long *dc,
 
 // The preset selection: the cluster-per-frame kernel where it applies (64
 // combinations, greedy only), else the grid-wide cooperative kernel.
+// `sse`: the tables hold squared errors (not eq. 14).
 static cudaError_t select_presets(const SearchBatch &b, const long long *dl, const long long *dc,
                                   unsigned long long *cur, unsigned long long *tot,
                                   SearchResultDev *results, uint8_t *block_ids, int *status,
-                                  int refine_passes, int width, const uint8_t *skipped,
+                                  int refine_passes, int width, const uint8_t *skipped, bool sse,
                                   cudaStream_t s)
 {
-    if (width == 64 && !skipped && refine_passes == 0 && preset_cluster_fits(b))
-        return launch_presets_cluster(b, dl, dc, results, block_ids, s);
+    if (width == 64 && !skipped && refine_passes == 0 && preset_cluster_fits(b)) {
+        // 8-bit squared errors: a block's luma and chroma entries sum to at
+        // most 3 x 4096 x 255^2 < 2^32
+        bool narrow = sse;
+        for (int i = 0; i < b.n; i++) narrow = narrow && b.f[i].bitdepth == 8;
+        return launch_presets_cluster(b, dl, dc, results, block_ids, narrow, s);
+    }
     void *ctl = tot + (size_t)b.n * width * width;
     return launch_presets(b, dl, dc, cur, tot, ctl, results, block_ids, status, refine_passes,
                           width, skipped, s);
@@ -870,7 +876,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
         if (e != cudaSuccess) return e;
         const int width = skipped ? 128 : 64;
         e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
-                           refine_passes, width, skipped, s);
+                           refine_passes, width, skipped, true, s);
         return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
     }
     if (tune.groups == 8) {   // eq. 14 tables
@@ -878,7 +884,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
         if (e != cudaSuccess) return e;
         e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
-                           refine_passes, 64, nullptr, s);
+                           refine_passes, 64, nullptr, false, s);
         return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
     }
     switch (tune.groups) {
@@ -890,7 +896,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     if (e != cudaSuccess) return e;
     const int width = skipped ? 128 : 64;
     e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
-                       refine_passes, width, skipped, s);
+                       refine_passes, width, skipped, true, s);
     return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
 }
 
