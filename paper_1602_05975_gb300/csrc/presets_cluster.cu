@@ -25,14 +25,13 @@ constexpr int kCT = 512;                 // threads per CTA
 constexpr int kTuples = 4096;            // presets of the 64-combination search
 constexpr int kPer = kTuples / kCT;      // presets per thread
 constexpr int kSlice = kTuples / kCS;    // presets reduced by one CTA
-constexpr int kStage = 16;               // blocks staged in shared memory at a time
 constexpr int kMaxOwn = 2048;            // blocks one CTA can hold (frames up to 16384 blocks)
+constexpr int kTabBytes = 128 * 1024;    // the CTA's luma and chroma table rows
 
 struct ClusterSmem {
     unsigned long long part[kTuples];            // this CTA's partial totals
-    unsigned long long dl[kStage][64], dc[kStage][64];
-    unsigned dl32[kStage][64], dc32[kStage][64]; // the same below 2^32 (narrow tables)
     unsigned long long cur[kMaxOwn];             // best distortion of the CTA's blocks
+    alignas(16) unsigned char tab[kTabBytes];    // table rows: luma [cap][64], chroma [cap][64]
     unsigned long long red_v[kCT / 32];
     int red_t[kCT / 32];
     unsigned long long slice_v;                  // this CTA's slice minimum
@@ -46,9 +45,60 @@ __device__ __forceinline__ bool better(unsigned long long a, int ta, unsigned lo
     return a < b || (a == b && ta < tb);
 }
 
-// kNarrow: every table entry of the call is below 2^32 (squared error of
-// 8-bit frames): the per-block minima are taken in 32 bits.
-template <bool kNarrow>
+// Eight consecutive entries of a shared-memory row (16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void load8(const T *p, T (&v)[kPer])
+{
+    static_assert(kPer == 8, "eight presets per thread");
+    if constexpr (sizeof(T) == 4) {
+        const uint4 x = reinterpret_cast<const uint4 *>(p)[0];
+        const uint4 y = reinterpret_cast<const uint4 *>(p)[1];
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+        v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const ulonglong2 x = reinterpret_cast<const ulonglong2 *>(p)[k];
+            v[2 * k] = x.x;
+            v[2 * k + 1] = x.y;
+        }
+    }
+}
+
+// a[j] += sum over n blocks of min(cur_b, L_b(lq + j) + C_b(c)).  With
+// 32-bit entries (8-bit squared errors: a block's luma and chroma entries
+// sum to at most 3 x 4096 x 255^2 < 2^30) four blocks' minima are summed
+// in 32 bits before the 64-bit totals.
+template <typename T>
+__device__ __forceinline__ void sum_blocks(const T (*rl)[64], const T (*rc)[64], const T *cur,
+                                           int n, int c, int lq, unsigned long long (&a)[kPer])
+{
+    constexpr int kChunk = sizeof(T) == 4 ? 4 : 1;
+    for (int b0 = 0; b0 < n; b0 += kChunk) {
+        T sum[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; j++) sum[j] = 0;
+#pragma unroll
+        for (int k = 0; k < kChunk; k++) {
+            const int bb = b0 + k;
+            if (kChunk > 1 && bb >= n) break;
+            const T cb = cur[bb], dcv = rc[bb][c];
+            T v[kPer];
+            load8(rl[bb] + lq, v);
+#pragma unroll
+            for (int j = 0; j < kPer; j++) {
+                const T x = v[j] + dcv;
+                sum[j] += x < cb ? x : cb;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; j++) a[j] += sum[j];
+    }
+}
+
+// T: the width of the per-block minima; 32 bits when every table entry of
+// the call is an 8-bit squared error (below 2^30).
+template <typename T>
 __global__ void __launch_bounds__(kCT)
 preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
                       const long long *__restrict__ dc, SearchResultDev *res, uint8_t *block_ids)
@@ -65,56 +115,42 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
     const int own = b1 - b0;
     const unsigned long long lp = allowed_pairs(F, 0), cp = allowed_pairs(F, 1);
     const bool full = (lp & cp) == ~0ull;
+    // table rows of `cap` blocks fit; with own <= cap they stay for all steps
+    constexpr int cap = kTabBytes / (2 * 64 * (int)sizeof(T));
+    T (*rl)[64] = reinterpret_cast<T (*)[64]>(sm.tab);
+    T (*rc)[64] = rl + cap;
+    T *cur = reinterpret_cast<T *>(sm.cur);
+    const bool resident = own <= cap;
+    auto stage = [&](int s0, int n) {
+        for (int i = tid; i < n * 64; i += kCT) {
+            const int bb = i >> 6, q = i & 63;
+            const int64_t g = (int64_t)(F.block_start + b0 + s0 + bb) * 64 + q;
+            rl[bb][q] = (T)dl[g];
+            rc[bb][q] = (T)dc[g];
+        }
+    };
 
-    for (int b = tid; b < own; b += kCT) sm.cur[b] = ULLONG_MAX;
+    for (int b = tid; b < own; b += kCT) cur[b] = (T)~0ull;
+    if (resident) stage(0, own);
     __syncthreads();
 
+    // thread tid: chroma pair c, luma pairs lq .. lq + 7 (presets (lq + j) * 64 + c)
+    const int c = tid & 63, lq = (tid >> 6) * kPer;
     for (int step = 0; step < 8; step++) {
-        // partial totals of this CTA's blocks: thread tid, presets tid + kCT j
-        // (chroma pair tid % 64 for every j, luma pair tid / 64 + (kCT / 64) j)
         unsigned long long a[kPer];
 #pragma unroll
         for (int j = 0; j < kPer; j++) a[j] = 0;
-        const int c = tid & 63, l0 = tid >> 6;
-        for (int s0 = 0; s0 < own; s0 += kStage) {
-            const int ns = min(kStage, own - s0);
-            for (int i = tid; i < ns * 64; i += kCT) {
-                const int bb = i >> 6, q = i & 63;
-                const int64_t g = (int64_t)(F.block_start + b0 + s0 + bb) * 64 + q;
-                if (kNarrow) {
-                    sm.dl32[bb][q] = (unsigned)dl[g];
-                    sm.dc32[bb][q] = (unsigned)dc[g];
-                } else {
-                    sm.dl[bb][q] = (unsigned long long)dl[g];
-                    sm.dc[bb][q] = (unsigned long long)dc[g];
-                }
+        for (int s0 = 0; s0 < own; s0 += cap) {
+            const int n = min(cap, own - s0);
+            if (!resident) {
+                stage(s0, n);
+                __syncthreads();
             }
-            __syncthreads();
-            for (int bb = 0; bb < ns; bb++) {
-                const unsigned long long cb = sm.cur[s0 + bb];
-                if (kNarrow) {
-                    // entries sum to below 2^32 (two tables of 8-bit squared
-                    // errors); the block minimum clamps to 32 bits
-                    const unsigned cb32 = cb > 0xffffffffull ? 0xffffffffu : (unsigned)cb;
-                    const unsigned dcv = sm.dc32[bb][c];
-#pragma unroll
-                    for (int j = 0; j < kPer; j++) {
-                        const unsigned v = sm.dl32[bb][l0 + (kCT / 64) * j] + dcv;
-                        a[j] += v < cb32 ? v : cb32;
-                    }
-                } else {
-                    const unsigned long long dcv = sm.dc[bb][c];
-#pragma unroll
-                    for (int j = 0; j < kPer; j++) {
-                        const unsigned long long v = sm.dl[bb][l0 + (kCT / 64) * j] + dcv;
-                        a[j] += v < cb ? v : cb;
-                    }
-                }
-            }
-            __syncthreads();
+            sum_blocks<T>(rl, rc, cur + s0, n, c, lq, a);
+            if (!resident) __syncthreads();
         }
 #pragma unroll
-        for (int j = 0; j < kPer; j++) sm.part[tid + kCT * j] = a[j];
+        for (int j = 0; j < kPer; j++) sm.part[(lq + j) * 64 + c] = a[j];
         cluster.sync();
 
         // this CTA's slice: the eight partial sums, then its least total
@@ -160,10 +196,14 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
         __syncthreads();
         const int best = sm.greedy[step];
         for (int b = tid; b < own; b += kCT) {
-            const int64_t g = F.block_start + b0 + b;
-            const unsigned long long d =
-                (unsigned long long)(dl[g * 64 + (best >> 6)] + dc[g * 64 + (best & 63)]);
-            if (d < sm.cur[b]) sm.cur[b] = d;
+            T d;
+            if (resident) {
+                d = rl[b][best >> 6] + rc[b][best & 63];
+            } else {
+                const int64_t g = F.block_start + b0 + b;
+                d = (T)(dl[g * 64 + (best >> 6)] + dc[g * 64 + (best & 63)]);
+            }
+            if (d < cur[b]) cur[b] = d;
         }
         __syncthreads();
     }
@@ -224,7 +264,7 @@ cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, co
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != configured_dev) {
-        for (auto *k : {preset_cluster_kernel<true>, preset_cluster_kernel<false>}) {
+        for (auto *k : {preset_cluster_kernel<unsigned>, preset_cluster_kernel<unsigned long long>}) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kSmem);
             if (e == cudaSuccess && kCS > 8)
@@ -245,8 +285,10 @@ cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, co
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return narrow ? cudaLaunchKernelEx(&cfg, preset_cluster_kernel<true>, b, dl, dc, results, block_ids)
-                  : cudaLaunchKernelEx(&cfg, preset_cluster_kernel<false>, b, dl, dc, results, block_ids);
+    return narrow ? cudaLaunchKernelEx(&cfg, preset_cluster_kernel<unsigned>, b, dl, dc, results,
+                                       block_ids)
+                  : cudaLaunchKernelEx(&cfg, preset_cluster_kernel<unsigned long long>, b, dl, dc,
+                                       results, block_ids);
 }
 
 }  // namespace cdefgb

@@ -858,6 +858,40 @@ def test_filter_frames_maximum_batch(cdef, ctx, ref):
         cdef.cdef_filter_frames(ctx, ins + ins[:1], prms + prms[:1], outs + [cdef.alloc_frame(64, 64, 8)])
 
 
+@pytest.mark.parametrize("sizes,bd", [
+    ([(2048, 2176)], 10),                   # 1088 blocks: 64-bit minima, tables staged twice a step
+    ([(7680, 4352), (256, 256)], 8),        # 8160 blocks (staged 4 times) with a resident frame
+    ([(8192, 8320)], 8),                    # 16640 blocks: beyond the cluster kernel's state
+])
+def test_search_large_periodic_frames(cdef, ctx, ref, sizes, bd):
+    """The search on frames far larger than the oracle's search can take,
+    through tables known by construction (`periodic_frames.py`): the
+    tables, presets, N, J and every block's id."""
+    from periodic_frames import periodic_search_case
+    cases = periodic_search_case(ref, sizes, bd, seed=6100 + bd)
+    recs = [cdef.frame_from_numpy(c["rec"], bd) for c in cases]
+    srcs = [cdef.frame_from_numpy(c["src"], bd) for c in cases]
+    nbs = [c["dl"].shape[0] for c in cases]
+    tot = sum(nbs)
+    ids = torch.zeros(tot, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(tot * 64, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(tot * 64, dtype=torch.int64, device="cuda")
+    res = cdef.cdef_search_strengths(ctx, recs, srcs, [c["damping"] for c in cases],
+                                     [c["lam"] for c in cases], ids, dl, dc)
+    assert ctx.status() == 0
+    dl, dc, ids = dl.cpu().numpy(), dc.cpu().numpy(), ids.cpu().numpy()
+    off = 0
+    for k, c in enumerate(cases):
+        nb, o = nbs[k], c["exp"]
+        assert np.array_equal(dl[off * 64:(off + nb) * 64].reshape(nb, 64), c["dl"])
+        assert np.array_equal(dc[off * 64:(off + nb) * 64].reshape(nb, 64), c["dc"])
+        assert res[k]["npresets"] == o["npresets"]
+        assert res[k]["cost"] == o["cost"]
+        assert [cdef.preset_index(p) for p in res[k]["presets"]] == list(o["presets"])
+        assert np.array_equal(ids[off:off + nb], o["block_ids"])
+        off += nb
+
+
 def test_search_maximum_batch(cdef, ctx, ref):
     """48 frames in one search call equal 48 oracle searches; 49 are refused."""
     from paper_1602_05975_gb300 import synth

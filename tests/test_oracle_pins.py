@@ -1230,3 +1230,18 @@ def test_eq14_tables_from_decoder_output(ref):
                             tot += ref.eq14_term(*_sums(f.src[k][y:y + 8, x:x + 8],
                                                         out[k][y:y + 8, x:x + 8]), 8)
                 assert tab[b, q] == tot, (q, pl, b)
+
+
+def test_periodic_frame_tables_by_class(ref):
+    """The construction behind the large-frame search tests: the oracle's
+    tables of frames that tile a 128x128 pattern equal the tables gathered
+    by block class from the 4x4-block frame of the pattern, and so do the
+    presets selected on them."""
+    from periodic_frames import periodic_search_case
+    for bd in (8, 10):
+        for c in periodic_search_case(ref, [(512, 384), (384, 256)], bd, seed=6100 + bd):
+            dl, dc = ref.distortion(c["rec"], c["src"], bd, c["damping"])
+            assert np.array_equal(dl, c["dl"]) and np.array_equal(dc, c["dc"])
+            o = ref.select_presets(dl, dc, c["lam"])
+            assert list(o["presets"]) == list(c["exp"]["presets"])
+            assert np.array_equal(o["block_ids"], c["exp"]["block_ids"])
