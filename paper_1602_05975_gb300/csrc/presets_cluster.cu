@@ -7,9 +7,11 @@
 // and finds their least total (lowest index on ties); after a second
 // barrier every CTA takes the least of the eight slice minima, so all of
 // them agree on the step's preset and lower their blocks' best distortion.
-// Then N in {1, 2, 4, 8} by J and each block's preset id, as in
-// presets.cu.  Used for the 64-combination search without re-optimisation
-// (the other variants take the grid-wide kernel).
+// The re-optimisation passes (section 5) re-choose one slot of a set at a
+// time with the same step, each block's best distortion being its least
+// over the set's other slots.  Then N in {1, 2, 4, 8} by J and each block's
+// preset id, as in presets.cu.  Used for the 64-combination search (the
+// 128-combination search takes the grid-wide kernel).
 #include <climits>
 #include <cooperative_groups.h>
 
@@ -36,8 +38,13 @@ struct ClusterSmem {
     int red_t[kCT / 32];
     unsigned long long slice_v;                  // this CTA's slice minimum
     int slice_t;
+    unsigned long long slice_old;                // total of the step's current preset (its slice's CTA)
+    int step_t;                                  // the step's chosen preset
+    unsigned long long step_v;                   // and its total
     int greedy[8];
     long long totals[8];
+    int refined[4][8];                           // sets of size 1, 2, 4, 8 (re-optimised)
+    long long ref_totals[4];
 };
 
 __device__ __forceinline__ bool better(unsigned long long a, int ta, unsigned long long b, int tb)
@@ -99,9 +106,10 @@ __device__ __forceinline__ void sum_blocks(const T (*rl)[64], const T (*rc)[64],
 // T: the width of the per-block minima; 32 bits when every table entry of
 // the call is an 8-bit squared error (below 2^30).
 template <typename T>
-__global__ void __launch_bounds__(kCT)
+__global__ void __launch_bounds__(kCT, 1)
 preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
-                      const long long *__restrict__ dc, SearchResultDev *res, uint8_t *block_ids)
+                      const long long *__restrict__ dc, SearchResultDev *res, uint8_t *block_ids,
+                      int refine_passes)
 {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     ClusterSmem &sm = *reinterpret_cast<ClusterSmem *>(smem_raw);
@@ -136,7 +144,17 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
 
     // thread tid: chroma pair c, luma pairs lq .. lq + 7 (presets (lq + j) * 64 + c)
     const int c = tid & 63, lq = (tid >> 6) * kPer;
-    for (int step = 0; step < 8; step++) {
+    // D_b(t) of the CTA's block b
+    auto dist = [&](int b, int t) -> T {
+        if (resident) return rl[b][t >> 6] + rc[b][t & 63];
+        const int64_t g = F.block_start + b0 + b;
+        return (T)(dl[g * 64 + (t >> 6)] + dc[g * 64 + (t & 63)]);
+    };
+    // One step: the cluster's least total sum_b min(cur_b, D_b(t)) over the
+    // allowed presets t (lowest index on ties) into sm.step_t / sm.step_v,
+    // identical in every CTA; with old >= 0 (re-optimisation of a slot
+    // holding preset `old`) old is kept when its total attains the minimum.
+    auto step = [&](int old) {
         unsigned long long a[kPer];
 #pragma unroll
         for (int j = 0; j < kPer; j++) a[j] = 0;
@@ -162,6 +180,7 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
 #pragma unroll
             for (int r = 0; r < kCS; r++) tot += cluster.map_shared_rank(sm.part, r)[t];
             if (full || ((lp >> (t >> 6)) & (cp >> (t & 63)) & 1)) { bv = tot; bt = t; }
+            if (t == old) sm.slice_old = tot;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -182,7 +201,9 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
         }
         cluster.sync();
 
-        // every CTA: the least of the slice minima (the same in all of them)
+        // every CTA: the least of the slice minima (the same in all of them);
+        // the slice values are rewritten only after the next step's first
+        // cluster barrier
         if (tid == 0) {
             unsigned long long v = ULLONG_MAX;
             int t = INT_MAX;
@@ -190,42 +211,87 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
                 const ClusterSmem *o = cluster.map_shared_rank(&sm, r);
                 if (better(o->slice_v, o->slice_t, v, t)) { v = o->slice_v; t = o->slice_t; }
             }
-            sm.greedy[step] = t;
-            sm.totals[step] = (long long)v;
+            if (old >= 0 && cluster.map_shared_rank(&sm, old / kSlice)->slice_old == v) t = old;
+            sm.step_t = t;
+            sm.step_v = v;
         }
         __syncthreads();
-        const int best = sm.greedy[step];
+    };
+
+    // ---- greedy: each step adds the preset of least total, then lowers
+    // every block's best distortion
+    for (int k = 0; k < 8; k++) {
+        step(-1);
+        const int best = sm.step_t;
+        if (tid == 0) {
+            sm.greedy[k] = best;
+            sm.totals[k] = (long long)sm.step_v;
+        }
         for (int b = tid; b < own; b += kCT) {
-            T d;
-            if (resident) {
-                d = rl[b][best >> 6] + rc[b][best & 63];
-            } else {
-                const int64_t g = F.block_start + b0 + b;
-                d = (T)(dl[g * 64 + (best >> 6)] + dc[g * 64 + (best & 63)]);
-            }
+            const T d = dist(b, best);
             if (d < cur[b]) cur[b] = d;
         }
         __syncthreads();
     }
+    if (tid < 4) {
+        for (int j = 0; j < 8; j++) sm.refined[tid][j] = j < (1 << tid) ? sm.greedy[j] : 0;
+        sm.ref_totals[tid] = sm.totals[(1 << tid) - 1];
+    }
+    __syncthreads();
 
-    // N in {1, 2, 4, 8} by J (ties to the smaller N); block ids over the set
+    // ---- re-optimisation of the sets of size 2, 4, 8, one preset at a
+    // time: slot k is re-chosen against every block's least distortion over
+    // the other slots; passes end when one changes nothing (every CTA takes
+    // the same decisions, so the cluster's barriers stay matched)
+    for (int lg = 1; lg <= 3 && refine_passes > 0; lg++) {
+        const int sz = 1 << lg;
+        for (int pass = 0; pass < refine_passes; pass++) {
+            bool changed = false;
+            for (int k = 0; k < sz; k++) {
+                for (int b = tid; b < own; b += kCT) {
+                    T m = (T)~0ull;
+                    for (int j = 0; j < sz; j++) {
+                        if (j == k) continue;
+                        const T d = dist(b, sm.refined[lg][j]);
+                        m = d < m ? d : m;
+                    }
+                    cur[b] = m;
+                }
+                __syncthreads();
+                const int old = sm.refined[lg][k];
+                step(old);
+                const int best = sm.step_t;
+                changed = changed || best != old;
+                __syncthreads();   // every thread has read the set before it changes
+                if (tid == 0) {
+                    sm.refined[lg][k] = best;
+                    sm.ref_totals[lg] = (long long)sm.step_v;
+                }
+                __syncthreads();
+            }
+            if (!changed) break;
+        }
+    }
+
+    // ---- N in {1, 2, 4, 8} by J (ties to the smaller N); block ids over the set
     int bl = 0;
     long long bj = 0;
     for (int lg = 0; lg < 4; lg++) {
-        const long long j = sm.totals[(1 << lg) - 1] + F.lambda * (long long)B * lg;
+        const long long j = sm.ref_totals[lg] + F.lambda * (long long)B * lg;
         if (lg == 0 || j < bj) { bl = lg; bj = j; }
     }
     const int N = 1 << bl;
     if (rank == 0 && tid == 0) {
         SearchResultDev &r = res[f];
         for (int j = 0; j < 8; j++) {
-            r.presets[j] = sm.greedy[j];
+            // entries past N keep the greedy order
+            r.presets[j] = j < N ? sm.refined[bl][j] : sm.greedy[j];
             r.greedy[j] = sm.greedy[j];
             r.totals[j] = sm.totals[j];
         }
         for (int lg = 0; lg < 4; lg++) {
-            for (int j = 0; j < 8; j++) r.refined[lg][j] = j < (1 << lg) ? sm.greedy[j] : 0;
-            r.ref_totals[lg] = sm.totals[(1 << lg) - 1];
+            for (int j = 0; j < 8; j++) r.refined[lg][j] = sm.refined[lg][j];
+            r.ref_totals[lg] = sm.ref_totals[lg];
         }
         r.cost = bj;
         r.npresets = N;
@@ -235,7 +301,7 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
         int id = 0;
         long long bestd = LLONG_MAX;
         for (int j = 0; j < N; j++) {
-            const int t = sm.greedy[j];
+            const int t = sm.refined[bl][j];
             const long long v = dl[g * 64 + (t >> 6)] + dc[g * 64 + (t & 63)];
             if (v < bestd) { bestd = v; id = j; }
         }
@@ -256,7 +322,7 @@ bool preset_cluster_fits(const SearchBatch &b)
 
 cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, const long long *dc,
                                    SearchResultDev *results, uint8_t *block_ids, bool narrow,
-                                   cudaStream_t s)
+                                   int refine_passes, cudaStream_t s)
 {
     static_assert(kSlice <= kCT && kCT % 64 == 0 && kTuples % kCT == 0, "thread layout");
     constexpr size_t kSmem = sizeof(ClusterSmem);
@@ -286,9 +352,9 @@ cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, co
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return narrow ? cudaLaunchKernelEx(&cfg, preset_cluster_kernel<unsigned>, b, dl, dc, results,
-                                       block_ids)
+                                       block_ids, refine_passes)
                   : cudaLaunchKernelEx(&cfg, preset_cluster_kernel<unsigned long long>, b, dl, dc,
-                                       results, block_ids);
+                                       results, block_ids, refine_passes);
 }
 
 }  // namespace cdefgb

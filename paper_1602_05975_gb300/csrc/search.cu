@@ -836,12 +836,12 @@ static cudaError_t select_presets(const SearchBatch &b, const long long *dl, con
                                   int refine_passes, int width, const uint8_t *skipped, bool sse,
                                   cudaStream_t s)
 {
-    if (width == 64 && !skipped && refine_passes == 0 && preset_cluster_fits(b)) {
+    if (width == 64 && !skipped && preset_cluster_fits(b)) {
         // 8-bit squared errors: a block's luma and chroma entries sum to at
         // most 3 x 4096 x 255^2 < 2^32
         bool narrow = sse;
         for (int i = 0; i < b.n; i++) narrow = narrow && b.f[i].bitdepth == 8;
-        return launch_presets_cluster(b, dl, dc, results, block_ids, narrow, s);
+        return launch_presets_cluster(b, dl, dc, results, block_ids, narrow, refine_passes, s);
     }
     void *ctl = tot + (size_t)b.n * width * width;
     return launch_presets(b, dl, dc, cur, tot, ctl, results, block_ids, status, refine_passes,
