@@ -169,15 +169,16 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
 cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *vars,
                                long long *dist_luma, long long *dist_chroma, uint8_t *skipped,
                                cudaStream_t s);
-// The preset selection of the 64-combination search (greedy, then up to
-// `refine_passes` re-optimisation passes), one cluster of 8 CTAs per frame
-// (no grid-wide barrier); preset_cluster_fits: every frame's blocks fit
-// the kernel's per-CTA state.
+// The preset selection (greedy, then up to `refine_passes` re-optimisation
+// passes), one cluster of 8 CTAs per frame (no grid-wide barrier);
+// preset_cluster_fits: every frame's blocks fit the kernel's per-CTA state.
+// `width` 64 or 128 and `skipped` as for launch_presets.
 bool preset_cluster_fits(const SearchBatch &b);
 // `narrow`: every table entry is below 2^32 (the squared error of 8-bit frames).
 cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, const long long *dc,
                                    SearchResultDev *results, uint8_t *block_ids, bool narrow,
-                                   int refine_passes, cudaStream_t s);
+                                   int refine_passes, int width, const uint8_t *skipped,
+                                   cudaStream_t s);
 // The preset selection alone (one cooperative launch); `ctl` is the control
 // block that follows `tot` in the scratch.
 // `width`: combinations per plane group in the tables (64 or 128; presets

@@ -1,17 +1,19 @@
-// The greedy preset search of section 5 (eq. 15) with one thread-block
+// The preset selection of section 5 (eq. 15) with one thread-block
 // cluster per frame: no grid-wide barrier.  The eight CTAs of a cluster
-// split the frame's filter blocks; each computes, for all 4096 (luma pair,
-// chroma pair) presets t, its blocks' sum_b min(best_b, D_b(t)) into its
-// own shared memory; after a cluster barrier CTA r adds the eight partial
-// sums of presets [512 r, 512 r + 512) through distributed shared memory
-// and finds their least total (lowest index on ties); after a second
-// barrier every CTA takes the least of the eight slice minima, so all of
-// them agree on the step's preset and lower their blocks' best distortion.
-// The re-optimisation passes (section 5) re-choose one slot of a set at a
-// time with the same step, each block's best distortion being its least
-// over the set's other slots.  Then N in {1, 2, 4, 8} by J and each block's
-// preset id, as in presets.cu.  Used for the 64-combination search (the
-// 128-combination search takes the grid-wide kernel).
+// split the frame's filter blocks; in a greedy step each computes, for all
+// W x W (luma combination, chroma combination) presets t (W = 64, or 128
+// with the skip-condition bit), its blocks' sum_b min(best_b, D_b(t)) into
+// its own shared memory; after a cluster barrier CTA r adds the eight
+// partial sums of its eighth of the presets through distributed shared
+// memory and finds their least total (lowest index on ties); after a
+// second barrier every CTA takes the least of the eight slice minima, so
+// all of them agree on the step's preset and lower their blocks' best
+// distortion.  The re-optimisation passes (section 5) re-choose one slot
+// of a set at a time with the same step, each block's best distortion
+// being its least over the set's other slots.  Then N in {1, 2, 4, 8} by J
+// and each block's preset id, as in presets.cu.  Filter blocks flagged
+// skipped (section 4, 128-combination search) add nothing to any total,
+// do not count in J's B and take id 0.
 #include <climits>
 #include <cooperative_groups.h>
 
@@ -24,16 +26,26 @@ namespace {
 
 constexpr int kCS = 8;                   // CTAs per cluster (per frame)
 constexpr int kCT = 512;                 // threads per CTA
-constexpr int kTuples = 4096;            // presets of the 64-combination search
-constexpr int kPer = kTuples / kCT;      // presets per thread
-constexpr int kSlice = kTuples / kCS;    // presets reduced by one CTA
+constexpr int kPer = 8;                  // presets per thread and group
 constexpr int kMaxOwn = 2048;            // blocks one CTA can hold (frames up to 16384 blocks)
-constexpr int kTabBytes = 128 * 1024;    // the CTA's luma and chroma table rows
 
+// Per combination count W: W x W presets, in groups of kCT x kPer per
+// thread pass; each CTA reduces an eighth of them; shared memory left for
+// the table rows.
+template <int kW>
+struct Geo {
+    static constexpr int kTuples = kW * kW;
+    static constexpr int kGroups = kTuples / (kCT * kPer);
+    static constexpr int kSlice = kTuples / kCS;
+    static constexpr int kTabBytes = kW == 64 ? 128 * 1024 : 64 * 1024;
+    static_assert(kTuples % (kCT * kPer) == 0 && kSlice % kCT == 0 && kCT % kW == 0, "layout");
+};
+
+template <int kW>
 struct ClusterSmem {
-    unsigned long long part[kTuples];            // this CTA's partial totals
+    unsigned long long part[kW * kW];            // this CTA's partial totals
     unsigned long long cur[kMaxOwn];             // best distortion of the CTA's blocks
-    alignas(16) unsigned char tab[kTabBytes];    // table rows: luma [cap][64], chroma [cap][64]
+    alignas(16) unsigned char tab[Geo<kW>::kTabBytes];   // table rows: luma [cap][W], chroma [cap][W]
     unsigned long long red_v[kCT / 32];
     int red_t[kCT / 32];
     unsigned long long slice_v;                  // this CTA's slice minimum
@@ -41,6 +53,7 @@ struct ClusterSmem {
     unsigned long long slice_old;                // total of the step's current preset (its slice's CTA)
     int step_t;                                  // the step's chosen preset
     unsigned long long step_v;                   // and its total
+    int coded;                                   // blocks of the frame that signal a preset id
     int greedy[8];
     long long totals[8];
     int refined[4][8];                           // sets of size 1, 2, 4, 8 (re-optimised)
@@ -76,8 +89,8 @@ __device__ __forceinline__ void load8(const T *p, T (&v)[kPer])
 // 32-bit entries (8-bit squared errors: a block's luma and chroma entries
 // sum to at most 3 x 4096 x 255^2 < 2^30) four blocks' minima are summed
 // in 32 bits before the 64-bit totals.
-template <typename T>
-__device__ __forceinline__ void sum_blocks(const T (*rl)[64], const T (*rc)[64], const T *cur,
+template <typename T, int kW>
+__device__ __forceinline__ void sum_blocks(const T (*rl)[kW], const T (*rc)[kW], const T *cur,
                                            int n, int c, int lq, unsigned long long (&a)[kPer])
 {
     constexpr int kChunk = sizeof(T) == 4 ? 4 : 1;
@@ -104,15 +117,18 @@ __device__ __forceinline__ void sum_blocks(const T (*rl)[64], const T (*rc)[64],
 }
 
 // T: the width of the per-block minima; 32 bits when every table entry of
-// the call is an 8-bit squared error (below 2^30).
-template <typename T>
+// the call is an 8-bit squared error (below 2^30).  kW: combinations per
+// plane group (64, or 128 with the skip-condition bit); `skipped` (W = 128
+// only, may be null): one flag per filter block.
+template <typename T, int kW>
 __global__ void __launch_bounds__(kCT, 1)
 preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long *__restrict__ dl,
                       const long long *__restrict__ dc, SearchResultDev *res, uint8_t *block_ids,
-                      int refine_passes)
+                      const uint8_t *skipped, int refine_passes)
 {
+    using G = Geo<kW>;
     extern __shared__ __align__(16) uint8_t smem_raw[];
-    ClusterSmem &sm = *reinterpret_cast<ClusterSmem *>(smem_raw);
+    ClusterSmem<kW> &sm = *reinterpret_cast<ClusterSmem<kW> *>(smem_raw);
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int f = blockIdx.x / kCS;
@@ -124,62 +140,81 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
     const unsigned long long lp = allowed_pairs(F, 0), cp = allowed_pairs(F, 1);
     const bool full = (lp & cp) == ~0ull;
     // table rows of `cap` blocks fit; with own <= cap they stay for all steps
-    constexpr int cap = kTabBytes / (2 * 64 * (int)sizeof(T));
-    T (*rl)[64] = reinterpret_cast<T (*)[64]>(sm.tab);
-    T (*rc)[64] = rl + cap;
+    constexpr int cap = G::kTabBytes / (2 * kW * (int)sizeof(T));
+    T (*rl)[kW] = reinterpret_cast<T (*)[kW]>(sm.tab);
+    T (*rc)[kW] = rl + cap;
     T *cur = reinterpret_cast<T *>(sm.cur);
     const bool resident = own <= cap;
     auto stage = [&](int s0, int n) {
-        for (int i = tid; i < n * 64; i += kCT) {
-            const int bb = i >> 6, q = i & 63;
-            const int64_t g = (int64_t)(F.block_start + b0 + s0 + bb) * 64 + q;
+        for (int i = tid; i < n * kW; i += kCT) {
+            const int bb = i / kW, q = i % kW;
+            const int64_t g = (int64_t)(F.block_start + b0 + s0 + bb) * kW + q;
             rl[bb][q] = (T)dl[g];
             rc[bb][q] = (T)dc[g];
         }
     };
+    auto skip = [&](int b) { return skipped && skipped[F.block_start + b0 + b]; };
 
-    for (int b = tid; b < own; b += kCT) cur[b] = (T)~0ull;
+    // a skipped block's best distortion stays 0: it adds nothing to a total
+    for (int b = tid; b < own; b += kCT) cur[b] = skip(b) ? (T)0 : (T)~0ull;
+    if (tid == 0) sm.coded = 0;
     if (resident) stage(0, own);
     __syncthreads();
+    if (skipped) {
+        int n = 0;
+        for (int b = tid; b < B; b += kCT) n += skipped[F.block_start + b] == 0;
+        atomicAdd(&sm.coded, n);
+    } else if (tid == 0) {
+        sm.coded = B;
+    }
 
-    // thread tid: chroma pair c, luma pairs lq .. lq + 7 (presets (lq + j) * 64 + c)
-    const int c = tid & 63, lq = (tid >> 6) * kPer;
     // D_b(t) of the CTA's block b
     auto dist = [&](int b, int t) -> T {
-        if (resident) return rl[b][t >> 6] + rc[b][t & 63];
+        if (resident) return rl[b][t / kW] + rc[b][t % kW];
         const int64_t g = F.block_start + b0 + b;
-        return (T)(dl[g * 64 + (t >> 6)] + dc[g * 64 + (t & 63)]);
+        return (T)(dl[g * kW + t / kW] + dc[g * kW + t % kW]);
     };
     // One step: the cluster's least total sum_b min(cur_b, D_b(t)) over the
     // allowed presets t (lowest index on ties) into sm.step_t / sm.step_v,
     // identical in every CTA; with old >= 0 (re-optimisation of a slot
     // holding preset `old`) old is kept when its total attains the minimum.
     auto step = [&](int old) {
-        unsigned long long a[kPer];
+        // thread tid, group g: chroma combination c, luma combinations lq .. lq + 7
+        const int c = tid % kW;
+#pragma unroll 1
+        for (int g = 0; g < G::kGroups; g++) {
+            const int lq = (tid / kW) * kPer + g * (kCT * kPer / kW);
+            unsigned long long a[kPer];
 #pragma unroll
-        for (int j = 0; j < kPer; j++) a[j] = 0;
-        for (int s0 = 0; s0 < own; s0 += cap) {
-            const int n = min(cap, own - s0);
-            if (!resident) {
-                stage(s0, n);
-                __syncthreads();
+            for (int j = 0; j < kPer; j++) a[j] = 0;
+            for (int s0 = 0; s0 < own; s0 += cap) {
+                const int n = min(cap, own - s0);
+                if (!resident) {
+                    stage(s0, n);
+                    __syncthreads();
+                }
+                sum_blocks<T, kW>(rl, rc, cur + s0, n, c, lq, a);
+                if (!resident) __syncthreads();
             }
-            sum_blocks<T>(rl, rc, cur + s0, n, c, lq, a);
-            if (!resident) __syncthreads();
-        }
 #pragma unroll
-        for (int j = 0; j < kPer; j++) sm.part[(lq + j) * 64 + c] = a[j];
+            for (int j = 0; j < kPer; j++) sm.part[(lq + j) * kW + c] = a[j];
+        }
         cluster.sync();
 
         // this CTA's slice: the eight partial sums, then its least total
         unsigned long long bv = ULLONG_MAX;
         int bt = INT_MAX;
-        if (tid < kSlice) {   // one preset of the slice per thread
-            const int t = rank * kSlice + tid;
+#pragma unroll 1
+        for (int i = 0; i < G::kSlice / kCT; i++) {
+            const int t = rank * G::kSlice + i * kCT + tid;
             unsigned long long tot = 0;
 #pragma unroll
             for (int r = 0; r < kCS; r++) tot += cluster.map_shared_rank(sm.part, r)[t];
-            if (full || ((lp >> (t >> 6)) & (cp >> (t & 63)) & 1)) { bv = tot; bt = t; }
+            // pairs: the combination without its skip-condition bit
+            if ((full || ((lp >> ((t / kW) & 63)) & (cp >> (t & 63)) & 1)) && better(tot, t, bv, bt)) {
+                bv = tot;
+                bt = t;
+            }
             if (t == old) sm.slice_old = tot;
         }
 #pragma unroll
@@ -208,10 +243,10 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
             unsigned long long v = ULLONG_MAX;
             int t = INT_MAX;
             for (int r = 0; r < kCS; r++) {
-                const ClusterSmem *o = cluster.map_shared_rank(&sm, r);
+                const ClusterSmem<kW> *o = cluster.map_shared_rank(&sm, r);
                 if (better(o->slice_v, o->slice_t, v, t)) { v = o->slice_v; t = o->slice_t; }
             }
-            if (old >= 0 && cluster.map_shared_rank(&sm, old / kSlice)->slice_old == v) t = old;
+            if (old >= 0 && cluster.map_shared_rank(&sm, old / G::kSlice)->slice_old == v) t = old;
             sm.step_t = t;
             sm.step_v = v;
         }
@@ -229,7 +264,7 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
         }
         for (int b = tid; b < own; b += kCT) {
             const T d = dist(b, best);
-            if (d < cur[b]) cur[b] = d;
+            if (d < cur[b]) cur[b] = d;   // never for a skipped block (0)
         }
         __syncthreads();
     }
@@ -249,7 +284,7 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
             bool changed = false;
             for (int k = 0; k < sz; k++) {
                 for (int b = tid; b < own; b += kCT) {
-                    T m = (T)~0ull;
+                    T m = skip(b) ? (T)0 : (T)~0ull;
                     for (int j = 0; j < sz; j++) {
                         if (j == k) continue;
                         const T d = dist(b, sm.refined[lg][j]);
@@ -277,7 +312,7 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
     int bl = 0;
     long long bj = 0;
     for (int lg = 0; lg < 4; lg++) {
-        const long long j = sm.ref_totals[lg] + F.lambda * (long long)B * lg;
+        const long long j = sm.ref_totals[lg] + F.lambda * (long long)sm.coded * lg;
         if (lg == 0 || j < bj) { bl = lg; bj = j; }
     }
     const int N = 1 << bl;
@@ -299,11 +334,13 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
     for (int b = tid; b < own; b += kCT) {
         const int64_t g = F.block_start + b0 + b;
         int id = 0;
-        long long bestd = LLONG_MAX;
-        for (int j = 0; j < N; j++) {
-            const int t = sm.refined[bl][j];
-            const long long v = dl[g * 64 + (t >> 6)] + dc[g * 64 + (t & 63)];
-            if (v < bestd) { bestd = v; id = j; }
+        if (!skip(b)) {
+            long long bestd = LLONG_MAX;
+            for (int j = 0; j < N; j++) {
+                const int t = sm.refined[bl][j];
+                const long long v = dl[g * kW + t / kW] + dc[g * kW + t % kW];
+                if (v < bestd) { bestd = v; id = j; }
+            }
         }
         block_ids[g] = (uint8_t)id;
     }
@@ -311,32 +348,23 @@ preset_cluster_kernel(const __grid_constant__ SearchBatch batch, const long long
     cluster.sync();
 }
 
-}  // namespace
-
-bool preset_cluster_fits(const SearchBatch &b)
+template <typename T, int kW>
+cudaError_t launch_one(const SearchBatch &b, const long long *dl, const long long *dc,
+                       SearchResultDev *results, uint8_t *block_ids, const uint8_t *skipped,
+                       int refine_passes, cudaStream_t s)
 {
-    for (int i = 0; i < b.n; i++)
-        if ((b.f[i].fb_cols * b.f[i].fb_rows + kCS - 1) / kCS > kMaxOwn) return false;
-    return true;
-}
-
-cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, const long long *dc,
-                                   SearchResultDev *results, uint8_t *block_ids, bool narrow,
-                                   int refine_passes, cudaStream_t s)
-{
-    static_assert(kSlice <= kCT && kCT % 64 == 0 && kTuples % kCT == 0, "thread layout");
-    constexpr size_t kSmem = sizeof(ClusterSmem);
+    constexpr size_t kSmem = sizeof(ClusterSmem<kW>);
+    static_assert(kSmem <= 227 * 1024, "shared memory of one CTA");
     static int configured_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != configured_dev) {
-        for (auto *k : {preset_cluster_kernel<unsigned>, preset_cluster_kernel<unsigned long long>}) {
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)kSmem);
-            if (e == cudaSuccess && kCS > 8)
-                e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            if (e != cudaSuccess) return e;
-        }
+        cudaError_t e = cudaFuncSetAttribute(preset_cluster_kernel<T, kW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (e == cudaSuccess && kCS > 8)
+            e = cudaFuncSetAttribute(preset_cluster_kernel<T, kW>,
+                                     cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
         configured_dev = dev;
     }
     cudaLaunchConfig_t cfg = {};
@@ -351,10 +379,32 @@ cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, co
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return narrow ? cudaLaunchKernelEx(&cfg, preset_cluster_kernel<unsigned>, b, dl, dc, results,
-                                       block_ids, refine_passes)
-                  : cudaLaunchKernelEx(&cfg, preset_cluster_kernel<unsigned long long>, b, dl, dc,
-                                       results, block_ids, refine_passes);
+    return cudaLaunchKernelEx(&cfg, preset_cluster_kernel<T, kW>, b, dl, dc, results, block_ids,
+                              skipped, refine_passes);
+}
+
+}  // namespace
+
+bool preset_cluster_fits(const SearchBatch &b)
+{
+    for (int i = 0; i < b.n; i++)
+        if ((b.f[i].fb_cols * b.f[i].fb_rows + kCS - 1) / kCS > kMaxOwn) return false;
+    return true;
+}
+
+cudaError_t launch_presets_cluster(const SearchBatch &b, const long long *dl, const long long *dc,
+                                   SearchResultDev *results, uint8_t *block_ids, bool narrow,
+                                   int refine_passes, int width, const uint8_t *skipped,
+                                   cudaStream_t s)
+{
+    if (width == 128)
+        return narrow ? launch_one<unsigned, 128>(b, dl, dc, results, block_ids, skipped,
+                                                  refine_passes, s)
+                      : launch_one<unsigned long long, 128>(b, dl, dc, results, block_ids, skipped,
+                                                            refine_passes, s);
+    return narrow ? launch_one<unsigned, 64>(b, dl, dc, results, block_ids, nullptr, refine_passes, s)
+                  : launch_one<unsigned long long, 64>(b, dl, dc, results, block_ids, nullptr,
+                                                       refine_passes, s);
 }
 
 }  // namespace cdefgb

@@ -827,8 +827,8 @@ cudaError_t launch_dist_eq14(const SearchBatch &b, long long *dl, long long *dc,
 
 }  // namespace
 
-// The preset selection: the cluster-per-frame kernel where it applies (64
-// combinations, greedy only), else the grid-wide cooperative kernel.
+// The preset selection: the cluster-per-frame kernel when every frame's
+// blocks fit its per-CTA state, else the grid-wide cooperative kernel.
 // `sse`: the tables hold squared errors (not eq. 14).
 static cudaError_t select_presets(const SearchBatch &b, const long long *dl, const long long *dc,
                                   unsigned long long *cur, unsigned long long *tot,
@@ -836,12 +836,13 @@ static cudaError_t select_presets(const SearchBatch &b, const long long *dl, con
                                   int refine_passes, int width, const uint8_t *skipped, bool sse,
                                   cudaStream_t s)
 {
-    if (width == 64 && !skipped && preset_cluster_fits(b)) {
+    if (preset_cluster_fits(b)) {
         // 8-bit squared errors: a block's luma and chroma entries sum to at
-        // most 3 x 4096 x 255^2 < 2^32
+        // most 3 x 4096 x 255^2 < 2^30
         bool narrow = sse;
         for (int i = 0; i < b.n; i++) narrow = narrow && b.f[i].bitdepth == 8;
-        return launch_presets_cluster(b, dl, dc, results, block_ids, narrow, refine_passes, s);
+        return launch_presets_cluster(b, dl, dc, results, block_ids, narrow, refine_passes, width,
+                                      skipped, s);
     }
     void *ctl = tot + (size_t)b.n * width * width;
     return launch_presets(b, dl, dc, cur, tot, ctl, results, block_ids, status, refine_passes,
