@@ -276,19 +276,27 @@ int cdef_search_strengths_coded(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
  * A field of 0 means "autotuned": the first search of a batch shape (frame
  * count, sizes and bit depths) on a context times every configuration on
  * that call's own inputs, on the call's stream, and keeps the fastest for
- * the later searches of that shape. */
+ * the later searches of that shape.
+ *   preset_kernel      : the kernel of the preset selection (eq. 15 and the
+ *                        re-optimisation); both give identical results.
+ *                        0 (default): one thread-block cluster per frame for
+ *                        frames of up to 16384 filter blocks, else one
+ *                        grid-wide cooperative kernel; 1: always the
+ *                        grid-wide kernel.  Not autotuned; set_tuning(NULL)
+ *                        resets it to 0. */
 typedef struct {
     int32_t search_groups;
     int32_t search_ctas_per_sm;
-    int32_t reserved[2];
+    int32_t preset_kernel;
+    int32_t reserved;      /* 0 */
 } cdef_tuning;
 
 /* Fix the configuration (NULL or zero fields: autotune, the default).
  * CDEF_ERR_ARG for a value outside the lists above.  Host only. */
 int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *tuning);
 
-/* The configuration the context's last search ran with (all zero before
- * the first search).  Host only. */
+/* The configuration the context's last search ran with (search fields
+ * zero before the first search; preset_kernel as set).  Host only. */
 int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
 
 /* Distortion measure of cdef_search_strengths (section 5):

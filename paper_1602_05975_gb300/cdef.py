@@ -57,7 +57,7 @@ class PresetCoded(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("search_groups", C.c_int32), ("search_ctas_per_sm", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("preset_kernel", C.c_int32), ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -325,9 +325,12 @@ class Context:
         _check(self._lib.cdef_ctx_set_overlap(self.handle, int(bool(enable))),
                "cdef_ctx_set_overlap")
 
-    def set_tuning(self, search_groups: int = 0, search_ctas_per_sm: int = 0):
-        """Fix the strength search's launch configuration (0 = autotune)."""
-        t = Tuning(search_groups, search_ctas_per_sm)
+    def set_tuning(self, search_groups: int = 0, search_ctas_per_sm: int = 0,
+                   preset_kernel: int = 0):
+        """Fix the strength search's launch configuration (0 = autotune);
+        preset_kernel 1: the preset selection always in the grid-wide
+        kernel (0: one thread-block cluster per frame where frames fit)."""
+        t = Tuning(search_groups, search_ctas_per_sm, preset_kernel)
         _check(self._lib.cdef_ctx_set_tuning(self.handle, C.byref(t)), "cdef_ctx_set_tuning")
 
     def tuning(self):

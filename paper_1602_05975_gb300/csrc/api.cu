@@ -38,6 +38,8 @@ struct cdef_ctx {
     int metric;                   // search distortion: 0 squared error, 1 eq. 14
     uint64_t pairs[2];            // allowed (S_p, S_s) pairs of the search (luma, chroma)
     int search_key_refine;        // refine_passes search_exec was recorded with
+    bool grid_presets;            // preset selection always in the grid-wide kernel
+    bool search_key_grid;         // and what search_exec was recorded with
     bool stage_timing;            // record stage events in the search graph
     bool search_key_timing;       // and whether search_exec holds them
     bool stage_valid;             // the events hold the last search's stages
@@ -309,11 +311,14 @@ int cdef_ctx_set_tuning(cdef_ctx *ctx, const cdef_tuning *t)
     if (!ctx) return CDEF_ERR_ARG;
     if (!t) {
         ctx->forced = {0, 0};
+        ctx->grid_presets = false;
         return CDEF_OK;
     }
     const int g = t->search_groups, c = t->search_ctas_per_sm;
     if (!(g == 0 || g == 1 || g == 2 || g == 4) || c < 0 || c > 2) return CDEF_ERR_ARG;
+    if (t->preset_kernel < 0 || t->preset_kernel > 1 || t->reserved != 0) return CDEF_ERR_ARG;
     ctx->forced = {g, c};
+    ctx->grid_presets = t->preset_kernel == 1;
     return CDEF_OK;
 }
 
@@ -384,6 +389,7 @@ int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last)
     memset(last, 0, sizeof(*last));
     last->search_groups = ctx->last.groups;
     last->search_ctas_per_sm = ctx->last.ctas_per_sm;
+    last->preset_kernel = ctx->grid_presets ? 1 : 0;
     return CDEF_OK;
 }
 
@@ -680,11 +686,13 @@ int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long 
             (ctx->forced.ctas_per_sm > 0 && t.ctas_per_sm != ctx->forced.ctas_per_sm))
             continue;
         e = launch_search(b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status, ctx->work,
-                          t, ctx->refine_passes, s, skipped);
+                          t, ctx->refine_passes, s, skipped, nullptr, nullptr, nullptr,
+                          ctx->grid_presets);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         if (e == cudaSuccess)
             e = launch_search(b, dl, dc, cur, tot, ctx->dev_results, block_ids, ctx->status,
-                              ctx->work, t, ctx->refine_passes, s, skipped);
+                              ctx->work, t, ctx->refine_passes, s, skipped, nullptr, nullptr,
+                              nullptr, ctx->grid_presets);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -823,14 +831,15 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
                       ctx->search_key_tune.groups == tune.groups &&
                       ctx->search_key_tune.ctas_per_sm == tune.ctas_per_sm &&
                       ctx->search_key_refine == ctx->refine_passes &&
-                      ctx->search_key_timing == ctx->stage_timing;
+                      ctx->search_key_timing == ctx->stage_timing &&
+                      ctx->search_key_grid == ctx->grid_presets;
     cudaError_t e = same ? cudaSuccess : cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess && !same) {
         const cudaError_t le = launch_search(*b, dl, dc, cur, tot, ctx->dev_results, block_ids,
                                              ctx->status, work, tune, ctx->refine_passes,
                                              ctx->capture, skipped,
                                              ctx->stage_timing ? ctx->stage_ev : nullptr,
-                                             wide_dirs, wide_vars);
+                                             wide_dirs, wide_vars, ctx->grid_presets);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(ctx->capture, &graph);
         if (e == cudaSuccess && le != cudaSuccess) e = le;
@@ -851,6 +860,7 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
                 memcpy(ctx->search_ptrs, ptrs, sizeof(ptrs));
                 ctx->search_key_tune = tune;
                 ctx->search_key_refine = ctx->refine_passes;
+                ctx->search_key_grid = ctx->grid_presets;
                 ctx->search_key_timing = ctx->stage_timing;
             }
         } else if (ctx->search_key) {

@@ -151,6 +151,8 @@ inline SearchTune default_search_tune(int total_blocks, int sms)
 // `stage_events` non-null: three events recorded before the distortion
 // kernel, between it and the preset selection, and after it (event nodes
 // when the stream is being captured into a graph).
+// `grid_presets`: the preset selection in the grid-wide kernel even where
+// the cluster-per-frame kernel applies.
 // `skipped` non-null: the 128-combination search of section 5 with section
 // 4's skip semantics (each frame's `coded` map; tables of 128 entries per
 // block; `skipped` receives one flag per block); null: 64 combinations.
@@ -160,7 +162,8 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
                           int refine_passes, cudaStream_t s, uint8_t *skipped = nullptr,
                           const cudaEvent_t *stage_events = nullptr,
-                          uint8_t *wide_dirs = nullptr, int32_t *wide_vars = nullptr);
+                          uint8_t *wide_dirs = nullptr, int32_t *wide_vars = nullptr,
+                          bool grid_presets = false);
 // Section 5's tables for 4:2:2, 4:4:4 and 12-bit frames (32-bit arithmetic
 // per sample): the direction maps of every frame into `dirs` / `vars` (at
 // each frame's map_start), then one CTA per filter block and plane group.

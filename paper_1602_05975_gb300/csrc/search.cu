@@ -834,9 +834,9 @@ static cudaError_t select_presets(const SearchBatch &b, const long long *dl, con
                                   unsigned long long *cur, unsigned long long *tot,
                                   SearchResultDev *results, uint8_t *block_ids, int *status,
                                   int refine_passes, int width, const uint8_t *skipped, bool sse,
-                                  cudaStream_t s)
+                                  bool grid_presets, cudaStream_t s)
 {
-    if (preset_cluster_fits(b)) {
+    if (!grid_presets && preset_cluster_fits(b)) {
         // 8-bit squared errors: a block's luma and chroma entries sum to at
         // most 3 x 4096 x 255^2 < 2^30
         bool narrow = sse;
@@ -866,7 +866,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
                           int refine_passes, cudaStream_t s, uint8_t *skipped,
                           const cudaEvent_t *stage_events, uint8_t *wide_dirs,
-                          int32_t *wide_vars)
+                          int32_t *wide_vars, bool grid_presets)
 {
     cudaError_t e = stage_mark(stage_events, 0, s);
     if (e != cudaSuccess) return e;
@@ -877,7 +877,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
         if (e != cudaSuccess) return e;
         const int width = skipped ? 128 : 64;
         e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
-                           refine_passes, width, skipped, true, s);
+                           refine_passes, width, skipped, true, grid_presets, s);
         return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
     }
     if (tune.groups == 8) {   // eq. 14 tables
@@ -885,7 +885,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
         if (e != cudaSuccess) return e;
         e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
-                           refine_passes, 64, nullptr, false, s);
+                           refine_passes, 64, nullptr, false, grid_presets, s);
         return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
     }
     switch (tune.groups) {
@@ -897,7 +897,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     if (e != cudaSuccess) return e;
     const int width = skipped ? 128 : 64;
     e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
-                       refine_passes, width, skipped, true, s);
+                       refine_passes, width, skipped, true, grid_presets, s);
     return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
 }
 

@@ -303,9 +303,9 @@ def test_search_every_launch_configuration(cdef, ctx, ref, groups, ctas):
 
 
 def test_tuning_rejects_unknown_configurations(cdef, ctx):
-    for g, c in [(3, 1), (8, 1), (1, 3), (-1, 0)]:
+    for g, c, k in [(3, 1, 0), (8, 1, 0), (1, 3, 0), (-1, 0, 0), (0, 0, 2), (0, 0, -1)]:
         with pytest.raises(cdef.CdefError):
-            ctx.set_tuning(g, c)
+            ctx.set_tuning(g, c, preset_kernel=k)
     ctx.set_tuning(0, 0)
 
 
@@ -410,10 +410,11 @@ def test_stream_order_kept_without_overlap(cdef, ctx, ref):
     _assert_frames_equal(c.to_numpy(), ref.filter_frame(*once, 10, f.params))
 
 
-@pytest.mark.parametrize("passes", [1, 4, 16])
-def test_search_preset_refinement(cdef, ctx, ref, passes):
+@pytest.mark.parametrize("passes,grid", [(1, 0), (4, 0), (16, 0), (1, 1), (4, 1)])
+def test_search_preset_refinement(cdef, ctx, ref, passes, grid):
     """Section 5's one-at-a-time re-optimisation of the presets after the
-    greedy search: presets, N, J and block ids equal the oracle's."""
+    greedy search: presets, N, J and block ids equal the oracle's, with the
+    cluster-per-frame and with the grid-wide preset kernel."""
     from paper_1602_05975_gb300 import synth
     specs = [(200, 136, 8, 16, 610), (136, 72, 10, 32, 611), (320, 192, 8, 64, 612)]
     frames = [synth.make_frame(w, h, bd, q, seed=s) for w, h, bd, q, s in specs]
@@ -421,12 +422,14 @@ def test_search_preset_refinement(cdef, ctx, ref, passes):
     nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
     ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     ctx.set_search_refine(passes)
+    ctx.set_tuning(0, 0, preset_kernel=grid)
     try:
         res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames],
                                          [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames],
                                          damping, lambdas, ids)
     finally:
         ctx.set_search_refine(0)
+        ctx.set_tuning(0, 0)
     assert ctx.status() == 0
     o0 = 0
     for f, r, d, lam in zip(frames, res, damping, lambdas):
@@ -500,8 +503,9 @@ def test_filter_bad_skip_bits_flagged(cdef, ctx):
 
 
 # --------------------------------------------------------------- 128-combination search
-@pytest.mark.parametrize("groups,passes", [(0, 0), (1, 0), (2, 0), (4, 0), (0, 4)])
-def test_search_coded_parity(cdef, ctx, ref, groups, passes):
+@pytest.mark.parametrize("groups,passes,grid", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (4, 0, 0), (0, 4, 0),
+                                               (0, 0, 1), (0, 4, 1)])
+def test_search_coded_parity(cdef, ctx, ref, groups, passes, grid):
     """Section 5 with section 4's skip bits: 128-entry tables, skipped filter
     blocks, presets, N, J and ids equal the oracle's, for every launch
     configuration and with re-optimisation."""
@@ -519,7 +523,7 @@ def test_search_coded_parity(cdef, ctx, ref, groups, passes):
     ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
     dl = torch.zeros(nb * 128, dtype=torch.int64, device="cuda")
     dc = torch.zeros(nb * 128, dtype=torch.int64, device="cuda")
-    ctx.set_tuning(groups, 2 if groups else 0)
+    ctx.set_tuning(groups, 2 if groups else 0, preset_kernel=grid)
     ctx.set_search_refine(passes)
     try:
         res = cdef.cdef_search_strengths_coded(
@@ -707,14 +711,16 @@ def test_search_subset_parity(cdef, ctx, ref, variant, passes):
     nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
     recs = [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames]
     srcs = [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames]
-    configs = [(0, 0)] if variant == "eq14" else [(0, 0), (1, 2), (4, 2)]
+    # (groups, CTAs per SM, preset kernel)
+    configs = [(0, 0, 0), (0, 0, 1)] if variant == "eq14" else [(0, 0, 0), (1, 2, 0), (4, 2, 0),
+                                                                 (0, 0, 1)]
     ctx.set_search_subset(lmask, cmask)
     ctx.set_search_refine(passes)
     if variant == "eq14":
         ctx.set_search_metric("eq14")
     try:
-        for groups, per_sm in configs:
-            ctx.set_tuning(groups, per_sm)
+        for groups, per_sm, grid in configs:
+            ctx.set_tuning(groups, per_sm, preset_kernel=grid)
             ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
             dl = torch.full((nb * width,), -1, dtype=torch.int64, device="cuda")
             dc = torch.full((nb * width,), -1, dtype=torch.int64, device="cuda")
@@ -766,8 +772,8 @@ def _format_search_frame(cdef, fmt, w, h, bd, seed):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("passes", [0, 2])
-def test_search_formats_parity(cdef, ctx, ref, passes):
+@pytest.mark.parametrize("passes,grid", [(0, 0), (2, 0), (2, 1)])
+def test_search_formats_parity(cdef, ctx, ref, passes, grid):
     """Section 5 over 4:4:4, 4:2:2 and 12-bit frames (reading R25), mixed
     with an 8-bit 4:2:0 frame in one call: tables, presets, N, J and ids
     equal the oracle's."""
@@ -780,11 +786,13 @@ def test_search_formats_parity(cdef, ctx, ref, passes):
     dl = torch.full((nb * 64,), -1, dtype=torch.int64, device="cuda")
     dc = torch.full((nb * 64,), -1, dtype=torch.int64, device="cuda")
     ctx.set_search_refine(passes)
+    ctx.set_tuning(0, 0, preset_kernel=grid)
     try:
         res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(r, f.bitdepth) for f, r, _ in frames],
                                          [cdef.frame_from_numpy(s_, f.bitdepth) for f, _, s_ in frames],
                                          damping, lambdas, ids, dl, dc)
     finally:
+        ctx.set_tuning(0, 0)
         ctx.set_search_refine(0)
     assert ctx.status() == 0
     o0 = 0
