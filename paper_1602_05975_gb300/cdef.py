@@ -166,6 +166,15 @@ class Frame:
         return (self.y, self.u, self.v)
 
     def desc(self) -> FrameDesc:
+        """The C descriptor of the frame, kept on the frame while the planes'
+        pointers, pitches and element sizes and the frame's fields stay."""
+        y, u, v = self.y, self.u, self.v
+        key = (y.data_ptr(), u.data_ptr(), v.data_ptr(), y.stride(0), u.stride(0), v.stride(0),
+               y.element_size(), u.element_size(), v.element_size(), self.width, self.height,
+               self.bitdepth, self.chroma)
+        cached = self.__dict__.get("_desc")
+        if cached is not None and cached[0] == key:
+            return cached[1]
         d = FrameDesc()
         cw, ch = chroma_size(self.width, self.height, self.chroma)
         for name, t, w, h in (("y", self.y, self.width, self.height),
@@ -176,6 +185,7 @@ class Frame:
             p.height = h
             p.pitch_bytes = t.stride(0) * t.element_size()
         d.bitdepth = self.bitdepth
+        self.__dict__["_desc"] = (key, d)
         return d
 
     def to_numpy(self):
@@ -378,6 +388,15 @@ def cdef_filter_frames(ctx: Context, srcs, params, outs, stream=None):
            "cdef_filter_frames")
 
 
+def _search_results(presets, fields: int, n: int, npre, cost):
+    """Per frame: its eight presets as tuples of their first `fields` bytes,
+    N and J."""
+    per = C.sizeof(presets) // (8 * n) if n else 0
+    a = np.frombuffer(presets, dtype=np.uint8).reshape(n, 8, per)[:, :, :fields].tolist()
+    return [dict(presets=[tuple(p) for p in a[i]], npresets=npre[i], cost=cost[i])
+            for i in range(n)]
+
+
 def cdef_search_strengths(ctx: Context, recs, srcs, damping, lambdas, block_ids: torch.Tensor,
                           dist_luma: torch.Tensor | None = None,
                           dist_chroma: torch.Tensor | None = None, stream=None):
@@ -396,11 +415,7 @@ def cdef_search_strengths(ctx: Context, recs, srcs, damping, lambdas, block_ids:
         None if dist_chroma is None else dist_chroma.data_ptr(),
         presets, npre, block_ids.data_ptr(), cost, _stream_ptr(stream)),
         "cdef_search_strengths")
-    out = []
-    for i in range(n):
-        ps = [(p.pri_y, p.sec_y, p.pri_uv, p.sec_uv) for p in presets[i * 8:(i + 1) * 8]]
-        out.append(dict(presets=ps, npresets=npre[i], cost=cost[i]))
-    return out
+    return _search_results(presets, 4, n, npre, cost)
 
 
 def cdef_search_strengths_noalloc(recs, srcs, damping, lambdas, block_ids: torch.Tensor,
@@ -426,11 +441,7 @@ def cdef_search_strengths_noalloc(recs, srcs, damping, lambdas, block_ids: torch
               dist_luma.data_ptr(), dist_chroma.data_ptr(), presets, npre,
               block_ids.data_ptr(), cost, _stream_ptr(stream)),
            "cdef_search_strengths_noalloc")
-    out = []
-    for i in range(n):
-        ps = [(p.pri_y, p.sec_y, p.pri_uv, p.sec_uv) for p in presets[i * 8:(i + 1) * 8]]
-        out.append(dict(presets=ps, npresets=npre[i], cost=cost[i]))
-    return out
+    return _search_results(presets, 4, n, npre, cost)
 
 
 def cdef_search_strengths_coded(ctx: Context, recs, srcs, coded, damping, lambdas,
@@ -454,11 +465,7 @@ def cdef_search_strengths_coded(ctx: Context, recs, srcs, coded, damping, lambda
         None if dist_chroma is None else dist_chroma.data_ptr(),
         presets, npre, block_ids.data_ptr(), cost, _stream_ptr(stream)),
         "cdef_search_strengths_coded")
-    out = []
-    for i in range(n):
-        ps = [(p.pri_y, p.sec_y, p.pri_uv, p.sec_uv, p.skip) for p in presets[i * 8:(i + 1) * 8]]
-        out.append(dict(presets=ps, npresets=npre[i], cost=cost[i]))
-    return out
+    return _search_results(presets, 5, n, npre, cost)
 
 
 def preset_index_coded(p) -> int:
