@@ -899,6 +899,46 @@ def test_search_large_periodic_frames(cdef, ctx, ref, sizes, bd):
         assert np.array_equal(ids[off:off + nb], o["block_ids"])
         off += nb
 
+@pytest.mark.parametrize("sizes,bd,grid", [
+    ([(2048, 2176)], 10, 0),                # 1088 blocks: 64-bit minima, 128-wide rows staged
+    ([(4096, 2176), (256, 256)], 8, 0),     # 2176 blocks (staged) with a resident frame
+    ([(2048, 2176)], 8, 1),                 # the grid-wide preset kernel
+])
+def test_search_coded_large_periodic_frames(cdef, ctx, ref, sizes, bd, grid):
+    """The 128-combination search (skipped filter blocks) on frames far
+    larger than the oracle's search can take, through tables known by
+    construction (`periodic_frames.py`): tables, skip-aware presets, N, J
+    and every block's id."""
+    from periodic_frames import periodic_search_case
+    cases = periodic_search_case(ref, sizes, bd, seed=6200 + bd, coded=True)
+    recs = [cdef.frame_from_numpy(c["rec"], bd) for c in cases]
+    srcs = [cdef.frame_from_numpy(c["src"], bd) for c in cases]
+    maps = [torch.from_numpy(c["coded"].reshape(-1)).cuda() for c in cases]
+    nbs = [c["dl"].shape[0] for c in cases]
+    tot = sum(nbs)
+    ids = torch.zeros(tot, dtype=torch.uint8, device="cuda")
+    dl = torch.zeros(tot * 128, dtype=torch.int64, device="cuda")
+    dc = torch.zeros(tot * 128, dtype=torch.int64, device="cuda")
+    ctx.set_tuning(0, 0, preset_kernel=grid)
+    try:
+        res = cdef.cdef_search_strengths_coded(ctx, recs, srcs, maps, [c["damping"] for c in cases],
+                                               [c["lam"] for c in cases], ids, dl, dc)
+    finally:
+        ctx.set_tuning(0, 0)
+    assert ctx.status() == 0
+    dl, dc, ids = dl.cpu().numpy(), dc.cpu().numpy(), ids.cpu().numpy()
+    off = 0
+    for k, c in enumerate(cases):
+        nb, o = nbs[k], c["exp"]
+        assert np.array_equal(dl[off * 128:(off + nb) * 128].reshape(nb, 128), c["dl"])
+        assert np.array_equal(dc[off * 128:(off + nb) * 128].reshape(nb, 128), c["dc"])
+        assert res[k]["npresets"] == o["npresets"]
+        assert res[k]["cost"] == o["cost"]
+        assert ([cdef.preset_index_coded(p) for p in res[k]["presets"][:o["npresets"]]] ==
+                [int(t) for t in o["presets"][:o["npresets"]]])
+        assert np.array_equal(ids[off:off + nb], o["block_ids"])
+        off += nb
+
 
 def test_search_maximum_batch(cdef, ctx, ref):
     """48 frames in one search call equal 48 oracle searches; 49 are refused."""

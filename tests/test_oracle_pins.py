@@ -1245,3 +1245,10 @@ def test_periodic_frame_tables_by_class(ref):
             o = ref.select_presets(dl, dc, c["lam"])
             assert list(o["presets"]) == list(c["exp"]["presets"])
             assert np.array_equal(o["block_ids"], c["exp"]["block_ids"])
+        for c in periodic_search_case(ref, [(512, 384)], bd, seed=6200 + bd, coded=True):
+            dl, dc, sk = ref.distortion_coded(c["rec"], c["src"], bd, c["damping"], c["coded"])
+            assert np.array_equal(dl, c["dl"]) and np.array_equal(dc, c["dc"])
+            assert np.array_equal(sk, c["skipped"]) and 0 < sk.sum() < sk.size
+            o = ref.select_presets_general(dl, dc, 128, sk, c["lam"])
+            assert list(o["presets"]) == list(c["exp"]["presets"])
+            assert np.array_equal(o["block_ids"], c["exp"]["block_ids"])
