@@ -20,6 +20,8 @@
 //   presets.cu.
 #include <climits>
 
+#include <type_traits>
+
 #include "tile.cuh"
 
 namespace cdefgb {
@@ -348,9 +350,11 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
 #pragma unroll 1
     for (int g = 0; g < (kEq14 ? kG : 1); g++) {
         const int p0 = kEq14 ? g * kPP : p0_unit;
-    #pragma unroll 1
-        for (int task = 0; task < 2; task++) {
-            const bool luma = task == 0;
+        // task 0 luma, task 1 chroma; the eq. 14 tables take a copy of the
+        // body per task (luma lanes are summed in one dot product)
+        auto task_body = [&](auto luma_c) {
+            const bool luma = luma_c;
+            const int task = luma ? 0 : 1;
             const int bx = lane >> 2, sub = lane & 3;
             const int blk = warp * 8 + bx;
             const int gby = fby * 8 + warp, gbx = fbx * 8 + bx;
@@ -478,14 +482,22 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                             const uint32_t r8 = __byte_perm(rb, 0, 0x0020);  // r of both lanes, bytes 0, 1
                             if (kEq14) {
                                 const int c = pp * 4 + s;
-                                const int rl = (int)(r8 & 0xffu), rh = (int)(r8 & 0xff00u);
                                 const int ax = (int)sadd16(rb, two_x);       // 2x + r
-                                e6[c][0] = __dp2a_lo((int)kLanes, rl, e6[c][0]);
-                                e6[c][1] = __dp2a_lo((int)kLanes, rh, e6[c][1]);
-                                e6[c][2] = __dp2a_lo(ax, rl, e6[c][2]);
-                                e6[c][3] = __dp2a_lo(ax, rh, e6[c][3]);
-                                e6[c][4] = __dp2a_lo((int)a, rl, e6[c][4]);
-                                e6[c][5] = __dp2a_lo((int)a, rh, e6[c][5]);
+                                if (luma) {
+                                    // both lanes in one 8x8 block: one sum
+                                    e6[c][0] = __dp2a_lo((int)kLanes, (int)r8, e6[c][0]);
+                                    e6[c][2] = __dp2a_lo(ax, (int)r8, e6[c][2]);
+                                    e6[c][4] = __dp2a_lo((int)a, (int)r8, e6[c][4]);
+                                } else {
+                                    // (U, V) lanes kept apart
+                                    const int rl = (int)(r8 & 0xffu), rh = (int)(r8 & 0xff00u);
+                                    e6[c][0] = __dp2a_lo((int)kLanes, rl, e6[c][0]);
+                                    e6[c][1] = __dp2a_lo((int)kLanes, rh, e6[c][1]);
+                                    e6[c][2] = __dp2a_lo(ax, rl, e6[c][2]);
+                                    e6[c][3] = __dp2a_lo(ax, rh, e6[c][3]);
+                                    e6[c][4] = __dp2a_lo((int)a, rl, e6[c][4]);
+                                    e6[c][5] = __dp2a_lo((int)a, rh, e6[c][5]);
+                                }
                             } else {
                                 acc[pp * 4 + s] = (uint32_t)__dp2a_lo((int)a, (int)r8, (int)acc[pp * 4 + s]);
                             }
@@ -627,6 +639,14 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     sm.accu[tid] = 0;
                 }
                 __syncthreads();
+            }
+        };
+        for (int task = 0; task < 2; task++) {
+            if constexpr (kEq14) {
+                if (task == 0) task_body(std::true_type{});
+                else task_body(std::false_type{});
+            } else {
+                task_body(task == 0);
             }
         }
         if constexpr (kEq14) {
