@@ -350,8 +350,9 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
 #pragma unroll 1
     for (int g = 0; g < (kEq14 ? kG : 1); g++) {
         const int p0 = kEq14 ? g * kPP : p0_unit;
-        // task 0 luma, task 1 chroma; the eq. 14 tables take a copy of the
-        // body per task (luma lanes are summed in one dot product)
+        // task 0 luma, task 1 chroma, a copy of the body each (the plane
+        // group's choices fixed at compile time; eq. 14 sums the luma lanes
+        // in one dot product)
         auto task_body = [&](auto luma_c) {
             const bool luma = luma_c;
             const int task = luma ? 0 : 1;
@@ -641,14 +642,8 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 __syncthreads();
             }
         };
-        for (int task = 0; task < 2; task++) {
-            if constexpr (kEq14) {
-                if (task == 0) task_body(std::true_type{});
-                else task_body(std::false_type{});
-            } else {
-                task_body(task == 0);
-            }
-        }
+        task_body(std::true_type{});
+        task_body(std::false_type{});
         if constexpr (kEq14) {
             // chroma 8x8 blocks: two planes x 16 blocks x the unit's candidates,
             // one per thread; lanes 8 apart hold the same candidate
