@@ -38,6 +38,8 @@
 // replaced by the filtered pixel itself, which is exactly equivalent: f(0) =
 // 0 and the pixel is already in the clip range.  12-bit frames, whose range
 // the packed biases do not cover, take a scalar path.
+#include <type_traits>
+
 #include "tile.cuh"
 
 namespace cdefgb {
@@ -286,18 +288,19 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
 
     // ---- filter: task 0 = row `warp` of 8x8 luma blocks (lane = block
     // column x pair column, 8 rows), task 1 = row `warp` of 4x4 chroma blocks
-    // (lane = block column x column, 4 rows).  One code path for both.
-#pragma unroll 1
-    for (int task = 0; task < (with_chroma ? 2 : 1); task++) {
-        const bool luma = task == 0;
+    // (lane = block column x column, 4 rows).  One body, compiled once per
+    // task so that the plane's geometry is fixed in each copy.
+    auto task_body = [&](auto luma_c) {
+        constexpr bool luma = decltype(luma_c)::value;
+        constexpr int task = luma ? 0 : 1;
         const int bx = lane >> 2, sub = lane & 3;
         const int blk = warp * 8 + bx;
         const int gby = fby * 8 + warp, gbx = fbx * 8 + bx;
         const bool inside = luma ? (gby * 8 < H && gbx * 8 < W) : (gby * 4 < CH && gbx * 4 < CW);
         // taps can leave the frame only in the outermost ring of 8x8 blocks
         const bool edge = gby == 0 || gbx == 0 || gby == (H >> 3) - 1 || gbx == bw - 1;
-        const int rows = luma ? 8 : 4;
-        const int pitch = luma ? kLumaPitch : kChromaPitch;
+        constexpr int rows = luma ? 8 : 4;
+        constexpr int pitch = luma ? kLumaPitch : kChromaPitch;
         const uint32_t *base = luma ? sm.t.le + (2 + warp * 8) * kLumaPitch + 4 + bx * 4 + sub
                                     : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
         // a block that is not filtered (section 4) takes the identity set
@@ -309,7 +312,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         const bool any_p = __any_sync(0xffffffffu, fl & 1), any_s = __any_sync(0xffffffffu, fl & 2);
         const bool any_clip = __any_sync(0xffffffffu, (fl & 3) == 3);
         const bool any_edge = __any_sync(0xffffffffu, inside && edge);
-        if (!__any_sync(0xffffffffu, inside)) continue;
+        if (!__any_sync(0xffffffffu, inside)) return;
         const int4 *op = reinterpret_cast<const int4 *>(sm.off[task][sm.dir[blk]]);
         const int4 o0 = op[0], o1 = op[1], o2 = op[2];
         const int o[12] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w};
@@ -341,7 +344,9 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
             o_a += pa;
             o_b += pb;
         }
-    }
+    };
+    task_body(std::true_type{});
+    if (with_chroma) task_body(std::false_type{});
 }
 
 struct BlockRef {
