@@ -14,6 +14,7 @@
 // is raised for S_p >= 8 take a second set of secondary sums), each rounded,
 // clipped (eq. 9-12) and its squared error summed across the CTA.  The
 // direction maps come from the direction-search kernel, launched first.
+#include <type_traits>
 #include "tile.cuh"
 
 namespace cdefgb {
@@ -85,7 +86,7 @@ __device__ __forceinline__ int pack_primary(int pri, int psh, bool odd, bool rai
 // unfiltered error likewise, and the (19, 7) preset's error; the entries
 // with the skip bit clear leave the uncoded blocks unfiltered.
 template <bool kCoded>
-__global__ void __launch_bounds__(kWThreads)
+__global__ void __launch_bounds__(kWThreads, 2)
 dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__restrict__ dirs,
                  const int32_t *__restrict__ vars, long long *dist_luma, long long *dist_chroma,
                  uint8_t *skipped)
@@ -93,8 +94,12 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
     __shared__ WideSmem sm;
     __shared__ unsigned long long acc_unc[64], base_sums[4];   // uncoded part; unfiltered, (19, 7)
     __shared__ int prim[64][16];
+    // one copy of the body per plane group (0 luma, 1 chroma), the group's
+    // plane count and strength rules fixed in each
+    auto body = [&](auto group_c) {
+    constexpr int group = decltype(group_c)::value;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int blk = blockIdx.x, group = blockIdx.y;
+    const int blk = blockIdx.x;
     int fi = 0;
     while (fi + 1 < batch.n && blk >= batch.f[fi + 1].block_start) fi++;
     const SearchFrameDev &F = batch.f[fi];
@@ -103,8 +108,8 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
     const bool wide = F.bitdepth > 8;
     const int sh8 = F.bitdepth - 8;
     const bool filtered = group == 0 || F.chroma_format != 422;
-    const int nplanes = group == 0 ? 1 : 2;
-    const bool chroma = group != 0;
+    constexpr int nplanes = group == 0 ? 1 : 2;
+    constexpr bool chroma = group != 0;
     const int bw = F.w >> 3;
     const int Dbase = chroma ? F.damping - 1 : F.damping;
 
@@ -285,6 +290,9 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
         long long *out = (group == 0 ? dist_luma : dist_chroma) + (int64_t)blk * 128;
         out[tid] = ((pairs >> q) & 1) ? v : 0;
     }
+    };
+    if (blockIdx.y == 0) body(std::integral_constant<int, 0>{});
+    else body(std::integral_constant<int, 1>{});
 }
 
 }  // namespace
