@@ -75,3 +75,39 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(cdef, "LIB_PATH", "/nonexistent/libcdef_gb300.so")
     with pytest.raises(RuntimeError):
         cdef.load()
+
+
+def test_frame_descriptor_follows_the_planes():
+    """The descriptor kept on a frame is rebuilt when a plane, its pitch or
+    a field of the frame changes (a stale pointer would reach the device)."""
+    torch = pytest.importorskip("torch")
+    from paper_1602_05975_gb300 import cdef
+    f = cdef.alloc_frame(128, 64, 8, device="cpu")
+    d0 = f.desc()
+    assert f.desc() is d0
+    assert d0.y.data == f.y.data_ptr() and d0.y.width == 128 and d0.u.height == 32
+    f.y = torch.zeros_like(f.y)
+    d1 = f.desc()
+    assert d1 is not d0 and d1.y.data == f.y.data_ptr()
+    f.bitdepth = 10
+    assert f.desc().bitdepth == 10
+    wide = torch.zeros((64, 256), dtype=f.y.dtype)[:, :160]
+    f.y = wide
+    assert f.desc().y.pitch_bytes == 256 * wide.element_size()
+
+
+def test_search_results_parsed_per_frame():
+    """Host-side parsing of the search's preset arrays: eight presets per
+    frame, the first four (or, with the skip bits, five) bytes of each."""
+    pytest.importorskip("torch")
+    from paper_1602_05975_gb300 import cdef
+    p = (cdef.Preset * 16)()
+    for i in range(16):
+        p[i].pri_y, p[i].sec_y, p[i].pri_uv, p[i].sec_uv = i, 1, 2, 3
+    out = cdef._search_results(p, 4, 2, [3, 8], [10, 20])
+    assert out[1]["presets"][0] == (8, 1, 2, 3) and len(out[0]["presets"]) == 8
+    assert (out[0]["npresets"], out[1]["cost"]) == (3, 20)
+    q = (cdef.PresetCoded * 8)()
+    q[5].pri_y, q[5].skip, q[5].reserved[0] = 7, 3, 9
+    out = cdef._search_results(q, 5, 1, [8], [0])
+    assert out[0]["presets"][5] == (7, 0, 0, 0, 3)
