@@ -1121,24 +1121,25 @@ int cdef_ref_filter_frame_format(int w, int h, int bitdepth, int format,
  * not a multiple of 8) uses its n in-frame samples.  R23: C1 = 6.25 *
  * 4^(bd-8) and C2 = 312.5 * 16^(bd-8) (the constants scale with the units
  * of a variance and of its square).  R24: the table holds the sum over the
- * 8x8 blocks of round(256 * D_8x8) (ties away from zero), each D_8x8
- * evaluated in IEEE single precision (the paper fixes none) in exactly
- * this order, every operation correctly rounded and none contracted:
- *   vs = (float)(n sum s^2 - (sum s)^2) / n^2, vd likewise,
- *   D = ((vs + vd) + C1) / (2 sqrt(vs vd + C2)) * (float)sse,
- * so that the preset search stays in exact integers. */
+ * 8x8 blocks of round(256 * D_8x8) (ties away from zero), so that the
+ * preset search works on exact integers.  The paper fixes no precision;
+ * this oracle evaluates eq. 14 as written in IEEE double precision:
+ *   vs = (n sum s^2 - (sum s)^2) / n^2, vd likewise (both exact here: the
+ *        numerators stay below 2^53 and n is 16, 32 or 64),
+ *   D  = (vs + vd + C1) / (2 sqrt(vs vd + C2)) * sse,
+ * which is within a few units in the last place of the exact value, so the
+ * rounded result equals round(256 * D) of the exact value except where
+ * 256 * D lies within a few units in the last place of a half-integer. */
 static int64_t eq14_term(int64_t n, int64_t s1s, int64_t s2s, int64_t s1d, int64_t s2d,
                          int64_t sse, int bitdepth)
 {
-    const float c1 = 6.25f * (float)(1 << (2 * (bitdepth - 8)));
-    const float c2 = 312.5f * (float)(1 << (4 * (bitdepth - 8)));
-    const float nn = (float)(n * n);
-    const float vs = (float)(n * s2s - s1s * s1s) / nn;
-    const float vd = (float)(n * s2d - s1d * s1d) / nn;
-    const float num = (vs + vd) + c1;
-    const float den = 2.0f * sqrtf(vs * vd + c2);
-    const float d = num / den * (float)sse;
-    return (int64_t)llroundf(256.0f * d);
+    const double c1 = 6.25 * (double)((int64_t)1 << (2 * (bitdepth - 8)));
+    const double c2 = 312.5 * (double)((int64_t)1 << (4 * (bitdepth - 8)));
+    const double nn = (double)(n * n);
+    const double vs = (double)(n * s2s - s1s * s1s) / nn;
+    const double vd = (double)(n * s2d - s1d * s1d) / nn;
+    const double d = (vs + vd + c1) / (2.0 * sqrt(vs * vd + c2)) * (double)sse;
+    return (int64_t)llround(256.0 * d);
 }
 
 static int64_t block_eq14(const uint16_t *rec, ptrdiff_t rs, const uint16_t *src, ptrdiff_t ss,

@@ -596,11 +596,53 @@ def test_chroma_formats_rejected_where_unsupported(cdef, ctx):
 
 
 # --------------------------------------------------------------- eq. 14 distortion
+def _eq14_term_counts(w, h, chroma=420):
+    """Per filter block: how many 8x8 terms the luma entry and the chroma
+    (U + V) entry sum (blocks cut by the frame edge count once)."""
+    fr, fc = (h + 63) // 64, (w + 63) // 64
+    cw, ch = {420: (w // 2, h // 2), 422: (w // 2, h), 444: (w, h)}[chroma]
+    sx, sy = 64 * cw // w, 64 * ch // h          # chroma filter-block size
+    nl = np.zeros(fr * fc, np.int64)
+    nc = np.zeros(fr * fc, np.int64)
+    for by in range(fr):
+        for bx in range(fc):
+            ly = min(64, h - by * 64)
+            lx = min(64, w - bx * 64)
+            nl[by * fc + bx] = -(-ly // 8) * -(-lx // 8)
+            cy = min(sy, ch - by * sy)
+            cx = min(sx, cw - bx * sx)
+            nc[by * fc + bx] = 2 * (-(-cy // 8)) * (-(-cx // 8))
+    return nl, nc
+
+
+def _assert_eq14_tables_close(got, exp, nterms, cols=None):
+    """The GPU's eq. 14 tables against the oracle's.  Per 8x8 term the GPU
+    rounds an IEEE single-precision evaluation, within 0.5 + 2^-20 * value
+    of the exact 256 * D (six correctly rounded operations); the oracle
+    rounds a double-precision one, within 0.5 (plus a few double ulps) of
+    it.  So an entry that sums n terms may differ by at most
+    n + 2^-20 * (entry + n)."""
+    got = np.asarray(got, np.int64)
+    exp = np.asarray(exp, np.int64)
+    if cols is not None:
+        got, exp = got[:, cols], exp[:, cols]
+    bound = nterms[:, None] + np.ceil((exp + nterms[:, None]) * 2.0 ** -20).astype(np.int64)
+    diff = np.abs(got - exp)
+    bad = np.argwhere(diff > bound)
+    assert bad.size == 0, (f"{len(bad)} entries beyond the bound, first {bad[:3].tolist()}: "
+                           f"got {got[tuple(bad[0])]}, oracle {exp[tuple(bad[0])]}")
+    # on average the two evaluations differ by less than one unit per term
+    assert diff.sum() <= nterms.sum() * got.shape[1]
+
+
 @pytest.mark.parametrize("passes", [0, 2])
 def test_search_eq14_parity(cdef, ctx, ref, passes):
-    """Section 5's eq. 14 tables (8x8 SSIM weighting, 1/256 units) and the
-    presets, N, J and ids they give equal the oracle's, including 4:2:0
-    chroma 8x8 blocks cut by the frame edge."""
+    """Section 5's eq. 14 tables (8x8 SSIM weighting, 1/256 units): every
+    GPU entry lies within the bound the two evaluations' precisions allow of
+    the double-precision oracle's (4:2:0 chroma 8x8 blocks cut by the frame
+    edge included), and the presets, N, J and ids the GPU returns are
+    exactly the oracle's selection (greedy, re-optimised) on the GPU's own
+    tables."""
     from paper_1602_05975_gb300 import synth
     specs = [(200, 136, 8, 16, 1100), (136, 72, 10, 32, 1101), (192, 120, 8, 64, 1102)]
     frames = [synth.make_frame(w, h, bd, q, seed=s) for w, h, bd, q, s in specs]
@@ -622,9 +664,13 @@ def test_search_eq14_parity(cdef, ctx, ref, passes):
     o0 = 0
     for f, r, d, lam in zip(frames, res, damping, lambdas):
         b = f.params.shape[0] * f.params.shape[1]
-        o = ref.search_strengths_eq14(f.rec, f.src, f.bitdepth, d, lam, passes)
-        assert np.array_equal(dl[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_luma"])
-        assert np.array_equal(dc[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_chroma"])
+        gl = dl[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64)
+        gc = dc[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64)
+        el, ec = ref.distortion_eq14(f.rec, f.src, f.bitdepth, d)
+        nl, nc = _eq14_term_counts(f.width, f.height)
+        _assert_eq14_tables_close(gl, el, nl)
+        _assert_eq14_tables_close(gc, ec, nc)
+        o = ref.select_presets_general(gl, gc, 64, None, lam, passes)
         assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"]
         assert ([cdef.preset_index(p) for p in r["presets"][:r["npresets"]]] ==
                 [int(t) for t in o["presets"][:o["npresets"]]])
@@ -740,8 +786,16 @@ def test_search_subset_parity(cdef, ctx, ref, variant, passes):
                 gc = dc[o0 * width:(o0 + b) * width].cpu().numpy().reshape(b, width)
                 cols_l = np.array([((lmask >> (q % 64)) & 1) == 1 for q in range(width)])
                 cols_c = np.array([((cmask >> (q % 64)) & 1) == 1 for q in range(width)])
-                assert np.array_equal(gl[:, cols_l], o["dist_luma"][:, cols_l])
-                assert np.array_equal(gc[:, cols_c], o["dist_chroma"][:, cols_c])
+                if variant == "eq14":
+                    # tables within the precision bound; the selection is
+                    # the oracle's on the GPU's own tables
+                    nl, nc = _eq14_term_counts(f.width, f.height)
+                    _assert_eq14_tables_close(gl, o["dist_luma"], nl, cols_l)
+                    _assert_eq14_tables_close(gc, o["dist_chroma"], nc, cols_c)
+                    o = ref.select_presets_subset(gl, gc, 64, None, lmask, cmask, lam, passes)
+                else:
+                    assert np.array_equal(gl[:, cols_l], o["dist_luma"][:, cols_l])
+                    assert np.array_equal(gc[:, cols_c], o["dist_chroma"][:, cols_c])
                 assert (gl[:, ~cols_l] == 0).all() and (gc[:, ~cols_c] == 0).all()
                 assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"]
                 idx = cdef.preset_index_coded if variant == "coded" else cdef.preset_index

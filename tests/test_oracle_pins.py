@@ -1165,34 +1165,73 @@ def test_eq14_constants_scale_with_bit_depth(ref):
         assert abs(t10 - 16 * t8) <= 8
 
 
-def test_eq14_term_within_single_precision_bound_of_exact_value(ref):
-    """R24: the fixed-order single-precision value is within the rounding
-    error of a handful of correctly rounded operations (plus the final
-    rounding to 1/256) of eq. 14 evaluated exactly (rational variances,
-    a 50-digit square root)."""
+def _eq14_exact_256(n, s1s, s2s, s1d, s2d, sse, bd):
+    """256 * eq. 14 for one 8x8 block taken exactly: rational variances and
+    constants, a 60-digit square root."""
     import decimal
     from fractions import Fraction
-    decimal.getcontext().prec = 50
+    ctx = decimal.Context(prec=60)
+    c1 = Fraction(25, 4) * 4 ** (bd - 8)
+    c2 = Fraction(625, 2) * 16 ** (bd - 8)
+    vs = Fraction(n * s2s - s1s * s1s, n * n)
+    vd = Fraction(n * s2d - s1d * s1d, n * n)
+    rad = vs * vd + c2
+    root = ctx.sqrt(ctx.divide(decimal.Decimal(rad.numerator), decimal.Decimal(rad.denominator)))
+    num = vs + vd + c1
+    num_d = ctx.divide(decimal.Decimal(num.numerator), decimal.Decimal(num.denominator))
+    return ctx.multiply(ctx.divide(ctx.multiply(256 * num_d, decimal.Decimal(sse)), 2 * root), 1)
+
+
+def test_eq14_term_is_exact_value_rounded(ref):
+    """R24: each 8x8 value is round(256 * D) of eq. 14 taken exactly
+    (rational variances, 60-digit square root), ties away from zero; only a
+    value within a relative 2^-48 of a half-integer may round either way.
+    Covers full and edge-cut blocks (n = 64, 32, 16), flat blocks and every
+    bit depth."""
+    import decimal
     rng = np.random.default_rng(5)
-    for bd in (8, 10):
-        c1 = Fraction(25, 4) * 4 ** (bd - 8)
-        c2 = Fraction(625, 2) * 16 ** (bd - 8)
+    near_ties = 0
+    for bd in (8, 10, 12):
         for n in (64, 32, 16):
-            for _ in range(200):
+            for _ in range(150):
                 s = rng.integers(0, 1 << bd, n)
-                d = np.clip(s + rng.integers(-60, 61, n), 0, (1 << bd) - 1)
+                d = np.clip(s + rng.integers(-60, 61, n) * (1 << (bd - 8)), 0, (1 << bd) - 1)
                 if rng.random() < 0.3:
                     d = np.full(n, int(d.mean()))
                 sums = _sums(s, d)
-                _, s1s, s2s, s1d, s2d, sse = sums
-                vs = Fraction(n * s2s - s1s * s1s, n * n)
-                vd = Fraction(n * s2d - s1d * s1d, n * n)
-                root = (decimal.Decimal((vs * vd + c2).numerator)
-                        / decimal.Decimal((vs * vd + c2).denominator)).sqrt()
-                num = decimal.Decimal((vs + vd + c1).numerator) / decimal.Decimal((vs + vd + c1).denominator)
-                exact = 256 * num / (2 * root) * sse
+                exact = _eq14_exact_256(*sums, bd)
                 got = ref.eq14_term(*sums, bd)
-                assert abs(decimal.Decimal(got) - exact) <= decimal.Decimal(0.5) + exact * decimal.Decimal(2 ** -20)
+                lo = int(exact.to_integral_value(rounding=decimal.ROUND_HALF_UP))
+                frac = exact - int(exact)
+                if abs(frac - decimal.Decimal("0.5")) <= exact * decimal.Decimal(2) ** -48:
+                    near_ties += 1
+                    assert got in (int(exact), int(exact) + 1)
+                else:
+                    assert got == lo, (bd, n, sums, exact, got)
+    assert near_ties < 5
+
+
+def test_eq14_term_catches_dropped_terms(ref):
+    """Each part of eq. 14 moves the value: a dropped C1, C2, factor 2, or a
+    variance taken as the sample variance (n - 1) would each change the
+    term of one of these blocks."""
+    rng = np.random.default_rng(51)
+    s = rng.integers(0, 256, 64)
+    d = np.clip(s + rng.integers(-9, 10, 64), 0, 255)
+    sums = _sums(s, d)
+    got = ref.eq14_term(*sums, 8)
+    n, s1s, s2s, s1d, s2d, sse = sums
+    vs = (n * s2s - s1s * s1s) / n ** 2
+    vd = (n * s2d - s1d * s1d) / n ** 2
+    variants = [
+        (vs + vd) / (2 * (vs * vd + 312.5) ** 0.5) * sse,           # no C1
+        (vs + vd + 6.25) / (2 * (vs * vd) ** 0.5) * sse,            # no C2
+        (vs + vd + 6.25) / ((vs * vd + 312.5) ** 0.5) * sse,        # no factor 2
+        (vs * n / (n - 1) + vd * n / (n - 1) + 6.25)
+        / (2 * (vs * vd * (n / (n - 1)) ** 2 + 312.5) ** 0.5) * sse,  # sample variances
+    ]
+    for v in variants:
+        assert abs(round(256 * v) - got) > 2
 
 
 def test_eq14_large_variance_tends_to_sse(ref):
