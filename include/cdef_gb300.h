@@ -381,20 +381,30 @@ int cdef_ctx_set_overlap(cdef_ctx *ctx, int enable);
  * library, which every GPU that loads the library holds until the process
  * exits: about 1.63 MiB (CDEF_NOALLOC_MAX_BLOCKS blocks, 48 frames).
  *
- *   - Same arguments, results and errors as cdef_search_strengths, except
- *     that there is no context and dist_luma / dist_chroma are required
- *     (device, sum_i B_i * 64 int64 each): the tables are outputs the caller
- *     provides.  Runs on the current device; the stream must belong to it.
+ *   - The arguments and results of cdef_search_strengths for 8- and 10-bit
+ *     4:2:0 frames, with the default search (squared error, 64 pairs, greedy
+ *     presets, no subset), except that there is no context and dist_luma /
+ *     dist_chroma are required (device, sum_i B_i * 64 int64 each): the
+ *     tables are outputs the caller provides.  Runs on the current device;
+ *     the stream must belong to it.
+ *   - 12-bit frames return CDEF_ERR_BITDEPTH and 4:2:2 or 4:4:4 frames
+ *     CDEF_ERR_SIZE (those take cdef_search_strengths' 32-bit path, which
+ *     needs direction-map scratch this variant does not hold).
  *   - At most CDEF_NOALLOC_MAX_BLOCKS filter blocks in total over the n
  *     frames (e.g. 8 frames of 3840x2160); beyond that it returns
  *     CDEF_ERR_NOMEM before doing any work.
+ *   - Kernel-reported errors come back as the call's status: CDEF_ERR_TIMEOUT
+ *     when a bounded device-side wait gave up, CDEF_ERR_DEVICE for any other
+ *     error bit; the outputs are then unspecified.
  *   - The first call on a device looks up the device address of the array
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *     (cudaGetSymbolAddress) with that device current.  No call may be made
+ *     while its stream is being captured into a graph: every call waits for
+ *     its stream to return its host outputs.
  *   - All calls on a device share the one array and it keeps the last
- *     call's contents (every word the kernels read is written earlier in the
- *     same call).  Calls whose work overlaps on the GPU -- on different
- *     streams, or from several host threads -- race on it: serialise them.
+ *     call's contents (every word the kernels read is written or cleared
+ *     earlier in the same call).  Calls whose work overlaps on the GPU -- on
+ *     different streams, or from several host threads -- race on it:
+ *     serialise them.
  *   - Synchronises the stream before returning (host outputs). */
 #define CDEF_NOALLOC_MAX_BLOCKS 16384
 int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
@@ -403,6 +413,23 @@ int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
                                   int64_t *dist_chroma, cdef_preset *presets,
                                   int32_t *npresets, uint8_t *block_ids,
                                   int64_t *cost, void *cuda_stream);
+
+/* Test aid (no paper counterpart): the limits of the kernels' bounded
+ * tile-load waits, process-wide, for every launch made after the call.
+ *   wait_cycles    : SM clock cycles a CTA waits for a block's tiles before
+ *                    it gives up (0 = the default, about 2^28)
+ *   extra_tx_bytes : bytes added to every tile load's expected transaction
+ *                    count that no load delivers (0..65536; 0 = none), so
+ *                    that every wait runs out after wait_cycles
+ * A CTA whose wait gives up sets the timeout status (cdef_ctx_status ->
+ * CDEF_ERR_TIMEOUT; cdef_search_strengths_noalloc returns it), takes back
+ * the undelivered bytes, waits (bounded) for the loads it did issue and
+ * leaves; its blocks stay unwritten.  Nothing faults and the context stays
+ * usable.  Searches record their launches into a cached graph, which takes
+ * the limits of the call that recorded it (a call with other limits is
+ * recorded again).  CDEF_ERR_ARG for values out of range.  Host only; not
+ * for concurrent use with launches from other host threads. */
+int cdef_debug_set_waits(int64_t wait_cycles, int32_t extra_tx_bytes);
 
 /* A static description of a status code. */
 const char *cdef_strerror(int status);

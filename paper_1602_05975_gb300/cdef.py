@@ -99,6 +99,7 @@ def load():
     L.cdef_search_strengths_coded.argtypes = [
         vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(vp), C.POINTER(i32),
         C.POINTER(i64), vp, vp, C.POINTER(PresetCoded), C.POINTER(i32), vp, C.POINTER(i64), vp]
+    L.cdef_debug_set_waits.argtypes = [i64, i32]
     L.cdef_strerror.argtypes = [C.c_int]
     L.cdef_strerror.restype = C.c_char_p
     L.cdef_version.restype = C.c_char_p
@@ -109,7 +110,7 @@ def load():
                  "cdef_ctx_set_search_refine", "cdef_search_strengths_coded",
                  "cdef_ctx_set_search_metric", "cdef_ctx_set_stage_timing",
                  "cdef_ctx_get_stage_times", "cdef_ctx_set_search_subset",
-                 "cdef_ctx_status_async"):
+                 "cdef_ctx_status_async", "cdef_debug_set_waits"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -479,6 +480,14 @@ def preset_index_coded(p) -> int:
 def preset_index(p) -> int:
     """(pri_y, sec_y, pri_uv, sec_uv) -> luma_pair * 64 + chroma_pair."""
     return (p[0] * 4 + SEC_VALUES.index(p[1])) * 64 + p[2] * 4 + SEC_VALUES.index(p[3])
+
+
+def debug_set_waits(wait_cycles: int = 0, extra_tx_bytes: int = 0):
+    """Test aid: the kernels' tile-load wait limit (SM cycles, 0 = default)
+    and bytes added to every load's expected count that no load delivers
+    (so that waits run out); process-wide, for later launches."""
+    _check(load().cdef_debug_set_waits(int(wait_cycles), int(extra_tx_bytes)),
+           "cdef_debug_set_waits")
 
 
 def version() -> str:

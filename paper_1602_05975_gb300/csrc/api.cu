@@ -143,6 +143,17 @@ int fb_count(const cdef_frame *f) { return ((f->y.width + 63) / 64) * ((f->y.hei
 
 namespace cdefgb {
 
+namespace {
+std::mutex g_wait_mutex;
+WaitLimits g_waits = {kDefaultWaitCycles, 0, 0};
+}  // namespace
+
+WaitLimits wait_limits()
+{
+    std::lock_guard<std::mutex> lock(g_wait_mutex);
+    return g_waits;
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
 // link-time dependency on libcuda).
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -478,6 +489,7 @@ int plane_pass(cdef_ctx *ctx, const cdef_frame *in, const cdef_plane &pin, const
     FilterBatch<1> b;
     b.n = 1;
     b.total_blocks = fb_count(in);
+        b.waits = wait_limits();
     int rc = fill_plane_dev(b.f[0], in, pin, pout, params, dir, var, coded, mode, 0);
     if (rc) return rc;
     unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
@@ -536,6 +548,7 @@ int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params
         FilterBatch<1> b;
         b.n = 1;
         b.total_blocks = fb_count(in);
+        b.waits = wait_limits();
         if ((rc = fill_filter_frame(b.f[0], in, out, params, dir, var, 0, coded))) return rc;
         unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
         return cuda_status(launch_filter_single(b, ctx->status, work, ctx->overlap, s));
@@ -571,6 +584,7 @@ int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params
     b.n = 3;
     const int B = fb_count(in);
     b.total_blocks = 3 * B;
+    b.waits = wait_limits();
     if ((rc = fill_plane_dev(b.f[0], in, in->y, out->y, params, dir, var, coded, 1, 0)) ||
         (rc = fill_plane_dev(b.f[1], in, in->u, out->u, params, dir, var, coded, 2, B)) ||
         (rc = fill_plane_dev(b.f[2], in, in->v, out->v, params, dir, var, coded, 2, 2 * B)))
@@ -625,6 +639,7 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
         start += fb_count(&in[i]);
     }
     bp->total_blocks = start;
+    bp->waits = wait_limits();
     unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
     const int rc = cuda_status(launch_filter_batch(*bp, ctx->status, work, ctx->overlap,
                                                    static_cast<cudaStream_t>(cuda_stream)));
@@ -776,6 +791,7 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
     if (rc != CDEF_OK) { delete b; return rc; }
     b->n = n;
     b->total_blocks = total;
+    b->waits = wait_limits();
 
     DeviceGuard g(ctx->device);
     if (!g.ok) { delete b; return CDEF_ERR_CUDA; }
@@ -943,5 +959,14 @@ const char *cdef_strerror(int status)
 }
 
 const char *cdef_version(void) { return "cdef_gb300 0.1 sm_103a"; }
+
+int cdef_debug_set_waits(int64_t wait_cycles, int32_t extra_tx_bytes)
+{
+    if (wait_cycles < 0 || extra_tx_bytes < 0 || extra_tx_bytes > (1 << 16)) return CDEF_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_wait_mutex);
+    g_waits.wait_cycles = wait_cycles ? wait_cycles : kDefaultWaitCycles;
+    g_waits.extra_tx = extra_tx_bytes;
+    return CDEF_OK;
+}
 
 }  // extern "C"

@@ -39,10 +39,25 @@ struct FilterFrameDev {  // aligned as CUtensorMap requires
     int block_start;                 // first CTA index of this frame
 };
 
+// Limits of the kernels' bounded tile-load waits.  `wait_cycles` is how long
+// a CTA waits for a block's tiles before it gives up (sets the timeout
+// status bit, waits for its own loads in flight and leaves); `extra_tx`
+// bytes are added to every tile load's expected transaction count, bytes no
+// load delivers, so that the wait runs out (a test aid: 0 outside tests).
+struct WaitLimits {
+    long long wait_cycles;
+    int extra_tx;
+    int pad;
+};
+constexpr long long kDefaultWaitCycles = 1ll << 28;   // ~0.13 s at 2 GHz
+// The process-wide limits every launch takes (cdef_debug_set_waits).
+WaitLimits wait_limits();
+
 template <int MAXF>
 struct FilterBatch {
     int n;
     int total_blocks;
+    WaitLimits waits = {kDefaultWaitCycles, 0, 0};
     FilterFrameDev f[MAXF];
 };
 
@@ -69,6 +84,7 @@ struct SearchFrameDev {  // aligned as CUtensorMap requires
 struct SearchBatch {
     int n;
     int total_blocks;
+    WaitLimits waits = {kDefaultWaitCycles, 0, 0};
     SearchFrameDev f[kMaxBatch];
 };
 static_assert(sizeof(SearchBatch) <= 32764, "a search batch must fit the kernel parameter space");

@@ -371,7 +371,7 @@ __device__ __forceinline__ void issue_loads(const FilterBatch<MAXF> &batch, int 
 {
     const BlockRef r = locate(batch, blk);
     const FilterFrameDev &F = batch.f[r.fi];
-    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar, F.mode == 0);
+    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar, F.mode == 0, batch.waits.extra_tx);
 }
 
 // Persistent: each CTA takes blocks from the launch's work counter
@@ -420,9 +420,12 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
         for (int it = 0;; it++) {
             const int blk = sm.blk_next;
             if (blk >= total) break;
-            const bool arrived = mbar_wait_bounded(&sm.bar, it & 1, kWaitCycles);
+            const bool arrived = mbar_wait_bounded(&sm.bar, it & 1, batch.waits.wait_cycles);
             if (__syncthreads_or(!arrived)) {  // the whole CTA leaves together
-                if (tid == 0) atomicOr(status, kStatusTimeout);
+                if (tid == 0) {
+                    atomicOr(status, kStatusTimeout);
+                    drain_tile_loads(&sm.bar, it & 1, batch.waits.extra_tx);
+                }
                 break;
             }
             auto prefetch = [&]() {

@@ -122,6 +122,7 @@ extern "C" int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
     }
     b.n = n;
     b.total_blocks = total;
+    b.waits = wait_limits();
 
     void *scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
@@ -136,7 +137,8 @@ extern "C" int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
     // call (the greedy minima and preset totals are reset at its start, the
     // result records written whole); the work counters start at zero (static
     // storage) and every launch leaves them at zero again.  The status word
-    // only collects error bits and is not read here.
+    // collects the kernels' error bits: cleared here, read back with the
+    // results.
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -144,17 +146,25 @@ extern "C" int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
         cudaGetLastError();
         return CDEF_ERR_CUDA;
     }
-    cudaError_t e = launch_search(b, reinterpret_cast<long long *>(dist_luma),
-                                  reinterpret_cast<long long *>(dist_chroma), cur, tot, results,
-                                  block_ids, status, work, default_search_tune(total, sms), 0, s);
-    SearchResultDev host[kMaxBatch];  // pageable stack copy: no pinned allocation
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = launch_search(b, reinterpret_cast<long long *>(dist_luma),
+                          reinterpret_cast<long long *>(dist_chroma), cur, tot, results, block_ids,
+                          status, work, default_search_tune(total, sms), 0, s);
+    SearchResultDev host[kMaxBatch];  // pageable stack copies: no pinned allocation
+    int host_status = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host, results, sizeof(SearchResultDev) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&host_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return CDEF_ERR_CUDA;
     }
+    // a kernel that gave up leaves the tables and presets unspecified
+    if (host_status & kStatusTimeout) return CDEF_ERR_TIMEOUT;
+    if (host_status) return CDEF_ERR_DEVICE;
     static const uint8_t kSec[4] = {0, 1, 2, 4};
     for (int i = 0; i < n; i++) {
         npresets[i] = host[i].npresets;

@@ -695,7 +695,7 @@ __device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTil
 {
     const SBlockRef r = slocate(batch, blk);
     const SearchFrameDev &F = batch.f[r.fi];
-    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar);
+    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar, true, batch.waits.extra_tx);
 }
 
 // Persistent distortion kernel (same work-counter scheme as the filter).
@@ -737,12 +737,14 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
                 sm.blk[buf ^ 1] = nb;
                 if (nb < total) sissue(batch, nb / kUnits, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
             }
-            const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, kWaitCycles);
+            const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, batch.waits.wait_cycles);
             if (__syncthreads_or(!arrived)) {
+                // leave once both buffers' loads in flight have landed
                 if (tid == 0) {
                     atomicOr(status, kStatusTimeout);
+                    drain_tile_loads(&sm.bar[buf], (it >> 1) & 1, batch.waits.extra_tx);
                     if (sm.blk[buf ^ 1] < total)
-                        mbar_wait_bounded(&sm.bar[buf ^ 1], ((it + 1) >> 1) & 1, kWaitCycles);
+                        drain_tile_loads(&sm.bar[buf ^ 1], ((it + 1) >> 1) & 1, batch.waits.extra_tx);
                 }
                 break;
             }

@@ -32,7 +32,7 @@ constexpr int kChromaPitch = 36;                   // words per row
 constexpr uint32_t kBias = 128;                    // sample bias in shared memory
 constexpr uint32_t kB1 = 2048;                     // bias of the K - |p - x| lanes
 constexpr uint32_t kLanes = 0x10001u;              // one in each 16-bit lane
-constexpr long long kWaitCycles = 1ll << 28;       // ~0.13 s at 2 GHz
+constexpr long long kWaitCycles = kDefaultWaitCycles;
 
 // Per-block constants of one tap set.
 struct SetC {
@@ -309,22 +309,35 @@ __device__ __forceinline__ void stage_relayout(PairTiles &sm, const RawTiles &ra
 }
 
 // Issued by one thread: the three tile loads of filter block (fby, fbx)
-// into `raw`, completing on `bar`.  `maps` are the y, u, v tile maps.
+// into `raw`, completing on `bar`.  `maps` are the y, u, v tile maps;
+// `extra_tx` bytes no load delivers are added to the expected count (the
+// test aid of WaitLimits).
 __device__ __forceinline__ void issue_tile_loads(const CUtensorMap *maps, int bitdepth, int fby,
                                                  int fbx, RawTiles &raw, uint64_t *bar,
-                                                 bool chroma = true)
+                                                 bool chroma = true, int extra_tx = 0)
 {
     const int B = bitdepth == 8 ? 1 : 2;
     const int lead = box_lead(B);
     // order earlier generic-proxy reads of this buffer before the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_arrive_expect_tx(bar, kLumaRows * luma_box_cols(B) * B +
-                                   (chroma ? 2 * kChromaRows * chroma_box_cols(B) * B : 0));
+                                   (chroma ? 2 * kChromaRows * chroma_box_cols(B) * B : 0) +
+                                   extra_tx);
     tma_load_2d(raw.y, &maps[0], fbx * 64 - lead, fby * 64 - 2, bar);
     if (chroma) {
         tma_load_2d(raw.u, &maps[1], fbx * 32 - lead, fby * 32 - 2, bar);
         tma_load_2d(raw.v, &maps[2], fbx * 32 - lead, fby * 32 - 2, bar);
     }
+}
+
+// After a wait on `bar` (phase `parity`) gave up: the calling thread takes
+// back the `extra_tx` bytes no load will deliver, then waits (bounded) until
+// the loads actually issued on the barrier have landed, so that no copy
+// writes into this CTA's shared memory after it leaves.
+__device__ __forceinline__ void drain_tile_loads(uint64_t *bar, uint32_t parity, int extra_tx)
+{
+    if (extra_tx) mbar_complete_tx(bar, (uint32_t)extra_tx);
+    mbar_wait_bounded(bar, parity, kWaitCycles);
 }
 
 }  // namespace tile

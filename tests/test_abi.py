@@ -50,6 +50,11 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.cdef_find_dir(None, None, 8, None, None, None) == -1
     assert lib.cdef_filter_frame(None, None, None, None, None, None, None) == -1
     assert lib.cdef_ctx_destroy(None) == 0
+    # the wait-limit test aid is host state: checked without a device
+    lib.cdef_debug_set_waits.argtypes = [C.c_int64, C.c_int32]
+    assert lib.cdef_debug_set_waits(-1, 0) == -1
+    assert lib.cdef_debug_set_waits(0, -1) == -1
+    assert lib.cdef_debug_set_waits(0, 0) == 0
 
 
 def test_struct_layout_matches_binding(tmp_path):
