@@ -414,6 +414,85 @@ int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
                                   int32_t *npresets, uint8_t *block_ids,
                                   int64_t *cost, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * The strength search split over devices (section 5, eq. 15).
+ *
+ * Section 5's tables are per filter block, so a search can be sharded: each
+ * device computes the tables of its own band of filter-block rows
+ * (cdef_search_tables), and the greedy search, the one-at-a-time
+ * re-optimisation, N by J and the block ids are then driven from the host,
+ * step by step, with one exchange per step: every device forms the totals
+ * over its blocks of all presets (cdef_preset_totals), the host sums them
+ * over devices (a collective), and every device takes the same least total
+ * (cdef_preset_argmin).  Per-block state stays on its device
+ * (cdef_preset_assign).  The totals of a step over several block ranges add
+ * up exactly to the totals over their union, so the sharded selection
+ * equals cdef_search_strengths' (its host driver is the package's
+ * shard.py).  All four are asynchronous on cuda_stream and allocate
+ * nothing.
+ * ------------------------------------------------------------------------ */
+
+/* Section 5's distortion tables (the first pass of cdef_search_strengths /
+ * cdef_search_strengths_coded) for a band of filter-block rows of each of n
+ * frames: rows row_begin[i] .. row_begin[i] + row_count[i] - 1 of frame i
+ * (HOST arrays; row_count 0 allowed), the blocks of frame i after those of
+ * frame i - 1, row-major within the band.  Taps and direction search read
+ * the whole frame, so a band's tables equal the same rows of the whole
+ * frame's tables.  The context's metric (squared error or eq. 14) and
+ * subset apply.
+ *   coded, skipped : both NULL (64 pairs) or both set (the 128 combinations
+ *                    of cdef_search_strengths_coded): coded = HOST array of
+ *                    n DEVICE maps, skipped = DEVICE, one flag per band block
+ *   dist_luma,
+ *   dist_chroma    : DEVICE, (band blocks) * 64 (or 128) int64 each, written
+ * Frames as cdef_search_strengths.  CDEF_ERR_ARG for a band outside the
+ * frame, eq. 14 with coded maps, or eq. 14 with a 12-bit, 4:2:2 or 4:4:4
+ * frame. */
+int cdef_search_tables(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
+                       const uint8_t *const *coded, const int32_t *damping,
+                       const int32_t *row_begin, const int32_t *row_count, int64_t *dist_luma,
+                       int64_t *dist_chroma, uint8_t *skipped, void *cuda_stream);
+
+/* One step's totals over nblocks blocks of tables with `width` (64 or 128)
+ * combinations per plane group: for every preset t = luma_q * width +
+ * chroma_q (width^2 of them),
+ *   totals[t] = sum over blocks b with skipped[b] == 0 of
+ *               min(best[b], dist_luma[b][luma_q] + dist_chroma[b][chroma_q])
+ *   dist_luma, dist_chroma : DEVICE tables, nblocks * width int64 each
+ *   skipped                : DEVICE, nblocks flags, or NULL (none skipped)
+ *   best                   : DEVICE, nblocks uint64, or NULL (no bound: the
+ *                            first greedy step)
+ *   totals                 : DEVICE, width^2 int64, written
+ * nblocks 0 gives zero totals. */
+int cdef_preset_totals(cdef_ctx *ctx, int32_t nblocks, int32_t width, const int64_t *dist_luma,
+                       const int64_t *dist_chroma, const uint8_t *skipped, const uint64_t *best,
+                       int64_t *totals, void *cuda_stream);
+
+/* The step's choice from (summed) totals: the least total over the presets
+ * whose luma and chroma pairs are allowed (bit q mod 64 of luma_pairs /
+ * chroma_pairs, as cdef_ctx_set_search_subset; ~0 for all), the lowest
+ * index on ties; in a re-optimisation step `keep` is the slot's current
+ * preset, kept when it attains the least total (-1: none).
+ *   totals : DEVICE, width^2 int64
+ *   result : DEVICE, 2 int64 written: the preset, its total */
+int cdef_preset_argmin(cdef_ctx *ctx, int32_t width, const int64_t *totals, uint64_t luma_pairs,
+                       uint64_t chroma_pairs, int32_t keep, int64_t *result, void *cuda_stream);
+
+/* Per-block state for a preset set P of npresets (0..8) presets (HOST array
+ * `presets`): for each block b,
+ *   best[b]      = min over P of D_b (2^64 - 1 when P is empty; 0 when
+ *                  skipped), the bound of the next totals;
+ *   block_ids[b] = the position in P of the first preset attaining it (0
+ *                  when skipped): the block's id once P is final;
+ *   sums         = {sum of best[b] over blocks not skipped (0 when P is
+ *                  empty), the number of blocks not skipped}: the set's
+ *                  total and the B of J.
+ * best, block_ids and sums are DEVICE outputs, each may be NULL. */
+int cdef_preset_assign(cdef_ctx *ctx, int32_t nblocks, int32_t width, const int64_t *dist_luma,
+                       const int64_t *dist_chroma, const uint8_t *skipped, const int32_t *presets,
+                       int32_t npresets, uint64_t *best, uint8_t *block_ids, int64_t *sums,
+                       void *cuda_stream);
+
 /* Test aid (no paper counterpart): the limits of the kernels' bounded
  * tile-load waits, process-wide, for every launch made after the call.
  *   wait_cycles    : SM clock cycles a CTA waits for a block's tiles before

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcdef_gb300.so")
-SOURCES = ["api.cu", "find_dir.cu", "filter.cu", "search.cu", "search_wide.cu", "presets.cu",
+SOURCES = ["api.cu", "find_dir.cu", "filter.cu", "search.cu", "search_wide.cu", "presets.cu", "shard.cu",
            "presets_cluster.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",

@@ -100,6 +100,13 @@ def load():
         vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(vp), C.POINTER(i32),
         C.POINTER(i64), vp, vp, C.POINTER(PresetCoded), C.POINTER(i32), vp, C.POINTER(i64), vp]
     L.cdef_debug_set_waits.argtypes = [i64, i32]
+    L.cdef_search_tables.argtypes = [vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc),
+                                     C.POINTER(vp), C.POINTER(i32), C.POINTER(i32),
+                                     C.POINTER(i32), vp, vp, vp, vp]
+    L.cdef_preset_totals.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    L.cdef_preset_argmin.argtypes = [vp, i32, vp, C.c_uint64, C.c_uint64, i32, vp, vp]
+    L.cdef_preset_assign.argtypes = [vp, i32, i32, vp, vp, vp, C.POINTER(i32), i32, vp, vp, vp,
+                                     vp]
     L.cdef_strerror.argtypes = [C.c_int]
     L.cdef_strerror.restype = C.c_char_p
     L.cdef_version.restype = C.c_char_p
@@ -110,7 +117,8 @@ def load():
                  "cdef_ctx_set_search_refine", "cdef_search_strengths_coded",
                  "cdef_ctx_set_search_metric", "cdef_ctx_set_stage_timing",
                  "cdef_ctx_get_stage_times", "cdef_ctx_set_search_subset",
-                 "cdef_ctx_status_async", "cdef_debug_set_waits"):
+                 "cdef_ctx_status_async", "cdef_debug_set_waits", "cdef_search_tables",
+                 "cdef_preset_totals", "cdef_preset_argmin", "cdef_preset_assign"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -280,6 +288,7 @@ class Context:
         _check(self._lib.cdef_ctx_create(C.byref(h), device, budget_bytes), "cdef_ctx_create")
         self.handle = h
         self.device = device
+        self.pairs = ((1 << 64) - 1, (1 << 64) - 1)   # the search subset (luma, chroma)
 
     def close(self):
         if self.handle:
@@ -317,6 +326,7 @@ class Context:
         group (default: all)."""
         _check(self._lib.cdef_ctx_set_search_subset(self.handle, luma_pairs, chroma_pairs),
                "cdef_ctx_set_search_subset")
+        self.pairs = (luma_pairs, chroma_pairs)
 
     def set_stage_timing(self, enable: bool):
         """Record per-stage device times of later strength searches."""
@@ -467,6 +477,57 @@ def cdef_search_strengths_coded(ctx: Context, recs, srcs, coded, damping, lambda
         presets, npre, block_ids.data_ptr(), cost, _stream_ptr(stream)),
         "cdef_search_strengths_coded")
     return _search_results(presets, 5, n, npre, cost)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def cdef_search_tables(ctx: Context, recs, srcs, damping, row_begin, row_count,
+                       dist_luma: torch.Tensor, dist_chroma: torch.Tensor, coded=None,
+                       skipped: torch.Tensor | None = None, stream=None):
+    """Section 5's tables of a band of filter-block rows per frame (rows
+    row_begin[i] .. row_begin[i] + row_count[i] - 1 of frame i); `coded`
+    (list of device maps) with `skipped` (device flags) selects the 128
+    combinations."""
+    n = len(recs)
+    ri = (FrameDesc * n)(*[f.desc() for f in recs])
+    si = (FrameDesc * n)(*[f.desc() for f in srcs])
+    cm = None if coded is None else (C.c_void_p * n)(*[c.data_ptr() for c in coded])
+    _check(ctx._lib.cdef_search_tables(
+        ctx.handle, n, ri, si, cm, (C.c_int32 * n)(*damping), (C.c_int32 * n)(*row_begin),
+        (C.c_int32 * n)(*row_count), dist_luma.data_ptr(), dist_chroma.data_ptr(), _ptr(skipped),
+        _stream_ptr(stream)), "cdef_search_tables")
+
+
+def cdef_preset_totals(ctx: Context, nblocks: int, width: int, dist_luma, dist_chroma, skipped,
+                       best, totals: torch.Tensor, stream=None):
+    """totals[t] = sum over the blocks not skipped of min(best[b], D_b(t))."""
+    _check(ctx._lib.cdef_preset_totals(ctx.handle, nblocks, width, _ptr(dist_luma),
+                                       _ptr(dist_chroma), _ptr(skipped), _ptr(best),
+                                       totals.data_ptr(), _stream_ptr(stream)),
+           "cdef_preset_totals")
+
+
+def cdef_preset_argmin(ctx: Context, width: int, totals: torch.Tensor, luma_pairs: int,
+                       chroma_pairs: int, keep: int, result: torch.Tensor, stream=None):
+    """result[0] = the least allowed preset (keep kept on ties with it),
+    result[1] = its total (device int64[2])."""
+    _check(ctx._lib.cdef_preset_argmin(ctx.handle, width, totals.data_ptr(), luma_pairs,
+                                       chroma_pairs, keep, result.data_ptr(), _stream_ptr(stream)),
+           "cdef_preset_argmin")
+
+
+def cdef_preset_assign(ctx: Context, nblocks: int, width: int, dist_luma, dist_chroma, skipped,
+                       presets, best=None, block_ids=None, sums=None, stream=None):
+    """Per block: least distortion over `presets` (best), the first preset
+    attaining it (block_ids); sums = (total of best, blocks not skipped)."""
+    n = len(presets)
+    arr = (C.c_int32 * max(n, 1))(*presets)
+    _check(ctx._lib.cdef_preset_assign(ctx.handle, nblocks, width, _ptr(dist_luma),
+                                       _ptr(dist_chroma), _ptr(skipped), arr, n, _ptr(best),
+                                       _ptr(block_ids), _ptr(sums), _stream_ptr(stream)),
+           "cdef_preset_assign")
 
 
 def preset_index_coded(p) -> int:

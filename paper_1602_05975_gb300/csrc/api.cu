@@ -732,35 +732,28 @@ int choose_search_tune(cdef_ctx *ctx, const SearchBatch &b, long long *dl, long 
 
 namespace {
 
-// The strength search; `coded` (host array of n device maps) selects the
-// 128-combination variant with section 4's skip semantics.  Exactly one of
-// presets / presets_coded is non-null.
-int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
-                const uint8_t *const *coded, const int32_t *damping, const int64_t *lambda,
-                int64_t *dist_luma, int64_t *dist_chroma, cdef_preset *presets,
-                cdef_preset_coded *presets_coded, int32_t *npresets, uint8_t *block_ids,
-                int64_t *cost, void *cuda_stream)
+// The search batch of n frames: validation, tile maps, per-frame fields.
+// row_begin / row_count (host, per frame; both null = whole frames) select
+// a band of filter-block rows of each frame.  *wide is set when a frame is
+// not 8/10-bit 4:2:0 (the 32-bit tables); *maps counts the 8x8 blocks of
+// the direction maps those need.
+int fill_search_batch(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
+                      const uint8_t *const *coded, const int32_t *damping, const int64_t *lambda,
+                      const int32_t *row_begin, const int32_t *row_count, SearchBatch *b,
+                      bool *wide_out, size_t *maps_out)
 {
-    if (!ctx || !rec || !src || !damping || !lambda || !(presets || presets_coded) || !npresets ||
-        !block_ids || !cost)
-        return CDEF_ERR_ARG;
-    const int width = coded ? 128 : 64;
-    if (n <= 0 || n > kMaxBatch) return CDEF_ERR_ARG;
-    if ((dist_luma == nullptr) != (dist_chroma == nullptr)) return CDEF_ERR_ARG;
-    SearchBatch *b = new (std::nothrow) SearchBatch();
-    if (!b) return CDEF_ERR_NOMEM;
     // frames other than 8/10-bit 4:2:0 take the wide tables (64 pairs,
     // squared error)
     bool wide = false;
     for (int i = 0; i < n; i++)
         if (rec[i].bitdepth > 10 || chroma_format(&rec[i]) != 420) wide = true;
-    if (wide && ctx->metric == CDEF_METRIC_EQ14) { delete b; return CDEF_ERR_ARG; }
+    if (wide && ctx->metric == CDEF_METRIC_EQ14) return CDEF_ERR_ARG;
     int total = 0, rc = CDEF_OK;
     size_t maps = 0;
     for (int i = 0; i < n && rc == CDEF_OK; i++) {
         if ((rc = check_frame(&rec[i], 7)) || (rc = check_frame(&src[i], 7))) break;
         if (!same_geometry(&rec[i], &src[i])) { rc = CDEF_ERR_SIZE; break; }
-        if (damping[i] < 3 || damping[i] > 6 || lambda[i] < 0) { rc = CDEF_ERR_ARG; break; }
+        if (damping[i] < 3 || damping[i] > 6 || (lambda && lambda[i] < 0)) { rc = CDEF_ERR_ARG; break; }
         if (coded && !coded[i]) { rc = CDEF_ERR_ARG; break; }
         SearchFrameDev &f = b->f[i];
         f.coded = coded ? coded[i] : nullptr;
@@ -782,16 +775,50 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
         f.damping = damping[i];
         f.fb_cols = (f.w + 63) / 64;
         f.fb_rows = (f.h + 63) / 64;
+        if (row_begin) {
+            const int r0 = row_begin[i], rn = row_count[i];
+            if (r0 < 0 || rn < 0 || r0 + rn > f.fb_rows) { rc = CDEF_ERR_ARG; break; }
+            f.fb_row0 = r0;
+            f.fb_rows = rn;
+        }
         f.block_start = total;
-        f.lambda = lambda[i];
+        f.lambda = lambda ? lambda[i] : 0;
         f.pairs[0] = ctx->pairs[0];
         f.pairs[1] = ctx->pairs[1];
         total += f.fb_cols * f.fb_rows;
     }
-    if (rc != CDEF_OK) { delete b; return rc; }
+    if (rc != CDEF_OK) return rc;
     b->n = n;
     b->total_blocks = total;
     b->waits = wait_limits();
+    *wide_out = wide;
+    *maps_out = maps;
+    return CDEF_OK;
+}
+
+// The strength search; `coded` (host array of n device maps) selects the
+// 128-combination variant with section 4's skip semantics.  Exactly one of
+// presets / presets_coded is non-null.
+int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
+                const uint8_t *const *coded, const int32_t *damping, const int64_t *lambda,
+                int64_t *dist_luma, int64_t *dist_chroma, cdef_preset *presets,
+                cdef_preset_coded *presets_coded, int32_t *npresets, uint8_t *block_ids,
+                int64_t *cost, void *cuda_stream)
+{
+    if (!ctx || !rec || !src || !damping || !lambda || !(presets || presets_coded) || !npresets ||
+        !block_ids || !cost)
+        return CDEF_ERR_ARG;
+    const int width = coded ? 128 : 64;
+    if (n <= 0 || n > kMaxBatch) return CDEF_ERR_ARG;
+    if ((dist_luma == nullptr) != (dist_chroma == nullptr)) return CDEF_ERR_ARG;
+    SearchBatch *b = new (std::nothrow) SearchBatch();
+    if (!b) return CDEF_ERR_NOMEM;
+    bool wide = false;
+    size_t maps = 0;
+    int rc = fill_search_batch(ctx, n, rec, src, coded, damping, lambda, nullptr, nullptr, b,
+                               &wide, &maps);
+    if (rc != CDEF_OK) { delete b; return rc; }
+    const int total = b->total_blocks;
 
     DeviceGuard g(ctx->device);
     if (!g.ok) { delete b; return CDEF_ERR_CUDA; }
@@ -941,6 +968,124 @@ int cdef_search_strengths_coded(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
     if (!coded || !presets) return CDEF_ERR_ARG;
     return search_impl(ctx, n, rec, src, coded, damping, lambda, dist_luma, dist_chroma, nullptr,
                        presets, npresets, block_ids, cost, cuda_stream);
+}
+
+int cdef_search_tables(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
+                       const uint8_t *const *coded, const int32_t *damping,
+                       const int32_t *row_begin, const int32_t *row_count, int64_t *dist_luma,
+                       int64_t *dist_chroma, uint8_t *skipped, void *cuda_stream)
+{
+    if (!ctx || !rec || !src || !damping || !row_begin || !row_count || !dist_luma ||
+        !dist_chroma || n <= 0 || n > kMaxBatch)
+        return CDEF_ERR_ARG;
+    if ((coded == nullptr) != (skipped == nullptr)) return CDEF_ERR_ARG;
+    if (coded && ctx->metric == CDEF_METRIC_EQ14) return CDEF_ERR_ARG;
+    SearchBatch *b = new (std::nothrow) SearchBatch();
+    if (!b) return CDEF_ERR_NOMEM;
+    bool wide = false;
+    size_t maps = 0;
+    int rc = fill_search_batch(ctx, n, rec, src, coded, damping, nullptr, row_begin, row_count, b,
+                               &wide, &maps);
+    if (rc != CDEF_OK) { delete b; return rc; }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) { delete b; return CDEF_ERR_CUDA; }
+    if (b->total_blocks == 0) { delete b; return CDEF_OK; }
+    uint8_t *wide_dirs = nullptr;
+    int32_t *wide_vars = nullptr;
+    SearchTune tune;
+    if (wide) {
+        if ((rc = ensure_map_set(ctx, maps, ctx->smaps_dir, ctx->smaps_var, ctx->smaps_blocks))) {
+            delete b;
+            return rc;
+        }
+        wide_dirs = ctx->smaps_dir;
+        wide_vars = ctx->smaps_var;
+        tune = {1, 1};
+    } else if (ctx->metric == CDEF_METRIC_EQ14) {
+        tune = {8, 2};
+    } else {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return CDEF_ERR_CUDA;
+        }
+        tune = default_search_tune(b->total_blocks, sms);
+    }
+    // the kernels' work counters: a filter-style slot (the call does not
+    // synchronise, so it must not share the search's pair)
+    unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));
+    const cudaError_t e = launch_search(*b, reinterpret_cast<long long *>(dist_luma),
+                                        reinterpret_cast<long long *>(dist_chroma), nullptr,
+                                        nullptr, nullptr, nullptr, ctx->status, work, tune, 0,
+                                        static_cast<cudaStream_t>(cuda_stream), skipped, nullptr,
+                                        wide_dirs, wide_vars, false, true);
+    delete b;
+    return cuda_status(e);
+}
+
+int cdef_preset_totals(cdef_ctx *ctx, int32_t nblocks, int32_t width, const int64_t *dist_luma,
+                       const int64_t *dist_chroma, const uint8_t *skipped, const uint64_t *best,
+                       int64_t *totals, void *cuda_stream)
+{
+    if (!ctx || !totals || nblocks < 0 || (width != 64 && width != 128)) return CDEF_ERR_ARG;
+    if (nblocks > 0 && (!dist_luma || !dist_chroma)) return CDEF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(totals, 0, sizeof(int64_t) * width * width, s);
+    if (e == cudaSuccess)
+        e = launch_preset_totals(nblocks, width, reinterpret_cast<const long long *>(dist_luma),
+                                 reinterpret_cast<const long long *>(dist_chroma), skipped,
+                                 reinterpret_cast<const unsigned long long *>(best),
+                                 reinterpret_cast<long long *>(totals), s);
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
+}
+
+int cdef_preset_argmin(cdef_ctx *ctx, int32_t width, const int64_t *totals, uint64_t luma_pairs,
+                       uint64_t chroma_pairs, int32_t keep, int64_t *result, void *cuda_stream)
+{
+    if (!ctx || !totals || !result || (width != 64 && width != 128) || !luma_pairs ||
+        !chroma_pairs || keep < -1 || keep >= width * width)
+        return CDEF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    const cudaError_t e = launch_preset_argmin(width, reinterpret_cast<const long long *>(totals),
+                                               luma_pairs, chroma_pairs, keep,
+                                               reinterpret_cast<long long *>(result),
+                                               static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
+}
+
+int cdef_preset_assign(cdef_ctx *ctx, int32_t nblocks, int32_t width, const int64_t *dist_luma,
+                       const int64_t *dist_chroma, const uint8_t *skipped, const int32_t *presets,
+                       int32_t npresets, uint64_t *best, uint8_t *block_ids, int64_t *sums,
+                       void *cuda_stream)
+{
+    if (!ctx || nblocks < 0 || (width != 64 && width != 128) || npresets < 0 || npresets > 8 ||
+        (npresets > 0 && !presets))
+        return CDEF_ERR_ARG;
+    if (nblocks > 0 && (!dist_luma || !dist_chroma)) return CDEF_ERR_ARG;
+    PresetList set = {};
+    set.n = npresets;
+    for (int k = 0; k < npresets; k++) {
+        if (presets[k] < 0 || presets[k] >= width * width) return CDEF_ERR_ARG;
+        set.t[k] = presets[k];
+    }
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = sums ? cudaMemsetAsync(sums, 0, 2 * sizeof(int64_t), s) : cudaSuccess;
+    if (e == cudaSuccess)
+        e = launch_preset_assign(nblocks, width, reinterpret_cast<const long long *>(dist_luma),
+                                 reinterpret_cast<const long long *>(dist_chroma), skipped, set,
+                                 reinterpret_cast<unsigned long long *>(best), block_ids,
+                                 reinterpret_cast<long long *>(sums), s);
+    if (e != cudaSuccess) cudaGetLastError();
+    return cuda_status(e);
 }
 
 const char *cdef_strerror(int status)

@@ -70,8 +70,9 @@ struct SearchFrameDev {  // aligned as CUtensorMap requires
     int w, h;                        // luma size
     int bitdepth;
     int damping;
-    int fb_cols, fb_rows;
+    int fb_cols, fb_rows;            // fb_rows: rows of filter blocks searched (a band)
     int block_start;                 // first filter block of this frame in the tables
+    int fb_row0 = 0;                 // first filter-block row of the band in the frame
     long long lambda;
     const uint8_t *coded;            // 8x8 coded-residual map (128-combination search only)
     int chroma_format = 420;         // 420, 422 or 444 (formats other than 4:2:0: wide tables)
@@ -179,7 +180,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
                           int refine_passes, cudaStream_t s, uint8_t *skipped = nullptr,
                           const cudaEvent_t *stage_events = nullptr,
                           uint8_t *wide_dirs = nullptr, int32_t *wide_vars = nullptr,
-                          bool grid_presets = false);
+                          bool grid_presets = false, bool tables_only = false);
 // Section 5's tables for 4:2:2, 4:4:4 and 12-bit frames (32-bit arithmetic
 // per sample): the direction maps of every frame into `dirs` / `vars` (at
 // each frame's map_start), then one CTA per filter block and plane group.
@@ -217,6 +218,31 @@ constexpr size_t search_scratch_bytes(int nframes, int nblocks, int width = 64)
     return sizeof(unsigned long long) * ((size_t)nblocks + (size_t)nframes * width * width) +
            kPresetCtlBytes + (width == 128 ? ((size_t)nblocks + 15) / 16 * 16 : 0);
 }
+
+// Pieces of the preset selection (eq. 15 and its re-optimisation) over a
+// block range of distortion tables, for a selection driven from the host
+// (a search sharded over devices, whose per-step totals are summed by a
+// collective).  `width` 64 or 128; presets t = luma_q * width + chroma_q.
+// totals[t] += sum over blocks b not skipped of min(best[b], D_b(t)), for
+// all width^2 presets (best null: no bound).
+cudaError_t launch_preset_totals(int nblocks, int width, const long long *dl, const long long *dc,
+                                 const uint8_t *skipped, const unsigned long long *best,
+                                 long long *totals, cudaStream_t s);
+// out[0] = the least allowed preset (lowest index on ties; `keep` >= 0 is
+// kept when it attains the least total), out[1] = its total.
+cudaError_t launch_preset_argmin(int width, const long long *totals, unsigned long long luma_pairs,
+                                 unsigned long long chroma_pairs, int keep, long long *out,
+                                 cudaStream_t s);
+// Per block: best[b] = min over the n presets of D_b (no preset: 2^64 - 1;
+// skipped: 0), ids[b] = the first preset attaining it (skipped: 0);
+// sums[0] += sum of best over blocks not skipped, sums[1] += their count.
+struct PresetList {
+    int t[8];
+    int n;
+};
+cudaError_t launch_preset_assign(int nblocks, int width, const long long *dl, const long long *dc,
+                                 const uint8_t *skipped, PresetList set, unsigned long long *best,
+                                 uint8_t *ids, long long *sums, cudaStream_t s);
 
 // Host: the three 2-D tile maps (filter-block boxes with halo) of a frame's
 // planes; returns a CDEF status.

@@ -688,7 +688,7 @@ __device__ __forceinline__ SBlockRef slocate(const SearchBatch &batch, int blk)
     while (fi + 1 < batch.n && blk >= batch.f[fi + 1].block_start) fi++;
     const int local = blk - batch.f[fi].block_start;
     const int fby = local / batch.f[fi].fb_cols;
-    return {fi, fby, local - fby * batch.f[fi].fb_cols};
+    return {fi, fby + batch.f[fi].fb_row0, local - fby * batch.f[fi].fb_cols};
 }
 
 __device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTiles &raw, uint64_t *bar)
@@ -883,7 +883,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
                           uint8_t *block_ids, int *status, unsigned *work, SearchTune tune,
                           int refine_passes, cudaStream_t s, uint8_t *skipped,
                           const cudaEvent_t *stage_events, uint8_t *wide_dirs,
-                          int32_t *wide_vars, bool grid_presets)
+                          int32_t *wide_vars, bool grid_presets, bool tables_only)
 {
     cudaError_t e = stage_mark(stage_events, 0, s);
     if (e != cudaSuccess) return e;
@@ -891,7 +891,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     if (wide_dirs) {   // 4:2:2, 4:4:4 or 12-bit frames
         e = launch_search_wide(b, wide_dirs, wide_vars, dist_luma, dist_chroma, skipped, s);
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess || tables_only) return e;
         const int width = skipped ? 128 : 64;
         e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
                            refine_passes, width, skipped, true, grid_presets, s);
@@ -900,7 +900,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     if (tune.groups == 8) {   // eq. 14 tables
         e = launch_dist_eq14(b, dist_luma, dist_chroma, status, work, s);
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess || tables_only) return e;
         e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
                            refine_passes, 64, nullptr, false, grid_presets, s);
         return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
@@ -911,7 +911,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     default: e = launch_dist<1>(b, dist_luma, dist_chroma, skipped, status, work, per_sm, s); break;
     }
     if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || tables_only) return e;
     const int width = skipped ? 128 : 64;
     e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
                        refine_passes, width, skipped, true, grid_presets, s);

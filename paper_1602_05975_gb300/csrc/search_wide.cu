@@ -104,7 +104,8 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
     while (fi + 1 < batch.n && blk >= batch.f[fi + 1].block_start) fi++;
     const SearchFrameDev &F = batch.f[fi];
     const int local = blk - F.block_start;
-    const int fby = local / F.fb_cols, fbx = local - fby * F.fb_cols;
+    const int brow = local / F.fb_cols, fbx = local - brow * F.fb_cols;
+    const int fby = brow + F.fb_row0;   // the frame's filter-block row
     const bool wide = F.bitdepth > 8;
     const int sh8 = F.bitdepth - 8;
     const bool filtered = group == 0 || F.chroma_format != 422;

@@ -115,7 +115,7 @@ def test_noalloc_near_capacity(cdef):
     rec, src = cdef.frame_from_numpy(f.rec, 8), cdef.frame_from_numpy(f.src, 8)
     n = 8
     tot = n * f.params.shape[0] * f.params.shape[1]
-    assert MAX_BLOCKS - 64 < tot <= MAX_BLOCKS
+    assert MAX_BLOCKS - 64 <= tot <= MAX_BLOCKS
     damping, lambdas = [3, 4, 5, 6] * 2, [64 << k for k in range(n)]
     ctx = cdef.Context(0)
     ids_a, dl_a, dc_a = _outputs(tot)
