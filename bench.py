@@ -484,27 +484,38 @@ def run_ours(args):
 
     peaks = measured_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    # launches overlap in the timed region: a launch's share of it is the
-    # region's time over the launches (CUDA events on the launching stream)
-    mean_launch = ms_per_step / nf
-    achieved = algorithmic_bytes_per_frame() / (mean_launch * 1e-3) / 1e9
-    ops = algorithmic_ops_per_frame() / (mean_launch * 1e-3) / 1e9
+    # the kernel's own duration: CUDA events around each launch, launches
+    # not overlapped; beside it the share of the timed region per launch
+    # (consecutive frames' launches overlap there: a throughput figure)
+    launch_ms = statistics.mean(isolated_ms)
+    share_ms = ms_per_step / nf
+    ops_b = algorithmic_ops_per_frame()
+    bytes_b = algorithmic_bytes_per_frame()
     peak_ops = alu_peak_gops(WORKLOAD["bitdepth"])
+    ops = ops_b / (launch_ms * 1e-3) / 1e9
+    achieved = bytes_b / (launch_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": ops, "peak": peak_ops, "unit": "Gop/s",
                 "frac": ops / peak_ops,
                 "traffic": ncu_traffic("filter_kernel") if WORKLOAD is FILTER_WORKLOADS["filter"]
                 else None,
                 "kernel": "filter_kernel (fused find_dir + filter)",
-                "ops_per_launch": algorithmic_ops_per_frame(),
+                "ops_per_launch": ops_b,
                 "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz"
                 if WORKLOAD["bitdepth"] <= 10 else "derived: 152 SMs x 128 lanes x 2070 MHz",
                 "hbm": {"achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "peak_source": "measured" if peaks else "fallback"},
-                "bytes_per_launch": algorithmic_bytes_per_frame(),
-                "mean_launch_us": mean_launch * 1e3,
-                "launch_time": "timed region / launches (consecutive frames overlap)"
-                if not args.no_overlap else "timed region / launches",
-                "isolated_launch_us": statistics.mean(isolated_ms) * 1e3}
+                "bytes_per_launch": bytes_b,
+                "launch_us": launch_ms * 1e3,
+                "launch_time": "mean of CUDA events around each launch, launches not overlapped",
+                "overlapped": {
+                    "share_us": share_ms * 1e3,
+                    "achieved": ops_b / (share_ms * 1e-3) / 1e9,
+                    "frac": ops_b / (share_ms * 1e-3) / 1e9 / peak_ops,
+                    "hbm_frac": bytes_b / (share_ms * 1e-3) / 1e9 / hbm,
+                    "what": "timed region / launches: consecutive frames' launches overlap "
+                            "(programmatic dependent launch), the tail of one filling the SMs "
+                            "the next starts on" if not args.no_overlap
+                            else "timed region / launches"}}
 
     cpu = None
     if pool is not None:
@@ -522,6 +533,12 @@ def run_ours(args):
                          f": {px / 1e6:.1f} Mpixel, "
                          f"{cpu_s:.1f} s of CPU work in {wall:.1f} s wall"}
 
+    # the other headline workloads (strength search, serving) on one GPU,
+    # after the filter's timed region, each with its own clock record
+    extra = None
+    if ws == 1 and not args.no_extras and WORKLOAD is FILTER_WORKLOADS["filter"]:
+        extra = {"search": search_extra(args), "serve": serve_extra(args)}
+
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -536,6 +553,7 @@ def run_ours(args):
                              f"other frames' traffic (L2: 129 MB) passes between two uses"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": args.steps * nf,
+            "extra": extra,
         }))
     if ws > 1:
         dist.destroy_process_group()
@@ -612,12 +630,19 @@ def run_search(args):
         from oracle import ref
         ref.build()
         pool = mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 16))
+    print(json.dumps(measure_search(args, args.search_variant, steps, warmup, pool)))
+
+
+def measure_search(args, variant, steps, warmup, pool=None):
+    """The search workload's measurement (see run_search): the batched call
+    timed with the L2 flushed before each call, its stages by CUDA events
+    inside the search graph, and the one-call-per-frame path on the same
+    frames; returns the bench line as a dict."""
     import torch
     from paper_1602_05975_gb300 import build, cdef, synth
     build.build()
     ctx = cdef.Context(0)
     ctx.set_search_refine(args.refine)
-    variant = args.search_variant
     if variant == "eq14":
         ctx.set_search_metric("eq14")
     bd, fmt = search_variant_format(variant)
@@ -662,7 +687,7 @@ def run_search(args):
             dc[a * width:b * width], stream=stream)
 
     starts = np.cumsum([0] + [fr.params.shape[0] * fr.params.shape[1] for fr in frames])
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         call()
     if args.check and variant == "sse":
         from oracle import ref
@@ -685,14 +710,14 @@ def run_search(args):
         return time.perf_counter() - t, r
 
     clocks.mark("begin")
-    sec = sum(timed(call)[0] for _ in range(args.steps)) / args.steps
+    sec = sum(timed(call)[0] for _ in range(steps)) / steps
     clocks.mark("end")
     clk = clocks.stop()
     tune = ctx.tuning()
     # the distortion kernel's own time: events around it in the search graph
     ctx.set_stage_timing(True)
     stage = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1)
         torch.cuda.synchronize()
         call()
@@ -710,12 +735,12 @@ def run_search(args):
             out += call(slice(i, i + 1))
         return out
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plain()
     plain_sec = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         dt, res_p = timed(plain)
-        plain_sec += dt / args.steps
+        plain_sec += dt / steps
     same = (res_p == res_b and torch.equal(batched[0], dl) and torch.equal(batched[1], dc)
             and torch.equal(batched[2], ids))
     assert same, "batched and one-frame-at-a-time searches differ"
@@ -749,10 +774,11 @@ def run_search(args):
                "sample": f"the {len(tasks)} 640x360 frames of the workload, one process per frame: "
                          f"{cand} candidates, {sum(r[1] for r in res):.1f} s of CPU work in "
                          f"{wall:.1f} s wall"}
-    print(json.dumps({
+    ctx.close()
+    return {
         "metric": "strength-search candidates/s", "value": nb * 2 * width / sec,
         "unit": "candidates/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": {"workload": SEARCH_WORKLOAD["name"], "blocks": nb,
                                         "luma_pixels": sum(f.width * f.height for f in frames),
@@ -762,8 +788,40 @@ def run_search(args):
         "refine_passes": args.refine, "variant": variant,
         "plain": {"ms_per_step": plain_sec * 1e3, "value": nb * 2 * width / plain_sec,
                   "what": "one cdef_search_strengths call per frame, identical outputs"},
-        "clocks": clk}))
-    ctx.close()
+        "clocks": clk}
+
+
+def search_extra(args):
+    """The strength-search workload (16 mixed frames, 64 + 64 pairs) for the
+    default line: candidates/s of the batched call, its stages, and the
+    one-call-per-frame path on the same frames."""
+    r = measure_search(args, "sse", 5, 2)
+    rl = r["roofline"]
+    return {"metric": r["metric"], "value": r["value"], "unit": r["unit"],
+            "workload": r["config"]["workload"], "ms_per_call": r["ms_per_step"],
+            "distortion_kernel_us": rl["mean_launch_us"], "preset_kernel_us": rl["preset_kernel_us"],
+            "plain_ms_per_call": r["plain"]["ms_per_step"],
+            "batched_over_plain": r["plain"]["ms_per_step"] / r["ms_per_step"],
+            "roofline": {k: rl[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel",
+                                            "peak_source")},
+            "tuning": r["tuning"], "l2": r["config"]["l2"], "calls": 5, "clocks": r["clocks"]}
+
+
+def serve_extra(args):
+    """The serving workload for the default line: Poisson arrivals at the
+    one-frame-at-a-time capacity (2000 requests), batched against one frame
+    at a time, plus both capacities."""
+    r = measure_serve(args, 2000, (1.0,), 100, 1000)
+    cfg = r["config"]
+    at = cfg["rates"]["1.0"]
+    keys = ("frames_per_s", "p50_ms", "p99_ms", "mean_ms", "mean_batch")
+    return {"metric": "served frames/s and latency at the one-frame-at-a-time capacity",
+            "workload": cfg["workload"], "requests": 2000,
+            "batched": {k: at["batched"][k] for k in keys},
+            "one_at_a_time": {k: at["one_at_a_time"][k] for k in keys},
+            "saturation_fps": {"batched": cfg["batched_capacity"]["frames_per_s"],
+                               "one_at_a_time": cfg["one_at_a_time_capacity"]["frames_per_s"]},
+            "verified": cfg["verified"], "clocks": r["clocks"]}
 
 
 SERVE_WORKLOAD = dict(
@@ -778,12 +836,20 @@ SERVE_WORKLOAD = dict(
 def run_serve(args):
     """The serving loop at Poisson arrival rates of 0.5-1.5x the measured
     one-frame-at-a-time capacity; both servers see the same arrivals."""
+    W = SERVE_WORKLOAD
+    print(json.dumps(measure_serve(args, args.requests or W["requests"], W["rates"],
+                                   W["verify_requests"], min(args.requests or W["requests"], 2000))))
+
+
+def measure_serve(args, n, rate_fracs, nv, ncap):
+    """The serving measurement (see run_serve) with n requests per arrival
+    rate, nv verified requests and ncap requests for the capacities;
+    returns the bench line as a dict."""
     import torch
     from paper_1602_05975_gb300 import build, cdef, serve, synth
     build.build()
     ctx = cdef.Context(0)
     W = SERVE_WORKLOAD
-    n = args.requests or W["requests"]
     rng = np.random.default_rng(W["seed"])
     contents = {}
     for si, (w, h) in enumerate(W["sizes"]):
@@ -793,7 +859,7 @@ def run_serve(args):
                                                         W["base_seed"] + 100 * si + 10 * bd + k).rec,
                                  bd) for k in range(W["contents"])]
     specs = []
-    for i in range(max(n, W["verify_requests"])):
+    for i in range(max(n, nv, ncap)):
         w, h = W["sizes"][rng.integers(len(W["sizes"]))]
         bd = W["bitdepths"][rng.integers(len(W["bitdepths"]))]
         specs.append((w, h, bd, int(rng.integers(W["contents"])), synth.random_params(rng, w, h)))
@@ -828,7 +894,6 @@ def run_serve(args):
 
     # 1. verification (untimed): every output of a mixed run equals the same
     #    frame filtered alone through the single-frame entry point
-    nv = W["verify_requests"]
     served = {}
 
     def keep(r):
@@ -852,7 +917,6 @@ def run_serve(args):
     keys = ("frames_per_s", "mpixel_per_s", "p50_ms", "p99_ms", "mean_ms", "batches",
             "mean_batch", "peak_device_bytes", "wall_s", "ok", "p99_tail")
     # 2. capacities: all requests present at t = 0 (after a warm-up run)
-    ncap = min(n, 2000)
     one_at_a_time().run(requests(np.zeros(400), 400), timeout=600)
     cap = one_at_a_time().run(requests(np.zeros(ncap), ncap), timeout=600)
     capacity = cap["frames_per_s"]
@@ -863,7 +927,7 @@ def run_serve(args):
     clocks.disabled = args.no_clocks
     clocks.start()
     rates = {}
-    for k, frac in enumerate(W["rates"]):
+    for k, frac in enumerate(rate_fracs):
         arr = serve.poisson_arrivals(n, frac * capacity, seed=W["seed"] + 1 + k)
         if frac == 1.0:
             clocks.mark("begin")
@@ -876,7 +940,8 @@ def run_serve(args):
         assert b["ok"] == n and o["ok"] == n
     clk = clocks.stop()
     head = rates["1.0"]["batched"]
-    print(json.dumps({
+    ctx.close()
+    return {
         "metric": "served frames/s at saturation (continuous batching)",
         "value": bcap["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": 1,
         "warmup": 1, "ms_per_step": bcap["wall_s"] * 1e3, "higher_is_better": True,
@@ -892,8 +957,7 @@ def run_serve(args):
                    "verified": f"{nv} requests served in mixed batches equal the "
                                f"single-frame path bit for bit",
                    "rates": rates},
-        "clocks": clk}))
-    ctx.close()
+        "clocks": clk}
 
 
 def main():
@@ -904,6 +968,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="filter only: leave out the search and serving figures")
     ap.add_argument("--no-overlap", action="store_true",
                     help="filter: keep stream order between frames (no overlapped launches)")
     ap.add_argument("--cpu-bands", type=int, default=0,

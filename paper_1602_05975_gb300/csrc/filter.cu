@@ -22,7 +22,12 @@
 //    (direction, strengths and damping are constant over an 8x8 block,
 //    section 3.1); then row w of the 4x4 chroma blocks, one (U, V) word per
 //    lane and row.  Both go through one code path; tap positions are
-//    per-lane word offsets from a per-direction table.
+//    per-lane word offsets from a per-direction table.  (A warp's 32 lanes
+//    read 32 consecutive words of a row: no shared-memory bank conflicts.)
+// 4. Store.  The warp's output rows pass through a 512-byte staging area of
+//    its own (the direction-cost array, idle while the block is filtered)
+//    and leave as 16-byte stores of whole row segments: a warp store writes
+//    full 128-byte lines.
 //
 // Packed arithmetic (two 16-bit lanes per word).  For a tap value p and the
 // filtered pixel x, eq. 7 with strength S and shift sh = D - floor(log2 S)
@@ -55,7 +60,12 @@ struct FilterSmem {
     RawTiles raw;                                       // the next block's tiles land here
     PairTiles t;
     alignas(16) int off[2][8][12];                      // tap word offsets [luma/chroma][d][tap]
-    int cost[64][8];
+    // direction costs (direction search) and, while the block is filtered,
+    // each warp's output rows on their way to 16-byte stores
+    union {
+        int cost[64][8];
+        alignas(16) uint32_t stage[8][128];
+    };
     BlockC lb[64];
     BlockC cb;
     BlockC bz;                                          // identity set (unfiltered blocks)
@@ -111,6 +121,97 @@ __device__ __forceinline__ uint32_t filter_word(uint32_t X, uint32_t v[12], cons
     return finish(X, P, Q, (bc.flags & 3) == 3, mn, mx);
 }
 
+// Output of the filter loops.  Each lane hands its word of a row (two
+// 16-bit lanes: a luma pixel pair, or a (U, V) pair) to its warp's 512-byte
+// staging area (stage_put); once a group of whole rows is staged, the warp
+// reads them back as 16-byte row segments and stores those (stage_flush),
+// so that a warp store writes full 128-byte lines.  A segment cut by the
+// frame's right edge stores only its blocks inside the frame.  The staging
+// holds 4 rows of 16-bit luma, 8 rows of 8-bit luma, or the 4 rows of a
+// chroma block row (U and V): kGroupRows.  kBytes: sample size in the frame.
+template <bool kLuma, int kBytes>
+struct StageOut {
+    static constexpr int kGroupRows = (kLuma && kBytes == 1) ? 8 : 4;
+    uint32_t off;        // byte offset in its plane of this lane's segment in its first row
+    int n;               // blocks of the segment inside the frame (0: the lane stores nothing)
+
+    // The lane's segment: which staged row and 16 bytes it reads, where
+    // they go.  fbx, fby: the filter block; warp: its block row.
+    __device__ __forceinline__ StageOut(const FilterFrameDev &F, int lane, int fby, int fbx,
+                                        int warp, bool row_in)
+    {
+        int plane = 0, r, c, nblk, blk_px, x_bytes, y0;
+        if (kLuma && kBytes == 2) {          // lane L: row L / 8 of block L % 8
+            r = lane >> 3, c = lane & 7, nblk = 1, blk_px = 8, x_bytes = (fbx * 64 + c * 8) * 2;
+            y0 = fby * 64 + warp * 8;
+        } else if (kLuma) {                  // row L / 4 of blocks 2 (L % 4), 2 (L % 4) + 1
+            r = lane >> 2, c = lane & 3, nblk = 2, blk_px = 8, x_bytes = fbx * 64 + c * 16;
+            y0 = fby * 64 + warp * 8;
+        } else if (kBytes == 2) {            // lanes 0-15 U, 16-31 V: row (L % 16) / 4, two blocks
+            plane = lane >> 4, r = (lane >> 2) & 3, c = lane & 3, nblk = 2, blk_px = 4;
+            x_bytes = fbx * 64 + c * 16, y0 = fby * 32 + warp * 4;
+        } else {                             // lanes 0-7 U, 8-15 V: row (L % 8) / 2, four blocks
+            plane = (lane >> 3) & 1, r = (lane >> 1) & 3, c = lane & 1, nblk = 4, blk_px = 4;
+            x_bytes = fbx * 32 + c * 16, y0 = fby * 32 + warp * 4;
+        }
+        const PlaneDev &P = kLuma ? F.p[0] : plane ? F.p[2] : F.p[1];
+        const int first = (fbx * 8 + c * nblk) * blk_px;
+        int k = (P.w - first) / blk_px;
+        k = k < 0 ? 0 : (k > nblk ? nblk : k);
+        n = (row_in && (kLuma || kBytes == 2 || lane < 16)) ? k : 0;
+        off = (uint32_t)((int64_t)(y0 + r) * P.out_pitch + x_bytes);
+    }
+
+    // the lane's word of row i (of the group) into the staging area
+    __device__ __forceinline__ static void put(uint8_t *st8, int lane, int i, uint32_t y)
+    {
+        if (kLuma && kBytes == 2) {
+            reinterpret_cast<uint32_t *>(st8)[i * 32 + lane] = y;
+        } else if (kLuma) {
+            reinterpret_cast<uint16_t *>(st8 + i * 64)[lane] = (uint16_t)__byte_perm(y, 0, 0x0020);
+        } else if (kBytes == 2) {
+            reinterpret_cast<uint16_t *>(st8 + i * 64)[lane] = (uint16_t)(y & 0xffff);
+            reinterpret_cast<uint16_t *>(st8 + 256 + i * 64)[lane] = (uint16_t)(y >> 16);
+        } else {
+            st8[i * 32 + lane] = (uint8_t)(y & 0xff);
+            st8[128 + i * 32 + lane] = (uint8_t)((y >> 16) & 0xff);
+        }
+    }
+
+    // the staged group out to the frame; the staging is free again after it
+    __device__ __forceinline__ void flush(const FilterFrameDev &F, const uint8_t *st8, int lane)
+    {
+        constexpr int nblk = kLuma ? (kBytes == 2 ? 1 : 2) : (kBytes == 2 ? 2 : 4);
+        __syncwarp();
+        if (n) {
+            int so;   // the segment in the staging area
+            if (kLuma && kBytes == 2) so = (lane >> 3) * 128 + (lane & 7) * 16;
+            else if (kLuma) so = (lane >> 2) * 64 + (lane & 3) * 16;
+            else if (kBytes == 2) so = (lane >> 4) * 256 + ((lane >> 2) & 3) * 64 + (lane & 3) * 16;
+            else so = ((lane >> 3) & 1) * 128 + ((lane >> 1) & 3) * 32 + (lane & 1) * 16;
+            // the plane, selected without indexing the parameter block
+            const bool v_plane = !kLuma && (kBytes == 2 ? lane >= 16 : ((lane >> 3) & 1));
+            uint8_t *dst = (kLuma ? F.p[0].out : v_plane ? F.p[2].out : F.p[1].out) + off;
+            const int64_t pitch = kLuma ? F.p[0].out_pitch : v_plane ? F.p[2].out_pitch : F.p[1].out_pitch;
+            const uint4 q = *reinterpret_cast<const uint4 *>(st8 + so);
+            if (n == nblk) {
+                *reinterpret_cast<uint4 *>(dst) = q;
+            } else if (kBytes == 2 || kLuma) {   // one of two 8-byte blocks
+                *reinterpret_cast<uint2 *>(dst) = make_uint2(q.x, q.y);
+            } else {                             // 1..3 of four 4-byte blocks
+                uint32_t *d32 = reinterpret_cast<uint32_t *>(dst);
+                d32[0] = q.x;
+                if (n > 1) d32[1] = q.y;
+                if (n > 2) d32[2] = q.z;
+            }
+            // the next group: 4 rows down (16-bit luma; the other layouts
+            // flush once per block row)
+            off += 4 * (uint32_t)pitch;
+        }
+        __syncwarp();
+    }
+};
+
 // ---------------------------------------------------------------------------
 // 12-bit frames: sums of 12-bit differences leave the 16-bit lanes, so each
 // sample of a word is filtered with 32-bit arithmetic (eq. 7-12 directly).
@@ -149,7 +250,8 @@ __device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int f
         const int blk = warp * 8 + bx;
         const int gby = fby * 8 + warp, gbx = fbx * 8 + bx;
         const bool inside = luma ? (gby * 8 < H && gbx * 8 < W) : (gby * 4 < CH && gbx * 4 < CW);
-        if (!inside) continue;
+        if (!__any_sync(0xffffffffu, inside)) continue;   // lanes outside compute, store nothing
+        const bool row_in = luma ? gby * 8 < H : gby * 4 < CH;
         const bool cpl = !luma || F.mode == 2;   // chroma parameters
         const bool on = any_coded && (sm.coded[blk] || (cpl ? skip_c : skip_l));
         Eff e = cpl ? make_eff(prm.pri_uv, prm.sec_uv, prm.damping, true, 0, sh8)
@@ -160,30 +262,32 @@ __device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int f
         const uint32_t *base = luma ? sm.t.le + (2 + warp * 8) * kLumaPitch + 4 + bx * 4 + sub
                                     : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
         const int *o = sm.off[task][sm.dir[blk]];
-        const int oy = luma ? fby * 64 + warp * 8 : fby * 32 + warp * 4;
-        const int ox = luma ? fbx * 64 + bx * 8 + 2 * sub : fbx * 32 + bx * 4 + sub;
-        for (int i = 0; i < rows; i++) {
-            const uint32_t *b = base + i * pitch;
-            const uint32_t X = b[0];
-            uint32_t v[12];
+        uint8_t *st8 = reinterpret_cast<uint8_t *>(sm.stage[warp]);
+        auto run = [&](auto luma_c) {
+            using Out = StageOut<decltype(luma_c)::value, 2>;
+            Out out(F, lane, fby, fbx, warp, row_in);
+            for (int g = 0; g < rows; g += Out::kGroupRows) {
+                for (int i = 0; i < Out::kGroupRows; i++) {
+                    const uint32_t *b = base + (g + i) * pitch;
+                    const uint32_t X = b[0];
+                    uint32_t v[12];
 #pragma unroll
-            for (int k = 0; k < 12; k++) v[k] = b[o[k]];
-            int y[2];
+                    for (int k = 0; k < 12; k++) v[k] = b[o[k]];
+                    int y[2];
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                int p[12];
+                    for (int h = 0; h < 2; h++) {
+                        int p[12];
 #pragma unroll
-                for (int k = 0; k < 12; k++) p[k] = (int)((v[k] >> (16 * h)) & 0xffffu);
-                y[h] = filter_sample_wide((int)((X >> (16 * h)) & 0xffffu), p, e) - (int)kBias;
+                        for (int k = 0; k < 12; k++) p[k] = (int)((v[k] >> (16 * h)) & 0xffffu);
+                        y[h] = filter_sample_wide((int)((X >> (16 * h)) & 0xffffu), p, e) - (int)kBias;
+                    }
+                    Out::put(st8, lane, i, (uint32_t)y[0] | ((uint32_t)y[1] << 16));
+                }
+                out.flush(F, st8, lane);
             }
-            if (luma) {
-                uint16_t *row = reinterpret_cast<uint16_t *>(F.p[0].out + (int64_t)(oy + i) * F.p[0].out_pitch);
-                *reinterpret_cast<uint32_t *>(row + ox) = (uint32_t)y[0] | ((uint32_t)y[1] << 16);
-            } else {
-                reinterpret_cast<uint16_t *>(F.p[1].out + (int64_t)(oy + i) * F.p[1].out_pitch)[ox] = (uint16_t)y[0];
-                reinterpret_cast<uint16_t *>(F.p[2].out + (int64_t)(oy + i) * F.p[2].out_pitch)[ox] = (uint16_t)y[1];
-            }
-        }
+        };
+        if (luma) run(std::true_type{});
+        else run(std::false_type{});
     }
 }
 
@@ -316,33 +420,23 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         const int4 *op = reinterpret_cast<const int4 *>(sm.off[task][sm.dir[blk]]);
         const int4 o0 = op[0], o1 = op[1], o2 = op[2];
         const int o[12] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w};
-        // output: row 0 of this lane's column
-        const int oy = luma ? fby * 64 + warp * 8 : fby * 32 + warp * 4;
-        const int ox = luma ? fbx * 64 + bx * 8 + 2 * sub : fbx * 32 + bx * 4 + sub;
-        uint8_t *o_a = (luma ? F.p[0].out : F.p[1].out) + (int64_t)oy * (luma ? F.p[0].out_pitch : F.p[1].out_pitch);
-        uint8_t *o_b = F.p[2].out + (int64_t)oy * F.p[2].out_pitch;
-        const int64_t pa = luma ? F.p[0].out_pitch : F.p[1].out_pitch, pb = F.p[2].out_pitch;
+        const bool row_in = luma ? gby * 8 < H : gby * 4 < CH;
+        using Out = StageOut<luma, sizeof(T)>;
+        Out out(F, lane, fby, fbx, warp, row_in);
+        uint8_t *st8 = reinterpret_cast<uint8_t *>(sm.stage[warp]);
+        const uint32_t *b = base;
+#pragma unroll 1
+        for (int g = 0; g < rows; g += Out::kGroupRows) {
 #pragma unroll 1  // a compact loop body: the hot code has to stay in the instruction cache
-        for (int i = 0; i < rows; i++) {
-            const uint32_t *b = base + i * pitch;
-            const uint32_t X = b[0];
-            uint32_t v[12];
+            for (int i = 0; i < Out::kGroupRows; i++, b += pitch) {
+                const uint32_t X = b[0];
+                uint32_t v[12];
 #pragma unroll
-            for (int k = 0; k < 12; k++) v[k] = b[o[k]];
-            uint32_t y = filter_word(X, v, bc, any_p, any_s, any_clip, any_edge) - kBias * kLanes;
-            if (inside) {
-                if (luma) {
-                    if (sizeof(T) == 2)
-                        *reinterpret_cast<uint32_t *>(o_a + 2 * ox) = y;
-                    else
-                        *reinterpret_cast<uint16_t *>(o_a + ox) = (uint16_t)__byte_perm(y, 0, 0x0020);
-                } else {
-                    reinterpret_cast<T *>(o_a)[ox] = (T)(y & 0xffff);
-                    reinterpret_cast<T *>(o_b)[ox] = (T)(y >> 16);
-                }
+                for (int k = 0; k < 12; k++) v[k] = b[o[k]];
+                Out::put(st8, lane, i, filter_word(X, v, bc, any_p, any_s, any_clip, any_edge) -
+                                           kBias * kLanes);
             }
-            o_a += pa;
-            o_b += pb;
+            out.flush(F, st8, lane);
         }
     };
     task_body(std::true_type{});

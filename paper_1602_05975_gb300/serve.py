@@ -35,23 +35,30 @@ from typing import Callable, Optional
 import numpy as np
 
 # Signalled ranges of section 4: primary 0..15 (19 for the skip mapping),
-# secondary {0, 1, 2, 4} (7 for the skip mapping), damping 3..6.
+# secondary {0, 1, 2, 4} (7 for the skip mapping), damping 3..6; as a table
+# of valid byte values per parameter field (pri_y, sec_y, pri_uv, sec_uv,
+# damping), so that a request is checked with one lookup.
 _PRI_OK = set(range(16)) | {19}
 _SEC_OK = {0, 1, 2, 4, 7}
+# _BITS[v]: bit k set where byte value v is valid for field k; a block's 8
+# bytes mapped through it and read as one little-endian uint64 must have
+# bit k of byte k set for k < 5 (bytes 5..7 are not checked here)
+_BITS = np.zeros(256, dtype=np.uint8)
+for _k, _ok in enumerate((_PRI_OK, _SEC_OK, _PRI_OK, _SEC_OK, range(3, 7))):
+    _BITS[list(_ok)] |= np.uint8(1 << _k)
+_WANT = np.uint64(sum((1 << k) << (8 * k) for k in range(5)))
+_DAMP = np.uint64((1 << 4) << 32)
 
 
 def validate_params(params: np.ndarray, width: int, height: int) -> Optional[str]:
     """Host-side check of a request's parameter array; None if valid."""
     rows, cols = -(-height // 64), -(-width // 64)
-    if params.shape != (rows, cols, 8):
-        return f"params shape {params.shape}, expected {(rows, cols, 8)}"
-    p = params.reshape(-1, 8)
-    for k, ok in ((0, _PRI_OK), (1, _SEC_OK), (2, _PRI_OK), (3, _SEC_OK)):
-        if not set(np.unique(p[:, k]).tolist()) <= ok:
-            return "strength out of range"
-    if p[:, 4].min() < 3 or p[:, 4].max() > 6:
-        return "damping out of range"
-    return None
+    if params.shape != (rows, cols, 8) or params.dtype != np.uint8:
+        return f"params shape {params.shape} ({params.dtype}), expected {(rows, cols, 8)} uint8"
+    m = np.take(_BITS, np.ascontiguousarray(params).reshape(-1)).view("<u8") & _WANT
+    if (m == _WANT).all():
+        return None
+    return "damping out of range" if ((m & _DAMP) != _DAMP).any() else "strength out of range"
 
 
 @dataclasses.dataclass(eq=False)
@@ -354,6 +361,10 @@ class CudaBackend(Backend):
         # device-to-host stream (no synchronous call in the loop)
         self.status_words = torch.zeros(256, dtype=torch.int32).pin_memory()
         self.next_word = 0
+        # the three events of each batch, reused round-robin with the status
+        # words (a ring far longer than the batches in flight)
+        self.events = [tuple(torch.cuda.Event() for _ in range(3))
+                       for _ in range(self.status_words.numel())]
 
     @staticmethod
     def key(req: Request):
@@ -403,8 +414,10 @@ class CudaBackend(Backend):
                                                         device=self.device, extra_bytes=n_params)
             flat_out, f_out, _ = self.cdef.alloc_packed(req.width, req.height, req.bitdepth,
                                                         device=self.device)
+            planes, _ = self.cdef.packed_layout(req.width, req.height, req.bitdepth)
             req.slot = {"flat_in": flat_in, "in": f_in, "params": prm, "flat_out": flat_out,
-                        "out": f_out, "bytes": req.need}
+                        "out": f_out, "bytes": req.need,
+                        "in_planes": flat_in[:planes[3]]}   # the planes, without parameters
             self.held_bytes += req.need
         hk = self.host_out[k]
         req.slot["host_out"] = hk.pop() if hk else self.cdef.alloc_packed(
@@ -422,26 +435,24 @@ class CudaBackend(Backend):
             if r.params_host is None:
                 r.params_host = torch.from_numpy(
                     np.ascontiguousarray(r.params, dtype=np.uint8).reshape(-1)).pin_memory()
+        ev_up, ev_c, ev_d = self.events[self.next_word]
+        word = self.status_words[self.next_word:self.next_word + 1]
+        self.next_word = (self.next_word + 1) % self.status_words.numel()
         with torch.cuda.stream(self.up):
             for r in reqs:
-                r.slot["flat_in"][:r.frame.numel()].copy_(r.frame, non_blocking=True)
+                r.slot["in_planes"].copy_(r.frame, non_blocking=True)
                 r.slot["params"].copy_(r.params_host, non_blocking=True)
-        ev_up = torch.cuda.Event()
         ev_up.record(self.up)
         self.comp.wait_event(ev_up)
         self.cdef.cdef_filter_frames(self.ctx, [r.slot["in"] for r in reqs],
                                      [r.slot["params"] for r in reqs],
                                      [r.slot["out"] for r in reqs], stream=self.comp)
-        ev_c = torch.cuda.Event()
         ev_c.record(self.comp)
         self.down.wait_event(ev_c)
-        word = self.status_words[self.next_word:self.next_word + 1]
-        self.next_word = (self.next_word + 1) % self.status_words.numel()
         with torch.cuda.stream(self.down):
             for r in reqs:
                 r.slot["host_out"][0].copy_(r.slot["flat_out"], non_blocking=True)
         self.ctx.status_async(word, stream=self.down)
-        ev_d = torch.cuda.Event()
         ev_d.record(self.down)
         # keep the host output reachable from the request once it is done
         for r in reqs:
