@@ -576,7 +576,8 @@ SEARCH_WORKLOAD = dict(
 # the (19, 7) preset's 12 taps and the uncoded part's accumulation per
 # candidate (1).  Per luma 8x8 block: the direction search as in the filter.
 def search_ops_per_sample(variant: str) -> int:
-    per_cand = {"sse": 8, "eq14": 11, "coded": 9, "444": 8, "12bit": 8, "444coded": 9}[variant]
+    per_cand = {"sse": 8, "eq14": 11, "coded": 9, "444": 8, "12bit": 8, "444coded": 9,
+                "444eq14": 11, "12biteq14": 11}[variant]
     extra = 12 * 8 if variant in ("coded", "444coded") else 0
     return 16 * 4 * 8 + 3 * 8 * 8 + 24 + 64 * per_cand + extra
 
@@ -600,7 +601,10 @@ def _oracle_search(task):
     bd, fmt = search_variant_format(variant)
     f = synth.make_frame(w, h, bd, None, seed, fmt)
     t = time.process_time()
-    if variant == "444coded":
+    if variant in ("444eq14", "12biteq14"):
+        dl, dc = ref.distortion_eq14_format(f.rec, f.src, bd, damping, fmt)
+        ref.select_presets_general(dl, dc, 64, None, lam, passes)
+    elif variant == "444coded":
         ref.search_strengths_coded_format(f.rec, f.src, bd, damping, lam, fmt, coded, passes)
     elif variant in ("444", "12bit"):
         ref.search_strengths_format(f.rec, f.src, bd, damping, lam, fmt, passes)
@@ -616,7 +620,8 @@ def _oracle_search(task):
 
 def search_variant_format(variant: str):
     """(bit depth, chroma format) of the search workload's frames."""
-    return {"444": (8, 444), "444coded": (8, 444), "12bit": (12, 420)}.get(variant, (8, 420))
+    return {"444": (8, 444), "444coded": (8, 444), "12bit": (12, 420), "444eq14": (8, 444),
+            "12biteq14": (12, 420)}.get(variant, (8, 420))
 
 
 def run_search(args):
@@ -643,7 +648,7 @@ def measure_search(args, variant, steps, warmup, pool=None):
     build.build()
     ctx = cdef.Context(0)
     ctx.set_search_refine(args.refine)
-    if variant == "eq14":
+    if variant.endswith("eq14"):
         ctx.set_search_metric("eq14")
     bd, fmt = search_variant_format(variant)
     frames = []
@@ -751,7 +756,9 @@ def measure_search(args, variant, steps, warmup, pool=None):
                 "unit": "Gop/s", "frac": ops / (dist_ms * 1e-3) / 1e9 / peak_ops,
                 "traffic": None,
                 "kernel": "dist_wide_kernel + find_dir_kernel (distortion tables, 32-bit lanes)"
-                if variant in ("444", "12bit", "444coded") else "dist_kernel (distortion tables)",
+                if variant in ("444", "12bit", "444coded")
+                else "dist_wide_eq14_kernel + find_dir_kernel (eq. 14 tables, 32-bit lanes)"
+                if variant in ("444eq14", "12biteq14") else "dist_kernel (distortion tables)",
                 "ops_per_launch": ops, "mean_launch_us": dist_ms * 1e3,
                 "launch_time": "CUDA events around the kernel inside the search graph",
                 "preset_kernel_us": pre_ms * 1e3,
@@ -795,7 +802,7 @@ def search_extra(args):
     """The strength-search workload (16 mixed frames, 64 + 64 pairs) for the
     default line: candidates/s of the batched call, its stages, and the
     one-call-per-frame path on the same frames."""
-    r = measure_search(args, "sse", 5, 2)
+    r = measure_search(args, "sse", 5, 3)
     rl = r["roofline"]
     return {"metric": r["metric"], "value": r["value"], "unit": r["unit"],
             "workload": r["config"]["workload"], "ms_per_call": r["ms_per_step"],
@@ -989,7 +996,8 @@ def main():
     ap.add_argument("--refine", type=int, default=0,
                     help="search: preset re-optimisation passes after the greedy search")
     ap.add_argument("--search-variant", default="sse",
-                    choices=["sse", "eq14", "coded", "444", "12bit", "444coded"],
+                    choices=["sse", "eq14", "coded", "444", "12bit", "444coded", "444eq14",
+                             "12biteq14"],
                     help="search: squared error (64 pairs), eq. 14 distortion, the "
                          "128-combination search with coded-residual maps, or the squared-error "
                          "search over 8-bit 4:4:4 or 12-bit 4:2:0 frames")

@@ -224,9 +224,7 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
  * with the chroma strengths and the co-located luma direction.  A call
  * holding any 12-bit, 4:2:2 or 4:4:4 frame computes its tables with 32-bit
  * arithmetic per sample (slower than the packed 8/10-bit 4:2:0 path) and
- * needs (W/8)(H/8) * 5 bytes of direction maps per frame in the context;
- * such calls take only the squared-error metric (CDEF_ERR_ARG with
- * CDEF_METRIC_EQ14).
+ * needs (W/8)(H/8) * 5 bytes of direction maps per frame in the context.
  * This call synchronises the stream before returning (host outputs).
  */
 int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
@@ -309,8 +307,13 @@ int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
  *                    312.5 * 16^(bd-8); each 8x8 value in units of 1/256,
  *                    rounded half away from zero after an IEEE
  *                    single-precision evaluation in a fixed order, so that the
- *                    tables are exact integers.  Not available with
- *                    cdef_search_strengths_coded (CDEF_ERR_ARG).
+ *                    tables are exact integers (an entry of n 8x8 terms is
+ *                    within n + 2^-20 (entry + n) of eq. 14 evaluated
+ *                    exactly).  Every chroma format and bit depth (4:2:2
+ *                    chroma: the unfiltered value for every pair), and the
+ *                    128 combinations of cdef_search_strengths_coded (each
+ *                    8x8 block's value from what the decoder outputs for
+ *                    the preset; formed by the 32-bit path).
  * Host only; applies to later searches on the context. */
 #define CDEF_METRIC_SSE 0
 #define CDEF_METRIC_EQ14 1
@@ -446,7 +449,6 @@ int cdef_search_strengths_noalloc(int32_t n, const cdef_frame *rec,
  *   dist_luma,
  *   dist_chroma    : DEVICE, (band blocks) * 64 (or 128) int64 each, written
  * Frames as cdef_search_strengths.  CDEF_ERR_ARG for a band outside the
- * frame, eq. 14 with coded maps, or eq. 14 with a 12-bit, 4:2:2 or 4:4:4
  * frame. */
 int cdef_search_tables(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_frame *src,
                        const uint8_t *const *coded, const int32_t *damping,

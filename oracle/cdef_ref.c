@@ -1219,6 +1219,203 @@ int cdef_ref_distortion_eq14(int w, int h, int bitdepth, int damping,
     return 0;
 }
 
+/* Eq. 14 tables for chroma format 420, 422 or 444 at any bit depth
+ * (readings R22-R25): the sum over the 8x8 blocks of each plane inside the
+ * filter block of eq. 14's value, with the chroma geometry of
+ * cdef_ref_distortion_format (4:2:2 chroma is never filtered: every pair
+ * gives the unfiltered value).  The 8x8 blocks are those of the plane's own
+ * grid; a block cut by the frame edge takes its in-frame samples. */
+static int64_t block_eq14_g(const uint16_t *rec, ptrdiff_t rs, const uint16_t *src, ptrdiff_t ss,
+                            int pw, int ph, int sub, int chroma, int filtered, int bitdepth,
+                            int fby, int fbx, int pri, int sec, int damping, const uint8_t *dir,
+                            const int32_t *var, int bw, int fbw, int fbh)
+{
+    int bs = 8 >> sub;
+    int64_t total = 0;
+    for (int by = fby * fbh; by < (fby + 1) * fbh && by < ph; by += 8) {
+        for (int bx = fbx * fbw; bx < (fbx + 1) * fbw && bx < pw; bx += 8) {
+            int64_t n = 0, s1s = 0, s2s = 0, s1d = 0, s2d = 0, sse = 0;
+            for (int i = by; i < by + 8 && i < ph; i++) {
+                for (int j = bx; j < bx + 8 && j < pw; j++) {
+                    int64_t d = rec[(ptrdiff_t)i * rs + j];
+                    if (filtered) {
+                        int b8 = (i / bs) * bw + (j / bs);
+                        cdef_ref_eff_params e;
+                        cdef_ref_block_params(pri, sec, damping, chroma, bitdepth,
+                                              chroma ? 0 : var[b8], &e);
+                        d = cdef_ref_filter_sample(rec, pw, ph, rs, i, j, dir[b8], &e);
+                    }
+                    int64_t sv = src[(ptrdiff_t)i * ss + j];
+                    n++;
+                    s1s += sv;
+                    s2s += sv * sv;
+                    s1d += d;
+                    s2d += d * d;
+                    sse += (d - sv) * (d - sv);
+                }
+            }
+            total += eq14_term(n, s1s, s2s, s1d, s2d, sse, bitdepth);
+        }
+    }
+    return total;
+}
+
+int cdef_ref_distortion_eq14_format(int w, int h, int bitdepth, int damping, int format,
+                                    const uint16_t *ry, ptrdiff_t rys,
+                                    const uint16_t *ru, ptrdiff_t rus,
+                                    const uint16_t *rv, ptrdiff_t rvs,
+                                    const uint16_t *sy, ptrdiff_t sys,
+                                    const uint16_t *su, ptrdiff_t sus,
+                                    const uint16_t *sv, ptrdiff_t svs,
+                                    int64_t *dist_luma, int64_t *dist_chroma)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    if (damping < 3 || damping > 6 || (format != 420 && format != 422 && format != 444))
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    uint8_t *dir = (uint8_t *)malloc((size_t)bw * bh);
+    int32_t *var = (int32_t *)malloc((size_t)bw * bh * sizeof(int32_t));
+    if (!dir || !var) {
+        free(dir);
+        free(var);
+        return -1;
+    }
+    cdef_ref_find_dir(ry, w, h, rys, bitdepth, dir, var);
+    int cw = format == 444 ? w : w / 2, ch = format == 420 ? h / 2 : h;
+    int csub = format == 444 ? 0 : 1;
+    int cfw = format == 444 ? 64 : 32, cfh = format == 420 ? 32 : 64;
+    int cfilt = format != 422;
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    for (int fby = 0; fby < fb_rows; fby++) {
+        for (int fbx = 0; fbx < fb_cols; fbx++) {
+            int b = fby * fb_cols + fbx;
+            for (int p = 0; p < 16; p++) {
+                for (int s = 0; s < 4; s++) {
+                    int q = p * 4 + s;
+                    dist_luma[b * 64 + q] =
+                        block_eq14_g(ry, rys, sy, sys, w, h, 0, 0, 1, bitdepth, fby, fbx, p,
+                                     sec_values[s], damping, dir, var, bw, 64, 64);
+                    dist_chroma[b * 64 + q] =
+                        block_eq14_g(ru, rus, su, sus, cw, ch, csub, 1, cfilt, bitdepth, fby, fbx,
+                                     p, sec_values[s], damping, dir, var, bw, cfw, cfh) +
+                        block_eq14_g(rv, rvs, sv, svs, cw, ch, csub, 1, cfilt, bitdepth, fby, fbx,
+                                     p, sec_values[s], damping, dir, var, bw, cfw, cfh);
+                }
+            }
+        }
+    }
+    free(dir);
+    free(var);
+    return 0;
+}
+
+/* Eq. 14 tables of the 128 combinations (readings R21-R25): as
+ * cdef_ref_distortion_coded_format with each entry the sum over the 8x8
+ * blocks of each plane (the plane's own grid) of eq. 14's value of what the
+ * decoder outputs for that preset: a sample of the 8x8 (4:2:0 chroma: 4x4)
+ * direction block j is filtered when the filter block has coded residual
+ * and (j's co-located luma block is coded or the skip bit k is set); (0, 0)
+ * with k set stands for (19, 7); 4:2:2 chroma is never filtered. */
+static int64_t block_eq14_coded_g(const uint16_t *rec, ptrdiff_t rs, const uint16_t *src,
+                                  ptrdiff_t ss, int pw, int ph, int sub, int chroma, int filtered,
+                                  int bitdepth, int fby, int fbx, int pri, int sec, int k,
+                                  int damping, const uint8_t *dir, const int32_t *var, int bw,
+                                  int fbw, int fbh, const uint8_t *coded, int fb_coded)
+{
+    int bs = 8 >> sub;
+    int64_t total = 0;
+    for (int by = fby * fbh; by < (fby + 1) * fbh && by < ph; by += 8) {
+        for (int bx = fbx * fbw; bx < (fbx + 1) * fbw && bx < pw; bx += 8) {
+            int64_t n = 0, s1s = 0, s2s = 0, s1d = 0, s2d = 0, sse = 0;
+            for (int i = by; i < by + 8 && i < ph; i++) {
+                for (int j = bx; j < bx + 8 && j < pw; j++) {
+                    int b8 = (i / bs) * bw + (j / bs);
+                    int on = filtered && fb_coded && (!coded || coded[b8] || k);
+                    int64_t d = rec[(ptrdiff_t)i * rs + j];
+                    if (on) {
+                        cdef_ref_eff_params e;
+                        cdef_ref_block_params(pri, sec, damping, chroma, bitdepth,
+                                              chroma ? 0 : var[b8], &e);
+                        d = cdef_ref_filter_sample(rec, pw, ph, rs, i, j, dir[b8], &e);
+                    }
+                    int64_t sv = src[(ptrdiff_t)i * ss + j];
+                    n++;
+                    s1s += sv;
+                    s2s += sv * sv;
+                    s1d += d;
+                    s2d += d * d;
+                    sse += (d - sv) * (d - sv);
+                }
+            }
+            total += eq14_term(n, s1s, s2s, s1d, s2d, sse, bitdepth);
+        }
+    }
+    return total;
+}
+
+int cdef_ref_distortion_eq14_coded_format(int w, int h, int bitdepth, int damping, int format,
+                                          const uint16_t *ry, ptrdiff_t rys,
+                                          const uint16_t *ru, ptrdiff_t rus,
+                                          const uint16_t *rv, ptrdiff_t rvs,
+                                          const uint16_t *sy, ptrdiff_t sys,
+                                          const uint16_t *su, ptrdiff_t sus,
+                                          const uint16_t *sv, ptrdiff_t svs,
+                                          const uint8_t *coded, int64_t *dist_luma,
+                                          int64_t *dist_chroma, uint8_t *skipped)
+{
+    if (w <= 0 || h <= 0 || w % 8 || h % 8 || bitdepth < 8 || bitdepth > 12)
+        return -1;
+    if (damping < 3 || damping > 6 || (format != 420 && format != 422 && format != 444))
+        return -1;
+    int bw = w / 8, bh = h / 8;
+    uint8_t *dir = (uint8_t *)malloc((size_t)bw * bh);
+    int32_t *var = (int32_t *)malloc((size_t)bw * bh * sizeof(int32_t));
+    if (!dir || !var) {
+        free(dir);
+        free(var);
+        return -1;
+    }
+    cdef_ref_find_dir(ry, w, h, rys, bitdepth, dir, var);
+    int cw = format == 444 ? w : w / 2, ch = format == 420 ? h / 2 : h;
+    int csub = format == 444 ? 0 : 1;
+    int cfw = format == 444 ? 64 : 32, cfh = format == 420 ? 32 : 64;
+    int cfilt = format != 422;
+    int fb_cols = (w + 63) / 64, fb_rows = (h + 63) / 64;
+    for (int fby = 0; fby < fb_rows; fby++) {
+        for (int fbx = 0; fbx < fb_cols; fbx++) {
+            int b = fby * fb_cols + fbx;
+            int fb_coded = fb_has_coded(coded, bw, bh, fby, fbx);
+            skipped[b] = (uint8_t)!fb_coded;
+            for (int k = 0; k < 2; k++) {
+                for (int p = 0; p < 16; p++) {
+                    for (int s = 0; s < 4; s++) {
+                        int q = k * 64 + p * 4 + s;
+                        int pri = p, sec = sec_values[s];
+                        if (k && p == 0 && s == 0) {
+                            pri = 19;
+                            sec = 7;
+                        }
+                        dist_luma[b * 128 + q] = block_eq14_coded_g(
+                            ry, rys, sy, sys, w, h, 0, 0, 1, bitdepth, fby, fbx, pri, sec, k,
+                            damping, dir, var, bw, 64, 64, coded, fb_coded);
+                        dist_chroma[b * 128 + q] =
+                            block_eq14_coded_g(ru, rus, su, sus, cw, ch, csub, 1, cfilt, bitdepth,
+                                               fby, fbx, pri, sec, k, damping, dir, var, bw, cfw,
+                                               cfh, coded, fb_coded) +
+                            block_eq14_coded_g(rv, rvs, sv, svs, cw, ch, csub, 1, cfilt, bitdepth,
+                                               fby, fbx, pri, sec, k, damping, dir, var, bw, cfw,
+                                               cfh, coded, fb_coded);
+                    }
+                }
+            }
+        }
+    }
+    free(dir);
+    free(var);
+    return 0;
+}
+
 /* The eq. 14 value of one 8x8 block from its sums (R22-R24), exported for
  * the pins. */
 int64_t cdef_ref_eq14_term(int64_t n, int64_t s1s, int64_t s2s, int64_t s1d, int64_t s2d,

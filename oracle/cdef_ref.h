@@ -230,6 +230,30 @@ int cdef_ref_distortion_eq14(int w, int h, int bitdepth, int damping,
                              const uint16_t *sv, ptrdiff_t svs,
                              int64_t *dist_luma, int64_t *dist_chroma);
 
+/* Eq. 14 tables for chroma format 420, 422 or 444 at any bit depth
+ * (readings R22-R25); 4:2:2 chroma entries are the unfiltered value. */
+int cdef_ref_distortion_eq14_format(int w, int h, int bitdepth, int damping, int format,
+                                    const uint16_t *ry, ptrdiff_t rys,
+                                    const uint16_t *ru, ptrdiff_t rus,
+                                    const uint16_t *rv, ptrdiff_t rvs,
+                                    const uint16_t *sy, ptrdiff_t sys,
+                                    const uint16_t *su, ptrdiff_t sus,
+                                    const uint16_t *sv, ptrdiff_t svs,
+                                    int64_t *dist_luma, int64_t *dist_chroma);
+
+/* Eq. 14 tables of the 128 combinations with section 4's skip semantics for
+ * chroma format 420, 422 or 444 (readings R21-R25): layout and skipped flags
+ * as cdef_ref_distortion_coded_format. */
+int cdef_ref_distortion_eq14_coded_format(int w, int h, int bitdepth, int damping, int format,
+                                          const uint16_t *ry, ptrdiff_t rys,
+                                          const uint16_t *ru, ptrdiff_t rus,
+                                          const uint16_t *rv, ptrdiff_t rvs,
+                                          const uint16_t *sy, ptrdiff_t sys,
+                                          const uint16_t *su, ptrdiff_t sus,
+                                          const uint16_t *sv, ptrdiff_t svs,
+                                          const uint8_t *coded, int64_t *dist_luma,
+                                          int64_t *dist_chroma, uint8_t *skipped);
+
 /* round(256 * D_8x8) of eq. 14 from one 8x8 block's sums over its n
  * in-frame samples: source sum and sum of squares, filtered sum and sum of
  * squares, squared error. */

@@ -126,6 +126,12 @@ def lib():
         L.cdef_ref_distortion_eq14.argtypes = (
             [C.c_int, C.c_int, C.c_int, C.c_int] + [_u16p, C.c_ssize_t] * 6 + [_i64p, _i64p])
         L.cdef_ref_distortion_eq14.restype = C.c_int
+        L.cdef_ref_distortion_eq14_format.argtypes = (
+            [C.c_int] * 5 + [_u16p, C.c_ssize_t] * 6 + [_i64p, _i64p])
+        L.cdef_ref_distortion_eq14_format.restype = C.c_int
+        L.cdef_ref_distortion_eq14_coded_format.argtypes = (
+            [C.c_int] * 5 + [_u16p, C.c_ssize_t] * 6 + [C.c_void_p, _i64p, _i64p, _u8p])
+        L.cdef_ref_distortion_eq14_coded_format.restype = C.c_int
         L.cdef_ref_eq14_term.argtypes = [C.c_int64] * 6 + [C.c_int]
         L.cdef_ref_eq14_term.restype = C.c_int64
         _lib = L
@@ -458,6 +464,42 @@ def distortion_eq14(rec, src, bitdepth: int, damping: int):
     if rc != 0:
         raise ValueError("oracle rejected distortion_eq14 arguments")
     return dl.reshape(nb, 64), dc.reshape(nb, 64)
+
+
+def distortion_eq14_format(rec, src, bitdepth: int, damping: int, fmt: int):
+    """Eq. 14 tables for chroma format 420, 422 or 444 (readings R22-R25)."""
+    ry, ru, rv = (_u16(p) for p in rec)
+    sy, su, sv = (_u16(p) for p in src)
+    h, w = ry.shape
+    nb = ((h + 63) // 64) * ((w + 63) // 64)
+    dl = np.zeros(nb * 64, np.int64)
+    dc = np.zeros(nb * 64, np.int64)
+    rc = lib().cdef_ref_distortion_eq14_format(
+        w, h, bitdepth, damping, fmt, ry, w, ru, ru.shape[1], rv, rv.shape[1],
+        sy, w, su, su.shape[1], sv, sv.shape[1], dl, dc)
+    if rc != 0:
+        raise ValueError("oracle rejected distortion_eq14_format arguments")
+    return dl.reshape(nb, 64), dc.reshape(nb, 64)
+
+
+def distortion_eq14_coded_format(rec, src, bitdepth: int, damping: int, fmt: int, coded=None):
+    """Eq. 14 tables of the 128 combinations (readings R21-R25): per filter
+    block 128 luma and 128 chroma entries and a skipped flag."""
+    ry, ru, rv = (_u16(p) for p in rec)
+    sy, su, sv = (_u16(p) for p in src)
+    h, w = ry.shape
+    nb = ((h + 63) // 64) * ((w + 63) // 64)
+    cod = None if coded is None else np.ascontiguousarray(coded, dtype=np.uint8)
+    dl = np.zeros(nb * 128, np.int64)
+    dc = np.zeros(nb * 128, np.int64)
+    sk = np.zeros(nb, np.uint8)
+    rc = lib().cdef_ref_distortion_eq14_coded_format(
+        w, h, bitdepth, damping, fmt, ry, w, ru, ru.shape[1], rv, rv.shape[1],
+        sy, w, su, su.shape[1], sv, sv.shape[1], None if cod is None else cod.ctypes.data,
+        dl, dc, sk)
+    if rc != 0:
+        raise ValueError("oracle rejected distortion_eq14_coded_format arguments")
+    return dl.reshape(nb, 128), dc.reshape(nb, 128), sk
 
 
 def eq14_term(n, s1s, s2s, s1d, s2d, sse, bitdepth: int) -> int:

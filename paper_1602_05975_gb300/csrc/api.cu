@@ -747,7 +747,8 @@ int fill_search_batch(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cde
     bool wide = false;
     for (int i = 0; i < n; i++)
         if (rec[i].bitdepth > 10 || chroma_format(&rec[i]) != 420) wide = true;
-    if (wide && ctx->metric == CDEF_METRIC_EQ14) return CDEF_ERR_ARG;
+    // the 128-combination eq. 14 tables are formed by the 32-bit path
+    if (coded && ctx->metric == CDEF_METRIC_EQ14) wide = true;
     int total = 0, rc = CDEF_OK;
     size_t maps = 0;
     for (int i = 0; i < n && rc == CDEF_OK; i++) {
@@ -853,9 +854,9 @@ int search_impl(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cdef_fram
         }
         wide_dirs = ctx->smaps_dir;
         wide_vars = ctx->smaps_var;
-        tune = {1, 1};   // one CTA per filter block and plane group
+        // one CTA per filter block and plane group; groups 8: eq. 14
+        tune = {ctx->metric == CDEF_METRIC_EQ14 ? 8 : 1, 1};
     } else if (ctx->metric == CDEF_METRIC_EQ14) {
-        if (coded) { delete b; return CDEF_ERR_ARG; }
         tune = {8, 2};   // the eq. 14 tables: 8 candidates per work unit
     } else if ((rc = choose_search_tune(ctx, *b, dl, dc, cur, tot, block_ids, skipped, s, &tune))) {
         delete b;
@@ -979,7 +980,6 @@ int cdef_search_tables(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cd
         !dist_chroma || n <= 0 || n > kMaxBatch)
         return CDEF_ERR_ARG;
     if ((coded == nullptr) != (skipped == nullptr)) return CDEF_ERR_ARG;
-    if (coded && ctx->metric == CDEF_METRIC_EQ14) return CDEF_ERR_ARG;
     SearchBatch *b = new (std::nothrow) SearchBatch();
     if (!b) return CDEF_ERR_NOMEM;
     bool wide = false;
@@ -1000,7 +1000,7 @@ int cdef_search_tables(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cd
         }
         wide_dirs = ctx->smaps_dir;
         wide_vars = ctx->smaps_var;
-        tune = {1, 1};
+        tune = {ctx->metric == CDEF_METRIC_EQ14 ? 8 : 1, 1};
     } else if (ctx->metric == CDEF_METRIC_EQ14) {
         tune = {8, 2};
     } else {

@@ -185,10 +185,11 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
 // per sample): the direction maps of every frame into `dirs` / `vars` (at
 // each frame's map_start), then one CTA per filter block and plane group.
 // `skipped` non-null: the 128-combination tables over each frame's coded
-// map (one flag per filter block written); null: 64 combinations.
+// map (one flag per filter block written); null: 64 combinations.  `eq14`:
+// section 5's eq. 14 tables instead of the squared error (64 combinations).
 cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *vars,
                                long long *dist_luma, long long *dist_chroma, uint8_t *skipped,
-                               cudaStream_t s);
+                               cudaStream_t s, bool eq14 = false);
 // The preset selection (greedy, then up to `refine_passes` re-optimisation
 // passes), one cluster of 8 CTAs per frame (no grid-wide barrier);
 // preset_cluster_fits: every frame's blocks fit the kernel's per-CTA state.

@@ -293,6 +293,20 @@ def test_adjust_strength(ref):
             sorted(ref.adjust_strength(S, v) for S in range(16))
 
 
+def test_adjust_strength_rounds_to_nearest(ref):
+    """Eq. 13 prints floor((S (4 + i) + 8) / 16): the strength scaled by
+    (4 + i) / 16, rounded to the nearest integer with halves up, where
+    i = min(floor(log2 floor(v / 2^16)), 12) (reading R3: 0 below 2^16).
+    Checked for every i and S against exact fractions."""
+    from fractions import Fraction
+    for i in range(13):
+        v = 1024 if i == 0 else (1 << 16) << i          # floor(log2(v / 2^16)) = i
+        for S in range(16):
+            exact = Fraction(S * (4 + i), 16)
+            want = int(exact + Fraction(1, 2))          # floor(x + 1/2): nearest, halves up
+            assert ref.adjust_strength(S, v) == want, (S, i)
+
+
 def test_chroma_damping_example(ref):
     g = GOLDEN["chroma_damping_example"]
     e = ref.block_params(g["chroma_primary"], 0, g["luma_damping"], True, 8)
@@ -491,15 +505,42 @@ def test_output_within_neighbourhood_range(ref):
                 assert nb.min() <= oy[i, j] <= nb.max()
 
 
+# Readings R8 and R9 typed here from their statement, independently of the
+# oracle's tables: the primary taps at distance 1 and 2 along direction d
+# (row, column offsets, each used with both signs), primary weights (near,
+# far) = (4, 2) for an even and (3, 3) for an odd strength, secondary taps
+# the primary taps of d + 2 and d - 2 with weights (2, 1).
+_R8_TAPS = {0: ((-1, 1), (-2, 2)), 1: ((0, 1), (-1, 2)), 2: ((0, 1), (0, 2)),
+            3: ((0, 1), (1, 2)), 4: ((1, 1), (2, 2)), 5: ((1, 0), (2, 1)),
+            6: ((1, 0), (2, 0)), 7: ((1, 0), (2, -1))}
+
+
+def _reading_weights(d, kind, parity):
+    """{(dr, dc): weight} of the primary (kind 0) or secondary (kind 1) taps
+    of direction d under readings R8/R9."""
+    if kind == 0:
+        dirs, (wn, wf) = (d,), ((4, 2) if parity == 0 else (3, 3))
+    else:
+        dirs, (wn, wf) = ((d + 2) % 8, (d + 6) % 8), (2, 1)
+    out = {}
+    for dd in dirs:
+        (nr, nc), (fr, fc) = _R8_TAPS[dd]
+        for sg in (1, -1):
+            out[(sg * nr, sg * nc)] = wn
+            out[(sg * fr, sg * fc)] = wf
+    return out
+
+
 def _py_filter_frame(ref, y, u, v, bd, prm):
     """An independent frame-level evaluator written from the paper in
-    Python: tap weights probed per direction, eq. 7 from its text, the
-    block/plane plumbing of sections 2-4 re-derived here."""
+    Python: the taps and weights of readings R8/R9 typed above, eq. 7 from
+    its text, the block/plane plumbing of sections 2-4 re-derived here (the
+    oracle supplies only the directions, pinned separately)."""
     wmap = {}
     for d in range(8):
-        wmap[(d, 0, 0)] = _probe_weights(ref, d, 14, 0)
-        wmap[(d, 0, 1)] = _probe_weights(ref, d, 15, 0)
-        wmap[(d, 1, 0)] = _probe_weights(ref, d, 0, 4)
+        wmap[(d, 0, 0)] = _reading_weights(d, 0, 0)
+        wmap[(d, 0, 1)] = _reading_weights(d, 0, 1)
+        wmap[(d, 1, 0)] = _reading_weights(d, 1, 0)
 
     def f(diff, S, D):
         if S == 0:
@@ -1291,3 +1332,103 @@ def test_periodic_frame_tables_by_class(ref):
             o = ref.select_presets_general(dl, dc, 128, sk, c["lam"])
             assert list(o["presets"]) == list(c["exp"]["presets"])
             assert np.array_equal(o["block_ids"], c["exp"]["block_ids"])
+
+
+def test_eq14_format_tables_for_420_equal_the_420_oracle(ref):
+    """The format-aware eq. 14 tables reduce to the 4:2:0 ones (8 and 12
+    bits, a chroma plane with edge-cut 8x8 blocks)."""
+    from paper_1602_05975_gb300 import synth
+    for bd, (w, h) in ((8, (136, 72)), (12, (72, 40))):
+        f = synth.make_frame(w, h, bd, 32, seed=72 + bd)
+        a = ref.distortion_eq14(f.rec, f.src, bd, 4)
+        b = ref.distortion_eq14_format(f.rec, f.src, bd, 4, 420)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("fmt,bd", [(444, 8), (422, 10), (444, 12)])
+def test_eq14_format_tables_from_decoder_output(ref, fmt, bd):
+    """Each entry of the 4:2:2 / 4:4:4 eq. 14 tables is the sum over the 8x8
+    blocks of each plane (the plane's own grid, edge-cut blocks included) of
+    eq. 14 on the filter oracle's output for that pair (reading R25: 4:2:2
+    chroma unfiltered, 4:4:4 chroma filtered in 8x8 blocks with the chroma
+    strengths)."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(136, 72, bd, 32, seed=73, chroma=fmt)
+    dl, dc = ref.distortion_eq14_format(f.rec, f.src, bd, 5, fmt)
+    params = np.zeros(f.params.shape, np.uint8)
+    params[..., 4] = 5
+    fr, fc = f.params.shape[:2]
+    for q in (0, 6, 37, 63):
+        p, s = q >> 2, (0, 1, 2, 4)[q & 3]
+        params[..., 0] = params[..., 2] = p
+        params[..., 1] = params[..., 3] = s
+        out = ref.filter_frame_format(*f.rec, bd, params, fmt)
+        for pl, tab in ((0, dl), (1, dc)):
+            planes = (0,) if pl == 0 else (1, 2)
+            h, w = out[planes[0]].shape
+            fh, fw = -(-h // fr), -(-w // fc)          # the filter block in this plane
+            fh, fw = (64 if fh > 32 else 32), (64 if fw > 32 else 32)
+            for b in range(tab.shape[0]):
+                by, bx = divmod(b, fc)
+                tot = 0
+                for k in planes:
+                    for y in range(by * fh, min((by + 1) * fh, h), 8):
+                        for x in range(bx * fw, min((bx + 1) * fw, w), 8):
+                            tot += ref.eq14_term(*_sums(f.src[k][y:y + 8, x:x + 8],
+                                                        out[k][y:y + 8, x:x + 8]), bd)
+                assert tab[b, q] == tot, (fmt, bd, q, pl, b)
+
+
+@pytest.mark.parametrize("fmt,bd", [(420, 8), (444, 10), (422, 12)])
+def test_eq14_coded_tables_from_decoder_output(ref, fmt, bd):
+    """Each entry of the 128-combination eq. 14 tables (reading R21 with
+    R22-R25) is the sum over the 8x8 blocks of each plane of eq. 14 on what
+    the filter oracle outputs for that preset with the coded-residual map:
+    skip bit clear leaves uncoded blocks unfiltered, (0, 0) with the bit set
+    is (19, 7), a filter block without coded residual is never filtered."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(136, 72, bd, 32, seed=74, chroma=fmt)
+    rng = np.random.default_rng(75)
+    coded = (rng.random((9, 17)) < 0.5).astype(np.uint8)
+    coded[:, 8:16] = 0                       # filter block (0, 1) without residual
+    dl, dc, sk = ref.distortion_eq14_coded_format(f.rec, f.src, bd, 5, fmt, coded)
+    assert sk.tolist() == [int(not coded[by * 8:by * 8 + 8, bx * 8:bx * 8 + 8].any())
+                           for by in range(2) for bx in range(3)]
+    assert sk[1] == 1 and sk[0] == 0
+    fr, fc = f.params.shape[:2]
+    params = np.zeros(f.params.shape, np.uint8)
+    params[..., 4] = 5
+    for q in (0, 64, 6, 70, 101):
+        k, p, s = q >> 6, (q & 63) >> 2, (0, 1, 2, 4)[q & 3]
+        params[..., 0] = params[..., 2] = p
+        params[..., 1] = params[..., 3] = s
+        params[..., 5] = 3 * k                 # the skip-condition bits of both groups
+        out = ref.filter_frame_format(*f.rec, bd, params, fmt, coded=coded)
+        for pl, tab in ((0, dl), (1, dc)):
+            planes = (0,) if pl == 0 else (1, 2)
+            h, w = out[planes[0]].shape
+            fh = 64 if -(-h // fr) > 32 else 32
+            fw = 64 if -(-w // fc) > 32 else 32
+            for b in range(tab.shape[0]):
+                by, bx = divmod(b, fc)
+                tot = 0
+                for kk in planes:
+                    for y in range(by * fh, min((by + 1) * fh, h), 8):
+                        for x in range(bx * fw, min((bx + 1) * fw, w), 8):
+                            tot += ref.eq14_term(*_sums(f.src[kk][y:y + 8, x:x + 8],
+                                                        out[kk][y:y + 8, x:x + 8]), bd)
+                assert tab[b, q] == tot, (fmt, bd, q, pl, b)
+
+
+def test_eq14_coded_tables_all_coded_reduce_to_64(ref):
+    """With every 8x8 block coded, both skip-bit halves equal the 64-pair
+    eq. 14 tables, except the (0, 0) slot with the bit set ((19, 7))."""
+    from paper_1602_05975_gb300 import synth
+    f = synth.make_frame(136, 72, 10, 32, seed=76)
+    dl, dc, sk = ref.distortion_eq14_coded_format(f.rec, f.src, 10, 4, 420,
+                                                  np.ones((9, 17), np.uint8))
+    el, ec = ref.distortion_eq14_format(f.rec, f.src, 10, 4, 420)
+    assert not sk.any()
+    for t, e in ((dl, el), (dc, ec)):
+        assert np.array_equal(t[:, :64], e)
+        assert np.array_equal(t[:, 65:], e[:, 1:])
