@@ -317,7 +317,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": walls / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "sample": "bounded oracle sample"},
+        "config": {"workload": WORKLOAD["name"], "sample": "bounded oracle sample",
+                   "inputs_sha256": synth.digest_of(frames)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -348,6 +349,8 @@ def run_ours(args):
 
     frames = make_frames(rank)
     nf = len(frames)
+    from paper_1602_05975_gb300 import synth
+    inputs_sha = synth.digest_of(frames)   # SHA-256 over the frames' digests
     ins = [cdef.frame_from_numpy(f.rec, f.bitdepth, device=dev) for f in frames]
     # two output sets, alternating by step: no two filter calls that may run
     # concurrently (overlapped launches) write the same buffer
@@ -548,6 +551,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD["name"], "frames_per_step": nf,
                        "width": WORKLOAD["width"], "height": WORKLOAD["height"],
                        "bitdepth": WORKLOAD["bitdepth"], "parallelism": f"replicas x{ws}",
+                       "inputs_sha256": inputs_sha,
                        "l2": f"each frame's buffers are touched once per step and "
                              f"{(nf - 1) * algorithmic_bytes_per_frame() / 1e6:.0f} MB of "
                              f"other frames' traffic (L2: 129 MB) passes between two uses"},
@@ -635,7 +639,7 @@ def run_search(args):
         from oracle import ref
         ref.build()
         pool = mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 16))
-    print(json.dumps(measure_search(args, args.search_variant, steps, warmup, pool)))
+    print(json.dumps(measure_search(args, args.search_variant, args.steps, args.warmup, pool)))
 
 
 def measure_search(args, variant, steps, warmup, pool=None):
@@ -788,6 +792,7 @@ def measure_search(args, variant, steps, warmup, pool=None):
         "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": {"workload": SEARCH_WORKLOAD["name"], "blocks": nb,
+                                        "inputs_sha256": synth.digest_of(frames),
                                         "luma_pixels": sum(f.width * f.height for f in frames),
                                         "l2": "L2 flushed (256 MB write) before each call"},
         "tuning": dict(zip(("search_groups", "search_ctas_per_sm"), tune)),

@@ -25,6 +25,7 @@ Everything is drawn from numpy's PCG64 seeded by the caller.
 """
 from __future__ import annotations
 
+import hashlib
 from dataclasses import dataclass
 
 import numpy as np
@@ -168,3 +169,24 @@ def workload_frames(name: str, base_seed: int, nframes=None):
         out.append(make_frame(cfg["width"], cfg["height"], cfg["bitdepth"], q,
                               base_seed + f))
     return out
+
+
+def frame_digest(f: Frame) -> str:
+    """SHA-256 of a synthetic frame: its geometry, bit depth and quantiser,
+    the source and decoded planes (as little-endian uint16) and the
+    parameters.  Recorded per workload (tests/golden/synth_manifest.json) so
+    that a change of the input recipe does not go unnoticed, and printed by
+    the benchmark so that two runs can be seen to use the same inputs."""
+    h = hashlib.sha256()
+    h.update(np.array([f.width, f.height, f.bitdepth, f.q], dtype="<i8").tobytes())
+    for p in tuple(f.src) + tuple(f.rec):
+        a = np.ascontiguousarray(p, dtype="<u2")
+        h.update(np.array(a.shape, dtype="<i8").tobytes())
+        h.update(a.tobytes())
+    h.update(np.ascontiguousarray(f.params, dtype=np.uint8).tobytes())
+    return h.hexdigest()
+
+
+def digest_of(frames) -> str:
+    """One SHA-256 over the digests of a list of frames."""
+    return hashlib.sha256("".join(frame_digest(f) for f in frames).encode()).hexdigest()
