@@ -70,7 +70,7 @@ def ncu_traffic(kernel: str):
     e = d.get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e
 
 
 # ------------------------------------------------------------------ workload
@@ -495,12 +495,13 @@ def run_ours(args):
     ops_b = algorithmic_ops_per_frame()
     bytes_b = algorithmic_bytes_per_frame()
     peak_ops = alu_peak_gops(WORKLOAD["bitdepth"])
+    traffic = ncu_traffic("filter_kernel") if WORKLOAD is FILTER_WORKLOADS["filter"] else None
     ops = ops_b / (launch_ms * 1e-3) / 1e9
     achieved = bytes_b / (launch_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": ops, "peak": peak_ops, "unit": "Gop/s",
                 "frac": ops / peak_ops,
-                "traffic": ncu_traffic("filter_kernel") if WORKLOAD is FILTER_WORKLOADS["filter"]
-                else None,
+                "traffic": (traffic or {}).get("dram_bytes_per_launch"),
+                "traffic_note": (traffic or {}).get("note"),
                 "kernel": "filter_kernel (fused find_dir + filter)",
                 "ops_per_launch": ops_b,
                 "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz"
