@@ -512,6 +512,21 @@ int cdef_preset_assign(cdef_ctx *ctx, int32_t nblocks, int32_t width, const int6
  * for concurrent use with launches from other host threads. */
 int cdef_debug_set_waits(int64_t wait_cycles, int32_t extra_tx_bytes);
 
+/* Test aid (no paper counterpart): the index checks of the library.  The
+ * library built with CDEF_DEBUG (libcdef_gb300_debug.so) checks every
+ * shared-memory tap load, output staging write and 16-byte row store of
+ * the filter and search kernels against its buffer before it is made; an
+ * access out of range is skipped (nothing faults), sets the context's
+ * status word (cdef_ctx_status -> CDEF_ERR_DEVICE; a search returns it) and
+ * is counted on the device.
+ *   faults : HOST output, the accesses skipped on ctx's device since the
+ *            last clear (always 0 in the release build)
+ *   clear  : nonzero = reset the count after reading it
+ * Waits for all work on the device first.  Returns 1 when the library was
+ * built with the checks, 0 when not, CDEF_ERR_ARG for a NULL argument,
+ * CDEF_ERR_CUDA when the device cannot be read. */
+int cdef_debug_checks(cdef_ctx *ctx, int64_t *faults, int32_t clear);
+
 /* A static description of a status code. */
 const char *cdef_strerror(int status);
 

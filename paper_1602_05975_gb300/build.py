@@ -3,6 +3,13 @@
 Each CUDA translation unit is compiled in parallel, then linked into one
 shared library with the CUDA runtime linked statically, so that loading the
 library needs no GPU and no libcudart on the loader path.
+
+`build(debug=True)` makes libcdef_gb300_debug.so from the same sources with
+CDEF_DEBUG defined: every shared-memory tap load, staging write and 16-byte
+row store of the kernels is checked against its buffer first; an index out
+of range sets a bit of the call's status word (the call then returns
+CDEF_ERR_DEVICE) and the access is skipped.  It is a test build (slower),
+loaded in place of the release library when CDEF_GB300_LIBRARY names it.
 """
 from __future__ import annotations
 
@@ -17,6 +24,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcdef_gb300.so")
+DEBUG_LIB = os.path.join(HERE, "libcdef_gb300_debug.so")
 SOURCES = ["api.cu", "find_dir.cu", "filter.cu", "search.cu", "search_wide.cu", "presets.cu", "shard.cu",
            "presets_cluster.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,15 +45,18 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    lib = DEBUG_LIB if debug else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    objdir = os.path.join(BUILD, "debug") if debug else BUILD
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
+    flags = CFLAGS + (["-DCDEF_DEBUG"] if debug else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc] + CFLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
+        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,14 +68,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs,
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -63,15 +63,23 @@ class Tuning(C.Structure):
 _lib = None
 
 
+def library_path() -> str:
+    """The library load() opens: libcdef_gb300.so next to this file, or the
+    one the CDEF_GB300_LIBRARY environment variable names (e.g. the
+    index-checking build libcdef_gb300_debug.so, made by build(debug=True))."""
+    return os.environ.get("CDEF_GB300_LIBRARY") or LIB_PATH
+
+
 def load():
-    """Load libcdef_gb300.so (built by build()); raises if it is missing."""
+    """Load the CUDA library (built by build()); raises if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"CUDA library {LIB_PATH} is missing; build it with "
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; build it with "
                            "paper_1602_05975_gb300.build.build()")
-    L = C.CDLL(LIB_PATH)
+    L = C.CDLL(path)
     vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
     L.cdef_ctx_create.argtypes = [C.POINTER(vp), C.c_int, C.c_size_t]
     L.cdef_ctx_destroy.argtypes = [vp]
@@ -100,6 +108,7 @@ def load():
         vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc), C.POINTER(vp), C.POINTER(i32),
         C.POINTER(i64), vp, vp, C.POINTER(PresetCoded), C.POINTER(i32), vp, C.POINTER(i64), vp]
     L.cdef_debug_set_waits.argtypes = [i64, i32]
+    L.cdef_debug_checks.argtypes = [vp, C.POINTER(i64), i32]
     L.cdef_search_tables.argtypes = [vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc),
                                      C.POINTER(vp), C.POINTER(i32), C.POINTER(i32),
                                      C.POINTER(i32), vp, vp, vp, vp]
@@ -117,7 +126,8 @@ def load():
                  "cdef_ctx_set_search_refine", "cdef_search_strengths_coded",
                  "cdef_ctx_set_search_metric", "cdef_ctx_set_stage_timing",
                  "cdef_ctx_get_stage_times", "cdef_ctx_set_search_subset",
-                 "cdef_ctx_status_async", "cdef_debug_set_waits", "cdef_search_tables",
+                 "cdef_ctx_status_async", "cdef_debug_set_waits", "cdef_debug_checks",
+                 "cdef_search_tables",
                  "cdef_preset_totals", "cdef_preset_argmin", "cdef_preset_assign"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -549,6 +559,17 @@ def debug_set_waits(wait_cycles: int = 0, extra_tx_bytes: int = 0):
     (so that waits run out); process-wide, for later launches."""
     _check(load().cdef_debug_set_waits(int(wait_cycles), int(extra_tx_bytes)),
            "cdef_debug_set_waits")
+
+
+def debug_checks(ctx, clear: bool = True):
+    """Test aid: (whether the loaded library checks its kernels' indexes,
+    accesses out of range that its kernels skipped on ctx's device since the
+    last clear).  Waits for the device."""
+    n = C.c_int64(0)
+    r = load().cdef_debug_checks(ctx.handle, C.byref(n), 1 if clear else 0)
+    if r < 0:
+        _check(r, "cdef_debug_checks")
+    return bool(r), int(n.value)
 
 
 def version() -> str:

@@ -413,7 +413,7 @@ int cdef_ctx_status(cdef_ctx *ctx, int clear)
         return CDEF_ERR_CUDA;
     if (clear && v && cudaMemset(ctx->status, 0, sizeof(int)) != cudaSuccess) return CDEF_ERR_CUDA;
     if (v & kStatusTimeout) return CDEF_ERR_TIMEOUT;
-    if (v & kStatusMisaligned) return CDEF_ERR_DEVICE;
+    if (v & (kStatusMisaligned | kStatusIndex)) return CDEF_ERR_DEVICE;
     return v ? CDEF_ERR_ARG : CDEF_OK;
 }
 
@@ -1104,6 +1104,28 @@ const char *cdef_strerror(int status)
 }
 
 const char *cdef_version(void) { return "cdef_gb300 0.1 sm_103a"; }
+
+int cdef_debug_checks(cdef_ctx *ctx, int64_t *faults, int32_t clear)
+{
+    if (!ctx || !faults) return CDEF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return CDEF_ERR_CUDA;
+    }
+    unsigned long long n = 0;
+    for (auto reader : {index_faults_filter, index_faults_search, index_faults_search_wide}) {
+        const unsigned long long v = reader(clear != 0);
+        if (v == ~0ull) {
+            cudaGetLastError();
+            return CDEF_ERR_CUDA;
+        }
+        n += v;
+    }
+    *faults = (int64_t)n;
+    return kIndexChecks ? 1 : 0;
+}
 
 int cdef_debug_set_waits(int64_t wait_cycles, int32_t extra_tx_bytes)
 {

@@ -187,9 +187,11 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma,
 // `skipped` non-null: the 128-combination tables over each frame's coded
 // map (one flag per filter block written); null: 64 combinations.  `eq14`:
 // section 5's eq. 14 tables instead of the squared error (64 combinations).
+// `status`: the search's status word (the index-checking build records
+// out-of-range tap loads there).
 cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *vars,
                                long long *dist_luma, long long *dist_chroma, uint8_t *skipped,
-                               cudaStream_t s, bool eq14 = false);
+                               cudaStream_t s, bool eq14, int *status);
 // The preset selection (greedy, then up to `refine_passes` re-optimisation
 // passes), one cluster of 8 CTAs per frame (no grid-wide barrier);
 // preset_cluster_fits: every frame's blocks fit the kernel's per-CTA state.
@@ -253,5 +255,51 @@ int encode_frame_tiles(CUtensorMap maps[3], const cdef_frame *f);
 constexpr int kStatusBadParams = 1;
 constexpr int kStatusTimeout = 2;
 constexpr int kStatusMisaligned = 4;  // internal: shared memory not aligned for tile loads
+constexpr int kStatusIndex = 8;       // index-checking build (CDEF_DEBUG): an access out of
+                                      // its buffer was found and skipped
+
+// Index checks of the CDEF_DEBUG build: CDEF_IN_BOUNDS(i, n, status) is i
+// in [0, n); when it is not, the status word gets kStatusIndex, the
+// translation unit's fault counter is incremented and the caller skips the
+// access.  Without CDEF_DEBUG the check is compiled out (always true).
+// CDEF_FAULT_COUNTER(name) defines `unsigned long long name(bool clear)`,
+// the host reader of the counter of the translation unit it is placed in
+// (always 0 without CDEF_DEBUG).
+#ifdef CDEF_DEBUG
+static __device__ unsigned long long g_index_faults;   // one per translation unit
+
+__device__ __noinline__ static void note_index_fault(int *status)
+{
+    atomicOr(status, kStatusIndex);
+    atomicAdd(&g_index_faults, 1ull);
+}
+
+#define CDEF_IN_BOUNDS(i, n, status) \
+    (((long long)(i) >= 0 && (long long)(i) < (long long)(n)) ? true : (note_index_fault(status), false))
+#define CDEF_DEBUG_PARAM(decl) , decl
+#define CDEF_DEBUG_ARG(name) , name
+#define CDEF_FAULT_COUNTER(name)                                                       \
+    unsigned long long name(bool clear)                                                 \
+    {                                                                                   \
+        unsigned long long v = 0, zero = 0;                                             \
+        if (cudaMemcpyFromSymbol(&v, g_index_faults, sizeof(v)) != cudaSuccess) return ~0ull; \
+        if (clear && v) cudaMemcpyToSymbol(g_index_faults, &zero, sizeof(zero));        \
+        return v;                                                                       \
+    }
+constexpr bool kIndexChecks = true;
+#else
+#define CDEF_IN_BOUNDS(i, n, status) true
+// release build: the status word is not threaded through device helpers,
+// so their register allocation is the same as without the checks
+#define CDEF_DEBUG_PARAM(decl)
+#define CDEF_DEBUG_ARG(name)
+#define CDEF_FAULT_COUNTER(name) \
+    unsigned long long name(bool) { return 0; }
+constexpr bool kIndexChecks = false;
+#endif
+// the counters of the translation units with checked accesses
+unsigned long long index_faults_filter(bool clear);
+unsigned long long index_faults_search(bool clear);
+unsigned long long index_faults_search_wide(bool clear);
 
 }  // namespace cdefgb

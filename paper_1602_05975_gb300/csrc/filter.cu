@@ -179,8 +179,10 @@ struct StageOut {
     }
 
     // the staged group out to the frame; the staging is free again after it
-    __device__ __forceinline__ void flush(const FilterFrameDev &F, const uint8_t *st8, int lane)
+    __device__ __forceinline__ void flush(const FilterFrameDev &F, const uint8_t *st8, int lane,
+                                          int *status)
     {
+        (void)status;   // used by the index-checking build
         constexpr int nblk = kLuma ? (kBytes == 2 ? 1 : 2) : (kBytes == 2 ? 2 : 4);
         __syncwarp();
         if (n) {
@@ -193,8 +195,15 @@ struct StageOut {
             const bool v_plane = !kLuma && (kBytes == 2 ? lane >= 16 : ((lane >> 3) & 1));
             uint8_t *dst = (kLuma ? F.p[0].out : v_plane ? F.p[2].out : F.p[1].out) + off;
             const int64_t pitch = kLuma ? F.p[0].out_pitch : v_plane ? F.p[2].out_pitch : F.p[1].out_pitch;
-            const uint4 q = *reinterpret_cast<const uint4 *>(st8 + so);
-            if (n == nblk) {
+            // the segment's last byte inside the plane's rows
+            const int ph = kLuma ? F.p[0].h : v_plane ? F.p[2].h : F.p[1].h;
+            const bool ok = CDEF_IN_BOUNDS((int64_t)off + 15, pitch * ph, status) &&
+                            CDEF_IN_BOUNDS(so + 15, 512, status);
+            (void)ph;
+            const uint4 q = ok ? *reinterpret_cast<const uint4 *>(st8 + so) : make_uint4(0, 0, 0, 0);
+            if (!ok) {
+                // (index-checking build) the access is skipped
+            } else if (n == nblk) {
                 *reinterpret_cast<uint4 *>(dst) = q;
             } else if (kBytes == 2 || kLuma) {   // one of two 8-byte blocks
                 *reinterpret_cast<uint2 *>(dst) = make_uint2(q.x, q.y);
@@ -237,7 +246,7 @@ __device__ __forceinline__ int filter_sample_wide(int x, const int p[12], const 
 // task 1 chroma (U, V) rows of 4x4 blocks), both samples of a word in turn.
 __device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int fbx,
                                          const cdef_fb_params &prm, bool any_coded, bool skip_l,
-                                         bool skip_c, FilterSmem &sm)
+                                         bool skip_c, FilterSmem &sm, int *status)
 {
     const int sh8 = F.bitdepth - 8;
     const int H = F.p[0].h, W = F.p[0].w, CH = F.p[1].h, CW = F.p[1].w;
@@ -263,6 +272,11 @@ __device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int f
                                     : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
         const int *o = sm.off[task][sm.dir[blk]];
         uint8_t *st8 = reinterpret_cast<uint8_t *>(sm.stage[warp]);
+        // the re-laid tile the taps read (luma: even and odd copies)
+        const uint32_t *tile0 = luma ? sm.t.le : sm.t.cw;
+        const int tile_words = luma ? 2 * kLumaRows * kLumaPitch : kChromaRows * kChromaPitch;
+        (void)tile0;
+        (void)tile_words;
         auto run = [&](auto luma_c) {
             using Out = StageOut<decltype(luma_c)::value, 2>;
             Out out(F, lane, fby, fbx, warp, row_in);
@@ -272,7 +286,8 @@ __device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int f
                     const uint32_t X = b[0];
                     uint32_t v[12];
 #pragma unroll
-                    for (int k = 0; k < 12; k++) v[k] = b[o[k]];
+                    for (int k = 0; k < 12; k++)
+                        v[k] = CDEF_IN_BOUNDS(b + o[k] - tile0, tile_words, status) ? b[o[k]] : X;
                     int y[2];
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
@@ -283,7 +298,7 @@ __device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int f
                     }
                     Out::put(st8, lane, i, (uint32_t)y[0] | ((uint32_t)y[1] << 16));
                 }
-                out.flush(F, st8, lane);
+                out.flush(F, st8, lane, status);
             }
         };
         if (luma) run(std::true_type{});
@@ -386,7 +401,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
 
     const int warp = tid >> 5, lane = tid & 31;
     if (F.bitdepth > 10) {
-        filter_wide(F, fby, fbx, prm, any_coded, skip_l, skip_c, sm);
+        filter_wide(F, fby, fbx, prm, any_coded, skip_l, skip_c, sm, status);
         return;
     }
 
@@ -423,6 +438,10 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         const bool row_in = luma ? gby * 8 < H : gby * 4 < CH;
         using Out = StageOut<luma, sizeof(T)>;
         Out out(F, lane, fby, fbx, warp, row_in);
+        // the re-laid tile the taps read (luma: even and odd copies)
+        const uint32_t *tile0 = luma ? sm.t.le : sm.t.cw;
+        constexpr int tile_words = luma ? 2 * kLumaRows * kLumaPitch : kChromaRows * kChromaPitch;
+        (void)tile0;
         uint8_t *st8 = reinterpret_cast<uint8_t *>(sm.stage[warp]);
         const uint32_t *b = base;
 #pragma unroll 1
@@ -432,11 +451,12 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
                 const uint32_t X = b[0];
                 uint32_t v[12];
 #pragma unroll
-                for (int k = 0; k < 12; k++) v[k] = b[o[k]];
+                for (int k = 0; k < 12; k++)
+                    v[k] = CDEF_IN_BOUNDS(b + o[k] - tile0, tile_words, status) ? b[o[k]] : X;
                 Out::put(st8, lane, i, filter_word(X, v, bc, any_p, any_s, any_clip, any_edge) -
                                            kBias * kLanes);
             }
-            out.flush(F, st8, lane);
+            out.flush(F, st8, lane, status);
         }
     };
     task_body(std::true_type{});
@@ -609,5 +629,7 @@ cudaError_t launch_filter_planes(const FilterBatch<3> &b, int *status, unsigned 
 {
     return launch_pdl<3>(b, status, work, overlap, s);
 }
+
+CDEF_FAULT_COUNTER(index_faults_filter)
 
 }  // namespace cdefgb

@@ -203,7 +203,7 @@ __device__ __forceinline__ int wentry(int N, int lane)
 template <typename T, int kG, bool kCoded, bool kEq14, bool kSub>
 __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global, int grp,
                            SearchSmem &sm, const RawTiles &raw, long long *dist_luma,
-                           long long *dist_chroma, uint8_t *skipped)
+                           long long *dist_chroma, uint8_t *skipped CDEF_DEBUG_PARAM(int *status))
 {
     constexpr int kPP = 16 / kG;           // primary strengths per unit
     constexpr int kN = 4 * kPP;            // candidates per plane group
@@ -318,6 +318,11 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
             const int pitch = luma ? kLumaPitch : kChromaPitch;
             const uint32_t *base = luma ? sm.t.le + (2 + warp * 8) * kLumaPitch + 4 + bx * 4 + sub
                                         : sm.t.cw + (2 + warp * 4) * kChromaPitch + 2 + bx * 4 + sub;
+            // the re-laid tile the taps read (luma: even and odd copies)
+            const uint32_t *tile0 = luma ? sm.t.le : sm.t.cw;
+            const int tile_words = luma ? 2 * kLumaRows * kLumaPitch : kChromaRows * kChromaPitch;
+            (void)tile0;
+            (void)tile_words;
             const int4 *op = reinterpret_cast<const int4 *>(sm.off[task][sm.dir[blk]]);
             const int4 o0 = op[0], o1 = op[1], o2 = op[2];
             const int o[12] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w};
@@ -362,7 +367,8 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     const uint32_t X = b[0];
                     uint32_t v[12];
     #pragma unroll
-                    for (int k = 0; k < 12; k++) v[k] = b[o[k]];
+                    for (int k = 0; k < 12; k++)
+                        v[k] = CDEF_IN_BOUNDS(b + o[k] - tile0, tile_words, status) ? b[o[k]] : X;
                     if (any_edge) {
     #pragma unroll
                         for (int k = 0; k < 12; k++) v[k] = in_frame(v[k], X);
@@ -706,11 +712,11 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             if (F.bitdepth == 8)
                 dist_block<uint8_t, kG, kCoded, kEq14, kSub>(F, r.fby, r.fbx, fb, grp, sm,
                                                              sm.raw[buf], dist_luma, dist_chroma,
-                                                             skipped);
+                                                             skipped CDEF_DEBUG_ARG(status));
             else
                 dist_block<uint16_t, kG, kCoded, kEq14, kSub>(F, r.fby, r.fbx, fb, grp, sm,
                                                               sm.raw[buf], dist_luma, dist_chroma,
-                                                              skipped);
+                                                              skipped CDEF_DEBUG_ARG(status));
             __syncthreads();
         }
     }
@@ -842,7 +848,8 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     const int per_sm = tune.ctas_per_sm;
     if (wide_dirs) {   // 4:2:2, 4:4:4 or 12-bit frames
         const bool eq14 = tune.groups == 8;   // the eq. 14 tables
-        e = launch_search_wide(b, wide_dirs, wide_vars, dist_luma, dist_chroma, skipped, s, eq14);
+        e = launch_search_wide(b, wide_dirs, wide_vars, dist_luma, dist_chroma, skipped, s, eq14,
+                               status);
         if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
         if (e != cudaSuccess || tables_only) return e;
         const int width = skipped ? 128 : 64;
@@ -870,5 +877,7 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
                        refine_passes, width, skipped, true, grid_presets, s);
     return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
 }
+
+CDEF_FAULT_COUNTER(index_faults_search)
 
 }  // namespace cdefgb

@@ -90,7 +90,7 @@ template <bool kCoded>
 __global__ void __launch_bounds__(kWThreads, 2)
 dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__restrict__ dirs,
                  const int32_t *__restrict__ vars, long long *dist_luma, long long *dist_chroma,
-                 uint8_t *skipped)
+                 uint8_t *skipped, int *status)
 {
     __shared__ WideSmem sm;
     __shared__ unsigned long long acc_unc[64], base_sums[4];   // uncoded part; unfiltered, (19, 7)
@@ -202,7 +202,8 @@ dist_wide_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__res
                 int pv[12], mn = x, mx = x;
 #pragma unroll
                 for (int m = 0; m < 12; m++) {
-                    const int pm = t[o[m]];
+                    const int pm = CDEF_IN_BOUNDS(t + o[m] - &sm.tile[k][0], kTile * kTile, status)
+                                       ? t[o[m]] : -1;
                     pv[m] = pm < 0 ? x : pm;   // outside the frame: adds nothing
                     mn = min(mn, pv[m]);
                     mx = max(mx, pv[m]);
@@ -336,7 +337,7 @@ template <int kGroup, bool kCoded>
 __device__ __forceinline__ void wide_eq14_body(const SearchBatch &batch, const uint8_t *dirs,
                                                const int32_t *vars, long long *dist_luma,
                                                long long *dist_chroma, uint8_t *skipped,
-                                               WideEq14Smem &sm)
+                                               WideEq14Smem &sm, int *status)
 {
     constexpr bool chroma = kGroup != 0;
     constexpr int nplanes = chroma ? 2 : 1;
@@ -476,7 +477,8 @@ __device__ __forceinline__ void wide_eq14_body(const SearchBatch &batch, const u
                     int pv[12], mn = x, mx = x;
 #pragma unroll
                     for (int m = 0; m < 12; m++) {
-                        const int pm = t[o[m]];
+                        const int pm = CDEF_IN_BOUNDS(t + o[m] - &sm.tile[k][0], kTile * kTile, status)
+                                           ? t[o[m]] : -1;
                         pv[m] = pm < 0 ? x : pm;   // outside the frame: adds nothing
                         mn = min(mn, pv[m]);
                         mx = max(mx, pv[m]);
@@ -606,21 +608,21 @@ template <bool kCoded>
 __global__ void __launch_bounds__(kWThreads, 2)
 dist_wide_eq14_kernel(const __grid_constant__ SearchBatch batch, const uint8_t *__restrict__ dirs,
                       const int32_t *__restrict__ vars, long long *dist_luma, long long *dist_chroma,
-                      uint8_t *skipped)
+                      uint8_t *skipped, int *status)
 {
     extern __shared__ __align__(16) uint8_t wsm_bytes[];
     WideEq14Smem &sm = *reinterpret_cast<WideEq14Smem *>(wsm_bytes);
     if (blockIdx.y == 0)
-        wide_eq14_body<0, kCoded>(batch, dirs, vars, dist_luma, dist_chroma, skipped, sm);
+        wide_eq14_body<0, kCoded>(batch, dirs, vars, dist_luma, dist_chroma, skipped, sm, status);
     else
-        wide_eq14_body<1, kCoded>(batch, dirs, vars, dist_luma, dist_chroma, skipped, sm);
+        wide_eq14_body<1, kCoded>(batch, dirs, vars, dist_luma, dist_chroma, skipped, sm, status);
 }
 
 }  // namespace
 
 cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *vars,
                                long long *dist_luma, long long *dist_chroma, uint8_t *skipped,
-                               cudaStream_t s, bool eq14)
+                               cudaStream_t s, bool eq14, int *status)
 {
     for (int i = 0; i < b.n; i++) {
         const SearchFrameDev &F = b.f[i];
@@ -641,17 +643,19 @@ cudaError_t launch_search_wide(const SearchBatch &b, uint8_t *dirs, int32_t *var
         }
         if (skipped)
             dist_wide_eq14_kernel<true><<<dim3(b.total_blocks, 2), kWThreads, sizeof(WideEq14Smem), s>>>(
-                b, dirs, vars, dist_luma, dist_chroma, skipped);
+                b, dirs, vars, dist_luma, dist_chroma, skipped, status);
         else
             dist_wide_eq14_kernel<false><<<dim3(b.total_blocks, 2), kWThreads, sizeof(WideEq14Smem), s>>>(
-                b, dirs, vars, dist_luma, dist_chroma, nullptr);
+                b, dirs, vars, dist_luma, dist_chroma, nullptr, status);
     } else if (skipped)
         dist_wide_kernel<true><<<dim3(b.total_blocks, 2), kWThreads, 0, s>>>(
-            b, dirs, vars, dist_luma, dist_chroma, skipped);
+            b, dirs, vars, dist_luma, dist_chroma, skipped, status);
     else
         dist_wide_kernel<false><<<dim3(b.total_blocks, 2), kWThreads, 0, s>>>(
-            b, dirs, vars, dist_luma, dist_chroma, nullptr);
+            b, dirs, vars, dist_luma, dist_chroma, nullptr, status);
     return cudaGetLastError();
 }
+
+CDEF_FAULT_COUNTER(index_faults_search_wide)
 
 }  // namespace cdefgb
