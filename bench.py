@@ -854,6 +854,20 @@ def run_serve(args):
                                    W["verify_requests"], min(args.requests or W["requests"], 2000))))
 
 
+def host_settings() -> dict:
+    """Kernel settings of the host that bear on serving-loop stalls (read
+    only): automatic NUMA balancing and transparent huge pages."""
+    out = {}
+    for key, path in (("numa_balancing", "/proc/sys/kernel/numa_balancing"),
+                      ("transparent_hugepage", "/sys/kernel/mm/transparent_hugepage/enabled"),
+                      ("cpus", None)):
+        try:
+            out[key] = os.cpu_count() if path is None else open(path).read().strip()
+        except OSError:
+            out[key] = None
+    return out
+
+
 def measure_serve(args, n, rate_fracs, nv, ncap):
     """The serving measurement (see run_serve) with n requests per arrival
     rate, nv verified requests and ncap requests for the capacities;
@@ -890,10 +904,12 @@ def measure_serve(args, n, rate_fracs, nv, ncap):
                 for i, (w, h, bd, k, prm) in enumerate(specs[:count])]
 
     budget = W["budget"]
-    batched_be = serve.CudaBackend(ctx, budget)
-    single_be = serve.CudaBackend(ctx, budget)
+    timing = bool(getattr(args, "serve_timing", False))
+    batched_be = serve.CudaBackend(ctx, budget, timing=timing)
+    single_be = serve.CudaBackend(ctx, budget, timing=timing)
     shapes = [(w, h, bd) for (w, h) in W["sizes"] for bd in W["bitdepths"]]
-    batched_be.prewarm(shapes, 24)      # up to four batches of each size held
+    # buffers for every burst the budget admits: no allocation while serving
+    batched_be.prewarm(shapes, 24, fill=0.9)
     single_be.prewarm(shapes, 2)
 
     def batched(on_done=None):
@@ -928,7 +944,8 @@ def measure_serve(args, n, rate_fracs, nv, ncap):
     assert mismatches == 0, f"{mismatches} served results differ from the single-frame path"
 
     keys = ("frames_per_s", "mpixel_per_s", "p50_ms", "p99_ms", "mean_ms", "batches",
-            "mean_batch", "peak_device_bytes", "wall_s", "ok", "p99_tail")
+            "mean_batch", "peak_device_bytes", "wall_s", "ok", "p99_tail", "buffer_allocs",
+            "host_calls") + (("device_stages",) if timing else ())
     # 2. capacities: all requests present at t = 0 (after a warm-up run)
     one_at_a_time().run(requests(np.zeros(400), 400), timeout=600)
     cap = one_at_a_time().run(requests(np.zeros(ncap), ncap), timeout=600)
@@ -969,6 +986,7 @@ def measure_serve(args, n, rate_fracs, nv, ncap):
                    "inflight": args.inflight or W["inflight"],
                    "verified": f"{nv} requests served in mixed batches equal the "
                                f"single-frame path bit for bit",
+                   "host_settings": host_settings(),
                    "rates": rates},
         "clocks": clk}
 
@@ -999,6 +1017,9 @@ def main():
                     help="serve: byte cap of one batch in MiB (0: the workload's)")
     ap.add_argument("--inflight", type=int, default=0,
                     help="serve: batches on the device at once (0: the workload's)")
+    ap.add_argument("--serve-timing", action="store_true",
+                    help="serve: time every batch's copy, kernel and read-back stages "
+                         "with CUDA events and report them")
     ap.add_argument("--refine", type=int, default=0,
                     help="search: preset re-optimisation passes after the greedy search")
     ap.add_argument("--search-variant", default="sse",

@@ -145,6 +145,9 @@ class Server:
         self.batch_sizes: list = []
         self.finished: list = []
         self._by_id: dict = {}
+        # host time spent in the backend's calls and in whole loop
+        # iterations (wall clock): where a stall of the serving loop sits
+        self.host = {"launch": _Stall(), "poll": _Stall(), "reserve": _Stall(), "loop": _Stall()}
 
     # ------------------------------------------------------------ requests
     def submit(self, req: Request, now: Optional[float] = None) -> bool:
@@ -188,7 +191,9 @@ class Server:
         # 1. completed batches
         still = []
         for handle, reqs in self.inflight:
+            t0 = time.perf_counter()
             res = self.backend.poll(handle)
+            self.host["poll"].add(time.perf_counter() - t0)
             if res is None:
                 still.append((handle, reqs))
                 continue
@@ -204,7 +209,9 @@ class Server:
         while (self.queue and len(self.ready) < self.max_ready
                and self.in_use + self.queue[0].need <= self.budget):
             r = self.queue.popleft()
+            t0 = time.perf_counter()
             self.backend.reserve(r)
+            self.host["reserve"].add(time.perf_counter() - t0)
             self.in_use += r.need
             self.peak_in_use = max(self.peak_in_use, self.in_use)
             r.status, r.t_admit = "admitted", now
@@ -221,7 +228,9 @@ class Server:
                 cut += 1
             batch, self.ready = self.ready[:cut], self.ready[cut:]
             try:
+                t0 = time.perf_counter()
                 handle = self.backend.launch(batch)
+                self.host["launch"].add(time.perf_counter() - t0)
             except Exception as e:  # noqa: BLE001 - the batch fails, the server goes on
                 for r in batch:
                     self._free(r)
@@ -259,7 +268,11 @@ class Server:
         self.clock = lambda: base() - start          # run-relative times
         try:
             i, n = 0, len(reqs)
+            loop, t_prev = self.host["loop"], time.perf_counter()
             while i < n or not self.idle():
+                t = time.perf_counter()
+                loop.add(t - t_prev)
+                t_prev = t
                 now = self.clock()
                 if now > timeout:
                     raise TimeoutError(f"{n - len(self.finished)} requests unfinished")
@@ -272,6 +285,7 @@ class Server:
                     gap = reqs[i].arrival - self.clock()
                     if gap > 300e-6:
                         time.sleep(gap - 200e-6)
+                        t_prev = time.perf_counter()   # a chosen sleep is no stall
             wall = self.clock()
         finally:
             self.clock = base
@@ -292,6 +306,27 @@ class Server:
         self.finished.append(r)
         if self.on_done is not None:
             self.on_done(r)
+
+
+class _Stall:
+    """Durations of one kind of host call: count, total, maximum and how
+    many took longer than 5 ms."""
+    __slots__ = ("n", "total", "max", "over_5ms")
+
+    def __init__(self):
+        self.n, self.total, self.max, self.over_5ms = 0, 0.0, 0.0, 0
+
+    def add(self, dt: float) -> None:
+        self.n += 1
+        self.total += dt
+        if dt > self.max:
+            self.max = dt
+        if dt > 5e-3:
+            self.over_5ms += 1
+
+    def summary(self) -> dict:
+        return {"calls": self.n, "total_ms": self.total * 1e3, "max_ms": self.max * 1e3,
+                "over_5ms": self.over_5ms}
 
 
 def percentile(xs, q):
@@ -323,8 +358,29 @@ def summarize(reqs, wall: float, server: Server) -> dict:
         "batches": server.batches,
         "mean_batch": float(np.mean(server.batch_sizes)) if server.batch_sizes else 0.0,
         "peak_device_bytes": server.peak_in_use,
+        "buffer_allocs": getattr(server.backend, "allocs", 0),
         "p99_tail": tail,
+        "host_calls": {k: v.summary() for k, v in server.host.items()},
+        **device_stage_summary(getattr(server.backend, "batch_times", None)),
     }
+
+
+def device_stage_summary(times) -> dict:
+    """The device stage times of a timed CudaBackend's batches: maximum and
+    99th percentile of each stage, and the slowest batch end to end."""
+    if not times:
+        return {}
+    a = np.asarray(times, dtype=np.float64)
+    out = {}
+    for j, name in enumerate(("h2d_ms", "stream_wait_ms", "kernel_ms", "d2h_ms", "d2h_wait_ms",
+                              "d2h_frames_ms", "d2h_status_ms"), start=2):
+        out[name] = {"max": float(a[:, j].max()), "p99": float(np.percentile(a[:, j], 99)),
+                     "mean": float(a[:, j].mean())}
+    k = int(np.argmax(a[:, 2:6].sum(axis=1)))
+    out["slowest_batch"] = {"frames": int(a[k, 0]), "bytes": int(a[k, 1]),
+                            "stages_ms": [float(x) for x in a[k, 2:]]}
+    times.clear()
+    return {"device_stages": out}
 
 
 def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
@@ -344,7 +400,7 @@ class CudaBackend(Backend):
     buffers are dropped when a new size needs the room, so that the device
     memory held never exceeds the server's budget."""
 
-    def __init__(self, ctx, budget_bytes: int, device: int = 0):
+    def __init__(self, ctx, budget_bytes: int, device: int = 0, timing: bool = False):
         import torch
         from . import cdef
         self.torch, self.cdef, self.ctx = torch, cdef, ctx
@@ -357,13 +413,21 @@ class CudaBackend(Backend):
         self.free_bytes = 0
         self.held_bytes = 0
         self.host_out: dict = collections.defaultdict(list)
+        self.allocs = 0         # buffer sets allocated while serving (after prewarm)
         # status words of the batches in flight, copied back on the
         # device-to-host stream (no synchronous call in the loop)
         self.status_words = torch.zeros(256, dtype=torch.int32).pin_memory()
         self.next_word = 0
-        # the three events of each batch, reused round-robin with the status
-        # words (a ring far longer than the batches in flight)
-        self.events = [tuple(torch.cuda.Event() for _ in range(3))
+        # the events of each batch, reused round-robin with the status words
+        # (a ring far longer than the batches in flight).  With `timing`,
+        # four more (copy start, kernel start, read-back start, frames read
+        # back) and every batch's stage times are kept in `batch_times`:
+        # (frames, bytes, host-to-device ms, wait for the kernel stream ms,
+        # kernel ms, device-to-host ms, of which: wait for the read-back
+        # stream, the frames' copies, the status word's copy).
+        self.timing = timing
+        self.batch_times: list = []
+        self.events = [tuple(torch.cuda.Event(enable_timing=timing) for _ in range(7 if timing else 3))
                        for _ in range(self.status_words.numel())]
 
     @staticmethod
@@ -380,22 +444,37 @@ class CudaBackend(Backend):
         _, in_b, out_b = self._sizes(req)
         return in_b + out_b
 
-    def prewarm(self, shapes, count: int) -> None:
-        """Allocate `count` device and pinned host buffer sets for each
-        (width, height, bitdepth) up front, within the budget, so that no
-        allocation happens while serving."""
+    def prewarm(self, shapes, count: int, fill: float = 0.0) -> None:
+        """Allocate device and pinned host buffer sets up front, so that no
+        allocation (a pinned host allocation of a 4K frame takes tens of
+        milliseconds) happens while serving: `count` sets of each (width,
+        height, bitdepth), then more, one of each shape in turn, until
+        `fill` of the budget is held."""
         dummy = []
-        for w, h, bd in shapes:
+
+        def take(w, h, bd):
             rows, cols = -(-h // 64), -(-w // 64)
+            r = Request(-1, w, h, bd, None, np.zeros((rows, cols, 8), np.uint8))
+            r.need = self.need_bytes(r)
+            if self.held_bytes + r.need > self.budget:
+                return False
+            self.reserve(r)
+            dummy.append(r)
+            return True
+
+        for w, h, bd in shapes:
             for _ in range(count):
-                r = Request(-1, w, h, bd, None, np.zeros((rows, cols, 8), np.uint8))
-                r.need = self.need_bytes(r)
-                if self.held_bytes + r.need > self.budget:
+                if not take(w, h, bd):
                     break
-                self.reserve(r)
-                dummy.append(r)
+        grew = True
+        while grew and self.held_bytes < fill * self.budget:
+            grew = False
+            for w, h, bd in shapes:
+                if self.held_bytes < fill * self.budget and take(w, h, bd):
+                    grew = True
         for r in dummy:
             self.release(r)
+        self.allocs = 0
 
     def reserve(self, req: Request) -> None:
         k = self.key(req)
@@ -410,6 +489,7 @@ class CudaBackend(Backend):
                     self.held_bytes -= s["bytes"]
                     self.free_bytes -= s["bytes"]
             n_params, _, _ = self._sizes(req)
+            self.allocs += 1
             flat_in, f_in, prm = self.cdef.alloc_packed(req.width, req.height, req.bitdepth,
                                                         device=self.device, extra_bytes=n_params)
             flat_out, f_out, _ = self.cdef.alloc_packed(req.width, req.height, req.bitdepth,
@@ -435,34 +515,49 @@ class CudaBackend(Backend):
             if r.params_host is None:
                 r.params_host = torch.from_numpy(
                     np.ascontiguousarray(r.params, dtype=np.uint8).reshape(-1)).pin_memory()
-        ev_up, ev_c, ev_d = self.events[self.next_word]
+        evs = self.events[self.next_word]
+        ev_up, ev_c, ev_d = evs[:3]
         word = self.status_words[self.next_word:self.next_word + 1]
         self.next_word = (self.next_word + 1) % self.status_words.numel()
+        if self.timing:
+            evs[3].record(self.up)
         with torch.cuda.stream(self.up):
             for r in reqs:
                 r.slot["in_planes"].copy_(r.frame, non_blocking=True)
                 r.slot["params"].copy_(r.params_host, non_blocking=True)
         ev_up.record(self.up)
         self.comp.wait_event(ev_up)
+        if self.timing:
+            evs[4].record(self.comp)
         self.cdef.cdef_filter_frames(self.ctx, [r.slot["in"] for r in reqs],
                                      [r.slot["params"] for r in reqs],
                                      [r.slot["out"] for r in reqs], stream=self.comp)
         ev_c.record(self.comp)
-        self.down.wait_event(ev_c)
-        with torch.cuda.stream(self.down):
+        down = self.down
+        down.wait_event(ev_c)
+        if self.timing:
+            evs[5].record(down)
+        with torch.cuda.stream(down):
             for r in reqs:
                 r.slot["host_out"][0].copy_(r.slot["flat_out"], non_blocking=True)
-        self.ctx.status_async(word, stream=self.down)
-        ev_d.record(self.down)
+        if self.timing:
+            evs[6].record(down)
+        self.ctx.status_async(word, stream=down)
+        ev_d.record(down)
         # keep the host output reachable from the request once it is done
         for r in reqs:
             r.out = r.slot["host_out"]
-        return (ev_d, len(reqs), word)
+        return (ev_d, len(reqs), word, evs, sum(r.need for r in reqs))
 
     def poll(self, handle):
-        ev, n, word = handle
+        ev, n, word, evs, nbytes = handle
         if not ev.query():
             return None
+        if self.timing:
+            up, c, d, s0, k0, d0, d1 = evs
+            self.batch_times.append((n, nbytes, s0.elapsed_time(up), up.elapsed_time(k0),
+                                     k0.elapsed_time(c), c.elapsed_time(d), c.elapsed_time(d0),
+                                     d0.elapsed_time(d1), d1.elapsed_time(d)))
         # The context's status word collects device-side parameter errors.
         # Requests are validated on the host before they are queued, so it
         # stays 0; if it is ever set, the batch that saw it fails (and the
