@@ -60,6 +60,9 @@ struct SearchSmem {
     // [plane][block][half][value]: per candidate (r, r(2x + r), r(2(x - s) + r)),
     // then n, x, x^2, s, s^2, (x - s)^2
     int e14h[2][16][2][30];
+    // eq. 14: per luma 8x8 block the candidate-free sums n, x, x^2, s, s^2,
+    // (x - s)^2, formed in the first candidate group and kept for the others
+    int e14l[64][6];
     unsigned long long base[2];       // sum of (x - s)^2 over the same pixels, per plane group
     int blk[2];
     alignas(8) uint64_t bar[2];
@@ -298,16 +301,26 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
     // ---- both plane groups through one code path: task 0 luma, task 1 chroma
     const int bw = W >> 3;
     // eq. 14: the unit is the whole block and its candidate groups are
-    // evaluated in turn on the same staged tiles, directions and tables
+    // evaluated in turn on the same staged tiles, directions and tables.
+    // Luma keeps one sum of each kind per candidate (the two samples of a
+    // word are in one 8x8 block), chroma one per candidate and plane, so a
+    // luma group holds twice the candidates of a chroma group: the luma
+    // groups' shared work (tap loads, clip range, secondary sums) is done
+    // half as often.
+    constexpr int kPPl = (kEq14 && 2 * kPP <= 16) ? 2 * kPP : kPP;   // luma primaries per group
+    constexpr int kGl = 16 / kPPl;                                     // luma groups
 #pragma unroll 1
     for (int g = 0; g < (kEq14 ? kG : 1); g++) {
-        const int p0 = kEq14 ? g * kPP : p0_unit;
         // task 0 luma, task 1 chroma, a copy of the body each (the plane
         // group's choices fixed at compile time; eq. 14 sums the luma lanes
         // in one dot product)
         auto task_body = [&](auto luma_c) {
-            const bool luma = luma_c;
+            constexpr bool kL = decltype(luma_c)::value;
+            const bool luma = kL;
             const int task = luma ? 0 : 1;
+            constexpr int kPPt = kL ? kPPl : kPP;   // primaries of this task's group
+            constexpr int kNt = 4 * kPPt;           // candidates of this task's group
+            const int p0 = kEq14 ? g * kPPt : p0_unit;
             const int bx = lane >> 2, sub = lane & 3;
             const int blk = warp * 8 + bx;
             const int gby = fby * 8 + warp, gbx = fbx * 8 + bx;
@@ -352,7 +365,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
             for (int q = 0; q < (kEq14 ? 1 : kN); q++) acc[q] = 0;
             // eq. 14: per candidate and sample lane the sums of r, r (2x + r),
             // r (2 (x - s) + r); then per lane x, x^2, s, s^2, (x - s)^2
-            constexpr int kE = kEq14 ? kN : 1;
+            constexpr int kE = kEq14 ? kNt : 1;
             int e6[kE][6], e0[10];
     #pragma unroll
             for (int q = 0; q < kE; q++)
@@ -390,7 +403,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     sse0 = add_sq<T>(sse0, X, S);
                     const uint32_t two_xs = sadd16(2u * (X + 4096u * kLanes - S), 0xdf00u * kLanes);
                     uint32_t two_x = 0;
-                    if (kEq14) {
+                    if (kEq14 && g == 0) {
                         const int xl = (int)(X & 0xffffu) - (int)kBias, xh = (int)(X >> 16) - (int)kBias;
                         const int sl = (int)(S & 0xffffu) - (int)kBias, sh = (int)(S >> 16) - (int)kBias;
                         e0[0] += xl; e0[1] += xh;
@@ -398,8 +411,8 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                         e0[4] += sl; e0[5] += sh;
                         e0[6] += sl * sl; e0[7] += sh * sh;
                         e0[8] += (xl - sl) * (xl - sl); e0[9] += (xh - sh) * (xh - sh);
-                        two_x = sadd16(X + X, 0xfe00u * kLanes);   // 2x - 256 per lane
                     }
+                    if (kEq14) two_x = sadd16(X + X, 0xfe00u * kLanes);   // 2x - 256 per lane
                     const uint32_t rlo = __vmaxu2(mn - X + 2048u * kLanes, 1792u * kLanes) - 1792u * kLanes;
                     const uint32_t rhi = mx - X + 256u * kLanes;
                     uint32_t Q[4], Qr[4];
@@ -415,7 +428,7 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     }
                     const uint32_t C = 4096u * kLanes - 24u * X;
     #pragma unroll
-                    for (int pp = 0; pp < kPP; pp++) {
+                    for (int pp = 0; pp < kPPt; pp++) {
                         const int p = p0 + pp;
                         if (kSub && !((pmask >> p) & 1)) continue;
                         const SetC sc = ps[p];
@@ -470,38 +483,51 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     // add the lanes, then the four lanes of the block
                     int n = inside ? 16 : 0, sx = e0[0] + e0[1], sx2 = e0[2] + e0[3];
                     int ssum = e0[4] + e0[5], ss2 = e0[6] + e0[7], sxs = e0[8] + e0[9];
-                    int A[kN], BX[kN], BS[kN];
+                    int A[kNt], BX[kNt], BS[kNt];
     #pragma unroll
-                    for (int c = 0; c < kN; c++) {
+                    for (int c = 0; c < kNt; c++) {
                         A[c] = e6[c][0] + e6[c][1];
                         BX[c] = e6[c][2] + e6[c][3];
                         BS[c] = e6[c][4] + e6[c][5];
                     }
     #pragma unroll
                     for (int o = 1; o <= 2; o <<= 1) {
-                        n += __shfl_xor_sync(0xffffffffu, n, o);
-                        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                        sx2 += __shfl_xor_sync(0xffffffffu, sx2, o);
-                        ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
-                        ss2 += __shfl_xor_sync(0xffffffffu, ss2, o);
-                        sxs += __shfl_xor_sync(0xffffffffu, sxs, o);
+                        if (g == 0) {
+                            n += __shfl_xor_sync(0xffffffffu, n, o);
+                            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                            sx2 += __shfl_xor_sync(0xffffffffu, sx2, o);
+                            ssum += __shfl_xor_sync(0xffffffffu, ssum, o);
+                            ss2 += __shfl_xor_sync(0xffffffffu, ss2, o);
+                            sxs += __shfl_xor_sync(0xffffffffu, sxs, o);
+                        }
     #pragma unroll
-                        for (int c = 0; c < kN; c++) {
+                        for (int c = 0; c < kNt; c++) {
                             A[c] += __shfl_xor_sync(0xffffffffu, A[c], o);
                             BX[c] += __shfl_xor_sync(0xffffffffu, BX[c], o);
                             BS[c] += __shfl_xor_sync(0xffffffffu, BS[c], o);
                         }
                     }
+                    // the candidate-free sums of the block: formed in the first
+                    // group (the four lanes agree after the butterfly), kept
+                    if (g == 0) {
+                        if (sub == 0) {
+                            int *k6 = sm.e14l[blk];
+                            k6[0] = n, k6[1] = sx, k6[2] = sx2, k6[3] = ssum, k6[4] = ss2, k6[5] = sxs;
+                        }
+                    } else {
+                        const int *k6 = sm.e14l[blk];
+                        n = k6[0], sx = k6[1], sx2 = k6[2], ssum = k6[3], ss2 = k6[4], sxs = k6[5];
+                    }
                     // each of the block's four lanes evaluates a quarter of the
                     // candidates; the eight blocks' values are summed across
                     // the warp before one shared atomic per candidate
-                    constexpr int kC = kN / 4;
+                    constexpr int kC = kNt / 4;
                     long long tv[kC];
     #pragma unroll
                     for (int j = 0; j < kC; j++) tv[j] = 0;
     #pragma unroll
-                    for (int c = 0; c < kN; c++) {
-                        if (n > 0 && (c * 4) / kN == sub)
+                    for (int c = 0; c < kNt; c++) {
+                        if (n > 0 && (c * 4) / kNt == sub)
                             tv[c % kC] = eq14_value(n, ssum, ss2, sx + A[c], (long long)sx2 + BX[c],
                                                     (long long)sxs + BS[c], F.bitdepth);
                     }
@@ -522,11 +548,12 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     for (int k = 0; k < 2; k++) {
                         int vals[30];
     #pragma unroll
-                        for (int c = 0; c < kN; c++) {
+                        for (int c = 0; c < kNt; c++) {
                             vals[3 * c] = e6[c][k];
                             vals[3 * c + 1] = e6[c][2 + k];
                             vals[3 * c + 2] = e6[c][4 + k];
                         }
+                        // the candidate-free sums: from the first group, kept
                         vals[24] = inside ? 4 : 0;
                         vals[25] = e0[k];
                         vals[26] = e0[2 + k];
@@ -536,10 +563,12 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
     #pragma unroll
                         for (int o = 1; o <= 4; o <<= 1)
     #pragma unroll
-                            for (int j = 0; j < 30; j++) vals[j] += __shfl_xor_sync(0xffffffffu, vals[j], o);
+                            for (int j = 0; j < 30; j++)
+                                if (j < 24 || g == 0) vals[j] += __shfl_xor_sync(0xffffffffu, vals[j], o);
                         if ((lane & 7) == 0)
     #pragma unroll
-                            for (int j = 0; j < 30; j++) sm.e14h[k][cb][half][j] = vals[j];
+                            for (int j = 0; j < 30; j++)
+                                if (j < 24 || g == 0) sm.e14h[k][cb][half][j] = vals[j];
                     }
                 }
                 __syncthreads();
@@ -600,7 +629,8 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 __syncthreads();
             }
         };
-        task_body(std::true_type{});
+        // eq. 14: the luma groups are the first kGl of the kG chroma groups
+        if (!kEq14 || g < kGl) task_body(std::true_type{});
         task_body(std::false_type{});
         if constexpr (kEq14) {
             // chroma 8x8 blocks: two planes x 16 blocks x the unit's candidates,
@@ -623,12 +653,16 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 if (lane < kN) atomicAdd(&sm.acc14c[c], (unsigned long long)t);
             }
             __syncthreads();
-            if (tid < kN) {
-                const int q = 4 * p0 + tid;
-                const bool on_l = (allowed_pairs(F, 0) >> q) & 1, on_c = (allowed_pairs(F, 1) >> q) & 1;
-                dist_luma[(int64_t)blk_global * 64 + q] = on_l ? (long long)sm.acc[tid] : 0;
-                dist_chroma[(int64_t)blk_global * 64 + q] = on_c ? (long long)sm.acc14c[tid] : 0;
+            if (g < kGl && tid < 4 * kPPl) {   // the luma group's candidates
+                const int q = 4 * kPPl * g + tid;
+                const bool on = (allowed_pairs(F, 0) >> q) & 1;
+                dist_luma[(int64_t)blk_global * 64 + q] = on ? (long long)sm.acc[tid] : 0;
                 sm.acc[tid] = 0;
+            }
+            if (tid < kN) {                    // the chroma group's
+                const int q = 4 * kPP * g + tid;
+                const bool on = (allowed_pairs(F, 1) >> q) & 1;
+                dist_chroma[(int64_t)blk_global * 64 + q] = on ? (long long)sm.acc14c[tid] : 0;
                 sm.acc14c[tid] = 0;
             }
             __syncthreads();
