@@ -63,10 +63,16 @@ struct SearchSmem {
     // eq. 14: per luma 8x8 block the candidate-free sums n, x, x^2, s, s^2,
     // (x - s)^2, formed in the first candidate group and kept for the others
     int e14l[64][6];
+    // eq. 14: secondary sums kept across the candidate groups (with the
+    // block's idle tile buffer, see dist_block)
+    uint32_t qc[12 * 256];
     unsigned long long base[2];       // sum of (x - s)^2 over the same pixels, per plane group
     int blk[2];
     alignas(8) uint64_t bar[2];
 };
+
+// two CTAs per SM (228 KB of shared memory, 1 KB reserved per CTA)
+static_assert(sizeof(SearchSmem) <= 112 * 1024, "the search kernels run two CTAs per SM");
 
 // The signalled secondary strengths {0, 1, 2, 4} by index.
 __device__ __forceinline__ int sec_value(int i) { return i == 3 ? 4 : i; }
@@ -205,7 +211,7 @@ __device__ __forceinline__ int wentry(int N, int lane)
 // search): primaries without an allowed pair are skipped.
 template <typename T, int kG, bool kCoded, bool kEq14, bool kSub>
 __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global, int grp,
-                           SearchSmem &sm, const RawTiles &raw, long long *dist_luma,
+                           SearchSmem &sm, RawTiles &raw, long long *dist_luma,
                            long long *dist_chroma, uint8_t *skipped CDEF_DEBUG_PARAM(int *status))
 {
     constexpr int kPP = 16 / kG;           // primary strengths per unit
@@ -309,12 +315,11 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
     // half as often.
     constexpr int kPPl = (kEq14 && 2 * kPP <= 16) ? 2 * kPP : kPP;   // luma primaries per group
     constexpr int kGl = 16 / kPPl;                                     // luma groups
-#pragma unroll 1
-    for (int g = 0; g < (kEq14 ? kG : 1); g++) {
+    {
         // task 0 luma, task 1 chroma, a copy of the body each (the plane
         // group's choices fixed at compile time; eq. 14 sums the luma lanes
-        // in one dot product)
-        auto task_body = [&](auto luma_c) {
+        // in one dot product); g: the candidate group (eq. 14)
+        auto task_body = [&](auto luma_c, const int g) {
             constexpr bool kL = decltype(luma_c)::value;
             const bool luma = kL;
             const int task = luma ? 0 : 1;
@@ -342,6 +347,19 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
             const SetC *ps = luma ? sm.pset[blk] : sm.cset;
             const uint32_t bits = luma ? sm.pbits[blk] : sm.cbits;
             const uint32_t raised = luma ? 0u : sm.craised;
+            // eq. 14: the secondary sums of the thread's words are formed in
+            // the task's first candidate group and kept for the others: luma
+            // S_s = 1, 2 in the block's tile buffer (idle once the tiles are
+            // re-laid, until the next block's loads are issued) and S_s = 4
+            // in qc; chroma all three in qc and those at the raised damping
+            // in the tile buffer
+            static_assert(sizeof(RawTiles) >= 2 * 8 * kThreads * 4 && kThreads == 256, "cache size");
+            uint32_t *const idle = reinterpret_cast<uint32_t *>(&raw);
+            auto qslot = [&](int s, int i) -> uint32_t & {
+                if (kL) return s < 3 ? idle[((s - 1) * 8 + i) * kThreads + tid] : sm.qc[i * kThreads + tid];
+                return sm.qc[((s - 1) * 4 + i) * kThreads + tid];
+            };
+            auto rslot = [&](int s, int i) -> uint32_t & { return idle[((s - 1) * 4 + i) * kThreads + tid]; };
             const SetC *ss = luma ? sm.sset[0] : sm.sset[1];
             SetC s7 = {};
             if (kCoded) s7 = luma ? sm.s7[blk] : sm.s7c;
@@ -417,11 +435,29 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     const uint32_t rhi = mx - X + 256u * kLanes;
                     uint32_t Q[4], Qr[4];
                     Q[0] = Qr[0] = 12u * X;
+                    if (!kEq14 || g == 0) {
     #pragma unroll
-                    for (int s = 1; s < 4; s++) Q[s] = sec_sum(v, X, ss[s]);
+                        for (int s = 1; s < 4; s++) Q[s] = sec_sum(v, X, ss[s]);
+                        if (kEq14) {
+    #pragma unroll
+                            for (int s = 1; s < 4; s++) qslot(s, i) = Q[s];
+                        }
+                    } else {
+    #pragma unroll
+                        for (int s = 1; s < 4; s++) Q[s] = qslot(s, i);
+                    }
                     if (raised) {
+                        if (!kEq14 || g == 0) {
     #pragma unroll
-                        for (int s = 1; s < 4; s++) Qr[s] = sec_sum(v, X, sm.sset[2][s]);
+                            for (int s = 1; s < 4; s++) Qr[s] = sec_sum(v, X, sm.sset[2][s]);
+                            if (kEq14) {
+    #pragma unroll
+                                for (int s = 1; s < 4; s++) rslot(s, i) = Qr[s];
+                            }
+                        } else {
+    #pragma unroll
+                            for (int s = 1; s < 4; s++) Qr[s] = rslot(s, i);
+                        }
                     } else {
     #pragma unroll
                         for (int s = 1; s < 4; s++) Qr[s] = Q[s];
@@ -629,43 +665,55 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 __syncthreads();
             }
         };
-        // eq. 14: the luma groups are the first kGl of the kG chroma groups
-        if (!kEq14 || g < kGl) task_body(std::true_type{});
-        task_body(std::false_type{});
-        if constexpr (kEq14) {
-            // chroma 8x8 blocks: two planes x 16 blocks x the unit's candidates,
-            // one per thread; lanes 8 apart hold the same candidate
-            static_assert(2 * 16 * kN == kThreads, "one chroma evaluation per thread");
-            {
-                const int k = tid / (16 * kN), cb = (tid / kN) % 16, c = tid % kN;
-                const int *h0 = sm.e14h[k][cb][0], *h1 = sm.e14h[k][cb][1];
-                const int n = h0[24] + h1[24];
-                long long t = 0;
-                if (n > 0) {
-                    const long long sx = h0[25] + h1[25], sx2 = h0[26] + h1[26];
-                    const long long ssum = h0[27] + h1[27], ss2 = h0[28] + h1[28], sxs = h0[29] + h1[29];
-                    t = eq14_value(n, ssum, ss2, sx + h0[3 * c] + h1[3 * c],
-                                   sx2 + h0[3 * c + 1] + h1[3 * c + 1],
-                                   sxs + h0[3 * c + 2] + h1[3 * c + 2], F.bitdepth);
+        if constexpr (!kEq14) {
+            task_body(std::true_type{}, 0);
+            task_body(std::false_type{}, 0);
+        } else {
+            // eq. 14: the luma groups, then the chroma groups (each task's
+            // secondary sums are formed in its first group and kept)
+#pragma unroll 1
+            for (int g = 0; g < kGl; g++) {
+                task_body(std::true_type{}, g);
+                if (tid < 4 * kPPl) {   // the group's luma candidates
+                    const int q = 4 * kPPl * g + tid;
+                    const bool on = (allowed_pairs(F, 0) >> q) & 1;
+                    dist_luma[(int64_t)blk_global * 64 + q] = on ? (long long)sm.acc[tid] : 0;
+                    sm.acc[tid] = 0;
                 }
-                t += __shfl_xor_sync(0xffffffffu, t, 8);
-                t += __shfl_xor_sync(0xffffffffu, t, 16);
-                if (lane < kN) atomicAdd(&sm.acc14c[c], (unsigned long long)t);
+                __syncthreads();
             }
-            __syncthreads();
-            if (g < kGl && tid < 4 * kPPl) {   // the luma group's candidates
-                const int q = 4 * kPPl * g + tid;
-                const bool on = (allowed_pairs(F, 0) >> q) & 1;
-                dist_luma[(int64_t)blk_global * 64 + q] = on ? (long long)sm.acc[tid] : 0;
-                sm.acc[tid] = 0;
+#pragma unroll 1
+            for (int g = 0; g < kG; g++) {
+                task_body(std::false_type{}, g);
+                // chroma 8x8 blocks: two planes x 16 blocks x the group's
+                // candidates, one per thread; lanes 8 apart hold the same
+                // candidate
+                static_assert(2 * 16 * kN == kThreads, "one chroma evaluation per thread");
+                {
+                    const int k = tid / (16 * kN), cb = (tid / kN) % 16, c = tid % kN;
+                    const int *h0 = sm.e14h[k][cb][0], *h1 = sm.e14h[k][cb][1];
+                    const int n = h0[24] + h1[24];
+                    long long t = 0;
+                    if (n > 0) {
+                        const long long sx = h0[25] + h1[25], sx2 = h0[26] + h1[26];
+                        const long long ssum = h0[27] + h1[27], ss2 = h0[28] + h1[28], sxs = h0[29] + h1[29];
+                        t = eq14_value(n, ssum, ss2, sx + h0[3 * c] + h1[3 * c],
+                                       sx2 + h0[3 * c + 1] + h1[3 * c + 1],
+                                       sxs + h0[3 * c + 2] + h1[3 * c + 2], F.bitdepth);
+                    }
+                    t += __shfl_xor_sync(0xffffffffu, t, 8);
+                    t += __shfl_xor_sync(0xffffffffu, t, 16);
+                    if (lane < kN) atomicAdd(&sm.acc14c[c], (unsigned long long)t);
+                }
+                __syncthreads();
+                if (tid < kN) {
+                    const int q = 4 * kPP * g + tid;
+                    const bool on = (allowed_pairs(F, 1) >> q) & 1;
+                    dist_chroma[(int64_t)blk_global * 64 + q] = on ? (long long)sm.acc14c[tid] : 0;
+                    sm.acc14c[tid] = 0;
+                }
+                __syncthreads();
             }
-            if (tid < kN) {                    // the chroma group's
-                const int q = 4 * kPP * g + tid;
-                const bool on = (allowed_pairs(F, 1) >> q) & 1;
-                dist_chroma[(int64_t)blk_global * 64 + q] = on ? (long long)sm.acc14c[tid] : 0;
-                sm.acc14c[tid] = 0;
-            }
-            __syncthreads();
         }
     }
 }
