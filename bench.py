@@ -760,10 +760,19 @@ def measure_search(args, variant, steps, warmup, pool=None):
     roofline = {"bound": "alu", "achieved": ops / (dist_ms * 1e-3) / 1e9, "peak": peak_ops,
                 "unit": "Gop/s", "frac": ops / (dist_ms * 1e-3) / 1e9 / peak_ops,
                 "traffic": None,
-                "kernel": "dist_wide_kernel + find_dir_kernel (distortion tables, 32-bit lanes)"
-                if variant in ("444", "12bit", "444coded")
+                "kernel": "dist_kernel, one plane per work unit (4:4:4 planes in the packed "
+                          "layout) + find_dir_kernel (distortion tables)"
+                if variant == "444"
+                else "dist_kernel<1, coded>, one plane per work unit (4:4:4 planes in the "
+                     "packed layout) + find_dir_kernel (128-combination tables)"
+                if variant == "444coded"
+                else "dist_wide_kernel + find_dir_kernel (distortion tables, 32-bit lanes)"
+                if variant == "12bit"
+                else "dist_kernel<8, eq. 14>, one plane per work unit (4:4:4 planes in the "
+                     "packed layout) + find_dir_kernel (eq. 14 tables)"
+                if variant == "444eq14"
                 else "dist_wide_eq14_kernel + find_dir_kernel (eq. 14 tables, 32-bit lanes)"
-                if variant in ("444eq14", "12biteq14") else "dist_kernel (distortion tables)",
+                if variant == "12biteq14" else "dist_kernel (distortion tables)",
                 "ops_per_launch": ops, "mean_launch_us": dist_ms * 1e3,
                 "launch_time": "CUDA events around the kernel inside the search graph",
                 "preset_kernel_us": pre_ms * 1e3,

@@ -482,6 +482,39 @@ int fill_plane_dev(FilterFrameDev &d, const cdef_frame *in, const cdef_plane &pi
     return CDEF_OK;
 }
 
+// One 8/10-bit 4:4:4 frame as a mode-3 entry: its three planes filtered in
+// turn by the CTA that takes a filter block (each plane's map with the luma
+// box), the luma directions of the block searched in its first stage (or
+// read from dir/var) and kept for the chroma planes.
+int fill_444_dev(FilterFrameDev &d, const cdef_frame *in, const cdef_frame *out,
+                 const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
+                 const uint8_t *coded)
+{
+    memset(&d, 0, sizeof(d));
+    const cdef_plane *pi[3] = {&in->y, &in->u, &in->v}, *po[3] = {&out->y, &out->u, &out->v};
+    const int bytes = sample_bytes(in->bitdepth);
+    for (int k = 0; k < 3; k++) {
+        d.p[k].in = static_cast<const uint8_t *>(pi[k]->data);
+        d.p[k].out = static_cast<uint8_t *>(po[k]->data);
+        d.p[k].in_pitch = pi[k]->pitch_bytes;
+        d.p[k].out_pitch = po[k]->pitch_bytes;
+        d.p[k].w = pi[k]->width;
+        d.p[k].h = pi[k]->height;
+        const int rc = encode_plane(&d.tmap[k], *pi[k], bytes, luma_box_cols(bytes), kLumaBoxRows);
+        if (rc) return rc;
+    }
+    d.params = params;
+    d.dir = dir;
+    d.var = var;
+    d.coded = coded;
+    d.mode = 3;
+    d.bitdepth = in->bitdepth;
+    d.fb_cols = (in->y.width + 63) / 64;
+    d.fb_rows = (in->y.height + 63) / 64;
+    d.block_start = 0;
+    return CDEF_OK;
+}
+
 int plane_pass(cdef_ctx *ctx, const cdef_frame *in, const cdef_plane &pin, const cdef_plane &pout,
                const cdef_fb_params *params, const uint8_t *dir, const int32_t *var,
                const uint8_t *coded, int mode, bool overlap, cudaStream_t s)
@@ -568,8 +601,19 @@ int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params
             }
         return CDEF_OK;
     }
-    // 4:4:4: the luma directions first (unless given), then the three planes
-    // in the luma geometry as one launch, which waits for the maps
+    // 8/10-bit 4:4:4: one launch, a CTA filtering the three planes of a
+    // block in turn (consecutive calls on a stream may overlap, as 4:2:0's)
+    if (in->bitdepth <= 10) {
+        FilterBatch<1> b;
+        b.n = 1;
+        b.total_blocks = fb_count(in);
+        b.waits = wait_limits();
+        if ((rc = fill_444_dev(b.f[0], in, out, params, dir, var, coded))) return rc;
+        unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
+        return cuda_status(launch_filter_single(b, ctx->status, work, ctx->overlap, s));
+    }
+    // 12-bit 4:4:4: the luma directions first (unless given), then the three
+    // planes in the luma geometry as one launch, which waits for the maps
     if (!dir) {
         const size_t blocks = (size_t)(in->y.width / 8) * (in->y.height / 8);
         if ((rc = ensure_maps(ctx, blocks))) return rc;
@@ -749,6 +793,13 @@ int fill_search_batch(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cde
         if (rec[i].bitdepth > 10 || chroma_format(&rec[i]) != 420) wide = true;
     // the 128-combination eq. 14 tables are formed by the 32-bit path
     if (coded && ctx->metric == CDEF_METRIC_EQ14) wide = true;
+    // 8/10-bit 4:4:4 frames (squared error over 64 pairs or the 128
+    // combinations, eq. 14 over 64 pairs): the packed tables with one plane
+    // per work unit (the direction maps formed first, as for the 32-bit
+    // path)
+    bool planes = n > 0 && !(coded && ctx->metric == CDEF_METRIC_EQ14);
+    for (int i = 0; i < n && planes; i++)
+        if (rec[i].bitdepth > 10 || chroma_format(&rec[i]) != 444) planes = false;
     int total = 0, rc = CDEF_OK;
     size_t maps = 0;
     for (int i = 0; i < n && rc == CDEF_OK; i++) {
@@ -762,6 +813,13 @@ int fill_search_batch(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cde
         f.map_start = (int)maps;
         maps += (size_t)(rec[i].y.width / 8) * (rec[i].y.height / 8);
         if (!wide && (rc = encode_frame_tiles(f.tmap, &rec[i]))) break;
+        if (planes) {   // every plane with the luma box
+            const int bytes = sample_bytes(rec[i].bitdepth);
+            const cdef_plane *pl[3] = {&rec[i].y, &rec[i].u, &rec[i].v};
+            for (int k = 0; k < 3 && rc == CDEF_OK; k++)
+                rc = encode_plane(&f.tmap[k], *pl[k], bytes, luma_box_cols(bytes), kLumaBoxRows);
+            if (rc) break;
+        }
         const cdef_plane *pr[3] = {&rec[i].y, &rec[i].u, &rec[i].v};
         const cdef_plane *ps[3] = {&src[i].y, &src[i].u, &src[i].v};
         for (int k = 0; k < 3; k++) {
@@ -791,6 +849,7 @@ int fill_search_batch(cdef_ctx *ctx, int32_t n, const cdef_frame *rec, const cde
     if (rc != CDEF_OK) return rc;
     b->n = n;
     b->total_blocks = total;
+    b->planes = planes ? 1 : 0;
     b->waits = wait_limits();
     *wide_out = wide;
     *maps_out = maps;

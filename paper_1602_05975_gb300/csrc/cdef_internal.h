@@ -33,7 +33,10 @@ struct FilterFrameDev {  // aligned as CUtensorMap requires
     const uint8_t *coded;            // optional 8x8 coded-residual map (NULL: all coded)
     int mode;                        // 0: 4:2:0 luma + chroma; 1: the luma plane alone;
                                      // 2: a full-resolution (4:4:4) chroma plane in the
-                                     //    luma slot, with maps (chroma parameters)
+                                     //    luma slot, with maps (chroma parameters);
+                                     // 3: an 8/10-bit 4:4:4 frame, its three planes
+                                     //    (p[0..2], each map with the luma box) filtered
+                                     //    in turn per filter block
     int bitdepth;
     int fb_cols, fb_rows;
     int block_start;                 // first CTA index of this frame
@@ -85,6 +88,9 @@ struct SearchFrameDev {  // aligned as CUtensorMap requires
 struct SearchBatch {
     int n;
     int total_blocks;
+    // 8/10-bit 4:4:4 frames searched one plane per work unit in the packed
+    // layout (squared error, 64 pairs); the direction maps are formed first
+    int planes = 0;
     WaitLimits waits = {kDefaultWaitCycles, 0, 0};
     SearchFrameDev f[kMaxBatch];
 };

@@ -73,6 +73,7 @@ struct FilterSmem {
     uint8_t coded[64];                                  // 8x8 block has coded residual
     int var[64];
     int blk_next;                                       // block id of the tiles in `raw`
+    int stage_next;                                     // and their plane (mode 3)
     alignas(8) uint64_t bar;
 };
 
@@ -134,11 +135,19 @@ struct StageOut {
     static constexpr int kGroupRows = (kLuma && kBytes == 1) ? 8 : 4;
     uint32_t off;        // byte offset in its plane of this lane's segment in its first row
     int n;               // blocks of the segment inside the frame (0: the lane stores nothing)
+    int sp;              // luma layout: the plane written (0; 1, 2: a 4:4:4 chroma plane)
+
+    // The plane in the luma layout a stage writes.
+    __device__ __forceinline__ static const PlaneDev &lplane(const FilterFrameDev &F, int sp)
+    {
+        return sp == 0 ? F.p[0] : sp == 1 ? F.p[1] : F.p[2];
+    }
 
     // The lane's segment: which staged row and 16 bytes it reads, where
     // they go.  fbx, fby: the filter block; warp: its block row.
     __device__ __forceinline__ StageOut(const FilterFrameDev &F, int lane, int fby, int fbx,
-                                        int warp, bool row_in)
+                                        int warp, bool row_in, int stage = 0)
+        : sp(stage)
     {
         int plane = 0, r, c, nblk, blk_px, x_bytes, y0;
         if (kLuma && kBytes == 2) {          // lane L: row L / 8 of block L % 8
@@ -154,7 +163,7 @@ struct StageOut {
             plane = (lane >> 3) & 1, r = (lane >> 1) & 3, c = lane & 1, nblk = 4, blk_px = 4;
             x_bytes = fbx * 32 + c * 16, y0 = fby * 32 + warp * 4;
         }
-        const PlaneDev &P = kLuma ? F.p[0] : plane ? F.p[2] : F.p[1];
+        const PlaneDev &P = kLuma ? lplane(F, sp) : plane ? F.p[2] : F.p[1];
         const int first = (fbx * 8 + c * nblk) * blk_px;
         int k = (P.w - first) / blk_px;
         k = k < 0 ? 0 : (k > nblk ? nblk : k);
@@ -193,10 +202,11 @@ struct StageOut {
             else so = ((lane >> 3) & 1) * 128 + ((lane >> 1) & 3) * 32 + (lane & 1) * 16;
             // the plane, selected without indexing the parameter block
             const bool v_plane = !kLuma && (kBytes == 2 ? lane >= 16 : ((lane >> 3) & 1));
-            uint8_t *dst = (kLuma ? F.p[0].out : v_plane ? F.p[2].out : F.p[1].out) + off;
-            const int64_t pitch = kLuma ? F.p[0].out_pitch : v_plane ? F.p[2].out_pitch : F.p[1].out_pitch;
+            const PlaneDev &P = kLuma ? lplane(F, sp) : v_plane ? F.p[2] : F.p[1];
+            uint8_t *dst = P.out + off;
+            const int64_t pitch = P.out_pitch;
             // the segment's last byte inside the plane's rows
-            const int ph = kLuma ? F.p[0].h : v_plane ? F.p[2].h : F.p[1].h;
+            const int ph = P.h;
             const bool ok = CDEF_IN_BOUNDS((int64_t)off + 15, pitch * ph, status) &&
                             CDEF_IN_BOUNDS(so + 15, 512, status);
             (void)ph;
@@ -312,7 +322,7 @@ __device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int f
 // so that the next block's tiles can land in the same buffer.
 template <typename T, typename Prefetch>
 __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *status,
-                              FilterSmem &sm, const RawTiles &raw, Prefetch prefetch)
+                              FilterSmem &sm, const RawTiles &raw, Prefetch prefetch, int stage)
 {
     const int sh8 = F.bitdepth - 8;
     const int W = F.p[0].w, H = F.p[0].h, CW = F.p[1].w, CH = F.p[1].h;
@@ -351,7 +361,11 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
     // ---- direction search
     const int bw = W >> 3;
     const bool fused = F.dir == nullptr;
-    if (fused) {
+    // mode 3 (8/10-bit 4:4:4, the three planes of a block in turn): stage 0
+    // is luma; stages 1 and 2 (U, V) keep its directions, contrasts and
+    // coded flags in shared memory and take the chroma parameters
+    const bool chroma_stage = stage > 0;
+    if (fused && !chroma_stage) {
         const int warp = tid >> 5, lane = tid & 31;
         const int blk = (warp >> 2) * 32 + lane;
         switch (warp & 3) {
@@ -363,7 +377,9 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         __syncthreads();
     }
     int coded = 0;
-    if (tid < 64) {
+    if (chroma_stage) {
+        if (tid < 64) coded = sm.coded[tid];
+    } else if (tid < 64) {
         const int gby = fby * 8 + (tid >> 3), gbx = fbx * 8 + (tid & 7);
         int d = 0, v = 0;
         if (gby * 8 < H && gbx * 8 < W) {
@@ -425,8 +441,9 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         // a block that is not filtered (section 4) takes the identity set
         // (strengths 0: every tap clamps to x, no clip), so the loop below
         // needs no per-word test
-        const bool on = any_coded && (sm.coded[blk] || ((luma && F.mode != 2) ? skip_l : skip_c));
-        const BlockC bc = !on ? sm.bz : luma ? sm.lb[blk] : sm.cb;
+        const bool lp = luma && F.mode != 2 && !chroma_stage;   // luma parameters
+        const bool on = any_coded && (sm.coded[blk] || (lp ? skip_l : skip_c));
+        const BlockC bc = !on ? sm.bz : (luma && !chroma_stage) ? sm.lb[blk] : sm.cb;
         const unsigned fl = inside ? bc.flags : 0u;
         const bool any_p = __any_sync(0xffffffffu, fl & 1), any_s = __any_sync(0xffffffffu, fl & 2);
         const bool any_clip = __any_sync(0xffffffffu, (fl & 3) == 3);
@@ -437,7 +454,7 @@ __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *st
         const int o[12] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w};
         const bool row_in = luma ? gby * 8 < H : gby * 4 < CH;
         using Out = StageOut<luma, sizeof(T)>;
-        Out out(F, lane, fby, fbx, warp, row_in);
+        Out out(F, lane, fby, fbx, warp, row_in, stage);
         // the re-laid tile the taps read (luma: even and odd copies)
         const uint32_t *tile0 = luma ? sm.t.le : sm.t.cw;
         constexpr int tile_words = luma ? 2 * kLumaRows * kLumaPitch : kChromaRows * kChromaPitch;
@@ -478,14 +495,16 @@ __device__ __forceinline__ BlockRef locate(const FilterBatch<MAXF> &batch, int b
     return {fi, fby, local - fby * batch.f[fi].fb_cols};
 }
 
-// Issued by one thread: the three tile loads of block `blk` into `raw`.
+// Issued by one thread: the tile loads of block `blk` into `raw` (mode 3:
+// the one plane of `stage`, whose map has the luma box).
 template <int MAXF>
 __device__ __forceinline__ void issue_loads(const FilterBatch<MAXF> &batch, int blk, RawTiles &raw,
-                                            uint64_t *bar)
+                                            uint64_t *bar, int stage = 0)
 {
     const BlockRef r = locate(batch, blk);
     const FilterFrameDev &F = batch.f[r.fi];
-    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar, F.mode == 0, batch.waits.extra_tx);
+    issue_tile_loads(F.mode == 3 ? &F.tmap[stage] : F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar,
+                     F.mode == 0, batch.waits.extra_tx);
 }
 
 // Persistent: each CTA takes blocks from the launch's work counter
@@ -518,6 +537,7 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
             mbar_init(&sm.bar, 1);
             const int b = (int)atomicAdd(&work[0], 1u);
             sm.blk_next = b;
+            sm.stage_next = 0;
             if (b < total) issue_loads(batch, b, sm.raw, &sm.bar);
         }
         if (tid < 192) {  // tap offset tables [luma/chroma][d][tap]
@@ -532,7 +552,7 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
         // then block n+1's loads are issued into the buffer while block n is
         // searched and filtered
         for (int it = 0;; it++) {
-            const int blk = sm.blk_next;
+            const int blk = sm.blk_next, stage = sm.stage_next;
             if (blk >= total) break;
             const bool arrived = mbar_wait_bounded(&sm.bar, it & 1, batch.waits.wait_cycles);
             if (__syncthreads_or(!arrived)) {  // the whole CTA leaves together
@@ -542,19 +562,25 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
                 }
                 break;
             }
-            auto prefetch = [&]() {
-                if (tid == 0) {
-                    const int nb = (int)atomicAdd(&work[0], 1u);
-                    sm.blk_next = nb;
-                    if (nb < total) issue_loads(batch, nb, sm.raw, &sm.bar);
-                }
-            };
             const BlockRef r = locate(batch, blk);
             const FilterFrameDev &F = batch.f[r.fi];
+            auto prefetch = [&]() {
+                if (tid == 0) {
+                    if (F.mode == 3 && stage < 2) {   // the block's next plane
+                        sm.stage_next = stage + 1;
+                        issue_loads(batch, blk, sm.raw, &sm.bar, stage + 1);
+                    } else {
+                        const int nb = (int)atomicAdd(&work[0], 1u);
+                        sm.blk_next = nb;
+                        sm.stage_next = 0;
+                        if (nb < total) issue_loads(batch, nb, sm.raw, &sm.bar);
+                    }
+                }
+            };
             if (F.bitdepth == 8)
-                process_block<uint8_t>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch);
+                process_block<uint8_t>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch, stage);
             else
-                process_block<uint16_t>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch);
+                process_block<uint16_t>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch, stage);
             __syncthreads();  // shared tiles, tables and the next block id are settled
         }
     }

@@ -209,14 +209,25 @@ __device__ __forceinline__ int wentry(int N, int lane)
 // entries (those blocks unfiltered) follow as base + total - uncoded part.
 // kSub: a subset of the pairs is allowed (section 5's low-complexity
 // search): primaries without an allowed pair are skipped.
-template <typename T, int kG, bool kCoded, bool kEq14, bool kSub>
+// kPl: 8/10-bit 4:4:4 frames, one plane per work unit (grp: 0 luma, 1 U,
+// 2 V).  Each plane's tile is staged and filtered in the luma layout (a
+// 4:4:4 chroma plane has the luma geometry and takes the chroma strengths,
+// section 3.2, with the co-located luma direction, read from the direction
+// map `mdir`, `mvar`); U's and V's entries are added into the chroma table,
+// which the caller zeroes first.
+template <typename T, int kG, bool kCoded, bool kEq14, bool kSub, bool kPl = false>
 __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_global, int grp,
                            SearchSmem &sm, RawTiles &raw, long long *dist_luma,
-                           long long *dist_chroma, uint8_t *skipped CDEF_DEBUG_PARAM(int *status))
+                           long long *dist_chroma, uint8_t *skipped, const uint8_t *mdir,
+                           const int32_t *mvar CDEF_DEBUG_PARAM(int *status))
 {
+    static_assert(!kPl || (kG == 1 && !kEq14) || (kG == 8 && kEq14 && !kCoded),
+                  "plane units: squared-error tables, or eq. 14 over 64 pairs");
+    const int plane = kPl ? grp : 0;
+    const bool cparams = kPl && plane > 0;   // a 4:4:4 chroma plane in the luma layout
     constexpr int kPP = 16 / kG;           // primary strengths per unit
     constexpr int kN = 4 * kPP;            // candidates per plane group
-    const int p0_unit = kG == 1 ? 0 : grp * kPP;
+    const int p0_unit = (kG == 1 || kPl) ? 0 : grp * kPP;
     const int sh8 = F.bitdepth - 8;
     const int W = F.w, H = F.h, CW = F.w >> 1, CH = F.h >> 1;
     const int ly0 = fby * 64, lx0 = fbx * 64, cy0 = fby * 32, cx0 = fbx * 32;
@@ -224,11 +235,11 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
     const int D = F.damping;
 
     const bool border = fby == 0 || fbx == 0 || ly0 + 66 > H || lx0 + 66 > W ||
-                        cy0 + 34 > CH || cx0 + 34 > CW;
-    stage_relayout<T, kThreads>(sm.t, raw, border, ly0, lx0, H, W, cy0, cx0, CH, CW);
+                        (!kPl && (cy0 + 34 > CH || cx0 + 34 > CW));
+    stage_relayout<T, kThreads>(sm.t, raw, border, ly0, lx0, H, W, cy0, cx0, CH, CW, !kPl);
     __syncthreads();
 
-    {   // direction search: four threads per 8x8 block, two directions each
+    if (!kPl) {   // direction search: four threads per 8x8 block, two directions each
         const int b = (warp >> 2) * 32 + lane;
         switch (warp & 3) {
         case 0: dir_costs<0>(sm.t.le, b, sh8, sm.cost); break;
@@ -236,15 +247,23 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         case 2: dir_costs<2>(sm.t.le, b, sh8, sm.cost); break;
         default: dir_costs<3>(sm.t.le, b, sh8, sm.cost); break;
         }
+        __syncthreads();
     }
-    __syncthreads();
     if (tid < 64) {
-        int best = 0, bc = sm.cost[tid][0];
+        if (kPl) {   // the luma direction and contrast from the map
+            const int gby = fby * 8 + (tid >> 3), gbx = fbx * 8 + (tid & 7);
+            const bool in = gby * 8 < H && gbx * 8 < W;
+            const int m = F.map_start + gby * (W >> 3) + gbx;
+            sm.dir[tid] = in ? mdir[m] : 0;
+            sm.var[tid] = in ? mvar[m] : 0;
+        } else {
+            int best = 0, bc = sm.cost[tid][0];
 #pragma unroll
-        for (int k = 1; k < 8; k++)
-            if (sm.cost[tid][k] > bc) { bc = sm.cost[tid][k]; best = k; }
-        sm.dir[tid] = (uint8_t)best;
-        sm.var[tid] = bc - sm.cost[tid][(best + 4) & 7];
+            for (int k = 1; k < 8; k++)
+                if (sm.cost[tid][k] > bc) { bc = sm.cost[tid][k]; best = k; }
+            sm.dir[tid] = (uint8_t)best;
+            sm.var[tid] = bc - sm.cost[tid][(best + 4) & 7];
+        }
         sm.acc[tid] = 0;
         sm.accu[tid] = 0;
         if (tid < 8) sm.acc14c[tid] = 0;
@@ -344,9 +363,13 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
             const int4 *op = reinterpret_cast<const int4 *>(sm.off[task][sm.dir[blk]]);
             const int4 o0 = op[0], o1 = op[1], o2 = op[2];
             const int o[12] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w, o2.x, o2.y, o2.z, o2.w};
-            const SetC *ps = luma ? sm.pset[blk] : sm.cset;
-            const uint32_t bits = luma ? sm.pbits[blk] : sm.cbits;
-            const uint32_t raised = luma ? 0u : sm.craised;
+            // the parameters: luma's, or the chroma planes' (4:2:0 chroma, or
+            // a 4:4:4 chroma plane in the luma layout); ptask: the table
+            const bool lp = luma && !cparams;
+            const int ptask = lp ? 0 : 1;
+            const SetC *ps = lp ? sm.pset[blk] : sm.cset;
+            const uint32_t bits = lp ? sm.pbits[blk] : sm.cbits;
+            const uint32_t raised = lp ? 0u : sm.craised;
             // eq. 14: the secondary sums of the thread's words are formed in
             // the task's first candidate group and kept for the others: luma
             // S_s = 1, 2 in the block's tile buffer (idle once the tiles are
@@ -359,20 +382,21 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 if (kL) return s < 3 ? idle[((s - 1) * 8 + i) * kThreads + tid] : sm.qc[i * kThreads + tid];
                 return sm.qc[((s - 1) * 4 + i) * kThreads + tid];
             };
+            // (4:2:0 chroma only: rows i < 4)
             auto rslot = [&](int s, int i) -> uint32_t & { return idle[((s - 1) * 4 + i) * kThreads + tid]; };
-            const SetC *ss = luma ? sm.sset[0] : sm.sset[1];
+            const SetC *ss = lp ? sm.sset[0] : sm.sset[1];
             SetC s7 = {};
-            if (kCoded) s7 = luma ? sm.s7[blk] : sm.s7c;
+            if (kCoded) s7 = lp ? sm.s7[blk] : sm.s7c;
             const int oy = luma ? ly0 + warp * 8 : cy0 + warp * 4;
             const int ox = luma ? lx0 + bx * 8 + 2 * sub : cx0 + bx * 4 + sub;
-            const uint8_t *sa = luma ? F.src[0] : F.src[1];
-            const int64_t spa = luma ? F.src_pitch[0] : F.src_pitch[1];
+            const uint8_t *sa = luma ? (kPl ? F.src[plane] : F.src[0]) : F.src[1];
+            const int64_t spa = luma ? (kPl ? F.src_pitch[plane] : F.src_pitch[0]) : F.src_pitch[1];
 
             // section 5's low-complexity search: primaries with no allowed pair
             // are not evaluated, entries of pairs outside the subset are 0
             uint32_t pmask = 0xffffu;
             if (kSub) {
-                const unsigned long long pairs = allowed_pairs(F, task);
+                const unsigned long long pairs = allowed_pairs(F, ptask);
                 pmask = 0;
     #pragma unroll
                 for (int p = 0; p < 16; p++) pmask |= (uint32_t)(((pairs >> (4 * p)) & 15ull) != 0) << p;
@@ -447,10 +471,12 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                         for (int s = 1; s < 4; s++) Q[s] = qslot(s, i);
                     }
                     if (raised) {
-                        if (!kEq14 || g == 0) {
+                        // kept for 4:2:0 chroma (4 rows); a 4:4:4 chroma plane in
+                        // the luma layout (8 rows) forms them in every group
+                        if (!kEq14 || g == 0 || kL) {
     #pragma unroll
                             for (int s = 1; s < 4; s++) Qr[s] = sec_sum(v, X, sm.sset[2][s]);
-                            if (kEq14) {
+                            if (kEq14 && !kL) {
     #pragma unroll
                                 for (int s = 1; s < 4; s++) rslot(s, i) = Qr[s];
                             }
@@ -646,18 +672,28 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                 __syncthreads();
                 if (tid < kN) {
                     const long long base_sse = (long long)sm.base[task];
-                    const bool on = (allowed_pairs(F, task) >> (4 * p0 + tid)) & 1;
+                    const bool on = (allowed_pairs(F, ptask) >> (4 * p0 + tid)) & 1;
+                    // a 4:4:4 chroma plane's entries are added into the zeroed
+                    // chroma table (U and V): every entry is linear in the
+                    // plane's sums
+                    auto put = [&](long long *p, long long v) {
+                        if (kPl && cparams) {
+                            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+                        } else {
+                            *p = v;
+                        }
+                    };
                     if (!kCoded) {
-                        long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
-                        out[tid] = on ? (long long)sm.acc[tid] + base_sse : 0;
+                        long long *out = (lp ? dist_luma : dist_chroma) + (int64_t)blk_global * 64 + 4 * p0;
+                        put(&out[tid], on ? (long long)sm.acc[tid] + base_sse : 0);
                     } else {
                         // q = k * 64 + p * 4 + s; skip bit clear: blocks without coded
                         // residual unfiltered, (0, 0) the unfiltered error
-                        long long *out = (luma ? dist_luma : dist_chroma) + (int64_t)blk_global * 128 +
+                        long long *out = (lp ? dist_luma : dist_chroma) + (int64_t)blk_global * 128 +
                                          4 * p0 + tid;
                         const long long tot = (long long)sm.acc[tid], un = (long long)sm.accu[tid];
-                        out[0] = !on ? 0 : (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un;
-                        out[64] = !on ? 0 : !any_coded ? base_sse : base_sse + tot;
+                        put(&out[0], !on ? 0 : (!any_coded || (p0 == 0 && tid == 0)) ? base_sse : base_sse + tot - un);
+                        put(&out[64], !on ? 0 : !any_coded ? base_sse : base_sse + tot);
                     }
                     sm.acc[tid] = 0;
                     sm.accu[tid] = 0;
@@ -667,23 +703,29 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
         };
         if constexpr (!kEq14) {
             task_body(std::true_type{}, 0);
-            task_body(std::false_type{}, 0);
+            if (!kPl) task_body(std::false_type{}, 0);
         } else {
             // eq. 14: the luma groups, then the chroma groups (each task's
             // secondary sums are formed in its first group and kept)
 #pragma unroll 1
             for (int g = 0; g < kGl; g++) {
                 task_body(std::true_type{}, g);
-                if (tid < 4 * kPPl) {   // the group's luma candidates
+                if (tid < 4 * kPPl) {   // the group's luma-layout candidates
                     const int q = 4 * kPPl * g + tid;
-                    const bool on = (allowed_pairs(F, 0) >> q) & 1;
-                    dist_luma[(int64_t)blk_global * 64 + q] = on ? (long long)sm.acc[tid] : 0;
+                    const bool on = (allowed_pairs(F, cparams ? 1 : 0) >> q) & 1;
+                    if (kPl && cparams) {   // a 4:4:4 chroma plane: into the zeroed chroma table
+                        if (on)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(
+                                          &dist_chroma[(int64_t)blk_global * 64 + q]), sm.acc[tid]);
+                    } else {
+                        dist_luma[(int64_t)blk_global * 64 + q] = on ? (long long)sm.acc[tid] : 0;
+                    }
                     sm.acc[tid] = 0;
                 }
                 __syncthreads();
             }
 #pragma unroll 1
-            for (int g = 0; g < kG; g++) {
+            for (int g = 0; g < (kPl ? 0 : kG); g++) {
                 task_body(std::false_type{}, g);
                 // chroma 8x8 blocks: two planes x 16 blocks x the group's
                 // candidates, one per thread; lanes 8 apart hold the same
@@ -731,24 +773,32 @@ __device__ __forceinline__ SBlockRef slocate(const SearchBatch &batch, int blk)
     return {fi, fby + batch.f[fi].fb_row0, local - fby * batch.f[fi].fb_cols};
 }
 
-__device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTiles &raw, uint64_t *bar)
+// The tile loads of filter block `blk` (plane < 0: its luma and 4:2:0 chroma
+// tiles; else the one plane, whose map has the luma box).
+__device__ __forceinline__ void sissue(const SearchBatch &batch, int blk, RawTiles &raw, uint64_t *bar,
+                                       int plane = -1)
 {
     const SBlockRef r = slocate(batch, blk);
     const SearchFrameDev &F = batch.f[r.fi];
-    issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar, true, batch.waits.extra_tx);
+    if (plane < 0)
+        issue_tile_loads(F.tmap, F.bitdepth, r.fby, r.fbx, raw, bar, true, batch.waits.extra_tx);
+    else
+        issue_tile_loads(&F.tmap[plane], F.bitdepth, r.fby, r.fbx, raw, bar, false, batch.waits.extra_tx);
 }
 
 // Persistent distortion kernel (same work-counter scheme as the filter).
 // Work unit u is filter block u / kG, primary-strength group u % kG.
-template <int kG, bool kCoded, bool kEq14, bool kSub>
+template <int kG, bool kCoded, bool kEq14, bool kSub, bool kPl = false>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
 dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, long long *dist_chroma,
-            uint8_t *skipped, int *status, unsigned *work)
+            uint8_t *skipped, int *status, unsigned *work, const uint8_t *mdir, const int32_t *mvar)
 {
     extern __shared__ __align__(128) uint8_t smem_bytes[];
     SearchSmem &sm = *reinterpret_cast<SearchSmem *>(smem_bytes);
     const int tid = threadIdx.x;
-    constexpr int kUnits = kEq14 ? 1 : kG;   // work units per filter block
+    // work units per filter block: its primary-strength groups, or (kPl) its
+    // three planes
+    constexpr int kUnits = kPl ? 3 : kEq14 ? 1 : kG;
     const int total = batch.total_blocks * kUnits;
 
     if (smem_u32(smem_bytes) & 127) {
@@ -759,7 +809,7 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             mbar_init(&sm.bar[1], 1);
             const int b = (int)atomicAdd(&work[0], 1u);
             sm.blk[0] = b;
-            if (b < total) sissue(batch, b / kUnits, sm.raw[0], &sm.bar[0]);
+            if (b < total) sissue(batch, b / kUnits, sm.raw[0], &sm.bar[0], kPl ? b % kUnits : -1);
         }
         if (tid < 192) {
             const int pl = tid / 96, d = (tid / 12) & 7, t = tid % 12;
@@ -775,7 +825,8 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             if (tid == 0) {
                 const int nb = (int)atomicAdd(&work[0], 1u);
                 sm.blk[buf ^ 1] = nb;
-                if (nb < total) sissue(batch, nb / kUnits, sm.raw[buf ^ 1], &sm.bar[buf ^ 1]);
+                if (nb < total)
+                    sissue(batch, nb / kUnits, sm.raw[buf ^ 1], &sm.bar[buf ^ 1], kPl ? nb % kUnits : -1);
             }
             const bool arrived = mbar_wait_bounded(&sm.bar[buf], (it >> 1) & 1, batch.waits.wait_cycles);
             if (__syncthreads_or(!arrived)) {
@@ -792,13 +843,13 @@ dist_kernel(const __grid_constant__ SearchBatch batch, long long *dist_luma, lon
             const SBlockRef r = slocate(batch, fb);
             const SearchFrameDev &F = batch.f[r.fi];
             if (F.bitdepth == 8)
-                dist_block<uint8_t, kG, kCoded, kEq14, kSub>(F, r.fby, r.fbx, fb, grp, sm,
-                                                             sm.raw[buf], dist_luma, dist_chroma,
-                                                             skipped CDEF_DEBUG_ARG(status));
+                dist_block<uint8_t, kG, kCoded, kEq14, kSub, kPl>(F, r.fby, r.fbx, fb, grp, sm,
+                                                                  sm.raw[buf], dist_luma, dist_chroma,
+                                                                  skipped, mdir, mvar CDEF_DEBUG_ARG(status));
             else
-                dist_block<uint16_t, kG, kCoded, kEq14, kSub>(F, r.fby, r.fbx, fb, grp, sm,
-                                                              sm.raw[buf], dist_luma, dist_chroma,
-                                                              skipped CDEF_DEBUG_ARG(status));
+                dist_block<uint16_t, kG, kCoded, kEq14, kSub, kPl>(F, r.fby, r.fbx, fb, grp, sm,
+                                                                   sm.raw[buf], dist_luma, dist_chroma,
+                                                                   skipped, mdir, mvar CDEF_DEBUG_ARG(status));
             __syncthreads();
         }
     }
@@ -816,14 +867,14 @@ constexpr size_t kSmemBytes = sizeof(SearchSmem);
 
 // Persistent grid: `per_sm` CTAs on every SM (at most what fits), never more
 // CTAs than work units.
-template <int kG, bool kCoded, bool kEq14, bool kSub>
+template <int kG, bool kCoded, bool kEq14, bool kSub, bool kPl = false>
 int dist_grid(int units, int per_sm)
 {
     static int cached_dev = -1, cached_sms = 0, cached_occ = 1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != cached_dev) {
-        auto *kern = dist_kernel<kG, kCoded, kEq14, kSub>;
+        auto *kern = dist_kernel<kG, kCoded, kEq14, kSub, kPl>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
@@ -838,13 +889,14 @@ int dist_grid(int units, int per_sm)
     return units < ctas ? units : ctas;
 }
 
-template <int kG, bool kCoded, bool kEq14, bool kSub>
+template <int kG, bool kCoded, bool kEq14, bool kSub, bool kPl = false>
 void launch_dist_kernel(const SearchBatch &b, long long *dl, long long *dc, uint8_t *skipped,
-                        int *status, unsigned *work, int units, int per_sm, cudaStream_t s)
+                        int *status, unsigned *work, int units, int per_sm, cudaStream_t s,
+                        const uint8_t *mdir = nullptr, const int32_t *mvar = nullptr)
 {
-    dist_kernel<kG, kCoded, kEq14, kSub><<<dist_grid<kG, kCoded, kEq14, kSub>(units, per_sm),
-                                           kThreads, kSmemBytes, s>>>(b, dl, dc, skipped, status,
-                                                                      work);
+    dist_kernel<kG, kCoded, kEq14, kSub, kPl><<<dist_grid<kG, kCoded, kEq14, kSub, kPl>(units, per_sm),
+                                                kThreads, kSmemBytes, s>>>(b, dl, dc, skipped, status,
+                                                                           work, mdir, mvar);
 }
 
 // Whether the call searches a subset of the pairs (the same for every frame).
@@ -865,6 +917,37 @@ cudaError_t launch_dist(const SearchBatch &b, long long *dl, long long *dc, uint
     } else {
         if (sub) launch_dist_kernel<kG, false, false, true>(b, dl, dc, nullptr, status, work, units, per_sm, s);
         else launch_dist_kernel<kG, false, false, false>(b, dl, dc, nullptr, status, work, units, per_sm, s);
+    }
+    return cudaGetLastError();
+}
+
+// 8/10-bit 4:4:4 squared-error tables: one work unit per filter block and
+// plane, the planes in the luma layout; the chroma table is zeroed first
+// (U and V add into it) and the direction maps are formed first.
+cudaError_t launch_dist_planes(const SearchBatch &b, uint8_t *dirs, int32_t *vars, long long *dl,
+                               long long *dc, uint8_t *skipped, int *status, unsigned *work,
+                               cudaStream_t s, bool eq14)
+{
+    for (int i = 0; i < b.n; i++) {
+        const SearchFrameDev &F = b.f[i];
+        const cudaError_t e = launch_find_dir(F.rec[0], F.rec_pitch[0], F.w, F.h, F.bitdepth,
+                                              dirs + F.map_start, vars + F.map_start, s);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t width = skipped ? 128 : 64;
+    cudaError_t e = cudaMemsetAsync(dc, 0, sizeof(long long) * width * (size_t)b.total_blocks, s);
+    if (e != cudaSuccess) return e;
+    const int units = b.total_blocks * 3;
+    const bool sub = subset_search(b);
+    if (eq14) {   // eq. 14 (64 pairs): the luma-layout groups of each plane
+        if (sub) launch_dist_kernel<8, false, true, true, true>(b, dl, dc, nullptr, status, work, units, 2, s, dirs, vars);
+        else launch_dist_kernel<8, false, true, false, true>(b, dl, dc, nullptr, status, work, units, 2, s, dirs, vars);
+    } else if (skipped) {
+        if (sub) launch_dist_kernel<1, true, false, true, true>(b, dl, dc, skipped, status, work, units, 2, s, dirs, vars);
+        else launch_dist_kernel<1, true, false, false, true>(b, dl, dc, skipped, status, work, units, 2, s, dirs, vars);
+    } else {
+        if (sub) launch_dist_kernel<1, false, false, true, true>(b, dl, dc, nullptr, status, work, units, 2, s, dirs, vars);
+        else launch_dist_kernel<1, false, false, false, true>(b, dl, dc, nullptr, status, work, units, 2, s, dirs, vars);
     }
     return cudaGetLastError();
 }
@@ -928,6 +1011,16 @@ cudaError_t launch_search(const SearchBatch &b, long long *dist_luma, long long 
     cudaError_t e = stage_mark(stage_events, 0, s);
     if (e != cudaSuccess) return e;
     const int per_sm = tune.ctas_per_sm;
+    if (wide_dirs && b.planes) {   // 8/10-bit 4:4:4 frames
+        const bool eq14 = tune.groups == 8;   // the eq. 14 tables
+        e = launch_dist_planes(b, wide_dirs, wide_vars, dist_luma, dist_chroma, skipped, status, work,
+                               s, eq14);
+        if (e == cudaSuccess) e = stage_mark(stage_events, 1, s);
+        if (e != cudaSuccess || tables_only) return e;
+        e = select_presets(b, dist_luma, dist_chroma, cur, tot, results, block_ids, status,
+                           refine_passes, skipped ? 128 : 64, skipped, !eq14, grid_presets, s);
+        return e == cudaSuccess ? stage_mark(stage_events, 2, s) : e;
+    }
     if (wide_dirs) {   // 4:2:2, 4:4:4 or 12-bit frames
         const bool eq14 = tune.groups == 8;   // the eq. 14 tables
         e = launch_search_wide(b, wide_dirs, wide_vars, dist_luma, dist_chroma, skipped, s, eq14,

@@ -580,6 +580,48 @@ def test_filter_chroma_formats(cdef, ctx, ref, fmt, w, h, bd, with_map):
     _assert_frames_equal(out.to_numpy(), ref.filter_frame_format(*planes, bd, params, fmt, coded))
 
 
+@pytest.mark.parametrize("bd", [8, 10])
+def test_filter_444_consecutive_and_given_maps(cdef, ctx, ref, bd):
+    """8/10-bit 4:4:4 frames filtered by the three-plane launch: four frames
+    back to back on one stream with overlapped launches (each its own
+    output), then the same frames with caller-supplied direction maps; every
+    output sample equals the oracle's."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(960 + bd)
+    sizes = [(136, 72), (200, 136), (64, 64), (72, 40)]
+    frames, exps, prms = [], [], []
+    for k, (w, h) in enumerate(sizes):
+        f = synth.make_frame(w, h, bd, 32, seed=970 + k, chroma=444)
+        params = synth.random_params(rng, w, h)
+        frames.append(f)
+        prms.append(params)
+        exps.append(ref.filter_frame_format(*f.rec, bd, params, 444))
+    ins = [cdef.frame_from_numpy(f.rec, bd) for f in frames]
+    s = torch.cuda.Stream()
+    for given in (False, True):
+        outs = [cdef.alloc_frame(f.width, f.height, bd, fill=0, chroma=444) for f in frames]
+        maps = []
+        ctx.set_overlap(not given)
+        try:
+            with torch.cuda.stream(s):
+                for i, (f, inp) in enumerate(zip(frames, ins)):
+                    if given:
+                        d = torch.zeros((f.height // 8) * (f.width // 8), dtype=torch.uint8, device="cuda")
+                        v = torch.zeros_like(d, dtype=torch.int32)
+                        cdef.cdef_find_dir(ctx, inp.y, f.width, f.height, bd, d, v, stream=s)
+                        maps.append((d, v))
+                        cdef.cdef_filter_frame(ctx, inp, cdef.params_tensor(prms[i]), outs[i], d, v,
+                                               stream=s)
+                    else:
+                        cdef.cdef_filter_frame(ctx, inp, cdef.params_tensor(prms[i]), outs[i], stream=s)
+            torch.cuda.synchronize()
+        finally:
+            ctx.set_overlap(False)
+        assert ctx.status() == 0
+        for o, e in zip(outs, exps):
+            _assert_frames_equal(o.to_numpy(), e)
+
+
 def test_chroma_formats_rejected_where_unsupported(cdef, ctx):
     from paper_1602_05975_gb300 import synth
     f = synth.make_frame(64, 64, 8, 32, seed=960)
@@ -929,6 +971,43 @@ def test_search_formats_subset_and_rejections(cdef, ctx, ref):
     assert ctx.status() == 0
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("passes,grid", [(0, 0), (2, 0), (2, 1)])
+def test_search_444_planes_parity(cdef, ctx, ref, passes, grid):
+    """8/10-bit 4:4:4 calls (every frame 4:4:4: one plane per work unit in
+    the packed layout, U and V added into the chroma table): ragged, 8x8 and
+    one-block frames; tables, presets, N, J and ids equal the oracle's."""
+    specs = [(444, 136, 72, 8, 1160), (444, 64, 64, 10, 1161), (444, 200, 136, 8, 1162),
+             (444, 8, 8, 10, 1163), (444, 72, 40, 8, 1164)]
+    frames = [_format_search_frame(cdef, *sp) for sp in specs]
+    damping, lambdas = [5, 3, 6, 4, 5], [64, 0, 4096, 900, 300]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f, _, _ in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.full((nb * 64,), -1, dtype=torch.int64, device="cuda")
+    dc = torch.full((nb * 64,), -1, dtype=torch.int64, device="cuda")
+    ctx.set_search_refine(passes)
+    ctx.set_tuning(0, 0, preset_kernel=grid)
+    try:
+        res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(r, f.bitdepth) for f, r, _ in frames],
+                                         [cdef.frame_from_numpy(s_, f.bitdepth) for f, _, s_ in frames],
+                                         damping, lambdas, ids, dl, dc)
+    finally:
+        ctx.set_tuning(0, 0)
+        ctx.set_search_refine(0)
+    assert ctx.status() == 0
+    o0 = 0
+    for (f, r, s_), sp, rr, d, lam in zip(frames, specs, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths_format(r, s_, f.bitdepth, d, lam, sp[0], passes)
+        assert np.array_equal(dl[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_luma"])
+        assert np.array_equal(dc[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64), o["dist_chroma"])
+        assert rr["npresets"] == o["npresets"] and rr["cost"] == o["cost"]
+        assert [cdef.preset_index(p) for p in rr["presets"][:rr["npresets"]]] == \
+            [int(t) for t in o["presets"][:o["npresets"]]]
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
+
+
 @pytest.mark.parametrize("passes", [0, 2])
 def test_search_eq14_formats_parity(cdef, ctx, ref, passes):
     """Eq. 14 tables of 4:4:4, 4:2:2 and 12-bit frames (and an 8-bit 4:2:0
@@ -969,6 +1048,59 @@ def test_search_eq14_formats_parity(cdef, ctx, ref, passes):
         assert [cdef.preset_index(p) for p in rr["presets"][:rr["npresets"]]] == \
             [int(t) for t in o["presets"][:o["npresets"]]]
         assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("passes,subset", [(0, False), (2, False), (0, True)])
+def test_search_444_planes_eq14_parity(cdef, ctx, ref, passes, subset):
+    """Eq. 14 over 8/10-bit 4:4:4 calls (one plane per work unit, each plane's
+    8x8 values in the luma layout, U and V added into the chroma table):
+    tables within the precision bound of the double-precision oracle's;
+    presets, N, J and ids exactly the oracle's selection on the GPU's own
+    tables; with a subset, the entries outside it are 0."""
+    specs = [(444, 136, 72, 8, 1200), (444, 64, 64, 10, 1201), (444, 72, 40, 8, 1202)]
+    frames = [_format_search_frame(cdef, *sp) for sp in specs]
+    damping, lambdas = [5, 3, 6], [64 << 8, 0, 900 << 8]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f, _, _ in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.full((nb * 64,), -1, dtype=torch.int64, device="cuda")
+    dc = torch.full((nb * 64,), -1, dtype=torch.int64, device="cuda")
+    lmask, cmask = sum(1 << q for q in (0, 5, 9, 33, 62)), sum(1 << q for q in (1, 2, 40, 63))
+    ctx.set_search_metric("eq14")
+    ctx.set_search_refine(passes)
+    if subset:
+        ctx.set_search_subset(lmask, cmask)
+    try:
+        res = cdef.cdef_search_strengths(ctx, [cdef.frame_from_numpy(r, f.bitdepth) for f, r, _ in frames],
+                                         [cdef.frame_from_numpy(s_, f.bitdepth) for f, _, s_ in frames],
+                                         damping, lambdas, ids, dl, dc)
+    finally:
+        ctx.set_search_metric("sse")
+        ctx.set_search_refine(0)
+        ctx.set_search_subset()
+    assert ctx.status() == 0
+    cl = np.array([(lmask >> q) & 1 for q in range(64)], bool) if subset else np.ones(64, bool)
+    cc = np.array([(cmask >> q) & 1 for q in range(64)], bool) if subset else np.ones(64, bool)
+    o0 = 0
+    for (f, r, s_), sp, rr, d, lam in zip(frames, specs, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        gl = dl[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64)
+        gc = dc[o0 * 64:(o0 + b) * 64].cpu().numpy().reshape(b, 64)
+        el, ec = ref.distortion_eq14_format(r, s_, f.bitdepth, d, 444)
+        nl, nc = _eq14_term_counts(f.width, f.height, 444)
+        _assert_eq14_tables_close(gl, el, nl, cols=np.flatnonzero(cl))
+        _assert_eq14_tables_close(gc, ec, nc, cols=np.flatnonzero(cc))
+        assert (gl[:, ~cl] == 0).all() and (gc[:, ~cc] == 0).all()
+        if subset:
+            o = ref.select_presets_subset(gl, gc, 64, None, lmask, cmask, lam, passes)
+        else:
+            o = ref.select_presets_general(gl, gc, 64, None, lam, passes)
+        assert rr["npresets"] == o["npresets"] and rr["cost"] == o["cost"]
+        if not subset:
+            assert [cdef.preset_index(p) for p in rr["presets"][:rr["npresets"]]] == \
+                [int(t) for t in o["presets"][:o["npresets"]]]
+            assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
         o0 += b
 
 
@@ -1131,6 +1263,53 @@ def test_search_coded_formats_parity(cdef, ctx, ref):
     for (f, r, s_), sp, m, rr, d, lam in zip(frames, specs, maps, res, damping, lambdas):
         b = f.params.shape[0] * f.params.shape[1]
         o = ref.search_strengths_coded_format(r, s_, f.bitdepth, d, lam, sp[0], m, 2)
+        assert np.array_equal(dl[o0 * 128:(o0 + b) * 128].cpu().numpy().reshape(b, 128),
+                              o["dist_luma"])
+        assert np.array_equal(dc[o0 * 128:(o0 + b) * 128].cpu().numpy().reshape(b, 128),
+                              o["dist_chroma"])
+        assert rr["npresets"] == o["npresets"] and rr["cost"] == o["cost"]
+        assert [cdef.preset_index_coded(p) for p in rr["presets"][:rr["npresets"]]] == \
+            [int(t) for t in o["presets"][:o["npresets"]]]
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("passes,grid", [(0, 0), (2, 1)])
+def test_search_444_planes_coded_parity(cdef, ctx, ref, passes, grid):
+    """The 128-combination search over 8/10-bit 4:4:4 calls (one plane per
+    work unit, U and V added into the chroma table, both skip-bit halves):
+    tables, skipped blocks, presets, N, J and ids equal the oracle's; a
+    filter block without coded residual and ragged frames included."""
+    specs = [(444, 136, 72, 8, 1190), (444, 64, 64, 10, 1191), (444, 200, 136, 8, 1192),
+             (444, 72, 40, 10, 1193)]
+    frames = [_format_search_frame(cdef, *sp) for sp in specs]
+    rng = np.random.default_rng(1194)
+    maps = []
+    for f, _, _ in frames:
+        m = (rng.random((f.height // 8, f.width // 8)) < 0.5).astype(np.uint8)
+        m[:8, :8] = 0                                       # first filter block: no residual
+        maps.append(m)
+    damping, lambdas = [5, 4, 3, 6], [64, 512, 4096, 0]
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f, _, _ in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.full((nb * 128,), -1, dtype=torch.int64, device="cuda")
+    dc = torch.full((nb * 128,), -1, dtype=torch.int64, device="cuda")
+    ctx.set_search_refine(passes)
+    ctx.set_tuning(0, 0, preset_kernel=grid)
+    try:
+        res = cdef.cdef_search_strengths_coded(
+            ctx, [cdef.frame_from_numpy(r, f.bitdepth) for f, r, _ in frames],
+            [cdef.frame_from_numpy(s_, f.bitdepth) for f, _, s_ in frames],
+            [torch.from_numpy(m.reshape(-1)).cuda() for m in maps], damping, lambdas, ids, dl, dc)
+    finally:
+        ctx.set_tuning(0, 0)
+        ctx.set_search_refine(0)
+    assert ctx.status() == 0
+    o0 = 0
+    for (f, r, s_), sp, m, rr, d, lam in zip(frames, specs, maps, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        o = ref.search_strengths_coded_format(r, s_, f.bitdepth, d, lam, sp[0], m, passes)
         assert np.array_equal(dl[o0 * 128:(o0 + b) * 128].cpu().numpy().reshape(b, 128),
                               o["dist_luma"])
         assert np.array_equal(dc[o0 * 128:(o0 + b) * 128].cpu().numpy().reshape(b, 128),
