@@ -610,7 +610,7 @@ int filter_one(cdef_ctx *ctx, const cdef_frame *in, const cdef_fb_params *params
         b.waits = wait_limits();
         if ((rc = fill_444_dev(b.f[0], in, out, params, dir, var, coded))) return rc;
         unsigned *work = ctx->work + 2 * (1 + ctx->next_slot++ % (kWorkSlots - 1));  // pair 0: search
-        return cuda_status(launch_filter_single(b, ctx->status, work, ctx->overlap, s));
+        return cuda_status(launch_filter_444(b, ctx->status, work, ctx->overlap, s));
     }
     // 12-bit 4:4:4: the luma directions first (unless given), then the three
     // planes in the luma geometry as one launch, which waits for the maps

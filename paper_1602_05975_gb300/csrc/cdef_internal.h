@@ -130,6 +130,9 @@ cudaError_t launch_filter_single(const FilterBatch<1> &b, int *status, unsigned 
                                  bool overlap, cudaStream_t s);
 cudaError_t launch_filter_batch(const FilterBatch<kMaxFilterBatch> &b, int *status,
                                 unsigned *work, bool overlap, cudaStream_t s);
+// One 8/10-bit 4:4:4 frame in mode 3 (its own kernel instantiation).
+cudaError_t launch_filter_444(const FilterBatch<1> &b, int *status, unsigned *work, bool overlap,
+                              cudaStream_t s);
 // The three planes of a 4:4:4 frame (entries in modes 1, 2, 2) in one launch.
 cudaError_t launch_filter_planes(const FilterBatch<3> &b, int *status, unsigned *work,
                                  bool overlap, cudaStream_t s);

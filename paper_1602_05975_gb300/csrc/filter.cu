@@ -320,10 +320,13 @@ __device__ __noinline__ void filter_wide(const FilterFrameDev &F, int fby, int f
 // per-block parameters, filtering and stores of one 64x64 filter block.
 // `prefetch` runs (on every thread) once the raw tiles have been re-laid,
 // so that the next block's tiles can land in the same buffer.
-template <typename T, typename Prefetch>
+// kM3: frame mode 3 (the plane `stage` of an 8/10-bit 4:4:4 block); other
+// modes are compiled with stage 0, so their code carries no stage logic.
+template <typename T, bool kM3, typename Prefetch>
 __device__ void process_block(const FilterFrameDev &F, int fby, int fbx, int *status,
-                              FilterSmem &sm, const RawTiles &raw, Prefetch prefetch, int stage)
+                              FilterSmem &sm, const RawTiles &raw, Prefetch prefetch, int stage_in)
 {
+    const int stage = kM3 ? stage_in : 0;
     const int sh8 = F.bitdepth - 8;
     const int W = F.p[0].w, H = F.p[0].h, CW = F.p[1].w, CH = F.p[1].h;
     const int ly0 = fby * 64, lx0 = fbx * 64;
@@ -512,7 +515,9 @@ __device__ __forceinline__ void issue_loads(const FilterBatch<MAXF> &batch, int 
 // its next block are loaded while it filters the current one.  The last CTA
 // to finish resets the counter pair (work[1] counts finished CTAs), so a
 // counter slot is ready for its next launch.
-template <int MAXF>
+// kM3: the launch of one mode-3 frame (8/10-bit 4:4:4, the three planes of
+// a filter block in turn); other launches are compiled without the stages.
+template <int MAXF, bool kM3 = false>
 __global__ void __launch_bounds__(kThreads, kMinCtas)
 filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsigned *work,
               int dep_wait)
@@ -552,7 +557,7 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
         // then block n+1's loads are issued into the buffer while block n is
         // searched and filtered
         for (int it = 0;; it++) {
-            const int blk = sm.blk_next, stage = sm.stage_next;
+            const int blk = sm.blk_next, stage = kM3 ? sm.stage_next : 0;
             if (blk >= total) break;
             const bool arrived = mbar_wait_bounded(&sm.bar, it & 1, batch.waits.wait_cycles);
             if (__syncthreads_or(!arrived)) {  // the whole CTA leaves together
@@ -566,7 +571,7 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
             const FilterFrameDev &F = batch.f[r.fi];
             auto prefetch = [&]() {
                 if (tid == 0) {
-                    if (F.mode == 3 && stage < 2) {   // the block's next plane
+                    if (kM3 && stage < 2) {   // the block's next plane
                         sm.stage_next = stage + 1;
                         issue_loads(batch, blk, sm.raw, &sm.bar, stage + 1);
                     } else {
@@ -578,9 +583,9 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
                 }
             };
             if (F.bitdepth == 8)
-                process_block<uint8_t>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch, stage);
+                process_block<uint8_t, kM3>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch, stage);
             else
-                process_block<uint16_t>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch, stage);
+                process_block<uint16_t, kM3>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch, stage);
             __syncthreads();  // shared tiles, tables and the next block id are settled
         }
     }
@@ -598,32 +603,32 @@ constexpr size_t kSmemBytes = sizeof(FilterSmem);
 
 // Grid size: one wave of persistent CTAs (resident CTAs per SM x SMs),
 // never more than the work.
-template <int MAXF>
+template <int MAXF, bool kM3 = false>
 int persistent_grid(int total)
 {
     static int cached_dev = -1, cached_ctas = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != cached_dev) {
-        cudaFuncSetAttribute(filter_kernel<MAXF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(filter_kernel<MAXF, kM3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSmemBytes);
-        cudaFuncSetAttribute(filter_kernel<MAXF>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(filter_kernel<MAXF, kM3>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, filter_kernel<MAXF>, kThreads, kSmemBytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, filter_kernel<MAXF, kM3>, kThreads, kSmemBytes);
         cached_ctas = sms * (occ > 0 ? occ : 1);
         cached_dev = dev;
     }
     return total < cached_ctas ? total : cached_ctas;
 }
 
-template <int MAXF>
+template <int MAXF, bool kM3 = false>
 cudaError_t launch_pdl(const FilterBatch<MAXF> &b, int *status, unsigned *work, bool overlap,
                        cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(persistent_grid<MAXF>(b.total_blocks));
+    cfg.gridDim = dim3(persistent_grid<MAXF, kM3>(b.total_blocks));
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = kSmemBytes;
     cfg.stream = s;
@@ -633,7 +638,7 @@ cudaError_t launch_pdl(const FilterBatch<MAXF> &b, int *status, unsigned *work, 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const int dep_wait = overlap ? 0 : 1;
-    return cudaLaunchKernelEx(&cfg, filter_kernel<MAXF>, b, status, work, dep_wait);
+    return cudaLaunchKernelEx(&cfg, filter_kernel<MAXF, kM3>, b, status, work, dep_wait);
 }
 
 }  // namespace
@@ -654,6 +659,12 @@ cudaError_t launch_filter_planes(const FilterBatch<3> &b, int *status, unsigned 
                                  bool overlap, cudaStream_t s)
 {
     return launch_pdl<3>(b, status, work, overlap, s);
+}
+
+cudaError_t launch_filter_444(const FilterBatch<1> &b, int *status, unsigned *work, bool overlap,
+                              cudaStream_t s)
+{
+    return launch_pdl<1, true>(b, status, work, overlap, s);
 }
 
 CDEF_FAULT_COUNTER(index_faults_filter)
