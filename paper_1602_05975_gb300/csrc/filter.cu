@@ -73,7 +73,7 @@ struct FilterSmem {
     uint8_t coded[64];                                  // 8x8 block has coded residual
     int var[64];
     int blk_next;                                       // block id of the tiles in `raw`
-    int stage_next;                                     // and their plane (mode 3)
+                                                        // (mode 3: plane << 28 | block)
     alignas(8) uint64_t bar;
 };
 
@@ -542,7 +542,6 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
             mbar_init(&sm.bar, 1);
             const int b = (int)atomicAdd(&work[0], 1u);
             sm.blk_next = b;
-            sm.stage_next = 0;
             if (b < total) issue_loads(batch, b, sm.raw, &sm.bar);
         }
         if (tid < 192) {  // tap offset tables [luma/chroma][d][tap]
@@ -557,7 +556,8 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
         // then block n+1's loads are issued into the buffer while block n is
         // searched and filtered
         for (int it = 0;; it++) {
-            const int blk = sm.blk_next, stage = kM3 ? sm.stage_next : 0;
+            const int bn = sm.blk_next;
+            const int blk = kM3 ? (bn & 0x0fffffff) : bn, stage = kM3 ? (bn >> 28) : 0;
             if (blk >= total) break;
             const bool arrived = mbar_wait_bounded(&sm.bar, it & 1, batch.waits.wait_cycles);
             if (__syncthreads_or(!arrived)) {  // the whole CTA leaves together
@@ -567,21 +567,20 @@ filter_kernel(const __grid_constant__ FilterBatch<MAXF> batch, int *status, unsi
                 }
                 break;
             }
-            const BlockRef r = locate(batch, blk);
-            const FilterFrameDev &F = batch.f[r.fi];
             auto prefetch = [&]() {
                 if (tid == 0) {
                     if (kM3 && stage < 2) {   // the block's next plane
-                        sm.stage_next = stage + 1;
+                        sm.blk_next = blk | ((stage + 1) << 28);
                         issue_loads(batch, blk, sm.raw, &sm.bar, stage + 1);
                     } else {
                         const int nb = (int)atomicAdd(&work[0], 1u);
                         sm.blk_next = nb;
-                        sm.stage_next = 0;
                         if (nb < total) issue_loads(batch, nb, sm.raw, &sm.bar);
                     }
                 }
             };
+            const BlockRef r = locate(batch, blk);
+            const FilterFrameDev &F = batch.f[r.fi];
             if (F.bitdepth == 8)
                 process_block<uint8_t, kM3>(F, r.fby, r.fbx, status, sm, sm.raw, prefetch, stage);
             else
