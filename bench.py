@@ -520,6 +520,18 @@ def run_ours(args):
                             "(programmatic dependent launch), the tail of one filling the SMs "
                             "the next starts on" if not args.no_overlap
                             else "timed region / launches"}}
+    # beside the derived ceiling, the measured one: the integer issue rate
+    # of the filter's tap instruction mix on this GPU (probe kernel)
+    if WORKLOAD["bitdepth"] <= 10:
+        mix = cdef.probe_int_mix(ctx, 0)
+        alu_only = cdef.probe_int_mix(ctx, 1)
+        peak_mix = 2 * mix / 1e9   # two 16-bit lanes per lane instruction, Gop/s
+        roofline["measured_int_ceiling"] = {
+            "peak": peak_mix, "unit": "Gop/s",
+            "frac": ops / peak_mix, "frac_overlapped": ops_b / (share_ms * 1e-3) / 1e9 / peak_mix,
+            "tap_mix_lane_instr_per_s": mix, "alu_only_lane_instr_per_s": alu_only,
+            "what": "cdef_probe_int_mix: the tap's 5 packed ALU operations and 3 multiply-adds "
+                    "in independent chains, 4 CTAs of 256 threads per SM, CUDA events"}
 
     cpu = None
     if pool is not None:

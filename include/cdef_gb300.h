@@ -527,6 +527,22 @@ int cdef_debug_set_waits(int64_t wait_cycles, int32_t extra_tx_bytes);
  * CDEF_ERR_CUDA when the device cannot be read. */
 int cdef_debug_checks(cdef_ctx *ctx, int64_t *faults, int32_t clear);
 
+/* Measurement aid (no paper counterpart): the integer issue rate of this
+ * GPU for the filter's tap instruction mix, the ceiling of the integer-
+ * pipe roofline the filter and the strength search are bound by (the
+ * library's kernels are otherwise compared with a ceiling derived from the
+ * SM count and clock).  A probe kernel runs `iters` steps of 8 independent
+ * chains per thread on 4 CTAs of 256 threads per SM; a step is the tap's 5
+ * packed 16-bit operations on the ALU pipe and 3 multiply-adds (mix 0) or
+ * the 5 ALU operations alone (mix 1).
+ *   lane_instr_per_s : HOST output, lane instructions per second (warp
+ *                      instructions x 32), from CUDA events around the
+ *                      launch after one warm-up launch
+ * Synchronises `cuda_stream`.  CDEF_ERR_ARG for mix not 0/1 or iters
+ * outside 1..2^20; CDEF_ERR_CUDA, CDEF_ERR_NOMEM on a runtime failure. */
+int cdef_probe_int_mix(cdef_ctx *ctx, int32_t mix, int32_t iters, double *lane_instr_per_s,
+                       void *cuda_stream);
+
 /* A static description of a status code. */
 const char *cdef_strerror(int status);
 

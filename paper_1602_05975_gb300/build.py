@@ -26,7 +26,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcdef_gb300.so")
 DEBUG_LIB = os.path.join(HERE, "libcdef_gb300_debug.so")
 SOURCES = ["api.cu", "find_dir.cu", "filter.cu", "search.cu", "search_wide.cu", "presets.cu", "shard.cu",
-           "presets_cluster.cu", "noalloc.cu"]
+           "presets_cluster.cu", "noalloc.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
                  "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

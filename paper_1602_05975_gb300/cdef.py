@@ -109,6 +109,7 @@ def load():
         C.POINTER(i64), vp, vp, C.POINTER(PresetCoded), C.POINTER(i32), vp, C.POINTER(i64), vp]
     L.cdef_debug_set_waits.argtypes = [i64, i32]
     L.cdef_debug_checks.argtypes = [vp, C.POINTER(i64), i32]
+    L.cdef_probe_int_mix.argtypes = [vp, i32, i32, C.POINTER(C.c_double), vp]
     L.cdef_search_tables.argtypes = [vp, i32, C.POINTER(FrameDesc), C.POINTER(FrameDesc),
                                      C.POINTER(vp), C.POINTER(i32), C.POINTER(i32),
                                      C.POINTER(i32), vp, vp, vp, vp]
@@ -127,6 +128,7 @@ def load():
                  "cdef_ctx_set_search_metric", "cdef_ctx_set_stage_timing",
                  "cdef_ctx_get_stage_times", "cdef_ctx_set_search_subset",
                  "cdef_ctx_status_async", "cdef_debug_set_waits", "cdef_debug_checks",
+                 "cdef_probe_int_mix",
                  "cdef_search_tables",
                  "cdef_preset_totals", "cdef_preset_argmin", "cdef_preset_assign"):
         getattr(L, name).restype = C.c_int
@@ -570,6 +572,16 @@ def debug_checks(ctx, clear: bool = True):
     if r < 0:
         _check(r, "cdef_debug_checks")
     return bool(r), int(n.value)
+
+
+def probe_int_mix(ctx, mix: int = 0, iters: int = 4096, stream=None) -> float:
+    """Measurement aid: lane instructions per second of the filter's tap
+    mix (mix 0) or of its integer-ALU operations alone (mix 1) on ctx's
+    device."""
+    r = C.c_double(0.0)
+    _check(load().cdef_probe_int_mix(ctx.handle, int(mix), int(iters), C.byref(r),
+                                     _stream_ptr(stream)), "cdef_probe_int_mix")
+    return float(r.value)
 
 
 def version() -> str:

@@ -1186,6 +1186,17 @@ int cdef_debug_checks(cdef_ctx *ctx, int64_t *faults, int32_t clear)
     return kIndexChecks ? 1 : 0;
 }
 
+int cdef_probe_int_mix(cdef_ctx *ctx, int32_t mix, int32_t iters, double *lane_instr_per_s,
+                       void *cuda_stream)
+{
+    if (!ctx || !lane_instr_per_s || (mix != 0 && mix != 1) || iters < 1 || iters > (1 << 20))
+        return CDEF_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return CDEF_ERR_CUDA;
+    return probe_int_mix(ctx->device, mix, iters, lane_instr_per_s,
+                         static_cast<cudaStream_t>(cuda_stream));
+}
+
 int cdef_debug_set_waits(int64_t wait_cycles, int32_t extra_tx_bytes)
 {
     if (wait_cycles < 0 || extra_tx_bytes < 0 || extra_tx_bytes > (1 << 16)) return CDEF_ERR_ARG;

@@ -256,6 +256,10 @@ cudaError_t launch_preset_assign(int nblocks, int width, const long long *dl, co
                                  const uint8_t *skipped, PresetList set, unsigned long long *best,
                                  uint8_t *ids, long long *sums, cudaStream_t s);
 
+// The integer-issue probe (probe.cu): lane instructions per second of the
+// filter's tap mix (mix 0) or of its ALU operations alone (mix 1).
+int probe_int_mix(int device, int mix, int iters, double *lane_instr_per_s, cudaStream_t s);
+
 // Host: the three 2-D tile maps (filter-block boxes with halo) of a frame's
 // planes; returns a CDEF status.
 int encode_frame_tiles(CUtensorMap maps[3], const cdef_frame *f);

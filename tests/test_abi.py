@@ -55,6 +55,10 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.cdef_debug_set_waits(-1, 0) == -1
     assert lib.cdef_debug_set_waits(0, -1) == -1
     assert lib.cdef_debug_set_waits(0, 0) == 0
+    lib.cdef_probe_int_mix.argtypes = [C.c_void_p, C.c_int32, C.c_int32,
+                                       C.POINTER(C.c_double), C.c_void_p]
+    r = C.c_double(0.0)
+    assert lib.cdef_probe_int_mix(None, 0, 16, C.byref(r), None) == -1
 
 
 def test_struct_layout_matches_binding(tmp_path):
