@@ -790,6 +790,12 @@ def measure_search(args, variant, steps, warmup, pool=None):
                 "preset_kernel_us": pre_ms * 1e3,
                 "peak_source": "derived: 152 SMs x 128 lanes x 2 (16-bit pairs) x 2070 MHz"
                 if bd <= 10 else "derived: 152 SMs x 128 lanes x 2070 MHz"}
+    if bd <= 10:   # the measured ceiling of the tap instruction mix (as for the filter)
+        peak_mix = 2 * cdef.probe_int_mix(ctx, 0) / 1e9
+        roofline["measured_int_ceiling"] = {
+            "peak": peak_mix, "unit": "Gop/s", "frac": roofline["achieved"] / peak_mix,
+            "what": "cdef_probe_int_mix: the filter tap's 5 packed ALU operations and 3 "
+                    "multiply-adds in independent chains"}
     cpu = None
     if pool is not None:
         sample = [i for i in range(len(frames)) if (frames[i].width, frames[i].height) == (640, 360)]
