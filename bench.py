@@ -732,7 +732,8 @@ def measure_search(args, variant, steps, warmup, pool=None):
         return time.perf_counter() - t, r
 
     clocks.mark("begin")
-    sec = sum(timed(call)[0] for _ in range(steps)) / steps
+    call_s = [timed(call)[0] for _ in range(steps)]
+    sec = sum(call_s) / steps
     clocks.mark("end")
     clk = clocks.stop()
     tune = ctx.tuning()
@@ -760,9 +761,11 @@ def measure_search(args, variant, steps, warmup, pool=None):
     for _ in range(warmup):
         plain()
     plain_sec = 0.0
+    plain_s = []
     for _ in range(steps):
         dt, res_p = timed(plain)
         plain_sec += dt / steps
+        plain_s.append(dt)
     same = (res_p == res_b and torch.equal(batched[0], dl) and torch.equal(batched[1], dc)
             and torch.equal(batched[2], ids))
     assert same, "batched and one-frame-at-a-time searches differ"
@@ -827,8 +830,16 @@ def measure_search(args, variant, steps, warmup, pool=None):
         "roofline": roofline, "cpu_baseline": cpu,
         "refine_passes": args.refine, "variant": variant,
         "plain": {"ms_per_step": plain_sec * 1e3, "value": nb * 2 * width / plain_sec,
-                  "what": "one cdef_search_strengths call per frame, identical outputs"},
+                  "what": "one cdef_search_strengths call per frame, identical outputs",
+                  "spread_ms": spread_ms(plain_s)},
+        "spread_ms": spread_ms(call_s),
         "clocks": clk}
+
+
+def spread_ms(secs) -> dict:
+    """Minimum, median and maximum of the timed calls (ms) and their count."""
+    v = sorted(x * 1e3 for x in secs)
+    return {"min": v[0], "median": statistics.median(v), "max": v[-1], "calls": len(v)}
 
 
 def search_extra(args):
@@ -842,8 +853,9 @@ def search_extra(args):
             "distortion_kernel_us": rl["mean_launch_us"], "preset_kernel_us": rl["preset_kernel_us"],
             "plain_ms_per_call": r["plain"]["ms_per_step"],
             "batched_over_plain": r["plain"]["ms_per_step"] / r["ms_per_step"],
+            "spread_ms": r["spread_ms"], "plain_spread_ms": r["plain"]["spread_ms"],
             "roofline": {k: rl[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel",
-                                            "peak_source")},
+                                            "peak_source", "measured_int_ceiling") if k in rl},
             "tuning": r["tuning"], "l2": r["config"]["l2"], "calls": 5, "clocks": r["clocks"]}
 
 
