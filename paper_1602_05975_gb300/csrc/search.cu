@@ -57,7 +57,7 @@ struct SearchSmem {
     unsigned long long accu[64];      // the part of them from blocks without coded residual
     unsigned long long acc14c[8];     // eq. 14: chroma block totals of the unit's candidates
     // eq. 14: sums over the 4-row halves of the 4:2:0 chroma 8x8 blocks,
-    // [plane][block][half][value]: per candidate (r, r(2x + r), r(2(x - s) + r)),
+    // [plane][block][half][value]: per candidate (r, r (s + 128), r (2 (x - s) + r)),
     // then n, x, x^2, s, s^2, (x - s)^2
     int e14h[2][16][2][30];
     // eq. 14: per luma 8x8 block the candidate-free sums n, x, x^2, s, s^2,
@@ -444,7 +444,6 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     // at 8 and 10 bits stays within a signed byte (|r| <= 57).
                     sse0 = add_sq<T>(sse0, X, S);
                     const uint32_t two_xs = sadd16(2u * (X + 4096u * kLanes - S), 0xdf00u * kLanes);
-                    uint32_t two_x = 0;
                     if (kEq14 && g == 0) {
                         const int xl = (int)(X & 0xffffu) - (int)kBias, xh = (int)(X >> 16) - (int)kBias;
                         const int sl = (int)(S & 0xffffu) - (int)kBias, sh = (int)(S >> 16) - (int)kBias;
@@ -454,7 +453,6 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                         e0[6] += sl * sl; e0[7] += sh * sh;
                         e0[8] += (xl - sl) * (xl - sl); e0[9] += (xh - sh) * (xh - sh);
                     }
-                    if (kEq14) two_x = sadd16(X + X, 0xfe00u * kLanes);   // 2x - 256 per lane
                     const uint32_t rlo = __vmaxu2(mn - X + 2048u * kLanes, 1792u * kLanes) - 1792u * kLanes;
                     const uint32_t rhi = mx - X + 256u * kLanes;
                     uint32_t Q[4], Qr[4];
@@ -516,19 +514,21 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                             const uint32_t r8 = __byte_perm(rb, 0, 0x0020);  // r of both lanes, bytes 0, 1
                             if (kEq14) {
                                 const int c = pp * 4 + s;
-                                const int ax = (int)sadd16(rb, two_x);       // 2x + r
+                                // sums of r, r (s + 128) (the source as staged) and
+                                // r (2 (x - s) + r); r (2x + r) follows from the last
+                                // two at the block (r (2 (x - s) + r) + 2 r s)
                                 if (luma) {
                                     // both lanes in one 8x8 block: one sum
                                     e6[c][0] = __dp2a_lo((int)kLanes, (int)r8, e6[c][0]);
-                                    e6[c][2] = __dp2a_lo(ax, (int)r8, e6[c][2]);
+                                    e6[c][2] = __dp2a_lo((int)S, (int)r8, e6[c][2]);
                                     e6[c][4] = __dp2a_lo((int)a, (int)r8, e6[c][4]);
                                 } else {
                                     // (U, V) lanes kept apart
                                     const int rl = (int)(r8 & 0xffu), rh = (int)(r8 & 0xff00u);
                                     e6[c][0] = __dp2a_lo((int)kLanes, rl, e6[c][0]);
                                     e6[c][1] = __dp2a_lo((int)kLanes, rh, e6[c][1]);
-                                    e6[c][2] = __dp2a_lo(ax, rl, e6[c][2]);
-                                    e6[c][3] = __dp2a_lo(ax, rh, e6[c][3]);
+                                    e6[c][2] = __dp2a_lo((int)S, rl, e6[c][2]);
+                                    e6[c][3] = __dp2a_lo((int)S, rh, e6[c][3]);
                                     e6[c][4] = __dp2a_lo((int)a, rl, e6[c][4]);
                                     e6[c][5] = __dp2a_lo((int)a, rh, e6[c][5]);
                                 }
@@ -569,6 +569,10 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                             BS[c] += __shfl_xor_sync(0xffffffffu, BS[c], o);
                         }
                     }
+                    // r (2x + r) = r (2 (x - s) + r) + 2 r s, from the sum of
+                    // r (s + 128)
+    #pragma unroll
+                    for (int c = 0; c < kNt; c++) BX[c] = BS[c] + 2 * (BX[c] - (int)kBias * A[c]);
                     // the candidate-free sums of the block: formed in the first
                     // group (the four lanes agree after the butterfly), kept
                     if (g == 0) {
@@ -739,9 +743,11 @@ __device__ void dist_block(const SearchFrameDev &F, int fby, int fbx, int blk_gl
                     if (n > 0) {
                         const long long sx = h0[25] + h1[25], sx2 = h0[26] + h1[26];
                         const long long ssum = h0[27] + h1[27], ss2 = h0[28] + h1[28], sxs = h0[29] + h1[29];
-                        t = eq14_value(n, ssum, ss2, sx + h0[3 * c] + h1[3 * c],
-                                       sx2 + h0[3 * c + 1] + h1[3 * c + 1],
-                                       sxs + h0[3 * c + 2] + h1[3 * c + 2], F.bitdepth);
+                        const long long ra = h0[3 * c] + h1[3 * c];
+                        const long long rs = h0[3 * c + 1] + h1[3 * c + 1];   // r (s + 128)
+                        const long long rq = h0[3 * c + 2] + h1[3 * c + 2];   // r (2 (x - s) + r)
+                        t = eq14_value(n, ssum, ss2, sx + ra, sx2 + rq + 2 * (rs - (long long)kBias * ra),
+                                       sxs + rq, F.bitdepth);
                     }
                     t += __shfl_xor_sync(0xffffffffu, t, 8);
                     t += __shfl_xor_sync(0xffffffffu, t, 16);
