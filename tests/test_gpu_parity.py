@@ -1398,3 +1398,79 @@ def test_search_random_fuzz(cdef, ctx, ref, seed):
             [int(t) for t in o["presets"][:o["npresets"]]]
         assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
         o0 += b
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_search_444_random_fuzz(cdef, ctx, ref, seed):
+    """Random all-4:4:4 calls (the packed plane units): sizes, 8/10-bit,
+    damping, lambda, with or without coded-residual maps; tables, presets,
+    N, J and ids equal the oracle's."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(6100 + seed)
+    with_maps = seed % 2 == 1
+    frames, maps = [], []
+    for _ in range(4):
+        w, h = 8 * int(rng.integers(1, 26)), 8 * int(rng.integers(1, 26))
+        bd = int(rng.choice([8, 10]))
+        frames.append(synth.make_frame(w, h, bd, None, seed=int(rng.integers(1 << 30)), chroma=444))
+        maps.append((rng.random((h // 8, w // 8)) < rng.random()).astype(np.uint8))
+    damping = [int(d) for d in rng.integers(3, 7, len(frames))]
+    lambdas = [int(l) for l in rng.integers(0, 5000, len(frames))]
+    width = 128 if with_maps else 64
+    nb = sum(f.params.shape[0] * f.params.shape[1] for f in frames)
+    ids = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    dl = torch.full((nb * width,), -1, dtype=torch.int64, device="cuda")
+    dc = torch.full((nb * width,), -1, dtype=torch.int64, device="cuda")
+    recs = [cdef.frame_from_numpy(f.rec, f.bitdepth) for f in frames]
+    srcs = [cdef.frame_from_numpy(f.src, f.bitdepth) for f in frames]
+    if with_maps:
+        res = cdef.cdef_search_strengths_coded(ctx, recs, srcs,
+                                               [torch.from_numpy(m.reshape(-1)).cuda() for m in maps],
+                                               damping, lambdas, ids, dl, dc)
+    else:
+        res = cdef.cdef_search_strengths(ctx, recs, srcs, damping, lambdas, ids, dl, dc)
+    assert ctx.status() == 0
+    o0 = 0
+    for f, m, r, d, lam in zip(frames, maps, res, damping, lambdas):
+        b = f.params.shape[0] * f.params.shape[1]
+        if with_maps:
+            o = ref.search_strengths_coded_format(f.rec, f.src, f.bitdepth, d, lam, 444, m)
+            idx = cdef.preset_index_coded
+        else:
+            o = ref.search_strengths_format(f.rec, f.src, f.bitdepth, d, lam, 444)
+            idx = cdef.preset_index
+        assert np.array_equal(dl[o0 * width:(o0 + b) * width].cpu().numpy().reshape(b, width),
+                              o["dist_luma"])
+        assert np.array_equal(dc[o0 * width:(o0 + b) * width].cpu().numpy().reshape(b, width),
+                              o["dist_chroma"])
+        assert r["npresets"] == o["npresets"] and r["cost"] == o["cost"]
+        assert [idx(p) for p in r["presets"][:r["npresets"]]] == \
+            [int(t) for t in o["presets"][:o["npresets"]]]
+        assert np.array_equal(ids[o0:o0 + b].cpu().numpy(), o["block_ids"])
+        o0 += b
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_filter_444_random_fuzz(cdef, ctx, ref, seed):
+    """Random 8/10-bit 4:4:4 frames through the three-plane launch: sizes,
+    strengths, damping, skip bits, with or without coded maps; every output
+    sample equals the oracle's."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(6200 + seed)
+    for _ in range(3):
+        w, h = 8 * int(rng.integers(1, 30)), 8 * int(rng.integers(1, 30))
+        bd = int(rng.choice([8, 10]))
+        f = synth.make_frame(w, h, bd, None, seed=int(rng.integers(1 << 30)), chroma=444)
+        params = synth.random_params(rng, w, h)
+        params[..., 5] = rng.integers(0, 4, params.shape[:2])
+        coded = (rng.random((h // 8, w // 8)) < rng.random()).astype(np.uint8) if seed % 2 else None
+        inp = cdef.frame_from_numpy(f.rec, bd)
+        out = cdef.alloc_frame(w, h, bd, fill=0, chroma=444)
+        prm = cdef.params_tensor(params)
+        if coded is not None:
+            cdef.cdef_filter_frame_coded(ctx, inp, prm, torch.from_numpy(coded.reshape(-1)).cuda(), out)
+        else:
+            cdef.cdef_filter_frame(ctx, inp, prm, out)
+        torch.cuda.synchronize()
+        assert ctx.status() == 0
+        _assert_frames_equal(out.to_numpy(), ref.filter_frame_format(*f.rec, bd, params, 444, coded))
