@@ -14,9 +14,13 @@
  *    are copied) and 4:4:4 frames (chroma W x H: each chroma plane is
  *    filtered in 8x8 blocks with the chroma strengths and damping and the
  *    co-located luma direction).  The format follows from the plane sizes.
- *    A 4:4:4 frame filtered without caller maps (dir = var = NULL) uses the
- *    context's direction-map scratch: such calls on one context belong on
- *    one stream (their launches are then ordered).
+ *    An 8/10-bit 4:4:4 frame is one launch in which the three planes of
+ *    each 64x64 filter block are filtered in turn (the luma directions
+ *    searched first, or read from dir/var); consecutive such calls overlap
+ *    under cdef_ctx_set_overlap as 4:2:0 calls do.  A 12-bit 4:4:4 frame
+ *    filtered without caller maps (dir = var = NULL) uses the context's
+ *    direction-map scratch: such calls on one context belong on one stream
+ *    (their launches are then ordered).
  *  - Samples are unsigned integers stored planar and row-major: uint8_t for
  *    bit depth 8, uint16_t (value in the low bits) for bit depths 10 and 12.
  *  - Plane memory is DEVICE memory owned by the caller.  `data` must be
@@ -221,10 +225,12 @@ int cdef_filter_frames(cdef_ctx *ctx, int32_t n, const cdef_frame *in,
  * (inferred from the chroma plane sizes as for cdef_filter_frame).  4:2:2
  * chroma is not filtered (section 4), so its entries are the unfiltered
  * error for every pair; 4:4:4 chroma planes are filtered in 8x8 blocks
- * with the chroma strengths and the co-located luma direction.  A call
- * holding any 12-bit, 4:2:2 or 4:4:4 frame computes its tables with 32-bit
- * arithmetic per sample (slower than the packed 8/10-bit 4:2:0 path) and
- * needs (W/8)(H/8) * 5 bytes of direction maps per frame in the context.
+ * with the chroma strengths and the co-located luma direction.  A call of
+ * 8/10-bit 4:4:4 frames only takes the packed 16-bit path one plane per
+ * work unit (its direction maps formed first); a call holding any 12-bit
+ * or 4:2:2 frame, or mixing 4:4:4 with other formats, computes its tables
+ * with 32-bit arithmetic per sample (slower).  Both need (W/8)(H/8) * 5
+ * bytes of direction maps per frame in the context.
  * This call synchronises the stream before returning (host outputs).
  */
 int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
@@ -251,8 +257,9 @@ int cdef_search_strengths(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
  *   dist_luma,
  *   dist_chroma  : DEVICE, sum_i B_i * 128 int64 each, or both NULL
  *   presets      : HOST, n*8 entries (first npresets[i] of frame i valid)
- * Frames: as cdef_search_strengths (4:2:2, 4:4:4 and 12-bit frames through
- * the 32-bit path; 4:2:2 chroma entries are the unfiltered error).
+ * Frames: as cdef_search_strengths (calls of 8/10-bit 4:4:4 frames only
+ * through the packed plane units, 4:2:2, 12-bit and mixed-format calls
+ * through the 32-bit path; 4:2:2 chroma entries are the unfiltered error).
  * Synchronises the stream before returning. */
 int cdef_search_strengths_coded(cdef_ctx *ctx, int32_t n, const cdef_frame *rec,
                                 const cdef_frame *src, const uint8_t *const *coded,
@@ -313,7 +320,9 @@ int cdef_ctx_get_tuning(const cdef_ctx *ctx, cdef_tuning *last);
  *                    chroma: the unfiltered value for every pair), and the
  *                    128 combinations of cdef_search_strengths_coded (each
  *                    8x8 block's value from what the decoder outputs for
- *                    the preset; formed by the 32-bit path).
+ *                    the preset; formed by the 32-bit path).  Calls of
+ *                    8/10-bit 4:4:4 frames only take the packed plane
+ *                    units (64 pairs).
  * Host only; applies to later searches on the context. */
 #define CDEF_METRIC_SSE 0
 #define CDEF_METRIC_EQ14 1
