@@ -530,7 +530,7 @@ def run_ours(args):
             "peak": peak_mix, "unit": "Gop/s",
             "frac": ops / peak_mix, "frac_overlapped": ops_b / (share_ms * 1e-3) / 1e9 / peak_mix,
             "tap_mix_lane_instr_per_s": mix, "alu_only_lane_instr_per_s": alu_only,
-            "what": "cdef_probe_int_mix: the tap's 5 packed ALU operations and 3 multiply-adds "
+            "what": "cdef_probe_int_mix: the tap's 6 ALU operations and 2 multiply-adds "
                     "in independent chains, 4 CTAs of 256 threads per SM, CUDA events"}
 
     cpu = None
@@ -797,7 +797,7 @@ def measure_search(args, variant, steps, warmup, pool=None):
         peak_mix = 2 * cdef.probe_int_mix(ctx, 0) / 1e9
         roofline["measured_int_ceiling"] = {
             "peak": peak_mix, "unit": "Gop/s", "frac": roofline["achieved"] / peak_mix,
-            "what": "cdef_probe_int_mix: the filter tap's 5 packed ALU operations and 3 "
+            "what": "cdef_probe_int_mix: the filter tap's 6 ALU operations and 2 "
                     "multiply-adds in independent chains"}
     cpu = None
     if pool is not None:

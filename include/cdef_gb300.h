@@ -541,9 +541,10 @@ int cdef_debug_checks(cdef_ctx *ctx, int64_t *faults, int32_t clear);
  * pipe roofline the filter and the strength search are bound by (the
  * library's kernels are otherwise compared with a ceiling derived from the
  * SM count and clock).  A probe kernel runs `iters` steps of 8 independent
- * chains per thread on 4 CTAs of 256 threads per SM; a step is the tap's 5
- * packed 16-bit operations on the ALU pipe and 3 multiply-adds (mix 0) or
- * the 5 ALU operations alone (mix 1).
+ * chains per thread on 4 CTAs of 256 threads per SM; a step is the tap's 6
+ * ALU operations (four packed 16-bit min/max/add-min, the shift and its
+ * per-lane mask) and 2 multiply-adds (mix 0), or five ALU operations alone
+ * (mix 1).
  *   lane_instr_per_s : HOST output, lane instructions per second (warp
  *                      instructions x 32), from CUDA events around the
  *                      launch after one warm-up launch

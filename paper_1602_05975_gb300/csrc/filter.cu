@@ -36,7 +36,7 @@
 //   lim = max(0, K - |p - x|) >> sh                       (exact)
 //   K - |p - x| = min((x + K) - p, p - (x - K)),
 // which maps onto the packed 16-bit min/max/add-min instructions, the shift
-// being a multiply-high.  S = 0 gives lim = 0, c = x: a tap set with zero
+// being one shift of the word and a per-lane mask.  S = 0 gives lim = 0, c = x: a tap set with zero
 // strength contributes nothing without a branch.  The weighted sum of the
 // clamped values minus 24x is the eq. 8 sum (each tap set's weights sum to
 // 12 sixteenths).  A tap outside the frame is ignored (section 3.1); it is

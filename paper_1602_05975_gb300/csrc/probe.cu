@@ -3,14 +3,13 @@
 // bounds the filter and the strength search is the integer pipes, whose
 // ceiling is derived from the SM count and clock; this measures it).
 //
-// Per tap the filter issues 5 packed 16-bit operations on the integer ALU
-// pipe (two add-min, two max, the mask of the shift) and 3 multiply-adds
-// (the subtractions and the shift by multiply-high), which the compiler
-// places on the FMA pipe.  The probe kernel runs that sequence in 8
-// independent chains per thread on 4 CTAs of 256 threads per SM, with
-// every operand a runtime value, and the host times it with CUDA events.
-// mix 0: the tap sequence (5 ALU + 3 FMA per step); mix 1: the ALU
-// operations alone (5 per step).
+// Per tap the filter issues 6 operations on the integer ALU pipe (two
+// packed add-min, two packed max, the shift and its per-lane mask) and 2
+// multiply-adds (the subtractions), which the compiler places on the FMA
+// pipe.  The probe kernel runs that sequence in 8 independent chains per
+// thread on 4 CTAs of 256 threads per SM, with every operand a runtime
+// value, and the host times it with CUDA events.  mix 0: the tap sequence
+// (6 ALU + 2 FMA per step); mix 1: five of the ALU operations alone.
 #include "cdef_internal.h"
 
 namespace cdefgb {
@@ -21,7 +20,7 @@ constexpr int kChains = 8;
 
 template <int kMix>
 __global__ void __launch_bounds__(kProbeThreads, 4)
-int_mix_kernel(uint32_t seed, uint32_t m1, uint32_t mul, uint32_t mask, uint32_t floor_,
+int_mix_kernel(uint32_t seed, uint32_t m1, uint32_t sh, uint32_t mask, uint32_t floor_,
                int iters, uint32_t *sink)
 {
     const uint32_t t = blockIdx.x * kProbeThreads + threadIdx.x;
@@ -37,11 +36,11 @@ int_mix_kernel(uint32_t seed, uint32_t m1, uint32_t mul, uint32_t mask, uint32_t
             if (kMix == 0) {
                 const uint32_t t1 = a[k] * m1 + b[k];                       // FMA pipe
                 uint32_t m = __vmaxu2(__viaddmin_u16x2(a[k], b[k], t1), floor_);
-                m = __umulhi(m, mul) & mask;                               // FMA, ALU
+                m = (m >> sh) & mask;                                      // ALU, ALU
                 const uint32_t q = __vmaxu2(a[k], m * m1 + b[k]);          // FMA, ALU
                 a[k] = __viaddmin_u16x2(m, b[k], q);
             } else {   // the five ALU operations alone
-                uint32_t m = __vmaxu2(__viaddmin_u16x2(a[k], b[k], mul), floor_);
+                uint32_t m = __vmaxu2(__viaddmin_u16x2(a[k], b[k], sh), floor_);
                 m &= mask;
                 a[k] = __viaddmin_u16x2(m, b[k], __vmaxu2(a[k], m));
             }
@@ -71,10 +70,10 @@ int probe_int_mix(int device, int mix, int iters, double *lane_instr_per_s, cuda
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     auto launch = [&](int n) {
         if (mix == 0)
-            int_mix_kernel<0><<<grid, kProbeThreads, 0, s>>>(0x1234567u, 0xffffffffu, 0x40000000u,
+            int_mix_kernel<0><<<grid, kProbeThreads, 0, s>>>(0x1234567u, 0xffffffffu, 2u,
                                                              0x3fff3fffu, 0x08000800u, n, sink);
         else
-            int_mix_kernel<1><<<grid, kProbeThreads, 0, s>>>(0x1234567u, 0xffffffffu, 0x40000000u,
+            int_mix_kernel<1><<<grid, kProbeThreads, 0, s>>>(0x1234567u, 0xffffffffu, 2u,
                                                              0x3fff3fffu, 0x08000800u, n, sink);
     };
     if (e == cudaSuccess) {

@@ -36,9 +36,9 @@ constexpr long long kWaitCycles = kDefaultWaitCycles;
 
 // Per-block constants of one tap set.
 struct SetC {
-    uint32_t mul;    // 2^(32 - sh); sh = 0: 0xffffffff (umulhi gives m - 1)
-    uint32_t mask;   // per-lane mask after the packed shift
-    uint32_t posb;   // (kB1 >> sh) in both lanes; sh = 0: the low lane one less
+    uint32_t sh;     // the damping shift of eq. 7 (0..15)
+    uint32_t mask;   // per-lane mask after the packed shift: (0xffff >> sh) per lane
+    uint32_t posb;   // (kB1 >> sh) in both lanes
     uint32_t kb;     // K + kB1 in both lanes
 };
 
@@ -82,16 +82,9 @@ __device__ __forceinline__ SetC make_set(int S, int sh)
 {
     SetC c;
     const uint32_t K = ((uint32_t)(S + 1) << sh) - 1;
-    const uint32_t b = kB1 >> sh;
-    if (sh) {
-        c.mul = 1u << (32 - sh);
-        c.mask = (0xffffu >> sh) * kLanes;
-        c.posb = b * kLanes;
-    } else {
-        c.mul = 0xffffffffu;
-        c.mask = 0xffffffffu;
-        c.posb = (kB1 << 16) | (kB1 - 1);
-    }
+    c.sh = (uint32_t)sh;
+    c.mask = (0xffffu >> sh) * kLanes;
+    c.posb = (kB1 >> sh) * kLanes;
     c.kb = (K + kB1) * kLanes;
     return c;
 }
@@ -111,13 +104,18 @@ __device__ __forceinline__ BlockC make_block_consts(const Eff &e)
 // One tap: clamp(p, x - lim, x + lim) on both lanes, xk1 = x + K + kB1,
 // xk2 = K + kB1 - x.
 //   m   = max(min(xk1 - p, p + xk2), kB1) = kB1 + max(0, K - |p - x|)
-//   L   = m >> sh (multiply-high, masked per lane), lim = L - (kB1 >> sh)
+//   L   = m >> sh (the word shifted, then masked per lane), lim = L - (kB1 >> sh)
+// The shift is a funnel shift on the integer ALU; a multiply-high by
+// 2^(32 - sh) does the same on the multiply-add pipe, where on this GPU it
+// takes four times the issue slots of a multiply-add (the tap's two
+// subtractions already run there): the filter's launches ran 3-5% slower
+// with it.
 __device__ __forceinline__ uint32_t tap(uint32_t p, uint32_t X, uint32_t xk1, uint32_t xk2,
                                         const SetC &s)
 {
     const uint32_t t1 = xk1 - p;
     uint32_t m = __vmaxu2(__viaddmin_u16x2(p, xk2, t1), kB1 * kLanes);
-    m = __umulhi(m, s.mul) & s.mask;
+    m = (m >> s.sh) & s.mask;
     const uint32_t lim = m - s.posb;
     const uint32_t lo = X - lim;
     return __viaddmin_u16x2(lim, X, __vmaxu2(p, lo));   // min(x + lim, max(p, x - lim))
@@ -131,7 +129,7 @@ __device__ __forceinline__ uint32_t tap_folded(uint32_t p, uint32_t xk1, uint32_
 {
     const uint32_t t1 = xk1 - p;
     uint32_t m = __vmaxu2(__viaddmin_u16x2(p, xk2, t1), kB1 * kLanes);
-    m = __umulhi(m, s.mul) & s.mask;
+    m = (m >> s.sh) & s.mask;
     return __viaddmin_u16x2(m, xm, __vmaxu2(p, xp - m));   // min(x + lim, max(p, x - lim))
 }
 
