@@ -29,7 +29,8 @@ SELECTION = ("find_dir or filter_parity or filter_every_strength or filter_extre
              "or filter_batch_mixed or filter_coded or filter_chroma_formats "
              "or search_parity or search_every_launch or search_preset_refinement "
              "or search_coded_parity or search_eq14 or search_formats or search_subset "
-             "or search_coded_formats or search_444 or filter_444 or consecutive_frames")
+             "or search_coded_formats or search_444 or filter_444 or consecutive_frames "
+             "or filter_rounds")
 
 
 @pytest.fixture(scope="module")

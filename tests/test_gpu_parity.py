@@ -170,6 +170,55 @@ def test_filter_batch_mixed(cdef, ctx, ref):
         _assert_frames_equal(o.to_numpy(), ref.filter_frame(*fr.rec, fr.bitdepth, fr.params))
 
 
+# Launches with more filter blocks than one round of persistent CTAs (4 per
+# SM), so that CTAs take several blocks from the work counter and the last
+# round is partial: frames with ragged right and bottom edges, coded maps,
+# 4:2:2 and 12-bit frames, against the oracle.
+@pytest.mark.parametrize("w,h,bd,fmt,with_map", [
+    (2600, 1096, 10, 420, False), (2600, 1096, 8, 420, True), (2600, 1096, 8, 422, False),
+    (2600, 1096, 12, 420, False)])
+def test_filter_rounds_parity(cdef, ctx, ref, w, h, bd, fmt, with_map):
+    from paper_1602_05975_gb300 import synth
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert -(-w // 64) * -(-h // 64) > 4 * sms   # more blocks than one round
+    rng = np.random.default_rng(w + h + bd + fmt)
+    planes = synth.make_frame(w, h, bd, 32, seed=990 + bd + fmt, chroma=fmt).rec
+    params = synth.random_params(rng, w, h)
+    params[..., 5] = rng.integers(0, 4, params.shape[:2])
+    coded = (rng.random((h // 8, w // 8)) < 0.6).astype(np.uint8) if with_map else None
+    ctx.set_overlap(False)
+    inp = cdef.frame_from_numpy(planes, bd)
+    out = cdef.alloc_frame(w, h, bd, fill=0, chroma=fmt)
+    prm = cdef.params_tensor(params)
+    if with_map:
+        cdef.cdef_filter_frame_coded(ctx, inp, prm, torch.from_numpy(coded.reshape(-1)).cuda(), out)
+    else:
+        cdef.cdef_filter_frame(ctx, inp, prm, out)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    _assert_frames_equal(out.to_numpy(), ref.filter_frame_format(*planes, bd, params, fmt, coded))
+
+
+def test_filter_rounds_batch(cdef, ctx, ref):
+    """One launch over frames whose blocks together exceed one round of CTAs:
+    the partial last round falls in the last frames of the batch."""
+    from paper_1602_05975_gb300 import synth
+    specs = [(1280, 720, 10), (1288, 728, 8), (1280, 720, 10), (648, 360, 8)]
+    frames, ins, outs, prms = [], [], [], []
+    for k, (w, h, bd) in enumerate(specs):
+        fr = synth.make_frame(w, h, bd, 32, seed=1000 + k)
+        frames.append(fr)
+        ins.append(cdef.frame_from_numpy(fr.rec, bd))
+        outs.append(cdef.alloc_frame(w, h, bd, fill=0))
+        prms.append(cdef.params_tensor(fr.params))
+    ctx.set_overlap(False)
+    cdef.cdef_filter_frames(ctx, ins, prms, outs)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    for fr, o in zip(frames, outs):
+        _assert_frames_equal(o.to_numpy(), ref.filter_frame(*fr.rec, fr.bitdepth, fr.params))
+
+
 def test_invalid_params_flagged(cdef, ctx):
     from paper_1602_05975_gb300 import synth
     fr = synth.make_frame(128, 64, 8, 32, seed=7)
