@@ -544,11 +544,14 @@ int cdef_debug_checks(cdef_ctx *ctx, int64_t *faults, int32_t clear);
  * chains per thread on 4 CTAs of 256 threads per SM; a step is the tap's 6
  * ALU operations (four packed 16-bit min/max/add-min, the shift and its
  * per-lane mask) and 2 multiply-adds (mix 0), or five ALU operations alone
- * (mix 1).
+ * (mix 1).  Mixes 2-6 measure the pipes apart, 4 instructions a step: 4
+ * integer multiply-adds (2), 4 multiplies-high (3), 2 packed 16-bit maxima
+ * and 2 multiply-adds (4), 2 logic operations and 2 multiply-adds (5), 4
+ * fp32 FMAs (6).
  *   lane_instr_per_s : HOST output, lane instructions per second (warp
  *                      instructions x 32), from CUDA events around the
  *                      launch after one warm-up launch
- * Synchronises `cuda_stream`.  CDEF_ERR_ARG for mix not 0/1 or iters
+ * Synchronises `cuda_stream`.  CDEF_ERR_ARG for mix outside 0..6 or iters
  * outside 1..2^20; CDEF_ERR_CUDA, CDEF_ERR_NOMEM on a runtime failure. */
 int cdef_probe_int_mix(cdef_ctx *ctx, int32_t mix, int32_t iters, double *lane_instr_per_s,
                        void *cuda_stream);

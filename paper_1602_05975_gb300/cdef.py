@@ -576,8 +576,10 @@ def debug_checks(ctx, clear: bool = True):
 
 def probe_int_mix(ctx, mix: int = 0, iters: int = 4096, stream=None) -> float:
     """Measurement aid: lane instructions per second of the filter's tap
-    mix (mix 0) or of its integer-ALU operations alone (mix 1) on ctx's
-    device."""
+    mix (mix 0), of its integer-ALU operations alone (mix 1), or of the
+    single-pipe mixes 2-6 (integer multiply-adds, multiplies-high, packed
+    maxima with multiply-adds, logic operations with multiply-adds, fp32
+    FMAs) on ctx's device."""
     r = C.c_double(0.0)
     _check(load().cdef_probe_int_mix(ctx.handle, int(mix), int(iters), C.byref(r),
                                      _stream_ptr(stream)), "cdef_probe_int_mix")

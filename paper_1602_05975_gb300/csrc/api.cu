@@ -1195,7 +1195,7 @@ int cdef_debug_checks(cdef_ctx *ctx, int64_t *faults, int32_t clear)
 int cdef_probe_int_mix(cdef_ctx *ctx, int32_t mix, int32_t iters, double *lane_instr_per_s,
                        void *cuda_stream)
 {
-    if (!ctx || !lane_instr_per_s || (mix != 0 && mix != 1) || iters < 1 || iters > (1 << 20))
+    if (!ctx || !lane_instr_per_s || mix < 0 || mix > 6 || iters < 1 || iters > (1 << 20))
         return CDEF_ERR_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return CDEF_ERR_CUDA;

@@ -31,6 +31,13 @@ def test_probe_rates_are_plausible(cdef):
         assert 0.1 * issue_limit < alu <= 0.55 * issue_limit
         # the multiply-adds of the tap mix issue beside the ALU operations
         assert mix > alu
+        # the single-pipe mixes: every rate within the issue limit; fp32 FMAs
+        # (two pipes) faster than integer multiply-adds (one), and
+        # multiplies-high slower than multiply-adds
+        rates = [cdef.probe_int_mix(ctx, m) for m in range(2, 7)]
+        assert all(0.05 * issue_limit < r <= 1.05 * issue_limit for r in rates)
+        imad, hi, fma = rates[0], rates[1], rates[4]
+        assert fma > imad > hi
     finally:
         ctx.close()
 
@@ -38,7 +45,7 @@ def test_probe_rates_are_plausible(cdef):
 def test_probe_rejects_bad_arguments(cdef):
     ctx = cdef.Context(0)
     try:
-        for mix, iters in ((2, 16), (-1, 16), (0, 0), (0, 1 << 21)):
+        for mix, iters in ((7, 16), (-1, 16), (0, 0), (0, 1 << 21)):
             with pytest.raises(cdef.CdefError):
                 cdef.probe_int_mix(ctx, mix, iters)
     finally:
