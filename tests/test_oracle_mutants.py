@@ -51,6 +51,10 @@ MUTANTS = [
      "int dd = c == 0 ? (d + 2) % 8 : (d + 6) % 8;",
      "int dd = c == 0 ? (d + 2) % 8 : (d + 4) % 8;",
      "tap_geometry or brute_force"),
+    ("Fig. 3 (reading R8): one direction's near tap off its line (d = 1 at (-1, 1))",
+     "    {{0, 1}, {-1, 2}},\n",
+     "    {{-1, 1}, {-1, 2}},\n",
+     "dihedral"),
     ("eq. 15: greedy ties go to the highest preset index (reading R16)",
      "            if (best_t < 0 || tot < best_total) {\n                best_t = t;\n                best_total = tot;\n            }\n        }\n        presets[n - 1] = best_t;",
      "            if (best_t < 0 || tot <= best_total) {\n                best_t = t;\n                best_total = tot;\n            }\n        }\n        presets[n - 1] = best_t;",

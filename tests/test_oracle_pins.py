@@ -85,6 +85,27 @@ def test_direction_angles(ref):
         assert abs(perp - 90.0) < 1e-6 or abs(perp - 90.0) < 5.0
 
 
+def test_direction_costs_dihedral_symmetry(ref):
+    """The eight directions are a symmetric fan (Fig. 1: d = 0 at 45
+    degrees, 22.5-degree steps): transposing a block maps the lines of d
+    onto those of (8 - d) mod 8, mirroring its columns onto those of
+    (4 - d) mod 8, and a half turn maps every direction's lines onto
+    themselves, so the costs s_d permute exactly (a line formula wrong for
+    one direction, or a floor where its mirror image takes a ceiling, breaks
+    this)."""
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        x = rng.integers(-128, 128, (8, 8))
+        s = ref.direction_costs(x)
+        st = ref.direction_costs(x.T)
+        sf = ref.direction_costs(x[:, ::-1])
+        sr = ref.direction_costs(x[::-1, ::-1])
+        for d in range(8):
+            assert st[(8 - d) % 8] == s[d]
+            assert sf[(4 - d) % 8] == s[d]
+            assert sr[d] == s[d]
+
+
 # --------------------------------------------------------------------------
 # Section 2: costs, eq. 1-5, Algorithm 1
 # --------------------------------------------------------------------------
@@ -416,6 +437,33 @@ def test_tap_geometry_and_weights(ref):
         assert set(secw) == expect and len(secw) == 8
         for (dr, dc), wt in secw.items():
             assert wt == (2 if max(abs(dr), abs(dc)) == 1 else 1)
+
+
+@pytest.mark.parametrize("bd", [8, 10])
+def test_filter_frame_dihedral_symmetry(ref, bd):
+    """Figs. 3-4 (figures missing) and R8: the taps of each direction are
+    those of its mirror images, so filtering a transposed (or mirrored)
+    frame with the correspondingly mapped directions, contrasts and
+    per-block parameters gives the transposed (mirrored) output, sample for
+    sample, luma and 4:2:0 chroma, frame edges included.  A tap offset wrong
+    in one direction's table fails it."""
+    from paper_1602_05975_gb300 import synth
+    rng = np.random.default_rng(30 + bd)
+    h, w = 128, 192
+    y, u, v = synth.random_frame_planes(rng, w, h, bd)
+    prm = synth.random_params(rng, w, h)
+    dirs = rng.integers(0, 8, (h // 8, w // 8)).astype(np.uint8)
+    var = rng.integers(0, 1 << 20, (h // 8, w // 8)).astype(np.int32)
+    oy, ou, ov = ref.filter_frame(y, u, v, bd, prm, dirs, var)
+    # transpose: d -> (8 - d) mod 8
+    ty, tu, tv = ref.filter_frame(y.T, u.T, v.T, bd, prm.transpose(1, 0, 2),
+                                  ((8 - dirs.astype(int)) % 8).astype(np.uint8).T, var.T)
+    assert (ty == oy.T).all() and (tu == ou.T).all() and (tv == ov.T).all()
+    # mirrored columns: d -> (4 - d) mod 8
+    fy, fu, fv = ref.filter_frame(y[:, ::-1], u[:, ::-1], v[:, ::-1], bd, prm[:, ::-1],
+                                  ((4 - dirs.astype(int)) % 8).astype(np.uint8)[:, ::-1],
+                                  var[:, ::-1])
+    assert (fy == oy[:, ::-1]).all() and (fu == ou[:, ::-1]).all() and (fv == ov[:, ::-1]).all()
 
 
 def test_zero_strength_identity(ref):
