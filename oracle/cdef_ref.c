@@ -24,10 +24,13 @@
  *   R16 greedy order and tie-breaks of the preset search
  *
  * Parity status: cdef_ref_line_number (R1) is pinned only through the counts
- * and cardinalities the paper prints and through geometric properties; the
+ * and cardinalities the paper prints and through geometric properties (the
+ * angles, and the costs permuting under the block's symmetries); the
  * direction numbering beyond d = 0/1 is unpinned.  The tap positions (R8)
- * are pinned to R1's geometry by tests, and the secondary weights and the
- * sixteenths normalisation (R9) are parity unpinned: their figure is missing.
+ * are pinned to R1's geometry and to the same symmetries by tests.  The
+ * secondary weights and the sixteenths normalisation (R9) are pinned only
+ * by section 3.2's statement that all the weights together exceed unity;
+ * otherwise they are parity unpinned: their figure is missing.
  */
 #include "cdef_ref.h"
 

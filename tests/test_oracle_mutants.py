@@ -55,6 +55,10 @@ MUTANTS = [
      "    {{0, 1}, {-1, 2}},\n",
      "    {{-1, 1}, {-1, 2}},\n",
      "dihedral"),
+    ("Fig. 4 (reading R9): the secondary weights summing to less (1, 1 instead of 2, 1)",
+     "static const int sec_weight[2] = {2, 1};",
+     "static const int sec_weight[2] = {1, 1};",
+     "exceed_unity"),
     ("eq. 15: greedy ties go to the highest preset index (reading R16)",
      "            if (best_t < 0 || tot < best_total) {\n                best_t = t;\n                best_total = tot;\n            }\n        }\n        presets[n - 1] = best_t;",
      "            if (best_t < 0 || tot <= best_total) {\n                best_t = t;\n                best_total = tot;\n            }\n        }\n        presets[n - 1] = best_t;",

@@ -520,6 +520,23 @@ def test_clip_to_taps(ref):
         assert ref.filter_sample(plane, 4, 4, d, e) == 101
 
 
+def test_weights_exceed_unity(ref):
+    """Section 3.2: the primary and secondary weights together exceed unity,
+    so without the clip a pixel can move by more than any contributing
+    neighbour differs from it.  Every tap one step delta above x, except the
+    far primary tap of d = 2 (along the row), set so far above that f = 0
+    for it while it keeps the clip range open: y moves by more than delta
+    (round(22 delta / 16) under the weights read from Figs. 3-4)."""
+    for delta in (2, 4):
+        plane = np.full((9, 9), 100 + delta, np.uint16)
+        plane[4, 4] = 100
+        plane[4, 6] = 250
+        e = ref.block_params(14, 4, 6, False, 8, 2 ** 31 - 1)
+        y = ref.filter_sample(plane, 4, 4, 2, e)
+        assert y - 100 > delta
+        assert y - 100 == ref.round16(22 * delta)
+
+
 def test_out_of_frame_taps_are_ignored(ref):
     """Section 3.1: a tap outside the frame is ignored (f = 0, not in the
     clip range).  Ignoring it is the same as an in-frame tap equal to the
